@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Throughput of the Jacobi-PCA hot path on scene-shaped cubes (one JSON line).
+
+Workload (one step): the two scene-shaped cubes of the paper's evaluation
+(610x340 pixels x 103 bands and 512x217 pixels x 224 bands, FP32, 12-endmember
+mixtures, k = 10, tol 1e-10, 30 sweeps max), each fitted end to end: band
+means + covariance, Jacobi eigen-decomposition, sort/sign, projection.
+
+Metric: Mpixel-bands/s = sum(N*B) / step time.  `value` is the mixed form
+(tensor-core covariance + FP64 refinement) with inputs resident in HBM; the
+plain FP32 form is measured beside it, each with its error against the FP64
+oracle.  The L2 is flushed (256 MiB write) before every timed step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With torchrun (N > 1) every rank fits its own copy of the workload (weak
+scaling, no data-path collective); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PCA Mpixel-bands/s end-to-end, mixed vs FP32 at stated error; % of roofline"
+UNIT = "Mpixel-bands/s"
+WORKLOAD = "paper-scene cubes 610x340x103 + 512x217x224, FP32, k=10"
+SM_LANES_FP32 = 128          # FP32 lanes per SM (sm_103a)
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="mix")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """Max of a host float over all ranks (the step time of the slowest rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(units_per_rank_step: float, steps: int, max_seconds: float, world: int) -> float:
+    """Whole-job throughput: units all ranks processed / the slowest rank's time."""
+    return units_per_rank_step * steps * world / max_seconds / 1e6
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def profiled_traffic(kernel: str):
+    """dram bytes per launch recorded in profiles/<kernel>*.md ('traffic_bytes_per_launch: X')."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for name in sorted(os.listdir(d)):
+        if name.startswith(kernel) and name.endswith(".md"):
+            m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", open(os.path.join(d, name)).read())
+            if m:
+                return float(m.group(1))
+    return None
+
+
+def jacobi_flops(B: int, sweeps: int) -> float:
+    """Algorithmic FP32 flops of the Jacobi kernel: every parallel step rotates the
+    B'(B'+1)/2 upper-triangle entries by their row pair and their column pair
+    (3 flops each side: c*a + s*b), B' steps per sweep."""
+    Bp = B + (B & 1)
+    return float(sweeps) * Bp * 3.0 * Bp * (Bp + 1)
+
+
+# ------------------------------------------------------------------ reference arm (oracle)
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    threads = oracle.set_threads(0)
+    cubes = synth.paper_scenes()
+    units = sum(c.N * c.B for c in cubes)
+    # bound the run: sample the pixels if one full step would take too long
+    t0 = time.perf_counter()
+    for c in cubes:
+        oracle.pca_fit(c.Y, c.k, tol=c.tol, sweeps_max=c.sweeps_max)
+    t_full = time.perf_counter() - t0
+    frac = 1.0
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    if t_full > budget:
+        frac = max(0.05, budget / t_full)
+    sample = [c.Y[: max(2, int(c.N * frac))] for c in cubes]
+    units_s = sum(s.shape[0] * s.shape[1] for s in sample)
+    for _ in range(args.warmup):
+        for c, Y in zip(cubes, sample):
+            oracle.pca_fit(Y, c.k, tol=c.tol, sweeps_max=c.sweeps_max)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for c, Y in zip(cubes, sample):
+            oracle.pca_fit(Y, c.k, tol=c.tol, sweeps_max=c.sweeps_max)
+    dt = time.perf_counter() - t0
+    value = units_s * args.steps / dt / 1e6
+    samp = ("full workload" if frac == 1.0 else
+            f"first {frac:.3f} of each cube's pixels (all bands), Jacobi unchanged")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "units_per_step": units},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": samp, "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return rc
+
+    import torch
+
+    import paper_2403_18321_gb300 as g
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g.load()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    cubes = synth.paper_scenes()
+    units = sum(c.N * c.B for c in cubes)
+    Yd = [torch.from_numpy(c.Y).to(dev) for c in cubes]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def setup(prec):
+        ws = [g.make_workspace(c.N, c.B, c.k, 0, prec, dev) for c in cubes]
+        outs = [(torch.empty(c.B, dtype=torch.float64, device=dev),
+                 torch.empty(c.B, dtype=torch.float64, device=dev),
+                 torch.empty(c.B, c.B, dtype=torch.float64, device=dev),
+                 torch.empty(c.N, c.k, dtype=torch.float32, device=dev)) for c in cubes]
+        return ws, outs
+
+    def step(prec, ws, outs, Ys=None):
+        Ys = Yd if Ys is None else Ys
+        for c, Y, w, o in zip(cubes, Ys, ws, outs):
+            g.fit(Y, c.k, tol=c.tol, sweeps_max=c.sweeps_max, precision=prec, out=o, workspace=w,
+                  sync=False)
+
+    def timed(prec, steps, warmup, with_profile=False, sampler=None):
+        ws, outs = setup(prec)
+        for _ in range(warmup):
+            step(prec, ws, outs)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        if with_profile:
+            g.profile(True)
+        total = 0.0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            for _ in range(steps):
+                flush.fill_(1)
+                e0.record()
+                step(prec, ws, outs)
+                e1.record()
+                e1.synchronize()
+                total += e0.elapsed_time(e1) / 1e3
+        stages = g.profile_collect() if with_profile else []
+        if with_profile:
+            g.profile(False)
+        torch.cuda.synchronize()
+        barrier(world)
+        infos = []
+        for c, Y, w, o in zip(cubes, Yd, ws, outs):
+            infos.append(g.fit(Y, c.k, tol=c.tol, sweeps_max=c.sweeps_max, precision=prec, out=o,
+                               workspace=w, sync=True)[4])
+        res = [tuple(t.cpu().numpy() for t in o) for o in outs]
+        return total, stages, infos, res
+
+    peaks, peak_src = load_peaks()
+    sampler = ClockSampler(local)
+    t_mix, stages, infos_mix, res_mix = timed(args.precision, args.steps, args.warmup, True, sampler)
+    t_mix = max_over_ranks(t_mix, world)
+    value = aggregate(units, args.steps, t_mix, world)
+    t_p32, _, infos_p32, res_p32 = timed("p32", args.steps, args.warmup)
+    t_p32 = max_over_ranks(t_p32, world)
+    value_p32 = aggregate(units, args.steps, t_p32, world)
+
+    # ---- per-stage times over the timed region (events on the launching stream)
+    nfit = len(cubes)
+    per_cube = [[r for i, r in enumerate(stages) if i % nfit == j] for j in range(nfit)]
+    stage_ms = {s: float(sum(np.mean([r[s] for r in pc]) for pc in per_cube if pc))
+                for s in g.STAGES}
+    dom = max(stage_ms, key=stage_ms.get)
+    roof = None
+    clocks = sampler.summary()
+    if dom == "jacobi":
+        # one launch per cube; report the larger-B cube's launch (the dominant one)
+        j = int(np.argmax([c.B for c in cubes]))
+        c = cubes[j]
+        ms = float(np.mean([r["jacobi"] for r in per_cube[j]]))
+        flops = jacobi_flops(c.B, infos_mix[j]["sweeps"])
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = SM_LANES_FP32 * 2 * mhz * 1e6 / 1e9          # GFLOP/s of the one SM the kernel uses
+        ach = flops / (ms / 1e3) / 1e9
+        roof = {"kernel": "k_jacobi", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "GFLOP/s", "frac": ach / peak,
+                "peak_basis": f"FP32 SIMT of 1 SM ({SM_LANES_FP32} lanes x 2 x {mhz:.0f} MHz; "
+                              f"the kernel is one CTA by design), {peak_src} clock",
+                "frac_of_gpu": ach / (peak * 152),
+                "traffic": profiled_traffic("k_jacobi"),
+                "launch_ms": ms, "cube": c.name, "sweeps": infos_mix[j]["sweeps"]}
+    else:
+        key = {"covariance": "k_syrk_tc", "project": "k_project"}.get(dom, dom)
+        byts = sum(c.N * c.B * 4 for c in cubes) / nfit
+        ms = stage_ms[dom] / nfit
+        ach = byts / (ms / 1e3) / 1e9
+        roof = {"kernel": key, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "peak_basis": peak_src,
+                "traffic": profiled_traffic(key), "launch_ms": ms}
+    # covariance and projection kernels against the HBM roofline (cube bytes per launch)
+    hbm = {}
+    for s, key in (("covariance", "k_syrk_tc"), ("project", "k_project")):
+        per = []
+        for j, c in enumerate(cubes):
+            ms = float(np.mean([r[s] for r in per_cube[j]]))
+            byts = c.N * c.B * 4 + (c.N * c.k * 4 if s == "project" else 0)
+            per.append({"cube": c.name, "ms": ms, "GB/s": byts / (ms / 1e3) / 1e9,
+                        "frac": byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]})
+        hbm[key] = per
+
+    # ---- errors against the oracle, and the CPU baseline (rank 0, N = 1 only)
+    errors = {}
+    cpu = None
+    if rank == 0:
+        import oracle
+        threads = oracle.set_threads(0)
+        t0 = time.perf_counter()
+        refs = [oracle.pca_fit(c.Y, c.k, tol=1e-14) for c in cubes]
+        t_ref_first = time.perf_counter() - t0
+        for name, res in (("mix", res_mix), ("p32", res_p32)):
+            e = []
+            for c, r, ref in zip(cubes, res, refs):
+                lam = r[1]
+                rel = np.abs(lam[:c.k] - ref["lam"][:c.k]) / np.abs(ref["lam"][:c.k])
+                e.append(float(rel.max()))
+            errors[name] = {"eig_rel_err_topk_max": max(e)}
+        if world == 1 and not args.no_cpu_baseline:
+            reps, t_cpu = 0, 0.0
+            while reps < 1 or (t_cpu < 10.0 and reps < 5):
+                t0 = time.perf_counter()
+                for c in cubes:
+                    oracle.pca_fit(c.Y, c.k, tol=c.tol, sweeps_max=c.sweeps_max)
+                t_cpu += time.perf_counter() - t0
+                reps += 1
+            cpu = {"value": units * reps / t_cpu / 1e6, "unit": UNIT, "cores": threads,
+                   "kind": "oracle",
+                   "sample": f"full workload (both cubes, all four stages) x {reps}, "
+                             f"FP64, OpenMP on the pixel loops, serial Jacobi"}
+
+    # ---- end to end from pinned host buffers through the public API
+    e2e = None
+    if not args.no_e2e:
+        Yh = [torch.from_numpy(c.Y).pin_memory() for c in cubes]
+        ws, outs = setup(args.precision)
+        host_out = [tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in o) for o in outs]
+        h2d = sum(y.numel() * 4 for y in Yh)
+        d2h = sum(sum(t.numel() * t.element_size() for t in o) for o in outs)
+
+        def e2e_step():
+            Ys = [y.to(dev, non_blocking=True) for y in Yh]
+            step(args.precision, ws, outs, Ys)
+            for o, h in zip(outs, host_out):
+                for t, th in zip(o, h):
+                    th.copy_(t, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        total = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0.record()
+            e2e_step()
+            e1.record()
+            e1.synchronize()
+            total += e0.elapsed_time(e1) / 1e3
+        total = max_over_ranks(total, world)
+        e2e = {"value": aggregate(units, args.steps, total, world), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": total / args.steps * 1e3}
+
+    launches = g.kernel_launches(args.precision, True) * len(cubes) * args.steps
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_mix / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3-f32acc+f32+f64" if args.precision == "mix" else args.precision,
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "cubes": [f"{c.name} N={c.N} B={c.B}" for c in cubes],
+                       "units_per_step": units, "l2": "flushed by a 256 MiB write before each step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "forms": {"mix": {"value": value, "ms_per_step": t_mix / args.steps * 1e3,
+                              "sweeps": [i["sweeps"] for i in infos_mix], **errors.get("mix", {})},
+                      "p32": {"value": value_p32, "ms_per_step": t_p32 / args.steps * 1e3,
+                              "sweeps": [i["sweeps"] for i in infos_p32], **errors.get("p32", {})}},
+            "stage_ms_per_step": stage_ms, "roofline": roof, "hbm_kernels": hbm,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
+if __name__ == "__main__":
+    sys.exit(main())

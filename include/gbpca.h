@@ -1,0 +1,150 @@
+/*
+ * gbpca.h -- C ABI of the GB300 (sm_103a) Jacobi-PCA library.
+ *
+ * The library computes the four stages of the paper's PCA (Algorithm 1 of
+ * "Jacobi-based PCA for hyperspectral dimensionality reduction", arXiv
+ * 2403.18321): per-band mean removal, the covariance C = X^T X / (N-1)
+ * (Sec. 4.2 stage 3), all eigen-pairs of C by cyclic Jacobi rotations
+ * (Sec. 2, Eqs. 2-10) sorted in descending order (Sec. 4.2 stage 4.3), and
+ * the projection of the centred cube onto the first k eigenvectors
+ * (Algorithm 1, stages 5-6).
+ *
+ * Conventions shared by every entry point
+ *   - The cube is N pixels x B bands, pixel-major ("band interleaved by
+ *     pixel"): value (n, b) at cube[n*B + b], element type given by
+ *     pca_dtype.  The paper's GPU code stores bands contiguously instead
+ *     (Sec. 4.2 data initialisation); this ABI takes the manycore layout of
+ *     Sec. 5 (image[i*BANDS + j]).
+ *   - Every pointer argument except `info` is a DEVICE pointer on the
+ *     current CUDA device, allocated and owned by the caller.  The library
+ *     allocates and frees nothing; all scratch lives in the caller's
+ *     workspace of pca_workspace_size() bytes.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is enqueued on it; nothing synchronises unless
+ *     `info` is non-NULL, in which case the call waits for the stream and
+ *     fills *info.
+ *   - Errors: argument errors are detected on the host before any launch
+ *     and returned as PCA_ERR_ARG / PCA_ERR_WORKSPACE.  A failed launch
+ *     returns PCA_ERR_CUDA.  Data-dependent outcomes (non-finite input,
+ *     Jacobi not converged) are written to a status word in the workspace;
+ *     they are returned only when `info` is given (else read them later
+ *     with pca_read_info).  No entry point traps, asserts or hangs on the
+ *     device.
+ */
+#ifndef GBPCA_H
+#define GBPCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PCA_OK = 0,
+  PCA_ERR_ARG = 1,        /* invalid argument (checked on the host)           */
+  PCA_ERR_NOCONV = 2,     /* Jacobi hit sweeps_max; outputs hold the last iterate */
+  PCA_ERR_NONFINITE = 3,  /* NaN or Inf in the cube; outputs are undefined      */
+  PCA_ERR_TIMEOUT = 4,    /* a bounded device wait gave up                      */
+  PCA_ERR_CUDA = 5,       /* a CUDA runtime call failed                          */
+  PCA_ERR_WORKSPACE = 6   /* workspace too small or misaligned                   */
+} pca_status;
+
+typedef enum { PCA_F32 = 0, PCA_BF16 = 1, PCA_F16 = 2 } pca_dtype;
+
+/*
+ * Precision forms.
+ *   PCA_PREC_P64: covariance accumulated in FP64 from exact products;
+ *     FP32 Jacobi followed by FP64 refinement iterations until the
+ *     eigen-decomposition is FP64-accurate.
+ *   PCA_PREC_P32: plain FP32 on the GPU (SIMT covariance, FP32 Jacobi, no
+ *     refinement).
+ *   PCA_PREC_MIX: covariance on the tensor cores from a two-term BF16
+ *     split of the centred cube (three products, FP32 accumulation per
+ *     chunk), FP32 Jacobi, one FP64 refinement iteration.
+ */
+typedef enum { PCA_PREC_P64 = 0, PCA_PREC_P32 = 1, PCA_PREC_MIX = 2 } pca_precision;
+
+typedef struct {
+  int status;        /* pca_status of the device-side work                    */
+  int sweeps;        /* Jacobi sweeps run                                      */
+  int refine_iters;  /* FP64 refinement iterations run                         */
+  int steps;         /* Jacobi parallel steps run (sweeps x steps per sweep)   */
+  double off_rel;    /* off(A)/||A||_F when the FP32 Jacobi stopped            */
+  double tol_used;   /* the stop threshold the FP32 Jacobi applied             */
+  double refine_res; /* largest |E_ij| of the last refinement correction (0 if none) */
+} pca_info;
+
+/*
+ * Bytes of device workspace pca_fit needs for this problem.  Returns 0 for
+ * arguments pca_fit would reject.  The workspace must be 256-byte aligned.
+ */
+size_t pca_workspace_size(int64_t N, int B, int k, pca_dtype dtype, pca_precision prec);
+
+/*
+ * pca_fit -- the whole hot path for one cube (Algorithm 1).
+ *
+ * cube       [N][B] device array of `dtype`, 16-byte aligned.
+ * N          pixels, N >= 2 (C is divided by N-1, Sec. 4.2 stage 3).
+ * B          bands, 2 <= B <= 232.
+ * k          components to project onto, 1 <= k <= min(B, 32).
+ * tol        Jacobi stop factor (Sec. 2, "until all off-diagonal elements are
+ *            smaller than the stop factor"), read as off(A) <= tol*||A||_F
+ *            with off(A) the Frobenius norm of the off-diagonal part.  The
+ *            FP32 Jacobi applies max(tol, 2^-22); *info reports it.  tol > 0.
+ * sweeps_max maximum Jacobi sweeps, >= 1.
+ * mu         [B] FP64 out: band means (Algorithm 1 stage 2).
+ * eigvals    [B] FP64 out: eigenvalues of C, descending; equal values keep
+ *            the order of the Jacobi's final diagonal positions.
+ * eigvecs    [B][B] FP64 out, row-major: column j is the unit eigenvector
+ *            of eigvals[j], its largest-magnitude entry (lowest row on
+ *            ties) positive.
+ * proj       [N][k] FP32 out: Q = (Y - 1 mu^T) eigvecs[:, :k].  May be NULL
+ *            to skip the projection.
+ * workspace  device scratch of ws_bytes >= pca_workspace_size(...) bytes.
+ * stream     cudaStream_t as void*.
+ * info       host pointer or NULL (see the conventions above).
+ * Returns PCA_OK when the work was enqueued (and, with info, finished
+ * without a data error), else a pca_status.
+ */
+int pca_fit(const void *cube, pca_dtype dtype, int64_t N, int B, int k, double tol,
+            int sweeps_max, pca_precision prec, double *mu, double *eigvals,
+            double *eigvecs, float *proj, void *workspace, size_t ws_bytes,
+            void *stream, pca_info *info);
+
+/*
+ * Waits for `stream` and copies the device-side outcome of the last
+ * pca_fit that used `workspace` into *info.  Returns info->status.
+ */
+int pca_read_info(const void *workspace, void *stream, pca_info *info);
+
+/* Static description of a status code. */
+const char *pca_status_string(int status);
+
+/* ABI version (major*100 + minor). */
+int pca_version(void);
+
+/* ---- instrumentation (no counterpart in the paper; used by the benchmark) */
+
+/* Number of kernels one pca_fit enqueues for this precision form. */
+int pca_kernel_launches(pca_precision prec, int with_projection);
+
+/*
+ * Per-stage timing.  pca_profile(1) makes every later pca_fit on the calling
+ * host thread record CUDA events on its stream around its eight stages
+ * (covariance, covariance finalisation, Jacobi, V replay, compaction,
+ * refinement, sort/sign, projection), up to 256 fits; pca_profile(0) stops.
+ * Both reset the record list and return the stage count (8).
+ * pca_profile_collect waits for the recorded events and writes, per fit
+ * r < max_records, the stage durations in ms to ms[r*8 + i]; returns the
+ * number of fits written.  Host memory only; no allocation on the device.
+ */
+int pca_profile(int enable);
+int pca_profile_collect(float *ms, int max_records);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBPCA_H */

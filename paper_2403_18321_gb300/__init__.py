@@ -1,0 +1,187 @@
+"""GB300 (sm_103a) Jacobi-PCA for hyperspectral cubes -- thin Python binding.
+
+Everything numeric runs in the CUDA library ``_lib/libgbpca.so`` behind the C
+ABI of ``include/gbpca.h``; this module only marshals arguments (PyTorch
+supplies device memory and the current stream).  There is no CPU path: if
+the library is missing or no GPU is present, calls raise.
+
+    mu, eigvals, eigvecs, proj, info = fit(cube, k=10)
+
+Stages (Algorithm 1 of the paper): band means, covariance X^T X/(N-1),
+cyclic Jacobi eigen-decomposition sorted in descending order, projection of
+the centred cube onto the first k eigenvectors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import _build
+
+__all__ = ["fit", "fit_host", "workspace_size", "load", "Info", "PCAError",
+           "PREC_P64", "PREC_P32", "PREC_MIX", "STATUS"]
+
+PREC_P64, PREC_P32, PREC_MIX = 0, 1, 2
+PRECISIONS = {"p64": PREC_P64, "p32": PREC_P32, "mix": PREC_MIX}
+STATUS = {0: "PCA_OK", 1: "PCA_ERR_ARG", 2: "PCA_ERR_NOCONV", 3: "PCA_ERR_NONFINITE",
+          4: "PCA_ERR_TIMEOUT", 5: "PCA_ERR_CUDA", 6: "PCA_ERR_WORKSPACE"}
+EXPORTS = ("pca_workspace_size", "pca_fit", "pca_read_info", "pca_status_string", "pca_version",
+           "pca_kernel_launches", "pca_profile", "pca_profile_collect")
+STAGES = ("covariance", "cov_finalize", "jacobi", "v_replay", "compact", "refine", "sort_sign",
+          "project")
+
+
+class PCAError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {what}")
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("sweeps", ctypes.c_int),
+                ("refine_iters", ctypes.c_int), ("steps", ctypes.c_int),
+                ("off_rel", ctypes.c_double), ("tol_used", ctypes.c_double),
+                ("refine_res", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = False):
+    """The loaded CUDA library (ctypes.CDLL).  Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, i, d, sz, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_int64
+    lib.pca_workspace_size.argtypes = [i64, i, i, i, i]
+    lib.pca_workspace_size.restype = sz
+    lib.pca_fit.argtypes = [P, i, i64, i, i, d, i, i, P, P, P, P, P, sz, P, ctypes.POINTER(Info)]
+    lib.pca_fit.restype = i
+    lib.pca_read_info.argtypes = [P, P, ctypes.POINTER(Info)]
+    lib.pca_read_info.restype = i
+    lib.pca_status_string.argtypes = [i]
+    lib.pca_status_string.restype = ctypes.c_char_p
+    lib.pca_version.restype = i
+    lib.pca_kernel_launches.argtypes = [i, i]
+    lib.pca_kernel_launches.restype = i
+    lib.pca_profile.argtypes = [i]
+    lib.pca_profile.restype = i
+    lib.pca_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_float), i]
+    lib.pca_profile_collect.restype = i
+    _lib = lib
+    return lib
+
+
+def _dtype_code(t):
+    import torch
+    codes = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
+    if t.dtype not in codes:
+        raise TypeError(f"cube dtype {t.dtype} not supported (float32, bfloat16, float16)")
+    return codes[t.dtype]
+
+
+def _prec_code(precision):
+    if isinstance(precision, str):
+        return PRECISIONS[precision.lower()]
+    return int(precision)
+
+
+def workspace_size(N: int, B: int, k: int, dtype_code: int = 0, precision="mix") -> int:
+    return int(load().pca_workspace_size(int(N), int(B), int(k), int(dtype_code),
+                                          _prec_code(precision)))
+
+
+@dataclass
+class Workspace:
+    """Reusable device scratch for repeated fits of one problem shape."""
+    buf: object
+    nbytes: int
+
+
+def make_workspace(N, B, k, dtype_code=0, precision="mix", device=None):
+    import torch
+    n = workspace_size(N, B, k, dtype_code, precision)
+    if n == 0:
+        raise PCAError(1, "pca_workspace_size rejected the shape")
+    buf = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
+    return Workspace(buf, n)
+
+
+def _ws_ptr(ws: Workspace) -> int:
+    p = ws.buf.data_ptr()
+    return (p + 255) & ~255
+
+
+def fit(cube, k: int, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
+        out=None, workspace: Workspace | None = None, project: bool = True,
+        sync: bool = True, stream=None):
+    """PCA of a device cube [N, B] (float32/bfloat16/float16, pixel-major).
+
+    Returns (mu [B] f64, eigvals [B] f64, eigvecs [B, B] f64, proj [N, k] f32 or None,
+    info dict or None).  With sync=False nothing waits for the GPU and info is None.
+    """
+    import torch
+    if not isinstance(cube, torch.Tensor) or not cube.is_cuda:
+        raise TypeError("cube must be a CUDA tensor")
+    if cube.dim() != 2 or not cube.is_contiguous():
+        raise ValueError("cube must be a contiguous [N, B] tensor")
+    N, B = cube.shape
+    dt = _dtype_code(cube)
+    prec = _prec_code(precision)
+    dev = cube.device
+    if out is None:
+        mu = torch.empty(B, dtype=torch.float64, device=dev)
+        ev = torch.empty(B, dtype=torch.float64, device=dev)
+        V = torch.empty(B, B, dtype=torch.float64, device=dev)
+        Q = torch.empty(N, k, dtype=torch.float32, device=dev) if project else None
+    else:
+        mu, ev, V, Q = out
+    if workspace is None:
+        workspace = make_workspace(N, B, k, dt, prec, dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    info = Info() if sync else None
+    rc = load().pca_fit(ctypes.c_void_p(cube.data_ptr()), dt, N, B, int(k), float(tol),
+                        int(sweeps_max), prec, ctypes.c_void_p(mu.data_ptr()),
+                        ctypes.c_void_p(ev.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                        ctypes.c_void_p(Q.data_ptr()) if Q is not None else None,
+                        ctypes.c_void_p(_ws_ptr(workspace)), workspace.nbytes,
+                        ctypes.c_void_p(st.cuda_stream),
+                        ctypes.byref(info) if info is not None else None)
+    if rc not in (0, 2) and not (rc == 3 and info is not None):
+        raise PCAError(rc, load().pca_status_string(rc).decode())
+    return mu, ev, V, Q, (info.as_dict() if info is not None else None)
+
+
+def kernel_launches(precision="mix", project: bool = True) -> int:
+    return int(load().pca_kernel_launches(_prec_code(precision), 1 if project else 0))
+
+
+def profile(enable: bool) -> None:
+    load().pca_profile(1 if enable else 0)
+
+
+def profile_collect(max_records: int = 256):
+    """List of dicts {stage: ms} for the fits recorded since profile(True)."""
+    buf = (ctypes.c_float * (max_records * len(STAGES)))()
+    n = load().pca_profile_collect(buf, max_records)
+    return [{s: float(buf[r * len(STAGES) + i]) for i, s in enumerate(STAGES)} for r in range(n)]
+
+
+def fit_host(cube_host, k: int, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
+             workspace: Workspace | None = None, device="cuda"):
+    """End-to-end from a (pinned) host cube: H2D copy, pca_fit, D2H of the results."""
+    import torch
+    d = cube_host.to(device, non_blocking=True)
+    mu, ev, V, Q, _ = fit(d, k, tol, sweeps_max, precision, workspace=workspace, sync=False)
+    outs = [t.to("cpu", non_blocking=True) for t in (mu, ev, V, Q) if t is not None]
+    torch.cuda.current_stream(d.device).synchronize()
+    return outs

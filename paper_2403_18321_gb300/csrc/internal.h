@@ -1,0 +1,96 @@
+// internal.h -- shared declarations of the sm_103a Jacobi-PCA kernels.
+// Not part of the public ABI (include/gbpca.h is).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gbpca.h"
+
+namespace gbpca {
+
+constexpr int kMaxB = 232;          // A (FP32, B' x B') must fit one SM's shared memory
+constexpr int kMaxK = 32;
+constexpr int kMaxPartials = 320;   // per-CTA covariance partial slots
+constexpr float kJacobiFloor = 2.384185791015625e-07f;  // 2^-22: FP32 Jacobi stop floor
+
+// Device-side outcome, first 256 bytes of the workspace.
+struct DevHeader {
+  int status;        // pca_status
+  int sweeps;
+  int steps;
+  int refine_iters;
+  int nonfinite;
+  int dummy_slot;    // slot of the padding index when B is odd, else -1
+  int pad0, pad1;
+  double off_rel;
+  double fro;
+  double tol_used;
+  double refine_res;
+  double delta;      // cluster threshold of the last refinement iteration
+};
+
+// Offsets (bytes) of every workspace region; all 256-byte aligned.
+struct Layout {
+  size_t hdr, shift, s1_part, s2_part, dvec, cov, diag32, log, v32, lam, vc, w, s, r, e, vk, muf;
+  size_t total;
+  int partials;      // number of covariance partial slots the SYRK uses
+  int s2_elems;      // packed upper-triangle entries per partial: B(B+1)/2
+  int s2_bytes_el;   // 4 (FP32 partials) or 8 (FP64 partials)
+};
+
+Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, int num_sms);
+
+__host__ __device__ inline int round_even(int b) { return b + (b & 1); }
+__host__ __device__ inline int64_t packed_index(int i, int j, int B) {  // i <= j
+  return (int64_t)i * B - (int64_t)i * (i - 1) / 2 + (j - i);
+}
+
+// ---------------------------------------------------------------- launchers
+// All return cudaError_t of the launch; none synchronises.
+
+// Covariance partials, SIMT: P32 (FP32 accumulate) or P64 (FP64 accumulate).
+// shift = first pixel; writes s1_part[G][B] (FP64) and s2_part[G][B(B+1)/2].
+cudaError_t launch_syrk_simt(const void* cube, pca_dtype dt, int64_t N, int B, bool fp64,
+                             float* shift, double* s1_part, void* s2_part, int partials,
+                             cudaStream_t st);
+
+// Covariance partials on the tensor cores (tcgen05, split-BF16, three products).
+cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
+                           double* s1_part, float* s2_part, int partials, DevHeader* hdr,
+                           cudaStream_t st);
+bool syrk_tc_supported(int B);
+
+// Sums the partials, applies the shift correction, writes mu (FP64), C (FP64, full
+// symmetric) and mu_f (FP32), flags non-finite sums in the header.
+cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const void* s2_part,
+                                bool fp64_partials, int partials, int64_t N, int B, double* mu,
+                                double* C, float* mu_f, double* dvec, DevHeader* hdr,
+                                cudaStream_t st);
+
+// FP32 odd-even Jacobi on one SM; logs (c, s) of every rotation.
+cudaError_t launch_jacobi(const double* C, int B, float tol32, int sweeps_max, float2* log,
+                          float* diag32, DevHeader* hdr, cudaStream_t st);
+
+// Replays the rotation log on the rows of V (starting from I) -> V32 [B'][B'].
+cudaError_t launch_vreplay(const float2* log, int B, const DevHeader* hdr, float* v32,
+                           cudaStream_t st);
+
+// Drops the padding slot: lam (FP64) [B] and Vc (FP64) [B][B] in slot order.
+cudaError_t launch_compact(const float* diag32, const float* v32, int B, DevHeader* hdr,
+                           double* lam, double* vc, cudaStream_t st);
+
+// One Newton-type refinement iteration of the eigen-decomposition in FP64.
+cudaError_t launch_refine(const double* C, int B, double* vc, double* lam, double* w, double* s,
+                          double* r, double* e, DevHeader* hdr, cudaStream_t st);
+
+// Sort descending, sign-normalise, write eigvals/eigvecs (FP64) and V_k (FP32).
+cudaError_t launch_sort_sign(const double* lam, const double* vc, int B, int k, double* eigvals,
+                             double* eigvecs, float* vk, DevHeader* hdr, cudaStream_t st);
+
+// Q = (Y - 1 mu^T) V_k, FP32.
+cudaError_t launch_project(const void* cube, pca_dtype dt, int64_t N, int B, int k,
+                           const float* mu_f, const float* vk, float* proj, cudaStream_t st);
+
+}  // namespace gbpca

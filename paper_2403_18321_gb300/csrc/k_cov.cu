@@ -1,0 +1,218 @@
+// k_cov.cu -- band means and covariance (Algorithm 1 stages 2-3; Sec. 4.2
+// stages 2 and 3) on SIMT cores, and the reduction of per-CTA partials.
+//
+// One pass over the cube.  Every partial slot g (a contiguous pixel range)
+// accumulates, for x = y - s with s the first pixel of the cube (a per-band
+// shift; any fixed s works),
+//     S1_g = sum_n x_n            (FP64, per band)
+//     S2_g = sum_n x_n x_n^T      (upper triangle, FP32 for P32 / FP64 for P64)
+// and the finalisation turns the totals into the paper's quantities:
+//     mu = s + S1/N,  C = (S2 - S1 S1^T / N) / (N - 1),
+// which equals X^T X/(N-1) with X = Y - 1 mu^T exactly in real arithmetic.
+// The shift keeps the summands centred near zero, so the correction term is
+// of the order of one band variance (no catastrophic cancellation) and the
+// cube is read once instead of twice (separate mean pass + covariance pass).
+#include "common.cuh"
+
+namespace gbpca {
+
+namespace {
+
+constexpr int kSyrkThreads = 256;
+constexpr int kChunk = 32;  // pixels staged in shared memory per iteration
+
+template <typename In>
+__device__ __forceinline__ float ld(const In* p) { return to_f32<In>(*p); }
+
+// Grid: x = partial slot (pixel range), y = tile group.  Each thread owns one
+// TM x TM tile of the upper block-triangle of S2.
+template <typename In, typename Acc, int TM>
+__global__ void __launch_bounds__(kSyrkThreads)
+k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, int Bt, int ntiles,
+            float* __restrict__ shift_out, double* __restrict__ s1_part,
+            Acc* __restrict__ s2_part, int s2_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Bpad = Bt * TM;
+  Acc* xs = reinterpret_cast<Acc*>(smem_raw);                   // [kChunk][Bpad]
+  float* sh = reinterpret_cast<float*>(xs + kChunk * Bpad);     // [Bpad] shift
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int64_t n0 = N * g / G, n1 = N * (g + 1) / G;
+
+  for (int b = tid; b < Bpad; b += kSyrkThreads) sh[b] = b < B ? ld(cube + b) : 0.f;
+  if (g == 0 && blockIdx.y == 0)
+    for (int b = tid; b < B; b += kSyrkThreads) shift_out[b] = ld(cube + b);
+
+  // tile of this thread: enumerate the upper block-triangle row by row
+  const int t = blockIdx.y * kSyrkThreads + tid;
+  int ti = -1, tj = -1;
+  if (t < ntiles) {
+    int rem = t;
+    for (int r = 0; r < Bt; ++r) {
+      const int len = Bt - r;
+      if (rem < len) { ti = r; tj = r + rem; break; }
+      rem -= len;
+    }
+  }
+  Acc acc[TM][TM];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) acc[i][j] = Acc(0);
+  double s1 = 0.0;  // band `tid` (block-row 0 of the grid only)
+  __syncthreads();
+
+  for (int64_t c0 = n0; c0 < n1; c0 += kChunk) {
+    const int cp = (int)((n1 - c0) < kChunk ? (n1 - c0) : kChunk);
+    for (int p = warp; p < kChunk; p += kSyrkThreads / 32) {
+      const In* row = cube + (c0 + p) * (int64_t)B;
+      for (int b = lane; b < Bpad; b += 32)
+        xs[p * Bpad + b] = (p < cp && b < B) ? Acc(ld(row + b)) - Acc(sh[b]) : Acc(0);
+    }
+    __syncthreads();
+    if (blockIdx.y == 0 && tid < B) {
+      Acc cs = Acc(0);
+      for (int p = 0; p < cp; ++p) cs += xs[p * Bpad + tid];
+      s1 += (double)cs;
+    }
+    if (ti >= 0) {
+      const Acc* xa = xs + ti * TM;
+      const Acc* xb = xs + tj * TM;
+      for (int p = 0; p < cp; ++p) {
+        Acc a[TM], bv[TM];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) { a[i] = xa[p * Bpad + i]; bv[i] = xb[p * Bpad + i]; }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TM; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+
+  if (blockIdx.y == 0 && tid < B) s1_part[(size_t)g * B + tid] = s1;
+  if (ti >= 0) {
+    Acc* out = s2_part + (size_t)g * s2_elems;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int r = ti * TM + i;
+#pragma unroll
+      for (int j = 0; j < TM; ++j) {
+        const int c = tj * TM + j;
+        if (r < B && c < B && r <= c) out[packed_index(r, c, B)] = acc[i][j];
+      }
+    }
+  }
+}
+
+template <typename In>
+cudaError_t syrk_simt_typed(const In* cube, int64_t N, int B, bool fp64, float* shift,
+                            double* s1_part, void* s2_part, int partials, cudaStream_t st) {
+  const int s2_elems = B * (B + 1) / 2;
+  if (fp64) {
+    constexpr int TM = 4;
+    const int Bt = (B + TM - 1) / TM, ntiles = Bt * (Bt + 1) / 2;
+    const int groups = (ntiles + kSyrkThreads - 1) / kSyrkThreads;
+    const size_t smem = (size_t)kChunk * Bt * TM * sizeof(double) + Bt * TM * sizeof(float);
+    auto kern = k_syrk_simt<In, double, TM>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(
+        cube, N, B, Bt, ntiles, shift, s1_part, (double*)s2_part, s2_elems);
+  } else {
+    constexpr int TM = 8;
+    const int Bt = (B + TM - 1) / TM, ntiles = Bt * (Bt + 1) / 2;
+    const int groups = (ntiles + kSyrkThreads - 1) / kSyrkThreads;
+    const size_t smem = (size_t)kChunk * Bt * TM * sizeof(float) + Bt * TM * sizeof(float);
+    auto kern = k_syrk_simt<In, float, TM>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(
+        cube, N, B, Bt, ntiles, shift, s1_part, (float*)s2_part, s2_elems);
+  }
+  return cudaGetLastError();
+}
+
+// d[b] = (sum_g S1_g[b]) / N, one warp per band (FP64 adds spread over SMs).
+__global__ void k_s1_reduce(const double* __restrict__ s1_part, int partials, int B, int64_t N,
+                            const float* __restrict__ shift, double* __restrict__ dvec,
+                            double* __restrict__ mu, float* __restrict__ mu_f,
+                            DevHeader* __restrict__ hdr) {
+  const int b = blockIdx.x, lane = threadIdx.x;
+  double s = 0.0;
+  for (int g = lane; g < partials; g += 32) s += s1_part[(size_t)g * B + b];
+  s = warp_sum(s);
+  if (lane == 0) {
+    const double d = s / (double)N;
+    const double m = (double)shift[b] + d;
+    dvec[b] = d;
+    mu[b] = m;
+    mu_f[b] = (float)m;
+    if (!isfinite(m)) { atomicOr(&hdr->nonfinite, 1); set_status(hdr, PCA_ERR_NONFINITE); }
+  }
+}
+
+// C_ij = (S2_ij - N d_i d_j) / (N - 1), S2 summed over the partials.
+// FP32 partials are summed with Kahan compensation (FP32 operations only).
+template <typename Acc>
+__global__ void k_cov_finalize(const Acc* __restrict__ s2_part, int partials, int s2_elems,
+                               int B, int64_t N, const double* __restrict__ dvec,
+                               double* __restrict__ C, DevHeader* __restrict__ hdr) {
+  const int i = blockIdx.y;
+  const int j = i + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B) return;
+  const int64_t e = packed_index(i, j, B);
+  double S2;
+  if constexpr (sizeof(Acc) == 4) {
+    float sum = 0.f, comp = 0.f;
+    for (int g = 0; g < partials; ++g) {
+      const float y = (float)s2_part[(size_t)g * s2_elems + e] - comp;
+      const float t = sum + y;
+      comp = (t - sum) - y;
+      sum = t;
+    }
+    S2 = (double)sum - (double)comp;
+  } else {
+    double sum = 0.0;
+    for (int g = 0; g < partials; ++g) sum += (double)s2_part[(size_t)g * s2_elems + e];
+    S2 = sum;
+  }
+  const double c = (S2 - (double)N * dvec[i] * dvec[j]) / (double)(N - 1);
+  C[(size_t)i * B + j] = c;
+  C[(size_t)j * B + i] = c;
+  if (!isfinite(c)) { atomicOr(&hdr->nonfinite, 1); set_status(hdr, PCA_ERR_NONFINITE); }
+}
+
+}  // namespace
+
+cudaError_t launch_syrk_simt(const void* cube, pca_dtype dt, int64_t N, int B, bool fp64,
+                             float* shift, double* s1_part, void* s2_part, int partials,
+                             cudaStream_t st) {
+  switch (dt) {
+    case PCA_F32:
+      return syrk_simt_typed((const float*)cube, N, B, fp64, shift, s1_part, s2_part, partials, st);
+    case PCA_BF16:
+      return syrk_simt_typed((const __nv_bfloat16*)cube, N, B, fp64, shift, s1_part, s2_part,
+                             partials, st);
+    case PCA_F16:
+      return syrk_simt_typed((const __half*)cube, N, B, fp64, shift, s1_part, s2_part, partials, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const void* s2_part,
+                                bool fp64_partials, int partials, int64_t N, int B, double* mu,
+                                double* C, float* mu_f, double* dvec, DevHeader* hdr,
+                                cudaStream_t st) {
+  k_s1_reduce<<<B, 32, 0, st>>>(s1_part, partials, B, N, shift, dvec, mu, mu_f, hdr);
+  const int s2_elems = B * (B + 1) / 2;
+  dim3 grid((B + 63) / 64, B);
+  if (fp64_partials)
+    k_cov_finalize<double><<<grid, 64, 0, st>>>((const double*)s2_part, partials, s2_elems, B, N,
+                                                dvec, C, hdr);
+  else
+    k_cov_finalize<float><<<grid, 64, 0, st>>>((const float*)s2_part, partials, s2_elems, B, N,
+                                               dvec, C, hdr);
+  return cudaGetLastError();
+}
+
+}  // namespace gbpca

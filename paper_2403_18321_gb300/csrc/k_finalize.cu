@@ -1,0 +1,169 @@
+// k_finalize.cu -- eigen-pair extraction, descending sort and sign rule
+// (Sec. 4.2 stage 4.3), and the projection of the centred cube onto the
+// first k eigenvectors (Algorithm 1 stages 5-6; Sec. 4.2 stage 5).
+#include "common.cuh"
+
+namespace gbpca {
+
+namespace {
+
+// One CTA.  Rank of eigenvalue j = number of eigenvalues that sort before it
+// (larger, or equal and at a lower position); no comparison sort needed for
+// B <= 232.  Then every output column is gathered and flipped so that its
+// largest-magnitude entry (lowest row on ties) is positive.
+__global__ void __launch_bounds__(256)
+k_sort_sign(const double* __restrict__ lam, const double* __restrict__ vc, int B, int k,
+            double* __restrict__ eigvals, double* __restrict__ eigvecs, float* __restrict__ vk) {
+  __shared__ int perm[kMaxB];
+  __shared__ double ls[kMaxB];
+  const int tid = threadIdx.x;
+  for (int j = tid; j < B; j += blockDim.x) { ls[j] = lam[j]; perm[j] = j; }
+  __syncthreads();
+  int rank = -1;
+  if (tid < B) {
+    const double lj = ls[tid];
+    rank = 0;
+    for (int i = 0; i < B; ++i) {
+      const double li = ls[i];
+      rank += (li > lj) || (li == lj && i < tid);
+    }
+  }
+  __syncthreads();
+  if (tid < B) perm[min(rank, B - 1)] = tid;
+  __syncthreads();
+  if (tid < B) {
+    const int r = tid, src = perm[r];
+    eigvals[r] = ls[src];
+    int im = 0;
+    double best = -1.0;
+    for (int i = 0; i < B; ++i) {
+      const double a = fabs(vc[(size_t)i * B + src]);
+      if (a > best) { best = a; im = i; }
+    }
+    const double sg = vc[(size_t)im * B + src] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < B; ++i) {
+      const double v = sg * vc[(size_t)i * B + src];
+      eigvecs[(size_t)i * B + r] = v;
+      if (r < k) vk[(size_t)i * k + r] = (float)v;
+    }
+  }
+}
+
+// Q[n][j] = sum_b (Y_nb - mu_b) V_bj, FP32, one pixel per thread.  V_k and mu
+// sit in shared memory; V_k rows are padded to KQ float4 groups so one
+// 16-byte load feeds four FMAs.
+constexpr int kProjThreads = 256;
+
+template <typename In, int KQ, bool kVec4>
+__global__ void __launch_bounds__(kProjThreads)
+k_project(const In* __restrict__ cube, int64_t N, int B, int k, const float* __restrict__ mu_f,
+          const float* __restrict__ vk, float* __restrict__ proj) {
+  extern __shared__ __align__(16) float sm[];
+  float4* v4 = reinterpret_cast<float4*>(sm);      // [B][KQ]
+  float* mus = sm + (size_t)B * KQ * 4;             // [B]
+  for (int e = threadIdx.x; e < B * KQ * 4; e += kProjThreads) {
+    const int b = e / (KQ * 4), j = e - b * (KQ * 4);
+    sm[e] = j < k ? vk[(size_t)b * k + j] : 0.f;
+  }
+  for (int b = threadIdx.x; b < B; b += kProjThreads) mus[b] = mu_f[b];
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * kProjThreads;
+  for (int64_t n = (int64_t)blockIdx.x * kProjThreads + threadIdx.x; n < N; n += stride) {
+    float4 acc[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const In* row = cube + n * (int64_t)B;
+    auto accum = [&](float x, int b) {
+      x -= mus[b];
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) {
+        const float4 v = v4[b * KQ + q];
+        acc[q].x = fmaf(x, v.x, acc[q].x);
+        acc[q].y = fmaf(x, v.y, acc[q].y);
+        acc[q].z = fmaf(x, v.z, acc[q].z);
+        acc[q].w = fmaf(x, v.w, acc[q].w);
+      }
+    };
+    if constexpr (kVec4) {
+      const float4* r4 = reinterpret_cast<const float4*>(row);
+      for (int b4 = 0; b4 < B / 4; ++b4) {
+        const float4 y = __ldg(r4 + b4);
+        accum(y.x, 4 * b4);
+        accum(y.y, 4 * b4 + 1);
+        accum(y.z, 4 * b4 + 2);
+        accum(y.w, 4 * b4 + 3);
+      }
+    } else {
+      for (int b = 0; b < B; ++b) accum(to_f32<In>(row[b]), b);
+    }
+    float* out = proj + n * (int64_t)k;
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+      const float vals[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (4 * q + t < k) out[4 * q + t] = vals[t];
+    }
+  }
+}
+
+template <typename In, int KQ>
+cudaError_t project_kq(const In* cube, int64_t N, int B, int k, const float* mu_f,
+                       const float* vk, float* proj, cudaStream_t st, bool vec4) {
+  const size_t smem = ((size_t)B * KQ * 4 + B) * sizeof(float);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (N + kProjThreads - 1) / kProjThreads;
+  const int blocks = (int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
+  if (vec4) {
+    auto kern = k_project<In, KQ, true>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<blocks, kProjThreads, smem, st>>>(cube, N, B, k, mu_f, vk, proj);
+  } else {
+    auto kern = k_project<In, KQ, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<blocks, kProjThreads, smem, st>>>(cube, N, B, k, mu_f, vk, proj);
+  }
+  return cudaGetLastError();
+}
+
+template <typename In>
+cudaError_t project_typed(const In* cube, int64_t N, int B, int k, const float* mu_f,
+                          const float* vk, float* proj, cudaStream_t st, bool vec4) {
+  const int kq = (k + 3) / 4;
+  switch (kq) {
+    case 1: return project_kq<In, 1>(cube, N, B, k, mu_f, vk, proj, st, vec4);
+    case 2: return project_kq<In, 2>(cube, N, B, k, mu_f, vk, proj, st, vec4);
+    case 3: return project_kq<In, 3>(cube, N, B, k, mu_f, vk, proj, st, vec4);
+    case 4: return project_kq<In, 4>(cube, N, B, k, mu_f, vk, proj, st, vec4);
+    case 5: return project_kq<In, 5>(cube, N, B, k, mu_f, vk, proj, st, vec4);
+    case 6: return project_kq<In, 6>(cube, N, B, k, mu_f, vk, proj, st, vec4);
+    case 7: return project_kq<In, 7>(cube, N, B, k, mu_f, vk, proj, st, vec4);
+    case 8: return project_kq<In, 8>(cube, N, B, k, mu_f, vk, proj, st, vec4);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_sort_sign(const double* lam, const double* vc, int B, int k, double* eigvals,
+                             double* eigvecs, float* vk, DevHeader* hdr, cudaStream_t st) {
+  (void)hdr;
+  k_sort_sign<<<1, 256, 0, st>>>(lam, vc, B, k, eigvals, eigvecs, vk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const void* cube, pca_dtype dt, int64_t N, int B, int k,
+                           const float* mu_f, const float* vk, float* proj, cudaStream_t st) {
+  const bool vec4 = dt == PCA_F32 && (B % 4) == 0 && ((uintptr_t)cube % 16) == 0;
+  switch (dt) {
+    case PCA_F32: return project_typed((const float*)cube, N, B, k, mu_f, vk, proj, st, vec4);
+    case PCA_BF16:
+      return project_typed((const __nv_bfloat16*)cube, N, B, k, mu_f, vk, proj, st, false);
+    case PCA_F16: return project_typed((const __half*)cube, N, B, k, mu_f, vk, proj, st, false);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gbpca

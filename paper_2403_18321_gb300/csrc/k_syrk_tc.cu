@@ -1,0 +1,396 @@
+// k_syrk_tc.cu -- covariance partials on the 5th-generation tensor cores
+// (tcgen05 + TMEM), the dense contraction of Algorithm 1 stage 3 (Sec. 4.2
+// stage 3 forms it with one cuBLAS SGEMM; here it is hand-written).
+//
+// One persistent CTA per SM walks a contiguous range of 32-pixel chunks:
+//   warp 0      TMA producer: cp.async.bulk of each chunk (pixel-major, a
+//               contiguous byte range of the cube) into a 4-stage FP32 ring;
+//   warps 2-9   converters: x = y - s (s = first pixel, a per-band shift),
+//               split into BF16 hi = bf16(x), lo = bf16(x - hi), written
+//               transposed ([band][pixel], K-major core-matrix layout) into
+//               a 2-stage operand ring; one extra operand row is all ones,
+//               so the same MMAs also produce the band sums S1 = sum x;
+//   warp 1      MMA issuer (one thread): D += hi hi^T + hi lo^T + lo hi^T
+//               for the upper block-triangle (row tile 0: bands 0-127 x all;
+//               row tile 1: bands 128-255 x bands 128-255) with FP32
+//               accumulation in TMEM;
+//   warps 2-5   epilogue: TMEM -> registers -> the CTA's partial slot
+//               (packed upper triangle, FP32) and S1 (FP64).
+// The partials are reduced and finalised by k_cov.cu exactly like the SIMT
+// forms.  Every mbarrier wait is bounded (one second of globaltimer); on
+// time-out the CTA records PCA_ERR_TIMEOUT, drains its MMAs, frees TMEM and
+// returns.
+#include "common.cuh"
+
+namespace gbpca {
+
+namespace {
+
+constexpr int kKC = 32;                 // pixels per chunk (K of one stage)
+constexpr int kStages = 4;              // FP32 TMA ring depth
+constexpr int kOpStages = 2;            // BF16 operand ring depth
+constexpr int kRows = 256;              // operand rows (bands, padded; ones row included)
+constexpr int kConvWarps = 8;
+constexpr int kThreads = (2 + kConvWarps) * 32;
+constexpr int kOpBytes = kRows * kKC * 2;        // one BF16 operand (hi or lo): 16 KB
+constexpr uint32_t kLBO = 128;                   // K-adjacent core matrices
+constexpr uint32_t kSBO = (kKC / 8) * 128;       // 8-row groups: 512 B
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s bound on every wait
+constexpr int kTmemCols = 512;
+
+struct __align__(8) SyncBlock {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t opfull[kOpStages];
+  uint64_t opempty[kOpStages];
+  uint64_t done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on time-out or when another role already aborted.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, SyncBlock* sb) {
+  if (mbar_try(b, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    if (mbar_try(b, parity)) return true;
+    if (*(volatile int*)&sb->abort) return false;
+    if (gtimer() - t0 > kWaitNs) {
+      atomicExch(&sb->abort, 1);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// K-major, no swizzle: core matrix = 8 rows x 16 bytes; LBO = K stride, SBO = row-group stride.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((kSBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  uint32_t r;  // low half = a, high half = b
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+__device__ __forceinline__ void unpack_bf16x2(uint32_t v, float& a, float& b) {
+  a = __uint_as_float(v << 16);
+  b = __uint_as_float(v & 0xffff0000u);
+}
+
+template <typename In>
+__device__ __forceinline__ float elem(const In* p) { return to_f32<In>(*p); }
+
+template <typename In>
+__global__ void __launch_bounds__(kThreads, 1)
+k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shift_out,
+          double* __restrict__ s1_part, float* __restrict__ s2_part, int s2_elems,
+          DevHeader* __restrict__ hdr) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int R16 = (B + 15) & ~15;     // first row after the padded bands = the ones row
+  const int stage_bytes_max = kKC * B * (int)sizeof(In);
+  const int stage_stride = (stage_bytes_max + 127) & ~127;
+  unsigned char* ops = smem;                                        // [kOpStages][hi|lo][kOpBytes]
+  unsigned char* stages = smem + kOpStages * 2 * kOpBytes;          // [kStages][stage_stride]
+  float* shs = reinterpret_cast<float*>(stages + kStages * stage_stride);  // [kRows]
+  SyncBlock* sb = reinterpret_cast<SyncBlock*>(shs + kRows);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int64_t nchunk_total = (N + kKC - 1) / kKC;
+  const int64_t c_begin = nchunk_total * g / G, c_end = nchunk_total * (g + 1) / G;
+  const int nch = (int)(c_end - c_begin);
+
+  const bool two_tiles = B > 128;
+  const int N0 = R16 + 16;                       // tile 0 columns: bands 0..R16-1 + ones block
+  const int N1 = two_tiles ? (R16 - 128 + 16) : 0;
+
+  // ---- set-up
+  for (int i = tid; i < kOpStages * 2 * kOpBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(ops)[i] = make_uint4(0, 0, 0, 0);
+  for (int b = tid; b < kRows; b += kThreads) shs[b] = b < B ? elem(cube + b) : 0.f;
+  if (g == 0)
+    for (int b = tid; b < B; b += kThreads) shift_out[b] = elem(cube + b);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) { mbar_init(&sb->full[s], 1); mbar_init(&sb->empty[s], kConvWarps); }
+    for (int s = 0; s < kOpStages; ++s) { mbar_init(&sb->opfull[s], kConvWarps); mbar_init(&sb->opempty[s], 1); }
+    mbar_init(&sb->done, 1);
+    sb->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&sb->tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = sb->tmem_base;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      for (int c = 0; c < nch; ++c) {
+        const int s = c % kStages;
+        if (!mbar_wait(&sb->empty[s], ((c / kStages) & 1) ^ 1, sb)) break;
+        const int64_t p0 = (c_begin + c) * kKC;
+        const int cp = (int)((N - p0) < kKC ? (N - p0) : kKC);
+        const uint32_t bytes = (uint32_t)(cp * B * (int)sizeof(In)) & ~15u;
+        mbar_expect_tx(&sb->full[s], bytes);
+        if (bytes) bulk_g2s(stages + s * stage_stride, cube + p0 * B, bytes, &sb->full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t ops_base = su32(ops);
+      const uint32_t id0 = idesc_bf16(N0), id1 = idesc_bf16(N1 > 0 ? N1 : 16);
+      bool issued = false;
+      for (int c = 0; c < nch; ++c) {
+        const int o = c % kOpStages;
+        if (!mbar_wait(&sb->opfull[o], (c / kOpStages) & 1, sb)) break;
+        tc_fence_after();
+        const uint32_t hi = ops_base + (uint32_t)(o * 2) * kOpBytes;
+        const uint32_t lo = hi + kOpBytes;
+#pragma unroll
+        for (int kk = 0; kk < kKC / 16; ++kk) {
+          const uint32_t ko = kk * 2 * kLBO;
+          const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+          // tile 0: rows 0..127 (A) x rows 0..N0-1 (B)
+          mma_bf16(tbase, sdesc(hi + ko), sdesc(hi + ko), id0, acc0);
+          mma_bf16(tbase, sdesc(hi + ko), sdesc(lo + ko), id0, 1u);
+          mma_bf16(tbase, sdesc(lo + ko), sdesc(hi + ko), id0, 1u);
+          if (two_tiles) {
+            const uint32_t r128 = (128 / 8) * kSBO;
+            const uint32_t t1 = tbase + (uint32_t)N0;
+            mma_bf16(t1, sdesc(hi + r128 + ko), sdesc(hi + r128 + ko), id1, acc0);
+            mma_bf16(t1, sdesc(hi + r128 + ko), sdesc(lo + r128 + ko), id1, 1u);
+            mma_bf16(t1, sdesc(lo + r128 + ko), sdesc(hi + r128 + ko), id1, 1u);
+          }
+        }
+        issued = true;
+        mma_commit(&sb->opempty[o]);  // operand stage free once these MMAs finished
+      }
+      (void)issued;
+      mma_commit(&sb->done);          // all MMAs of this CTA finished
+    }
+  } else {
+    // ---------------------------------------------------------- converters
+    const int ct = tid - 64;               // 0..255
+    const int items = (B + 1) * (kKC / 8); // (band or ones row) x 8-pixel group
+    for (int c = 0; c < nch; ++c) {
+      const int s = c % kStages, o = c % kOpStages;
+      const bool ok1 = mbar_wait(&sb->full[s], (c / kStages) & 1, sb);
+      const bool ok2 = ok1 && mbar_wait(&sb->opempty[o], ((c / kOpStages) & 1) ^ 1, sb);
+      if (!ok2) break;
+      const int64_t p0 = (c_begin + c) * kKC;
+      const int cp = (int)((N - p0) < kKC ? (N - p0) : kKC);
+      const int copied = (int)(((uint32_t)(cp * B * (int)sizeof(In)) & ~15u) / sizeof(In));
+      const In* st = reinterpret_cast<const In*>(stages + s * stage_stride);
+      const In* gsrc = cube + p0 * B;
+      unsigned char* hi = ops + (size_t)(o * 2) * kOpBytes;
+      unsigned char* lo = hi + kOpBytes;
+      for (int w = ct; w < items; w += kConvWarps * 32) {
+        const int pg = w / (B + 1);
+        const int b = w - pg * (B + 1);
+        uint32_t h[4], l[4];
+        int row;
+        if (b < B) {
+          row = b;
+          const float sh = shs[b];
+          float x[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int p = pg * 8 + i;
+            const int e = p * B + b;
+            float v = 0.f;
+            if (p < cp) v = (e < copied ? elem(st + e) : elem(gsrc + e)) - sh;
+            x[i] = v;
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            h[i] = pack_bf16x2(x[2 * i], x[2 * i + 1]);
+            float a, bb;
+            unpack_bf16x2(h[i], a, bb);
+            l[i] = pack_bf16x2(x[2 * i] - a, x[2 * i + 1] - bb);
+          }
+        } else {
+          row = R16;  // ones row: 1 for real pixels, 0 for the tail
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int p = pg * 8 + 2 * i;
+            h[i] = pack_bf16x2(p < cp ? 1.f : 0.f, p + 1 < cp ? 1.f : 0.f);
+            l[i] = 0u;
+          }
+        }
+        const int off = (row >> 3) * (int)kSBO + pg * 128 + (row & 7) * 16;
+        *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) { mbar_arrive(&sb->opfull[o]); mbar_arrive(&sb->empty[s]); }
+    }
+    // ---------------------------------------------------------- epilogue
+    if (warp >= 2 && warp < 6) {
+      const bool ok = mbar_wait(&sb->done, 0, sb) && !*(volatile int*)&sb->abort;
+      tc_fence_after();
+      const int q = warp & 3;          // TMEM lane quarter this warp may read
+      const int r = q * 32 + lane;     // accumulator row
+      const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+      float* out = s2_part + (size_t)g * s2_elems;
+      // tile 0: row r = band r, column j = band j (j < R16), column R16 = band sums
+      for (int j0 = 0; j0 < N0; j0 += 16) {
+        float v[16];
+        if (ok) tmem_ld16(tbase + lane_off + (uint32_t)j0, v);
+        else
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int j = j0 + i;
+          if (r < B && r < 128) {
+            if (j < B && j >= r) out[packed_index(r, j, B)] = v[i];
+            if (j == R16) s1_part[(size_t)g * B + r] = (double)v[i];
+          }
+        }
+      }
+      if (two_tiles) {
+        const int band = 128 + r;
+        for (int j0 = 0; j0 < N1; j0 += 16) {
+          float v[16];
+          if (ok) tmem_ld16(tbase + lane_off + (uint32_t)(N0 + j0), v);
+          else
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int jb = 128 + j0 + i;
+            if (band < B) {
+              if (jb < B && jb >= band) out[packed_index(band, jb, B)] = v[i];
+              if (jb == R16) s1_part[(size_t)g * B + band] = (double)v[i];
+            }
+          }
+        }
+      }
+      if (!ok && lane == 0) set_status(hdr, PCA_ERR_TIMEOUT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+template <typename In>
+cudaError_t syrk_tc_typed(const In* cube, int64_t N, int B, float* shift, double* s1_part,
+                          float* s2_part, int partials, DevHeader* hdr, cudaStream_t st) {
+  const int stage_stride = ((kKC * B * (int)sizeof(In)) + 127) & ~127;
+  const size_t smem = 1024 + (size_t)kOpStages * 2 * kOpBytes + (size_t)kStages * stage_stride +
+                      kRows * sizeof(float) + sizeof(SyncBlock);
+  auto kern = k_syrk_tc<In>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<partials, kThreads, smem, st>>>(cube, N, B, shift, s1_part, s2_part, B * (B + 1) / 2, hdr);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool syrk_tc_supported(int B) { return B >= 2 && B <= kMaxB; }
+
+cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
+                           double* s1_part, float* s2_part, int partials, DevHeader* hdr,
+                           cudaStream_t st) {
+  switch (dt) {
+    case PCA_F32:
+      return syrk_tc_typed((const float*)cube, N, B, shift, s1_part, s2_part, partials, hdr, st);
+    case PCA_BF16:
+      return syrk_tc_typed((const __nv_bfloat16*)cube, N, B, shift, s1_part, s2_part, partials, hdr,
+                           st);
+    case PCA_F16:
+      return syrk_tc_typed((const __half*)cube, N, B, shift, s1_part, s2_part, partials, hdr, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gbpca

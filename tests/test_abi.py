@@ -1,0 +1,51 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every entry
+point include/gbpca.h declares.  No compute call (no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbpca.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pca_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pca_fit", "pca_workspace_size", "pca_status_string", "pca_read_info"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2403_18321_gb300 import _build
+    lib_path = _build.build()
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in gbpca.h but not exported"
+
+
+def test_status_strings_and_version_need_no_gpu():
+    import paper_2403_18321_gb300 as g
+    lib = g.load(build_if_missing=True)
+    assert lib.pca_version() >= 100
+    for code in range(7):
+        assert lib.pca_status_string(code)
+    assert lib.pca_status_string(99) == b"unknown status"
+
+
+def test_binding_names_match_the_abi():
+    import paper_2403_18321_gb300 as g
+    assert set(g.EXPORTS) <= set(declared_functions())
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+    import paper_2403_18321_gb300 as g
+    with pytest.raises(TypeError):
+        g.fit(torch.zeros(10, 4), 2)
