@@ -56,8 +56,10 @@ typedef enum { PCA_F32 = 0, PCA_BF16 = 1, PCA_F16 = 2 } pca_dtype;
 /*
  * Precision forms.
  *   PCA_PREC_P64: covariance accumulated in FP64 from exact products;
- *     FP32 Jacobi followed by FP64 refinement iterations until the
- *     eigen-decomposition is FP64-accurate.
+ *     FP32 Jacobi followed by three FP64 refinement iterations (eigen-pairs
+ *     separated from the rest of the spectrum by more than about 1e-6 of
+ *     ||C|| come out FP64-accurate; tighter clusters keep FP32-level
+ *     accuracy of the cluster, at least 1e-7 ||C|| absolute).
  *   PCA_PREC_P32: plain FP32 on the GPU (SIMT covariance, FP32 Jacobi, no
  *     refinement).
  *   PCA_PREC_MIX: covariance on the tensor cores from a two-term BF16
@@ -112,6 +114,32 @@ int pca_fit(const void *cube, pca_dtype dtype, int64_t N, int B, int k, double t
             int sweeps_max, pca_precision prec, double *mu, double *eigvals,
             double *eigvecs, float *proj, void *workspace, size_t ws_bytes,
             void *stream, pca_info *info);
+
+/*
+ * The stages of pca_fit as separate calls (same conventions, same workspace
+ * size as pca_fit for the same N, B, k, dtype, prec).
+ *
+ * pca_covariance -- Algorithm 1 stages 2-3: mu [B] and C = X^T X/(N-1),
+ *   cov [B][B] FP64 row-major (full symmetric).  prec selects the
+ *   covariance form (P64: FP64 accumulation; P32: FP32 SIMT; MIX: split-BF16
+ *   tensor cores).
+ * pca_eigh -- Algorithm 1 stage 4 on a given symmetric matrix A [B][B] FP64
+ *   (device): cyclic Jacobi (Eqs. 2-10), FP64 refinement (P32: none, MIX:
+ *   one iteration, P64: three), descending sort and sign rule; eigvals [B],
+ *   eigvecs [B][B] as in pca_fit.  The workspace is that of pca_fit with
+ *   N = 2 (any N works).
+ * pca_project -- Algorithm 1 stages 5-6: proj [N][k] FP32 = (Y - 1 mu^T) V[:, :k]
+ *   with mu [B] and eigvecs [B][B] FP64 on the device (narrowed to FP32).
+ */
+int pca_covariance(const void *cube, pca_dtype dtype, int64_t N, int B, pca_precision prec,
+                   double *mu, double *cov, void *workspace, size_t ws_bytes, void *stream,
+                   pca_info *info);
+int pca_eigh(const double *A, int B, double tol, int sweeps_max, pca_precision prec,
+             double *eigvals, double *eigvecs, void *workspace, size_t ws_bytes, void *stream,
+             pca_info *info);
+int pca_project(const void *cube, pca_dtype dtype, int64_t N, int B, int k, const double *mu,
+                const double *eigvecs, float *proj, void *workspace, size_t ws_bytes,
+                void *stream);
 
 /*
  * Waits for `stream` and copies the device-side outcome of the last

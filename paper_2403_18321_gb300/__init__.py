@@ -26,7 +26,8 @@ PREC_P64, PREC_P32, PREC_MIX = 0, 1, 2
 PRECISIONS = {"p64": PREC_P64, "p32": PREC_P32, "mix": PREC_MIX}
 STATUS = {0: "PCA_OK", 1: "PCA_ERR_ARG", 2: "PCA_ERR_NOCONV", 3: "PCA_ERR_NONFINITE",
           4: "PCA_ERR_TIMEOUT", 5: "PCA_ERR_CUDA", 6: "PCA_ERR_WORKSPACE"}
-EXPORTS = ("pca_workspace_size", "pca_fit", "pca_read_info", "pca_status_string", "pca_version",
+EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_project",
+           "pca_read_info", "pca_status_string", "pca_version",
            "pca_kernel_launches", "pca_profile", "pca_profile_collect")
 STAGES = ("covariance", "cov_finalize", "jacobi", "v_replay", "compact", "refine", "sort_sign",
           "project")
@@ -66,6 +67,12 @@ def load(build_if_missing: bool = False):
     lib.pca_workspace_size.restype = sz
     lib.pca_fit.argtypes = [P, i, i64, i, i, d, i, i, P, P, P, P, P, sz, P, ctypes.POINTER(Info)]
     lib.pca_fit.restype = i
+    lib.pca_covariance.argtypes = [P, i, i64, i, i, P, P, P, sz, P, ctypes.POINTER(Info)]
+    lib.pca_covariance.restype = i
+    lib.pca_eigh.argtypes = [P, i, d, i, i, P, P, P, sz, P, ctypes.POINTER(Info)]
+    lib.pca_eigh.restype = i
+    lib.pca_project.argtypes = [P, i, i64, i, i, P, P, P, P, sz, P]
+    lib.pca_project.restype = i
     lib.pca_read_info.argtypes = [P, P, ctypes.POINTER(Info)]
     lib.pca_read_info.restype = i
     lib.pca_status_string.argtypes = [i]
@@ -159,6 +166,67 @@ def fit(cube, k: int, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
     if rc not in (0, 2) and not (rc == 3 and info is not None):
         raise PCAError(rc, load().pca_status_string(rc).decode())
     return mu, ev, V, Q, (info.as_dict() if info is not None else None)
+
+
+def _check_rc(rc, allow=(0,)):
+    if rc not in allow:
+        raise PCAError(rc, load().pca_status_string(rc).decode())
+    return rc
+
+
+def covariance(cube, precision="mix", workspace: Workspace | None = None, stream=None):
+    """Stages 2-3 only: (mu [B] f64, C [B, B] f64, info)."""
+    import torch
+    N, B = cube.shape
+    dt, prec, dev = _dtype_code(cube), _prec_code(precision), cube.device
+    mu = torch.empty(B, dtype=torch.float64, device=dev)
+    C = torch.empty(B, B, dtype=torch.float64, device=dev)
+    workspace = workspace or make_workspace(N, B, 1, dt, prec, dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    info = Info()
+    rc = load().pca_covariance(ctypes.c_void_p(cube.data_ptr()), dt, N, B, prec,
+                               ctypes.c_void_p(mu.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+                               ctypes.c_void_p(_ws_ptr(workspace)), workspace.nbytes,
+                               ctypes.c_void_p(st.cuda_stream), ctypes.byref(info))
+    _check_rc(rc, (0, 3))
+    return mu, C, info.as_dict()
+
+
+def eigh(A, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
+         workspace: Workspace | None = None, stream=None):
+    """Stage 4 only, on a symmetric device matrix A [B, B] f64: (eigvals, eigvecs, info)."""
+    import torch
+    B = A.shape[0]
+    A = A.contiguous()
+    prec, dev = _prec_code(precision), A.device
+    ev = torch.empty(B, dtype=torch.float64, device=dev)
+    V = torch.empty(B, B, dtype=torch.float64, device=dev)
+    workspace = workspace or make_workspace(2, B, 1, 0, prec, dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    info = Info()
+    rc = load().pca_eigh(ctypes.c_void_p(A.data_ptr()), B, float(tol), int(sweeps_max), prec,
+                         ctypes.c_void_p(ev.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                         ctypes.c_void_p(_ws_ptr(workspace)), workspace.nbytes,
+                         ctypes.c_void_p(st.cuda_stream), ctypes.byref(info))
+    _check_rc(rc, (0, 2, 3))
+    return ev, V, info.as_dict()
+
+
+def project(cube, mu, eigvecs, k: int, workspace: Workspace | None = None, stream=None):
+    """Stages 5-6 only: proj [N, k] f32 = (Y - 1 mu^T) V[:, :k]."""
+    import torch
+    N, B = cube.shape
+    dt, dev = _dtype_code(cube), cube.device
+    Q = torch.empty(N, k, dtype=torch.float32, device=dev)
+    workspace = workspace or make_workspace(N, B, k, dt, PREC_P32, dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = load().pca_project(ctypes.c_void_p(cube.data_ptr()), dt, N, B, int(k),
+                            ctypes.c_void_p(mu.contiguous().data_ptr()),
+                            ctypes.c_void_p(eigvecs.contiguous().data_ptr()),
+                            ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(_ws_ptr(workspace)),
+                            workspace.nbytes, ctypes.c_void_p(st.cuda_stream))
+    _check_rc(rc)
+    return Q
 
 
 def kernel_launches(precision="mix", project: bool = True) -> int:

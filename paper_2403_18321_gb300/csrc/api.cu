@@ -70,7 +70,7 @@ struct StageMark {
 };
 
 int refine_iterations(pca_precision prec) {
-  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 2);
+  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 3);
 }
 
 }  // namespace
@@ -144,6 +144,98 @@ int pca_read_info(const void* workspace, void* stream, pca_info* info) {
   return info->status;
 }
 
+}  // extern "C"
+
+namespace gbpca {
+namespace {
+
+struct Ptrs {
+  DevHeader* hdr;
+  float* shift;
+  double* s1p;
+  void* s2p;
+  double* dvec;
+  double* C;
+  float* diag32;
+  float2* log;
+  float* v32;
+  double* lam;
+  double* vc;
+  double* w;
+  double* s;
+  double* g;
+  double* e;
+  float* vk;
+  float* muf;
+};
+
+Ptrs carve(void* workspace, const Layout& L) {
+  char* ws = static_cast<char*>(workspace);
+  Ptrs p;
+  p.hdr = reinterpret_cast<DevHeader*>(ws + L.hdr);
+  p.shift = reinterpret_cast<float*>(ws + L.shift);
+  p.s1p = reinterpret_cast<double*>(ws + L.s1_part);
+  p.s2p = ws + L.s2_part;
+  p.dvec = reinterpret_cast<double*>(ws + L.dvec);
+  p.C = reinterpret_cast<double*>(ws + L.cov);
+  p.diag32 = reinterpret_cast<float*>(ws + L.diag32);
+  p.log = reinterpret_cast<float2*>(ws + L.log);
+  p.v32 = reinterpret_cast<float*>(ws + L.v32);
+  p.lam = reinterpret_cast<double*>(ws + L.lam);
+  p.vc = reinterpret_cast<double*>(ws + L.vc);
+  p.w = reinterpret_cast<double*>(ws + L.w);
+  p.s = reinterpret_cast<double*>(ws + L.s);
+  p.g = reinterpret_cast<double*>(ws + L.r);
+  p.e = reinterpret_cast<double*>(ws + L.e);
+  p.vk = reinterpret_cast<float*>(ws + L.vk);
+  p.muf = reinterpret_cast<float*>(ws + L.muf);
+  return p;
+}
+
+// largest first-order angle the refinement applies (pairs above it count as clustered)
+double refine_max_angle(pca_precision prec) { return prec == PCA_PREC_MIX ? 1.0 / 1024 : 1.0 / 64; }
+
+// stages 2-3 of Algorithm 1: band means and covariance in one pass over the cube
+cudaError_t run_cov(const void* cube, pca_dtype dt, int64_t N, int B, pca_precision prec,
+                    const Layout& L, const Ptrs& P, double* mu, cudaStream_t st, StageMark& pm) {
+  cudaError_t e;
+  pm.mark(0);
+  if (prec == PCA_PREC_MIX)
+    e = launch_syrk_tc(cube, dt, N, B, P.shift, P.s1p, (float*)P.s2p, L.partials, P.hdr, st);
+  else
+    e = launch_syrk_simt(cube, dt, N, B, prec == PCA_PREC_P64, P.shift, P.s1p, P.s2p, L.partials, st);
+  if (e != cudaSuccess) return e;
+  pm.mark(1);
+  return launch_cov_finalize(P.shift, P.s1p, P.s2p, L.s2_bytes_el == 8, L.partials, N, B, mu, P.C,
+                             P.muf, P.dvec, P.hdr, st);
+}
+
+// stage 4: Jacobi, V replay, FP64 refinement, sort and sign rule
+cudaError_t run_eigh(const double* A, int B, float tol32, int sweeps_max, pca_precision prec,
+                     int k, const Ptrs& P, double* eigvals, double* eigvecs, cudaStream_t st,
+                     StageMark& pm) {
+  cudaError_t e;
+  pm.mark(2);
+  if ((e = launch_jacobi(A, B, tol32, sweeps_max, P.log, P.diag32, P.hdr, st)) != cudaSuccess) return e;
+  pm.mark(3);
+  if ((e = launch_vreplay(P.log, B, P.hdr, P.v32, st)) != cudaSuccess) return e;
+  pm.mark(4);
+  if ((e = launch_compact(P.diag32, P.v32, B, P.hdr, P.lam, P.vc, st)) != cudaSuccess) return e;
+  pm.mark(5);
+  const int iters = refine_iterations(prec);
+  for (int it = 0; it < iters; ++it)
+    if ((e = launch_refine(A, B, P.vc, P.lam, P.w, P.s, P.g, P.e, P.hdr, refine_max_angle(prec),
+                           st)) != cudaSuccess)
+      return e;
+  pm.mark(6);
+  return launch_sort_sign(P.lam, P.vc, B, k, eigvals, eigvecs, P.vk, P.hdr, st);
+}
+
+}  // namespace
+}  // namespace gbpca
+
+extern "C" {
+
 int pca_fit(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol, int sweeps_max,
             pca_precision prec, double* mu, double* eigvals, double* eigvecs, float* proj,
             void* workspace, size_t ws_bytes, void* stream, pca_info* info) {
@@ -152,59 +244,72 @@ int pca_fit(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol,
   if (!workspace || ((uintptr_t)workspace) % 256 != 0) return PCA_ERR_WORKSPACE;
   const Layout L = make_layout(N, B, k, dt, prec, device_sms());
   if (ws_bytes < L.total) return PCA_ERR_WORKSPACE;
-
-  char* ws = static_cast<char*>(workspace);
-  DevHeader* hdr = reinterpret_cast<DevHeader*>(ws + L.hdr);
-  float* shift = reinterpret_cast<float*>(ws + L.shift);
-  double* s1p = reinterpret_cast<double*>(ws + L.s1_part);
-  void* s2p = ws + L.s2_part;
-  double* dvec = reinterpret_cast<double*>(ws + L.dvec);
-  double* C = reinterpret_cast<double*>(ws + L.cov);
-  float* diag32 = reinterpret_cast<float*>(ws + L.diag32);
-  float2* log = reinterpret_cast<float2*>(ws + L.log);
-  float* v32 = reinterpret_cast<float*>(ws + L.v32);
-  double* lam = reinterpret_cast<double*>(ws + L.lam);
-  double* vc = reinterpret_cast<double*>(ws + L.vc);
-  double* w = reinterpret_cast<double*>(ws + L.w);
-  double* s = reinterpret_cast<double*>(ws + L.s);
-  double* g = reinterpret_cast<double*>(ws + L.r);
-  double* e = reinterpret_cast<double*>(ws + L.e);
-  float* vk = reinterpret_cast<float*>(ws + L.vk);
-  float* muf = reinterpret_cast<float*>(ws + L.muf);
+  const Ptrs P = carve(workspace, L);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-
-  const int iters = refine_iterations(prec);
   const float tol32 = std::max((float)tol, kJacobiFloor);
   StageMark pm(st);
-  k_header_init<<<1, 1, 0, st>>>(hdr, iters, tol32);
+  k_header_init<<<1, 1, 0, st>>>(P.hdr, refine_iterations(prec), tol32);
   GB_CK(cudaGetLastError());
-
-  // stages 2-3 of Algorithm 1: band means and covariance, one pass
-  pm.mark(0);
-  if (prec == PCA_PREC_MIX)
-    GB_CK(launch_syrk_tc(cube, dt, N, B, shift, s1p, (float*)s2p, L.partials, hdr, st));
-  else
-    GB_CK(launch_syrk_simt(cube, dt, N, B, prec == PCA_PREC_P64, shift, s1p, s2p, L.partials, st));
-  pm.mark(1);
-  GB_CK(launch_cov_finalize(shift, s1p, s2p, L.s2_bytes_el == 8, L.partials, N, B, mu, C, muf,
-                            dvec, hdr, st));
-  // stage 4: eigen-decomposition
-  pm.mark(2);
-  GB_CK(launch_jacobi(C, B, tol32, sweeps_max, log, diag32, hdr, st));
-  pm.mark(3);
-  GB_CK(launch_vreplay(log, B, hdr, v32, st));
-  pm.mark(4);
-  GB_CK(launch_compact(diag32, v32, B, hdr, lam, vc, st));
-  pm.mark(5);
-  for (int it = 0; it < iters; ++it) GB_CK(launch_refine(C, B, vc, lam, w, s, g, e, hdr, st));
-  pm.mark(6);
-  GB_CK(launch_sort_sign(lam, vc, B, k, eigvals, eigvecs, vk, hdr, st));
+  GB_CK(run_cov(cube, dt, N, B, prec, L, P, mu, st, pm));
+  GB_CK(run_eigh(P.C, B, tol32, sweeps_max, prec, k, P, eigvals, eigvecs, st, pm));
   // stages 5-6: projection onto the first k eigenvectors
   pm.mark(7);
-  if (proj) GB_CK(launch_project(cube, dt, N, B, k, muf, vk, proj, st));
+  if (proj) GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st));
   pm.mark(8);
+  if (info) return pca_read_info(workspace, stream, info);
+  return PCA_OK;
+}
 
-  if (info) return pca_read_info(ws, stream, info);
+int pca_covariance(const void* cube, pca_dtype dt, int64_t N, int B, pca_precision prec,
+                   double* mu, double* cov, void* workspace, size_t ws_bytes, void* stream,
+                   pca_info* info) {
+  if (!args_ok(cube, dt, N, B, 1, 1.0, 1, prec) || !mu || !cov) return PCA_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace) % 256 != 0) return PCA_ERR_WORKSPACE;
+  const Layout L = make_layout(N, B, 1, dt, prec, device_sms());
+  if (ws_bytes < L.total) return PCA_ERR_WORKSPACE;
+  const Ptrs P = carve(workspace, L);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  StageMark pm(st);
+  k_header_init<<<1, 1, 0, st>>>(P.hdr, 0, 0.f);
+  GB_CK(cudaGetLastError());
+  GB_CK(run_cov(cube, dt, N, B, prec, L, P, mu, st, pm));
+  GB_CK(cudaMemcpyAsync(cov, P.C, sizeof(double) * (size_t)B * B, cudaMemcpyDeviceToDevice, st));
+  if (info) return pca_read_info(workspace, stream, info);
+  return PCA_OK;
+}
+
+int pca_eigh(const double* A, int B, double tol, int sweeps_max, pca_precision prec,
+             double* eigvals, double* eigvecs, void* workspace, size_t ws_bytes, void* stream,
+             pca_info* info) {
+  static const float kDummy[4] = {0.f, 0.f, 0.f, 0.f};
+  if (!A || !eigvals || !eigvecs || !args_ok(kDummy, PCA_F32, 2, B, 1, tol, sweeps_max, prec))
+    return PCA_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace) % 256 != 0) return PCA_ERR_WORKSPACE;
+  const Layout L = make_layout(2, B, 1, PCA_F32, prec, device_sms());
+  if (ws_bytes < L.total) return PCA_ERR_WORKSPACE;
+  const Ptrs P = carve(workspace, L);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const float tol32 = std::max((float)tol, kJacobiFloor);
+  StageMark pm(st);
+  k_header_init<<<1, 1, 0, st>>>(P.hdr, refine_iterations(prec), tol32);
+  GB_CK(cudaGetLastError());
+  GB_CK(run_eigh(A, B, tol32, sweeps_max, prec, 1, P, eigvals, eigvecs, st, pm));
+  if (info) return pca_read_info(workspace, stream, info);
+  return PCA_OK;
+}
+
+int pca_project(const void* cube, pca_dtype dt, int64_t N, int B, int k, const double* mu,
+                const double* eigvecs, float* proj, void* workspace, size_t ws_bytes,
+                void* stream) {
+  if (!args_ok(cube, dt, N, B, k, 1.0, 1, PCA_PREC_P32) || !mu || !eigvecs || !proj)
+    return PCA_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace) % 256 != 0) return PCA_ERR_WORKSPACE;
+  const Layout L = make_layout(N, B, k, dt, PCA_PREC_P32, device_sms());
+  if (ws_bytes < L.total) return PCA_ERR_WORKSPACE;
+  const Ptrs P = carve(workspace, L);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GB_CK(launch_narrow_inputs(mu, eigvecs, B, k, P.muf, P.vk, st));
+  GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st));
   return PCA_OK;
 }
 
@@ -225,8 +330,8 @@ int pca_version(void) { return 100; }
 
 int pca_kernel_launches(pca_precision prec, int with_projection) {
   // header init, covariance, band-sum reduce, covariance finalise, Jacobi,
-  // V replay, compact, 6 per refinement iteration, sort/sign, projection
-  return 7 + 6 * refine_iterations(prec) + 1 + (with_projection ? 1 : 0);
+  // V replay, compact, 4 per refinement iteration, sort/sign, projection
+  return 7 + 4 * refine_iterations(prec) + 1 + (with_projection ? 1 : 0);
 }
 
 int pca_profile(int enable) {

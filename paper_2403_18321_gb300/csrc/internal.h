@@ -82,12 +82,17 @@ cudaError_t launch_compact(const float* diag32, const float* v32, int B, DevHead
                            double* lam, double* vc, cudaStream_t st);
 
 // One Newton-type refinement iteration of the eigen-decomposition in FP64.
+// max_angle: pairs whose first-order angle exceeds it are only re-orthogonalised.
 cudaError_t launch_refine(const double* C, int B, double* vc, double* lam, double* w, double* s,
-                          double* r, double* e, DevHeader* hdr, cudaStream_t st);
+                          double* r, double* e, DevHeader* hdr, double max_angle, cudaStream_t st);
 
 // Sort descending, sign-normalise, write eigvals/eigvecs (FP64) and V_k (FP32).
 cudaError_t launch_sort_sign(const double* lam, const double* vc, int B, int k, double* eigvals,
                              double* eigvecs, float* vk, DevHeader* hdr, cudaStream_t st);
+
+// mu_f = (float)mu, vk = (float)eigvecs[:, :k] (eigvecs B x B row-major).
+cudaError_t launch_narrow_inputs(const double* mu, const double* eigvecs, int B, int k, float* mu_f,
+                                 float* vk, cudaStream_t st);
 
 // Q = (Y - 1 mu^T) V_k, FP32.
 cudaError_t launch_project(const void* cube, pca_dtype dt, int64_t N, int B, int k,

@@ -7,42 +7,61 @@ namespace gbpca {
 
 namespace {
 
-// One CTA.  Rank of eigenvalue j = number of eigenvalues that sort before it
-// (larger, or equal and at a lower position); no comparison sort needed for
-// B <= 232.  Then every output column is gathered and flipped so that its
-// largest-magnitude entry (lowest row on ties) is positive.
-__global__ void __launch_bounds__(256)
+// One CTA of 4 x 256 threads.  Rank of eigenvalue j = number of eigenvalues
+// that sort before it (larger, or equal and at a lower position); no
+// comparison sort is needed for B <= 232.  Thread (q, j) scans rows i = q
+// mod 4 of source column j (coalesced across j) for the entry of largest
+// magnitude (lowest row on ties), the four partial results are combined, and
+// every column is written to its sorted position with the sign that makes
+// that entry positive.
+__global__ void __launch_bounds__(1024)
 k_sort_sign(const double* __restrict__ lam, const double* __restrict__ vc, int B, int k,
             double* __restrict__ eigvals, double* __restrict__ eigvecs, float* __restrict__ vk) {
-  __shared__ int perm[kMaxB];
   __shared__ double ls[kMaxB];
-  const int tid = threadIdx.x;
-  for (int j = tid; j < B; j += blockDim.x) { ls[j] = lam[j]; perm[j] = j; }
+  __shared__ int rank_s[kMaxB];
+  __shared__ double sgn_s[kMaxB];
+  __shared__ double best_v[4][256];
+  __shared__ int best_i[4][256];
+  const int j = threadIdx.x & 255, q = threadIdx.x >> 8;
+  for (int t = threadIdx.x; t < B; t += blockDim.x) ls[t] = lam[t];
   __syncthreads();
-  int rank = -1;
-  if (tid < B) {
-    const double lj = ls[tid];
-    rank = 0;
+  if (q == 0 && j < B) {
+    const double lj = ls[j];
+    int r = 0;
     for (int i = 0; i < B; ++i) {
       const double li = ls[i];
-      rank += (li > lj) || (li == lj && i < tid);
+      r += (li > lj) || (li == lj && i < j);
     }
+    rank_s[j] = min(r, B - 1);
+  }
+  if (j < B) {
+    double bv = -1.0;
+    int bi = 0;
+    for (int i = q; i < B; i += 4) {
+      const double a = fabs(vc[(size_t)i * B + j]);
+      if (a > bv) { bv = a; bi = i; }
+    }
+    best_v[q][j] = bv;
+    best_i[q][j] = bi;
   }
   __syncthreads();
-  if (tid < B) perm[min(rank, B - 1)] = tid;
-  __syncthreads();
-  if (tid < B) {
-    const int r = tid, src = perm[r];
-    eigvals[r] = ls[src];
-    int im = 0;
-    double best = -1.0;
-    for (int i = 0; i < B; ++i) {
-      const double a = fabs(vc[(size_t)i * B + src]);
-      if (a > best) { best = a; im = i; }
+  if (q == 0 && j < B) {
+    double bv = best_v[0][j];
+    int bi = best_i[0][j];
+    for (int t = 1; t < 4; ++t) {
+      const double v = best_v[t][j];
+      const int i = best_i[t][j];
+      if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
     }
-    const double sg = vc[(size_t)im * B + src] < 0.0 ? -1.0 : 1.0;
-    for (int i = 0; i < B; ++i) {
-      const double v = sg * vc[(size_t)i * B + src];
+    sgn_s[j] = vc[(size_t)bi * B + j] < 0.0 ? -1.0 : 1.0;
+    eigvals[rank_s[j]] = ls[j];
+  }
+  __syncthreads();
+  if (j < B) {
+    const int r = rank_s[j];
+    const double sg = sgn_s[j];
+    for (int i = q; i < B; i += 4) {
+      const double v = sg * vc[(size_t)i * B + j];
       eigvecs[(size_t)i * B + r] = v;
       if (r < k) vk[(size_t)i * k + r] = (float)v;
     }
@@ -145,12 +164,28 @@ cudaError_t project_typed(const In* cube, int64_t N, int B, int k, const float* 
   return cudaErrorInvalidValue;
 }
 
+__global__ void k_narrow(const double* __restrict__ mu, const double* __restrict__ V, int B, int k,
+                         float* __restrict__ mu_f, float* __restrict__ vk) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * k; e += gridDim.x * blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    vk[e] = (float)V[(size_t)i * B + j];
+  }
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+    mu_f[b] = (float)mu[b];
+}
+
 }  // namespace
+
+cudaError_t launch_narrow_inputs(const double* mu, const double* eigvecs, int B, int k, float* mu_f,
+                                 float* vk, cudaStream_t st) {
+  k_narrow<<<(B * k + 255) / 256, 256, 0, st>>>(mu, eigvecs, B, k, mu_f, vk);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sort_sign(const double* lam, const double* vc, int B, int k, double* eigvals,
                              double* eigvecs, float* vk, DevHeader* hdr, cudaStream_t st) {
   (void)hdr;
-  k_sort_sign<<<1, 256, 0, st>>>(lam, vc, B, k, eigvals, eigvecs, vk);
+  k_sort_sign<<<1, 1024, 0, st>>>(lam, vc, B, k, eigvals, eigvecs, vk);
   return cudaGetLastError();
 }
 

@@ -28,6 +28,23 @@ namespace gbpca {
 namespace {
 
 constexpr int kJacThreads = 1024;
+constexpr int kBandWarps = 4;   // diagonal band: super-diagonal blocks, next angles, edges
+
+__device__ __forceinline__ float rcp_nr(float x) {  // 1/x: hardware estimate + one Newton step
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return fmaf(r, fmaf(-x, r, 1.f), r);
+}
+__device__ __forceinline__ float rsqrt_nr(float x) {  // 1/sqrt(x), x > 0: estimate + Newton
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return fmaf(y, fmaf(-0.5f * x * y, y, 0.5f), y);
+}
+__device__ __forceinline__ float sqrt_est(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // Eqs. 2-5 for the pair with diagonal app, aqq and off-diagonal apq: the small
 // root t of Eq. 3 in the form t = sgn(tau)/(|tau| + sqrt(1 + tau^2)),
@@ -36,18 +53,24 @@ constexpr int kJacThreads = 1024;
 // without a rotation (c = 1, s = 0).
 __device__ __forceinline__ void jacobi_angle(float app, float aqq, float apq, float& c, float& s,
                                              float& t) {
-  const float thr = 5.9604645e-08f * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq));
+  const float thr = 5.9604645e-08f * sqrt_est(fabsf(app)) * sqrt_est(fabsf(aqq));
   if (!(fabsf(apq) > thr)) { c = 1.f; s = 0.f; t = 0.f; return; }
-  const float tau = (aqq - app) / (2.f * apq);
+  const float tau = (aqq - app) * rcp_nr(2.f * apq);
   const float at = fabsf(tau);
-  float tt = (at > 1e18f) ? 0.5f / at : 1.f / (at + sqrtf(fmaf(tau, tau, 1.f)));
+  float tt;
+  if (at > 1e18f) {
+    tt = 0.5f * rcp_nr(at);
+  } else {
+    const float u = fmaf(tau, tau, 1.f);
+    tt = rcp_nr(at + u * rsqrt_nr(u));
+  }
   tt = (tau >= 0.f) ? tt : -tt;
-  c = 1.f / sqrtf(fmaf(tt, tt, 1.f));
+  c = rsqrt_nr(fmaf(tt, tt, 1.f));
   s = tt * c;
   t = tt;
 }
 
-// M' = G_I M G_J for the 2x2 block M = [[m00, m01], [m10, m11]].
+// M' = G_I M G_J for the 2x2 block M = [[m00, m01], [m10, m11]], G = [[s, c], [c, -s]].
 __device__ __forceinline__ void rot_block(float2 csI, float2 csJ, float& m00, float& m01,
                                           float& m10, float& m11) {
   const float cI = csI.x, sI = csI.y, cJ = csJ.x, sJ = csJ.y;
@@ -59,13 +82,142 @@ __device__ __forceinline__ void rot_block(float2 csI, float2 csJ, float& m00, fl
   m11 = fmaf(cI, t01, -sI * t11);
 }
 
+// Rotates the pair (p, q = p+1) whose off-diagonal value is apq (already in a
+// register) and whose diagonals sit in A; finishes the diagonal block (rotate,
+// then swap the two positions) and publishes (c, s).  Returns nothing; the
+// caller stores 0 at (p, q).
+__device__ __forceinline__ void pair_rotation(float* A, int Bp, int p, float apq, float2* cs_slot,
+                                              float2* log_slot) {
+  float* dp = A + p * Bp + p;
+  float* dq = dp + Bp + 1;
+  const float app = *dp, aqq = *dq;
+  float c, s, t;
+  jacobi_angle(app, aqq, apq, c, s, t);
+  const float2 v = make_float2(c, s);
+  *cs_slot = v;
+  *log_slot = v;
+  // R^T [[app, apq], [apq, aqq]] R = diag(app - t apq, aqq + t apq); then swap
+  *dp = fmaf(t, apq, aqq);
+  *dq = fmaf(-t, apq, app);
+}
+
+// One parallel step.  Even steps (e = 0) rotate position pairs (2J, 2J+1),
+// odd steps (e = 1) the pairs (2J+1, 2J+2) with positions 0 and Bp-1 idle.
+// The diagonal blocks of this step were finished (and cur[] filled) before it
+// started.  Band warps update the super-diagonal blocks (I, I+1) and, unless
+// this is the last step of the sweep, immediately rotate the diagonal block
+// of the next step's pair that block completes, filling nxt[]; they also
+// handle the idle row 0 / column Bp-1 of odd steps.  The other warps update
+// every block (I, J) with J >= I + 2.
+__device__ __forceinline__ void jacobi_step(float* A, int Bp, int P, int e, bool last,
+                                            const float2* cur, float2* nxt, float2* log_next) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int np = P - e;
+  if (warp < kBandWarps) {
+    const int b = tid;
+    if (b < np - 1) {  // super-diagonal block (I, I+1)
+      const int I = b, pI = 2 * I + e;
+      float* r0 = A + pI * Bp + pI + 2;
+      float* r1 = r0 + Bp;
+      float m00, m01, m10, m11;
+      if (e == 0) {
+        const float2 x = *reinterpret_cast<const float2*>(r0);
+        const float2 y = *reinterpret_cast<const float2*>(r1);
+        m00 = x.x; m01 = x.y; m10 = y.x; m11 = y.y;
+      } else {
+        m00 = r0[0]; m01 = r0[1]; m10 = r1[0]; m11 = r1[1];
+      }
+      rot_block(cur[I], cur[I + 1], m00, m01, m10, m11);
+      if (!last) {  // (q_I, p_{I+1}) is the off-diagonal of the next step's pair
+        const int J2 = e == 0 ? I : I + 1;
+        pair_rotation(A, Bp, pI + 1, m10, nxt + J2, log_next + J2);
+        m10 = 0.f;
+      }
+      if (e == 0) {
+        *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
+        *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
+      } else {
+        r0[0] = m00; r0[1] = m01; r1[0] = m10; r1[1] = m11;
+      }
+    }
+    if (e) {  // idle row 0 against every pair, every pair against idle column Bp-1
+      for (int w = b; w < 2 * np; w += kBandWarps * 32) {
+        if (w < np) {
+          const float2 g = cur[w];
+          float* a = A + 2 * w + 1;  // (0, p), (0, q)
+          const float x = a[0], y = a[1];
+          float n0 = fmaf(x, g.y, y * g.x);
+          const float n1 = fmaf(x, g.x, -y * g.y);
+          if (w == 0 && !last) {  // (0, 1) is the off-diagonal of the next even pair 0
+            pair_rotation(A, Bp, 0, n0, nxt, log_next);
+            n0 = 0.f;
+          }
+          a[0] = n0;
+          a[1] = n1;
+        } else {
+          const int I = w - np;
+          const float2 g = cur[I];
+          float* a = A + (2 * I + 1) * Bp + (Bp - 1);  // (p, L), (q, L)
+          const float x = a[0], y = a[Bp];
+          const float n0 = fmaf(g.y, x, g.x * y);
+          float n1 = fmaf(g.x, x, -g.y * y);
+          if (I == P - 2 && !last) {  // (Bp-2, Bp-1) is the next even pair P-1
+            pair_rotation(A, Bp, Bp - 2, n1, nxt + (P - 1), log_next + (P - 1));
+            n1 = 0.f;
+          }
+          a[0] = n0;
+          a[Bp] = n1;
+        }
+      }
+    }
+  } else {
+    // blocks (I, J), J >= I + 2: row I holds np-2-I of them; fold row f with
+    // row np-3-f so that every fold holds np-1 blocks
+    const int rows = np - 2;
+    if (rows <= 0) return;
+    const int nfold = (rows + 1) / 2;
+    const int per = np - 1;
+    const int nch = (per + 31) >> 5;
+    const int bw = warp - kBandWarps, nbw = kJacThreads / 32 - kBandWarps;
+    for (int wi = bw; wi < nfold * nch; wi += nbw) {
+      const int f = wi / nch;
+      const int x = ((wi - f * nch) << 5) + lane;
+      const int first = np - 2 - f;
+      const int limit = (2 * f + 1 == rows) ? first : per;
+      if (x >= limit) continue;
+      int I, J;
+      if (x < first) { I = f; J = f + 2 + x; }
+      else { I = np - 3 - f; J = I + 2 + (x - first); }
+      const int pI = 2 * I + e, pJ = 2 * J + e;
+      float* r0 = A + pI * Bp + pJ;
+      float* r1 = r0 + Bp;
+      float m00, m01, m10, m11;
+      if (e == 0) {
+        const float2 u = *reinterpret_cast<const float2*>(r0);
+        const float2 v = *reinterpret_cast<const float2*>(r1);
+        m00 = u.x; m01 = u.y; m10 = v.x; m11 = v.y;
+      } else {
+        m00 = r0[0]; m01 = r0[1]; m10 = r1[0]; m11 = r1[1];
+      }
+      rot_block(cur[I], cur[J], m00, m01, m10, m11);
+      if (e == 0) {
+        *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
+        *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
+      } else {
+        r0[0] = m00; r0[1] = m01; r1[0] = m10; r1[1] = m11;
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kJacThreads, 1)
 k_jacobi(const double* __restrict__ C, int B, float tol32, int sweeps_max,
          float2* __restrict__ log, float* __restrict__ diag32, DevHeader* __restrict__ hdr) {
   extern __shared__ __align__(16) float A[];  // [Bp][Bp]
-  __shared__ float2 cs[kMaxB / 2];
+  __shared__ float2 cs[2][kMaxB / 2];
   __shared__ double red[2][32];
   __shared__ int s_flag;
+  __shared__ int s_viol[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Bp = B + (B & 1), P = Bp / 2;
 
@@ -82,25 +234,40 @@ k_jacobi(const double* __restrict__ C, int B, float tol32, int sweeps_max,
 
   int sweep = 0, status = PCA_OK;
   for (;;) {
-    // stop test (before every sweep): off(A) <= tol * ||A||_F
+    // stop test (before every sweep).  Element-wise relative: every
+    // off-diagonal |a_pq| <= tol * sqrt(|a_pp a_qq|) -- the paper's "all
+    // off-diagonal elements below the stop factor", scaled per pair so that
+    // small eigenvalues converge to the same relative accuracy as large
+    // ones.  off(A)/||A||_F is reported beside it.
     float so = 0.f, sd = 0.f;
+    int viol = 0;
+    const float tol2 = tol32 * tol32;
     for (int i = warp; i < Bp; i += 32) {
       const float* Ai = A + i * Bp;
+      const float aii = fabsf(Ai[i]);
       for (int j = i + lane; j < Bp; j += 32) {
         const float a = Ai[j];
-        if (j == i) sd = fmaf(a, a, sd); else so = fmaf(a, a, so);
+        if (j == i) {
+          sd = fmaf(a, a, sd);
+        } else {
+          so = fmaf(a, a, so);
+          const float ajj = fabsf(A[j * Bp + j]);
+          viol |= (a * a > tol2 * aii * ajj) ? 1 : 0;
+        }
       }
     }
     so = warp_sum(so);
     sd = warp_sum(sd);
-    if (lane == 0) { red[0][warp] = (double)so; red[1][warp] = (double)sd; }
+    viol = __any_sync(kFull, viol);
+    if (lane == 0) { red[0][warp] = (double)so; red[1][warp] = (double)sd; s_viol[warp] = viol; }
     __syncthreads();
     if (warp == 0) {
       const double o = warp_sum(red[0][lane]), d = warp_sum(red[1][lane]);
+      const int anyv = __any_sync(kFull, s_viol[lane]);
       if (lane == 0) {
         const double off = sqrt(2.0 * o), fro = sqrt(2.0 * o + d);
         int flag = 0;
-        if (fro == 0.0 || off <= (double)tol32 * fro) flag = 1;
+        if (fro == 0.0 || !anyv) flag = 1;
         else if (sweep >= sweeps_max) flag = 2;
         s_flag = flag;
         hdr->off_rel = fro == 0.0 ? 0.0 : off / fro;
@@ -111,75 +278,17 @@ k_jacobi(const double* __restrict__ C, int B, float tol32, int sweeps_max,
     const int flag = s_flag;
     if (flag) { status = flag == 1 ? PCA_OK : PCA_ERR_NOCONV; break; }
 
+    // the first step's pairs (even): rotate their diagonal blocks
+    float2* logs = log + (size_t)sweep * Bp * P;
+    if (tid < P) {
+      float* ap = A + (2 * tid) * Bp + 2 * tid + 1;
+      pair_rotation(A, Bp, 2 * tid, *ap, &cs[0][tid], logs + tid);
+      *ap = 0.f;
+    }
+    __syncthreads();
     for (int step = 0; step < Bp; ++step) {
-      const int e = step & 1;
-      const int np = P - e;  // odd steps leave positions 0 and Bp-1 idle
-      // phase A: angles of the np pairs; the diagonal block is finished here
-      if (tid < np) {
-        const int p = 2 * tid + e, q = p + 1;
-        float* Ap = A + p * Bp;
-        float* Aq = A + q * Bp;
-        const float app = Ap[p], aqq = Aq[q], apq = Ap[q];
-        float c, s, t;
-        jacobi_angle(app, aqq, apq, c, s, t);
-        const float2 v = make_float2(c, s);
-        cs[tid] = v;
-        log[((size_t)sweep * Bp + step) * P + tid] = v;
-        // R^T [[app, apq], [apq, aqq]] R = diag(app - t apq, aqq + t apq); then swap
-        Ap[p] = fmaf(t, apq, aqq);
-        Aq[q] = fmaf(-t, apq, app);
-        Ap[q] = 0.f;
-      }
-      __syncthreads();
-      // phase B: off-diagonal blocks (I < J), folded so that every warp row
-      // holds np blocks: row f with row np-2-f.
-      const int R = np - 1;
-      const int nfold = (R + 1) / 2;
-      for (int f = warp; f < nfold; f += 32) {
-        const int first = np - 1 - f;                       // blocks in row f
-        const int limit = (2 * f + 1 == R) ? first : np;    // middle row when R is odd
-        for (int x = lane; x < limit; x += 32) {
-          int I, J;
-          if (x < first) { I = f; J = f + 1 + x; }
-          else { I = np - 2 - f; J = I + 1 + (x - first); }
-          const int pI = 2 * I + e, pJ = 2 * J + e;
-          float* r0 = A + pI * Bp + pJ;
-          float* r1 = r0 + Bp;
-          float m00, m01, m10, m11;
-          if (e == 0) {
-            const float2 a = *reinterpret_cast<const float2*>(r0);
-            const float2 b = *reinterpret_cast<const float2*>(r1);
-            m00 = a.x; m01 = a.y; m10 = b.x; m11 = b.y;
-          } else {
-            m00 = r0[0]; m01 = r0[1]; m10 = r1[0]; m11 = r1[1];
-          }
-          rot_block(cs[I], cs[J], m00, m01, m10, m11);
-          if (e == 0) {
-            *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
-            *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
-          } else {
-            r0[0] = m00; r0[1] = m01; r1[0] = m10; r1[1] = m11;
-          }
-        }
-      }
-      if (e) {  // row 0 (idle position) against every pair, every pair against column Bp-1
-        for (int w = tid; w < 2 * np; w += kJacThreads) {
-          if (w < np) {
-            const float2 g = cs[w];
-            float* a = A + 2 * w + 1;  // (0, p), (0, q)
-            const float x = a[0], y = a[1];
-            a[0] = fmaf(x, g.y, y * g.x);
-            a[1] = fmaf(x, g.x, -y * g.y);
-          } else {
-            const int I = w - np;
-            const float2 g = cs[I];
-            float* a = A + (2 * I + 1) * Bp + (Bp - 1);  // (p, L), (q, L)
-            const float x = a[0], y = a[Bp];
-            a[0] = fmaf(g.y, x, g.x * y);
-            a[Bp] = fmaf(g.x, x, -g.y * y);
-          }
-        }
-      }
+      jacobi_step(A, Bp, P, step & 1, step == Bp - 1, cs[step & 1], cs[(step + 1) & 1],
+                  logs + (size_t)(step + 1) * P);
       __syncthreads();
     }
     ++sweep;

@@ -8,9 +8,10 @@
 // limit t ~ m/2 = C_ij / (C_jj - C_ii) of Eqs. 3 and 7, corrected for the
 // non-orthogonality R -- and V <- V (I + E).  This is the iterative
 // refinement of Ogita and Aishima (Japan J. Indust. Appl. Math. 35, 2018),
-// which converges quadratically: one iteration takes the FP32 result to
-// FP64 accuracy for eigenvalues separated by more than delta; pairs closer
-// than delta are only re-orthogonalised (E_ij = R_ij / 2).
+// which converges quadratically.  Their global cluster threshold (built from
+// norms of S - diag and of R) is replaced by a per-pair test on the angle
+// itself: pairs whose first-order angle exceeds 1/16 are treated as one
+// cluster and only re-orthogonalised (E_ij = R_ij / 2).
 //
 // GB300 executes FP64 at about 1/58 of its FP32 rate, so only these O(B^3)
 // GEMMs (spread over every SM) and the small element-wise steps run in FP64.
@@ -55,42 +56,6 @@ k_dgemm(const double* __restrict__ A, const double* __restrict__ Bm,
   }
 }
 
-// delta = 2 (||S - diag(lam~)||_F + ||C||_F ||I - G||_F), with lam~_i = S_ii/(1 - R_ii)
-// and R = I - G.  The norms only set a threshold, so they are summed in FP32.
-__global__ void __launch_bounds__(1024)
-k_refine_norms(const double* __restrict__ C, const double* __restrict__ S,
-               const double* __restrict__ G, int n, DevHeader* __restrict__ hdr) {
-  __shared__ float red[3][32];
-  float a = 0.f, b = 0.f, c = 0.f;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e - i * n;
-    const float cij = (float)C[e];
-    c = fmaf(cij, cij, c);
-    const float r = (i == j ? 1.f : 0.f) - (float)G[e];
-    b = fmaf(r, r, b);
-    if (i != j) {
-      const float s = (float)S[e];
-      a = fmaf(s, s, a);
-    } else {
-      const double lam = S[e] / (1.0 - (1.0 - G[e]));
-      const float d = (float)(S[e] - lam);
-      a = fmaf(d, d, a);
-    }
-  }
-  a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = c; }
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x / 32;
-    a = lane < nw ? red[0][lane] : 0.f;
-    b = lane < nw ? red[1][lane] : 0.f;
-    c = lane < nw ? red[2][lane] : 0.f;
-    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
-    if (lane == 0) hdr->delta = 2.0 * (sqrt((double)a) + sqrt((double)c) * sqrt((double)b));
-  }
-}
-
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   // non-negative doubles order like their bit patterns
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
@@ -99,17 +64,21 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
 // E_ij and lam~ (written by the diagonal entries).
 __global__ void k_refine_E(const double* __restrict__ S, const double* __restrict__ G, int n,
                            double* __restrict__ E, double* __restrict__ lam,
-                           DevHeader* __restrict__ hdr) {
+                           DevHeader* __restrict__ hdr, double inv_max_angle) {
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const double delta = hdr->delta;
   const double rii = 1.0 - G[(size_t)i * n + i], rjj = 1.0 - G[(size_t)j * n + j];
-  const double li = S[(size_t)i * n + i] / (1.0 - rii);
+  const double li = S[(size_t)i * n + i] / (1.0 - rii);   // = S_ii / G_ii
   const double lj = S[(size_t)j * n + j] / (1.0 - rjj);
   const double rij = (i == j ? 1.0 : 0.0) - G[(size_t)i * n + j];
+  const double num = S[(size_t)i * n + j] + lj * rij;
+  const double gap = lj - li;
+  // the first-order Jacobi angle where it is small (|t| <= max_angle); a pair
+  // whose angle is larger is treated as part of a cluster and only
+  // re-orthogonalised
   double e;
-  if (fabs(li - lj) > delta) e = (S[(size_t)i * n + j] + lj * rij) / (lj - li);
+  if (i != j && fabs(gap) > inv_max_angle * fabs(num)) e = num / gap;
   else e = 0.5 * rij;
   E[(size_t)i * n + j] = e;
   if (i == j) lam[i] = li;
@@ -119,14 +88,13 @@ __global__ void k_refine_E(const double* __restrict__ S, const double* __restric
 }  // namespace
 
 cudaError_t launch_refine(const double* C, int B, double* vc, double* lam, double* w, double* s,
-                          double* g, double* e, DevHeader* hdr, cudaStream_t st) {
+                          double* g, double* e, DevHeader* hdr, double max_angle, cudaStream_t st) {
   const dim3 grid((B + kT - 1) / kT, (B + kT - 1) / kT);
   k_dgemm<false><<<grid, kT * kT, 0, st>>>(C, vc, nullptr, w, B);   // W = C V
   k_dgemm<true><<<grid, kT * kT, 0, st>>>(vc, w, nullptr, s, B);    // S = V^T W
   k_dgemm<true><<<grid, kT * kT, 0, st>>>(vc, vc, nullptr, g, B);   // G = V^T V
-  k_refine_norms<<<1, 1024, 0, st>>>(C, s, g, B, hdr);
   cudaMemsetAsync(&hdr->refine_res, 0, sizeof(double), st);
-  k_refine_E<<<dim3((B + 127) / 128, B), 128, 0, st>>>(s, g, B, e, lam, hdr);
+  k_refine_E<<<dim3((B + 127) / 128, B), 128, 0, st>>>(s, g, B, e, lam, hdr, 1.0 / max_angle);
   k_dgemm<false><<<grid, kT * kT, 0, st>>>(vc, e, vc, w, B);        // V' = V E + V
   cudaMemcpyAsync(vc, w, sizeof(double) * (size_t)B * B, cudaMemcpyDeviceToDevice, st);
   return cudaGetLastError();

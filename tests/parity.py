@@ -20,6 +20,7 @@ EPS = {"p64": 1e-15, "mix": 1e-7, "p32": 1e-6}
 LAM_TOL = {"p64": 1e-10, "mix": 2e-5, "p32": 2e-3}
 MU_TOL = {"p64": 1e-12, "mix": 1e-6, "p32": 1e-6}
 LAM_ALL_TOL = {"p64": 1e-8, "mix": 1e-4, "p32": 2e-3}
+ORTH_TOL = {"p64": 1e-12, "mix": 1e-6, "p32": 1e-4}
 Q_TOL = {"p64": 1e-4, "mix": 1e-4, "p32": 1e-2}
 
 
@@ -73,7 +74,7 @@ def compare(gpu, ref, k, form, check_q=True):
         assert np.all(lam == 0.0)
     # orthogonality of the returned eigenvectors
     m["orth"] = float(np.abs(V.T @ V - np.eye(B)).max())
-    assert m["orth"] <= {"p64": 1e-12, "mix": 1e-12, "p32": 1e-4}[form], m
+    assert m["orth"] <= ORTH_TOL[form], m
     # eigenvectors: individually where separated, else subspace of the top-k
     Vs, Vr = sign_norm(V), ref["V"]
     vec_err = 0.0

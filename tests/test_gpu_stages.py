@@ -1,0 +1,100 @@
+"""Stage-by-stage GPU parity through the C ABI (pca_covariance, pca_eigh,
+pca_project) against the FP64 oracle, so that each row of the hot path is
+checked on its own inputs:
+
+  band means + covariance  (Algorithm 1 stages 2-3)   pca_covariance
+  Jacobi + sort + sign     (stage 4, Eqs. 2-10)       pca_eigh on the oracle's C
+  projection               (stages 5-6)               pca_project on the oracle's mu, V
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity import LAM_TOL, ORTH_TOL, rel_gaps, sign_norm
+
+# covariance: max_ij |C - C*| / max_ij |C*|
+COV_TOL = {"p64": 1e-13, "p32": 2e-6, "mix": 2e-5}
+MU_TOL = {"p64": 1e-13, "p32": 1e-6, "mix": 1e-6}
+
+
+def cubes_small():
+    return [synth.linear_mixing(seed=7, rows=37, cols=41, bands=64, endmembers=5),
+            synth.linear_mixing(seed=8, rows=33, cols=31, bands=103, endmembers=6)] + \
+        synth.paper_scenes(scale=0.2)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", ["p32", "mix", "p64"])
+def test_covariance_stage(gbpca_lib, form):
+    g = gbpca_lib
+    for cube in cubes_small():
+        Y = torch.from_numpy(cube.Y).cuda()
+        mu, C, info = g.covariance(Y, precision=form)
+        torch.cuda.synchronize()
+        assert info["status"] == 0
+        mu_ref = oracle.band_means(cube.Y)
+        C_ref = oracle.covariance(cube.Y, mu_ref)
+        mu_err = np.abs(mu.cpu().numpy() - mu_ref).max() / np.abs(mu_ref).max()
+        cov_err = np.abs(C.cpu().numpy() - C_ref).max() / np.abs(C_ref).max()
+        print(f"{cube.name} {form} mu_err={mu_err:.3e} cov_err={cov_err:.3e}")
+        assert mu_err <= MU_TOL[form]
+        assert cov_err <= COV_TOL[form]
+        assert np.array_equal(C.cpu().numpy(), C.cpu().numpy().T)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", ["p32", "mix", "p64"])
+def test_eigh_stage_on_oracle_covariance(gbpca_lib, form):
+    g = gbpca_lib
+    for cube in cubes_small():
+        C_ref = oracle.covariance(cube.Y)
+        ev, V, info = g.eigh(torch.from_numpy(C_ref).cuda(), precision=form)
+        torch.cuda.synchronize()
+        assert info["status"] == 0, info
+        A_k, V_ref, _ = oracle.jacobi(C_ref, tol=1e-15)
+        lam_ref, V_ref = oracle.sort_sign(np.diag(A_k), V_ref)
+        lam = ev.cpu().numpy()
+        Vg = V.cpu().numpy()
+        k = cube.k
+        gaps = rel_gaps(lam_ref)
+        eps = {"p64": 1e-15, "mix": 1e-12, "p32": 1e-6}[form]
+        pinned = gaps[:k] >= 1e3 * eps
+        rel = np.abs(lam[:k] - lam_ref[:k]) / np.abs(lam_ref[:k])
+        print(f"{cube.name} {form} eig_rel_topk={rel[pinned].max():.3e} "
+              f"all/l1={np.abs(lam - lam_ref).max() / lam_ref[0]:.3e} "
+              f"orth={np.abs(Vg.T @ Vg - np.eye(cube.B)).max():.3e} sweeps={info['sweeps']}")
+        tol = {"p64": 1e-10, "mix": 1e-9, "p32": LAM_TOL["p32"]}[form]
+        assert rel[pinned].max() <= tol
+        assert np.abs(Vg.T @ Vg - np.eye(cube.B)).max() <= ORTH_TOL[form]
+        # residual of the eigen-equation, relative to ||C||
+        res = np.abs(C_ref @ Vg[:, :k] - Vg[:, :k] * lam[None, :k]).max() / lam_ref[0]
+        assert res <= {"p64": 1e-12, "mix": 1e-9, "p32": 1e-4}[form]
+        assert np.array_equal(sign_norm(Vg), Vg)
+
+
+@pytest.mark.gpu
+def test_eigh_sort_ties_and_diagonal_input(gbpca_lib):
+    g = gbpca_lib
+    A = np.diag([3.0, 1.0, 3.0, 2.0, 0.5])
+    for form in ("p32", "mix", "p64"):
+        ev, V, info = g.eigh(torch.from_numpy(A).cuda(), precision=form)
+        assert info["sweeps"] == 0
+        assert list(ev.cpu().numpy()) == [3.0, 3.0, 2.0, 1.0, 0.5]
+        assert np.array_equal(V.cpu().numpy()[:, :2], np.eye(5)[:, [0, 2]])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
+def test_project_stage(gbpca_lib, dtype):
+    g = gbpca_lib
+    cube = synth.linear_mixing(seed=11, rows=45, cols=47, bands=96, endmembers=6, k=6)
+    Yt = torch.from_numpy(cube.Y).to(dtype)
+    ref = oracle.pca_fit(Yt, cube.k, tol=1e-14)
+    Q = g.project(Yt.cuda(), torch.from_numpy(ref["mu"]).cuda(), torch.from_numpy(ref["V"]).cuda(),
+                  cube.k)
+    Qn = Q.cpu().numpy().astype(np.float64)
+    for j in range(cube.k):
+        err = np.abs(Qn[:, j] - ref["Q"][:, j]).max() / np.abs(ref["Q"][:, j]).max()
+        assert err <= 1e-5, (j, err)
