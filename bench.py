@@ -247,11 +247,24 @@ def main(argv=None):
                  torch.empty(c.N, c.k, dtype=torch.float32, device=dev)) for c in cubes]
         return ws, outs
 
+    # the cubes are independent problems: each gets its own stream, joined per step
+    side = [torch.cuda.Stream(device=dev) for _ in cubes]
+
     def step(prec, ws, outs, Ys=None):
         Ys = Yd if Ys is None else Ys
-        for c, Y, w, o in zip(cubes, Ys, ws, outs):
+        main = torch.cuda.current_stream(dev)
+        fork = torch.cuda.Event()
+        fork.record(main)
+        joins = []
+        for c, Y, w, o, st in zip(cubes, Ys, ws, outs, side):
+            st.wait_event(fork)
             g.fit(Y, c.k, tol=c.tol, sweeps_max=c.sweeps_max, precision=prec, out=o, workspace=w,
-                  sync=False)
+                  sync=False, stream=st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+            joins.append(ev)
+        for ev in joins:
+            main.wait_event(ev)
 
     def timed(prec, steps, warmup, with_profile=False, sampler=None):
         ws, outs = setup(prec)
@@ -283,6 +296,7 @@ def main(argv=None):
         for c, Y, w, o in zip(cubes, Yd, ws, outs):
             infos.append(g.fit(Y, c.k, tol=c.tol, sweeps_max=c.sweeps_max, precision=prec, out=o,
                                workspace=w, sync=True)[4])
+        torch.cuda.synchronize()
         res = [tuple(t.cpu().numpy() for t in o) for o in outs]
         return total, stages, infos, res
 
@@ -379,6 +393,7 @@ def main(argv=None):
         def e2e_step():
             Ys = [y.to(dev, non_blocking=True) for y in Yh]
             step(args.precision, ws, outs, Ys)
+            # the copies back wait for both cubes' streams (joined into the current stream)
             for o, h in zip(outs, host_out):
                 for t, th in zip(o, h):
                     th.copy_(t, non_blocking=True)
@@ -411,7 +426,8 @@ def main(argv=None):
             "config": {"workload": WORKLOAD, "precision": args.precision,
                        "cubes": [f"{c.name} N={c.N} B={c.B}" for c in cubes],
                        "units_per_step": units, "l2": "flushed by a 256 MiB write before each step",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "streams": "one CUDA stream per cube, joined every step"},
             "forms": {"mix": {"value": value, "ms_per_step": t_mix / args.steps * 1e3,
                               "sweeps": [i["sweeps"] for i in infos_mix], **errors.get("mix", {})},
                       "p32": {"value": value_p32, "ms_per_step": t_p32 / args.steps * 1e3,

@@ -64,7 +64,10 @@ typedef enum { PCA_F32 = 0, PCA_BF16 = 1, PCA_F16 = 2 } pca_dtype;
  *     refinement).
  *   PCA_PREC_MIX: covariance on the tensor cores from a two-term BF16
  *     split of the centred cube (three products, FP32 accumulation per
- *     chunk), FP32 Jacobi, one FP64 refinement iteration.
+ *     chunk), FP32 Jacobi stopped on the Frobenius test, one refinement
+ *     iteration and two orthogonalisation steps in double-float/FP64.  The
+ *     BF16 split bounds the covariance at about 2^-17 relative per element,
+ *     so eigenvalue errors are about 2e-5 of the largest eigenvalue.
  */
 typedef enum { PCA_PREC_P64 = 0, PCA_PREC_P32 = 1, PCA_PREC_MIX = 2 } pca_precision;
 
@@ -92,9 +95,11 @@ size_t pca_workspace_size(int64_t N, int B, int k, pca_dtype dtype, pca_precisio
  * B          bands, 2 <= B <= 232.
  * k          components to project onto, 1 <= k <= min(B, 32).
  * tol        Jacobi stop factor (Sec. 2, "until all off-diagonal elements are
- *            smaller than the stop factor"), read as off(A) <= tol*||A||_F
- *            with off(A) the Frobenius norm of the off-diagonal part.  The
- *            FP32 Jacobi applies max(tol, 2^-22); *info reports it.  tol > 0.
+ *            smaller than the stop factor").  The FP32 Jacobi applies
+ *            tau = max(tol, 2^-22) (*info reports it): P32 and P64 stop when
+ *            every |a_pq| <= tau sqrt(|a_pp a_qq|); MIX stops when
+ *            off(A) <= tau ||A||_F (off: Frobenius norm of the off-diagonal
+ *            part) and leaves the rest to the refinement.  tol > 0.
  * sweeps_max maximum Jacobi sweeps, >= 1.
  * mu         [B] FP64 out: band means (Algorithm 1 stage 2).
  * eigvals    [B] FP64 out: eigenvalues of C, descending; equal values keep

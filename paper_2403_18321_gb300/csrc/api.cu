@@ -96,6 +96,9 @@ Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, in
   L.s2_part = take((size_t)L.s2_bytes_el * L.partials * L.s2_elems);
   L.dvec = take(sizeof(double) * B);
   L.cov = take(BB8);
+  L.cdf = take(BB8);
+  L.rank = take(sizeof(int) * B);
+  L.sgn = take(sizeof(double) * B);
   L.diag32 = take(sizeof(float) * Bp);
   L.log = take(sizeof(float2) * (size_t)kMaxSweeps * Bp * P);
   L.v32 = take(sizeof(float) * (size_t)Bp * Bp);
@@ -156,15 +159,18 @@ struct Ptrs {
   void* s2p;
   double* dvec;
   double* C;
+  float2* cdf;
+  int* rank;
+  double* sgn;
   float* diag32;
   float2* log;
   float* v32;
   double* lam;
-  double* vc;
-  double* w;
-  double* s;
-  double* g;
-  double* e;
+  float2* vc;
+  float2* w;
+  float2* s;
+  float2* g;
+  float2* e;
   float* vk;
   float* muf;
 };
@@ -178,22 +184,30 @@ Ptrs carve(void* workspace, const Layout& L) {
   p.s2p = ws + L.s2_part;
   p.dvec = reinterpret_cast<double*>(ws + L.dvec);
   p.C = reinterpret_cast<double*>(ws + L.cov);
+  p.cdf = reinterpret_cast<float2*>(ws + L.cdf);
+  p.rank = reinterpret_cast<int*>(ws + L.rank);
+  p.sgn = reinterpret_cast<double*>(ws + L.sgn);
   p.diag32 = reinterpret_cast<float*>(ws + L.diag32);
   p.log = reinterpret_cast<float2*>(ws + L.log);
   p.v32 = reinterpret_cast<float*>(ws + L.v32);
   p.lam = reinterpret_cast<double*>(ws + L.lam);
-  p.vc = reinterpret_cast<double*>(ws + L.vc);
-  p.w = reinterpret_cast<double*>(ws + L.w);
-  p.s = reinterpret_cast<double*>(ws + L.s);
-  p.g = reinterpret_cast<double*>(ws + L.r);
-  p.e = reinterpret_cast<double*>(ws + L.e);
+  p.vc = reinterpret_cast<float2*>(ws + L.vc);
+  p.w = reinterpret_cast<float2*>(ws + L.w);
+  p.s = reinterpret_cast<float2*>(ws + L.s);
+  p.g = reinterpret_cast<float2*>(ws + L.r);
+  p.e = reinterpret_cast<float2*>(ws + L.e);
   p.vk = reinterpret_cast<float*>(ws + L.vk);
   p.muf = reinterpret_cast<float*>(ws + L.muf);
   return p;
 }
 
 // largest first-order angle the refinement applies (pairs above it count as clustered)
-double refine_max_angle(pca_precision prec) { return prec == PCA_PREC_MIX ? 1.0 / 1024 : 1.0 / 64; }
+double refine_max_angle(pca_precision prec) { (void)prec; return 1.0 / 64; }
+// closing Newton-Schulz orthogonalisation steps
+int ortho_steps(pca_precision prec) { return prec == PCA_PREC_P32 ? 0 : 2; }
+// MIX stops its FP32 sweeps on the Frobenius test (the refinement resolves what
+// the element-wise test would still demand); P32 and P64 use the element-wise test
+bool relative_stop(pca_precision prec) { return prec != PCA_PREC_MIX; }
 
 // stages 2-3 of Algorithm 1: band means and covariance in one pass over the cube
 cudaError_t run_cov(const void* cube, pca_dtype dt, int64_t N, int B, pca_precision prec,
@@ -216,19 +230,24 @@ cudaError_t run_eigh(const double* A, int B, float tol32, int sweeps_max, pca_pr
                      StageMark& pm) {
   cudaError_t e;
   pm.mark(2);
-  if ((e = launch_jacobi(A, B, tol32, sweeps_max, P.log, P.diag32, P.hdr, st)) != cudaSuccess) return e;
+  if ((e = launch_jacobi(A, B, tol32, sweeps_max, relative_stop(prec), P.log, P.diag32, P.hdr,
+                         st)) != cudaSuccess)
+    return e;
   pm.mark(3);
   if ((e = launch_vreplay(P.log, B, P.hdr, P.v32, st)) != cudaSuccess) return e;
   pm.mark(4);
   if ((e = launch_compact(P.diag32, P.v32, B, P.hdr, P.lam, P.vc, st)) != cudaSuccess) return e;
   pm.mark(5);
   const int iters = refine_iterations(prec);
+  if (iters > 0 && (e = launch_to_df(A, P.cdf, B * B, st)) != cudaSuccess) return e;
   for (int it = 0; it < iters; ++it)
-    if ((e = launch_refine(A, B, P.vc, P.lam, P.w, P.s, P.g, P.e, P.hdr, refine_max_angle(prec),
-                           st)) != cudaSuccess)
+    if ((e = launch_refine(P.cdf, B, P.vc, P.lam, P.w, P.s, P.g, P.e, P.hdr,
+                           refine_max_angle(prec), st)) != cudaSuccess)
       return e;
+  for (int it = 0; it < ortho_steps(prec); ++it)
+    if ((e = launch_orthonormalize(P.vc, B, P.w, P.g, P.e, st)) != cudaSuccess) return e;
   pm.mark(6);
-  return launch_sort_sign(P.lam, P.vc, B, k, eigvals, eigvecs, P.vk, P.hdr, st);
+  return launch_sort_sign(P.lam, P.vc, B, k, eigvals, eigvecs, P.vk, P.rank, P.sgn, st);
 }
 
 }  // namespace
@@ -330,8 +349,10 @@ int pca_version(void) { return 100; }
 
 int pca_kernel_launches(pca_precision prec, int with_projection) {
   // header init, covariance, band-sum reduce, covariance finalise, Jacobi,
-  // V replay, compact, 4 per refinement iteration, sort/sign, projection
-  return 7 + 4 * refine_iterations(prec) + 1 + (with_projection ? 1 : 0);
+  // V replay, compact, 4 per refinement iteration, 1 conversion, 3 per
+  // orthogonalisation step, rank/sign + scatter, projection
+  const int it = refine_iterations(prec);
+  return 7 + 4 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
 }
 
 int pca_profile(int enable) {

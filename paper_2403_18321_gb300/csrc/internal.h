@@ -33,7 +33,7 @@ struct DevHeader {
 
 // Offsets (bytes) of every workspace region; all 256-byte aligned.
 struct Layout {
-  size_t hdr, shift, s1_part, s2_part, dvec, cov, diag32, log, v32, lam, vc, w, s, r, e, vk, muf;
+  size_t hdr, shift, s1_part, s2_part, dvec, cov, cdf, rank, sgn, diag32, log, v32, lam, vc, w, s, r, e, vk, muf;
   size_t total;
   int partials;      // number of covariance partial slots the SYRK uses
   int s2_elems;      // packed upper-triangle entries per partial: B(B+1)/2
@@ -69,26 +69,38 @@ cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const
                                 double* C, float* mu_f, double* dvec, DevHeader* hdr,
                                 cudaStream_t st);
 
-// FP32 odd-even Jacobi on one SM; logs (c, s) of every rotation.
-cudaError_t launch_jacobi(const double* C, int B, float tol32, int sweeps_max, float2* log,
-                          float* diag32, DevHeader* hdr, cudaStream_t st);
+// FP32 odd-even Jacobi on one SM; logs (c, s) of every rotation.  relative_stop
+// selects the element-wise relative stop test (else off(A) <= tol ||A||_F).
+cudaError_t launch_jacobi(const double* C, int B, float tol32, int sweeps_max, bool relative_stop,
+                          float2* log, float* diag32, DevHeader* hdr, cudaStream_t st);
 
 // Replays the rotation log on the rows of V (starting from I) -> V32 [B'][B'].
 cudaError_t launch_vreplay(const float2* log, int B, const DevHeader* hdr, float* v32,
                            cudaStream_t st);
 
-// Drops the padding slot: lam (FP64) [B] and Vc (FP64) [B][B] in slot order.
+// Drops the padding slot: lam (FP64) [B] and Vc [B][B] in slot order, Vc as
+// double-float (hi, lo) pairs.
 cudaError_t launch_compact(const float* diag32, const float* v32, int B, DevHeader* hdr,
-                           double* lam, double* vc, cudaStream_t st);
+                           double* lam, float2* vc, cudaStream_t st);
+
+// dst = src as double-float (hi, lo) pairs.
+cudaError_t launch_to_df(const double* src, float2* dst, int count, cudaStream_t st);
 
 // One Newton-type refinement iteration of the eigen-decomposition in FP64.
-// max_angle: pairs whose first-order angle exceeds it are only re-orthogonalised.
-cudaError_t launch_refine(const double* C, int B, double* vc, double* lam, double* w, double* s,
-                          double* r, double* e, DevHeader* hdr, double max_angle, cudaStream_t st);
+// One refinement iteration (double-float products, FP64 angles); C, vc, w, s,
+// g, e are B x B double-float.  max_angle: pairs whose first-order angle
+// exceeds it are only re-orthogonalised.
+cudaError_t launch_refine(const float2* C, int B, float2* vc, double* lam, float2* w, float2* s,
+                          float2* g, float2* e, DevHeader* hdr, double max_angle, cudaStream_t st);
+
+// One Newton-Schulz orthogonalisation step of V (double-float).
+cudaError_t launch_orthonormalize(float2* vc, int B, float2* w, float2* g, float2* e,
+                                  cudaStream_t st);
 
 // Sort descending, sign-normalise, write eigvals/eigvecs (FP64) and V_k (FP32).
-cudaError_t launch_sort_sign(const double* lam, const double* vc, int B, int k, double* eigvals,
-                             double* eigvecs, float* vk, DevHeader* hdr, cudaStream_t st);
+// rank [B] (int) and sgn [B] (FP64) are scratch.
+cudaError_t launch_sort_sign(const double* lam, const float2* vc, int B, int k, double* eigvals,
+                             double* eigvecs, float* vk, int* rank, double* sgn, cudaStream_t st);
 
 // mu_f = (float)mu, vk = (float)eigvecs[:, :k] (eigvecs B x B row-major).
 cudaError_t launch_narrow_inputs(const double* mu, const double* eigvecs, int B, int k, float* mu_f,

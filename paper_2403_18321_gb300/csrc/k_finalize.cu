@@ -7,64 +7,65 @@ namespace gbpca {
 
 namespace {
 
-// One CTA of 4 x 256 threads.  Rank of eigenvalue j = number of eigenvalues
-// that sort before it (larger, or equal and at a lower position); no
-// comparison sort is needed for B <= 232.  Thread (q, j) scans rows i = q
-// mod 4 of source column j (coalesced across j) for the entry of largest
-// magnitude (lowest row on ties), the four partial results are combined, and
-// every column is written to its sorted position with the sign that makes
-// that entry positive.
-__global__ void __launch_bounds__(1024)
-k_sort_sign(const double* __restrict__ lam, const double* __restrict__ vc, int B, int k,
-            double* __restrict__ eigvals, double* __restrict__ eigvecs, float* __restrict__ vk) {
-  __shared__ double ls[kMaxB];
-  __shared__ int rank_s[kMaxB];
-  __shared__ double sgn_s[kMaxB];
-  __shared__ double best_v[4][256];
-  __shared__ int best_i[4][256];
-  const int j = threadIdx.x & 255, q = threadIdx.x >> 8;
-  for (int t = threadIdx.x; t < B; t += blockDim.x) ls[t] = lam[t];
-  __syncthreads();
-  if (q == 0 && j < B) {
-    const double lj = ls[j];
-    int r = 0;
-    for (int i = 0; i < B; ++i) {
-      const double li = ls[i];
-      r += (li > lj) || (li == lj && i < j);
-    }
-    rank_s[j] = min(r, B - 1);
+// Sort and sign rule in two fully parallel passes.
+// k_rank_sign: one CTA per eigen-pair j.  Its rank = number of eigenvalues
+// that sort before it (larger, or equal and at a lower position) -- no
+// comparison sort needed for B <= 232 -- and the sign that makes the entry of
+// largest magnitude (lowest row on ties) of column j positive.
+__global__ void __launch_bounds__(256)
+k_rank_sign(const double* __restrict__ lam, const float2* __restrict__ vc, int B,
+            int* __restrict__ rank, double* __restrict__ sgn, double* __restrict__ eigvals) {
+  __shared__ int cnt[8];
+  __shared__ double bv[8];
+  __shared__ int bi[8];
+  const int j = blockIdx.x, i = threadIdx.x, lane = i & 31, warp = i >> 5;
+  const double lj = lam[j];
+  int c = 0;
+  double v = -1.0;
+  int vi = 0x7fffffff;
+  if (i < B) {
+    const double li = lam[i];
+    c = (li > lj) || (li == lj && i < j);
+    const float2 x = vc[(size_t)i * B + j];
+    v = fabs((double)x.x + (double)x.y);
+    vi = i;
   }
-  if (j < B) {
-    double bv = -1.0;
-    int bi = 0;
-    for (int i = q; i < B; i += 4) {
-      const double a = fabs(vc[(size_t)i * B + j]);
-      if (a > bv) { bv = a; bi = i; }
-    }
-    best_v[q][j] = bv;
-    best_i[q][j] = bi;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(kFull, c, o);
+    const double ov = __shfl_xor_sync(kFull, v, o);
+    const int oi = __shfl_xor_sync(kFull, vi, o);
+    if (ov > v || (ov == v && oi < vi)) { v = ov; vi = oi; }
   }
+  if (lane == 0) { cnt[warp] = c; bv[warp] = v; bi[warp] = vi; }
   __syncthreads();
-  if (q == 0 && j < B) {
-    double bv = best_v[0][j];
-    int bi = best_i[0][j];
-    for (int t = 1; t < 4; ++t) {
-      const double v = best_v[t][j];
-      const int i = best_i[t][j];
-      if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+  if (i == 0) {
+    int tot = 0;
+    double best = -1.0;
+    int besti = 0x7fffffff;
+    for (int w = 0; w < 8; ++w) {
+      tot += cnt[w];
+      if (bv[w] > best || (bv[w] == best && bi[w] < besti)) { best = bv[w]; besti = bi[w]; }
     }
-    sgn_s[j] = vc[(size_t)bi * B + j] < 0.0 ? -1.0 : 1.0;
-    eigvals[rank_s[j]] = ls[j];
+    const int r = min(tot, B - 1);
+    const float2 x = vc[(size_t)besti * B + j];
+    rank[j] = r;
+    sgn[j] = ((double)x.x + (double)x.y) < 0.0 ? -1.0 : 1.0;
+    eigvals[r] = lj;
   }
-  __syncthreads();
-  if (j < B) {
-    const int r = rank_s[j];
-    const double sg = sgn_s[j];
-    for (int i = q; i < B; i += 4) {
-      const double v = sg * vc[(size_t)i * B + j];
-      eigvecs[(size_t)i * B + r] = v;
-      if (r < k) vk[(size_t)i * k + r] = (float)v;
-    }
+}
+
+// k_scatter: one CTA per row i of V writes row i of the sorted, signed eigvecs.
+__global__ void __launch_bounds__(256)
+k_scatter(const float2* __restrict__ vc, int B, int k, const int* __restrict__ rank,
+          const double* __restrict__ sgn, double* __restrict__ eigvecs, float* __restrict__ vk) {
+  const int i = blockIdx.x;
+  for (int j = threadIdx.x; j < B; j += blockDim.x) {
+    const float2 x = vc[(size_t)i * B + j];
+    const double v = sgn[j] * ((double)x.x + (double)x.y);
+    const int r = rank[j];
+    eigvecs[(size_t)i * B + r] = v;
+    if (r < k) vk[(size_t)i * k + r] = (float)v;
   }
 }
 
@@ -182,10 +183,10 @@ cudaError_t launch_narrow_inputs(const double* mu, const double* eigvecs, int B,
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_sign(const double* lam, const double* vc, int B, int k, double* eigvals,
-                             double* eigvecs, float* vk, DevHeader* hdr, cudaStream_t st) {
-  (void)hdr;
-  k_sort_sign<<<1, 1024, 0, st>>>(lam, vc, B, k, eigvals, eigvecs, vk);
+cudaError_t launch_sort_sign(const double* lam, const float2* vc, int B, int k, double* eigvals,
+                             double* eigvecs, float* vk, int* rank, double* sgn, cudaStream_t st) {
+  k_rank_sign<<<B, 256, 0, st>>>(lam, vc, B, rank, sgn, eigvals);
+  k_scatter<<<B, 256, 0, st>>>(vc, B, k, rank, sgn, eigvecs, vk);
   return cudaGetLastError();
 }
 

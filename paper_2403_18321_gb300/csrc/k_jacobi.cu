@@ -101,17 +101,50 @@ __device__ __forceinline__ void pair_rotation(float* A, int Bp, int p, float apq
   *dq = fmaf(-t, apq, app);
 }
 
+// Blocks (I, J) with J >= I + 2 of a step with np pairs, dealt to the bulk
+// warps: row I holds np-2-I of them; row f is folded with row np-3-f so that
+// every fold holds np-1 blocks; (fold, 32-lane chunk) work items go round-robin
+// over the bulk warps.  Every lane packs its blocks once per launch into
+// registers: word = I << 24 | J << 16 | shared-memory offset of (p_I, p_J).
+constexpr int kBulkWarps = kJacThreads / 32 - kBandWarps;
+constexpr int kMaxItems = 9;   // ceil(ceil((116-2)/2) * ceil(115/32) / 28) for B' = 232
+
+__device__ __forceinline__ void build_items(int np, int e, int Bp, uint32_t* items) {
+  const int lane = threadIdx.x & 31, bw = (threadIdx.x >> 5) - kBandWarps;
+  const int rows = np - 2;
+  const int nfold = rows > 0 ? (rows + 1) / 2 : 0;
+  const int per = np - 1;
+  const int nch = (per + 31) >> 5;
+#pragma unroll
+  for (int t = 0; t < kMaxItems; ++t) {
+    items[t] = 0xffffffffu;
+    const int wi = bw + t * kBulkWarps;
+    if (rows <= 0 || wi >= nfold * nch) continue;
+    const int f = wi / nch;
+    const int x = ((wi - f * nch) << 5) + lane;
+    const int first = np - 2 - f;
+    const int limit = (2 * f + 1 == rows) ? first : per;
+    if (x >= limit) continue;
+    int I, J;
+    if (x < first) { I = f; J = f + 2 + x; }
+    else { I = np - 3 - f; J = I + 2 + (x - first); }
+    const int off = (2 * I + e) * Bp + 2 * J + e;
+    items[t] = ((uint32_t)I << 24) | ((uint32_t)J << 16) | (uint32_t)off;
+  }
+}
+
 // One parallel step.  Even steps (e = 0) rotate position pairs (2J, 2J+1),
 // odd steps (e = 1) the pairs (2J+1, 2J+2) with positions 0 and Bp-1 idle.
 // The diagonal blocks of this step were finished (and cur[] filled) before it
 // started.  Band warps update the super-diagonal blocks (I, I+1) and, unless
 // this is the last step of the sweep, immediately rotate the diagonal block
 // of the next step's pair that block completes, filling nxt[]; they also
-// handle the idle row 0 / column Bp-1 of odd steps.  The other warps update
-// every block (I, J) with J >= I + 2.
+// handle the idle row 0 / column Bp-1 of odd steps.  The bulk warps update
+// every block (I, J) with J >= I + 2 from their packed item lists.
 __device__ __forceinline__ void jacobi_step(float* A, int Bp, int P, int e, bool last,
-                                            const float2* cur, float2* nxt, float2* log_next) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+                                            const float2* cur, float2* nxt, float2* log_next,
+                                            const uint32_t* items) {
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int np = P - e;
   if (warp < kBandWarps) {
     const int b = tid;
@@ -171,25 +204,12 @@ __device__ __forceinline__ void jacobi_step(float* A, int Bp, int P, int e, bool
       }
     }
   } else {
-    // blocks (I, J), J >= I + 2: row I holds np-2-I of them; fold row f with
-    // row np-3-f so that every fold holds np-1 blocks
-    const int rows = np - 2;
-    if (rows <= 0) return;
-    const int nfold = (rows + 1) / 2;
-    const int per = np - 1;
-    const int nch = (per + 31) >> 5;
-    const int bw = warp - kBandWarps, nbw = kJacThreads / 32 - kBandWarps;
-    for (int wi = bw; wi < nfold * nch; wi += nbw) {
-      const int f = wi / nch;
-      const int x = ((wi - f * nch) << 5) + lane;
-      const int first = np - 2 - f;
-      const int limit = (2 * f + 1 == rows) ? first : per;
-      if (x >= limit) continue;
-      int I, J;
-      if (x < first) { I = f; J = f + 2 + x; }
-      else { I = np - 3 - f; J = I + 2 + (x - first); }
-      const int pI = 2 * I + e, pJ = 2 * J + e;
-      float* r0 = A + pI * Bp + pJ;
+#pragma unroll
+    for (int t = 0; t < kMaxItems; ++t) {
+      const uint32_t w = items[t];
+      if (w == 0xffffffffu) continue;
+      const float2 csI = cur[w >> 24], csJ = cur[(w >> 16) & 0xff];
+      float* r0 = A + (w & 0xffff);
       float* r1 = r0 + Bp;
       float m00, m01, m10, m11;
       if (e == 0) {
@@ -199,7 +219,7 @@ __device__ __forceinline__ void jacobi_step(float* A, int Bp, int P, int e, bool
       } else {
         m00 = r0[0]; m01 = r0[1]; m10 = r1[0]; m11 = r1[1];
       }
-      rot_block(cur[I], cur[J], m00, m01, m10, m11);
+      rot_block(csI, csJ, m00, m01, m10, m11);
       if (e == 0) {
         *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
         *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
@@ -211,7 +231,7 @@ __device__ __forceinline__ void jacobi_step(float* A, int Bp, int P, int e, bool
 }
 
 __global__ void __launch_bounds__(kJacThreads, 1)
-k_jacobi(const double* __restrict__ C, int B, float tol32, int sweeps_max,
+k_jacobi(const double* __restrict__ C, int B, float tol32, int sweeps_max, int relative_stop,
          float2* __restrict__ log, float* __restrict__ diag32, DevHeader* __restrict__ hdr) {
   extern __shared__ __align__(16) float A[];  // [Bp][Bp]
   __shared__ float2 cs[2][kMaxB / 2];
@@ -230,15 +250,28 @@ k_jacobi(const double* __restrict__ C, int B, float tol32, int sweeps_max,
     const int i = e / Bp, j = e - i * Bp;
     A[e] = (i < B && j < B) ? (float)C[(size_t)i * B + j] : 0.f;
   }
+  uint32_t items0[kMaxItems], items1[kMaxItems];
+  {  // the packed lists must hold every block of both parities (true for B' <= 232)
+    const int nw0 = ((P - 1) / 2) * ((P - 1 + 31) / 32);
+    if (nw0 > kMaxItems * kBulkWarps) {
+      if (tid == 0) { set_status(hdr, PCA_ERR_ARG); hdr->sweeps = 0; hdr->steps = 0; }
+      return;
+    }
+  }
+  if (warp >= kBandWarps) {
+    build_items(P, 0, Bp, items0);
+    build_items(P - 1, 1, Bp, items1);
+  }
   __syncthreads();
 
   int sweep = 0, status = PCA_OK;
   for (;;) {
-    // stop test (before every sweep).  Element-wise relative: every
+    // stop test (before every sweep).  relative_stop: element-wise, every
     // off-diagonal |a_pq| <= tol * sqrt(|a_pp a_qq|) -- the paper's "all
     // off-diagonal elements below the stop factor", scaled per pair so that
     // small eigenvalues converge to the same relative accuracy as large
-    // ones.  off(A)/||A||_F is reported beside it.
+    // ones; otherwise off(A) <= tol * ||A||_F (enough when an FP64
+    // refinement follows).  off(A)/||A||_F is reported either way.
     float so = 0.f, sd = 0.f;
     int viol = 0;
     const float tol2 = tol32 * tol32;
@@ -267,7 +300,8 @@ k_jacobi(const double* __restrict__ C, int B, float tol32, int sweeps_max,
       if (lane == 0) {
         const double off = sqrt(2.0 * o), fro = sqrt(2.0 * o + d);
         int flag = 0;
-        if (fro == 0.0 || !anyv) flag = 1;
+        const bool conv = relative_stop ? !anyv : off <= (double)tol32 * fro;
+        if (fro == 0.0 || conv) flag = 1;
         else if (sweep >= sweeps_max) flag = 2;
         s_flag = flag;
         hdr->off_rel = fro == 0.0 ? 0.0 : off / fro;
@@ -286,9 +320,11 @@ k_jacobi(const double* __restrict__ C, int B, float tol32, int sweeps_max,
       *ap = 0.f;
     }
     __syncthreads();
-    for (int step = 0; step < Bp; ++step) {
-      jacobi_step(A, Bp, P, step & 1, step == Bp - 1, cs[step & 1], cs[(step + 1) & 1],
-                  logs + (size_t)(step + 1) * P);
+    for (int step = 0; step < Bp; step += 2) {
+      jacobi_step(A, Bp, P, 0, false, cs[0], cs[1], logs + (size_t)(step + 1) * P, items0);
+      __syncthreads();
+      jacobi_step(A, Bp, P, 1, step + 1 == Bp - 1, cs[1], cs[0], logs + (size_t)(step + 2) * P,
+                  items1);
       __syncthreads();
     }
     ++sweep;
@@ -405,7 +441,7 @@ k_vreplay(const float2* __restrict__ log, int B, const DevHeader* __restrict__ h
 // lam[c], vc[i][c] for the real rows i < B and the real slots (padding slot dropped).
 __global__ void k_compact(const float* __restrict__ diag32, const float* __restrict__ v32, int B,
                           DevHeader* __restrict__ hdr, double* __restrict__ lam,
-                          double* __restrict__ vc) {
+                          float2* __restrict__ vc) {
   const int Bp = B + (B & 1);
   __shared__ int s_dummy;
   if (threadIdx.x == 0) s_dummy = -1;
@@ -422,7 +458,7 @@ __global__ void k_compact(const float* __restrict__ diag32, const float* __restr
     if (j == dmy) continue;
     const int c = (dmy >= 0 && j > dmy) ? j - 1 : j;
     if (c >= B) continue;
-    vc[(size_t)i * B + c] = (double)v32[(size_t)i * Bp + j];
+    vc[(size_t)i * B + c] = make_float2(v32[(size_t)i * Bp + j], 0.f);
     if (i == 0) lam[c] = (double)diag32[j];
   }
   if (i == 0 && threadIdx.x == 0) hdr->dummy_slot = dmy;
@@ -430,14 +466,15 @@ __global__ void k_compact(const float* __restrict__ diag32, const float* __restr
 
 }  // namespace
 
-cudaError_t launch_jacobi(const double* C, int B, float tol32, int sweeps_max, float2* log,
-                          float* diag32, DevHeader* hdr, cudaStream_t st) {
+cudaError_t launch_jacobi(const double* C, int B, float tol32, int sweeps_max, bool relative_stop,
+                          float2* log, float* diag32, DevHeader* hdr, cudaStream_t st) {
   const int Bp = round_even(B);
   const size_t smem = (size_t)Bp * Bp * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_jacobi<<<1, kJacThreads, smem, st>>>(C, B, tol32, sweeps_max, log, diag32, hdr);
+  k_jacobi<<<1, kJacThreads, smem, st>>>(C, B, tol32, sweeps_max, relative_stop ? 1 : 0, log,
+                                         diag32, hdr);
   return cudaGetLastError();
 }
 
@@ -458,7 +495,7 @@ cudaError_t launch_vreplay(const float2* log, int B, const DevHeader* hdr, float
 }
 
 cudaError_t launch_compact(const float* diag32, const float* v32, int B, DevHeader* hdr,
-                           double* lam, double* vc, cudaStream_t st) {
+                           double* lam, float2* vc, cudaStream_t st) {
   k_compact<<<B, 256, 0, st>>>(diag32, v32, B, hdr, lam, vc);
   return cudaGetLastError();
 }

@@ -1,59 +1,149 @@
-// k_refine.cu -- FP64 refinement of the FP32 Jacobi result.
+// k_refine.cu -- high-precision refinement of the FP32 Jacobi result.
 //
 // The FP32 sweeps leave eigenvalues and eigenvectors with errors of order
 // 2^-24 ||C||.  One refinement iteration is one simultaneous Jacobi-like
-// sweep in FP64 over all pairs at once: with S = V^T C V (nearly diagonal)
-// and R = I - V^T V, each pair (i, j) is turned by the first-order Jacobi
-// angle  E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)  -- the small-angle
-// limit t ~ m/2 = C_ij / (C_jj - C_ii) of Eqs. 3 and 7, corrected for the
-// non-orthogonality R -- and V <- V (I + E).  This is the iterative
-// refinement of Ogita and Aishima (Japan J. Indust. Appl. Math. 35, 2018),
-// which converges quadratically.  Their global cluster threshold (built from
-// norms of S - diag and of R) is replaced by a per-pair test on the angle
-// itself: pairs whose first-order angle exceeds 1/16 are treated as one
-// cluster and only re-orthogonalised (E_ij = R_ij / 2).
+// sweep over all pairs at once: with S = V^T C V (nearly diagonal) and
+// R = I - V^T V, each pair (i, j) is turned by the first-order Jacobi angle
+//     E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)
+// -- the small-angle limit t ~ m/2 = C_ij / (C_jj - C_ii) of Eqs. 3 and 7,
+// corrected for the non-orthogonality R -- and V <- V (I + E).  This is the
+// iterative refinement of Ogita and Aishima (Japan J. Indust. Appl. Math. 35,
+// 2018), which converges quadratically.  Their global cluster threshold is
+// replaced by a per-pair test on the angle itself: a pair whose first-order
+// angle exceeds `max_angle` is treated as part of a cluster and only
+// re-orthogonalised (E_ij = R_ij / 2).  A first-order update leaves V
+// non-orthogonal by O(||E||^2); a closing Newton-Schulz step
+// V <- V (3I - V^T V)/2 squares that away (launch_orthonormalize).
 //
-// GB300 executes FP64 at about 1/58 of its FP32 rate, so only these O(B^3)
-// GEMMs (spread over every SM) and the small element-wise steps run in FP64.
+// Arithmetic: GB300 executes FP64 at about 1/58 of its FP32 rate (1.9 DFMA
+// per clock per SM), which would make each B^3 product cost ~20 us at
+// B = 224.  The products therefore run in double-float: every matrix is kept
+// as an unevaluated sum hi + lo of two FP32 values (48-bit significand), each
+// product is formed exactly with one FMA (Dekker/Kahan "TwoProduct"), and the
+// running sum is carried with Knuth's "TwoSum" (error-free transformations;
+// Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26, 2005).  Only the O(B^2)
+// element-wise steps (angles, lambda) use FP64.
 #include "common.cuh"
 
 namespace gbpca {
 
 namespace {
 
-constexpr int kT = 16;  // output tile edge; 16x16 tiles spread B<=232 over ~200 CTAs
+constexpr int kT = 16;           // output tile edge per CTA
+constexpr int kTh = 64;          // threads per CTA: 8 x 8, each 2 x 2 outputs
 
-// D = op(A) Bm (+ X), all n x n row-major FP64.  op(A) = A or A^T.
+__device__ __forceinline__ double df_to_d(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ float2 d_to_df(double d) {
+  const float hi = (float)d;
+  return make_float2(hi, (float)(d - (double)hi));
+}
+
+// acc += a * b in double-float.  The _rn intrinsics keep the compiler from
+// contracting the error-free transformations into fused operations.
+__device__ __forceinline__ void df_mac(float2& acc, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);           // exact: a.x*b.x = p + e
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);                  // a.y*b.y (2^-48 relative) dropped
+  const float s = __fadd_rn(acc.x, p);    // TwoSum(acc.x, p)
+  const float z = __fsub_rn(s, acc.x);
+  const float t = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, z)), __fsub_rn(p, z));
+  acc.y = __fadd_rn(acc.y, __fadd_rn(t, e));
+  acc.x = s;
+}
+__device__ __forceinline__ float2 df_norm(float2 v) {  // Fast2Sum renormalisation
+  const float s = __fadd_rn(v.x, v.y);
+  return make_float2(s, __fsub_rn(v.y, __fsub_rn(s, v.x)));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float z = __fsub_rn(s, a.x);
+  const float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, z)), __fsub_rn(b.x, z));
+  return df_norm(make_float2(s, __fadd_rn(__fadd_rn(t, a.y), b.y)));
+}
+
+// D = op(A) Bm (+ X), n x n row-major double-float (float2 = hi, lo).
+// CTA = 16 x 16 output tile, 256 threads = 4 K-groups x (8 x 8 threads with
+// 2 x 2 outputs each); the K-groups take every fourth 16-wide K chunk and
+// their partial sums are added at the end (enough warps per SM to hide the
+// dependent chains of the error-free transformations).
 template <bool kTransA>
-__global__ void __launch_bounds__(kT* kT)
-k_dgemm(const double* __restrict__ A, const double* __restrict__ Bm,
-        const double* __restrict__ X, double* __restrict__ D, int n) {
-  __shared__ double as[kT][kT + 1];
-  __shared__ double bs[kT][kT + 1];
-  const int tx = threadIdx.x % kT, ty = threadIdx.x / kT;
-  const int row = blockIdx.y * kT + ty, col = blockIdx.x * kT + tx;
-  double acc = 0.0;
-  for (int k0 = 0; k0 < n; k0 += kT) {
-    // as[ty][tx] = op(A)[row][k0 + tx]
-    {
-      const int r = blockIdx.y * kT + ty, k = k0 + tx;
-      double v = 0.0;
-      if (r < n && k < n) v = kTransA ? A[(size_t)k * n + r] : A[(size_t)r * n + k];
-      as[ty][tx] = v;
-    }
-    {
-      const int k = k0 + ty, c = blockIdx.x * kT + tx;
-      bs[ty][tx] = (k < n && c < n) ? Bm[(size_t)k * n + c] : 0.0;
-    }
-    __syncthreads();
+__global__ void __launch_bounds__(kTh * 4)
+k_dfgemm(const float2* __restrict__ A, const float2* __restrict__ Bm,
+         const float2* __restrict__ X, float2* __restrict__ D, int n) {
+  __shared__ float2 as[4][kT][kT + 1];  // as[group][k][row]
+  __shared__ float2 bs[4][kT][kT + 1];  // bs[group][k][col]
+  __shared__ float2 red[3][kT * kT];
+  const int grp = threadIdx.x / kTh, t = threadIdx.x % kTh;
+  const int tx = t & 7, ty = t >> 3;
+  const int r0 = blockIdx.y * kT, c0 = blockIdx.x * kT;
+  float2 acc[2][2];
 #pragma unroll
-    for (int kk = 0; kk < kT; ++kk) acc = fma(as[ty][kk], bs[kk][tx], acc);
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  const int nchunks = (n + kT - 1) / kT;
+  for (int base = 0; base < nchunks; base += 4) {
+    const int ch = base + grp;
+    const int k0 = ch * kT;
+    if (ch < nchunks) {
+      for (int e = t; e < kT * kT; e += kTh) {
+        const int a = e / kT, b = e % kT;
+        {  // as[k = b][row = a] = op(A)[r0 + a][k0 + b]
+          const int r = r0 + a, k = k0 + b;
+          float2 v = make_float2(0.f, 0.f);
+          if (r < n && k < n) v = kTransA ? A[(size_t)k * n + r] : A[(size_t)r * n + k];
+          as[grp][b][a] = v;
+        }
+        {  // bs[k = a][col = b] = Bm[k0 + a][c0 + b]
+          const int k = k0 + a, c = c0 + b;
+          bs[grp][a][b] = (k < n && c < n) ? Bm[(size_t)k * n + c] : make_float2(0.f, 0.f);
+        }
+      }
+    }
+    __syncthreads();
+    if (ch < nchunks) {
+#pragma unroll 4
+      for (int kk = 0; kk < kT; ++kk) {
+        const float2 a0 = as[grp][kk][2 * ty], a1 = as[grp][kk][2 * ty + 1];
+        const float2 b0 = bs[grp][kk][2 * tx], b1 = bs[grp][kk][2 * tx + 1];
+        df_mac(acc[0][0], a0, b0);
+        df_mac(acc[0][1], a0, b1);
+        df_mac(acc[1][0], a1, b0);
+        df_mac(acc[1][1], a1, b1);
+      }
+    }
     __syncthreads();
   }
-  if (row < n && col < n) {
-    if (X) acc += X[(size_t)row * n + col];
-    D[(size_t)row * n + col] = acc;
+  if (grp > 0) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) red[grp - 1][(2 * ty + i) * kT + 2 * tx + j] = df_norm(acc[i][j]);
   }
+  __syncthreads();
+  if (grp == 0) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int r = r0 + 2 * ty + i, c = c0 + 2 * tx + j;
+        float2 v = df_norm(acc[i][j]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v = df_add(v, red[q][(2 * ty + i) * kT + 2 * tx + j]);
+        if (r < n && c < n) {
+          if (X) v = df_add(v, X[(size_t)r * n + c]);
+          D[(size_t)r * n + c] = v;
+        }
+      }
+  }
+}
+
+void dfgemm(bool transA, const float2* A, const float2* Bm, const float2* X, float2* D, int n,
+            cudaStream_t st) {
+  const dim3 grid((n + kT - 1) / kT, (n + kT - 1) / kT);
+  if (transA) k_dfgemm<true><<<grid, kTh * 4, 0, st>>>(A, Bm, X, D, n);
+  else k_dfgemm<false><<<grid, kTh * 4, 0, st>>>(A, Bm, X, D, n);
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
@@ -61,42 +151,70 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// E_ij and lam~ (written by the diagonal entries).
-__global__ void k_refine_E(const double* __restrict__ S, const double* __restrict__ G, int n,
-                           double* __restrict__ E, double* __restrict__ lam,
+// E_ij and lam~_i = S_ii / G_ii (written by the diagonal entries), FP64.
+__global__ void k_refine_E(const float2* __restrict__ S, const float2* __restrict__ G, int n,
+                           float2* __restrict__ E, double* __restrict__ lam,
                            DevHeader* __restrict__ hdr, double inv_max_angle) {
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const double rii = 1.0 - G[(size_t)i * n + i], rjj = 1.0 - G[(size_t)j * n + j];
-  const double li = S[(size_t)i * n + i] / (1.0 - rii);   // = S_ii / G_ii
-  const double lj = S[(size_t)j * n + j] / (1.0 - rjj);
-  const double rij = (i == j ? 1.0 : 0.0) - G[(size_t)i * n + j];
-  const double num = S[(size_t)i * n + j] + lj * rij;
+  const double li = df_to_d(S[(size_t)i * n + i]) / df_to_d(G[(size_t)i * n + i]);
+  const double lj = df_to_d(S[(size_t)j * n + j]) / df_to_d(G[(size_t)j * n + j]);
+  const double rij = (i == j ? 1.0 : 0.0) - df_to_d(G[(size_t)i * n + j]);
+  const double sij = df_to_d(S[(size_t)i * n + j]);
+  const double num = sij + lj * rij;
   const double gap = lj - li;
-  // the first-order Jacobi angle where it is small (|t| <= max_angle); a pair
-  // whose angle is larger is treated as part of a cluster and only
-  // re-orthogonalised
+  // classified the same way from (i, j) and (j, i), so that E_ij + E_ji = R_ij
+  const double size = fabs(sij) + fmax(fabs(li), fabs(lj)) * fabs(rij);
   double e;
-  if (i != j && fabs(gap) > inv_max_angle * fabs(num)) e = num / gap;
+  if (i != j && fabs(gap) > inv_max_angle * size) e = num / gap;
   else e = 0.5 * rij;
-  E[(size_t)i * n + j] = e;
+  E[(size_t)i * n + j] = d_to_df(e);
   if (i == j) lam[i] = li;
   atomic_max_pos(&hdr->refine_res, fabs(e));
 }
 
+// E = (I - G) / 2: one Newton-Schulz step V <- V (3I - V^T V)/2 = V + V E.
+__global__ void k_ns_E(const float2* __restrict__ G, int n, float2* __restrict__ E) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const float2 g = G[(size_t)i * n + j];
+  const float2 r = i == j ? df_add(make_float2(1.f, 0.f), make_float2(-g.x, -g.y))
+                          : make_float2(-g.x, -g.y);
+  E[(size_t)i * n + j] = make_float2(0.5f * r.x, 0.5f * r.y);
+}
+
+__global__ void k_to_df(const double* __restrict__ src, float2* __restrict__ dst, int count) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+    dst[e] = d_to_df(src[e]);
+}
+
 }  // namespace
 
-cudaError_t launch_refine(const double* C, int B, double* vc, double* lam, double* w, double* s,
-                          double* g, double* e, DevHeader* hdr, double max_angle, cudaStream_t st) {
-  const dim3 grid((B + kT - 1) / kT, (B + kT - 1) / kT);
-  k_dgemm<false><<<grid, kT * kT, 0, st>>>(C, vc, nullptr, w, B);   // W = C V
-  k_dgemm<true><<<grid, kT * kT, 0, st>>>(vc, w, nullptr, s, B);    // S = V^T W
-  k_dgemm<true><<<grid, kT * kT, 0, st>>>(vc, vc, nullptr, g, B);   // G = V^T V
+cudaError_t launch_to_df(const double* src, float2* dst, int count, cudaStream_t st) {
+  k_to_df<<<(count + 255) / 256, 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orthonormalize(float2* vc, int B, float2* w, float2* g, float2* e,
+                                  cudaStream_t st) {
+  dfgemm(true, vc, vc, nullptr, g, B, st);                       // G = V^T V
+  k_ns_E<<<dim3((B + 127) / 128, B), 128, 0, st>>>(g, B, e);
+  dfgemm(false, vc, e, vc, w, B, st);                            // V' = V E + V
+  cudaMemcpyAsync(vc, w, sizeof(float2) * (size_t)B * B, cudaMemcpyDeviceToDevice, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const float2* C, int B, float2* vc, double* lam, float2* w, float2* s,
+                          float2* g, float2* e, DevHeader* hdr, double max_angle, cudaStream_t st) {
+  dfgemm(false, C, vc, nullptr, w, B, st);    // W = C V
+  dfgemm(true, vc, w, nullptr, s, B, st);     // S = V^T W
+  dfgemm(true, vc, vc, nullptr, g, B, st);    // G = V^T V
   cudaMemsetAsync(&hdr->refine_res, 0, sizeof(double), st);
   k_refine_E<<<dim3((B + 127) / 128, B), 128, 0, st>>>(s, g, B, e, lam, hdr, 1.0 / max_angle);
-  k_dgemm<false><<<grid, kT * kT, 0, st>>>(vc, e, vc, w, B);        // V' = V E + V
-  cudaMemcpyAsync(vc, w, sizeof(double) * (size_t)B * B, cudaMemcpyDeviceToDevice, st);
+  dfgemm(false, vc, e, vc, w, B, st);         // V' = V E + V
+  cudaMemcpyAsync(vc, w, sizeof(float2) * (size_t)B * B, cudaMemcpyDeviceToDevice, st);
   return cudaGetLastError();
 }
 

