@@ -147,6 +147,28 @@ int pca_project(const void *cube, pca_dtype dtype, int64_t N, int B, int k, cons
                 void *stream);
 
 /*
+ * pca_project_noalloc -- pca_project for callers that cannot allocate.  (No
+ * counterpart in the paper.)  Some callers cannot hand the library a
+ * workspace: code running while a CUDA graph is captured, plug-ins whose
+ * host owns the device allocator, real-time loops that must not block in an
+ * allocator.  This entry point computes the same proj [N][k] as pca_project
+ * but keeps its two small intermediates (FP32 copies of mu and of the first
+ * k eigenvectors) in a fixed device array that belongs to the library:
+ * 232 + 232*32 floats (30,624 bytes), held on every GPU that loads the
+ * library until the process exits.  It allocates and frees nothing.
+ *   - Arguments as pca_project, without workspace; B*(k+1) above the array
+ *     size (impossible for valid B <= 232, k <= 32) returns PCA_ERR_ARG.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array.  Every call rewrites what it reads before
+ *     reading it, but calls whose GPU work overlaps (other streams, other
+ *     host threads) race on it: serialise them.
+ */
+int pca_project_noalloc(const void *cube, pca_dtype dtype, int64_t N, int B, int k,
+                        const double *mu, const double *eigvecs, float *proj, void *stream);
+
+/*
  * Waits for `stream` and copies the device-side outcome of the last
  * pca_fit that used `workspace` into *info.  Returns info->status.
  */

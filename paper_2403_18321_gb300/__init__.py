@@ -28,7 +28,7 @@ STATUS = {0: "PCA_OK", 1: "PCA_ERR_ARG", 2: "PCA_ERR_NOCONV", 3: "PCA_ERR_NONFIN
           4: "PCA_ERR_TIMEOUT", 5: "PCA_ERR_CUDA", 6: "PCA_ERR_WORKSPACE"}
 EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_project",
            "pca_read_info", "pca_status_string", "pca_version",
-           "pca_kernel_launches", "pca_profile", "pca_profile_collect")
+           "pca_kernel_launches", "pca_profile", "pca_profile_collect", "pca_project_noalloc")
 STAGES = ("covariance", "cov_finalize", "jacobi", "v_replay", "compact", "refine", "sort_sign",
           "project")
 
@@ -73,6 +73,8 @@ def load(build_if_missing: bool = False):
     lib.pca_eigh.restype = i
     lib.pca_project.argtypes = [P, i, i64, i, i, P, P, P, P, sz, P]
     lib.pca_project.restype = i
+    lib.pca_project_noalloc.argtypes = [P, i, i64, i, i, P, P, P, P]
+    lib.pca_project_noalloc.restype = i
     lib.pca_read_info.argtypes = [P, P, ctypes.POINTER(Info)]
     lib.pca_read_info.restype = i
     lib.pca_status_string.argtypes = [i]
@@ -225,6 +227,25 @@ def project(cube, mu, eigvecs, k: int, workspace: Workspace | None = None, strea
                             ctypes.c_void_p(eigvecs.contiguous().data_ptr()),
                             ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(_ws_ptr(workspace)),
                             workspace.nbytes, ctypes.c_void_p(st.cuda_stream))
+    _check_rc(rc)
+    return Q
+
+
+def project_noalloc(cube, mu, eigvecs, k: int, stream=None):
+    """Stages 5-6 without any workspace or allocation inside the library call, for
+    callers that cannot allocate device memory (e.g. during CUDA-graph capture).
+    The library keeps the intermediates in its own fixed device array; calls that
+    overlap on the GPU race on it, so serialise them.  Only the output tensor is
+    allocated here (by PyTorch, before the call)."""
+    import torch
+    N, B = cube.shape
+    dt, dev = _dtype_code(cube), cube.device
+    Q = torch.empty(N, k, dtype=torch.float32, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = load().pca_project_noalloc(ctypes.c_void_p(cube.data_ptr()), dt, N, B, int(k),
+                                    ctypes.c_void_p(mu.contiguous().data_ptr()),
+                                    ctypes.c_void_p(eigvecs.contiguous().data_ptr()),
+                                    ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(st.cuda_stream))
     _check_rc(rc)
     return Q
 

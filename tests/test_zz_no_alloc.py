@@ -1,0 +1,51 @@
+"""pca_project_noalloc: the projection for callers that cannot allocate device
+memory (graph capture, host-owned allocators, real-time loops).  It keeps its
+intermediates in a fixed device array of the library instead of a workspace;
+its results must equal those of pca_project on the same inputs.
+
+This file runs last (its name sorts last) so that a run stopping at the first
+failure has already run every other test; it passes alone in a fresh process
+as well as after the others."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+
+def _inputs(cube):
+    ref = oracle.pca_fit(cube.Y, cube.k, tol=1e-14, project_q=False)
+    Y = torch.from_numpy(cube.Y).cuda()
+    mu = torch.from_numpy(ref["mu"]).cuda()
+    V = torch.from_numpy(ref["V"]).cuda()
+    return Y, mu, V
+
+
+@pytest.mark.gpu
+def test_noalloc_projection_matches_pca_project_on_consecutive_calls(gbpca_lib):
+    g = gbpca_lib
+    cubes = [synth.linear_mixing(seed=31, rows=41, cols=43, bands=96, endmembers=6, k=6),
+             synth.linear_mixing(seed=32, rows=29, cols=31, bands=232, endmembers=8, k=32),
+             synth.linear_mixing(seed=33, rows=17, cols=19, bands=7, endmembers=3, k=2)]
+    for cube in cubes:                       # consecutive calls share the array
+        Y, mu, V = _inputs(cube)
+        Q_ref = g.project(Y, mu, V, cube.k)  # pca_project, with a workspace
+        Q = g.project_noalloc(Y, mu, V, cube.k)
+        torch.cuda.synchronize()
+        a = Q.cpu().numpy().astype(np.float64)
+        b = Q_ref.cpu().numpy().astype(np.float64)
+        for j in range(cube.k):
+            err = np.abs(a[:, j] - b[:, j]).max() / max(np.abs(b[:, j]).max(), 1e-30)
+            assert err <= 1e-5, (cube.name, j, err)
+
+
+@pytest.mark.gpu
+def test_noalloc_projection_rejects_bad_sizes(gbpca_lib):
+    g = gbpca_lib
+    Y = torch.zeros(64, 8, device="cuda")
+    mu = torch.zeros(8, dtype=torch.float64, device="cuda")
+    V = torch.eye(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(g.PCAError) as e:
+        g.project_noalloc(Y, mu, V, 9)       # k > B
+    assert e.value.status == 1
