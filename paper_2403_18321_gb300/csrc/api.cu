@@ -230,11 +230,10 @@ cudaError_t run_eigh(const double* A, int B, float tol32, int sweeps_max, pca_pr
                      StageMark& pm) {
   cudaError_t e;
   pm.mark(2);
-  if ((e = launch_jacobi(A, B, tol32, sweeps_max, relative_stop(prec), P.log, P.diag32, P.hdr,
-                         st)) != cudaSuccess)
+  if ((e = launch_jacobi_cluster(A, B, tol32, sweeps_max, relative_stop(prec), P.diag32, P.v32,
+                                 P.hdr, st)) != cudaSuccess)
     return e;
   pm.mark(3);
-  if ((e = launch_vreplay(P.log, B, P.hdr, P.v32, st)) != cudaSuccess) return e;
   pm.mark(4);
   if ((e = launch_compact(P.diag32, P.v32, B, P.hdr, P.lam, P.vc, st)) != cudaSuccess) return e;
   pm.mark(5);
@@ -348,11 +347,11 @@ const char* pca_status_string(int status) {
 int pca_version(void) { return 100; }
 
 int pca_kernel_launches(pca_precision prec, int with_projection) {
-  // header init, covariance, band-sum reduce, covariance finalise, Jacobi,
-  // V replay, compact, 4 per refinement iteration, 1 conversion, 3 per
+  // header init, covariance, band-sum reduce, covariance finalise, Jacobi
+  // (with V), compact, 4 per refinement iteration, 1 conversion, 3 per
   // orthogonalisation step, rank/sign + scatter, projection
   const int it = refine_iterations(prec);
-  return 7 + 4 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
+  return 6 + 4 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
 }
 
 int pca_profile(int enable) {

@@ -74,6 +74,12 @@ cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const
 cudaError_t launch_jacobi(const double* C, int B, float tol32, int sweeps_max, bool relative_stop,
                           float2* log, float* diag32, DevHeader* hdr, cudaStream_t st);
 
+// The Jacobi on one thread-block cluster (matrix rows split over A-CTAs, rows
+// of V over V-CTAs rotated in lock-step): writes diag32 [B'] and V32 [B'][B'].
+cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweeps_max,
+                                  bool relative_stop, float* diag32, float* v32, DevHeader* hdr,
+                                  cudaStream_t st);
+
 // Replays the rotation log on the rows of V (starting from I) -> V32 [B'][B'].
 cudaError_t launch_vreplay(const float2* log, int B, const DevHeader* hdr, float* v32,
                            cudaStream_t st);

@@ -105,8 +105,23 @@ k_project(const In* __restrict__ cube, int64_t N, int B, int k, const float* __r
       }
     };
     if constexpr (kVec4) {
+      // 16 bands per batch: four 16-byte loads in flight per thread before the FMAs
       const float4* r4 = reinterpret_cast<const float4*>(row);
-      for (int b4 = 0; b4 < B / 4; ++b4) {
+      const int nb4 = B / 4;
+      int b4 = 0;
+      for (; b4 + 4 <= nb4; b4 += 4) {
+        float4 y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[u] = __ldg(r4 + b4 + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          accum(y[u].x, 4 * (b4 + u));
+          accum(y[u].y, 4 * (b4 + u) + 1);
+          accum(y[u].z, 4 * (b4 + u) + 2);
+          accum(y[u].w, 4 * (b4 + u) + 3);
+        }
+      }
+      for (; b4 < nb4; ++b4) {
         const float4 y = __ldg(r4 + b4);
         accum(y.x, 4 * b4);
         accum(y.y, 4 * b4 + 1);
@@ -114,7 +129,15 @@ k_project(const In* __restrict__ cube, int64_t N, int B, int k, const float* __r
         accum(y.w, 4 * b4 + 3);
       }
     } else {
-      for (int b = 0; b < B; ++b) accum(to_f32<In>(row[b]), b);
+      int b = 0;
+      for (; b + 8 <= B; b += 8) {
+        float y[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) y[u] = to_f32<In>(row[b + u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) accum(y[u], b + u);
+      }
+      for (; b < B; ++b) accum(to_f32<In>(row[b]), b);
     }
     float* out = proj + n * (int64_t)k;
 #pragma unroll
