@@ -62,12 +62,16 @@ typedef enum { PCA_F32 = 0, PCA_BF16 = 1, PCA_F16 = 2 } pca_dtype;
  *     accuracy of the cluster, at least 1e-7 ||C|| absolute).
  *   PCA_PREC_P32: plain FP32 on the GPU (SIMT covariance, FP32 Jacobi, no
  *     refinement).
- *   PCA_PREC_MIX: covariance on the tensor cores from a two-term BF16
- *     split of the centred cube (three products, FP32 accumulation per
- *     chunk), FP32 Jacobi stopped on the Frobenius test, one refinement
- *     iteration and two orthogonalisation steps in double-float/FP64.  The
- *     BF16 split bounds the covariance at about 2^-17 relative per element,
- *     so eigenvalue errors are about 2e-5 of the largest eigenvalue.
+ *   PCA_PREC_MIX: covariance on the tensor cores from a two-term FP16
+ *     split of the cube, shifted by a sampled band mean and scaled per band
+ *     by a power of two (three products, FP32 accumulation in tensor
+ *     memory), FP32 Jacobi stopped on the Frobenius test at
+ *     max(tol, 1e-5), two refinement iterations and one orthogonalisation
+ *     step in double-float/FP64.  The
+ *     split keeps 22 bits of every value; the remaining covariance error
+ *     comes from the tensor cores' FP32 accumulation.  A value that leaves
+ *     the scaled FP16 range makes the covariance be recomputed in FP32 on
+ *     the SIMT cores (pca_info.cov_fallback).
  */
 typedef enum { PCA_PREC_P64 = 0, PCA_PREC_P32 = 1, PCA_PREC_MIX = 2 } pca_precision;
 
@@ -79,6 +83,8 @@ typedef struct {
   double off_rel;    /* off(A)/||A||_F when the FP32 Jacobi stopped            */
   double tol_used;   /* the stop threshold the FP32 Jacobi applied             */
   double refine_res; /* largest |E_ij| of the last refinement correction (0 if none) */
+  int cov_fallback;  /* MIX only: 1 if a scaled value left the FP16 range and the
+                        covariance was recomputed in FP32 on the SIMT cores     */
 } pca_info;
 
 /*
@@ -96,10 +102,11 @@ size_t pca_workspace_size(int64_t N, int B, int k, pca_dtype dtype, pca_precisio
  * k          components to project onto, 1 <= k <= min(B, 32).
  * tol        Jacobi stop factor (Sec. 2, "until all off-diagonal elements are
  *            smaller than the stop factor").  The FP32 Jacobi applies
- *            tau = max(tol, 2^-22) (*info reports it): P32 and P64 stop when
- *            every |a_pq| <= tau sqrt(|a_pp a_qq|); MIX stops when
- *            off(A) <= tau ||A||_F (off: Frobenius norm of the off-diagonal
- *            part) and leaves the rest to the refinement.  tol > 0.
+ *            tau = max(tol, 2^-22) for P32 and P64, which stop when every
+ *            |a_pq| <= tau sqrt(|a_pp a_qq|), and tau = max(tol, 1e-5) for
+ *            MIX, which stops when off(A) <= tau ||A||_F (off: Frobenius
+ *            norm of the off-diagonal part) and leaves the rest to the
+ *            refinement; *info reports tau.  tol > 0.
  * sweeps_max maximum Jacobi sweeps, >= 1.
  * mu         [B] FP64 out: band means (Algorithm 1 stage 2).
  * eigvals    [B] FP64 out: eigenvalues of C, descending; equal values keep
@@ -126,8 +133,8 @@ int pca_fit(const void *cube, pca_dtype dtype, int64_t N, int B, int k, double t
  *
  * pca_covariance -- Algorithm 1 stages 2-3: mu [B] and C = X^T X/(N-1),
  *   cov [B][B] FP64 row-major (full symmetric).  prec selects the
- *   covariance form (P64: FP64 accumulation; P32: FP32 SIMT; MIX: split-BF16
- *   tensor cores).
+ *   covariance form (P64: FP64 accumulation; P32: FP32 SIMT; MIX: split-FP16
+ *   tensor cores on per-band shifted and power-of-two scaled values).
  * pca_eigh -- Algorithm 1 stage 4 on a given symmetric matrix A [B][B] FP64
  *   (device): cyclic Jacobi (Eqs. 2-10), FP64 refinement (P32: none, MIX:
  *   one iteration, P64: three), descending sort and sign rule; eigvals [B],
@@ -184,6 +191,9 @@ int pca_version(void);
 
 /* Number of kernels one pca_fit enqueues for this precision form. */
 int pca_kernel_launches(pca_precision prec, int with_projection);
+
+/* SMs (CTAs of one cluster) the Jacobi stage occupies for B bands; 0 if B is invalid. */
+int pca_jacobi_sms(int B);
 
 /*
  * Per-stage timing.  pca_profile(1) makes every later pca_fit on the calling

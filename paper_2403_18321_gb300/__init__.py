@@ -28,7 +28,8 @@ STATUS = {0: "PCA_OK", 1: "PCA_ERR_ARG", 2: "PCA_ERR_NOCONV", 3: "PCA_ERR_NONFIN
           4: "PCA_ERR_TIMEOUT", 5: "PCA_ERR_CUDA", 6: "PCA_ERR_WORKSPACE"}
 EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_project",
            "pca_read_info", "pca_status_string", "pca_version",
-           "pca_kernel_launches", "pca_profile", "pca_profile_collect", "pca_project_noalloc")
+           "pca_kernel_launches", "pca_profile", "pca_profile_collect", "pca_project_noalloc",
+           "pca_jacobi_sms")
 STAGES = ("covariance", "cov_finalize", "jacobi", "v_replay", "compact", "refine", "sort_sign",
           "project")
 
@@ -43,7 +44,7 @@ class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("sweeps", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("steps", ctypes.c_int),
                 ("off_rel", ctypes.c_double), ("tol_used", ctypes.c_double),
-                ("refine_res", ctypes.c_double)]
+                ("refine_res", ctypes.c_double), ("cov_fallback", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -82,6 +83,8 @@ def load(build_if_missing: bool = False):
     lib.pca_version.restype = i
     lib.pca_kernel_launches.argtypes = [i, i]
     lib.pca_kernel_launches.restype = i
+    lib.pca_jacobi_sms.argtypes = [i]
+    lib.pca_jacobi_sms.restype = i
     lib.pca_profile.argtypes = [i]
     lib.pca_profile.restype = i
     lib.pca_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_float), i]
@@ -252,6 +255,10 @@ def project_noalloc(cube, mu, eigvecs, k: int, stream=None):
 
 def kernel_launches(precision="mix", project: bool = True) -> int:
     return int(load().pca_kernel_launches(_prec_code(precision), 1 if project else 0))
+
+
+def jacobi_sms(B: int) -> int:
+    return int(load().pca_jacobi_sms(int(B)))
 
 
 def profile(enable: bool) -> None:

@@ -70,7 +70,15 @@ struct StageMark {
 };
 
 int refine_iterations(pca_precision prec) {
-  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 3);
+  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 2 : 3);
+}
+// Lowest stop threshold of the FP32 sweeps.  MIX hands the eigen-pairs to its
+// two quadratically convergent refinement iterations once off(A) <= 1e-5
+// ||A||_F: on the scene cubes that saves two to three sweeps and leaves the
+// separated eigen-pairs more accurate than sweeping on to 2^-22 with one
+// iteration; P32 and P64 sweep to the FP32 floor.
+float stop_floor(pca_precision prec) {
+  return prec == PCA_PREC_MIX ? kMixJacobiFloor : kJacobiFloor;
 }
 
 }  // namespace
@@ -92,6 +100,7 @@ Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, in
   auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
   L.hdr = take(sizeof(DevHeader));
   L.shift = take(sizeof(float) * B);
+  L.escale = take(sizeof(int) * B);
   L.s1_part = take(sizeof(double) * (size_t)L.partials * B);
   L.s2_part = take((size_t)L.s2_bytes_el * L.partials * L.s2_elems);
   L.dvec = take(sizeof(double) * B);
@@ -144,6 +153,7 @@ int pca_read_info(const void* workspace, void* stream, pca_info* info) {
   info->off_rel = h.off_rel;
   info->tol_used = h.tol_used;
   info->refine_res = h.refine_res;
+  info->cov_fallback = h.cov_range != 0 ? 1 : 0;
   return info->status;
 }
 
@@ -155,6 +165,7 @@ namespace {
 struct Ptrs {
   DevHeader* hdr;
   float* shift;
+  int* escale;
   double* s1p;
   void* s2p;
   double* dvec;
@@ -180,6 +191,7 @@ Ptrs carve(void* workspace, const Layout& L) {
   Ptrs p;
   p.hdr = reinterpret_cast<DevHeader*>(ws + L.hdr);
   p.shift = reinterpret_cast<float*>(ws + L.shift);
+  p.escale = reinterpret_cast<int*>(ws + L.escale);
   p.s1p = reinterpret_cast<double*>(ws + L.s1_part);
   p.s2p = ws + L.s2_part;
   p.dvec = reinterpret_cast<double*>(ws + L.dvec);
@@ -204,7 +216,7 @@ Ptrs carve(void* workspace, const Layout& L) {
 // largest first-order angle the refinement applies (pairs above it count as clustered)
 double refine_max_angle(pca_precision prec) { (void)prec; return 1.0 / 64; }
 // closing Newton-Schulz orthogonalisation steps
-int ortho_steps(pca_precision prec) { return prec == PCA_PREC_P32 ? 0 : 2; }
+int ortho_steps(pca_precision prec) { return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 2); }
 // MIX stops its FP32 sweeps on the Frobenius test (the refinement resolves what
 // the element-wise test would still demand); P32 and P64 use the element-wise test
 bool relative_stop(pca_precision prec) { return prec != PCA_PREC_MIX; }
@@ -214,14 +226,23 @@ cudaError_t run_cov(const void* cube, pca_dtype dt, int64_t N, int B, pca_precis
                     const Layout& L, const Ptrs& P, double* mu, cudaStream_t st, StageMark& pm) {
   cudaError_t e;
   pm.mark(0);
-  if (prec == PCA_PREC_MIX)
-    e = launch_syrk_tc(cube, dt, N, B, P.shift, P.s1p, (float*)P.s2p, L.partials, P.hdr, st);
-  else
+  if (prec == PCA_PREC_MIX) {
+    e = launch_band_probe(cube, dt, N, B, P.shift, P.escale, st);
+    if (e != cudaSuccess) return e;
+    e = launch_syrk_tc(cube, dt, N, B, P.shift, P.escale, P.s1p, (float*)P.s2p, L.partials, P.hdr,
+                       st);
+    if (e != cudaSuccess) return e;
+    // a value outside the scaled FP16 range: the SIMT form recomputes the partials
+    // (its CTAs return at once when the flag is clear)
+    e = launch_syrk_simt(cube, dt, N, B, false, P.shift, P.s1p, P.s2p, L.partials, st,
+                         &P.hdr->cov_range, P.escale);
+  } else {
     e = launch_syrk_simt(cube, dt, N, B, prec == PCA_PREC_P64, P.shift, P.s1p, P.s2p, L.partials, st);
+  }
   if (e != cudaSuccess) return e;
   pm.mark(1);
   return launch_cov_finalize(P.shift, P.s1p, P.s2p, L.s2_bytes_el == 8, L.partials, N, B, mu, P.C,
-                             P.muf, P.dvec, P.hdr, st);
+                             P.muf, P.dvec, P.hdr, st, prec == PCA_PREC_MIX ? P.escale : nullptr);
 }
 
 // stage 4: Jacobi, V replay, FP64 refinement, sort and sign rule
@@ -264,7 +285,7 @@ int pca_fit(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol,
   if (ws_bytes < L.total) return PCA_ERR_WORKSPACE;
   const Ptrs P = carve(workspace, L);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const float tol32 = std::max((float)tol, kJacobiFloor);
+  const float tol32 = std::max((float)tol, stop_floor(prec));
   StageMark pm(st);
   k_header_init<<<1, 1, 0, st>>>(P.hdr, refine_iterations(prec), tol32);
   GB_CK(cudaGetLastError());
@@ -307,7 +328,7 @@ int pca_eigh(const double* A, int B, double tol, int sweeps_max, pca_precision p
   if (ws_bytes < L.total) return PCA_ERR_WORKSPACE;
   const Ptrs P = carve(workspace, L);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const float tol32 = std::max((float)tol, kJacobiFloor);
+  const float tol32 = std::max((float)tol, stop_floor(prec));
   StageMark pm(st);
   k_header_init<<<1, 1, 0, st>>>(P.hdr, refine_iterations(prec), tol32);
   GB_CK(cudaGetLastError());
@@ -347,11 +368,21 @@ const char* pca_status_string(int status) {
 int pca_version(void) { return 100; }
 
 int pca_kernel_launches(pca_precision prec, int with_projection) {
-  // header init, covariance, band-sum reduce, covariance finalise, Jacobi
-  // (with V), compact, 4 per refinement iteration, 1 conversion, 3 per
+  // header init, covariance (MIX: band probe + tensor-core pass + guarded
+  // SIMT re-computation), band-sum reduce, covariance finalise, Jacobi (with
+  // V), compact, 4 per refinement iteration, 1 conversion, 3 per
   // orthogonalisation step, rank/sign + scatter, projection
   const int it = refine_iterations(prec);
-  return 6 + 4 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
+  const int cov = prec == PCA_PREC_MIX ? 3 : 1;
+  return 5 + cov + 4 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
+}
+
+int pca_jacobi_sms(int B) {
+  if (B < 2 || B > kMaxB) return 0;
+  int nA = 0, nV = 0;
+  jacobi_cluster_shape(B, &nA, &nV);
+  const int P = round_even(B) / 2;
+  return (nA > P ? P : nA) + nV;
 }
 
 int pca_profile(int enable) {

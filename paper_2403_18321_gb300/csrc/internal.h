@@ -14,6 +14,7 @@ constexpr int kMaxB = 232;          // A (FP32, B' x B') must fit one SM's share
 constexpr int kMaxK = 32;
 constexpr int kMaxPartials = 320;   // per-CTA covariance partial slots
 constexpr float kJacobiFloor = 2.384185791015625e-07f;  // 2^-22: FP32 Jacobi stop floor
+constexpr float kMixJacobiFloor = 1e-5f;                 // MIX: refinement takes over from here
 
 // Device-side outcome, first 256 bytes of the workspace.
 struct DevHeader {
@@ -23,7 +24,8 @@ struct DevHeader {
   int refine_iters;
   int nonfinite;
   int dummy_slot;    // slot of the padding index when B is odd, else -1
-  int pad0, pad1;
+  int cov_range;     // tensor-core covariance met a value outside its scaled FP16 range
+  int pad1;
   double off_rel;
   double fro;
   double tol_used;
@@ -33,7 +35,7 @@ struct DevHeader {
 
 // Offsets (bytes) of every workspace region; all 256-byte aligned.
 struct Layout {
-  size_t hdr, shift, s1_part, s2_part, dvec, cov, cdf, rank, sgn, diag32, log, v32, lam, vc, w, s, r, e, vk, muf;
+  size_t hdr, shift, escale, s1_part, s2_part, dvec, cov, cdf, rank, sgn, diag32, log, v32, lam, vc, w, s, r, e, vk, muf;
   size_t total;
   int partials;      // number of covariance partial slots the SYRK uses
   int s2_elems;      // packed upper-triangle entries per partial: B(B+1)/2
@@ -52,22 +54,33 @@ __host__ __device__ inline int64_t packed_index(int i, int j, int B) {  // i <= 
 
 // Covariance partials, SIMT: P32 (FP32 accumulate) or P64 (FP64 accumulate).
 // shift = first pixel; writes s1_part[G][B] (FP64) and s2_part[G][B(B+1)/2].
+// With guard != nullptr every CTA returns at once unless *guard != 0; a run
+// then also zeroes escale[B] (the partials it writes are unscaled).
 cudaError_t launch_syrk_simt(const void* cube, pca_dtype dt, int64_t N, int B, bool fp64,
                              float* shift, double* s1_part, void* s2_part, int partials,
-                             cudaStream_t st);
+                             cudaStream_t st, const int* guard = nullptr, int* escale = nullptr);
 
-// Covariance partials on the tensor cores (tcgen05, split-BF16, three products).
-cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
-                           double* s1_part, float* s2_part, int partials, DevHeader* hdr,
-                           cudaStream_t st);
+// Per-band shift (mean of a strided pixel sample) and power-of-two scale
+// exponent for the tensor-core covariance: shift [B] (FP32), escale [B] (int).
+cudaError_t launch_band_probe(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
+                              int* escale, cudaStream_t st);
+
+// Covariance partials on the tensor cores (tcgen05, split-FP16 of the scaled,
+// shifted values, three products).  Reads shift/escale from launch_band_probe;
+// S1 partials are unscaled, S2 partials stay scaled by 2^(e_i + e_j).  A value
+// outside the FP16 range after scaling sets hdr->cov_range.
+cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, const float* shift,
+                           const int* escale, double* s1_part, float* s2_part, int partials,
+                           DevHeader* hdr, cudaStream_t st);
 bool syrk_tc_supported(int B);
 
 // Sums the partials, applies the shift correction, writes mu (FP64), C (FP64, full
 // symmetric) and mu_f (FP32), flags non-finite sums in the header.
+// escale (nullable): S2 partials are scaled by 2^(escale[i] + escale[j]).
 cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const void* s2_part,
                                 bool fp64_partials, int partials, int64_t N, int B, double* mu,
                                 double* C, float* mu_f, double* dvec, DevHeader* hdr,
-                                cudaStream_t st);
+                                cudaStream_t st, const int* escale = nullptr);
 
 // FP32 odd-even Jacobi on one SM; logs (c, s) of every rotation.  relative_stop
 // selects the element-wise relative stop test (else off(A) <= tol ||A||_F).
@@ -79,6 +92,9 @@ cudaError_t launch_jacobi(const double* C, int B, float tol32, int sweeps_max, b
 cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweeps_max,
                                   bool relative_stop, float* diag32, float* v32, DevHeader* hdr,
                                   cudaStream_t st);
+
+// CTAs (= SMs) the cluster Jacobi uses for B bands: nA matrix CTAs + nV V CTAs.
+bool jacobi_cluster_shape(int B, int* nA, int* nV);
 
 // Replays the rotation log on the rows of V (starting from I) -> V32 [B'][B'].
 cudaError_t launch_vreplay(const float2* log, int B, const DevHeader* hdr, float* v32,

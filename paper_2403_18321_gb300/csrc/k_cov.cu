@@ -30,7 +30,10 @@ template <typename In, typename Acc, int TM>
 __global__ void __launch_bounds__(kSyrkThreads)
 k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, int Bt, int ntiles,
             float* __restrict__ shift_out, double* __restrict__ s1_part,
-            Acc* __restrict__ s2_part, int s2_elems) {
+            Acc* __restrict__ s2_part, int s2_elems, const int* __restrict__ guard,
+            int* __restrict__ escale) {
+  // guarded form: the re-computation after an out-of-range tensor-core pass
+  if (guard != nullptr && *(volatile const int*)guard == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Bpad = Bt * TM;
   Acc* xs = reinterpret_cast<Acc*>(smem_raw);                   // [kChunk][Bpad]
@@ -41,7 +44,10 @@ k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, int Bt, int ntiles,
 
   for (int b = tid; b < Bpad; b += kSyrkThreads) sh[b] = b < B ? ld(cube + b) : 0.f;
   if (g == 0 && blockIdx.y == 0)
-    for (int b = tid; b < B; b += kSyrkThreads) shift_out[b] = ld(cube + b);
+    for (int b = tid; b < B; b += kSyrkThreads) {
+      shift_out[b] = ld(cube + b);
+      if (escale != nullptr) escale[b] = 0;
+    }
 
   // tile of this thread: enumerate the upper block-triangle row by row
   const int t = blockIdx.y * kSyrkThreads + tid;
@@ -108,7 +114,8 @@ k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, int Bt, int ntiles,
 
 template <typename In>
 cudaError_t syrk_simt_typed(const In* cube, int64_t N, int B, bool fp64, float* shift,
-                            double* s1_part, void* s2_part, int partials, cudaStream_t st) {
+                            double* s1_part, void* s2_part, int partials, cudaStream_t st,
+                            const int* guard, int* escale) {
   const int s2_elems = B * (B + 1) / 2;
   if (fp64) {
     constexpr int TM = 4;
@@ -118,7 +125,7 @@ cudaError_t syrk_simt_typed(const In* cube, int64_t N, int B, bool fp64, float* 
     auto kern = k_syrk_simt<In, double, TM>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(
-        cube, N, B, Bt, ntiles, shift, s1_part, (double*)s2_part, s2_elems);
+        cube, N, B, Bt, ntiles, shift, s1_part, (double*)s2_part, s2_elems, guard, escale);
   } else {
     constexpr int TM = 8;
     const int Bt = (B + TM - 1) / TM, ntiles = Bt * (Bt + 1) / 2;
@@ -127,9 +134,78 @@ cudaError_t syrk_simt_typed(const In* cube, int64_t N, int B, bool fp64, float* 
     auto kern = k_syrk_simt<In, float, TM>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(
-        cube, N, B, Bt, ntiles, shift, s1_part, (float*)s2_part, s2_elems);
+        cube, N, B, Bt, ntiles, shift, s1_part, (float*)s2_part, s2_elems, guard, escale);
   }
   return cudaGetLastError();
+}
+
+// Band probe for the tensor-core form: over S = min(N, 1024) pixels spread
+// evenly through the cube, per band b
+//   shift_b = sample mean (FP32),
+//   escale_b = 6 - E with max_n |y_nb - shift_b| <= 2^E  (frexp),
+// so that the sampled deviations scale into (2^5, 2^6]; a scaled value leaves
+// the FP16 range (65504) only if it lies about a thousand times further from
+// the shift than every sampled one.  A degenerate sample falls back to
+// |shift_b|, then to scale 1.
+constexpr int kProbeSamples = 1024;
+constexpr int kProbeWarps = 32;
+constexpr int kProbeUnroll = 8;   // independent loads in flight per thread
+
+template <typename In>
+__global__ void __launch_bounds__(kProbeWarps * 32)
+k_band_probe(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shift,
+             int* __restrict__ escale) {
+  __shared__ double ssum[kProbeWarps][32];
+  __shared__ float smin[kProbeWarps][32], smax[kProbeWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int b = blockIdx.x * 32 + lane;
+  const int S = (int)(N < kProbeSamples ? N : kProbeSamples);
+  double sum = 0.0;
+  float lo = INFINITY, hi = -INFINITY;
+  if (b < B) {
+    // warp w takes samples w, w + 32, ...; kProbeUnroll loads are issued
+    // before any of them is used
+    for (int i0 = warp; i0 < S; i0 += kProbeWarps * kProbeUnroll) {
+      float y[kProbeUnroll];
+#pragma unroll
+      for (int u = 0; u < kProbeUnroll; ++u) {
+        const int i = i0 + u * kProbeWarps;
+        y[u] = i < S ? ld(cube + ((int64_t)i * N / S) * B + b) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kProbeUnroll; ++u) {
+        if (i0 + u * kProbeWarps < S) {
+          sum += (double)y[u];
+          lo = fminf(lo, y[u]);
+          hi = fmaxf(hi, y[u]);
+        }
+      }
+    }
+  }
+  ssum[warp][lane] = sum;
+  smin[warp][lane] = lo;
+  smax[warp][lane] = hi;
+  __syncthreads();
+  if (warp == 0 && b < B) {
+    for (int w = 1; w < kProbeWarps; ++w) {
+      sum += ssum[w][lane];
+      lo = fminf(lo, smin[w][lane]);
+      hi = fmaxf(hi, smax[w][lane]);
+    }
+    float m = (float)(sum / (double)S);
+    double dev = fmax((double)hi - (double)m, (double)m - (double)lo);
+    if (!isfinite(m) || !isfinite(dev)) { m = 0.f; dev = 0.0; }
+    if (!(dev > 0.0)) dev = fabs((double)m);
+    int e = 0;
+    if (dev > 0.0) {
+      int E;
+      frexp(dev, &E);
+      e = 6 - E;
+      e = e < -120 ? -120 : (e > 120 ? 120 : e);
+    }
+    shift[b] = m;
+    escale[b] = e;
+  }
 }
 
 // d[b] = (sum_g S1_g[b]) / N, one warp per band (FP64 adds spread over SMs).
@@ -156,7 +232,8 @@ __global__ void k_s1_reduce(const double* __restrict__ s1_part, int partials, in
 template <typename Acc>
 __global__ void k_cov_finalize(const Acc* __restrict__ s2_part, int partials, int s2_elems,
                                int B, int64_t N, const double* __restrict__ dvec,
-                               double* __restrict__ C, DevHeader* __restrict__ hdr) {
+                               double* __restrict__ C, DevHeader* __restrict__ hdr,
+                               const int* __restrict__ escale) {
   const int i = blockIdx.y;
   const int j = i + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= B) return;
@@ -176,6 +253,7 @@ __global__ void k_cov_finalize(const Acc* __restrict__ s2_part, int partials, in
     for (int g = 0; g < partials; ++g) sum += (double)s2_part[(size_t)g * s2_elems + e];
     S2 = sum;
   }
+  if (escale != nullptr) S2 = ldexp(S2, -(escale[i] + escale[j]));  // exact power of two
   const double c = (S2 - (double)N * dvec[i] * dvec[j]) / (double)(N - 1);
   C[(size_t)i * B + j] = c;
   C[(size_t)j * B + i] = c;
@@ -186,32 +264,53 @@ __global__ void k_cov_finalize(const Acc* __restrict__ s2_part, int partials, in
 
 cudaError_t launch_syrk_simt(const void* cube, pca_dtype dt, int64_t N, int B, bool fp64,
                              float* shift, double* s1_part, void* s2_part, int partials,
-                             cudaStream_t st) {
+                             cudaStream_t st, const int* guard, int* escale) {
   switch (dt) {
     case PCA_F32:
-      return syrk_simt_typed((const float*)cube, N, B, fp64, shift, s1_part, s2_part, partials, st);
+      return syrk_simt_typed((const float*)cube, N, B, fp64, shift, s1_part, s2_part, partials, st,
+                             guard, escale);
     case PCA_BF16:
       return syrk_simt_typed((const __nv_bfloat16*)cube, N, B, fp64, shift, s1_part, s2_part,
-                             partials, st);
+                             partials, st, guard, escale);
     case PCA_F16:
-      return syrk_simt_typed((const __half*)cube, N, B, fp64, shift, s1_part, s2_part, partials, st);
+      return syrk_simt_typed((const __half*)cube, N, B, fp64, shift, s1_part, s2_part, partials, st,
+                             guard, escale);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_band_probe(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
+                              int* escale, cudaStream_t st) {
+  const dim3 grid((B + 31) / 32), block(kProbeWarps * 32);
+  switch (dt) {
+    case PCA_F32:
+      k_band_probe<<<grid, block, 0, st>>>((const float*)cube, N, B, shift, escale);
+      break;
+    case PCA_BF16:
+      k_band_probe<<<grid, block, 0, st>>>((const __nv_bfloat16*)cube, N, B, shift, escale);
+      break;
+    case PCA_F16:
+      k_band_probe<<<grid, block, 0, st>>>((const __half*)cube, N, B, shift, escale);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const void* s2_part,
                                 bool fp64_partials, int partials, int64_t N, int B, double* mu,
                                 double* C, float* mu_f, double* dvec, DevHeader* hdr,
-                                cudaStream_t st) {
+                                cudaStream_t st, const int* escale) {
   k_s1_reduce<<<B, 32, 0, st>>>(s1_part, partials, B, N, shift, dvec, mu, mu_f, hdr);
   const int s2_elems = B * (B + 1) / 2;
   dim3 grid((B + 63) / 64, B);
   if (fp64_partials)
     k_cov_finalize<double><<<grid, 64, 0, st>>>((const double*)s2_part, partials, s2_elems, B, N,
-                                                dvec, C, hdr);
+                                                dvec, C, hdr, escale);
   else
     k_cov_finalize<float><<<grid, 64, 0, st>>>((const float*)s2_part, partials, s2_elems, B, N,
-                                               dvec, C, hdr);
+                                               dvec, C, hdr, escale);
   return cudaGetLastError();
 }
 

@@ -69,9 +69,10 @@ k_scatter(const float2* __restrict__ vc, int B, int k, const int* __restrict__ r
   }
 }
 
-// Q[n][j] = sum_b (Y_nb - mu_b) V_bj, FP32, one pixel per thread.  V_k and mu
-// sit in shared memory; V_k rows are padded to KQ float4 groups so one
-// 16-byte load feeds four FMAs.
+// Q[n][j] = sum_b (Y_nb - mu_b) V_bj, FP32.  Each thread computes two pixels
+// so that every 16-byte V_k load from shared memory feeds eight FMAs; V_k
+// rows are padded to KQ float4 groups, mu sits beside them.  Rows are read
+// 16 bands at a time (four 16-byte loads in flight per pixel).
 constexpr int kProjThreads = 256;
 
 template <typename In, int KQ, bool kVec4>
@@ -87,65 +88,76 @@ k_project(const In* __restrict__ cube, int64_t N, int B, int k, const float* __r
   }
   for (int b = threadIdx.x; b < B; b += kProjThreads) mus[b] = mu_f[b];
   __syncthreads();
+  const int64_t half = (N + 1) / 2;
   const int64_t stride = (int64_t)gridDim.x * kProjThreads;
-  for (int64_t n = (int64_t)blockIdx.x * kProjThreads + threadIdx.x; n < N; n += stride) {
-    float4 acc[KQ];
+  for (int64_t n0 = (int64_t)blockIdx.x * kProjThreads + threadIdx.x; n0 < half; n0 += stride) {
+    const int64_t n1 = n0 + half;
+    const bool two = n1 < N;
+    float4 a0[KQ], a1[KQ];
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const In* row = cube + n * (int64_t)B;
-    auto accum = [&](float x, int b) {
-      x -= mus[b];
+    for (int q = 0; q < KQ; ++q) { a0[q] = make_float4(0.f, 0.f, 0.f, 0.f); a1[q] = a0[q]; }
+    const In* row0 = cube + n0 * (int64_t)B;
+    const In* row1 = cube + (two ? n1 : n0) * (int64_t)B;
+    auto accum = [&](float x0, float x1, int b) {
+      const float m = mus[b];
+      x0 -= m;
+      x1 -= m;
 #pragma unroll
       for (int q = 0; q < KQ; ++q) {
         const float4 v = v4[b * KQ + q];
-        acc[q].x = fmaf(x, v.x, acc[q].x);
-        acc[q].y = fmaf(x, v.y, acc[q].y);
-        acc[q].z = fmaf(x, v.z, acc[q].z);
-        acc[q].w = fmaf(x, v.w, acc[q].w);
+        a0[q].x = fmaf(x0, v.x, a0[q].x); a1[q].x = fmaf(x1, v.x, a1[q].x);
+        a0[q].y = fmaf(x0, v.y, a0[q].y); a1[q].y = fmaf(x1, v.y, a1[q].y);
+        a0[q].z = fmaf(x0, v.z, a0[q].z); a1[q].z = fmaf(x1, v.z, a1[q].z);
+        a0[q].w = fmaf(x0, v.w, a0[q].w); a1[q].w = fmaf(x1, v.w, a1[q].w);
       }
     };
     if constexpr (kVec4) {
-      // 16 bands per batch: four 16-byte loads in flight per thread before the FMAs
-      const float4* r4 = reinterpret_cast<const float4*>(row);
+      const float4* p0 = reinterpret_cast<const float4*>(row0);
+      const float4* p1 = reinterpret_cast<const float4*>(row1);
       const int nb4 = B / 4;
       int b4 = 0;
       for (; b4 + 4 <= nb4; b4 += 4) {
-        float4 y[4];
+        float4 y0[4], y1[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) y[u] = __ldg(r4 + b4 + u);
+        for (int u = 0; u < 4; ++u) { y0[u] = __ldg(p0 + b4 + u); y1[u] = __ldg(p1 + b4 + u); }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          accum(y[u].x, 4 * (b4 + u));
-          accum(y[u].y, 4 * (b4 + u) + 1);
-          accum(y[u].z, 4 * (b4 + u) + 2);
-          accum(y[u].w, 4 * (b4 + u) + 3);
+          accum(y0[u].x, y1[u].x, 4 * (b4 + u));
+          accum(y0[u].y, y1[u].y, 4 * (b4 + u) + 1);
+          accum(y0[u].z, y1[u].z, 4 * (b4 + u) + 2);
+          accum(y0[u].w, y1[u].w, 4 * (b4 + u) + 3);
         }
       }
       for (; b4 < nb4; ++b4) {
-        const float4 y = __ldg(r4 + b4);
-        accum(y.x, 4 * b4);
-        accum(y.y, 4 * b4 + 1);
-        accum(y.z, 4 * b4 + 2);
-        accum(y.w, 4 * b4 + 3);
+        const float4 y0 = __ldg(p0 + b4), y1 = __ldg(p1 + b4);
+        accum(y0.x, y1.x, 4 * b4);
+        accum(y0.y, y1.y, 4 * b4 + 1);
+        accum(y0.z, y1.z, 4 * b4 + 2);
+        accum(y0.w, y1.w, 4 * b4 + 3);
       }
     } else {
       int b = 0;
       for (; b + 8 <= B; b += 8) {
-        float y[8];
+        float y0[8], y1[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) y[u] = to_f32<In>(row[b + u]);
+        for (int u = 0; u < 8; ++u) { y0[u] = to_f32<In>(row0[b + u]); y1[u] = to_f32<In>(row1[b + u]); }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) accum(y[u], b + u);
+        for (int u = 0; u < 8; ++u) accum(y0[u], y1[u], b + u);
       }
-      for (; b < B; ++b) accum(to_f32<In>(row[b]), b);
+      for (; b < B; ++b) accum(to_f32<In>(row0[b]), to_f32<In>(row1[b]), b);
     }
-    float* out = proj + n * (int64_t)k;
+    float* out0 = proj + n0 * (int64_t)k;
+    float* out1 = proj + n1 * (int64_t)k;
 #pragma unroll
     for (int q = 0; q < KQ; ++q) {
-      const float vals[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
+      const float v0[4] = {a0[q].x, a0[q].y, a0[q].z, a0[q].w};
+      const float v1[4] = {a1[q].x, a1[q].y, a1[q].z, a1[q].w};
 #pragma unroll
       for (int t = 0; t < 4; ++t)
-        if (4 * q + t < k) out[4 * q + t] = vals[t];
+        if (4 * q + t < k) {
+          out0[4 * q + t] = v0[t];
+          if (two) out1[4 * q + t] = v1[t];
+        }
     }
   }
 }
@@ -157,7 +169,7 @@ cudaError_t project_kq(const In* cube, int64_t N, int B, int k, const float* mu_
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t want = (N + kProjThreads - 1) / kProjThreads;
+  const int64_t want = ((N + 1) / 2 + kProjThreads - 1) / kProjThreads;
   const int blocks = (int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
   if (vec4) {
     auto kern = k_project<In, KQ, true>;

@@ -3,22 +3,27 @@
 //
 // Same ordering and arithmetic as k_jacobi.cu (odd-even parallel ordering
 // with a position swap after every rotation, G = [[s, c], [c, -s]], FP32,
-// B'/2 disjoint rotations per step), but the B' x B' matrix is split by rows
-// over nA "A" CTAs and the eigenvector matrix V by rows over nV "V" CTAs of
-// the same cluster, so that every step costs each SM only a fraction of the
-// shared-memory traffic, and V is rotated in lock-step instead of being
-// replayed afterwards.
+// B'/2 disjoint rotations per step).  The B' x B' matrix is split by rows
+// over the nA CTAs of the cluster, and every CTA also holds a slice of the
+// rows of the eigenvector matrix V in registers.
 //
-//   * A-CTA r owns the even row pairs [rp[r], rp[r+1]) -- rows
-//     [2rp[r], 2rp[r+1]) -- plus one halo row 2rp[r+1] (the next CTA's first
-//     row).  Even steps update its own rows; odd steps update the odd row
-//     pairs [rp[r], rp[r+1]) -- rows [2rp[r]+1, 2rp[r+1]] -- whose last row
-//     is the halo.  After every step the row that changed hands is copied to
-//     its other holder through distributed shared memory.
-//   * The diagonal lives in a replicated array dg[] in every CTA; whoever
-//     rotates a diagonal block writes (c, s) and the two new diagonal values
-//     into every CTA of the cluster.
-//   * One cluster barrier per step (release/acquire) orders all of it.
+//   * CTA r owns the even row pairs [rp[r], rp[r+1]) -- rows
+//     [2rp[r], 2rp[r+1]) -- in shared memory, plus one halo row 2rp[r+1]
+//     (the next CTA's first row).  Even steps update its own rows; odd steps
+//     update the odd row pairs [rp[r], rp[r+1]) -- rows [2rp[r]+1, 2rp[r+1]]
+//     -- whose last row is the halo.  The threads that compute a row which
+//     changes holder also write it straight into the other holder's copy
+//     (distributed shared memory), so a step needs no CTA-local barrier.
+//   * Whoever rotates the diagonal block of a pair of the next step writes
+//     one 16-byte record (c, s, new a_pp, new a_qq) into every CTA of the
+//     cluster.  Records rotate through three slots by global step number,
+//     so the diagonal of the last two steps stays readable and the V
+//     rotations of a step can run after the cluster-barrier arrive.
+//   * V rows live in registers: lane l of a warp holds positions
+//     [W l, W l + W) of a row.  Even-step pairs are lane-local; an odd-step
+//     pair that straddles two lanes is completed by both lanes from one
+//     shuffle each way.
+//   * One cluster barrier (arrive.release / wait.acquire) per step.
 // Control flow is identical in every CTA (the stop decision is made by CTA 0
 // and broadcast), so every CTA reaches every cluster barrier.
 #include <cooperative_groups.h>
@@ -33,12 +38,16 @@ namespace gbpca {
 
 namespace {
 
-constexpr int kThreads = 1024;
+constexpr int kThreads = 640;
 constexpr int kBandWarps = 4;
-constexpr int kBulkLanes = kThreads - kBandWarps * 32;
+constexpr int kBulkWarps = kThreads / 32 - kBandWarps;
+constexpr int kBulkLanes = kBulkWarps * 32;
 constexpr int kMaxItems = 4;      // bulk blocks per lane per parity (checked)
-constexpr int kMaxVItems = 8;     // V pair-rotations per thread per parity (checked)
+constexpr int kVRows = 2;         // V rows per bulk warp (checked)
 constexpr int kMaxCl = 8;
+constexpr int kSlots = 3;
+constexpr int kRecs = 128;        // records per slot: 32 lanes x W/2 pairs, W <= 8
+constexpr uint32_t kNone = 0xffffffffu;
 
 struct Params {
   const double* C;
@@ -46,9 +55,8 @@ struct Params {
   float tol32;
   int sweeps_max;
   int relative_stop;
-  int nA, nV;
-  int rp[kMaxCl + 1];     // even row-pair boundaries of the A-CTAs, rp[nA] = P
-  int vr[kMaxCl + 1];     // row boundaries of the V-CTAs, vr[nV] = B'
+  int nA;
+  int rp[kMaxCl + 1];     // even row-pair boundaries of the CTAs, rp[nA] = P
   float* diag32;
   float* v32;
   DevHeader* hdr;
@@ -72,11 +80,11 @@ __device__ __forceinline__ float sqrt_est(float x) {
 
 // Eqs. 2-5: small root t of Eq. 3 as t = sgn(tau)/(|tau| + sqrt(1+tau^2)),
 // tau = (aqq - app)/(2 apq); an off-diagonal below 2^-24 sqrt(|app aqq|) is
-// dropped without rotating (c = 1, s = 0).
-__device__ __forceinline__ void jacobi_angle(float app, float aqq, float apq, float& c, float& s,
-                                             float& t) {
+// dropped without rotating (c = 1, s = 0).  Returns the record of the pair:
+// (c, s) and the two diagonal values after the rotation and position swap.
+__device__ __forceinline__ float4 pair_record(float app, float aqq, float apq) {
   const float thr = 5.9604645e-08f * sqrt_est(fabsf(app)) * sqrt_est(fabsf(aqq));
-  if (!(fabsf(apq) > thr)) { c = 1.f; s = 0.f; t = 0.f; return; }
+  if (!(fabsf(apq) > thr)) return make_float4(1.f, 0.f, aqq, app);
   const float tau = (aqq - app) * rcp_nr(2.f * apq);
   const float at = fabsf(tau);
   float tt;
@@ -87,9 +95,8 @@ __device__ __forceinline__ void jacobi_angle(float app, float aqq, float apq, fl
     tt = rcp_nr(at + u * rsqrt_nr(u));
   }
   tt = (tau >= 0.f) ? tt : -tt;
-  c = rsqrt_nr(fmaf(tt, tt, 1.f));
-  s = tt * c;
-  t = tt;
+  const float c = rsqrt_nr(fmaf(tt, tt, 1.f));
+  return make_float4(c, tt * c, fmaf(tt, apq, aqq), fmaf(-tt, apq, app));
 }
 
 // M' = G_I M G_J, G = [[s, c], [c, -s]].
@@ -105,8 +112,8 @@ __device__ __forceinline__ void rot_block(float2 csI, float2 csJ, float& m00, fl
 }
 
 struct Shared {
-  float2 cs[2][kMaxB / 2];
-  float dg[kMaxB];
+  float4 rec[kSlots][kRecs];
+  float dg[kMaxB];        // diagonal at the sweep boundary
   double part_o[kMaxCl], part_d[kMaxCl];
   int part_v[kMaxCl];
   double wred[2][32];
@@ -116,34 +123,69 @@ struct Shared {
   double off_rel, fro;
 };
 
-// Rotates the diagonal block of pair (p, p+1) whose off-diagonal apq is in a
-// register: new (c, s) into cs_next[J] and the rotated-and-swapped diagonal
-// into dg[p], dg[p+1] of every CTA of the cluster.
-__device__ __forceinline__ void pair_rotation(cg::cluster_group& cl, Shared* sh, int ncl, int p,
-                                              float apq, int slot, int J) {
-  const float app = sh->dg[p], aqq = sh->dg[p + 1];
-  float c, s, t;
-  jacobi_angle(app, aqq, apq, c, s, t);
-  const float2 v = make_float2(c, s);
-  const float np0 = fmaf(t, apq, aqq), np1 = fmaf(-t, apq, app);
-  for (int r = 0; r < ncl; ++r) {
-    Shared* o = cl.map_shared_rank(sh, r);
-    o->cs[slot][J] = v;
-    o->dg[p] = np0;
-    o->dg[p + 1] = np1;
-  }
+// Record index of pair J: lane l of a V warp reads the records of its pairs
+// l*H .. l*H+H-1 as H conflict-free 16-byte loads (index t*32 + l).
+template <int H>
+__device__ __forceinline__ int rix(int J) { return (J % H) * 32 + J / H; }
+
+__device__ __forceinline__ float2 cs_of(const float4& r) { return make_float2(r.x, r.y); }
+
+template <int H>
+__device__ __forceinline__ void push_record(cg::cluster_group& cl, Shared* sh, int ncl, int slot,
+                                            int J, float4 r) {
+  const int i = rix<H>(J);
+  for (int q = 0; q < ncl; ++q) cl.map_shared_rank(sh, q)->rec[slot][i] = r;
 }
 
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Diagonal position x after an odd step (records in slot so) preceded by an
+// even step (slot se): positions 0 and B'-1 sat out the odd step.
+template <int H>
+__device__ __forceinline__ float diag_after_odd(const Shared* sh, int so, int se, int x, int Bp) {
+  const int P = Bp / 2;
+  if (x == 0) return sh->rec[se][rix<H>(0)].z;
+  if (x == Bp - 1) return sh->rec[se][rix<H>(P - 1)].w;
+  return (x & 1) ? sh->rec[so][rix<H>((x - 1) >> 1)].z : sh->rec[so][rix<H>((x - 2) >> 1)].w;
+}
+
+template <int W>
 __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm) {
+  constexpr int H = W / 2;                 // pairs per lane in a V row
   extern __shared__ __align__(16) float rows[];
   __shared__ Shared sh;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int B = prm.B, Bp = B + (B & 1), P = Bp / 2;
-  const int ncl = prm.nA + prm.nV;
-  const bool isA = rank < prm.nA;
+  const int ncl = prm.nA;
   const double* C = prm.C;
+  const bool band = warp < kBandWarps;
+  const int bw = warp - kBandWarps;        // bulk warp index
+  const int lid = tid - kBandWarps * 32;   // bulk lane index
+
+  // ---- this CTA's rows and V rows
+  // (the parameter array is read with constant indices: a dynamic index
+  // would copy it to local memory)
+  int I_lo = 0, I_hi = 0, prev_lo = 0;
+#pragma unroll
+  for (int r = 0; r < kMaxCl; ++r) {
+    if (r == rank) { I_lo = prm.rp[r]; I_hi = prm.rp[r + 1]; }
+    if (r + 1 == rank) prev_lo = prm.rp[r];
+  }
+  const int R0 = 2 * I_lo;
+  const int nrows = 2 * (I_hi - I_lo) + (I_hi < P ? 1 : 0);
+  const int V0 = (int)((long)Bp * rank / ncl), V1 = (int)((long)Bp * (rank + 1) / ncl);
+  // remote copies a handed-over row goes to: the previous CTA's halo row
+  // (after even steps) and the next CTA's first row (after odd steps)
+  float* halo_prev =
+      rank > 0 ? cl.map_shared_rank(rows, rank - 1) + (size_t)(2 * (I_lo - prev_lo)) * Bp : nullptr;
+  float* first_next = rank + 1 < ncl ? cl.map_shared_rank(rows, rank + 1) : nullptr;
 
   // ---- uniform early exit (every CTA reads the same header word)
   if (prm.hdr->nonfinite) {
@@ -151,49 +193,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
       for (int i = tid; i < Bp; i += kThreads) prm.diag32[i] = 0.f;
       if (tid == 0) { prm.hdr->sweeps = 0; prm.hdr->steps = 0; prm.hdr->tol_used = prm.tol32; }
     }
-    if (!isA) {
-      const int v = rank - prm.nA;
-      for (int e = tid; e < (prm.vr[v + 1] - prm.vr[v]) * Bp; e += kThreads) {
-        const int r = prm.vr[v] + e / Bp, c = e % Bp;
-        prm.v32[(size_t)r * Bp + c] = (r == c) ? 1.f : 0.f;
-      }
+    for (int e = tid; e < (V1 - V0) * Bp; e += kThreads) {
+      const int r = V0 + e / Bp, c = e % Bp;
+      prm.v32[(size_t)r * Bp + c] = (r == c) ? 1.f : 0.f;
     }
     return;
   }
 
-  // ---- this CTA's rows
-  const int I_lo = isA ? prm.rp[rank] : 0, I_hi = isA ? prm.rp[rank + 1] : 0;
-  const int R0 = 2 * I_lo;
-  const int nrows = isA ? 2 * (I_hi - I_lo) + (I_hi < P ? 1 : 0) : 0;
-  const int v = rank - prm.nA;
-  const int V0 = isA ? 0 : prm.vr[v], V1 = isA ? 0 : prm.vr[v + 1];
-  const int prev_lo = (isA && rank > 0) ? prm.rp[rank - 1] : 0;  // previous A-CTA's first pair
-
-  for (int i = tid; i < Bp; i += kThreads) sh.dg[i] = i < B ? (float)C[(size_t)i * B + i] : 0.f;
-  if (tid == 0) { sh.ovf = 0; sh.flag = 0; }
-  if (isA) {
-    for (int e = tid; e < nrows * Bp; e += kThreads) {
-      const int i = R0 + e / Bp, j = e % Bp;
-      rows[e] = (i < B && j < B) ? (float)C[(size_t)i * B + j] : 0.f;
-    }
-  } else {
-    for (int e = tid; e < (V1 - V0) * Bp; e += kThreads) {
-      const int i = V0 + e / Bp, j = e % Bp;
-      rows[e] = (i == j) ? 1.f : 0.f;
-    }
+  // ---- matrix rows, and records that reproduce the initial diagonal as the
+  //      state after an odd step (slot 2) preceded by an even step (slot 1)
+  for (int e = tid; e < nrows * Bp; e += kThreads) {
+    const int i = R0 + e / Bp, j = e % Bp;
+    rows[e] = (i < B && j < B) ? (float)C[(size_t)i * B + j] : 0.f;
   }
-  cl.sync();  // every CTA's flags are initialised before anyone writes them remotely
+  auto d0 = [&](int i) { return i < B ? (float)C[(size_t)i * B + i] : 0.f; };
+  for (int J = tid; J < P; J += kThreads) {
+    sh.rec[1][rix<H>(J)] = make_float4(1.f, 0.f, d0(2 * J), d0(2 * J + 1));
+    sh.rec[2][rix<H>(J)] = make_float4(1.f, 0.f, d0(2 * J + 1), J + 1 < P ? d0(2 * J + 2) : 0.f);
+  }
+  if (tid == 0) { sh.ovf = 0; sh.flag = 0; }
 
-  // A-CTAs use lst[e][0..kMaxItems), V-CTAs lst[e][0..kMaxVItems)
-  uint32_t lst[2][kMaxVItems];
+  // ---- V rows in registers: bulk warp bw holds rows V0 + bw + kBulkWarps*k
+  float v[kVRows][W];
+  int vrow[kVRows];
+#pragma unroll
+  for (int k = 0; k < kVRows; ++k) {
+    vrow[k] = band ? -1 : V0 + bw + kBulkWarps * k;
+    if (vrow[k] >= V1) vrow[k] = -1;
+#pragma unroll
+    for (int c = 0; c < W; ++c) v[k][c] = (vrow[k] >= 0 && vrow[k] == W * lane + c) ? 1.f : 0.f;
+  }
+
+  // ---- bulk block lists (blocks (I, J >= I+2) of this CTA's row pairs)
+  uint32_t lst[2][kMaxItems];
+  uint32_t xitem = kNone;   // odd steps: one row-0 or last-column item
   int overflow = 0;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     const int np = P - e;
 #pragma unroll
-    for (int t = 0; t < kMaxVItems; ++t) lst[e][t] = 0xffffffffu;
-    if (isA && warp >= kBandWarps) {
-      const int lid = tid - kBandWarps * 32;
+    for (int t = 0; t < kMaxItems; ++t) lst[e][t] = kNone;
+    if (!band) {
       const int Ihi = min(I_hi, np - 2);  // rows that hold a block with J >= I + 2
       int total = 0;
       for (int I = I_lo; I < Ihi; ++I) total += np - 2 - I;
@@ -210,23 +250,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
         }
       }
     }
-    if (!isA) {
-      const int total = (V1 - V0) * np;
-      if (total > kMaxVItems * kThreads) overflow = 1;
-#pragma unroll
-      for (int t = 0; t < kMaxVItems; ++t) {
-        const int idx = tid + t * kThreads;
-        if (idx < total) {
-          const int lr = idx / np, J = idx - lr * np;
-          const int off = lr * Bp + 2 * J + e;
-          lst[e][t] = ((uint32_t)J << 16) | (uint32_t)off;
-        }
-      }
+  }
+  if (!band) {
+    // odd-step extras: row 0 against odd pairs 1..P-2 (CTA 0), and this CTA's
+    // odd pairs against the idle last column (pair P-2 goes to a band thread)
+    const int nrow0 = (rank == 0 && P > 2) ? P - 2 : 0;
+    const int Ioe = min(I_hi, P - 1);
+    const int ncol = Ioe > I_lo ? Ioe - I_lo : 0;
+    if (nrow0 + ncol > kBulkLanes) overflow = 1;
+    if (lid < nrow0) {
+      xitem = (uint32_t)(lid + 1);
+    } else if (lid < nrow0 + ncol) {
+      const int I = I_lo + (lid - nrow0);
+      if (I != P - 2) xitem = (1u << 31) | (uint32_t)I;
     }
   }
-  // the capacities hold for every B <= 232 with the partitions the host builds;
-  // a violation is made known to every CTA so that all of them stop together
+  if (V1 - V0 > kVRows * kBulkWarps || P > 32 * H) overflow = 1;
   overflow = __syncthreads_or(overflow);
+  cl.sync();  // every CTA's flags and records are initialised before remote writes
   if (overflow && tid == 0)
     for (int r = 0; r < ncl; ++r) atomicOr(&cl.map_shared_rank(&sh, r)->ovf, 1);
   cl.sync();
@@ -234,11 +275,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
   if (ovf && rank == 0 && tid == 0) set_status(prm.hdr, PCA_ERR_ARG);
 
   int sweep = 0, status = PCA_OK;
+  int gs = 0;                    // global step number; step gs uses record slot gs % 3
   const float tol2 = prm.tol32 * prm.tol32;
   for (; !ovf;) {
-    // ---------------- stop test over the A-CTAs' own rows, decided by CTA 0
-    if (isA) {
-      float so = 0.f, sd = 0.f;
+    // ---------------- diagonal at the sweep boundary (after the last odd step)
+    {
+      const int so = (gs + 2) % kSlots, se = (gs + 1) % kSlots;
+      for (int x = tid; x < Bp; x += kThreads) sh.dg[x] = diag_after_odd<H>(&sh, so, se, x, Bp);
+    }
+    __syncthreads();
+    // ---------------- stop test over this CTA's own rows, decided by CTA 0
+    {
+      float so2 = 0.f, sd = 0.f;
       int viol = 0;
       for (int i = R0 + warp; i < 2 * I_hi; i += kThreads / 32) {
         const float* Ai = rows + (i - R0) * Bp;
@@ -247,18 +295,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
         const float aii = fabsf(dii);
         for (int j = i + 1 + lane; j < Bp; j += 32) {
           const float a = Ai[j];
-          so = fmaf(a, a, so);
+          so2 = fmaf(a, a, so2);
           viol |= (a * a > tol2 * aii * fabsf(sh.dg[j])) ? 1 : 0;
         }
       }
-      so = warp_sum(so);
+      so2 = warp_sum(so2);
       sd = warp_sum(sd);
       viol = __any_sync(kFull, viol);
-      if (lane == 0) { sh.wred[0][warp] = (double)so; sh.wred[1][warp] = (double)sd; sh.wviol[warp] = viol; }
+      if (lane == 0) {
+        sh.wred[0][warp] = (double)so2;
+        sh.wred[1][warp] = (double)sd;
+        sh.wviol[warp] = viol;
+      }
       __syncthreads();
       if (warp == 0) {
-        const double o = warp_sum(sh.wred[0][lane]), d = warp_sum(sh.wred[1][lane]);
-        const int anyv = __any_sync(kFull, sh.wviol[lane]);
+        constexpr int kWarps = kThreads / 32;
+        const bool has = lane < kWarps;
+        const double o = warp_sum(has ? sh.wred[0][lane] : 0.0);
+        const double d = warp_sum(has ? sh.wred[1][lane] : 0.0);
+        const int anyv = __any_sync(kFull, has && sh.wviol[lane]);
         if (lane == 0) {
           Shared* s0 = cl.map_shared_rank(&sh, 0);
           s0->part_o[rank] = o;
@@ -271,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
     if (rank == 0 && tid == 0) {
       double o = 0.0, d = 0.0;
       int anyv = 0;
-      for (int r = 0; r < prm.nA; ++r) { o += sh.part_o[r]; d += sh.part_d[r]; anyv |= sh.part_v[r]; }
+      for (int r = 0; r < ncl; ++r) { o += sh.part_o[r]; d += sh.part_d[r]; anyv |= sh.part_v[r]; }
       const double off = sqrt(2.0 * o), fro = sqrt(2.0 * o + d);
       const bool conv = prm.relative_stop ? !anyv : off <= (double)prm.tol32 * fro;
       int flag = 0;
@@ -286,143 +341,182 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
     if (flag) { status = flag == 1 ? PCA_OK : PCA_ERR_NOCONV; break; }
 
     // ---------------- the first (even) step's pairs: rotate their diagonal blocks
-    if (isA && tid < I_hi - I_lo) {
+    if (tid < I_hi - I_lo) {
       const int I = I_lo + tid, p = 2 * I;
       float* apq = rows + (p - R0) * Bp + p + 1;
-      pair_rotation(cl, &sh, ncl, p, *apq, 0, I);
+      push_record<H>(cl, &sh, ncl, gs % kSlots, I, pair_record(sh.dg[p], sh.dg[p + 1], *apq));
       *apq = 0.f;
+      if (I == I_lo && halo_prev) halo_prev[p + 1] = 0.f;
     }
     cl.sync();
 
     auto step_body = [&](auto E_, bool last) {
       constexpr int e = decltype(E_)::value;
       const int np = P - e;
-      const float2* cur = sh.cs[e];
-      const int nslot = e ^ 1;
-      if (isA) {
-        if (warp < kBandWarps) {
-          // super-diagonal blocks (I, I+1) of this CTA's row pairs
-          const int I = I_lo + tid;
-          const int Iend = min(I_hi, np - 1);
-          if (I < Iend) {
-            const int pI = 2 * I + e;
-            float* r0 = rows + (pI - R0) * Bp + pI + 2;
-            float* r1 = r0 + Bp;
-            float m00, m01, m10, m11;
-            if (e == 0) {
-              const float2 x = *reinterpret_cast<const float2*>(r0);
-              const float2 y = *reinterpret_cast<const float2*>(r1);
-              m00 = x.x; m01 = x.y; m10 = y.x; m11 = y.y;
-            } else {
-              m00 = r0[0]; m01 = r0[1]; m10 = r1[0]; m11 = r1[1];
+      const int cur = gs % kSlots, nxt = (gs + 1) % kSlots, prv = (gs + 2) % kSlots;
+      const float4* rc = sh.rec[cur];
+      if (band) {
+        // super-diagonal blocks (I, I+1) of this CTA's row pairs
+        const int I = I_lo + tid;
+        const int Iend = min(I_hi, np - 1);
+        if (I < Iend) {
+          const int pI = 2 * I + e;
+          float* r0 = rows + (pI - R0) * Bp + pI + 2;
+          float* r1 = r0 + Bp;
+          float m00, m01, m10, m11;
+          if (e == 0) {
+            const float2 x = *reinterpret_cast<const float2*>(r0);
+            const float2 y = *reinterpret_cast<const float2*>(r1);
+            m00 = x.x; m01 = x.y; m10 = y.x; m11 = y.y;
+          } else {
+            m00 = r0[0]; m01 = r0[1]; m10 = r1[0]; m11 = r1[1];
+          }
+          const float4 gI = rc[rix<H>(I)], gJ = rc[rix<H>(I + 1)];
+          rot_block(cs_of(gI), cs_of(gJ), m00, m01, m10, m11);
+          if (!last) {  // (q_I, p_{I+1}) is the off-diagonal of a next-step pair
+            push_record<H>(cl, &sh, ncl, nxt, e == 0 ? I : I + 1, pair_record(gI.w, gJ.z, m10));
+            m10 = 0.f;
+          }
+          if (e == 0) {
+            *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
+            *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
+            if (I == I_lo && halo_prev)
+              *reinterpret_cast<float2*>(halo_prev + pI + 2) = make_float2(m00, m01);
+          } else {
+            r0[0] = m00; r0[1] = m01; r1[0] = m10; r1[1] = m11;
+            if (I == I_hi - 1 && first_next) { first_next[pI + 2] = m10; first_next[pI + 3] = m11; }
+          }
+        }
+        if (e) {
+          // odd-step items whose result is the off-diagonal of a next even
+          // pair, each on a thread of its own: (0, 1) -> pair 0 (CTA 0) and
+          // (B'-2, B'-1) -> pair P-1 (the CTA that holds odd pair P-2)
+          if (tid == kBandWarps * 32 - 1 && rank == 0 && P >= 2) {
+            const float4 g = rc[rix<H>(0)];
+            float* a = rows + 1;                     // (0, 1), (0, 2)
+            const float x = a[0], y = a[1];
+            float n0 = fmaf(x, g.y, y * g.x);
+            const float n1 = fmaf(x, g.x, -y * g.y);
+            if (!last) {
+              push_record<H>(cl, &sh, ncl, nxt, 0, pair_record(sh.rec[prv][rix<H>(0)].z, g.z, n0));
+              n0 = 0.f;
             }
-            rot_block(cur[I], cur[I + 1], m00, m01, m10, m11);
-            if (!last) {  // (q_I, p_{I+1}) is the off-diagonal of a next-step pair
-              pair_rotation(cl, &sh, ncl, pI + 1, m10, nslot, e == 0 ? I : I + 1);
-              m10 = 0.f;
+            a[0] = n0;
+            a[1] = n1;
+          }
+          if (tid == kBandWarps * 32 - 2 && P >= 2 && I_lo <= P - 2 && P - 2 < I_hi) {
+            const float4 g = rc[rix<H>(P - 2)];
+            float* a = rows + (Bp - 3 - R0) * Bp + (Bp - 1);  // (B'-3, L), (B'-2, L)
+            const float x = a[0], y = a[Bp];
+            const float n0 = fmaf(g.y, x, g.x * y);
+            float n1 = fmaf(g.x, x, -g.y * y);
+            if (!last) {
+              push_record<H>(cl, &sh, ncl, nxt, P - 1,
+                             pair_record(g.w, sh.rec[prv][rix<H>(P - 1)].w, n1));
+              n1 = 0.f;
             }
-            if (e == 0) {
-              *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
-              *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
-            } else {
-              r0[0] = m00; r0[1] = m01; r1[0] = m10; r1[1] = m11;
+            a[0] = n0;
+            a[Bp] = n1;
+            if (P - 2 == I_hi - 1 && first_next) first_next[Bp - 1] = n1;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < kMaxItems; ++t) {
+          const uint32_t w = lst[e][t];
+          if (w == kNone) continue;
+          const int I = (int)(w >> 24), J = (int)((w >> 16) & 0xff);
+          const float2 csI = cs_of(rc[rix<H>(I)]), csJ = cs_of(rc[rix<H>(J)]);
+          float* r0 = rows + (w & 0xffff);
+          float* r1 = r0 + Bp;
+          float m00, m01, m10, m11;
+          if (e == 0) {
+            const float2 u = *reinterpret_cast<const float2*>(r0);
+            const float2 q = *reinterpret_cast<const float2*>(r1);
+            m00 = u.x; m01 = u.y; m10 = q.x; m11 = q.y;
+          } else {
+            m00 = r0[0]; m01 = r0[1]; m10 = r1[0]; m11 = r1[1];
+          }
+          rot_block(csI, csJ, m00, m01, m10, m11);
+          if (e == 0) {
+            *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
+            *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
+            if (I == I_lo && halo_prev)
+              *reinterpret_cast<float2*>(halo_prev + 2 * J) = make_float2(m00, m01);
+          } else {
+            r0[0] = m00; r0[1] = m01; r1[0] = m10; r1[1] = m11;
+            if (I == I_hi - 1 && first_next) {
+              first_next[2 * J + 1] = m10;
+              first_next[2 * J + 2] = m11;
             }
           }
-          if (e) {
-            // idle row 0 (CTA 0) against every pair; this CTA's odd pairs
-            // against the idle column Bp-1
-            const int nrow0 = rank == 0 ? np : 0;
-            const int Ioe = min(I_hi, np);
-            const int ncol = Ioe > I_lo ? Ioe - I_lo : 0;
-            for (int w = tid; w < nrow0 + ncol; w += kBandWarps * 32) {
-              if (w < nrow0) {
-                const float2 g = cur[w];
-                float* a = rows + 2 * w + 1;  // (0, p), (0, q)
-                const float x = a[0], y = a[1];
-                float n0 = fmaf(x, g.y, y * g.x);
-                const float n1 = fmaf(x, g.x, -y * g.y);
-                if (w == 0 && !last) {  // (0, 1): next even pair 0
-                  pair_rotation(cl, &sh, ncl, 0, n0, nslot, 0);
-                  n0 = 0.f;
-                }
-                a[0] = n0;
-                a[1] = n1;
-              } else {
-                const int I = I_lo + (w - nrow0);
-                const float2 g = cur[I];
-                float* a = rows + (2 * I + 1 - R0) * Bp + (Bp - 1);  // (p, L), (q, L)
-                const float x = a[0], y = a[Bp];
-                const float n0 = fmaf(g.y, x, g.x * y);
-                float n1 = fmaf(g.x, x, -g.y * y);
-                if (I == P - 2 && !last) {  // (Bp-2, Bp-1): next even pair P-1
-                  pair_rotation(cl, &sh, ncl, Bp - 2, n1, nslot, P - 1);
-                  n1 = 0.f;
-                }
-                a[0] = n0;
-                a[Bp] = n1;
+        }
+        if (e && xitem != kNone) {
+          if (!(xitem >> 31)) {        // (0, p), (0, q) against column pair w
+            const int wp = (int)(xitem & 0xffff);
+            const float2 g = cs_of(rc[rix<H>(wp)]);
+            float* a = rows + 2 * wp + 1;
+            const float x = a[0], y = a[1];
+            a[0] = fmaf(x, g.y, y * g.x);
+            a[1] = fmaf(x, g.x, -y * g.y);
+          } else {                     // (p, L), (q, L) against row pair I
+            const int I = (int)(xitem & 0xffff);
+            const float2 g = cs_of(rc[rix<H>(I)]);
+            float* a = rows + (2 * I + 1 - R0) * Bp + (Bp - 1);
+            const float x = a[0], y = a[Bp];
+            const float n1 = fmaf(g.x, x, -g.y * y);
+            a[0] = fmaf(g.y, x, g.x * y);
+            a[Bp] = n1;
+            if (I == I_hi - 1 && first_next) first_next[Bp - 1] = n1;
+          }
+        }
+      }
+      cluster_arrive();
+      // V rows: (v_p, v_q) <- (v_p, v_q) G for every pair of this step.  The
+      // records of this slot are rewritten only after every CTA has arrived
+      // at the next step's barrier, which this CTA does after these lines.
+      if (!band && vrow[0] >= 0) {
+        const int J0 = H * lane;
+        float2 g[H];
+#pragma unroll
+        for (int t = 0; t < H; ++t) g[t] = cs_of(rc[t * 32 + lane]);
+        if (e == 0) {
+#pragma unroll
+          for (int k = 0; k < kVRows; ++k) {
+            if (vrow[k] < 0) continue;
+#pragma unroll
+            for (int t = 0; t < H; ++t) {
+              if (J0 + t < P) {
+                const float x = v[k][2 * t], y = v[k][2 * t + 1];
+                v[k][2 * t] = fmaf(x, g[t].y, y * g[t].x);
+                v[k][2 * t + 1] = fmaf(x, g[t].x, -y * g[t].y);
               }
             }
           }
         } else {
+          // pair J0-1 straddles this lane and the previous one
+          const float2 gp = lane > 0 ? cs_of(rc[(H - 1) * 32 + lane - 1]) : make_float2(1.f, 0.f);
 #pragma unroll
-          for (int t = 0; t < kMaxItems; ++t) {
-            const uint32_t w = lst[e][t];
-            if (w == 0xffffffffu) continue;
-            const float2 csI = cur[w >> 24], csJ = cur[(w >> 16) & 0xff];
-            float* r0 = rows + (w & 0xffff);
-            float* r1 = r0 + Bp;
-            float m00, m01, m10, m11;
-            if (e == 0) {
-              const float2 u = *reinterpret_cast<const float2*>(r0);
-              const float2 q = *reinterpret_cast<const float2*>(r1);
-              m00 = u.x; m01 = u.y; m10 = q.x; m11 = q.y;
-            } else {
-              m00 = r0[0]; m01 = r0[1]; m10 = r1[0]; m11 = r1[1];
+          for (int k = 0; k < kVRows; ++k) {
+            if (vrow[k] < 0) continue;        // uniform over the warp
+            const float yn = __shfl_down_sync(kFull, v[k][0], 1);     // next lane's first
+            const float xp = __shfl_up_sync(kFull, v[k][W - 1], 1);   // previous lane's last
+            const float xl = v[k][W - 1], y0 = v[k][0];
+#pragma unroll
+            for (int t = 0; t < H - 1; ++t) {
+              if (J0 + t < P - 1) {
+                const float x = v[k][2 * t + 1], y = v[k][2 * t + 2];
+                v[k][2 * t + 1] = fmaf(x, g[t].y, y * g[t].x);
+                v[k][2 * t + 2] = fmaf(x, g[t].x, -y * g[t].y);
+              }
             }
-            rot_block(csI, csJ, m00, m01, m10, m11);
-            if (e == 0) {
-              *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
-              *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
-            } else {
-              r0[0] = m00; r0[1] = m01; r1[0] = m10; r1[1] = m11;
-            }
+            if (J0 + H - 1 < P - 1) v[k][W - 1] = fmaf(xl, g[H - 1].y, yn * g[H - 1].x);
+            if (lane > 0 && J0 - 1 < P - 1) v[k][0] = fmaf(xp, gp.x, -y0 * gp.y);
           }
         }
-      } else {
-        // V rows: (v_p, v_q) <- (v_p, v_q) G for every pair of this step
-#pragma unroll
-        for (int t = 0; t < kMaxVItems; ++t) {
-          const uint32_t w = lst[e][t];
-          if (w == 0xffffffffu) continue;
-          const float2 g = cur[w >> 16];
-          float* a = rows + (w & 0xffff);
-          float x, y;
-          if (e == 0) {
-            const float2 u = *reinterpret_cast<const float2*>(a);
-            x = u.x; y = u.y;
-          } else {
-            x = a[0]; y = a[1];
-          }
-          const float nx = fmaf(x, g.y, y * g.x), ny = fmaf(x, g.x, -y * g.y);
-          if (e == 0) *reinterpret_cast<float2*>(a) = make_float2(nx, ny);
-          else { a[0] = nx; a[1] = ny; }
-        }
       }
-      __syncthreads();
-      // hand over the row that changes holder: after an even step this CTA's
-      // first row goes to the previous A-CTA's halo; after an odd step its halo
-      // row goes back to the next A-CTA's first row
-      if (isA) {
-        if (e == 0 && rank > 0) {
-          float* dst = cl.map_shared_rank(rows, rank - 1) + (size_t)(2 * (I_lo - prev_lo)) * Bp;
-          for (int j = R0 + tid; j < Bp; j += kThreads) dst[j] = rows[j];
-        } else if (e == 1 && rank + 1 < prm.nA) {
-          const float* src = rows + (size_t)(2 * (I_hi - I_lo)) * Bp;
-          float* dst = cl.map_shared_rank(rows, rank + 1);
-          for (int j = 2 * I_hi + tid; j < Bp; j += kThreads) dst[j] = src[j];
-        }
-      }
-      cl.sync();
+      cluster_wait();
+      ++gs;
     };
     for (int step = 0; step < Bp; step += 2) {
       step_body(std::integral_constant<int, 0>{}, false);
@@ -432,7 +526,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
   }
 
   if (rank == 0) {
-    for (int i = tid; i < Bp; i += kThreads) prm.diag32[i] = sh.dg[i];
+    const int so = (gs + 2) % kSlots, se = (gs + 1) % kSlots;
+    for (int x = tid; x < Bp; x += kThreads)
+      prm.diag32[x] = ovf ? 0.f : diag_after_odd<H>(&sh, so, se, x, Bp);
     if (tid == 0) {
       prm.hdr->sweeps = sweep;
       prm.hdr->steps = sweep * Bp;
@@ -442,20 +538,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
       if (status != PCA_OK) set_status(prm.hdr, status);
     }
   }
-  if (!isA) {
-    for (int e = tid; e < (V1 - V0) * Bp; e += kThreads)
-      prm.v32[(size_t)V0 * Bp + e] = rows[e];
+#pragma unroll
+  for (int k = 0; k < kVRows; ++k) {
+    if (vrow[k] < 0) continue;
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      const int pos = W * lane + c;
+      if (pos < Bp) prm.v32[(size_t)vrow[k] * Bp + pos] = v[k][c];
+    }
   }
-  cl.sync();  // no CTA leaves while others may still read its shared memory
+  cl.sync();  // no CTA leaves while others may still write its shared memory
 }
+
+int v_width(int Bp) { return Bp <= 64 ? 2 : (Bp <= 128 ? 4 : 8); }
 
 }  // namespace
 
 bool jacobi_cluster_shape(int B, int* nA, int* nV) {
   const int Bp = round_even(B);
-  if (Bp <= 64) { *nA = 1; *nV = 1; }
-  else if (Bp <= 128) { *nA = 2; *nV = 2; }
-  else { *nA = 4; *nV = 4; }
+  *nA = Bp <= 32 ? 1 : (Bp <= 64 ? 2 : (Bp <= 128 ? 4 : 8));
+  *nV = 0;
   return true;
 }
 
@@ -469,9 +571,10 @@ cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweep
   prm.tol32 = tol32;
   prm.sweeps_max = sweeps_max;
   prm.relative_stop = relative_stop ? 1 : 0;
-  jacobi_cluster_shape(B, &prm.nA, &prm.nV);
+  int nV = 0;
+  jacobi_cluster_shape(B, &prm.nA, &nV);
   if (prm.nA > P) prm.nA = P;
-  // A rows: balance the blocks (I, J >= I) of the even steps
+  // rows: balance the blocks (I, J >= I) of the even steps
   const long total = (long)P * (P + 1) / 2;
   prm.rp[0] = 0;
   long acc = 0;
@@ -486,7 +589,6 @@ cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweep
     for (int i = 0; i < I; ++i) acc += P - i;
   }
   prm.rp[prm.nA] = P;
-  for (int r = 0; r <= prm.nV; ++r) prm.vr[r] = (int)((long)Bp * r / prm.nV);
   prm.diag32 = diag32;
   prm.v32 = v32;
   prm.hdr = hdr;
@@ -496,27 +598,28 @@ cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweep
     const int n = 2 * (prm.rp[r + 1] - prm.rp[r]) + (prm.rp[r + 1] < P ? 1 : 0);
     maxrows = n > maxrows ? n : maxrows;
   }
-  for (int r = 0; r < prm.nV; ++r) {
-    const int n = prm.vr[r + 1] - prm.vr[r];
-    maxrows = n > maxrows ? n : maxrows;
-  }
   const size_t smem = (size_t)maxrows * Bp * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi_cluster,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void (*kern)(const Params);
+  switch (v_width(Bp)) {
+    case 2: kern = k_jacobi_cluster<2>; break;
+    case 4: kern = k_jacobi_cluster<4>; break;
+    default: kern = k_jacobi_cluster<8>; break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(prm.nA + prm.nV);
+  cfg.gridDim = dim3(prm.nA);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = prm.nA + prm.nV;
+  at[0].val.clusterDim.x = prm.nA;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k_jacobi_cluster, prm);
+  e = cudaLaunchKernelEx(&cfg, kern, prm);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -89,11 +89,13 @@ k_dfgemm(const float2* __restrict__ A, const float2* __restrict__ Bm,
     if (ch < nchunks) {
       for (int e = t; e < kT * kT; e += kTh) {
         const int a = e / kT, b = e % kT;
-        {  // as[k = b][row = a] = op(A)[r0 + a][k0 + b]
-          const int r = r0 + a, k = k0 + b;
+        {  // as[k][row] = op(A)[r0 + row][k0 + k]; the index that runs fastest
+           // over the threads is the one contiguous in memory
+          const int row = kTransA ? b : a, kk = kTransA ? a : b;
+          const int r = r0 + row, k = k0 + kk;
           float2 v = make_float2(0.f, 0.f);
           if (r < n && k < n) v = kTransA ? A[(size_t)k * n + r] : A[(size_t)r * n + k];
-          as[grp][b][a] = v;
+          as[grp][kk][row] = v;
         }
         {  // bs[k = a][col = b] = Bm[k0 + a][c0 + b]
           const int k = k0 + a, c = c0 + b;

@@ -5,21 +5,25 @@
 // One persistent CTA per SM walks a contiguous range of 32-pixel chunks:
 //   warp 0      TMA producer: cp.async.bulk of each chunk (pixel-major, a
 //               contiguous byte range of the cube) into a 4-stage FP32 ring;
-//   warps 2-17  converters: x = y - s (s = first pixel, a per-band shift),
-//               split into BF16 hi = bf16(x), lo = bf16(x - hi), written
-//               transposed ([band][pixel], K-major core-matrix layout) into
-//               a 2-stage operand ring; one extra operand row is all ones,
-//               so the same MMAs also produce the band sums S1 = sum x;
+//   warps 2-17  converters: x = (y - s) 2^e per band (s = sample mean and e
+//               a power-of-two scale, both from the band probe), split into
+//               FP16 hi = fp16(x), lo = fp16(x - hi) -- 22 significant bits
+//               of x -- written transposed ([band][pixel], K-major core-
+//               matrix layout) into a 2-stage operand ring; one extra operand
+//               row is all ones, so the same MMAs also produce the band sums
+//               S1 = sum x;
 //   warp 1      MMA issuer (one thread): D += hi hi^T + hi lo^T + lo hi^T
 //               for the upper block-triangle (row tile 0: bands 0-127 x all;
 //               row tile 1: bands 128-255 x bands 128-255) with FP32
 //               accumulation in TMEM;
 //   warps 2-5   epilogue: TMEM -> registers -> the CTA's partial slot
-//               (packed upper triangle, FP32) and S1 (FP64).
-// The partials are reduced and finalised by k_cov.cu exactly like the SIMT
-// forms.  Every mbarrier wait is bounded (one second of globaltimer); on
-// time-out the CTA records PCA_ERR_TIMEOUT, drains its MMAs, frees TMEM and
-// returns.
+//               (packed upper triangle, FP32, still scaled by 2^(e_i+e_j))
+//               and S1 (FP64, unscaled).
+// A scaled value outside the FP16 range sets hdr->cov_range; the caller then
+// recomputes the partials on the SIMT path.  The partials are reduced and
+// finalised by k_cov.cu.  Every mbarrier wait is bounded (one second of
+// globaltimer); on time-out the CTA records PCA_ERR_TIMEOUT, drains its MMAs,
+// frees TMEM and returns.
 #include "common.cuh"
 
 namespace gbpca {
@@ -28,11 +32,11 @@ namespace {
 
 constexpr int kKC = 32;                 // pixels per chunk (K of one stage)
 constexpr int kStages = 4;              // FP32 TMA ring depth
-constexpr int kOpStages = 2;            // BF16 operand ring depth
+constexpr int kOpStages = 2;            // FP16 operand ring depth
 constexpr int kRows = 256;              // operand rows (bands, padded; ones row included)
 constexpr int kConvWarps = 16;
 constexpr int kThreads = (2 + kConvWarps) * 32;
-constexpr int kOpBytes = kRows * kKC * 2;        // one BF16 operand (hi or lo): 16 KB
+constexpr int kOpBytes = kRows * kKC * 2;        // one FP16 operand (hi or lo): 16 KB
 constexpr uint32_t kLBO = 128;                   // K-adjacent core matrices
 constexpr uint32_t kSBO = (kKC / 8) * 128;       // 8-row groups: 512 B
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s bound on every wait
@@ -111,11 +115,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((kSBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
-// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// kind::f16 instruction descriptor: D F32, A/B F16 (format 0), both K-major,
+// M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -141,14 +146,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
   uint32_t r;  // low half = a, high half = b
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
   return r;
 }
-__device__ __forceinline__ void unpack_bf16x2(uint32_t v, float& a, float& b) {
-  a = __uint_as_float(v << 16);
-  b = __uint_as_float(v & 0xffff0000u);
+__device__ __forceinline__ void unpack_f16x2(uint32_t v, float& a, float& b) {
+  a = __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
+  b = __half2float(__ushort_as_half((unsigned short)(v >> 16)));
 }
 
 template <typename In>
@@ -156,9 +161,9 @@ __device__ __forceinline__ float elem(const In* p) { return to_f32<In>(*p); }
 
 template <typename In>
 __global__ void __launch_bounds__(kThreads, 1)
-k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shift_out,
-          double* __restrict__ s1_part, float* __restrict__ s2_part, int s2_elems,
-          DevHeader* __restrict__ hdr) {
+k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict__ shift,
+          const int* __restrict__ escale, double* __restrict__ s1_part,
+          float* __restrict__ s2_part, int s2_elems, DevHeader* __restrict__ hdr) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int R16 = (B + 15) & ~15;     // first row after the padded bands = the ones row
   const int stage_bytes_max = kKC * B * (int)sizeof(In);
@@ -181,9 +186,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
   // ---- set-up
   for (int i = tid; i < kOpStages * 2 * kOpBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(ops)[i] = make_uint4(0, 0, 0, 0);
-  for (int b = tid; b < kRows; b += kThreads) shs[b] = b < B ? elem(cube + b) : 0.f;
-  if (g == 0)
-    for (int b = tid; b < B; b += kThreads) shift_out[b] = elem(cube + b);
+  for (int b = tid; b < kRows; b += kThreads) shs[b] = b < B ? shift[b] : 0.f;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(&sb->full[s], 1); mbar_init(&sb->empty[s], kConvWarps); }
     for (int s = 0; s < kOpStages; ++s) { mbar_init(&sb->opfull[s], kConvWarps); mbar_init(&sb->opempty[s], 1); }
@@ -203,6 +206,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = sb->tmem_base;
+  int out_of_range = 0;   // a scaled value this thread converted left the FP16 range
 
   if (warp == 0) {
     // ---------------------------------------------------------- TMA producer
@@ -221,7 +225,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const uint32_t ops_base = su32(ops);
-      const uint32_t id0 = idesc_bf16(N0), id1 = idesc_bf16(N1 > 0 ? N1 : 16);
+      const uint32_t id0 = idesc_f16(N0), id1 = idesc_f16(N1 > 0 ? N1 : 16);
       bool issued = false;
       for (int c = 0; c < nch; ++c) {
         const int o = c % kOpStages;
@@ -234,15 +238,15 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
           const uint32_t ko = kk * 2 * kLBO;
           const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
           // tile 0: rows 0..127 (A) x rows 0..N0-1 (B)
-          mma_bf16(tbase, sdesc(hi + ko), sdesc(hi + ko), id0, acc0);
-          mma_bf16(tbase, sdesc(hi + ko), sdesc(lo + ko), id0, 1u);
-          mma_bf16(tbase, sdesc(lo + ko), sdesc(hi + ko), id0, 1u);
+          mma_f16(tbase, sdesc(hi + ko), sdesc(hi + ko), id0, acc0);
+          mma_f16(tbase, sdesc(hi + ko), sdesc(lo + ko), id0, 1u);
+          mma_f16(tbase, sdesc(lo + ko), sdesc(hi + ko), id0, 1u);
           if (two_tiles) {
             const uint32_t r128 = (128 / 8) * kSBO;
             const uint32_t t1 = tbase + (uint32_t)N0;
-            mma_bf16(t1, sdesc(hi + r128 + ko), sdesc(hi + r128 + ko), id1, acc0);
-            mma_bf16(t1, sdesc(hi + r128 + ko), sdesc(lo + r128 + ko), id1, 1u);
-            mma_bf16(t1, sdesc(lo + r128 + ko), sdesc(hi + r128 + ko), id1, 1u);
+            mma_f16(t1, sdesc(hi + r128 + ko), sdesc(hi + r128 + ko), id1, acc0);
+            mma_f16(t1, sdesc(hi + r128 + ko), sdesc(lo + r128 + ko), id1, 1u);
+            mma_f16(t1, sdesc(lo + r128 + ko), sdesc(hi + r128 + ko), id1, 1u);
           }
         }
         issued = true;
@@ -258,7 +262,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
     const int ct = tid - 64;
     const int items = (B + 1) * (kKC / 8);
     int ib[2], ipg[2], ioff[2];
-    float ish[2];
+    float ish[2], isc[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int w = ct + u * kConvWarps * 32;
@@ -267,12 +271,19 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
       const int row = ib[u] < B ? ib[u] : R16;
       ioff[u] = (row >> 3) * (int)kSBO + (ipg[u] < 0 ? 0 : ipg[u]) * 128 + (row & 7) * 16;
       ish[u] = ib[u] < B ? shs[ib[u]] : 0.f;
+      isc[u] = ib[u] < B ? ldexpf(1.f, escale[ib[u]]) : 1.f;
     }
     for (int c = 0; c < nch; ++c) {
       const int s = c % kStages, o = c % kOpStages;
-      const bool ok1 = mbar_wait(&sb->full[s], (c / kStages) & 1, sb);
-      const bool ok2 = ok1 && mbar_wait(&sb->opempty[o], ((c / kOpStages) & 1) ^ 1, sb);
-      if (!ok2) break;
+      // one lane per warp polls the barriers (the others would only add
+      // shared-memory traffic), then the warp proceeds together
+      int ok = 1;
+      if (lane == 0) {
+        ok = mbar_wait(&sb->full[s], (c / kStages) & 1, sb) ? 1 : 0;
+        if (ok) ok = mbar_wait(&sb->opempty[o], ((c / kOpStages) & 1) ^ 1, sb) ? 1 : 0;
+      }
+      ok = __shfl_sync(kFull, ok, 0);
+      if (!ok) break;
       const int64_t p0 = (c_begin + c) * kKC;
       const int cp = (int)((N - p0) < kKC ? (N - p0) : kKC);
       const int copied = (int)(((uint32_t)(cp * B * (int)sizeof(In)) & ~15u) / sizeof(In));
@@ -287,34 +298,37 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
         if (pg < 0) continue;
         uint32_t h[4], l[4];
         if (b < B) {
-          const float sh = ish[u];
+          const float sh = ish[u], sc = isc[u];
           float x[8];
           if (full) {
             const In* src = st + pg * 8 * B + b;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = elem(src + i * B) - sh;
+            for (int i = 0; i < 8; ++i) x[i] = (elem(src + i * B) - sh) * sc;
           } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const int p = pg * 8 + i;
               const int e = p * B + b;
               float v = 0.f;
-              if (p < cp) v = (e < copied ? elem(st + e) : elem(gsrc + e)) - sh;
+              if (p < cp) v = ((e < copied ? elem(st + e) : elem(gsrc + e)) - sh) * sc;
               x[i] = v;
             }
           }
+          // NaN compares false, so it counts as out of range too
+#pragma unroll
+          for (int i = 0; i < 8; ++i) out_of_range |= !(fabsf(x[i]) <= 65504.f);
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            h[i] = pack_bf16x2(x[2 * i], x[2 * i + 1]);
+            h[i] = pack_f16x2(x[2 * i], x[2 * i + 1]);
             float a, bb;
-            unpack_bf16x2(h[i], a, bb);
-            l[i] = pack_bf16x2(x[2 * i] - a, x[2 * i + 1] - bb);
+            unpack_f16x2(h[i], a, bb);
+            l[i] = pack_f16x2(x[2 * i] - a, x[2 * i + 1] - bb);
           }
         } else {  // ones row: 1 for real pixels, 0 for the tail
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int p = pg * 8 + 2 * i;
-            h[i] = pack_bf16x2(p < cp ? 1.f : 0.f, p + 1 < cp ? 1.f : 0.f);
+            h[i] = pack_f16x2(p < cp ? 1.f : 0.f, p + 1 < cp ? 1.f : 0.f);
             l[i] = 0u;
           }
         }
@@ -327,7 +341,9 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
     }
     // ---------------------------------------------------------- epilogue
     if (warp >= 2 && warp < 6) {
-      const bool ok = mbar_wait(&sb->done, 0, sb) && !*(volatile int*)&sb->abort;
+      int okw = 0;
+      if (lane == 0) okw = (mbar_wait(&sb->done, 0, sb) && !*(volatile int*)&sb->abort) ? 1 : 0;
+      const bool ok = __shfl_sync(kFull, okw, 0) != 0;
       tc_fence_after();
       const int q = warp & 3;          // TMEM lane quarter this warp may read
       const int r = q * 32 + lane;     // accumulator row
@@ -344,7 +360,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
           const int j = j0 + i;
           if (r < B && r < 128) {
             if (j < B && j >= r) out[packed_index(r, j, B)] = v[i];
-            if (j == R16) s1_part[(size_t)g * B + r] = (double)v[i];
+            if (j == R16) s1_part[(size_t)g * B + r] = ldexp((double)v[i], -escale[r]);
           }
         }
       }
@@ -360,7 +376,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
             const int jb = 128 + j0 + i;
             if (band < B) {
               if (jb < B && jb >= band) out[packed_index(band, jb, B)] = v[i];
-              if (jb == R16) s1_part[(size_t)g * B + band] = (double)v[i];
+              if (jb == R16) s1_part[(size_t)g * B + band] = ldexp((double)v[i], -escale[band]);
             }
           }
         }
@@ -369,7 +385,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
     }
   }
   tc_fence_before();
-  __syncthreads();
+  if (__syncthreads_or(out_of_range) && tid == 0) atomicOr(&hdr->cov_range, 1);
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
@@ -379,15 +395,17 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
 }
 
 template <typename In>
-cudaError_t syrk_tc_typed(const In* cube, int64_t N, int B, float* shift, double* s1_part,
-                          float* s2_part, int partials, DevHeader* hdr, cudaStream_t st) {
+cudaError_t syrk_tc_typed(const In* cube, int64_t N, int B, const float* shift, const int* escale,
+                          double* s1_part, float* s2_part, int partials, DevHeader* hdr,
+                          cudaStream_t st) {
   const int stage_stride = ((kKC * B * (int)sizeof(In)) + 127) & ~127;
   const size_t smem = 1024 + (size_t)kOpStages * 2 * kOpBytes + (size_t)kStages * stage_stride +
                       kRows * sizeof(float) + sizeof(SyncBlock);
   auto kern = k_syrk_tc<In>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<partials, kThreads, smem, st>>>(cube, N, B, shift, s1_part, s2_part, B * (B + 1) / 2, hdr);
+  kern<<<partials, kThreads, smem, st>>>(cube, N, B, shift, escale, s1_part, s2_part,
+                                         B * (B + 1) / 2, hdr);
   return cudaGetLastError();
 }
 
@@ -395,17 +413,19 @@ cudaError_t syrk_tc_typed(const In* cube, int64_t N, int B, float* shift, double
 
 bool syrk_tc_supported(int B) { return B >= 2 && B <= kMaxB; }
 
-cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
-                           double* s1_part, float* s2_part, int partials, DevHeader* hdr,
-                           cudaStream_t st) {
+cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, const float* shift,
+                           const int* escale, double* s1_part, float* s2_part, int partials,
+                           DevHeader* hdr, cudaStream_t st) {
   switch (dt) {
     case PCA_F32:
-      return syrk_tc_typed((const float*)cube, N, B, shift, s1_part, s2_part, partials, hdr, st);
-    case PCA_BF16:
-      return syrk_tc_typed((const __nv_bfloat16*)cube, N, B, shift, s1_part, s2_part, partials, hdr,
+      return syrk_tc_typed((const float*)cube, N, B, shift, escale, s1_part, s2_part, partials, hdr,
                            st);
+    case PCA_BF16:
+      return syrk_tc_typed((const __nv_bfloat16*)cube, N, B, shift, escale, s1_part, s2_part,
+                           partials, hdr, st);
     case PCA_F16:
-      return syrk_tc_typed((const __half*)cube, N, B, shift, s1_part, s2_part, partials, hdr, st);
+      return syrk_tc_typed((const __half*)cube, N, B, shift, escale, s1_part, s2_part, partials,
+                           hdr, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -98,3 +98,25 @@ def test_project_stage(gbpca_lib, dtype):
     for j in range(cube.k):
         err = np.abs(Qn[:, j] - ref["Q"][:, j]).max() / np.abs(ref["Q"][:, j]).max()
         assert err <= 1e-5, (j, err)
+
+
+@pytest.mark.gpu
+def test_mix_range_guard_recomputes_on_simt(gbpca_lib):
+    """MIX scales every band by a power of two taken from a pixel sample; a
+    value far outside the sampled spread leaves the FP16 range, which must
+    make the covariance be recomputed in FP32 (same result up to P32
+    accuracy), while an ordinary cube stays on the tensor-core form."""
+    g = gbpca_lib
+    cube = synth.linear_mixing(seed=21, rows=61, cols=67, bands=48, endmembers=5)
+    assert cube.N > 1024          # pixel 1 is then outside the strided sample
+    Y = cube.Y.copy()
+    _, _, info = g.covariance(torch.from_numpy(Y).cuda(), precision="mix")
+    assert info["status"] == 0 and info["cov_fallback"] == 0
+    Y[1, 7] = 5e6                 # the data lie in [0, 1]
+    mu, C, info = g.covariance(torch.from_numpy(Y).cuda(), precision="mix")
+    torch.cuda.synchronize()
+    assert info["status"] == 0 and info["cov_fallback"] == 1
+    mu_ref = oracle.band_means(Y)
+    C_ref = oracle.covariance(Y, mu_ref)
+    assert np.abs(mu.cpu().numpy() - mu_ref).max() / np.abs(mu_ref).max() <= MU_TOL["p32"]
+    assert np.abs(C.cpu().numpy() - C_ref).max() / np.abs(C_ref).max() <= COV_TOL["p32"]
