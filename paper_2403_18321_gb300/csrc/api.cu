@@ -2,6 +2,7 @@
 // layout and the launch sequence of the four PCA stages (Algorithm 1).
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 #include "common.cuh"
 
@@ -227,8 +228,6 @@ cudaError_t run_cov(const void* cube, pca_dtype dt, int64_t N, int B, pca_precis
   cudaError_t e;
   pm.mark(0);
   if (prec == PCA_PREC_MIX) {
-    e = launch_band_probe(cube, dt, N, B, P.shift, P.escale, st);
-    if (e != cudaSuccess) return e;
     e = launch_syrk_tc(cube, dt, N, B, P.shift, P.escale, P.s1p, (float*)P.s2p, L.partials, P.hdr,
                        st);
     if (e != cudaSuccess) return e;
@@ -260,14 +259,21 @@ cudaError_t run_eigh(const double* A, int B, float tol32, int sweeps_max, pca_pr
   pm.mark(5);
   const int iters = refine_iterations(prec);
   if (iters > 0 && (e = launch_to_df(A, P.cdf, B * B, st)) != cudaSuccess) return e;
-  for (int it = 0; it < iters; ++it)
-    if ((e = launch_refine(P.cdf, B, P.vc, P.lam, P.w, P.s, P.g, P.e, P.hdr,
-                           refine_max_angle(prec), st)) != cudaSuccess)
+  // V alternates between two buffers, so that no step copies it back
+  float2* v = P.vc;
+  float2* other = P.w;
+  for (int it = 0; it < iters; ++it) {
+    if ((e = launch_refine(P.cdf, B, v, other, P.lam, P.s, P.g, P.e, P.hdr, refine_max_angle(prec),
+                           st)) != cudaSuccess)
       return e;
-  for (int it = 0; it < ortho_steps(prec); ++it)
-    if ((e = launch_orthonormalize(P.vc, B, P.w, P.g, P.e, st)) != cudaSuccess) return e;
+    std::swap(v, other);
+  }
+  for (int it = 0; it < ortho_steps(prec); ++it) {
+    if ((e = launch_orthonormalize(v, other, B, P.g, P.e, st)) != cudaSuccess) return e;
+    std::swap(v, other);
+  }
   pm.mark(6);
-  return launch_sort_sign(P.lam, P.vc, B, k, eigvals, eigvecs, P.vk, P.rank, P.sgn, st);
+  return launch_sort_sign(P.lam, v, B, k, eigvals, eigvecs, P.vk, P.rank, P.sgn, st);
 }
 
 }  // namespace
@@ -293,7 +299,7 @@ int pca_fit(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol,
   GB_CK(run_eigh(P.C, B, tol32, sweeps_max, prec, k, P, eigvals, eigvecs, st, pm));
   // stages 5-6: projection onto the first k eigenvectors
   pm.mark(7);
-  if (proj) GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st));
+  if (proj) GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st, P.hdr));
   pm.mark(8);
   if (info) return pca_read_info(workspace, stream, info);
   return PCA_OK;
@@ -348,7 +354,7 @@ int pca_project(const void* cube, pca_dtype dt, int64_t N, int B, int k, const d
   const Ptrs P = carve(workspace, L);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GB_CK(launch_narrow_inputs(mu, eigvecs, B, k, P.muf, P.vk, st));
-  GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st));
+  GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st, P.hdr));
   return PCA_OK;
 }
 
@@ -368,13 +374,14 @@ const char* pca_status_string(int status) {
 int pca_version(void) { return 100; }
 
 int pca_kernel_launches(pca_precision prec, int with_projection) {
-  // header init, covariance (MIX: band probe + tensor-core pass + guarded
-  // SIMT re-computation), band-sum reduce, covariance finalise, Jacobi (with
-  // V), compact, 4 per refinement iteration, 1 conversion, 3 per
-  // orthogonalisation step, rank/sign + scatter, projection
+  // header init, covariance (MIX: tensor-core pass + guarded SIMT
+  // re-computation), band-sum reduce, covariance finalise, Jacobi (with
+  // V), compact, 5 per refinement iteration (four products and the angle
+  // kernel), 1 conversion, 3 per orthogonalisation step, rank/sign +
+  // scatter, projection
   const int it = refine_iterations(prec);
-  const int cov = prec == PCA_PREC_MIX ? 3 : 1;
-  return 5 + cov + 4 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
+  const int cov = prec == PCA_PREC_MIX ? 2 : 1;
+  return 5 + cov + 5 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
 }
 
 int pca_jacobi_sms(int B) {

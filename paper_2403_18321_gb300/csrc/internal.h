@@ -45,8 +45,12 @@ struct Layout {
 Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, int num_sms);
 
 __host__ __device__ inline int round_even(int b) { return b + (b & 1); }
+// Packed upper triangle, column by column: entry (i, j), i <= j, of a B x B
+// symmetric matrix at j(j+1)/2 + i, so that the rows of one column -- the
+// TMEM lanes of the tensor-core epilogue -- are contiguous.
 __host__ __device__ inline int64_t packed_index(int i, int j, int B) {  // i <= j
-  return (int64_t)i * B - (int64_t)i * (i - 1) / 2 + (j - i);
+  (void)B;
+  return (int64_t)j * (j + 1) / 2 + i;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -60,17 +64,14 @@ cudaError_t launch_syrk_simt(const void* cube, pca_dtype dt, int64_t N, int B, b
                              float* shift, double* s1_part, void* s2_part, int partials,
                              cudaStream_t st, const int* guard = nullptr, int* escale = nullptr);
 
-// Per-band shift (mean of a strided pixel sample) and power-of-two scale
-// exponent for the tensor-core covariance: shift [B] (FP32), escale [B] (int).
-cudaError_t launch_band_probe(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
-                              int* escale, cudaStream_t st);
-
 // Covariance partials on the tensor cores (tcgen05, split-FP16 of the scaled,
-// shifted values, three products).  Reads shift/escale from launch_band_probe;
-// S1 partials are unscaled, S2 partials stay scaled by 2^(e_i + e_j).  A value
+// shifted values, three products).  Every CTA derives the per-band shift
+// (mean of 32 sampled pixels) and power-of-two scale exponent from the same
+// pixels; CTA 0 writes them to shift [B] (FP32) and escale [B] (int).  S1
+// partials are unscaled, S2 partials stay scaled by 2^(e_i + e_j).  A value
 // outside the FP16 range after scaling sets hdr->cov_range.
-cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, const float* shift,
-                           const int* escale, double* s1_part, float* s2_part, int partials,
+cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
+                           int* escale, double* s1_part, float* s2_part, int partials,
                            DevHeader* hdr, cudaStream_t st);
 bool syrk_tc_supported(int B);
 
@@ -108,15 +109,16 @@ cudaError_t launch_compact(const float* diag32, const float* v32, int B, DevHead
 // dst = src as double-float (hi, lo) pairs.
 cudaError_t launch_to_df(const double* src, float2* dst, int count, cudaStream_t st);
 
-// One Newton-type refinement iteration of the eigen-decomposition in FP64.
-// One refinement iteration (double-float products, FP64 angles); C, vc, w, s,
-// g, e are B x B double-float.  max_angle: pairs whose first-order angle
-// exceeds it are only re-orthogonalised.
-cudaError_t launch_refine(const float2* C, int B, float2* vc, double* lam, float2* w, float2* s,
-                          float2* g, float2* e, DevHeader* hdr, double max_angle, cudaStream_t st);
+// One refinement iteration (double-float products, FP64 angles) from V (v)
+// to V' (vout; also the scratch for C V); C, s, g, e are B x B double-float.
+// max_angle: pairs whose first-order angle exceeds it are only
+// re-orthogonalised.
+cudaError_t launch_refine(const float2* C, int B, const float2* v, float2* vout, double* lam,
+                          float2* s, float2* g, float2* e, DevHeader* hdr, double max_angle,
+                          cudaStream_t st);
 
-// One Newton-Schulz orthogonalisation step of V (double-float).
-cudaError_t launch_orthonormalize(float2* vc, int B, float2* w, float2* g, float2* e,
+// One Newton-Schulz orthogonalisation step of V (double-float), v -> vout.
+cudaError_t launch_orthonormalize(const float2* v, float2* vout, int B, float2* g, float2* e,
                                   cudaStream_t st);
 
 // Sort descending, sign-normalise, write eigvals/eigvecs (FP64) and V_k (FP32).
@@ -128,8 +130,10 @@ cudaError_t launch_sort_sign(const double* lam, const float2* vc, int B, int k, 
 cudaError_t launch_narrow_inputs(const double* mu, const double* eigvecs, int B, int k, float* mu_f,
                                  float* vk, cudaStream_t st);
 
-// Q = (Y - 1 mu^T) V_k, FP32.
+// Q = (Y - 1 mu^T) V_k, FP32 (TMA-streamed).  hdr (nullable) receives
+// PCA_ERR_TIMEOUT if a bounded wait gives up (the output range is then NaN).
 cudaError_t launch_project(const void* cube, pca_dtype dt, int64_t N, int B, int k,
-                           const float* mu_f, const float* vk, float* proj, cudaStream_t st);
+                           const float* mu_f, const float* vk, float* proj, cudaStream_t st,
+                           DevHeader* hdr = nullptr);
 
 }  // namespace gbpca

@@ -139,75 +139,6 @@ cudaError_t syrk_simt_typed(const In* cube, int64_t N, int B, bool fp64, float* 
   return cudaGetLastError();
 }
 
-// Band probe for the tensor-core form: over S = min(N, 1024) pixels spread
-// evenly through the cube, per band b
-//   shift_b = sample mean (FP32),
-//   escale_b = 6 - E with max_n |y_nb - shift_b| <= 2^E  (frexp),
-// so that the sampled deviations scale into (2^5, 2^6]; a scaled value leaves
-// the FP16 range (65504) only if it lies about a thousand times further from
-// the shift than every sampled one.  A degenerate sample falls back to
-// |shift_b|, then to scale 1.
-constexpr int kProbeSamples = 1024;
-constexpr int kProbeWarps = 32;
-constexpr int kProbeUnroll = 8;   // independent loads in flight per thread
-
-template <typename In>
-__global__ void __launch_bounds__(kProbeWarps * 32)
-k_band_probe(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shift,
-             int* __restrict__ escale) {
-  __shared__ double ssum[kProbeWarps][32];
-  __shared__ float smin[kProbeWarps][32], smax[kProbeWarps][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int b = blockIdx.x * 32 + lane;
-  const int S = (int)(N < kProbeSamples ? N : kProbeSamples);
-  double sum = 0.0;
-  float lo = INFINITY, hi = -INFINITY;
-  if (b < B) {
-    // warp w takes samples w, w + 32, ...; kProbeUnroll loads are issued
-    // before any of them is used
-    for (int i0 = warp; i0 < S; i0 += kProbeWarps * kProbeUnroll) {
-      float y[kProbeUnroll];
-#pragma unroll
-      for (int u = 0; u < kProbeUnroll; ++u) {
-        const int i = i0 + u * kProbeWarps;
-        y[u] = i < S ? ld(cube + ((int64_t)i * N / S) * B + b) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < kProbeUnroll; ++u) {
-        if (i0 + u * kProbeWarps < S) {
-          sum += (double)y[u];
-          lo = fminf(lo, y[u]);
-          hi = fmaxf(hi, y[u]);
-        }
-      }
-    }
-  }
-  ssum[warp][lane] = sum;
-  smin[warp][lane] = lo;
-  smax[warp][lane] = hi;
-  __syncthreads();
-  if (warp == 0 && b < B) {
-    for (int w = 1; w < kProbeWarps; ++w) {
-      sum += ssum[w][lane];
-      lo = fminf(lo, smin[w][lane]);
-      hi = fmaxf(hi, smax[w][lane]);
-    }
-    float m = (float)(sum / (double)S);
-    double dev = fmax((double)hi - (double)m, (double)m - (double)lo);
-    if (!isfinite(m) || !isfinite(dev)) { m = 0.f; dev = 0.0; }
-    if (!(dev > 0.0)) dev = fabs((double)m);
-    int e = 0;
-    if (dev > 0.0) {
-      int E;
-      frexp(dev, &E);
-      e = 6 - E;
-      e = e < -120 ? -120 : (e > 120 ? 120 : e);
-    }
-    shift[b] = m;
-    escale[b] = e;
-  }
-}
-
 // d[b] = (sum_g S1_g[b]) / N, one warp per band (FP64 adds spread over SMs).
 __global__ void k_s1_reduce(const double* __restrict__ s1_part, int partials, int B, int64_t N,
                             const float* __restrict__ shift, double* __restrict__ dvec,
@@ -227,37 +158,55 @@ __global__ void k_s1_reduce(const double* __restrict__ s1_part, int partials, in
   }
 }
 
-// C_ij = (S2_ij - N d_i d_j) / (N - 1), S2 summed over the partials.
-// FP32 partials are summed with Kahan compensation (FP32 operations only).
+// C_ij = (S2_ij - N d_i d_j) / (N - 1), S2 summed over the partials.  One
+// CTA per 32 consecutive packed entries: lane = entry (coalesced reads of
+// every partial), warp w adds the partials w, w + 8, ...  FP32 partials are
+// added as an unevaluated FP32 pair (hi, lo) with error-free TwoSum steps --
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU --
+// and the eight warp sums are added in FP64 in a fixed order.
+constexpr int kFinWarps = 8;
+
 template <typename Acc>
-__global__ void k_cov_finalize(const Acc* __restrict__ s2_part, int partials, int s2_elems,
-                               int B, int64_t N, const double* __restrict__ dvec,
-                               double* __restrict__ C, DevHeader* __restrict__ hdr,
-                               const int* __restrict__ escale) {
-  const int i = blockIdx.y;
-  const int j = i + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= B) return;
-  const int64_t e = packed_index(i, j, B);
-  double S2;
-  if constexpr (sizeof(Acc) == 4) {
-    float sum = 0.f, comp = 0.f;
-    for (int g = 0; g < partials; ++g) {
-      const float y = (float)s2_part[(size_t)g * s2_elems + e] - comp;
-      const float t = sum + y;
-      comp = (t - sum) - y;
-      sum = t;
+__global__ void __launch_bounds__(kFinWarps * 32)
+k_cov_finalize(const Acc* __restrict__ s2_part, int partials, int s2_elems, int B, int64_t N,
+               const double* __restrict__ dvec, double* __restrict__ C,
+               DevHeader* __restrict__ hdr, const int* __restrict__ escale) {
+  __shared__ double part[kFinWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  double sum = 0.0;
+  if (e < s2_elems) {
+    if constexpr (sizeof(Acc) == 4) {
+      float hi = 0.f, lo = 0.f;
+      for (int g = warp; g < partials; g += kFinWarps) {
+        const float v = (float)s2_part[(size_t)g * s2_elems + e];
+        const float s = __fadd_rn(hi, v);          // TwoSum(hi, v)
+        const float z = __fsub_rn(s, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(v, z)));
+        hi = s;
+      }
+      sum = (double)hi + (double)lo;
+    } else {
+      for (int g = warp; g < partials; g += kFinWarps) sum += (double)s2_part[(size_t)g * s2_elems + e];
     }
-    S2 = (double)sum - (double)comp;
-  } else {
-    double sum = 0.0;
-    for (int g = 0; g < partials; ++g) sum += (double)s2_part[(size_t)g * s2_elems + e];
-    S2 = sum;
   }
-  if (escale != nullptr) S2 = ldexp(S2, -(escale[i] + escale[j]));  // exact power of two
-  const double c = (S2 - (double)N * dvec[i] * dvec[j]) / (double)(N - 1);
-  C[(size_t)i * B + j] = c;
-  C[(size_t)j * B + i] = c;
-  if (!isfinite(c)) { atomicOr(&hdr->nonfinite, 1); set_status(hdr, PCA_ERR_NONFINITE); }
+  part[warp][lane] = sum;
+  __syncthreads();
+  if (warp == 0 && e < s2_elems) {
+    double S2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < kFinWarps; ++w) S2 += part[w][lane];
+    // (i, j) of packed entry e = j(j+1)/2 + i
+    int j = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while ((int64_t)(j + 1) * (j + 2) / 2 <= e) ++j;
+    while ((int64_t)j * (j + 1) / 2 > e) --j;
+    const int i = (int)(e - (int64_t)j * (j + 1) / 2);
+    if (escale != nullptr) S2 = ldexp(S2, -(escale[i] + escale[j]));  // exact power of two
+    const double c = (S2 - (double)N * dvec[i] * dvec[j]) / (double)(N - 1);
+    C[(size_t)i * B + j] = c;
+    C[(size_t)j * B + i] = c;
+    if (!isfinite(c)) { atomicOr(&hdr->nonfinite, 1); set_status(hdr, PCA_ERR_NONFINITE); }
+  }
 }
 
 }  // namespace
@@ -279,38 +228,19 @@ cudaError_t launch_syrk_simt(const void* cube, pca_dtype dt, int64_t N, int B, b
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_band_probe(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
-                              int* escale, cudaStream_t st) {
-  const dim3 grid((B + 31) / 32), block(kProbeWarps * 32);
-  switch (dt) {
-    case PCA_F32:
-      k_band_probe<<<grid, block, 0, st>>>((const float*)cube, N, B, shift, escale);
-      break;
-    case PCA_BF16:
-      k_band_probe<<<grid, block, 0, st>>>((const __nv_bfloat16*)cube, N, B, shift, escale);
-      break;
-    case PCA_F16:
-      k_band_probe<<<grid, block, 0, st>>>((const __half*)cube, N, B, shift, escale);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
 cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const void* s2_part,
                                 bool fp64_partials, int partials, int64_t N, int B, double* mu,
                                 double* C, float* mu_f, double* dvec, DevHeader* hdr,
                                 cudaStream_t st, const int* escale) {
   k_s1_reduce<<<B, 32, 0, st>>>(s1_part, partials, B, N, shift, dvec, mu, mu_f, hdr);
   const int s2_elems = B * (B + 1) / 2;
-  dim3 grid((B + 63) / 64, B);
+  const int grid = (s2_elems + 31) / 32;
   if (fp64_partials)
-    k_cov_finalize<double><<<grid, 64, 0, st>>>((const double*)s2_part, partials, s2_elems, B, N,
-                                                dvec, C, hdr, escale);
+    k_cov_finalize<double><<<grid, kFinWarps * 32, 0, st>>>((const double*)s2_part, partials,
+                                                            s2_elems, B, N, dvec, C, hdr, escale);
   else
-    k_cov_finalize<float><<<grid, 64, 0, st>>>((const float*)s2_part, partials, s2_elems, B, N,
-                                               dvec, C, hdr, escale);
+    k_cov_finalize<float><<<grid, kFinWarps * 32, 0, st>>>((const float*)s2_part, partials,
+                                                           s2_elems, B, N, dvec, C, hdr, escale);
   return cudaGetLastError();
 }
 

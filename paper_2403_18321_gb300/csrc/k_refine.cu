@@ -159,21 +159,27 @@ __global__ void k_refine_E(const float2* __restrict__ S, const float2* __restric
                            DevHeader* __restrict__ hdr, double inv_max_angle) {
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const double li = df_to_d(S[(size_t)i * n + i]) / df_to_d(G[(size_t)i * n + i]);
-  const double lj = df_to_d(S[(size_t)j * n + j]) / df_to_d(G[(size_t)j * n + j]);
-  const double rij = (i == j ? 1.0 : 0.0) - df_to_d(G[(size_t)i * n + j]);
-  const double sij = df_to_d(S[(size_t)i * n + j]);
-  const double num = sij + lj * rij;
-  const double gap = lj - li;
-  // classified the same way from (i, j) and (j, i), so that E_ij + E_ji = R_ij
-  const double size = fabs(sij) + fmax(fabs(li), fabs(lj)) * fabs(rij);
-  double e;
-  if (i != j && fabs(gap) > inv_max_angle * size) e = num / gap;
-  else e = 0.5 * rij;
-  E[(size_t)i * n + j] = d_to_df(e);
-  if (i == j) lam[i] = li;
-  atomic_max_pos(&hdr->refine_res, fabs(e));
+  double e = 0.0;
+  if (j < n) {
+    const double li = df_to_d(S[(size_t)i * n + i]) / df_to_d(G[(size_t)i * n + i]);
+    const double lj = df_to_d(S[(size_t)j * n + j]) / df_to_d(G[(size_t)j * n + j]);
+    const double rij = (i == j ? 1.0 : 0.0) - df_to_d(G[(size_t)i * n + j]);
+    const double sij = df_to_d(S[(size_t)i * n + j]);
+    const double num = sij + lj * rij;
+    const double gap = lj - li;
+    // classified the same way from (i, j) and (j, i), so that E_ij + E_ji = R_ij
+    const double size = fabs(sij) + fmax(fabs(li), fabs(lj)) * fabs(rij);
+    if (i != j && fabs(gap) > inv_max_angle * size) e = num / gap;
+    else e = 0.5 * rij;
+    E[(size_t)i * n + j] = d_to_df(e);
+    if (i == j) lam[i] = li;
+  }
+  // largest |E_ij|: one atomic per warp (one max over all B^2 entries on a
+  // single word would serialise)
+  double m = fabs(e);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_pos(&hdr->refine_res, m);
 }
 
 // E = (I - G) / 2: one Newton-Schulz step V <- V (3I - V^T V)/2 = V + V E.
@@ -199,24 +205,23 @@ cudaError_t launch_to_df(const double* src, float2* dst, int count, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_orthonormalize(float2* vc, int B, float2* w, float2* g, float2* e,
+cudaError_t launch_orthonormalize(const float2* v, float2* vout, int B, float2* g, float2* e,
                                   cudaStream_t st) {
-  dfgemm(true, vc, vc, nullptr, g, B, st);                       // G = V^T V
+  dfgemm(true, v, v, nullptr, g, B, st);                         // G = V^T V
   k_ns_E<<<dim3((B + 127) / 128, B), 128, 0, st>>>(g, B, e);
-  dfgemm(false, vc, e, vc, w, B, st);                            // V' = V E + V
-  cudaMemcpyAsync(vc, w, sizeof(float2) * (size_t)B * B, cudaMemcpyDeviceToDevice, st);
+  dfgemm(false, v, e, v, vout, B, st);                           // V' = V E + V
   return cudaGetLastError();
 }
 
-cudaError_t launch_refine(const float2* C, int B, float2* vc, double* lam, float2* w, float2* s,
-                          float2* g, float2* e, DevHeader* hdr, double max_angle, cudaStream_t st) {
-  dfgemm(false, C, vc, nullptr, w, B, st);    // W = C V
-  dfgemm(true, vc, w, nullptr, s, B, st);     // S = V^T W
-  dfgemm(true, vc, vc, nullptr, g, B, st);    // G = V^T V
+cudaError_t launch_refine(const float2* C, int B, const float2* v, float2* vout, double* lam,
+                          float2* s, float2* g, float2* e, DevHeader* hdr, double max_angle,
+                          cudaStream_t st) {
+  dfgemm(false, C, v, nullptr, vout, B, st);  // W = C V (in vout, free until the last product)
+  dfgemm(true, v, vout, nullptr, s, B, st);   // S = V^T W
+  dfgemm(true, v, v, nullptr, g, B, st);      // G = V^T V
   cudaMemsetAsync(&hdr->refine_res, 0, sizeof(double), st);
   k_refine_E<<<dim3((B + 127) / 128, B), 128, 0, st>>>(s, g, B, e, lam, hdr, 1.0 / max_angle);
-  dfgemm(false, vc, e, vc, w, B, st);         // V' = V E + V
-  cudaMemcpyAsync(vc, w, sizeof(float2) * (size_t)B * B, cudaMemcpyDeviceToDevice, st);
+  dfgemm(false, v, e, v, vout, B, st);        // V' = V E + V
   return cudaGetLastError();
 }
 

@@ -4,9 +4,11 @@
 //
 // One persistent CTA per SM walks a contiguous range of 32-pixel chunks:
 //   warp 0      TMA producer: cp.async.bulk of each chunk (pixel-major, a
-//               contiguous byte range of the cube) into a 4-stage FP32 ring;
-//   warps 2-17  converters: x = (y - s) 2^e per band (s = sample mean and e
-//               a power-of-two scale, both from the band probe), split into
+//               contiguous byte range of the cube) into a ring of as many
+//               stages (up to 12) as shared memory holds;
+//   warps 2-17  converters: x = (y - s) 2^e per band (s = the mean of 32
+//               pixels spread through the cube and e a power-of-two scale,
+//               both computed by every CTA from the same pixels), split into
 //               FP16 hi = fp16(x), lo = fp16(x - hi) -- 22 significant bits
 //               of x -- written transposed ([band][pixel], K-major core-
 //               matrix layout) into a 2-stage operand ring; one extra operand
@@ -24,14 +26,14 @@
 // finalised by k_cov.cu.  Every mbarrier wait is bounded (one second of
 // globaltimer); on time-out the CTA records PCA_ERR_TIMEOUT, drains its MMAs,
 // frees TMEM and returns.
-#include "common.cuh"
+#include "tma.cuh"
 
 namespace gbpca {
 
 namespace {
 
 constexpr int kKC = 32;                 // pixels per chunk (K of one stage)
-constexpr int kStages = 4;              // FP32 TMA ring depth
+constexpr int kMaxStages = 12;          // TMA ring depth: as many stages as shared memory holds
 constexpr int kOpStages = 2;            // FP16 operand ring depth
 constexpr int kRows = 256;              // operand rows (bands, padded; ones row included)
 constexpr int kConvWarps = 16;
@@ -39,12 +41,12 @@ constexpr int kThreads = (2 + kConvWarps) * 32;
 constexpr int kOpBytes = kRows * kKC * 2;        // one FP16 operand (hi or lo): 16 KB
 constexpr uint32_t kLBO = 128;                   // K-adjacent core matrices
 constexpr uint32_t kSBO = (kKC / 8) * 128;       // 8-row groups: 512 B
-constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s bound on every wait
 constexpr int kTmemCols = 512;
+constexpr int kProbe = 32;               // pixels of the band probe
 
 struct __align__(8) SyncBlock {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
   uint64_t opfull[kOpStages];
   uint64_t opempty[kOpStages];
   uint64_t done;
@@ -52,58 +54,6 @@ struct __align__(8) SyncBlock {
   int abort;
 };
 
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait; false on time-out or when another role already aborted.
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity, SyncBlock* sb) {
-  if (mbar_try(b, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  for (;;) {
-    if (mbar_try(b, parity)) return true;
-    if (*(volatile int*)&sb->abort) return false;
-    if (gtimer() - t0 > kWaitNs) {
-      atomicExch(&sb->abort, 1);
-      return false;
-    }
-  }
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          su32(dst)),
-      "l"(src), "r"(bytes), "r"(su32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -159,19 +109,28 @@ __device__ __forceinline__ void unpack_f16x2(uint32_t v, float& a, float& b) {
 template <typename In>
 __device__ __forceinline__ float elem(const In* p) { return to_f32<In>(*p); }
 
+// barrier among the converter warps only (the producer and MMA warps are busy)
+__device__ __forceinline__ void conv_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory");
+}
+
 template <typename In>
 __global__ void __launch_bounds__(kThreads, 1)
-k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict__ shift,
-          const int* __restrict__ escale, double* __restrict__ s1_part,
-          float* __restrict__ s2_part, int s2_elems, DevHeader* __restrict__ hdr) {
+k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shift_out,
+          int* __restrict__ escale_out, double* __restrict__ s1_part,
+          float* __restrict__ s2_part, int s2_elems, DevHeader* __restrict__ hdr, int S) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int R16 = (B + 15) & ~15;     // first row after the padded bands = the ones row
   const int stage_bytes_max = kKC * B * (int)sizeof(In);
   const int stage_stride = (stage_bytes_max + 127) & ~127;
   unsigned char* ops = smem;                                        // [kOpStages][hi|lo][kOpBytes]
-  unsigned char* stages = smem + kOpStages * 2 * kOpBytes;          // [kStages][stage_stride]
-  float* shs = reinterpret_cast<float*>(stages + kStages * stage_stride);  // [kRows]
-  SyncBlock* sb = reinterpret_cast<SyncBlock*>(shs + kRows);
+  unsigned char* stages = smem + kOpStages * 2 * kOpBytes;          // [S][stage_stride]
+  float* shs = reinterpret_cast<float*>(stages + S * stage_stride);        // [kRows] shift
+  int* sesc = reinterpret_cast<int*>(shs + kRows);                         // [kRows] exponent
+  double* psum = reinterpret_cast<double*>(sesc + kRows);                  // [2][kRows]
+  float* pmin = reinterpret_cast<float*>(psum + 2 * kRows);                // [2][kRows]
+  float* pmax = pmin + 2 * kRows;                                          // [2][kRows]
+  SyncBlock* sb = reinterpret_cast<SyncBlock*>(pmax + 2 * kRows);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x, g = blockIdx.x;
@@ -186,9 +145,8 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict
   // ---- set-up
   for (int i = tid; i < kOpStages * 2 * kOpBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(ops)[i] = make_uint4(0, 0, 0, 0);
-  for (int b = tid; b < kRows; b += kThreads) shs[b] = b < B ? shift[b] : 0.f;
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) { mbar_init(&sb->full[s], 1); mbar_init(&sb->empty[s], kConvWarps); }
+    for (int s = 0; s < S; ++s) { mbar_init(&sb->full[s], 1); mbar_init(&sb->empty[s], kConvWarps); }
     for (int s = 0; s < kOpStages; ++s) { mbar_init(&sb->opfull[s], kConvWarps); mbar_init(&sb->opempty[s], 1); }
     mbar_init(&sb->done, 1);
     sb->abort = 0;
@@ -212,8 +170,8 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict
     // ---------------------------------------------------------- TMA producer
     if (lane == 0) {
       for (int c = 0; c < nch; ++c) {
-        const int s = c % kStages;
-        if (!mbar_wait(&sb->empty[s], ((c / kStages) & 1) ^ 1, sb)) break;
+        const int s = c % S;
+        if (!mbar_wait(&sb->empty[s], ((c / S) & 1) ^ 1, &sb->abort)) break;
         const int64_t p0 = (c_begin + c) * kKC;
         const int cp = (int)((N - p0) < kKC ? (N - p0) : kKC);
         const uint32_t bytes = (uint32_t)(cp * B * (int)sizeof(In)) & ~15u;
@@ -229,7 +187,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict
       bool issued = false;
       for (int c = 0; c < nch; ++c) {
         const int o = c % kOpStages;
-        if (!mbar_wait(&sb->opfull[o], (c / kOpStages) & 1, sb)) break;
+        if (!mbar_wait(&sb->opfull[o], (c / kOpStages) & 1, &sb->abort)) break;
         tc_fence_after();
         const uint32_t hi = ops_base + (uint32_t)(o * 2) * kOpBytes;
         const uint32_t lo = hi + kOpBytes;
@@ -260,6 +218,62 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict
     // Item = (band or ones row, 8-pixel group); a thread owns the same items in
     // every chunk (at most two for B <= 232), so their decode happens once.
     const int ct = tid - 64;
+    // Band probe (every CTA computes the same values from the same pixels):
+    // over S = min(N, 32) pixels spread evenly through the cube, per band b
+    //   shift_b = sample mean,  escale_b = 6 - E with max |y - shift_b| <= 2^E,
+    // so that the sampled deviations scale into (2^5, 2^6] and a scaled value
+    // leaves the FP16 range (65504) only if it lies about a thousand times
+    // further from the shift than every sampled one.  A degenerate sample
+    // falls back to |shift_b|, then to scale 1.
+    {
+      const int S = (int)(N < kProbe ? N : kProbe);
+      const int b = ct % kRows, half = ct / kRows;     // 512 threads: two halves of the sample
+      double sum = 0.0;
+      float lo = INFINITY, hi = -INFINITY;
+      if (b < B) {
+        float y[kProbe / 2];
+#pragma unroll
+        for (int u = 0; u < kProbe / 2; ++u) {
+          const int i = half + 2 * u;
+          y[u] = i < S ? elem(cube + ((int64_t)i * N / S) * B + b) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kProbe / 2; ++u) {
+          if (half + 2 * u < S) {
+            sum += (double)y[u];
+            lo = fminf(lo, y[u]);
+            hi = fmaxf(hi, y[u]);
+          }
+        }
+      }
+      psum[half * kRows + b] = sum;
+      pmin[half * kRows + b] = lo;
+      pmax[half * kRows + b] = hi;
+      conv_sync();
+      if (ct < kRows) {
+        float m = 0.f;
+        int e = 0;
+        if (b < B) {
+          const double tot = psum[b] + psum[kRows + b];
+          lo = fminf(pmin[b], pmin[kRows + b]);
+          hi = fmaxf(pmax[b], pmax[kRows + b]);
+          m = (float)(tot / (double)S);
+          double dev = fmax((double)hi - (double)m, (double)m - (double)lo);
+          if (!isfinite(m) || !isfinite(dev)) { m = 0.f; dev = 0.0; }
+          if (!(dev > 0.0)) dev = fabs((double)m);
+          if (dev > 0.0) {
+            int E;
+            frexp(dev, &E);
+            e = 6 - E;
+            e = e < -120 ? -120 : (e > 120 ? 120 : e);
+          }
+          if (g == 0) { shift_out[b] = m; escale_out[b] = e; }
+        }
+        shs[b] = m;
+        sesc[b] = e;
+      }
+      conv_sync();
+    }
     const int items = (B + 1) * (kKC / 8);
     int ib[2], ipg[2], ioff[2];
     float ish[2], isc[2];
@@ -271,16 +285,16 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict
       const int row = ib[u] < B ? ib[u] : R16;
       ioff[u] = (row >> 3) * (int)kSBO + (ipg[u] < 0 ? 0 : ipg[u]) * 128 + (row & 7) * 16;
       ish[u] = ib[u] < B ? shs[ib[u]] : 0.f;
-      isc[u] = ib[u] < B ? ldexpf(1.f, escale[ib[u]]) : 1.f;
+      isc[u] = ib[u] < B ? ldexpf(1.f, sesc[ib[u]]) : 1.f;
     }
     for (int c = 0; c < nch; ++c) {
-      const int s = c % kStages, o = c % kOpStages;
+      const int s = c % S, o = c % kOpStages;
       // one lane per warp polls the barriers (the others would only add
       // shared-memory traffic), then the warp proceeds together
       int ok = 1;
       if (lane == 0) {
-        ok = mbar_wait(&sb->full[s], (c / kStages) & 1, sb) ? 1 : 0;
-        if (ok) ok = mbar_wait(&sb->opempty[o], ((c / kOpStages) & 1) ^ 1, sb) ? 1 : 0;
+        ok = mbar_wait(&sb->full[s], (c / S) & 1, &sb->abort) ? 1 : 0;
+        if (ok) ok = mbar_wait(&sb->opempty[o], ((c / kOpStages) & 1) ^ 1, &sb->abort) ? 1 : 0;
       }
       ok = __shfl_sync(kFull, ok, 0);
       if (!ok) break;
@@ -342,7 +356,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict
     // ---------------------------------------------------------- epilogue
     if (warp >= 2 && warp < 6) {
       int okw = 0;
-      if (lane == 0) okw = (mbar_wait(&sb->done, 0, sb) && !*(volatile int*)&sb->abort) ? 1 : 0;
+      if (lane == 0) okw = (mbar_wait(&sb->done, 0, &sb->abort) && !*(volatile int*)&sb->abort) ? 1 : 0;
       const bool ok = __shfl_sync(kFull, okw, 0) != 0;
       tc_fence_after();
       const int q = warp & 3;          // TMEM lane quarter this warp may read
@@ -360,7 +374,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict
           const int j = j0 + i;
           if (r < B && r < 128) {
             if (j < B && j >= r) out[packed_index(r, j, B)] = v[i];
-            if (j == R16) s1_part[(size_t)g * B + r] = ldexp((double)v[i], -escale[r]);
+            if (j == R16) s1_part[(size_t)g * B + r] = ldexp((double)v[i], -sesc[r]);
           }
         }
       }
@@ -376,7 +390,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict
             const int jb = 128 + j0 + i;
             if (band < B) {
               if (jb < B && jb >= band) out[packed_index(band, jb, B)] = v[i];
-              if (jb == R16) s1_part[(size_t)g * B + band] = ldexp((double)v[i], -escale[band]);
+              if (jb == R16) s1_part[(size_t)g * B + band] = ldexp((double)v[i], -sesc[band]);
             }
           }
         }
@@ -395,17 +409,22 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, const float* __restrict
 }
 
 template <typename In>
-cudaError_t syrk_tc_typed(const In* cube, int64_t N, int B, const float* shift, const int* escale,
+cudaError_t syrk_tc_typed(const In* cube, int64_t N, int B, float* shift, int* escale,
                           double* s1_part, float* s2_part, int partials, DevHeader* hdr,
                           cudaStream_t st) {
   const int stage_stride = ((kKC * B * (int)sizeof(In)) + 127) & ~127;
-  const size_t smem = 1024 + (size_t)kOpStages * 2 * kOpBytes + (size_t)kStages * stage_stride +
-                      kRows * sizeof(float) + sizeof(SyncBlock);
+  const size_t fixed = 1024 + (size_t)kOpStages * 2 * kOpBytes +
+                       kRows * (sizeof(float) + sizeof(int)) +
+                       2 * kRows * (sizeof(double) + 2 * sizeof(float)) + sizeof(SyncBlock);
+  int S = (int)((227 * 1024 - fixed) / stage_stride);
+  S = S > kMaxStages ? kMaxStages : S;
+  if (S < 2) return cudaErrorInvalidValue;
+  const size_t smem = fixed + (size_t)S * stage_stride;
   auto kern = k_syrk_tc<In>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<partials, kThreads, smem, st>>>(cube, N, B, shift, escale, s1_part, s2_part,
-                                         B * (B + 1) / 2, hdr);
+                                         B * (B + 1) / 2, hdr, S);
   return cudaGetLastError();
 }
 
@@ -413,8 +432,8 @@ cudaError_t syrk_tc_typed(const In* cube, int64_t N, int B, const float* shift, 
 
 bool syrk_tc_supported(int B) { return B >= 2 && B <= kMaxB; }
 
-cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, const float* shift,
-                           const int* escale, double* s1_part, float* s2_part, int partials,
+cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
+                           int* escale, double* s1_part, float* s2_part, int partials,
                            DevHeader* hdr, cudaStream_t st) {
   switch (dt) {
     case PCA_F32:

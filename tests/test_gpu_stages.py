@@ -87,9 +87,14 @@ def test_eigh_sort_ties_and_diagonal_input(gbpca_lib):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
-def test_project_stage(gbpca_lib, dtype):
+@pytest.mark.parametrize("bands", [96, 103, 102, 232])
+def test_project_stage(gbpca_lib, dtype, bands):
+    """Both load paths of the streamed projection: rows that are a whole number
+    of 16-byte units go through the swizzled 2-D tensor map (96, 232 bands in
+    FP32; 96, 232 in 16-bit), the others through one contiguous copy per
+    chunk; 45 x 47 pixels leave a ragged last chunk."""
     g = gbpca_lib
-    cube = synth.linear_mixing(seed=11, rows=45, cols=47, bands=96, endmembers=6, k=6)
+    cube = synth.linear_mixing(seed=11, rows=45, cols=47, bands=bands, endmembers=6, k=6)
     Yt = torch.from_numpy(cube.Y).to(dtype)
     ref = oracle.pca_fit(Yt, cube.k, tol=1e-14)
     Q = g.project(Yt.cuda(), torch.from_numpy(ref["mu"]).cuda(), torch.from_numpy(ref["V"]).cuda(),
