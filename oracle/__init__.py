@@ -63,6 +63,7 @@ def _bind(lib):
     lib.oracle_sort_sign.argtypes = [i, P, P]
     lib.oracle_project.argtypes = [P, l, i, P, P, i, P]
     lib.oracle_pca_fit.argtypes = [P, l, i, i, d, i, i, P, P, P, P, P, P, P]
+    lib.oracle_backward.argtypes = [P, l, i, i, P, P, P, P, P, d, P]
     return lib
 
 
@@ -207,3 +208,18 @@ def pca_fit(Y, k, tol=1e-14, sweeps_max=60, ordering=ROW_CYCLIC, project_q=True)
     _check(st, (OK, ERR_NOCONV))
     return dict(mu=mu, lam=lam, V=V, Q=Q, status=st, sweeps=sw.value, off_rel=off.value,
                 rotations=nrot.value)
+
+
+def backward(Y, k, mu, lam, V, dQ, dlam=None, gap_eps=1e-6) -> np.ndarray:
+    """dL/dY of the projection layer Q = (Y - 1 mu^T) V_k (and of lam when dlam is
+    given) from the forward results; see oracle_backward in pca_oracle.c."""
+    Y = as_f64(Y)
+    N, B = Y.shape
+    mu, lam, V, dQ = as_f64(mu), as_f64(lam), as_f64(V), as_f64(dQ)
+    if dQ.shape != (N, k):
+        raise ValueError("dQ must be [N, k]")
+    dl = as_f64(dlam) if dlam is not None else None
+    dY = np.empty((N, B))
+    _check(_load().oracle_backward(_p(Y), N, B, int(k), _p(mu), _p(lam), _p(V), _p(dQ),
+                                   _p(dl) if dl is not None else None, float(gap_eps), _p(dY)))
+    return dY

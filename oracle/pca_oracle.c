@@ -360,3 +360,93 @@ int oracle_pca_fit(const double *Y, long N, int B, int k, double tol, int sweeps
   }
   return js;
 }
+
+/*
+ * Adjoint of the whole path (not in the paper; the backward pass of the PCA
+ * projection layer, written from first-order perturbation theory of the
+ * symmetric eigenproblem).  Given the forward results mu [B], lam [B]
+ * (descending), V [B][B] (column j = eigenvector j) of the cube Y [N][B], the
+ * upstream gradient dQ [N][k] of Q = X V_k and, optionally, dlam [B] (NULL =
+ * zero), it forms, step by step:
+ *   X        = Y - 1 mu^T
+ *   dVk      = X^T dQ                                   (B x k)
+ *   M        = V^T [dVk, 0]                             (B x B, columns >= k zero)
+ *   G_ij     = M_ij / (lam_j - lam_i)  for i != j with |lam_j - lam_i| > gap_eps |lam_1|,
+ *              0 for the other off-diagonal entries,  G_ii = dlam_i
+ *   dA       = V G V^T,   S = (dA + dA^T) / 2
+ *   dY       = (dQ - 1 mean_n(dQ)) V_k^T + 2/(N-1) X S
+ * (C = X^T X/(N-1) gives dX = 2 X S/(N-1); the centring maps dX to
+ * dX - 1 mean_n(dX), and 1^T X = 0 leaves the second term unchanged.)
+ */
+int oracle_backward(const double *Y, long N, int B, int k, const double *mu,
+                    const double *lam, const double *V, const double *dQ, const double *dlam,
+                    double gap_eps, double *dY) {
+  if (N < 2 || B < 1 || k < 1 || k > B) return ORC_ERR_ARG;
+  const size_t BB = (size_t)B * B;
+  double *dVk = (double *)calloc((size_t)B * k, sizeof(double));
+  double *M = (double *)calloc(BB, sizeof(double));
+  double *G = (double *)calloc(BB, sizeof(double));
+  double *T = (double *)calloc(BB, sizeof(double));
+  double *S = (double *)calloc(BB, sizeof(double));
+  double *mdq = (double *)calloc((size_t)k, sizeof(double));
+  if (!dVk || !M || !G || !T || !S || !mdq) {
+    free(dVk); free(M); free(G); free(T); free(S); free(mdq);
+    return ORC_ERR_ARG;
+  }
+  /* dVk = X^T dQ and the column means of dQ */
+  for (long n = 0; n < N; ++n)
+    for (int b = 0; b < B; ++b) {
+      const double x = Y[n * B + b] - mu[b];
+      for (int j = 0; j < k; ++j) dVk[(size_t)b * k + j] += x * dQ[n * k + j];
+    }
+  for (long n = 0; n < N; ++n)
+    for (int j = 0; j < k; ++j) mdq[j] += dQ[n * k + j];
+  for (int j = 0; j < k; ++j) mdq[j] /= (double)N;
+  /* M = V^T [dVk, 0] */
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      for (int b = 0; b < B; ++b) s += V[(size_t)b * B + i] * dVk[(size_t)b * k + j];
+      M[(size_t)i * B + j] = s;
+    }
+  /* G = F o M + diag(dlam) */
+  const double big = fabs(lam[0]);
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j) {
+      if (i == j) {
+        G[(size_t)i * B + j] = dlam ? dlam[i] : 0.0;
+      } else {
+        const double gap = lam[j] - lam[i];
+        G[(size_t)i * B + j] = fabs(gap) > gap_eps * big ? M[(size_t)i * B + j] / gap : 0.0;
+      }
+    }
+  /* dA = V G V^T (T = V G first), S = (dA + dA^T)/2 */
+  for (int a = 0; a < B; ++a)
+    for (int j = 0; j < B; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < B; ++i) s += V[(size_t)a * B + i] * G[(size_t)i * B + j];
+      T[(size_t)a * B + j] = s;
+    }
+  for (int a = 0; a < B; ++a)
+    for (int c = 0; c < B; ++c) {
+      double s = 0.0;
+      for (int j = 0; j < B; ++j) s += T[(size_t)a * B + j] * V[(size_t)c * B + j];
+      S[(size_t)a * B + c] += 0.5 * s;
+      S[(size_t)c * B + a] += 0.5 * s;
+    }
+  /* dY */
+  const double f = 2.0 / (double)(N - 1);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
+  for (long n = 0; n < N; ++n)
+    for (int c = 0; c < B; ++c) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += (dQ[n * k + j] - mdq[j]) * V[(size_t)c * B + j];
+      double t = 0.0;
+      for (int b = 0; b < B; ++b) t += (Y[n * B + b] - mu[b]) * S[(size_t)b * B + c];
+      dY[n * B + c] = s + f * t;
+    }
+  free(dVk); free(M); free(G); free(T); free(S); free(mdq);
+  return ORC_OK;
+}

@@ -367,7 +367,77 @@ MUTANTS = {
                          "s += (Y[n * B + b] - mu[b]) * V[(size_t)j * B + b];"),
     "stop rule absolute": ("if (fro == 0.0 || off <= tol * fro)",
                            "if (fro == 0.0 || off <= tol)"),
+    "adjoint gap sign": ("M[(size_t)i * B + j] / gap : 0.0;", "M[(size_t)i * B + j] / -gap : 0.0;"),
+    "adjoint dQ not centred": ("s += (dQ[n * k + j] - mdq[j]) * V[(size_t)c * B + j];",
+                               "s += dQ[n * k + j] * V[(size_t)c * B + j];"),
+    "adjoint covariance factor": ("const double f = 2.0 / (double)(N - 1);",
+                                  "const double f = 1.0 / (double)(N - 1);"),
+    "adjoint M transposed": ("s += V[(size_t)b * B + i] * dVk[(size_t)b * k + j];",
+                             "s += V[(size_t)i * B + b] * dVk[(size_t)b * k + j];"),
 }
+
+
+# ---------------------------------------------------------------- adjoint of the path
+
+def _adjoint_case(seed=5):
+    import synth
+    c = synth.gradient_cube(seed=seed, side=16, bands=24, comps=7, k=5)
+    rng = np.random.default_rng(seed + 100)
+    dQ = rng.standard_normal((c.N, c.k))
+    dl = rng.standard_normal(c.B)
+    return c.Y.astype(np.float64), c.k, dQ, dl
+
+
+def _loss(Y, k, dQ, dl):
+    r = oracle.pca_fit(Y, k, tol=1e-14)
+    return float(np.sum(dQ * r["Q"]) + np.dot(dl, r["lam"]))
+
+
+def test_adjoint_matches_central_differences():
+    """dL/dY of L = <dQ, Q(Y)> + <dlam, lam(Y)> against central finite
+    differences (h = 1e-6, FP64) on sampled entries and random directions of a
+    planted cube whose top k+2 eigenvalues are 10% apart."""
+    Y, k, dQ, dl = _adjoint_case()
+    r = oracle.pca_fit(Y, k, tol=1e-14)
+    adj = oracle.backward(Y, k, r["mu"], r["lam"], r["V"], dQ, dl, gap_eps=1e-9)
+    scale = np.abs(adj).max()
+    h = 1e-6
+    rng = np.random.default_rng(7)
+    N, B = Y.shape
+    for _ in range(12):
+        n, b = int(rng.integers(N)), int(rng.integers(B))
+        Yp, Ym = Y.copy(), Y.copy()
+        Yp[n, b] += h
+        Ym[n, b] -= h
+        fd = (_loss(Yp, k, dQ, dl) - _loss(Ym, k, dQ, dl)) / (2 * h)
+        assert abs(fd - adj[n, b]) <= 2e-6 * scale, (n, b, fd, adj[n, b])
+    for _ in range(2):
+        D = rng.standard_normal(Y.shape)
+        fd = (_loss(Y + h * D, k, dQ, dl) - _loss(Y - h * D, k, dQ, dl)) / (2 * h)
+        # error bound on the scale of |<adj, D>| <= ||adj|| ||D|| (Cauchy-Schwarz)
+        assert abs(fd - np.sum(adj * D)) <= 1e-6 * np.linalg.norm(adj) * np.linalg.norm(D), fd
+
+
+def test_adjoint_special_cases():
+    """dQ = 0 and dlam = e_i: dlam_i/dY = 2/(N-1) X v_i v_i^T (the derivative of
+    a simple eigenvalue of C = X^T X/(N-1)); all-zero gradients give zero."""
+    Y, k, dQ, dl = _adjoint_case(6)
+    r = oracle.pca_fit(Y, k, tol=1e-14)
+    N, B = Y.shape
+    X = Y - r["mu"][None, :]
+    for i in (0, 3):
+        e = np.zeros(B)
+        e[i] = 1.0
+        adj = oracle.backward(Y, k, r["mu"], r["lam"], r["V"], np.zeros((N, k)), e)
+        v = r["V"][:, i]
+        expect = 2.0 / (N - 1) * np.outer(X @ v, v)
+        assert np.abs(adj - expect).max() <= 1e-12 * np.abs(expect).max()
+    z = oracle.backward(Y, k, r["mu"], r["lam"], r["V"], np.zeros((N, k)))
+    assert np.all(z == 0.0)
+    # a gradient of Q only: the centring makes every column of dY sum to what
+    # X S contributes, and the V_k^T term has zero column sums
+    adj = oracle.backward(Y, k, r["mu"], r["lam"], r["V"], dQ)
+    assert np.abs(adj.sum(axis=0)).max() <= 1e-10 * np.abs(adj).max() * N
 
 
 def _pins_pass() -> bool:
@@ -386,6 +456,8 @@ def _pins_pass() -> bool:
         test_covariance_and_eigs_vs_lapack(500, 7)
         test_rank_one_cube()
         test_stop_rule_is_relative_to_the_norm()
+        test_adjoint_special_cases()
+        test_adjoint_matches_central_differences()
     except (AssertionError, oracle.OracleError):
         return False
     return True
