@@ -176,8 +176,39 @@ int pca_project_noalloc(const void *cube, pca_dtype dtype, int64_t N, int B, int
                         const double *mu, const double *eigvecs, float *proj, void *stream);
 
 /*
+ * pca_backward -- adjoint of the projection layer Q = (Y - 1 mu^T) V_k and,
+ * optionally, of the eigenvalues (no counterpart in the paper: the backward
+ * pass that makes the PCA usable as a differentiable layer).  With the
+ * forward results of the same cube it computes, from first-order
+ * perturbation theory of the symmetric eigenproblem,
+ *     dV_k = X^T dproj,
+ *     G    = F o (V^T [dV_k, 0]) + diag(deigvals),
+ *            F_ij = 1/(lam_j - lam_i) for i != j with
+ *            |lam_j - lam_i| > gap_eps |lam_1|, else 0 (degenerate gaps),
+ *     S    = (V G V^T + (V G V^T)^T) / 2,
+ *     dcube = (dproj - 1 mean_n dproj) V_k^T + 2/(N-1) X S.
+ * cube, dtype, N, B, k  as in pca_fit.
+ * mu [B], eigvals [B] (descending), eigvecs [B][B] (column j = vector j):
+ *            the forward outputs, FP64, device.
+ * dproj      [N][k] FP32 device, 16-byte aligned: gradient of proj.
+ * deigvals   [B] FP64 device, or NULL: gradient of eigvals.
+ * gap_eps    >= 0, finite.
+ * dcube      [N][B] FP32 device out: gradient of the cube.
+ * workspace  pca_backward_workspace_size(N, B, k) bytes, 256-byte aligned.
+ * info       as in pca_fit (sweeps and refinement fields are 0).
+ * Arithmetic: the pass over the cube accumulates in FP32 per CTA and adds the
+ * partials in FP64; the B x B algebra is FP64; dcube is formed in FP32.
+ */
+size_t pca_backward_workspace_size(int64_t N, int B, int k);
+int pca_backward(const void *cube, pca_dtype dtype, int64_t N, int B, int k, const double *mu,
+                 const double *eigvals, const double *eigvecs, const float *dproj,
+                 const double *deigvals, double gap_eps, float *dcube, void *workspace,
+                 size_t ws_bytes, void *stream, pca_info *info);
+
+/*
  * Waits for `stream` and copies the device-side outcome of the last
- * pca_fit that used `workspace` into *info.  Returns info->status.
+ * pca_fit (or pca_backward) that used `workspace` into *info.  Returns
+ * info->status.
  */
 int pca_read_info(const void *workspace, void *stream, pca_info *info);
 

@@ -29,7 +29,7 @@ STATUS = {0: "PCA_OK", 1: "PCA_ERR_ARG", 2: "PCA_ERR_NOCONV", 3: "PCA_ERR_NONFIN
 EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_project",
            "pca_read_info", "pca_status_string", "pca_version",
            "pca_kernel_launches", "pca_profile", "pca_profile_collect", "pca_project_noalloc",
-           "pca_jacobi_sms")
+           "pca_jacobi_sms", "pca_backward", "pca_backward_workspace_size")
 STAGES = ("covariance", "cov_finalize", "jacobi", "v_replay", "compact", "refine", "sort_sign",
           "project")
 
@@ -76,6 +76,11 @@ def load(build_if_missing: bool = False):
     lib.pca_project.restype = i
     lib.pca_project_noalloc.argtypes = [P, i, i64, i, i, P, P, P, P]
     lib.pca_project_noalloc.restype = i
+    lib.pca_backward_workspace_size.argtypes = [i64, i, i]
+    lib.pca_backward_workspace_size.restype = sz
+    lib.pca_backward.argtypes = [P, i, i64, i, i, P, P, P, P, P, d, P, P, sz, P,
+                                 ctypes.POINTER(Info)]
+    lib.pca_backward.restype = i
     lib.pca_read_info.argtypes = [P, P, ctypes.POINTER(Info)]
     lib.pca_read_info.restype = i
     lib.pca_status_string.argtypes = [i]
@@ -281,3 +286,73 @@ def fit_host(cube_host, k: int, tol: float = 1e-10, sweeps_max: int = 30, precis
     outs = [t.to("cpu", non_blocking=True) for t in (mu, ev, V, Q) if t is not None]
     torch.cuda.current_stream(d.device).synchronize()
     return outs
+
+
+def backward(cube, mu, eigvals, eigvecs, dproj, deigvals=None, gap_eps: float = 1e-6,
+             sync: bool = True, stream=None):
+    """Adjoint of proj = (cube - 1 mu^T) eigvecs[:, :k] (and of eigvals when
+    deigvals is given): returns dcube [N, B] float32.  mu, eigvals, eigvecs are
+    the forward outputs (float64, device); dproj [N, k] float32."""
+    import torch
+    N, B = cube.shape
+    k = dproj.shape[1]
+    dt, dev = _dtype_code(cube), cube.device
+    dproj = dproj.to(torch.float32).contiguous()
+    dcube = torch.empty(N, B, dtype=torch.float32, device=dev)
+    n = load().pca_backward_workspace_size(N, B, k)
+    if n == 0:
+        raise PCAError(1, "pca_backward_workspace_size rejected the shape")
+    ws = Workspace(torch.empty(n + 256, dtype=torch.uint8, device=dev), n)
+    dl = deigvals.to(torch.float64).contiguous() if deigvals is not None else None
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    info = Info() if sync else None
+    rc = load().pca_backward(ctypes.c_void_p(cube.data_ptr()), dt, N, B, int(k),
+                             ctypes.c_void_p(mu.contiguous().data_ptr()),
+                             ctypes.c_void_p(eigvals.contiguous().data_ptr()),
+                             ctypes.c_void_p(eigvecs.contiguous().data_ptr()),
+                             ctypes.c_void_p(dproj.data_ptr()),
+                             ctypes.c_void_p(dl.data_ptr()) if dl is not None else None,
+                             float(gap_eps), ctypes.c_void_p(dcube.data_ptr()),
+                             ctypes.c_void_p(_ws_ptr(ws)), ws.nbytes,
+                             ctypes.c_void_p(st.cuda_stream),
+                             ctypes.byref(info) if info is not None else None)
+    _check_rc(rc)
+    return dcube
+
+
+def _autograd_function():
+    import torch
+
+    class PCAProjection(torch.autograd.Function):
+        """proj = PCAProjection.apply(cube, k, precision, tol, sweeps_max, gap_eps):
+        the forward pass is pca_fit, the backward pass pca_backward (gradient
+        with respect to the cube; the centred cube is recomputed, not stored)."""
+
+        @staticmethod
+        def forward(ctx, cube, k, precision="p64", tol=1e-10, sweeps_max=30, gap_eps=1e-6):
+            mu, ev, V, Q, _ = fit(cube.detach().contiguous(), int(k), tol=tol,
+                                  sweeps_max=sweeps_max, precision=precision)
+            ctx.save_for_backward(cube, mu, ev, V)
+            ctx.gap_eps = gap_eps
+            return Q
+
+        @staticmethod
+        def backward(ctx, dQ):
+            cube, mu, ev, V = ctx.saved_tensors
+            dY = backward(cube.detach().contiguous(), mu, ev, V, dQ.contiguous(),
+                          gap_eps=ctx.gap_eps)
+            return dY.to(cube.dtype), None, None, None, None, None
+
+    return PCAProjection
+
+
+_pca_projection = None
+
+
+def __getattr__(name):
+    global _pca_projection
+    if name == "PCAProjection":
+        if _pca_projection is None:
+            _pca_projection = _autograd_function()
+        return _pca_projection
+    raise AttributeError(name)

@@ -124,6 +124,40 @@ Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, in
   return L;
 }
 
+namespace {
+
+struct BwdLayout {
+  size_t hdr, dv_part, dqs_part, dVk, Gk, dA, S32, vk32, mdq, mu32, total;
+  int parts;
+};
+
+BwdLayout make_bwd_layout(int64_t N, int B, int k, int num_sms) {
+  BwdLayout L{};
+  L.parts = (int)std::min<int64_t>(num_sms, std::max<int64_t>(1, (N + 63) / 64));
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
+  L.hdr = take(sizeof(DevHeader));
+  L.dv_part = take(sizeof(float) * (size_t)L.parts * B * k);
+  L.dqs_part = take(sizeof(float) * (size_t)L.parts * k);
+  L.dVk = take(sizeof(double) * (size_t)B * k);
+  L.Gk = take(sizeof(double) * (size_t)B * k);
+  L.dA = take(sizeof(double) * (size_t)B * B);
+  L.S32 = take(sizeof(float) * (size_t)B * B);
+  L.vk32 = take(sizeof(float) * (size_t)B * k);
+  L.mdq = take(sizeof(float) * (size_t)k);
+  L.mu32 = take(sizeof(float) * (size_t)B);
+  L.total = o;
+  return L;
+}
+
+bool bwd_args_ok(const void* cube, pca_dtype dt, int64_t N, int B, int k, double gap_eps) {
+  static const float kDummy[4] = {0.f, 0.f, 0.f, 0.f};
+  return args_ok(cube ? cube : kDummy, dt, N, B, k, 1.0, 1, PCA_PREC_P32) && gap_eps >= 0.0 &&
+         std::isfinite(gap_eps);
+}
+
+}  // namespace
+
 }  // namespace gbpca
 
 using namespace gbpca;
@@ -369,6 +403,43 @@ const char* pca_status_string(int status) {
     case PCA_ERR_WORKSPACE: return "workspace too small or misaligned";
   }
   return "unknown status";
+}
+
+size_t pca_backward_workspace_size(int64_t N, int B, int k) {
+  if (!bwd_args_ok(nullptr, PCA_F32, N, B, k, 0.0)) return 0;
+  return make_bwd_layout(N, B, k, device_sms()).total;
+}
+
+int pca_backward(const void* cube, pca_dtype dt, int64_t N, int B, int k, const double* mu,
+                 const double* eigvals, const double* eigvecs, const float* dproj,
+                 const double* deigvals, double gap_eps, float* dcube, void* workspace,
+                 size_t ws_bytes, void* stream, pca_info* info) {
+  if (!bwd_args_ok(cube, dt, N, B, k, gap_eps)) return PCA_ERR_ARG;
+  if (!mu || !eigvals || !eigvecs || !dproj || !dcube) return PCA_ERR_ARG;
+  if (((uintptr_t)dproj) % 16 != 0) return PCA_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace) % 256 != 0) return PCA_ERR_WORKSPACE;
+  const BwdLayout L = make_bwd_layout(N, B, k, device_sms());
+  if (ws_bytes < L.total) return PCA_ERR_WORKSPACE;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  BwdPtrs w{};
+  w.parts = L.parts;
+  w.dv_part = reinterpret_cast<float*>(ws + L.dv_part);
+  w.dqs_part = reinterpret_cast<float*>(ws + L.dqs_part);
+  w.dVk = reinterpret_cast<double*>(ws + L.dVk);
+  w.Gk = reinterpret_cast<double*>(ws + L.Gk);
+  w.dA = reinterpret_cast<double*>(ws + L.dA);
+  w.S32 = reinterpret_cast<float*>(ws + L.S32);
+  w.vk32 = reinterpret_cast<float*>(ws + L.vk32);
+  w.mdq = reinterpret_cast<float*>(ws + L.mdq);
+  w.mu32 = reinterpret_cast<float*>(ws + L.mu32);
+  DevHeader* hdr = reinterpret_cast<DevHeader*>(ws + L.hdr);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_header_init<<<1, 1, 0, st>>>(hdr, 0, 0.f);
+  GB_CK(cudaGetLastError());
+  GB_CK(launch_backward(cube, dt, N, B, k, mu, eigvals, eigvecs, dproj, deigvals, gap_eps, dcube, w,
+                        hdr, st));
+  if (info) return pca_read_info(workspace, stream, info);
+  return PCA_OK;
 }
 
 int pca_version(void) { return 100; }

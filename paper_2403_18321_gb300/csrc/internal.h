@@ -136,4 +136,28 @@ cudaError_t launch_project(const void* cube, pca_dtype dt, int64_t N, int B, int
                            const float* mu_f, const float* vk, float* proj, cudaStream_t st,
                            DevHeader* hdr = nullptr);
 
+// Scratch of the backward pass (all device pointers, inside the caller's
+// workspace): parts per-CTA partials of X^T dQ [parts][B][k] and of the column
+// sums of dQ [parts][k] (FP32); dVk [B][k], Gk [B][k], dA [B][B] (FP64); S'
+// [B][B], V_k [B][k], mean dQ [k], mu [B] (FP32).
+struct BwdPtrs {
+  int parts;
+  float* dv_part;
+  float* dqs_part;
+  double* dVk;
+  double* Gk;
+  double* dA;
+  float* S32;
+  float* vk32;
+  float* mdq;
+  float* mu32;
+};
+
+// dY = (dQ - 1 mean dQ) V_k^T + 2/(N-1) X S (the adjoint of the projection
+// layer; dlam nullable).
+cudaError_t launch_backward(const void* cube, pca_dtype dt, int64_t N, int B, int k,
+                            const double* mu, const double* lam, const double* V,
+                            const float* dq, const double* dlam, double gap_eps, float* dY,
+                            const BwdPtrs& w, DevHeader* hdr, cudaStream_t st);
+
 }  // namespace gbpca
