@@ -48,6 +48,8 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default="mix")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-diff", action="store_true",
+                    help="skip the differentiation form (forward + backward on 512 x 512 x 200)")
     ap.add_argument("--ncu-case", choices=["scenes", "big"], default=None,
                     help="untimed fits for profiler captures: 'scenes' = the bench cubes, "
                          "'big' = one 1024x400x224 scene cube (367 MB, larger than L2); "
@@ -453,11 +455,47 @@ def main(argv=None):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": total / args.steps * 1e3}
 
+    # ---- differentiation form: forward + adjoint of the projection layer on the
+    #      512 x 512 x 200 planted cube, k = 10, dQ ~ N(0, 1) (rank 0 only)
+    diff = None
+    if not args.no_diff and rank == 0:
+        gc = synth.gradient_cube()
+        Yg = torch.from_numpy(gc.Y).to(dev)
+        dQg = torch.from_numpy(gc.meta["dQ"]).to(dev)
+        wsg = g.make_workspace(gc.N, gc.B, gc.k, 0, args.precision, dev)
+        outg = g.fit(Yg, gc.k, precision=args.precision, workspace=wsg)
+        mu_g, ev_g, V_g = outg[0], outg[1], outg[2]
+        for _ in range(args.warmup):
+            g.fit(Yg, gc.k, precision=args.precision, workspace=wsg, sync=False)
+            g.backward(Yg, mu_g, ev_g, V_g, dQg, sync=False)
+        torch.cuda.synchronize()
+        f0, f1, b1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        tf = tb = 0.0
+        reps = max(3, min(args.steps, 10))
+        for _ in range(reps):
+            flush.fill_(1)
+            f0.record()
+            g.fit(Yg, gc.k, precision=args.precision, workspace=wsg, sync=False)
+            f1.record()
+            g.backward(Yg, mu_g, ev_g, V_g, dQg, sync=False)
+            b1.record()
+            b1.synchronize()
+            tf += f0.elapsed_time(f1) / 1e3
+            tb += f1.elapsed_time(b1) / 1e3
+        tf, tb = tf / reps, tb / reps
+        units_g = gc.N * gc.B
+        diff = {"workload": "planted 512x512x200 FP32, k=10, dQ ~ N(0,1) (seed 40)",
+                "forward_ms": tf * 1e3, "backward_ms": tb * 1e3,
+                "value": units_g / (tf + tb) / 1e6, "unit": UNIT,
+                "backward_value": units_g / tb / 1e6,
+                "backward_bytes": 2 * gc.N * gc.B * 4 + 2 * gc.N * gc.k * 4 + gc.N * gc.B * 4,
+                "backward_GB/s": (2 * gc.N * gc.B * 4 + 2 * gc.N * gc.k * 4 + gc.N * gc.B * 4) / tb / 1e9}
+
     launches = g.kernel_launches(args.precision, True) * len(cubes) * args.steps
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_mix / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3-f32acc+f32+f64" if args.precision == "mix" else args.precision,
+            "dtype": "f16x3-f32acc+f32+f64" if args.precision == "mix" else args.precision,
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": args.precision,
                        "cubes": [f"{c.name} N={c.N} B={c.B}" for c in cubes],
@@ -469,7 +507,8 @@ def main(argv=None):
                       "p32": {"value": value_p32, "ms_per_step": t_p32 / args.steps * 1e3,
                               "sweeps": [i["sweeps"] for i in infos_p32], **errors.get("p32", {})}},
             "stage_ms_per_step": stage_ms, "roofline": roof, "hbm_kernels": hbm,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "differentiation": diff}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

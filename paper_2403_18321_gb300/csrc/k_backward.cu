@@ -27,6 +27,21 @@ constexpr int kDvWarps = 8;               // thread = band (B <= 256)
 constexpr int kDvThreads = kDvWarps * 32 + 32;
 constexpr int kDvStages = 3;
 
+__device__ __forceinline__ void dv_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kDvWarps * 32) : "memory");
+}
+// AND of a flag over the compute warps (they leave the chunk loop together)
+__device__ __forceinline__ int dv_and(int v) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
+      " selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(v), "n"(kDvWarps * 32)
+      : "memory");
+  return r;
+}
+
 struct __align__(8) DvSync {
   uint64_t full[kDvStages];
   uint64_t empty[kDvStages];
@@ -42,7 +57,8 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
   unsigned char* cst = smem;                                        // [S][cube_stage]
   float* dqst = reinterpret_cast<float*>(smem + kDvStages * cube_stage);  // [S][dq_stage/4]
   float* mus = dqst + kDvStages * dq_stage / 4;                     // [256]
-  DvSync* sy = reinterpret_cast<DvSync*>(mus + 256);
+  float4* dqpad = reinterpret_cast<float4*>(mus + 256);              // [2][kDvPx][KQ]
+  DvSync* sy = reinterpret_cast<DvSync*>(dqpad + 2 * kDvPx * KQ);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x, g = blockIdx.x;
   const int64_t nch_total = (N + kDvPx - 1) / kDvPx;
@@ -84,7 +100,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
     int ok = 1;
     if (lane == 0) ok = mbar_wait(&sy->full[s], (c / kDvStages) & 1, &sy->abort) ? 1 : 0;
     ok = __shfl_sync(kFull, ok, 0);
-    if (!ok) break;
+    if (!dv_and(ok)) break;
     const int64_t p0 = (c_begin + c) * kDvPx;
     const int cp = (int)((N - p0) < kDvPx ? (N - p0) : kDvPx);
     const In* xs = reinterpret_cast<const In*>(cst + (size_t)s * cube_stage);
@@ -92,13 +108,25 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
     const int copied_x = (int)((((size_t)cp * B * sizeof(In)) & ~(size_t)15) / sizeof(In));
     const int copied_d = (int)((((size_t)cp * k * 4) & ~(size_t)15) / 4);
     const bool whole = copied_x == cp * B && copied_d == cp * k;
+    // dQ rows of this chunk padded to 16-byte rows (two buffers by chunk
+    // parity), so that every pixel's row is read as KQ vectors
+    float4* dqp = dqpad + (size_t)(c & 1) * kDvPx * KQ;
+    for (int e = tid; e < cp * KQ * 4; e += kDvWarps * 32) {
+      const int pp = e / (KQ * 4), j = e - pp * (KQ * 4);
+      const int ed = pp * k + j;
+      reinterpret_cast<float*>(dqp)[e] = j < k ? (ed < copied_d ? ds[ed] : dq[p0 * k + ed]) : 0.f;
+    }
+    dv_sync();
     for (int p = 0; p < cp; ++p) {
       float x = 0.f;
       float dv[KQ * 4];
       if (whole) {
         if (b < B) x = to_f32<In>(xs[p * B + b]) - m;
 #pragma unroll
-        for (int j = 0; j < KQ * 4; ++j) dv[j] = j < k ? ds[p * k + j] : 0.f;
+        for (int q = 0; q < KQ; ++q) {
+          const float4 v = dqp[p * KQ + q];
+          dv[4 * q] = v.x; dv[4 * q + 1] = v.y; dv[4 * q + 2] = v.z; dv[4 * q + 3] = v.w;
+        }
       } else {
         const int ex = p * B + b;
         if (b < B) x = (ex < copied_x ? to_f32<In>(xs[ex]) : to_f32<In>(cube[p0 * B + ex])) - m;
@@ -115,10 +143,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
         acc[q].z = fmaf(x, dv[4 * q + 2], acc[q].z);
         acc[q].w = fmaf(x, dv[4 * q + 3], acc[q].w);
       }
-      if (tid < k) {
-        const int ed = p * k + tid;
-        csum += ed < copied_d ? ds[ed] : dq[p0 * k + ed];
-      }
+      if (tid < k) csum += reinterpret_cast<const float*>(dqp)[p * KQ * 4 + tid];
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&sy->empty[s]);
@@ -139,63 +164,95 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
 
 // ------------------------------------------------------------------ k_bwd_reduce
 // dVk[b][j] = sum over the partials (FP64), FP32 copy of mu; CTA 0 also forms
-// the column means of dQ.  One CTA (one warp) per band.
-__global__ void k_bwd_reduce(const float* __restrict__ dv_part, const float* __restrict__ dqs_part,
-                             int parts, int64_t N, int B, int k, const double* __restrict__ mu,
-                             double* __restrict__ dVk, float* __restrict__ mdq,
-                             float* __restrict__ mu32) {
-  const int b = blockIdx.x, j = threadIdx.x;
-  if (j < k) {
-    double s = 0.0;
-    for (int gg = 0; gg < parts; ++gg) s += (double)dv_part[((size_t)gg * B + b) * k + j];
-    dVk[(size_t)b * k + j] = s;
-    if (b == 0) {
-      double t = 0.0;
-      for (int gg = 0; gg < parts; ++gg) t += (double)dqs_part[(size_t)gg * k + j];
-      mdq[j] = (float)(t / (double)N);
+// the column means of dQ.  One CTA per band: warp w adds the partials
+// w, w + 8, ... for every column (lane = column), then the eight warp sums.
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(kRedWarps * 32)
+k_bwd_reduce(const float* __restrict__ dv_part, const float* __restrict__ dqs_part, int parts,
+             int64_t N, int B, int k, const double* __restrict__ mu, double* __restrict__ dVk,
+             float* __restrict__ mdq, float* __restrict__ mu32) {
+  __shared__ double red[2][kRedWarps][32];
+  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double s = 0.0, t = 0.0;
+  if (lane < k) {
+    for (int gg = warp; gg < parts; gg += kRedWarps) {
+      s += (double)dv_part[((size_t)gg * B + b) * k + lane];
+      if (b == 0) t += (double)dqs_part[(size_t)gg * k + lane];
     }
   }
-  if (j == 0) mu32[b] = (float)mu[b];
+  red[0][warp][lane] = s;
+  red[1][warp][lane] = t;
+  __syncthreads();
+  if (warp == 0 && lane < k) {
+    double a = 0.0, c = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRedWarps; ++w) { a += red[0][w][lane]; c += red[1][w][lane]; }
+    dVk[(size_t)b * k + lane] = a;
+    if (b == 0) mdq[lane] = (float)(c / (double)N);
+  }
+  if (threadIdx.x == 0) mu32[b] = (float)mu[b];
 }
 
 // ------------------------------------------------------------------ k_bwd_m
-// G_ij = F_ij (V^T dVk)_ij for j < k (i != j), G_jj = dlam_j; one warp per row i.
-__global__ void k_bwd_m(int B, int k, const double* __restrict__ lam, const double* __restrict__ V,
-                        const double* __restrict__ dVk, const double* __restrict__ dlam,
-                        double gap_eps, double* __restrict__ Gk) {
-  const int i = blockIdx.x, j = threadIdx.x;
-  if (j >= k) return;
-  double m = 0.0;
-  for (int bb = 0; bb < B; ++bb) m += V[(size_t)bb * B + i] * dVk[(size_t)bb * k + j];
-  double gval;
-  if (i == j) {
-    gval = dlam ? dlam[i] : 0.0;
-  } else {
-    const double gap = lam[j] - lam[i];
-    gval = fabs(gap) > gap_eps * fabs(lam[0]) ? m / gap : 0.0;
+// G_ij = F_ij (V^T dVk)_ij for j < k (i != j), G_jj = dlam_j.  One CTA per
+// row i; thread = band b, the k products summed by shuffles and shared memory.
+__global__ void __launch_bounds__(256)
+k_bwd_m(int B, int k, const double* __restrict__ lam, const double* __restrict__ V,
+        const double* __restrict__ dVk, const double* __restrict__ dlam, double gap_eps,
+        double* __restrict__ Gk) {
+  __shared__ double part[8][32];
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double v = tid < B ? V[(size_t)tid * B + i] : 0.0;
+  for (int j = 0; j < k; ++j) {
+    double m = tid < B ? v * dVk[(size_t)tid * k + j] : 0.0;
+    m = warp_sum(m);
+    if (lane == 0) part[warp][j] = m;
   }
-  Gk[(size_t)i * k + j] = gval;
+  __syncthreads();
+  if (tid < k) {
+    const int j = tid;
+    double m = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m += part[w][j];
+    double gval;
+    if (i == j) {
+      gval = dlam ? dlam[i] : 0.0;
+    } else {
+      const double gap = lam[j] - lam[i];
+      gval = fabs(gap) > gap_eps * fabs(lam[0]) ? m / gap : 0.0;
+    }
+    Gk[(size_t)i * k + j] = gval;
+  }
 }
 
 // ------------------------------------------------------------------ k_bwd_s
-// dA = V G V^T = T V^T with T = V G: T_aj = sum_{i} V_ai G_ij for j < k
-// (plus V_aj dlam_j for j >= k), then S' = 2/(N-1) (dA + dA^T)/2 in FP32 and
-// V_k in FP32.  One CTA per row a.
+// dA = V G V^T = T V^T with T = V G: T_aj = sum_i V_ai G_ij for j < k (plus
+// V_aj dlam_j for j >= k), and V_k in FP32.  One CTA per row a.
 __global__ void __launch_bounds__(256)
 k_bwd_s(const double* __restrict__ V, const double* __restrict__ Gk, const double* __restrict__ dlam,
         int64_t N, int B, int k, double* __restrict__ dA, float* __restrict__ vk32) {
   __shared__ double T[256];
-  const int a = blockIdx.x, tid = threadIdx.x;
-  for (int j = tid; j < B; j += 256) {
+  __shared__ double part[8][32];
+  const int a = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double vai = tid < B ? V[(size_t)a * B + tid] : 0.0;   // thread = i
+  for (int j = 0; j < k; ++j) {
+    double t = tid < B ? vai * Gk[(size_t)tid * k + j] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) part[warp][j] = t;
+  }
+  __syncthreads();
+  if (tid < B) {
     double t;
-    if (j < k) {
+    if (tid < k) {
       t = 0.0;
-      for (int i = 0; i < B; ++i) t += V[(size_t)a * B + i] * Gk[(size_t)i * k + j];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += part[w][tid];
+      vk32[(size_t)a * k + tid] = (float)vai;
     } else {
-      t = dlam ? V[(size_t)a * B + j] * dlam[j] : 0.0;
+      t = dlam ? vai * dlam[tid] : 0.0;
     }
-    T[j] = t;
-    if (j < k) vk32[(size_t)a * k + j] = (float)V[(size_t)a * B + j];
+    T[tid] = t;
   }
   __syncthreads();
   const int jmax = dlam ? B : k;
@@ -214,76 +271,100 @@ __global__ void k_bwd_sym(const double* __restrict__ dA, int64_t N, int B, float
 }
 
 // ------------------------------------------------------------------ k_bwd_dy
-// dY[n][c] = sum_b x_nb S'_bc + sum_j (dq_nj - mdq_j) V_cj over a 128-pixel x
-// 64-band output tile per CTA (256 threads, 8 x 4 outputs each), K staged in
-// steps of 16 through shared memory; the band tiles of one pixel block are
+// dY[n][c] = sum_b x_nb S'_bc + sum_j (dq_nj - mdq_j) V_cj: the product
+// [X | dQ'] [S'; V_k^T] over 128-pixel x 128-band output tiles (256 threads,
+// 8 x 8 outputs each: pixels {4ty..4ty+3, 64+4ty..}, bands {4tx.., 64+4tx..},
+// read as 16-byte shared-memory vectors), K in steps of 8 with the next step's
+// tiles held in registers while the current one is multiplied; the cube is
+// centred while it is staged.  The band tiles of one pixel block are
 // consecutive blocks of the grid, so that they reuse its cube rows from L2.
-constexpr int kTM = 128, kTN = 64, kTK = 16;
+constexpr int kTM = 128, kTN = 128, kTK = 8;
 
 template <typename In>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_bwd_dy(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, int B, int k,
          const float* __restrict__ mu32, const float* __restrict__ mdq, const float* __restrict__ S32,
          const float* __restrict__ vk32, float* __restrict__ dY) {
-  __shared__ float As[kTK][kTM + 4];
-  __shared__ float Bs[kTK][kTN + 4];
+  __shared__ __align__(16) float As[2][kTK][kTM + 4];
+  __shared__ __align__(16) float Bs[2][kTK][kTN + 4];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;          // 16 x 16 threads
-  const int nbt = (B + kTN - 1) / kTN;            // band tiles of one pixel block
+  const int tx = tid & 15, ty = tid >> 4;
+  const int nbt = (B + kTN - 1) / kTN;
   const int c0 = (int)(blockIdx.x % nbt) * kTN;
   const int64_t n0 = (int64_t)(blockIdx.x / nbt) * kTM;
-  float acc[8][4];
+  const int KT = B + k;
+  // staging roles: A -- pixel ar = tid / 2, columns ak0 .. ak0 + 3;
+  //                B -- row br = tid / 32, bands bc0 .. bc0 + 3
+  const int ar = tid >> 1, ak0 = (tid & 1) * 4;
+  const int br = tid >> 5, bc0 = (tid & 31) * 4;
+  const int64_t an = n0 + ar;
+  float ra[4], rb[4];
+  auto load = [&](int kk) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  const int KT = B + k;                            // [X | dQ'] times [S'; V_k^T]
-  for (int kk = 0; kk < KT; kk += kTK) {
-    // A tile: rows n0.., columns kk.. of [X | dQ']
-    for (int e = tid; e < kTK * kTM; e += 256) {
-      const int r = e / kTK, q = e % kTK;          // q fastest: consecutive columns
-      const int col = kk + q;
-      const int64_t n = n0 + r;
+    for (int e = 0; e < 4; ++e) {
+      const int col = kk + ak0 + e;
       float v = 0.f;
-      if (n < N) {
-        if (col < B) v = to_f32<In>(cube[n * B + col]) - mu32[col];
-        else if (col < KT) v = dq[n * k + (col - B)] - mdq[col - B];
+      if (an < N) {
+        if (col < B) v = to_f32<In>(cube[an * B + col]) - mu32[col];
+        else if (col < KT) v = dq[an * k + (col - B)] - mdq[col - B];
       }
-      As[q][r] = v;
+      ra[e] = v;
     }
-    // B tile: rows kk.. of [S'; V_k^T], columns c0..
-    for (int e = tid; e < kTK * kTN; e += 256) {
-      const int q = e / kTN, cc = e % kTN;
-      const int row = kk + q, c = c0 + cc;
+    const int row = kk + br;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int c = c0 + bc0 + e;
       float v = 0.f;
       if (c < B) {
         if (row < B) v = S32[(size_t)row * B + c];
         else if (row < KT) v = vk32[(size_t)c * k + (row - B)];
       }
-      Bs[q][cc] = v;
+      rb[e] = v;
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) As[buf][ak0 + e][ar] = ra[e];
+    *reinterpret_cast<float4*>(&Bs[buf][br][bc0]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int kk = 0; kk < KT; kk += kTK) {
+    const bool more = kk + kTK < KT;
+    if (more) load(kk + kTK);
 #pragma unroll
     for (int q = 0; q < kTK; ++q) {
-      float a[8], bv[4];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = As[q][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[q][tx + 16 * j];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][q][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][q][64 + 4 * ty]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][q][4 * tx]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][q][64 + 4 * tx]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
     }
-    __syncthreads();
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int64_t n = n0 + ty + 16 * i;
+    const int64_t n = n0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + (i - 4));
     if (n >= N) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx + 16 * j;
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + (j - 4));
       if (c < B) dY[n * B + c] = acc[i][j];
     }
   }
@@ -294,7 +375,8 @@ cudaError_t dv_kq(const In* cube, const float* dq, int64_t N, int B, int k, cons
                   float* dv_part, float* dqs_part, int parts, DevHeader* hdr, cudaStream_t st) {
   const int cube_stage = (int)((((size_t)kDvPx * B * sizeof(In)) + 127) & ~(size_t)127);
   const int dq_stage = (int)((((size_t)kDvPx * k * 4) + 127) & ~(size_t)127);
-  const size_t smem = (size_t)kDvStages * (cube_stage + dq_stage) + 256 * 4 + sizeof(DvSync);
+  const size_t smem = (size_t)kDvStages * (cube_stage + dq_stage) + 256 * 4 +
+                      (size_t)2 * kDvPx * KQ * 16 + sizeof(DvSync);
   auto kern = k_bwd_dv<In, KQ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -351,8 +433,8 @@ cudaError_t launch_backward(const void* cube, pca_dtype dt, int64_t N, int B, in
       return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
-  k_bwd_reduce<<<B, 32, 0, st>>>(w.dv_part, w.dqs_part, w.parts, N, B, k, mu, w.dVk, w.mdq, w.mu32);
-  k_bwd_m<<<B, 32, 0, st>>>(B, k, lam, V, w.dVk, dlam, gap_eps, w.Gk);
+  k_bwd_reduce<<<B, kRedWarps * 32, 0, st>>>(w.dv_part, w.dqs_part, w.parts, N, B, k, mu, w.dVk, w.mdq, w.mu32);
+  k_bwd_m<<<B, 256, 0, st>>>(B, k, lam, V, w.dVk, dlam, gap_eps, w.Gk);
   k_bwd_s<<<B, 256, 0, st>>>(V, w.Gk, dlam, N, B, k, w.dA, w.vk32);
   k_bwd_sym<<<dim3((B + 127) / 128, B), 128, 0, st>>>(w.dA, N, B, w.S32);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
