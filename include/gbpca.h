@@ -98,7 +98,7 @@ size_t pca_workspace_size(int64_t N, int B, int k, pca_dtype dtype, pca_precisio
  *
  * cube       [N][B] device array of `dtype`, 16-byte aligned.
  * N          pixels, N >= 2 (C is divided by N-1, Sec. 4.2 stage 3).
- * B          bands, 2 <= B <= 232.
+ * B          bands, 2 <= B <= 256.
  * k          components to project onto, 1 <= k <= min(B, 32).
  * tol        Jacobi stop factor (Sec. 2, "until all off-diagonal elements are
  *            smaller than the stop factor").  The FP32 Jacobi applies
@@ -161,10 +161,10 @@ int pca_project(const void *cube, pca_dtype dtype, int64_t N, int B, int k, cons
  * allocator.  This entry point computes the same proj [N][k] as pca_project
  * but keeps its two small intermediates (FP32 copies of mu and of the first
  * k eigenvectors) in a fixed device array that belongs to the library:
- * 232 + 232*32 floats (30,624 bytes), held on every GPU that loads the
+ * 256 + 256*32 floats (33,792 bytes), held on every GPU that loads the
  * library until the process exits.  It allocates and frees nothing.
  *   - Arguments as pca_project, without workspace; B*(k+1) above the array
- *     size (impossible for valid B <= 232, k <= 32) returns PCA_ERR_ARG.
+ *     size (impossible for valid B <= 256, k <= 32) returns PCA_ERR_ARG.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
@@ -229,8 +229,9 @@ int pca_jacobi_sms(int B);
 /*
  * Per-stage timing.  pca_profile(1) makes every later pca_fit on the calling
  * host thread record CUDA events on its stream around its eight stages
- * (covariance, covariance finalisation, Jacobi, V replay, compaction,
- * refinement, sort/sign, projection), up to 256 fits; pca_profile(0) stops.
+ * (covariance, covariance finalisation, Jacobi, a fourth slot that is always
+ * 0 because the Jacobi kernel rotates V itself, compaction, refinement,
+ * sort/sign, projection), up to 256 fits; pca_profile(0) stops.
  * Both reset the record list and return the stage count (8).
  * pca_profile_collect waits for the recorded events and writes, per fit
  * r < max_records, the stage durations in ms to ms[r*8 + i]; returns the

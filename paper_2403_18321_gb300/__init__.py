@@ -30,7 +30,7 @@ EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_p
            "pca_read_info", "pca_status_string", "pca_version",
            "pca_kernel_launches", "pca_profile", "pca_profile_collect", "pca_project_noalloc",
            "pca_jacobi_sms", "pca_backward", "pca_backward_workspace_size")
-STAGES = ("covariance", "cov_finalize", "jacobi", "v_replay", "compact", "refine", "sort_sign",
+STAGES = ("covariance", "cov_finalize", "jacobi", "empty", "compact", "refine", "sort_sign",
           "project")
 
 

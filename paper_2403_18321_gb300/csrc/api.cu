@@ -45,7 +45,7 @@ bool args_ok(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol
 }
 
 // ---- optional per-stage CUDA-event timing (profiling entry points of gbpca.h)
-constexpr int kProfStages = 8;  // cov, cov_finalize, jacobi, vreplay, compact, refine, sort, project
+constexpr int kProfStages = 8;  // cov, cov_finalize, jacobi, (empty), compact, refine, sort, project
 constexpr int kProfRecords = 256;
 struct ProfState {
   bool on = false;
@@ -87,7 +87,7 @@ float stop_floor(pca_precision prec) {
 Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, int num_sms) {
   (void)dt;
   Layout L{};
-  const int Bp = round_even(B), P = Bp / 2;
+  const int Bp = round_even(B);
   if (prec == PCA_PREC_MIX) {
     L.partials = (int)std::min<int64_t>(num_sms, std::max<int64_t>(1, (N + 127) / 128));
     L.s2_bytes_el = 4;
@@ -110,7 +110,6 @@ Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, in
   L.rank = take(sizeof(int) * B);
   L.sgn = take(sizeof(double) * B);
   L.diag32 = take(sizeof(float) * Bp);
-  L.log = take(sizeof(float2) * (size_t)kMaxSweeps * Bp * P);
   L.v32 = take(sizeof(float) * (size_t)Bp * Bp);
   L.lam = take(sizeof(double) * B);
   L.vc = take(BB8);
@@ -209,7 +208,6 @@ struct Ptrs {
   int* rank;
   double* sgn;
   float* diag32;
-  float2* log;
   float* v32;
   double* lam;
   float2* vc;
@@ -235,7 +233,6 @@ Ptrs carve(void* workspace, const Layout& L) {
   p.rank = reinterpret_cast<int*>(ws + L.rank);
   p.sgn = reinterpret_cast<double*>(ws + L.sgn);
   p.diag32 = reinterpret_cast<float*>(ws + L.diag32);
-  p.log = reinterpret_cast<float2*>(ws + L.log);
   p.v32 = reinterpret_cast<float*>(ws + L.v32);
   p.lam = reinterpret_cast<double*>(ws + L.lam);
   p.vc = reinterpret_cast<float2*>(ws + L.vc);
@@ -278,7 +275,7 @@ cudaError_t run_cov(const void* cube, pca_dtype dt, int64_t N, int B, pca_precis
                              P.muf, P.dvec, P.hdr, st, prec == PCA_PREC_MIX ? P.escale : nullptr);
 }
 
-// stage 4: Jacobi, V replay, FP64 refinement, sort and sign rule
+// stage 4: Jacobi (rotating V), FP64 refinement, sort and sign rule
 cudaError_t run_eigh(const double* A, int B, float tol32, int sweeps_max, pca_precision prec,
                      int k, const Ptrs& P, double* eigvals, double* eigvecs, cudaStream_t st,
                      StageMark& pm) {

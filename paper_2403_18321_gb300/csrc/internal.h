@@ -10,7 +10,7 @@
 
 namespace gbpca {
 
-constexpr int kMaxB = 232;          // A (FP32, B' x B') must fit one SM's shared memory
+constexpr int kMaxB = 256;          // two 128-row tensor-core tiles; 8 Jacobi CTAs x 32 V rows
 constexpr int kMaxK = 32;
 constexpr int kMaxPartials = 320;   // per-CTA covariance partial slots
 constexpr float kJacobiFloor = 2.384185791015625e-07f;  // 2^-22: FP32 Jacobi stop floor
@@ -35,7 +35,7 @@ struct DevHeader {
 
 // Offsets (bytes) of every workspace region; all 256-byte aligned.
 struct Layout {
-  size_t hdr, shift, escale, s1_part, s2_part, dvec, cov, cdf, rank, sgn, diag32, log, v32, lam, vc, w, s, r, e, vk, muf;
+  size_t hdr, shift, escale, s1_part, s2_part, dvec, cov, cdf, rank, sgn, diag32, v32, lam, vc, w, s, r, e, vk, muf;
   size_t total;
   int partials;      // number of covariance partial slots the SYRK uses
   int s2_elems;      // packed upper-triangle entries per partial: B(B+1)/2
@@ -83,23 +83,16 @@ cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const
                                 double* C, float* mu_f, double* dvec, DevHeader* hdr,
                                 cudaStream_t st, const int* escale = nullptr);
 
-// FP32 odd-even Jacobi on one SM; logs (c, s) of every rotation.  relative_stop
-// selects the element-wise relative stop test (else off(A) <= tol ||A||_F).
-cudaError_t launch_jacobi(const double* C, int B, float tol32, int sweeps_max, bool relative_stop,
-                          float2* log, float* diag32, DevHeader* hdr, cudaStream_t st);
-
-// The Jacobi on one thread-block cluster (matrix rows split over A-CTAs, rows
-// of V over V-CTAs rotated in lock-step): writes diag32 [B'] and V32 [B'][B'].
+// FP32 odd-even Jacobi on one thread-block cluster (matrix rows split over
+// the CTAs, rows of V in registers): writes diag32 [B'] and V32 [B'][B'].
+// relative_stop selects the element-wise relative stop test (else
+// off(A) <= tol ||A||_F).
 cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweeps_max,
                                   bool relative_stop, float* diag32, float* v32, DevHeader* hdr,
                                   cudaStream_t st);
 
 // CTAs (= SMs) the cluster Jacobi uses for B bands: nA matrix CTAs + nV V CTAs.
 bool jacobi_cluster_shape(int B, int* nA, int* nV);
-
-// Replays the rotation log on the rows of V (starting from I) -> V32 [B'][B'].
-cudaError_t launch_vreplay(const float2* log, int B, const DevHeader* hdr, float* v32,
-                           cudaStream_t st);
 
 // Drops the padding slot: lam (FP64) [B] and Vc [B][B] in slot order, Vc as
 // double-float (hi, lo) pairs.

@@ -10,7 +10,7 @@ namespace {
 // Sort and sign rule in two fully parallel passes.
 // k_rank_sign: one CTA per eigen-pair j.  Its rank = number of eigenvalues
 // that sort before it (larger, or equal and at a lower position) -- no
-// comparison sort needed for B <= 232 -- and the sign that makes the entry of
+// comparison sort needed for B <= 256 -- and the sign that makes the entry of
 // largest magnitude (lowest row on ties) of column j positive.
 __global__ void __launch_bounds__(256)
 k_rank_sign(const double* __restrict__ lam, const float2* __restrict__ vc, int B,

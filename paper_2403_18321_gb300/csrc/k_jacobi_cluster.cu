@@ -1,11 +1,23 @@
 // k_jacobi_cluster.cu -- the cyclic Jacobi eigen-solver (Sec. 2, Eqs. 2-10)
 // spread over one thread-block cluster.
 //
-// Same ordering and arithmetic as k_jacobi.cu (odd-even parallel ordering
-// with a position swap after every rotation, G = [[s, c], [c, -s]], FP32,
-// B'/2 disjoint rotations per step).  The B' x B' matrix is split by rows
-// over the nA CTAs of the cluster, and every CTA also holds a slice of the
-// rows of the eigenvector matrix V in registers.
+// The paper zeroes one element per host round trip (Sec. 4.2 stage 4) and
+// notes that rotations on disjoint row/column pairs commute (Sec. 2, last
+// paragraph).  Here every parallel step applies B'/2 disjoint rotations
+// (B' = B rounded up to even, a zero padding index when B is odd), FP32.
+//
+// Ordering: odd-even.  Even steps rotate the position pairs (0,1),(2,3),...,
+// odd steps (1,2),(3,4),...; after each rotation the two positions swap, so
+// the rotation actually applied is G = R Pi with R = [[c, s], [-s, c]] the
+// Eq. 1/Eq. 6 rotation and Pi the 2x2 swap, G = [[s, c], [c, -s]].  With the
+// swap every index pair meets exactly once in B' steps (a valid cyclic
+// sweep), and the pairs are always adjacent positions: a step touches only
+// 2x2 blocks in place, with no index tables.  V receives the same G
+// (V <- V G), so at the end eigenvalue diag(A)[j] belongs to column j of V.
+//
+// The B' x B' matrix (upper triangle i <= j only) is split by rows over the
+// nA CTAs of the cluster, and every CTA also holds a slice of the rows of
+// the eigenvector matrix V in registers.
 //
 //   * CTA r owns the even row pairs [rp[r], rp[r+1]) -- rows
 //     [2rp[r], 2rp[r+1]) -- in shared memory, plus one halo row 2rp[r+1]

@@ -11,16 +11,16 @@
 //               both computed by every CTA from the same pixels), split into
 //               FP16 hi = fp16(x), lo = fp16(x - hi) -- 22 significant bits
 //               of x -- written transposed ([band][pixel], K-major core-
-//               matrix layout) into a 2-stage operand ring; one extra operand
-//               row is all ones, so the same MMAs also produce the band sums
-//               S1 = sum x;
+//               matrix layout) into a 2-stage operand ring, and keep the
+//               band sums S1 = sum x of the values they converted (FP32 over
+//               16 chunks, then FP64);
 //   warp 1      MMA issuer (one thread): D += hi hi^T + hi lo^T + lo hi^T
 //               for the upper block-triangle (row tile 0: bands 0-127 x all;
 //               row tile 1: bands 128-255 x bands 128-255) with FP32
 //               accumulation in TMEM;
 //   warps 2-5   epilogue: TMEM -> registers -> the CTA's partial slot
-//               (packed upper triangle, FP32, still scaled by 2^(e_i+e_j))
-//               and S1 (FP64, unscaled).
+//               (packed upper triangle, FP32, still scaled by 2^(e_i+e_j));
+//               the converters write S1 (FP64, unscaled).
 // A scaled value outside the FP16 range sets hdr->cov_range; the caller then
 // recomputes the partials on the SIMT path.  The partials are reduced and
 // finalised by k_cov.cu.  Every mbarrier wait is bounded (one second of
@@ -35,7 +35,7 @@ namespace {
 constexpr int kKC = 32;                 // pixels per chunk (K of one stage)
 constexpr int kMaxStages = 12;          // TMA ring depth: as many stages as shared memory holds
 constexpr int kOpStages = 2;            // FP16 operand ring depth
-constexpr int kRows = 256;              // operand rows (bands, padded; ones row included)
+constexpr int kRows = 256;              // operand rows (bands, padded to 16)
 constexpr int kConvWarps = 16;
 constexpr int kThreads = (2 + kConvWarps) * 32;
 constexpr int kOpBytes = kRows * kKC * 2;        // one FP16 operand (hi or lo): 16 KB
@@ -43,6 +43,7 @@ constexpr uint32_t kLBO = 128;                   // K-adjacent core matrices
 constexpr uint32_t kSBO = (kKC / 8) * 128;       // 8-row groups: 512 B
 constexpr int kTmemCols = 512;
 constexpr int kProbe = 32;               // pixels of the band probe
+constexpr int kS1Flush = 16;             // chunks summed in FP32 before the FP64 add
 
 struct __align__(8) SyncBlock {
   uint64_t full[kMaxStages];
@@ -120,15 +121,15 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
           int* __restrict__ escale_out, double* __restrict__ s1_part,
           float* __restrict__ s2_part, int s2_elems, DevHeader* __restrict__ hdr, int S) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int R16 = (B + 15) & ~15;     // first row after the padded bands = the ones row
+  const int R16 = (B + 15) & ~15;     // bands padded to the 16-row MMA granule
   const int stage_bytes_max = kKC * B * (int)sizeof(In);
   const int stage_stride = (stage_bytes_max + 127) & ~127;
   unsigned char* ops = smem;                                        // [kOpStages][hi|lo][kOpBytes]
   unsigned char* stages = smem + kOpStages * 2 * kOpBytes;          // [S][stage_stride]
   float* shs = reinterpret_cast<float*>(stages + S * stage_stride);        // [kRows] shift
   int* sesc = reinterpret_cast<int*>(shs + kRows);                         // [kRows] exponent
-  double* psum = reinterpret_cast<double*>(sesc + kRows);                  // [2][kRows]
-  float* pmin = reinterpret_cast<float*>(psum + 2 * kRows);                // [2][kRows]
+  double* psum = reinterpret_cast<double*>(sesc + kRows);                  // [4][kRows]
+  float* pmin = reinterpret_cast<float*>(psum + 4 * kRows);                // [2][kRows]
   float* pmax = pmin + 2 * kRows;                                          // [2][kRows]
   SyncBlock* sb = reinterpret_cast<SyncBlock*>(pmax + 2 * kRows);
 
@@ -139,8 +140,8 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
   const int nch = (int)(c_end - c_begin);
 
   const bool two_tiles = B > 128;
-  const int N0 = R16 + 16;                       // tile 0 columns: bands 0..R16-1 + ones block
-  const int N1 = two_tiles ? (R16 - 128 + 16) : 0;
+  const int N0 = R16;                            // tile 0 columns: bands 0..R16-1
+  const int N1 = two_tiles ? (R16 - 128) : 0;     // tile 1 columns: bands 128..R16-1
 
   // ---- set-up
   for (int i = tid; i < kOpStages * 2 * kOpBytes / 16; i += kThreads)
@@ -215,8 +216,8 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
     }
   } else {
     // ---------------------------------------------------------- converters
-    // Item = (band or ones row, 8-pixel group); a thread owns the same items in
-    // every chunk (at most two for B <= 232), so their decode happens once.
+    // Item = (band, 8-pixel group); a thread owns the same items in every
+    // chunk (at most two for B <= 256), so their decode happens once.
     const int ct = tid - 64;
     // Band probe (every CTA computes the same values from the same pixels):
     // over S = min(N, 32) pixels spread evenly through the cube, per band b
@@ -274,18 +275,19 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
       }
       conv_sync();
     }
-    const int items = (B + 1) * (kKC / 8);
+    const int items = B * (kKC / 8);
     int ib[2], ipg[2], ioff[2];
-    float ish[2], isc[2];
+    float ish[2], isc[2], s1f[2] = {0.f, 0.f};
+    double s1d[2] = {0.0, 0.0};
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int w = ct + u * kConvWarps * 32;
-      ipg[u] = w < items ? w / (B + 1) : -1;
-      ib[u] = w < items ? w - ipg[u] * (B + 1) : 0;
-      const int row = ib[u] < B ? ib[u] : R16;
+      ipg[u] = w < items ? w / B : -1;
+      ib[u] = w < items ? w - ipg[u] * B : 0;
+      const int row = ib[u];
       ioff[u] = (row >> 3) * (int)kSBO + (ipg[u] < 0 ? 0 : ipg[u]) * 128 + (row & 7) * 16;
-      ish[u] = ib[u] < B ? shs[ib[u]] : 0.f;
-      isc[u] = ib[u] < B ? ldexpf(1.f, sesc[ib[u]]) : 1.f;
+      ish[u] = shs[row];
+      isc[u] = ldexpf(1.f, sesc[row]);
     }
     for (int c = 0; c < nch; ++c) {
       const int s = c % S, o = c % kOpStages;
@@ -311,7 +313,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
         const int pg = ipg[u], b = ib[u];
         if (pg < 0) continue;
         uint32_t h[4], l[4];
-        if (b < B) {
+        {
           const float sh = ish[u], sc = isc[u];
           float x[8];
           if (full) {
@@ -331,19 +333,13 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
           // NaN compares false, so it counts as out of range too
 #pragma unroll
           for (int i = 0; i < 8; ++i) out_of_range |= !(fabsf(x[i]) <= 65504.f);
+          s1f[u] += ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             h[i] = pack_f16x2(x[2 * i], x[2 * i + 1]);
             float a, bb;
             unpack_f16x2(h[i], a, bb);
             l[i] = pack_f16x2(x[2 * i] - a, x[2 * i + 1] - bb);
-          }
-        } else {  // ones row: 1 for real pixels, 0 for the tail
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int p = pg * 8 + 2 * i;
-            h[i] = pack_f16x2(p < cp ? 1.f : 0.f, p + 1 < cp ? 1.f : 0.f);
-            l[i] = 0u;
           }
         }
         *reinterpret_cast<uint4*>(hi + ioff[u]) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -352,7 +348,20 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) { mbar_arrive(&sb->opfull[o]); mbar_arrive(&sb->empty[s]); }
+      if ((c + 1) % kS1Flush == 0) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) { s1d[u] += (double)s1f[u]; s1f[u] = 0.f; }
+      }
     }
+    // band sums: the four 8-pixel groups of a band meet in shared memory (the
+    // probe's sums are no longer read once the loop has started)
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (ipg[u] >= 0) psum[ipg[u] * kRows + ib[u]] = s1d[u] + (double)s1f[u];
+    conv_sync();
+    for (int b = ct; b < B; b += kConvWarps * 32)
+      s1_part[(size_t)g * B + b] =
+          ldexp((psum[b] + psum[kRows + b]) + (psum[2 * kRows + b] + psum[3 * kRows + b]), -sesc[b]);
     // ---------------------------------------------------------- epilogue
     if (warp >= 2 && warp < 6) {
       int okw = 0;
@@ -363,7 +372,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
       const int r = q * 32 + lane;     // accumulator row
       const uint32_t lane_off = (uint32_t)(q * 32) << 16;
       float* out = s2_part + (size_t)g * s2_elems;
-      // tile 0: row r = band r, column j = band j (j < R16), column R16 = band sums
+      // tile 0: row r = band r, column j = band j (j < R16)
       for (int j0 = 0; j0 < N0; j0 += 16) {
         float v[16];
         if (ok) tmem_ld16(tbase + lane_off + (uint32_t)j0, v);
@@ -372,10 +381,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int j = j0 + i;
-          if (r < B && r < 128) {
-            if (j < B && j >= r) out[packed_index(r, j, B)] = v[i];
-            if (j == R16) s1_part[(size_t)g * B + r] = ldexp((double)v[i], -sesc[r]);
-          }
+          if (r < B && r < 128 && j < B && j >= r) out[packed_index(r, j, B)] = v[i];
         }
       }
       if (two_tiles) {
@@ -388,10 +394,7 @@ k_syrk_tc(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shi
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int jb = 128 + j0 + i;
-            if (band < B) {
-              if (jb < B && jb >= band) out[packed_index(band, jb, B)] = v[i];
-              if (jb == R16) s1_part[(size_t)g * B + band] = ldexp((double)v[i], -sesc[band]);
-            }
+            if (band < B && jb < B && jb >= band) out[packed_index(band, jb, B)] = v[i];
           }
         }
       }
@@ -415,7 +418,7 @@ cudaError_t syrk_tc_typed(const In* cube, int64_t N, int B, float* shift, int* e
   const int stage_stride = ((kKC * B * (int)sizeof(In)) + 127) & ~127;
   const size_t fixed = 1024 + (size_t)kOpStages * 2 * kOpBytes +
                        kRows * (sizeof(float) + sizeof(int)) +
-                       2 * kRows * (sizeof(double) + 2 * sizeof(float)) + sizeof(SyncBlock);
+                       kRows * (4 * sizeof(double) + 4 * sizeof(float)) + sizeof(SyncBlock);
   int S = (int)((227 * 1024 - fixed) / stage_stride);
   S = S > kMaxStages ? kMaxStages : S;
   if (S < 2) return cudaErrorInvalidValue;

@@ -10,8 +10,8 @@
 // keeps those intermediates in a fixed array in device memory that belongs
 // to this library instead, so it neither allocates nor needs a workspace.
 //
-// The array holds kNoAllocFloats floats (B + B*k <= 232 + 232*32 = 7,656
-// floats, 30,624 bytes) and stays allocated on every GPU that loads the
+// The array holds kNoAllocFloats floats (B + B*k <= 256 + 256*32 = 8,448
+// floats, 33,792 bytes) and stays allocated on every GPU that loads the
 // library until the process exits.  All calls share it, and each call
 // rewrites every entry it reads before reading it, so nothing has to start
 // at zero -- but two calls whose work overlaps on the GPU (different streams,

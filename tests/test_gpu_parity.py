@@ -56,9 +56,12 @@ def test_paper_scene_reduced(gbpca_lib, form):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("form", FORMS)
-def test_max_bands(gbpca_lib, form):
-    skip_if_unsupported(gbpca_lib, form, 232)
-    cube = synth.linear_mixing(seed=5, rows=30, cols=40, bands=232, endmembers=8)
+@pytest.mark.parametrize("bands", [232, 255, 256])
+def test_max_bands(gbpca_lib, form, bands):
+    """Up to the largest band count: both 128-row tensor-core tiles full (256),
+    an odd count with the padding index (255), and 8-CTA Jacobi clusters."""
+    skip_if_unsupported(gbpca_lib, form, bands)
+    cube = synth.linear_mixing(seed=5, rows=30, cols=40, bands=bands, endmembers=8)
     ref = oracle.pca_fit(cube.Y, 8, tol=1e-14)
     out, info = run(gbpca_lib, cube.Y, 8, form)
     assert info["status"] == 0, info
@@ -110,7 +113,8 @@ def test_bad_arguments_are_rejected_on_the_host(gbpca_lib):
         assert e.value.status == 1
     assert lib.pca_workspace_size(1, 8, 2, 0, 1) == 0          # N < 2
     assert lib.pca_workspace_size(100, 1, 1, 0, 1) == 0        # B < 2
-    assert lib.pca_workspace_size(100, 400, 2, 0, 1) == 0      # B too large
+    assert lib.pca_workspace_size(100, 257, 2, 0, 1) == 0      # B too large
+    assert lib.pca_workspace_size(100, 256, 2, 0, 1) > 0
     with pytest.raises(g.PCAError):                            # misaligned cube pointer
         g.fit(Y.view(-1)[1:793].view(99, 8), 2, precision="p32")
 

@@ -87,11 +87,11 @@ def test_eigh_sort_ties_and_diagonal_input(gbpca_lib):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
-@pytest.mark.parametrize("bands", [96, 103, 102, 232])
+@pytest.mark.parametrize("bands", [96, 103, 102, 232, 256])
 def test_project_stage(gbpca_lib, dtype, bands):
     """Both load paths of the streamed projection: rows that are a whole number
-    of 16-byte units go through the swizzled 2-D tensor map (96, 232 bands in
-    FP32; 96, 232 in 16-bit), the others through one contiguous copy per
+    of 16-byte units go through the swizzled 2-D tensor map (96, 232, 256
+    bands in FP32; 96, 232, 256 in 16-bit), the others through one contiguous copy per
     chunk; 45 x 47 pixels leave a ragged last chunk."""
     g = gbpca_lib
     cube = synth.linear_mixing(seed=11, rows=45, cols=47, bands=bands, endmembers=6, k=6)

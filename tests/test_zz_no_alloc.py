@@ -26,7 +26,7 @@ def _inputs(cube):
 def test_noalloc_projection_matches_pca_project_on_consecutive_calls(gbpca_lib):
     g = gbpca_lib
     cubes = [synth.linear_mixing(seed=31, rows=41, cols=43, bands=96, endmembers=6, k=6),
-             synth.linear_mixing(seed=32, rows=29, cols=31, bands=232, endmembers=8, k=32),
+             synth.linear_mixing(seed=32, rows=29, cols=31, bands=256, endmembers=8, k=32),
              synth.linear_mixing(seed=33, rows=17, cols=19, bands=7, endmembers=3, k=2)]
     for cube in cubes:                       # consecutive calls share the array
         Y, mu, V = _inputs(cube)
