@@ -15,10 +15,12 @@
  *     pca_dtype.  The paper's GPU code stores bands contiguously instead
  *     (Sec. 4.2 data initialisation); this ABI takes the manycore layout of
  *     Sec. 5 (image[i*BANDS + j]).
- *   - Every pointer argument except `info` is a DEVICE pointer on the
- *     current CUDA device, allocated and owned by the caller.  The library
- *     allocates and frees nothing; all scratch lives in the caller's
- *     workspace of pca_workspace_size() bytes.
+ *   - Every pointer argument except `info` (and the host-side arrays of the
+ *     batched form) is a DEVICE pointer on the current CUDA device,
+ *     allocated and owned by the caller.  The library allocates no device
+ *     memory; all scratch lives in the caller's workspace of
+ *     pca_workspace_size() bytes.  (Only a batch plan allocates, in host
+ *     memory, together with its streams and events.)
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  All work is enqueued on it; nothing synchronises unless
  *     `info` is non-NULL, in which case the call waits for the stream and
@@ -206,6 +208,69 @@ int pca_backward(const void *cube, pca_dtype dtype, int64_t N, int B, int k, con
                  size_t ws_bytes, void *stream, pca_info *info);
 
 /*
+ * Batched form -- many independent cubes ("tiles": the tiles of a large
+ * scene, or many scenes) fitted in one go, each tile exactly as pca_fit
+ * would fit it (Algorithm 1 per tile; the paper fits one image at a time,
+ * the batching is this library's).
+ *
+ * One persistent covariance launch walks a list of (tile, pixel range)
+ * items balanced by bytes over the SMs; the Jacobi runs one thread-block
+ * cluster per tile (tiles grouped by cluster shape, the groups on forked
+ * streams); every small per-tile stage is one launch over all tiles; one
+ * persistent projection launch walks (tile, pixel range) items.
+ *
+ * pca_tile   cube [N][B] device array of the batch's dtype, 16-byte aligned;
+ *            N >= 2, 2 <= B <= 256, 1 <= k <= min(B, 32); device outputs
+ *            mu [B], eigvals [B], eigvecs [B][B] (FP64, as pca_fit) and
+ *            proj [N][k] FP32 (NULL: no projection for this tile).
+ * All tiles share dtype, precision, tol and sweeps_max (as in pca_fit).
+ *
+ * pca_batch_workspace_size  bytes of device workspace for these tiles on the
+ *     current device (0 if a tile is invalid); 256-byte aligned.
+ * pca_batch_create  checks every tile (the index of the first bad one goes
+ *     to *bad_tile when not NULL), lays out the workspace, encodes the
+ *     tensor maps of the cubes and writes the work lists and per-tile
+ *     descriptors into the workspace with one synchronous host-to-device
+ *     copy.  The plan lives in host memory and owns four CUDA streams and
+ *     five events (no device memory); the tiles' pointers and the workspace
+ *     must stay valid for its life.  Returns PCA_OK, PCA_ERR_ARG,
+ *     PCA_ERR_WORKSPACE or PCA_ERR_CUDA.
+ * pca_batch_run  enqueues the fit of every tile on `stream`.  It launches
+ *     kernels and records events only -- no allocation, copy or
+ *     synchronisation -- so it can be captured into a CUDA graph and
+ *     replayed (new input values between replays, same addresses and
+ *     shapes).  Two runs of one plan must not overlap.
+ * pca_batch_read_info  waits for `stream`, fills infos[ntiles] (NULL: not
+ *     filled) and returns the status of the first tile that is not PCA_OK
+ *     (PCA_OK if none).
+ * pca_batch_destroy  releases the plan (its streams finish their work first).
+ * pca_fit_batched  create + run + read_info (only when infos != NULL) +
+ *     destroy.
+ */
+typedef struct {
+  const void *cube;
+  int64_t N;
+  int B;
+  int k;
+  double *mu;
+  double *eigvals;
+  double *eigvecs;
+  float *proj;
+} pca_tile;
+typedef struct pca_batch pca_batch;
+size_t pca_batch_workspace_size(int ntiles, const pca_tile *tiles, pca_dtype dtype,
+                                pca_precision prec);
+int pca_batch_create(pca_batch **plan, int ntiles, const pca_tile *tiles, pca_dtype dtype,
+                     double tol, int sweeps_max, pca_precision prec, void *workspace,
+                     size_t ws_bytes, int *bad_tile);
+int pca_batch_run(pca_batch *plan, void *stream);
+int pca_batch_read_info(pca_batch *plan, void *stream, pca_info *infos);
+void pca_batch_destroy(pca_batch *plan);
+int pca_fit_batched(int ntiles, const pca_tile *tiles, pca_dtype dtype, double tol, int sweeps_max,
+                    pca_precision prec, void *workspace, size_t ws_bytes, void *stream,
+                    pca_info *infos);
+
+/*
  * Waits for `stream` and copies the device-side outcome of the last
  * pca_fit (or pca_backward) that used `workspace` into *info.  Returns
  * info->status.
@@ -222,6 +287,9 @@ int pca_version(void);
 
 /* Number of kernels one pca_fit enqueues for this precision form. */
 int pca_kernel_launches(pca_precision prec, int with_projection);
+
+/* Number of kernels one pca_batch_run of this plan enqueues. */
+int pca_batch_kernel_launches(const pca_batch *plan);
 
 /* SMs (CTAs of one cluster) the Jacobi stage occupies for B bands; 0 if B is invalid. */
 int pca_jacobi_sms(int B);

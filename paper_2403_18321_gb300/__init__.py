@@ -19,7 +19,7 @@ from dataclasses import dataclass
 
 from . import _build
 
-__all__ = ["fit", "fit_host", "workspace_size", "load", "Info", "PCAError",
+__all__ = ["fit", "fit_host", "fit_batched", "Batch", "workspace_size", "load", "Info", "PCAError",
            "PREC_P64", "PREC_P32", "PREC_MIX", "STATUS"]
 
 PREC_P64, PREC_P32, PREC_MIX = 0, 1, 2
@@ -29,7 +29,9 @@ STATUS = {0: "PCA_OK", 1: "PCA_ERR_ARG", 2: "PCA_ERR_NOCONV", 3: "PCA_ERR_NONFIN
 EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_project",
            "pca_read_info", "pca_status_string", "pca_version",
            "pca_kernel_launches", "pca_profile", "pca_profile_collect", "pca_project_noalloc",
-           "pca_jacobi_sms", "pca_backward", "pca_backward_workspace_size")
+           "pca_jacobi_sms", "pca_backward", "pca_backward_workspace_size",
+           "pca_batch_workspace_size", "pca_batch_create", "pca_batch_run", "pca_batch_read_info",
+           "pca_batch_destroy", "pca_fit_batched", "pca_batch_kernel_launches")
 STAGES = ("covariance", "cov_finalize", "jacobi", "empty", "compact", "refine", "sort_sign",
           "project")
 
@@ -48,6 +50,13 @@ class Info(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Tile(ctypes.Structure):
+    """pca_tile of include/gbpca.h."""
+    _fields_ = [("cube", ctypes.c_void_p), ("N", ctypes.c_int64), ("B", ctypes.c_int),
+                ("k", ctypes.c_int), ("mu", ctypes.c_void_p), ("eigvals", ctypes.c_void_p),
+                ("eigvecs", ctypes.c_void_p), ("proj", ctypes.c_void_p)]
 
 
 _lib = None
@@ -94,6 +103,22 @@ def load(build_if_missing: bool = False):
     lib.pca_profile.restype = i
     lib.pca_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_float), i]
     lib.pca_profile_collect.restype = i
+    TP = ctypes.POINTER(Tile)
+    lib.pca_batch_workspace_size.argtypes = [i, TP, i, i]
+    lib.pca_batch_workspace_size.restype = sz
+    lib.pca_batch_create.argtypes = [ctypes.POINTER(P), i, TP, i, d, i, i, P, sz,
+                                     ctypes.POINTER(i)]
+    lib.pca_batch_create.restype = i
+    lib.pca_batch_run.argtypes = [P, P]
+    lib.pca_batch_run.restype = i
+    lib.pca_batch_read_info.argtypes = [P, P, ctypes.POINTER(Info)]
+    lib.pca_batch_read_info.restype = i
+    lib.pca_batch_destroy.argtypes = [P]
+    lib.pca_batch_destroy.restype = None
+    lib.pca_batch_kernel_launches.argtypes = [P]
+    lib.pca_batch_kernel_launches.restype = i
+    lib.pca_fit_batched.argtypes = [i, TP, i, d, i, i, P, sz, P, ctypes.POINTER(Info)]
+    lib.pca_fit_batched.restype = i
     _lib = lib
     return lib
 
@@ -318,6 +343,96 @@ def backward(cube, mu, eigvals, eigvecs, dproj, deigvals=None, gap_eps: float = 
                              ctypes.byref(info) if info is not None else None)
     _check_rc(rc)
     return dcube
+
+
+class Batch:
+    """A plan for fitting many device cubes [N_t, B_t] (one dtype) in one go
+    (pca_batch_create).  Outputs per tile are allocated here:
+    ``results[t] = (mu, eigvals, eigvecs, proj or None)``.  ``run()`` enqueues
+    the fits on the current stream (no synchronisation, capturable into a CUDA
+    graph); ``info()`` waits and returns (worst status, per-tile info dicts)."""
+
+    def __init__(self, cubes, k, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
+                 project: bool = True):
+        import torch
+        if not cubes:
+            raise ValueError("no cubes")
+        ks = list(k) if isinstance(k, (list, tuple)) else [int(k)] * len(cubes)
+        dt = _dtype_code(cubes[0])
+        for c in cubes:
+            if not isinstance(c, torch.Tensor) or not c.is_cuda or c.dim() != 2 or not c.is_contiguous():
+                raise ValueError("every cube must be a contiguous 2-D CUDA tensor")
+            if _dtype_code(c) != dt:
+                raise TypeError("all cubes of a batch share one dtype")
+        self.cubes = list(cubes)
+        self.precision = _prec_code(precision)
+        dev = cubes[0].device
+        self.results = []
+        tiles = (Tile * len(cubes))()
+        for t, (c, kt) in enumerate(zip(cubes, ks)):
+            N, B = c.shape
+            mu = torch.empty(B, dtype=torch.float64, device=dev)
+            ev = torch.empty(B, dtype=torch.float64, device=dev)
+            V = torch.empty(B, B, dtype=torch.float64, device=dev)
+            Q = torch.empty(N, kt, dtype=torch.float32, device=dev) if project else None
+            self.results.append((mu, ev, V, Q))
+            tiles[t] = Tile(c.data_ptr(), N, B, int(kt), mu.data_ptr(), ev.data_ptr(),
+                            V.data_ptr(), Q.data_ptr() if Q is not None else None)
+        self._tiles = tiles
+        lib = load()
+        n = lib.pca_batch_workspace_size(len(cubes), tiles, dt, self.precision)
+        if n == 0:
+            bad = next(t for t in range(len(cubes))
+                       if lib.pca_batch_workspace_size(1, ctypes.byref(tiles[t]), dt,
+                                                       self.precision) == 0)
+            raise PCAError(1, f"pca_batch_workspace_size rejected tile {bad}")
+        self.workspace = Workspace(torch.empty(n + 256, dtype=torch.uint8, device=dev), n)
+        self._plan = ctypes.c_void_p()
+        bad = ctypes.c_int(-1)
+        rc = lib.pca_batch_create(ctypes.byref(self._plan), len(cubes), tiles, dt, float(tol),
+                                  int(sweeps_max), self.precision,
+                                  ctypes.c_void_p(_ws_ptr(self.workspace)), n, ctypes.byref(bad))
+        if rc != 0:
+            raise PCAError(rc, f"pca_batch_create (tile {bad.value})")
+
+    def run(self, stream=None):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(self.cubes[0].device)
+        _check_rc(load().pca_batch_run(self._plan, ctypes.c_void_p(st.cuda_stream)))
+
+    def info(self, stream=None):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(self.cubes[0].device)
+        infos = (Info * len(self.cubes))()
+        rc = load().pca_batch_read_info(self._plan, ctypes.c_void_p(st.cuda_stream), infos)
+        if rc in (1, 5, 6):
+            raise PCAError(rc, "pca_batch_read_info")
+        return rc, [i.as_dict() for i in infos]
+
+    def kernel_launches(self) -> int:
+        return int(load().pca_batch_kernel_launches(self._plan))
+
+    def close(self):
+        if self._plan:
+            load().pca_batch_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fit_batched(cubes, k, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
+                project: bool = True):
+    """Fits every cube of the list (pca_batch_*): returns (results, status, infos) with
+    results[t] = (mu, eigvals, eigvecs, proj or None)."""
+    b = Batch(cubes, k, tol, sweeps_max, precision, project)
+    b.run()
+    status, infos = b.info()
+    b.close()
+    return b.results, status, infos
 
 
 def _autograd_function():

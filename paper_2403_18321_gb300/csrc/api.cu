@@ -14,14 +14,6 @@ constexpr int kMaxSweeps = 100;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-int device_sms() {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-    return 148;
-  return sms;
-}
-
 __global__ void k_header_init(DevHeader* h, int refine_iters, float tol32) {
   DevHeader z;
   memset(&z, 0, sizeof(z));
@@ -29,6 +21,16 @@ __global__ void k_header_init(DevHeader* h, int refine_iters, float tol32) {
   z.tol_used = tol32;
   z.dummy_slot = -1;
   *h = z;
+}
+
+}  // namespace
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    return 148;
+  return sms;
 }
 
 bool args_ok(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol,
@@ -43,6 +45,8 @@ bool args_ok(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol
   if (prec == PCA_PREC_MIX && !syrk_tc_supported(B)) return false;
   return true;
 }
+
+namespace {
 
 // ---- optional per-stage CUDA-event timing (profiling entry points of gbpca.h)
 constexpr int kProfStages = 8;  // cov, cov_finalize, jacobi, (empty), compact, refine, sort, project
@@ -69,18 +73,6 @@ struct StageMark {
     g_prof.used[rec][i] = true;
   }
 };
-
-int refine_iterations(pca_precision prec) {
-  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 2 : 3);
-}
-// Lowest stop threshold of the FP32 sweeps.  MIX hands the eigen-pairs to its
-// two quadratically convergent refinement iterations once off(A) <= 1e-5
-// ||A||_F: on the scene cubes that saves two to three sweeps and leaves the
-// separated eigen-pairs more accurate than sweeping on to 2^-22 with one
-// iteration; P32 and P64 sweep to the FP32 floor.
-float stop_floor(pca_precision prec) {
-  return prec == PCA_PREC_MIX ? kMixJacobiFloor : kJacobiFloor;
-}
 
 }  // namespace
 
@@ -244,14 +236,6 @@ Ptrs carve(void* workspace, const Layout& L) {
   p.muf = reinterpret_cast<float*>(ws + L.muf);
   return p;
 }
-
-// largest first-order angle the refinement applies (pairs above it count as clustered)
-double refine_max_angle(pca_precision prec) { (void)prec; return 1.0 / 64; }
-// closing Newton-Schulz orthogonalisation steps
-int ortho_steps(pca_precision prec) { return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 2); }
-// MIX stops its FP32 sweeps on the Frobenius test (the refinement resolves what
-// the element-wise test would still demand); P32 and P64 use the element-wise test
-bool relative_stop(pca_precision prec) { return prec != PCA_PREC_MIX; }
 
 // stages 2-3 of Algorithm 1: band means and covariance in one pass over the cube
 cudaError_t run_cov(const void* cube, pca_dtype dt, int64_t N, int B, pca_precision prec,

@@ -1,0 +1,439 @@
+// batch.cu -- the batched form of include/gbpca.h: many independent cubes
+// ("tiles") fitted in one go, each as pca_fit fits one cube (Algorithm 1 per
+// tile).
+//
+// Plan (host, once): per-tile workspace regions; the covariance work list --
+// (tile, pixel range) items balanced by bytes over the CTAs of one
+// persistent launch, each item with its own partial slot; the projection
+// work list, balanced the same way; the Jacobi parameter lists, one per
+// cluster shape; the tensor maps of the cubes.  All of it is written into the
+// workspace with one copy.
+//
+// Run (per call, kernels only): header init, covariance partials (tensor
+// cores for MIX, with the guarded SIMT recomputation; SIMT for P32/P64),
+// finalisation, one Jacobi launch per cluster shape on forked streams,
+// compaction, refinement (MIX/P64), sort and sign, projection.  Every small
+// stage is one launch over all tiles (tile = blockIdx.y or .z).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gbpca {
+namespace {
+
+constexpr int kCovChunk = 32;    // pixel granularity of covariance items
+constexpr int kProjChunk = 64;   // pixel granularity of projection items
+constexpr int kBuckets = 4;      // Jacobi cluster shapes
+constexpr int kSimtItemsPerSm = 4;
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+__global__ void k_header_init_batched(TileDesc* __restrict__ T, int ntiles, int refine_iters,
+                                      float tol32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntiles) return;
+  DevHeader z;
+  memset(&z, 0, sizeof(z));
+  z.refine_iters = refine_iters;
+  z.tol_used = tol32;
+  z.dummy_slot = -1;
+  *T[i].hdr = z;
+}
+
+// Splits the tiles' chunks (weight B per chunk, i.e. bytes) into `ctas`
+// contiguous ranges of equal weight; every (tile, range) piece is one item.
+// Returns the items grouped by CTA and the number of items of every tile.
+struct Split {
+  std::vector<std::vector<CovItem>> per_cta;
+  std::vector<int> parts;
+};
+Split split_chunks(const std::vector<pca_tile>& tiles, int chunk, int ctas) {
+  Split sp;
+  const int n = (int)tiles.size();
+  sp.per_cta.assign(ctas, {});
+  sp.parts.assign(n, 0);
+  long double total = 0;
+  for (const pca_tile& t : tiles) total += (long double)((t.N + chunk - 1) / chunk) * t.B;
+  long double w0 = 0;  // weight before the current tile
+  int g = 0;
+  for (int ti = 0; ti < n; ++ti) {
+    const int64_t nch = (tiles[ti].N + chunk - 1) / chunk;
+    const int B = tiles[ti].B;
+    int64_t c = 0;
+    while (c < nch) {
+      int64_t cend = nch;
+      if (g < ctas - 1) {
+        const long double end = total * (g + 1) / ctas;  // weight at which CTA g stops
+        const long double x = (end - w0) / B;
+        cend = x <= 0 ? 0 : std::min<int64_t>(nch, (int64_t)std::ceil((double)x));
+        if (cend <= c) { ++g; continue; }
+      }
+      CovItem it;
+      it.tile = ti;
+      it.slot = sp.parts[ti]++;
+      it.p0 = c * chunk;
+      it.p1 = std::min<int64_t>(tiles[ti].N, cend * chunk);
+      sp.per_cta[g].push_back(it);
+      c = cend;
+    }
+    w0 += (long double)nch * B;
+  }
+  return sp;
+}
+
+}  // namespace
+}  // namespace gbpca
+
+using namespace gbpca;
+
+struct pca_batch {
+  int ntiles = 0;
+  pca_dtype dt = PCA_F32;
+  pca_precision prec = PCA_PREC_P32;
+  float tol32 = 0.f;
+  int maxB = 0, maxk = 0;
+  TileDesc* T = nullptr;          // device
+  DevHeader* hdrs = nullptr;      // device, [ntiles] contiguous
+  // covariance items
+  CovItem* cov_items = nullptr;
+  int* cov_off = nullptr;
+  int cov_ctas = 0, cov_nitems = 0;
+  // projection items
+  ProjItem* proj_items = nullptr;
+  int* proj_off = nullptr;
+  int proj_ctas = 0;
+  void* maps = nullptr;           // device CUtensorMap[ntiles] or null (untiled loads)
+  // Jacobi lists
+  struct Bucket {
+    void* list = nullptr;         // device
+    int count = 0;
+    size_t smem = 0;
+    std::vector<unsigned char> first;  // host copy of the first entry (launch shape)
+  } bucket[kBuckets];
+  cudaStream_t aux[kBuckets] = {};
+  cudaEvent_t fork = nullptr, join[kBuckets] = {};
+};
+
+namespace {
+
+bool tile_ok(const pca_tile& t, pca_dtype dt, pca_precision prec, double tol, int sweeps_max) {
+  if (!t.mu || !t.eigvals || !t.eigvecs) return false;
+  return args_ok(t.cube, dt, t.N, t.B, t.k, tol, sweeps_max, prec);
+}
+
+// Workspace layout of a batch.  With descs != nullptr the per-tile
+// descriptors are filled in, pointing into the workspace at `base`.
+struct BatchLayout {
+  size_t tiles, hdrs, cov_items, cov_off, proj_items, proj_off, maps, lists[kBuckets];
+  size_t total;
+  Split cov, proj;
+};
+
+BatchLayout batch_layout(const std::vector<pca_tile>& tiles, pca_dtype dt, pca_precision prec,
+                         int sms, std::vector<TileDesc>* descs, char* base) {
+  (void)dt;
+  BatchLayout L{};
+  const int n = (int)tiles.size();
+  const bool mix = prec == PCA_PREC_MIX, p64 = prec == PCA_PREC_P64;
+  const bool refine = refine_iterations(prec) > 0;
+  const int cov_ctas = mix ? sms : kSimtItemsPerSm * sms;
+  L.cov = split_chunks(tiles, kCovChunk, cov_ctas);
+  std::vector<pca_tile> ptiles;
+  std::vector<int> pmap;
+  for (int i = 0; i < n; ++i)
+    if (tiles[i].proj) { ptiles.push_back(tiles[i]); pmap.push_back(i); }
+  L.proj = split_chunks(ptiles, kProjChunk, sms);
+  for (auto& v : L.proj.per_cta)
+    for (auto& it : v) it.tile = pmap[it.tile];
+  int ncov = 0, nproj = 0;
+  for (auto& v : L.cov.per_cta) ncov += (int)v.size();
+  for (auto& v : L.proj.per_cta) nproj += (int)v.size();
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t at = o; o = al256(o + bytes); return at; };
+  L.tiles = take(sizeof(TileDesc) * n);
+  L.hdrs = take(sizeof(DevHeader) * n);
+  L.cov_items = take(sizeof(CovItem) * std::max(ncov, 1));
+  L.cov_off = take(sizeof(int) * (cov_ctas + 1));
+  L.proj_items = take(sizeof(ProjItem) * std::max(nproj, 1));
+  L.proj_off = take(sizeof(int) * (sms + 1));
+  L.maps = take(128 * (size_t)n);
+  for (int b = 0; b < kBuckets; ++b) L.lists[b] = take(jacobi_params_bytes() * n);
+  if (descs) descs->assign(n, TileDesc{});
+  for (int i = 0; i < n; ++i) {
+    const pca_tile& t = tiles[i];
+    const int B = t.B, Bp = round_even(B), k = t.k;
+    const int parts = L.cov.parts[i];
+    const size_t BB = (size_t)B * B;
+    TileDesc d{};
+    auto at = [&](size_t off) -> void* { return base ? base + off : nullptr; };
+    d.cube = t.cube;
+    d.N = t.N;
+    d.B = B;
+    d.k = k;
+    d.mu = t.mu;
+    d.eigvals = t.eigvals;
+    d.eigvecs = t.eigvecs;
+    d.proj = t.proj;
+    d.hdr = static_cast<DevHeader*>(at(L.hdrs + sizeof(DevHeader) * i));
+    d.parts = parts;
+    d.shift = static_cast<float*>(at(take(sizeof(float) * B)));
+    d.escale = static_cast<int*>(at(take(sizeof(int) * B)));
+    d.s1p = static_cast<double*>(at(take(sizeof(double) * parts * B)));
+    d.s2p = at(take((p64 ? 8 : 4) * (size_t)parts * (B * (B + 1) / 2)));
+    d.dvec = static_cast<double*>(at(take(sizeof(double) * B)));
+    d.C = static_cast<double*>(at(take(sizeof(double) * BB)));
+    d.cdf = refine ? static_cast<float2*>(at(take(sizeof(float2) * BB))) : nullptr;
+    d.rank = static_cast<int*>(at(take(sizeof(int) * B)));
+    d.sgn = static_cast<double*>(at(take(sizeof(double) * B)));
+    d.diag32 = static_cast<float*>(at(take(sizeof(float) * Bp)));
+    d.v32 = static_cast<float*>(at(take(sizeof(float) * (size_t)Bp * Bp)));
+    d.lam = static_cast<double*>(at(take(sizeof(double) * B)));
+    d.vc = static_cast<float2*>(at(take(sizeof(float2) * BB)));
+    if (refine) {
+      d.w = static_cast<float2*>(at(take(sizeof(float2) * BB)));
+      d.s = static_cast<float2*>(at(take(sizeof(float2) * BB)));
+      d.g = static_cast<float2*>(at(take(sizeof(float2) * BB)));
+      d.e = static_cast<float2*>(at(take(sizeof(float2) * BB)));
+    }
+    d.vk = static_cast<float*>(at(take(sizeof(float) * (size_t)B * k)));
+    d.muf = static_cast<float*>(at(take(sizeof(float) * B)));
+    if (descs) (*descs)[i] = d;
+  }
+  L.total = o;
+  return L;
+}
+
+std::vector<pca_tile> as_vector(int ntiles, const pca_tile* tiles) {
+  return std::vector<pca_tile>(tiles, tiles + ntiles);
+}
+
+#define GB_CK(x)                                   \
+  do {                                             \
+    if ((x) != cudaSuccess) return PCA_ERR_CUDA;   \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+size_t pca_batch_workspace_size(int ntiles, const pca_tile* tiles, pca_dtype dtype,
+                                pca_precision prec) {
+  static const float kDummy[4] = {0.f, 0.f, 0.f, 0.f};
+  if (ntiles < 1 || !tiles) return 0;
+  std::vector<pca_tile> v = as_vector(ntiles, tiles);
+  for (pca_tile& t : v) {
+    if (!args_ok(kDummy, dtype, t.N, t.B, t.k, 1.0, 1, prec)) return 0;
+    t.cube = kDummy;
+  }
+  return batch_layout(v, dtype, prec, device_sms(), nullptr, nullptr).total;
+}
+
+int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dtype dtype,
+                     double tol, int sweeps_max, pca_precision prec, void* workspace,
+                     size_t ws_bytes, int* bad_tile) {
+  if (!plan) return PCA_ERR_ARG;
+  *plan = nullptr;
+  if (ntiles < 1 || !tiles) return PCA_ERR_ARG;
+  for (int i = 0; i < ntiles; ++i)
+    if (!tile_ok(tiles[i], dtype, prec, tol, sweeps_max)) {
+      if (bad_tile) *bad_tile = i;
+      return PCA_ERR_ARG;
+    }
+  if (!workspace || ((uintptr_t)workspace) % 256 != 0) return PCA_ERR_WORKSPACE;
+  const std::vector<pca_tile> v = as_vector(ntiles, tiles);
+  const int sms = device_sms();
+  char* ws = static_cast<char*>(workspace);
+  std::vector<TileDesc> descs;
+  const BatchLayout L = batch_layout(v, dtype, prec, sms, &descs, ws);
+  if (ws_bytes < L.total) return PCA_ERR_WORKSPACE;
+
+  pca_batch* b = new (std::nothrow) pca_batch;
+  if (!b) return PCA_ERR_ARG;
+  b->ntiles = ntiles;
+  b->dt = dtype;
+  b->prec = prec;
+  b->tol32 = std::max((float)tol, stop_floor(prec));
+  for (const pca_tile& t : v) { b->maxB = std::max(b->maxB, t.B); b->maxk = std::max(b->maxk, t.k); }
+  b->T = reinterpret_cast<TileDesc*>(ws + L.tiles);
+  b->hdrs = reinterpret_cast<DevHeader*>(ws + L.hdrs);
+
+  // the table region [0, end of the Jacobi lists) is built on the host and copied once
+  const size_t table = L.lists[kBuckets - 1] + jacobi_params_bytes() * ntiles;
+  std::vector<unsigned char> img(table, 0);
+  std::memcpy(img.data() + L.tiles, descs.data(), sizeof(TileDesc) * ntiles);
+  {  // covariance items, CTA by CTA
+    std::vector<CovItem> items;
+    std::vector<int> off(1, 0);
+    for (const auto& c : L.cov.per_cta) {
+      items.insert(items.end(), c.begin(), c.end());
+      off.push_back((int)items.size());
+    }
+    std::memcpy(img.data() + L.cov_items, items.data(), sizeof(CovItem) * items.size());
+    std::memcpy(img.data() + L.cov_off, off.data(), sizeof(int) * off.size());
+    b->cov_items = reinterpret_cast<CovItem*>(ws + L.cov_items);
+    b->cov_off = reinterpret_cast<int*>(ws + L.cov_off);
+    b->cov_ctas = (int)L.cov.per_cta.size();
+    b->cov_nitems = (int)items.size();
+  }
+  {  // projection items (64-pixel chunks), CTA by CTA
+    std::vector<ProjItem> items;
+    std::vector<int> off(1, 0);
+    for (const auto& c : L.proj.per_cta) {
+      for (const CovItem& it : c) {
+        ProjItem p{};
+        p.tile = it.tile;
+        p.c0 = it.p0 / kProjChunk;
+        p.c1 = (it.p1 + kProjChunk - 1) / kProjChunk;
+        items.push_back(p);
+      }
+      off.push_back((int)items.size());
+    }
+    std::memcpy(img.data() + L.proj_items, items.data(), sizeof(ProjItem) * items.size());
+    std::memcpy(img.data() + L.proj_off, off.data(), sizeof(int) * off.size());
+    b->proj_items = reinterpret_cast<ProjItem*>(ws + L.proj_items);
+    b->proj_off = reinterpret_cast<int*>(ws + L.proj_off);
+    b->proj_ctas = items.empty() ? 0 : (int)L.proj.per_cta.size();
+  }
+  {  // tensor maps: the tiled load when every projected cube qualifies
+    bool all = true;
+    for (int i = 0; i < ntiles && all; ++i)
+      if (v[i].proj) all = encode_cube_map(dtype, v[i].cube, v[i].N, v[i].B, img.data() + L.maps + 128 * (size_t)i);
+    b->maps = all ? ws + L.maps : nullptr;
+  }
+  {  // Jacobi lists: one per cluster shape, largest matrices first
+    std::vector<int> order(ntiles);
+    for (int i = 0; i < ntiles; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return v[a].B > v[c].B; });
+    const size_t pb = jacobi_params_bytes();
+    for (int i : order) {
+      const int bk = jacobi_bucket(v[i].B);
+      pca_batch::Bucket& bu = b->bucket[bk];
+      unsigned char* dst = img.data() + L.lists[bk] + pb * bu.count;
+      const size_t smem = jacobi_fill_params(dst, descs[i].C, v[i].B, b->tol32, sweeps_max,
+                                             relative_stop(prec), descs[i].diag32, descs[i].v32,
+                                             descs[i].hdr);
+      bu.smem = std::max(bu.smem, smem);
+      if (bu.count == 0) bu.first.assign(dst, dst + pb);
+      ++bu.count;
+    }
+    for (int bk = 0; bk < kBuckets; ++bk) b->bucket[bk].list = ws + L.lists[bk];
+  }
+  bool ok = cudaMemcpy(ws, img.data(), table, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int bk = 0; bk < kBuckets && ok; ++bk) {
+    ok = cudaStreamCreateWithFlags(&b->aux[bk], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->join[bk], cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) {
+    pca_batch_destroy(b);
+    return PCA_ERR_CUDA;
+  }
+  *plan = b;
+  return PCA_OK;
+}
+
+int pca_batch_run(pca_batch* b, void* stream) {
+  if (!b) return PCA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = b->ntiles, maxB = b->maxB;
+  const pca_precision prec = b->prec;
+  const int iters = refine_iterations(prec), ortho = ortho_steps(prec);
+  k_header_init_batched<<<(n + 127) / 128, 128, 0, st>>>(b->T, n, iters, b->tol32);
+  GB_CK(cudaGetLastError());
+  // stages 2-3: band means and covariance
+  if (prec == PCA_PREC_MIX) {
+    GB_CK(launch_syrk_tc_grouped(b->T, b->cov_items, b->cov_off, b->cov_ctas, maxB, b->dt, st));
+    GB_CK(launch_syrk_simt_grouped(b->T, b->cov_items, b->cov_nitems, maxB, b->dt, false, true, st));
+  } else {
+    GB_CK(launch_syrk_simt_grouped(b->T, b->cov_items, b->cov_nitems, maxB, b->dt,
+                                   prec == PCA_PREC_P64, false, st));
+  }
+  GB_CK(launch_cov_finalize_batched(b->T, n, maxB, prec == PCA_PREC_P64, prec == PCA_PREC_MIX, st));
+  // stage 4: one Jacobi launch per cluster shape, side by side
+  GB_CK(cudaEventRecord(b->fork, st));
+  for (int bk = 0; bk < kBuckets; ++bk) {
+    pca_batch::Bucket& bu = b->bucket[bk];
+    if (bu.count == 0) continue;
+    GB_CK(cudaStreamWaitEvent(b->aux[bk], b->fork, 0));
+    GB_CK(launch_jacobi_cluster_list(bu.first.data(), bu.list, bu.count, bu.smem, b->aux[bk]));
+    GB_CK(cudaEventRecord(b->join[bk], b->aux[bk]));
+  }
+  for (int bk = 0; bk < kBuckets; ++bk)
+    if (b->bucket[bk].count > 0) GB_CK(cudaStreamWaitEvent(st, b->join[bk], 0));
+  GB_CK(launch_compact_batched(b->T, n, maxB, st));
+  bool in_w = false;  // V alternates between vc and w
+  if (iters > 0) GB_CK(launch_to_df_batched(b->T, n, maxB, st));
+  for (int it = 0; it < iters; ++it, in_w = !in_w)
+    GB_CK(launch_refine_batched(b->T, n, maxB, in_w, refine_max_angle(prec), st));
+  for (int it = 0; it < ortho; ++it, in_w = !in_w)
+    GB_CK(launch_orthonormalize_batched(b->T, n, maxB, in_w, st));
+  GB_CK(launch_sort_sign_batched(b->T, n, maxB, in_w, st));
+  // stages 5-6: projection
+  GB_CK(launch_project_grouped(b->T, b->maps, b->proj_items, b->proj_off, b->proj_ctas, maxB,
+                               b->maxk, b->dt, st));
+  return PCA_OK;
+}
+
+int pca_batch_read_info(pca_batch* b, void* stream, pca_info* infos) {
+  if (!b) return PCA_ERR_ARG;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return PCA_ERR_CUDA;
+  std::vector<DevHeader> h(b->ntiles);
+  if (cudaMemcpy(h.data(), b->hdrs, sizeof(DevHeader) * b->ntiles, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return PCA_ERR_CUDA;
+  int worst = PCA_OK;
+  for (int i = 0; i < b->ntiles; ++i) {
+    if (worst == PCA_OK && h[i].status != PCA_OK) worst = h[i].status;
+    if (!infos) continue;
+    pca_info& o = infos[i];
+    o.status = h[i].status;
+    o.sweeps = h[i].sweeps;
+    o.refine_iters = h[i].refine_iters;
+    o.steps = h[i].steps;
+    o.off_rel = h[i].off_rel;
+    o.tol_used = h[i].tol_used;
+    o.refine_res = h[i].refine_res;
+    o.cov_fallback = h[i].cov_range != 0 ? 1 : 0;
+  }
+  return worst;
+}
+
+int pca_batch_kernel_launches(const pca_batch* b) {
+  if (!b) return 0;
+  const int iters = refine_iterations(b->prec), ortho = ortho_steps(b->prec);
+  int n = 1 + (b->prec == PCA_PREC_MIX ? 2 : 1) + 2;  // header, covariance, finalisation
+  for (int bk = 0; bk < kBuckets; ++bk) n += b->bucket[bk].count > 0 ? 1 : 0;
+  n += 1;                                              // compaction
+  n += (iters > 0 ? 1 : 0) + 6 * iters + 3 * ortho;    // refinement
+  n += 2;                                              // rank/sign, scatter
+  n += b->proj_ctas > 0 ? 1 : 0;
+  return n;
+}
+
+void pca_batch_destroy(pca_batch* b) {
+  if (!b) return;
+  for (int bk = 0; bk < kBuckets; ++bk) {
+    if (b->aux[bk]) cudaStreamDestroy(b->aux[bk]);
+    if (b->join[bk]) cudaEventDestroy(b->join[bk]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+int pca_fit_batched(int ntiles, const pca_tile* tiles, pca_dtype dtype, double tol, int sweeps_max,
+                    pca_precision prec, void* workspace, size_t ws_bytes, void* stream,
+                    pca_info* infos) {
+  pca_batch* b = nullptr;
+  int r = pca_batch_create(&b, ntiles, tiles, dtype, tol, sweeps_max, prec, workspace, ws_bytes,
+                           nullptr);
+  if (r != PCA_OK) return r;
+  r = pca_batch_run(b, stream);
+  if (r == PCA_OK && infos) r = pca_batch_read_info(b, stream, infos);
+  pca_batch_destroy(b);
+  return r;
+}
+
+}  // extern "C"

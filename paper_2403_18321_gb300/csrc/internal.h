@@ -53,6 +53,79 @@ __host__ __device__ inline int64_t packed_index(int i, int j, int B) {  // i <= 
   return (int64_t)j * (j + 1) / 2 + i;
 }
 
+// ---------------------------------------------------------------- precision policy
+// FP64 refinement iterations after the FP32 sweeps.
+inline int refine_iterations(pca_precision prec) {
+  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 2 : 3);
+}
+// Lowest stop threshold of the FP32 sweeps.  MIX hands the eigen-pairs to its
+// two quadratically convergent refinement iterations once off(A) <= 1e-5
+// ||A||_F: on the scene cubes that saves two to three sweeps and leaves the
+// separated eigen-pairs more accurate than sweeping on to 2^-22 with one
+// iteration; P32 and P64 sweep to the FP32 floor.
+inline float stop_floor(pca_precision prec) {
+  return prec == PCA_PREC_MIX ? kMixJacobiFloor : kJacobiFloor;
+}
+// Largest first-order angle the refinement applies (pairs above it count as clustered).
+inline double refine_max_angle(pca_precision prec) { (void)prec; return 1.0 / 64; }
+// Closing Newton-Schulz orthogonalisation steps.
+inline int ortho_steps(pca_precision prec) {
+  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 2);
+}
+// MIX stops its FP32 sweeps on the Frobenius test (the refinement resolves what
+// the element-wise test would still demand); P32 and P64 use the element-wise test.
+inline bool relative_stop(pca_precision prec) { return prec != PCA_PREC_MIX; }
+
+// Argument checks shared by the entry points; SMs of the current device.
+bool args_ok(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol,
+             int sweeps_max, pca_precision prec);
+int device_sms();
+
+// ---------------------------------------------------------------- batched form
+// One tile of a batch: its input, the caller's outputs and its workspace
+// regions.  Device-resident, written once when the batch is planned.
+struct TileDesc {
+  const void* cube;    // [N][B], 16-byte aligned
+  int64_t N;
+  int B, k;
+  double* mu;          // caller outputs
+  double* eigvals;
+  double* eigvecs;
+  float* proj;         // nullable
+  DevHeader* hdr;      // workspace
+  float* shift;
+  int* escale;
+  double* s1p;         // [parts][B]
+  void* s2p;           // [parts][B(B+1)/2], FP32 or FP64
+  int parts;           // covariance partial slots of this tile
+  int pad0;
+  double* dvec;
+  double* C;
+  float2* cdf;
+  int* rank;
+  double* sgn;
+  float* diag32;
+  float* v32;
+  double* lam;
+  float2* vc;
+  float2* w;
+  float2* s;
+  float2* g;
+  float2* e;
+  float* vk;
+  float* muf;
+};
+// Pixels [p0, p1) of one tile and the partial slot they are summed into.
+struct CovItem {
+  int tile, slot;
+  int64_t p0, p1;
+};
+// 64-pixel chunks [c0, c1) of one tile.
+struct ProjItem {
+  int tile, pad;
+  int64_t c0, c1;
+};
+
 // ---------------------------------------------------------------- launchers
 // All return cudaError_t of the launch; none synchronises.
 
@@ -152,5 +225,48 @@ cudaError_t launch_backward(const void* cube, pca_dtype dt, int64_t N, int B, in
                             const double* mu, const double* lam, const double* V,
                             const float* dq, const double* dlam, double gap_eps, float* dY,
                             const BwdPtrs& w, DevHeader* hdr, cudaStream_t st);
+
+// ---- batched launchers: tile t of T[] is blockIdx.y (or an item's tile)
+cudaError_t launch_header_init_batched(TileDesc* T, int ntiles, int refine_iters, float tol32,
+                                       cudaStream_t st);
+// SIMT partials of every item (grid: items x band-tile groups of the largest B).
+// guarded: a tile is skipped unless its hdr->cov_range is set, and a run then
+// zeroes its escale.
+cudaError_t launch_syrk_simt_grouped(const TileDesc* T, const CovItem* items, int nitems,
+                                     int maxB, pca_dtype dt, bool fp64, bool guarded,
+                                     cudaStream_t st);
+// Tensor-core partials: CTA g walks items [cta_items[g], cta_items[g+1]).
+cudaError_t launch_syrk_tc_grouped(const TileDesc* T, const CovItem* items, const int* cta_items,
+                                   int ctas, int maxB, pca_dtype dt, cudaStream_t st);
+cudaError_t launch_cov_finalize_batched(const TileDesc* T, int ntiles, int maxB, bool fp64,
+                                        bool escaled, cudaStream_t st);
+// Jacobi parameter lists: matrices of one bucket (equal cluster shape) run in
+// one launch, one cluster each.
+int jacobi_bucket(int B);  // 0..3
+size_t jacobi_params_bytes();
+// Writes the parameters of one matrix to dst (host); returns the dynamic
+// shared memory its cluster needs.
+size_t jacobi_fill_params(void* dst, const double* C, int B, float tol32, int sweeps_max,
+                          bool relative_stop, float* diag32, float* v32, DevHeader* hdr);
+cudaError_t launch_jacobi_cluster_list(const void* host_first, const void* dev_list, int count,
+                                       size_t smem, cudaStream_t st);
+cudaError_t launch_compact_batched(const TileDesc* T, int ntiles, int maxB, cudaStream_t st);
+cudaError_t launch_to_df_batched(const TileDesc* T, int ntiles, int maxB, cudaStream_t st);
+// One refinement iteration / orthogonalisation step of every tile; `flip`
+// selects the direction of the V double buffer (false: vc -> w).
+cudaError_t launch_refine_batched(const TileDesc* T, int ntiles, int maxB, bool flip,
+                                  double max_angle, cudaStream_t st);
+cudaError_t launch_orthonormalize_batched(const TileDesc* T, int ntiles, int maxB, bool flip,
+                                          cudaStream_t st);
+cudaError_t launch_sort_sign_batched(const TileDesc* T, int ntiles, int maxB, bool final_in_w,
+                                     cudaStream_t st);
+// Streamed projection of every item; maps (nullable, 64-byte aligned, one per
+// tile) are 2-D tensor maps of the cubes for the swizzled tiled load.
+// Encodes the 2-D tensor map (CUtensorMap, 128 bytes, 64-byte aligned) of a cube
+// for the tiled projection load; false when the cube does not qualify.
+bool encode_cube_map(pca_dtype dt, const void* cube, int64_t N, int B, void* map);
+cudaError_t launch_project_grouped(const TileDesc* T, const void* maps, const ProjItem* items,
+                                   const int* cta_items, int ctas, int maxB, int maxk,
+                                   pca_dtype dt, cudaStream_t st);
 
 }  // namespace gbpca

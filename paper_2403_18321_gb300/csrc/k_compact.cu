@@ -9,10 +9,12 @@ namespace gbpca {
 
 namespace {
 
-// lam[c], vc[i][c] for the real rows i < B and the real slots (padding slot dropped).
-__global__ void k_compact(const float* __restrict__ diag32, const float* __restrict__ v32, int B,
-                          DevHeader* __restrict__ hdr, double* __restrict__ lam,
-                          float2* __restrict__ vc) {
+// lam[c], vc[i][c] for the real rows i < B and the real slots (padding slot
+// dropped); one CTA per row i.
+__device__ __forceinline__ void compact_row(int i, const float* __restrict__ diag32,
+                                            const float* __restrict__ v32, int B,
+                                            DevHeader* __restrict__ hdr, double* __restrict__ lam,
+                                            float2* __restrict__ vc) {
   const int Bp = B + (B & 1);
   __shared__ int s_dummy;
   if (threadIdx.x == 0) s_dummy = -1;
@@ -24,7 +26,6 @@ __global__ void k_compact(const float* __restrict__ diag32, const float* __restr
   }
   __syncthreads();
   const int dmy = s_dummy;
-  const int i = blockIdx.x;  // row of V
   for (int j = threadIdx.x; j < Bp; j += blockDim.x) {
     if (j == dmy) continue;
     const int c = (dmy >= 0 && j > dmy) ? j - 1 : j;
@@ -34,12 +35,28 @@ __global__ void k_compact(const float* __restrict__ diag32, const float* __restr
   }
   if (i == 0 && threadIdx.x == 0) hdr->dummy_slot = dmy;
 }
+__global__ void k_compact(const float* __restrict__ diag32, const float* __restrict__ v32, int B,
+                          DevHeader* __restrict__ hdr, double* __restrict__ lam,
+                          float2* __restrict__ vc) {
+  compact_row(blockIdx.x, diag32, v32, B, hdr, lam, vc);
+}
+__global__ void k_compact_batched(const TileDesc* __restrict__ T) {
+  const TileDesc& t = T[blockIdx.y];
+  if ((int)blockIdx.x >= t.B) return;
+  compact_row(blockIdx.x, t.diag32, t.v32, t.B, t.hdr, t.lam, t.vc);
+}
 
 }  // namespace
 
 cudaError_t launch_compact(const float* diag32, const float* v32, int B, DevHeader* hdr,
                            double* lam, float2* vc, cudaStream_t st) {
   k_compact<<<B, 256, 0, st>>>(diag32, v32, B, hdr, lam, vc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_batched(const TileDesc* T, int ntiles, int maxB, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  k_compact_batched<<<dim3(maxB, ntiles), 256, 0, st>>>(T);
   return cudaGetLastError();
 }
 

@@ -24,33 +24,32 @@ constexpr int kChunk = 32;  // pixels staged in shared memory per iteration
 template <typename In>
 __device__ __forceinline__ float ld(const In* p) { return to_f32<In>(*p); }
 
-// Grid: x = partial slot (pixel range), y = tile group.  Each thread owns one
-// TM x TM tile of the upper block-triangle of S2.
+// One CTA: pixels [n0, n1) of the cube into partial slot g (S1 when grp is
+// 0), band-tile group grp.  Each thread owns one TM x TM tile of the upper
+// block-triangle of S2.
 template <typename In, typename Acc, int TM>
-__global__ void __launch_bounds__(kSyrkThreads)
-k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, int Bt, int ntiles,
-            float* __restrict__ shift_out, double* __restrict__ s1_part,
-            Acc* __restrict__ s2_part, int s2_elems, const int* __restrict__ guard,
-            int* __restrict__ escale) {
-  // guarded form: the re-computation after an out-of-range tensor-core pass
-  if (guard != nullptr && *(volatile const int*)guard == 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void syrk_simt_cta(const In* __restrict__ cube, int B, int64_t n0,
+                                              int64_t n1, int g, int grp,
+                                              float* __restrict__ shift_out,
+                                              double* __restrict__ s1_part,
+                                              Acc* __restrict__ s2_part,
+                                              int* __restrict__ escale, unsigned char* smem_raw) {
+  const int Bt = (B + TM - 1) / TM, ntiles = Bt * (Bt + 1) / 2;
+  const int s2_elems = B * (B + 1) / 2;
   const int Bpad = Bt * TM;
   Acc* xs = reinterpret_cast<Acc*>(smem_raw);                   // [kChunk][Bpad]
   float* sh = reinterpret_cast<float*>(xs + kChunk * Bpad);     // [Bpad] shift
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int G = gridDim.x, g = blockIdx.x;
-  const int64_t n0 = N * g / G, n1 = N * (g + 1) / G;
 
   for (int b = tid; b < Bpad; b += kSyrkThreads) sh[b] = b < B ? ld(cube + b) : 0.f;
-  if (g == 0 && blockIdx.y == 0)
+  if (g == 0 && grp == 0)
     for (int b = tid; b < B; b += kSyrkThreads) {
       shift_out[b] = ld(cube + b);
       if (escale != nullptr) escale[b] = 0;
     }
 
   // tile of this thread: enumerate the upper block-triangle row by row
-  const int t = blockIdx.y * kSyrkThreads + tid;
+  const int t = grp * kSyrkThreads + tid;
   int ti = -1, tj = -1;
   if (t < ntiles) {
     int rem = t;
@@ -76,7 +75,7 @@ k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, int Bt, int ntiles,
         xs[p * Bpad + b] = (p < cp && b < B) ? Acc(ld(row + b)) - Acc(sh[b]) : Acc(0);
     }
     __syncthreads();
-    if (blockIdx.y == 0 && tid < B) {
+    if (grp == 0 && tid < B) {
       Acc cs = Acc(0);
       for (int p = 0; p < cp; ++p) cs += xs[p * Bpad + tid];
       s1 += (double)cs;
@@ -97,7 +96,7 @@ k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, int Bt, int ntiles,
     __syncthreads();
   }
 
-  if (blockIdx.y == 0 && tid < B) s1_part[(size_t)g * B + tid] = s1;
+  if (grp == 0 && tid < B) s1_part[(size_t)g * B + tid] = s1;
   if (ti >= 0) {
     Acc* out = s2_part + (size_t)g * s2_elems;
 #pragma unroll
@@ -112,11 +111,40 @@ k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, int Bt, int ntiles,
   }
 }
 
+// Grid: x = partial slot (pixel range), y = band-tile group.
+template <typename In, typename Acc, int TM>
+__global__ void __launch_bounds__(kSyrkThreads)
+k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shift_out,
+            double* __restrict__ s1_part, Acc* __restrict__ s2_part,
+            const int* __restrict__ guard, int* __restrict__ escale) {
+  // guarded form: the re-computation after an out-of-range tensor-core pass
+  if (guard != nullptr && *(volatile const int*)guard == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int G = gridDim.x, g = blockIdx.x;
+  syrk_simt_cta<In, Acc, TM>(cube, B, N * g / G, N * (g + 1) / G, g, blockIdx.y, shift_out,
+                             s1_part, s2_part, escale, smem_raw);
+}
+
+// Grid: x = item, y = band-tile group (groups beyond the item's tile return).
+template <typename In, typename Acc, int TM>
+__global__ void __launch_bounds__(kSyrkThreads)
+k_syrk_simt_grouped(const TileDesc* __restrict__ T, const CovItem* __restrict__ items,
+                    int guarded) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const CovItem it = items[blockIdx.x];
+  const TileDesc& t = T[it.tile];
+  const int B = t.B, Bt = (B + TM - 1) / TM;
+  if ((int)blockIdx.y * kSyrkThreads >= Bt * (Bt + 1) / 2) return;
+  if (guarded && *(volatile const int*)&t.hdr->cov_range == 0) return;
+  syrk_simt_cta<In, Acc, TM>(static_cast<const In*>(t.cube), B, it.p0, it.p1, it.slot, blockIdx.y,
+                             t.shift, t.s1p, static_cast<Acc*>(t.s2p), guarded ? t.escale : nullptr,
+                             smem_raw);
+}
+
 template <typename In>
 cudaError_t syrk_simt_typed(const In* cube, int64_t N, int B, bool fp64, float* shift,
                             double* s1_part, void* s2_part, int partials, cudaStream_t st,
                             const int* guard, int* escale) {
-  const int s2_elems = B * (B + 1) / 2;
   if (fp64) {
     constexpr int TM = 4;
     const int Bt = (B + TM - 1) / TM, ntiles = Bt * (Bt + 1) / 2;
@@ -124,8 +152,8 @@ cudaError_t syrk_simt_typed(const In* cube, int64_t N, int B, bool fp64, float* 
     const size_t smem = (size_t)kChunk * Bt * TM * sizeof(double) + Bt * TM * sizeof(float);
     auto kern = k_syrk_simt<In, double, TM>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(
-        cube, N, B, Bt, ntiles, shift, s1_part, (double*)s2_part, s2_elems, guard, escale);
+    kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(cube, N, B, shift, s1_part,
+                                                             (double*)s2_part, guard, escale);
   } else {
     constexpr int TM = 8;
     const int Bt = (B + TM - 1) / TM, ntiles = Bt * (Bt + 1) / 2;
@@ -133,18 +161,44 @@ cudaError_t syrk_simt_typed(const In* cube, int64_t N, int B, bool fp64, float* 
     const size_t smem = (size_t)kChunk * Bt * TM * sizeof(float) + Bt * TM * sizeof(float);
     auto kern = k_syrk_simt<In, float, TM>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(
-        cube, N, B, Bt, ntiles, shift, s1_part, (float*)s2_part, s2_elems, guard, escale);
+    kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(cube, N, B, shift, s1_part,
+                                                             (float*)s2_part, guard, escale);
+  }
+  return cudaGetLastError();
+}
+
+template <typename In>
+cudaError_t syrk_simt_grouped_typed(const TileDesc* T, const CovItem* items, int nitems, int maxB,
+                                    bool fp64, bool guarded, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  if (fp64) {
+    constexpr int TM = 4;
+    const int Bt = (maxB + TM - 1) / TM, groups = (Bt * (Bt + 1) / 2 + kSyrkThreads - 1) / kSyrkThreads;
+    const size_t smem = (size_t)kChunk * Bt * TM * sizeof(double) + Bt * TM * sizeof(float);
+    auto kern = k_syrk_simt_grouped<In, double, TM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(nitems, groups), kSyrkThreads, smem, st>>>(T, items, guarded ? 1 : 0);
+  } else {
+    constexpr int TM = 8;
+    const int Bt = (maxB + TM - 1) / TM, groups = (Bt * (Bt + 1) / 2 + kSyrkThreads - 1) / kSyrkThreads;
+    const size_t smem = (size_t)kChunk * Bt * TM * sizeof(float) + Bt * TM * sizeof(float);
+    auto kern = k_syrk_simt_grouped<In, float, TM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(nitems, groups), kSyrkThreads, smem, st>>>(T, items, guarded ? 1 : 0);
   }
   return cudaGetLastError();
 }
 
 // d[b] = (sum_g S1_g[b]) / N, one warp per band (FP64 adds spread over SMs).
-__global__ void k_s1_reduce(const double* __restrict__ s1_part, int partials, int B, int64_t N,
-                            const float* __restrict__ shift, double* __restrict__ dvec,
-                            double* __restrict__ mu, float* __restrict__ mu_f,
-                            DevHeader* __restrict__ hdr) {
-  const int b = blockIdx.x, lane = threadIdx.x;
+__device__ __forceinline__ void s1_reduce_band(int b, const double* __restrict__ s1_part,
+                                               int partials, int B, int64_t N,
+                                               const float* __restrict__ shift,
+                                               double* __restrict__ dvec, double* __restrict__ mu,
+                                               float* __restrict__ mu_f,
+                                               DevHeader* __restrict__ hdr) {
+  const int lane = threadIdx.x;
   double s = 0.0;
   for (int g = lane; g < partials; g += 32) s += s1_part[(size_t)g * B + b];
   s = warp_sum(s);
@@ -157,6 +211,17 @@ __global__ void k_s1_reduce(const double* __restrict__ s1_part, int partials, in
     if (!isfinite(m)) { atomicOr(&hdr->nonfinite, 1); set_status(hdr, PCA_ERR_NONFINITE); }
   }
 }
+__global__ void k_s1_reduce(const double* __restrict__ s1_part, int partials, int B, int64_t N,
+                            const float* __restrict__ shift, double* __restrict__ dvec,
+                            double* __restrict__ mu, float* __restrict__ mu_f,
+                            DevHeader* __restrict__ hdr) {
+  s1_reduce_band(blockIdx.x, s1_part, partials, B, N, shift, dvec, mu, mu_f, hdr);
+}
+__global__ void k_s1_reduce_batched(const TileDesc* __restrict__ T) {
+  const TileDesc& t = T[blockIdx.y];
+  if ((int)blockIdx.x >= t.B) return;
+  s1_reduce_band(blockIdx.x, t.s1p, t.parts, t.B, t.N, t.shift, t.dvec, t.mu, t.muf, t.hdr);
+}
 
 // C_ij = (S2_ij - N d_i d_j) / (N - 1), S2 summed over the partials.  One
 // CTA per 32 consecutive packed entries: lane = entry (coalesced reads of
@@ -167,13 +232,15 @@ __global__ void k_s1_reduce(const double* __restrict__ s1_part, int partials, in
 constexpr int kFinWarps = 8;
 
 template <typename Acc>
-__global__ void __launch_bounds__(kFinWarps * 32)
-k_cov_finalize(const Acc* __restrict__ s2_part, int partials, int s2_elems, int B, int64_t N,
-               const double* __restrict__ dvec, double* __restrict__ C,
-               DevHeader* __restrict__ hdr, const int* __restrict__ escale) {
+__device__ __forceinline__ void cov_finalize_block(int blk, const Acc* __restrict__ s2_part,
+                                                   int partials, int s2_elems, int B, int64_t N,
+                                                   const double* __restrict__ dvec,
+                                                   double* __restrict__ C,
+                                                   DevHeader* __restrict__ hdr,
+                                                   const int* __restrict__ escale) {
   __shared__ double part[kFinWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t e = (int64_t)blk * 32 + lane;
   double sum = 0.0;
   if (e < s2_elems) {
     if constexpr (sizeof(Acc) == 4) {
@@ -208,6 +275,22 @@ k_cov_finalize(const Acc* __restrict__ s2_part, int partials, int s2_elems, int 
     if (!isfinite(c)) { atomicOr(&hdr->nonfinite, 1); set_status(hdr, PCA_ERR_NONFINITE); }
   }
 }
+template <typename Acc>
+__global__ void __launch_bounds__(kFinWarps * 32)
+k_cov_finalize(const Acc* __restrict__ s2_part, int partials, int s2_elems, int B, int64_t N,
+               const double* __restrict__ dvec, double* __restrict__ C,
+               DevHeader* __restrict__ hdr, const int* __restrict__ escale) {
+  cov_finalize_block<Acc>(blockIdx.x, s2_part, partials, s2_elems, B, N, dvec, C, hdr, escale);
+}
+template <typename Acc>
+__global__ void __launch_bounds__(kFinWarps * 32)
+k_cov_finalize_batched(const TileDesc* __restrict__ T, int escaled) {
+  const TileDesc& t = T[blockIdx.y];
+  const int s2_elems = t.B * (t.B + 1) / 2;
+  if ((int)blockIdx.x * 32 >= s2_elems) return;
+  cov_finalize_block<Acc>(blockIdx.x, static_cast<const Acc*>(t.s2p), t.parts, s2_elems, t.B, t.N,
+                          t.dvec, t.C, t.hdr, escaled ? t.escale : nullptr);
+}
 
 }  // namespace
 
@@ -241,6 +324,32 @@ cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const
   else
     k_cov_finalize<float><<<grid, kFinWarps * 32, 0, st>>>((const float*)s2_part, partials,
                                                            s2_elems, B, N, dvec, C, hdr, escale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_syrk_simt_grouped(const TileDesc* T, const CovItem* items, int nitems,
+                                     int maxB, pca_dtype dt, bool fp64, bool guarded,
+                                     cudaStream_t st) {
+  switch (dt) {
+    case PCA_F32:
+      return syrk_simt_grouped_typed<float>(T, items, nitems, maxB, fp64, guarded, st);
+    case PCA_BF16:
+      return syrk_simt_grouped_typed<__nv_bfloat16>(T, items, nitems, maxB, fp64, guarded, st);
+    case PCA_F16:
+      return syrk_simt_grouped_typed<__half>(T, items, nitems, maxB, fp64, guarded, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cov_finalize_batched(const TileDesc* T, int ntiles, int maxB, bool fp64,
+                                        bool escaled, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  k_s1_reduce_batched<<<dim3(maxB, ntiles), 32, 0, st>>>(T);
+  const dim3 grid((maxB * (maxB + 1) / 2 + 31) / 32, ntiles);
+  if (fp64)
+    k_cov_finalize_batched<double><<<grid, kFinWarps * 32, 0, st>>>(T, escaled ? 1 : 0);
+  else
+    k_cov_finalize_batched<float><<<grid, kFinWarps * 32, 0, st>>>(T, escaled ? 1 : 0);
   return cudaGetLastError();
 }
 

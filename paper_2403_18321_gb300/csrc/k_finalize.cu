@@ -12,13 +12,14 @@ namespace {
 // that sort before it (larger, or equal and at a lower position) -- no
 // comparison sort needed for B <= 256 -- and the sign that makes the entry of
 // largest magnitude (lowest row on ties) of column j positive.
-__global__ void __launch_bounds__(256)
-k_rank_sign(const double* __restrict__ lam, const float2* __restrict__ vc, int B,
-            int* __restrict__ rank, double* __restrict__ sgn, double* __restrict__ eigvals) {
+__device__ __forceinline__ void rank_sign_pair(int j, const double* __restrict__ lam,
+                                               const float2* __restrict__ vc, int B,
+                                               int* __restrict__ rank, double* __restrict__ sgn,
+                                               double* __restrict__ eigvals) {
   __shared__ int cnt[8];
   __shared__ double bv[8];
   __shared__ int bi[8];
-  const int j = blockIdx.x, i = threadIdx.x, lane = i & 31, warp = i >> 5;
+  const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
   const double lj = lam[j];
   int c = 0;
   double v = -1.0;
@@ -54,12 +55,17 @@ k_rank_sign(const double* __restrict__ lam, const float2* __restrict__ vc, int B
     eigvals[r] = lj;
   }
 }
-
-// k_scatter: one CTA per row i of V writes row i of the sorted, signed eigvecs.
 __global__ void __launch_bounds__(256)
-k_scatter(const float2* __restrict__ vc, int B, int k, const int* __restrict__ rank,
-          const double* __restrict__ sgn, double* __restrict__ eigvecs, float* __restrict__ vk) {
-  const int i = blockIdx.x;
+k_rank_sign(const double* __restrict__ lam, const float2* __restrict__ vc, int B,
+            int* __restrict__ rank, double* __restrict__ sgn, double* __restrict__ eigvals) {
+  rank_sign_pair(blockIdx.x, lam, vc, B, rank, sgn, eigvals);
+}
+
+// scatter: one CTA per row i of V writes row i of the sorted, signed eigvecs.
+__device__ __forceinline__ void scatter_row(int i, const float2* __restrict__ vc, int B, int k,
+                                            const int* __restrict__ rank,
+                                            const double* __restrict__ sgn,
+                                            double* __restrict__ eigvecs, float* __restrict__ vk) {
   for (int j = threadIdx.x; j < B; j += blockDim.x) {
     const float2 x = vc[(size_t)i * B + j];
     const double v = sgn[j] * ((double)x.x + (double)x.y);
@@ -68,7 +74,23 @@ k_scatter(const float2* __restrict__ vc, int B, int k, const int* __restrict__ r
     if (r < k) vk[(size_t)i * k + r] = (float)v;
   }
 }
-
+__global__ void __launch_bounds__(256)
+k_scatter(const float2* __restrict__ vc, int B, int k, const int* __restrict__ rank,
+          const double* __restrict__ sgn, double* __restrict__ eigvecs, float* __restrict__ vk) {
+  scatter_row(blockIdx.x, vc, B, k, rank, sgn, eigvecs, vk);
+}
+__global__ void __launch_bounds__(256)
+k_rank_sign_batched(const TileDesc* __restrict__ T, int in_w) {
+  const TileDesc& t = T[blockIdx.y];
+  if ((int)blockIdx.x >= t.B) return;
+  rank_sign_pair(blockIdx.x, t.lam, in_w ? t.w : t.vc, t.B, t.rank, t.sgn, t.eigvals);
+}
+__global__ void __launch_bounds__(256)
+k_scatter_batched(const TileDesc* __restrict__ T, int in_w) {
+  const TileDesc& t = T[blockIdx.y];
+  if ((int)blockIdx.x >= t.B) return;
+  scatter_row(blockIdx.x, in_w ? t.w : t.vc, t.B, t.k, t.rank, t.sgn, t.eigvecs, t.vk);
+}
 __global__ void k_narrow(const double* __restrict__ mu, const double* __restrict__ V, int B, int k,
                          float* __restrict__ mu_f, float* __restrict__ vk) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * k; e += gridDim.x * blockDim.x) {
@@ -91,6 +113,14 @@ cudaError_t launch_sort_sign(const double* lam, const float2* vc, int B, int k, 
                              double* eigvecs, float* vk, int* rank, double* sgn, cudaStream_t st) {
   k_rank_sign<<<B, 256, 0, st>>>(lam, vc, B, rank, sgn, eigvals);
   k_scatter<<<B, 256, 0, st>>>(vc, B, k, rank, sgn, eigvecs, vk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_sign_batched(const TileDesc* T, int ntiles, int maxB, bool final_in_w,
+                                     cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  k_rank_sign_batched<<<dim3(maxB, ntiles), 256, 0, st>>>(T, final_in_w ? 1 : 0);
+  k_scatter_batched<<<dim3(maxB, ntiles), 256, 0, st>>>(T, final_in_w ? 1 : 0);
   return cudaGetLastError();
 }
 

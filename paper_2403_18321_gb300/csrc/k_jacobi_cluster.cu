@@ -166,17 +166,26 @@ __device__ __forceinline__ float diag_after_odd(const Shared* sh, int so, int se
   return (x & 1) ? sh->rec[so][rix<H>((x - 1) >> 1)].z : sh->rec[so][rix<H>((x - 2) >> 1)].w;
 }
 
+// The parameters of this CTA's matrix, read in place (parameter space or global
+// memory) at each use rather than held in registers.
+__device__ __forceinline__ const Params& par(const Params& one, const Params* list) {
+  return list != nullptr ? list[blockIdx.x / one.nA] : one;
+}
+
+// One matrix per cluster: `one` when list is null, else list[cluster index]
+// (every entry of a list has the cluster size one.nA).
 template <int W>
-__global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm) {
+__global__ void __launch_bounds__(kThreads, 1)
+k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ list) {
   constexpr int H = W / 2;                 // pairs per lane in a V row
   extern __shared__ __align__(16) float rows[];
   __shared__ Shared sh;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int B = prm.B, Bp = B + (B & 1), P = Bp / 2;
-  const int ncl = prm.nA;
-  const double* C = prm.C;
+  const int B = par(one, list).B, Bp = B + (B & 1), P = Bp / 2;
+  const int ncl = par(one, list).nA;
+  const double* C = par(one, list).C;
   const bool band = warp < kBandWarps;
   const int bw = warp - kBandWarps;        // bulk warp index
   const int lid = tid - kBandWarps * 32;   // bulk lane index
@@ -187,8 +196,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
   int I_lo = 0, I_hi = 0, prev_lo = 0;
 #pragma unroll
   for (int r = 0; r < kMaxCl; ++r) {
-    if (r == rank) { I_lo = prm.rp[r]; I_hi = prm.rp[r + 1]; }
-    if (r + 1 == rank) prev_lo = prm.rp[r];
+    if (r == rank) { I_lo = par(one, list).rp[r]; I_hi = par(one, list).rp[r + 1]; }
+    if (r + 1 == rank) prev_lo = par(one, list).rp[r];
   }
   const int R0 = 2 * I_lo;
   const int nrows = 2 * (I_hi - I_lo) + (I_hi < P ? 1 : 0);
@@ -200,14 +209,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
   float* first_next = rank + 1 < ncl ? cl.map_shared_rank(rows, rank + 1) : nullptr;
 
   // ---- uniform early exit (every CTA reads the same header word)
-  if (prm.hdr->nonfinite) {
+  if (par(one, list).hdr->nonfinite) {
     if (rank == 0) {
-      for (int i = tid; i < Bp; i += kThreads) prm.diag32[i] = 0.f;
-      if (tid == 0) { prm.hdr->sweeps = 0; prm.hdr->steps = 0; prm.hdr->tol_used = prm.tol32; }
+      for (int i = tid; i < Bp; i += kThreads) par(one, list).diag32[i] = 0.f;
+      if (tid == 0) { par(one, list).hdr->sweeps = 0; par(one, list).hdr->steps = 0; par(one, list).hdr->tol_used = par(one, list).tol32; }
     }
     for (int e = tid; e < (V1 - V0) * Bp; e += kThreads) {
       const int r = V0 + e / Bp, c = e % Bp;
-      prm.v32[(size_t)r * Bp + c] = (r == c) ? 1.f : 0.f;
+      par(one, list).v32[(size_t)r * Bp + c] = (r == c) ? 1.f : 0.f;
     }
     return;
   }
@@ -284,11 +293,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
     for (int r = 0; r < ncl; ++r) atomicOr(&cl.map_shared_rank(&sh, r)->ovf, 1);
   cl.sync();
   const bool ovf = *(volatile int*)&sh.ovf != 0;
-  if (ovf && rank == 0 && tid == 0) set_status(prm.hdr, PCA_ERR_ARG);
+  if (ovf && rank == 0 && tid == 0) set_status(par(one, list).hdr, PCA_ERR_ARG);
 
   int sweep = 0, status = PCA_OK;
   int gs = 0;                    // global step number; step gs uses record slot gs % 3
-  const float tol2 = prm.tol32 * prm.tol32;
+  const float tol2 = par(one, list).tol32 * par(one, list).tol32;
   for (; !ovf;) {
     // ---------------- diagonal at the sweep boundary (after the last odd step)
     {
@@ -340,10 +349,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
       int anyv = 0;
       for (int r = 0; r < ncl; ++r) { o += sh.part_o[r]; d += sh.part_d[r]; anyv |= sh.part_v[r]; }
       const double off = sqrt(2.0 * o), fro = sqrt(2.0 * o + d);
-      const bool conv = prm.relative_stop ? !anyv : off <= (double)prm.tol32 * fro;
+      const bool conv = par(one, list).relative_stop ? !anyv : off <= (double)par(one, list).tol32 * fro;
       int flag = 0;
       if (fro == 0.0 || conv) flag = 1;
-      else if (sweep >= prm.sweeps_max) flag = 2;
+      else if (sweep >= par(one, list).sweeps_max) flag = 2;
       for (int r = 0; r < ncl; ++r) cl.map_shared_rank(&sh, r)->flag = flag;
       sh.off_rel = fro == 0.0 ? 0.0 : off / fro;
       sh.fro = fro;
@@ -540,14 +549,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
   if (rank == 0) {
     const int so = (gs + 2) % kSlots, se = (gs + 1) % kSlots;
     for (int x = tid; x < Bp; x += kThreads)
-      prm.diag32[x] = ovf ? 0.f : diag_after_odd<H>(&sh, so, se, x, Bp);
+      par(one, list).diag32[x] = ovf ? 0.f : diag_after_odd<H>(&sh, so, se, x, Bp);
     if (tid == 0) {
-      prm.hdr->sweeps = sweep;
-      prm.hdr->steps = sweep * Bp;
-      prm.hdr->tol_used = prm.tol32;
-      prm.hdr->off_rel = sh.off_rel;
-      prm.hdr->fro = sh.fro;
-      if (status != PCA_OK) set_status(prm.hdr, status);
+      par(one, list).hdr->sweeps = sweep;
+      par(one, list).hdr->steps = sweep * Bp;
+      par(one, list).hdr->tol_used = par(one, list).tol32;
+      par(one, list).hdr->off_rel = sh.off_rel;
+      par(one, list).hdr->fro = sh.fro;
+      if (status != PCA_OK) set_status(par(one, list).hdr, status);
     }
   }
 #pragma unroll
@@ -556,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_jacobi_cluster(const Params prm
 #pragma unroll
     for (int c = 0; c < W; ++c) {
       const int pos = W * lane + c;
-      if (pos < Bp) prm.v32[(size_t)vrow[k] * Bp + pos] = v[k][c];
+      if (pos < Bp) par(one, list).v32[(size_t)vrow[k] * Bp + pos] = v[k][c];
     }
   }
   cl.sync();  // no CTA leaves while others may still write its shared memory
@@ -573,9 +582,11 @@ bool jacobi_cluster_shape(int B, int* nA, int* nV) {
   return true;
 }
 
-cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweeps_max,
-                                  bool relative_stop, float* diag32, float* v32, DevHeader* hdr,
-                                  cudaStream_t st) {
+namespace {
+
+// Parameters of one matrix, and the dynamic shared memory its cluster needs.
+size_t make_params(const double* C, int B, float tol32, int sweeps_max, bool relative_stop,
+                   float* diag32, float* v32, DevHeader* hdr, Params* out) {
   const int Bp = round_even(B), P = Bp / 2;
   Params prm{};
   prm.C = C;
@@ -604,15 +615,19 @@ cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweep
   prm.diag32 = diag32;
   prm.v32 = v32;
   prm.hdr = hdr;
-
   int maxrows = 0;
   for (int r = 0; r < prm.nA; ++r) {
     const int n = 2 * (prm.rp[r + 1] - prm.rp[r]) + (prm.rp[r + 1] < P ? 1 : 0);
     maxrows = n > maxrows ? n : maxrows;
   }
-  const size_t smem = (size_t)maxrows * Bp * sizeof(float);
-  void (*kern)(const Params);
-  switch (v_width(Bp)) {
+  *out = prm;
+  return (size_t)maxrows * Bp * sizeof(float);
+}
+
+cudaError_t launch_clusters(int w, const Params& one, const Params* list, int count, size_t smem,
+                            cudaStream_t st) {
+  void (*kern)(const Params, const Params*);
+  switch (w) {
     case 2: kern = k_jacobi_cluster<2>; break;
     case 4: kern = k_jacobi_cluster<4>; break;
     default: kern = k_jacobi_cluster<8>; break;
@@ -620,20 +635,51 @@ cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweep
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(prm.nA);
+  cfg.gridDim = dim3(one.nA * count);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = prm.nA;
+  at[0].val.clusterDim.x = one.nA;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, kern, prm);
+  e = cudaLaunchKernelEx(&cfg, kern, one, list);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweeps_max,
+                                  bool relative_stop, float* diag32, float* v32, DevHeader* hdr,
+                                  cudaStream_t st) {
+  Params prm;
+  const size_t smem = make_params(C, B, tol32, sweeps_max, relative_stop, diag32, v32, hdr, &prm);
+  return launch_clusters(v_width(round_even(B)), prm, nullptr, 1, smem, st);
+}
+
+int jacobi_bucket(int B) {
+  const int Bp = round_even(B);
+  return Bp <= 32 ? 0 : (Bp <= 64 ? 1 : (Bp <= 128 ? 2 : 3));
+}
+
+size_t jacobi_params_bytes() { return sizeof(Params); }
+
+size_t jacobi_fill_params(void* dst, const double* C, int B, float tol32, int sweeps_max,
+                          bool relative_stop, float* diag32, float* v32, DevHeader* hdr) {
+  return make_params(C, B, tol32, sweeps_max, relative_stop, diag32, v32, hdr,
+                     static_cast<Params*>(dst));
+}
+
+cudaError_t launch_jacobi_cluster_list(const void* host_first, const void* dev_list, int count,
+                                       size_t smem, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const Params& one = *static_cast<const Params*>(host_first);
+  return launch_clusters(v_width(round_even(one.B)), one, static_cast<const Params*>(dev_list),
+                         count, smem, st);
 }
 
 }  // namespace gbpca

@@ -28,7 +28,6 @@ constexpr int kParts = 8;                // compute warps (band parts)
 constexpr int kCompute = kParts * 32;
 constexpr int kThreadsP = kCompute + 32;
 constexpr int kMaxStages = 8;
-constexpr int kMaxU = (kMaxB + 4 * kParts - 1) / (4 * kParts);  // 16-byte units per band part
 
 struct __align__(8) ProjSync {
   uint64_t full[kMaxStages];
@@ -96,33 +95,69 @@ struct ProjArgs {
   const float* mu_f;
   const float* vk;
   float* proj;
-  int stages, stage_bytes;
   DevHeader* hdr;
 };
 
+// One work item: chunks [c0, c1) of one cube and its tensor map.
+struct PItem {
+  ProjArgs a;
+  const CUtensorMap* map;
+  int64_t c0, c1;
+};
+
+__device__ __forceinline__ PItem proj_item(const ProjArgs& one, const CUtensorMap* one_map,
+                                           const TileDesc* __restrict__ T,
+                                           const CUtensorMap* __restrict__ maps,
+                                           const ProjItem* __restrict__ items,
+                                           const int* __restrict__ cta_items, int i) {
+  PItem it;
+  if (T == nullptr) {  // single cube: CTA g takes its share of the chunks
+    const int G = gridDim.x, g = blockIdx.x;
+    const int64_t nch = (one.N + kPc - 1) / kPc;
+    it.a = one;
+    it.map = one_map;
+    it.c0 = nch * g / G;
+    it.c1 = nch * (g + 1) / G;
+  } else {
+    const ProjItem pi = items[cta_items[blockIdx.x] + i];
+    const TileDesc& d = T[pi.tile];
+    it.a.cube = d.cube;
+    it.a.N = d.N;
+    it.a.B = d.B;
+    it.a.k = d.k;
+    it.a.mu_f = d.muf;
+    it.a.vk = d.vk;
+    it.a.proj = d.proj;
+    it.a.hdr = d.hdr;
+    it.map = maps != nullptr ? maps + pi.tile : nullptr;
+    it.c0 = pi.c0;
+    it.c1 = pi.c1;
+  }
+  return it;
+}
+
+// maxB, maxk: the largest bands and components of the items (shared-memory
+// sizing); the single-cube form takes its cube as `one` with map `tmap`.
 template <typename In, int KQ, bool kTiled>
 __global__ void __launch_bounds__(kThreadsP, 1)
-k_project(const __grid_constant__ CUtensorMap tmap, const ProjArgs a) {
+k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ ProjArgs one,
+          const TileDesc* __restrict__ T, const CUtensorMap* __restrict__ maps,
+          const ProjItem* __restrict__ items, const int* __restrict__ cta_items, int maxB,
+          int maxk, int S, int stage_bytes) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned start (the 128-byte swizzle repeats every 1024 bytes);
   // offsetting the array itself keeps every access a shared-memory one
   unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   constexpr int E = 16 / (int)sizeof(In);           // elements per 16-byte unit
-  const In* cube = static_cast<const In*>(a.cube);
-  const int64_t N = a.N;
-  const int B = a.B, k = a.k, S = a.stages;
-  const int B8 = (B + 7) & ~7;
+  const int B8m = (maxB + 7) & ~7;
   unsigned char* stages = smem;
-  float4* vs = reinterpret_cast<float4*>(stages + (size_t)S * a.stage_bytes);  // [B8][KQ]
-  float* mus = reinterpret_cast<float*>(vs + (size_t)B8 * KQ);                  // [B8]
-  float* red = mus + B8;                                                        // [kParts][kPc][k]
-  ProjSync* sy = reinterpret_cast<ProjSync*>(red + (size_t)kParts * kPc * k);
+  float4* vs = reinterpret_cast<float4*>(stages + (size_t)S * stage_bytes);  // [B8][KQ]
+  float* mus = reinterpret_cast<float*>(vs + (size_t)B8m * KQ);              // [B8]
+  float* red = mus + B8m;                                                    // [kParts][kPc][k]
+  ProjSync* sy = reinterpret_cast<ProjSync*>(red + (size_t)kParts * kPc * maxk);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int G = gridDim.x, g = blockIdx.x;
-  const int64_t nch_total = (N + kPc - 1) / kPc;
-  const int64_t c_begin = nch_total * g / G, c_end = nch_total * (g + 1) / G;
-  const int nch = (int)(c_end - c_begin);
+  const int nitems = T == nullptr ? 1 : cta_items[blockIdx.x + 1] - cta_items[blockIdx.x];
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&sy->full[s], 1); mbar_init(&sy->empty[s], kParts); }
@@ -130,36 +165,35 @@ k_project(const __grid_constant__ CUtensorMap tmap, const ProjArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // the producer starts streaming at once; the compute warps stage V_k and mu
-  // meanwhile and meet at their own barrier
-  if (warp < kParts) {
-    for (int e = tid; e < B8 * KQ * 4; e += kCompute) {
-      const int b = e / (KQ * 4), j = e - b * (KQ * 4);
-      reinterpret_cast<float*>(vs)[e] = (b < B && j < k) ? a.vk[(size_t)b * k + j] : 0.f;
-    }
-    for (int b = tid; b < B8; b += kCompute) mus[b] = b < B ? a.mu_f[b] : 0.f;
-    named_sync();
-  }
 
   if (warp == kParts) {
     // ------------------------------------------------------------ producer
+    // streams every item's chunks through one ring, ahead of the compute warps
     if (lane == 0) {
-      const int nbox = (B * (int)sizeof(In) + 127) / 128;
-      for (int c = 0; c < nch; ++c) {
-        const int s = c % S;
-        if (!mbar_wait(&sy->empty[s], ((c / S) & 1) ^ 1, &sy->abort)) break;
-        const int64_t p0 = (c_begin + c) * kPc;
-        unsigned char* dst = stages + (size_t)s * a.stage_bytes;
-        if constexpr (kTiled) {
-          mbar_expect_tx(&sy->full[s], (uint32_t)(nbox * kPc * 128));
-          for (int bx = 0; bx < nbox; ++bx)
-            tma_load_2d(dst + (size_t)bx * kPc * 128, &tmap, bx * (128 / (int)sizeof(In)), (int)p0,
-                        &sy->full[s]);
-        } else {
-          const int cp = (int)((N - p0) < kPc ? (N - p0) : kPc);
-          const uint32_t bytes = (uint32_t)((size_t)cp * B * sizeof(In)) & ~15u;
-          mbar_expect_tx(&sy->full[s], bytes);
-          if (bytes) bulk_g2s(dst, cube + p0 * B, bytes, &sy->full[s]);
+      int q = 0;
+      bool ok = true;
+      for (int i = 0; i < nitems && ok; ++i) {
+        const PItem it = proj_item(one, &tmap, T, maps, items, cta_items, i);
+        const In* cube = static_cast<const In*>(it.a.cube);
+        const int64_t N = it.a.N;
+        const int B = it.a.B;
+        const int nbox = (B * (int)sizeof(In) + 127) / 128;
+        for (int64_t c = it.c0; c < it.c1; ++c, ++q) {
+          const int s = q % S;
+          if (!mbar_wait(&sy->empty[s], ((q / S) & 1) ^ 1, &sy->abort)) { ok = false; break; }
+          const int64_t p0 = c * kPc;
+          unsigned char* dst = stages + (size_t)s * stage_bytes;
+          if constexpr (kTiled) {
+            mbar_expect_tx(&sy->full[s], (uint32_t)(nbox * kPc * 128));
+            for (int bx = 0; bx < nbox; ++bx)
+              tma_load_2d(dst + (size_t)bx * kPc * 128, it.map, bx * (128 / (int)sizeof(In)),
+                          (int)p0, &sy->full[s]);
+          } else {
+            const int cp = (int)((N - p0) < kPc ? (N - p0) : kPc);
+            const uint32_t bytes = (uint32_t)((size_t)cp * B * sizeof(In)) & ~15u;
+            mbar_expect_tx(&sy->full[s], bytes);
+            if (bytes) bulk_g2s(dst, cube + p0 * B, bytes, &sy->full[s]);
+          }
         }
       }
     }
@@ -169,16 +203,33 @@ k_project(const __grid_constant__ CUtensorMap tmap, const ProjArgs a) {
   // -------------------------------------------------------------- compute
   const int h = warp;
   const int pa = lane, pb = lane + 32;
-  int c = 0;
-  for (; c < nch; ++c) {
-    const int s = c % S;
+  int q = 0;
+  bool stop = false;
+  for (int i = 0; i < nitems && !stop; ++i) {
+  const PItem it = proj_item(one, &tmap, T, maps, items, cta_items, i);
+  const ProjArgs& a = it.a;
+  const In* cube = static_cast<const In*>(a.cube);
+  const int64_t N = a.N;
+  const int B = a.B, k = a.k;
+  const int B8 = (B + 7) & ~7;
+  // V_k and mu of this item's cube (the producer is already streaming)
+  if (i > 0) named_sync();   // every warp is done with the previous item's V_k
+  for (int e = tid; e < B8 * KQ * 4; e += kCompute) {
+    const int b = e / (KQ * 4), j = e - b * (KQ * 4);
+    reinterpret_cast<float*>(vs)[e] = (b < B && j < k) ? a.vk[(size_t)b * k + j] : 0.f;
+  }
+  for (int b = tid; b < B8; b += kCompute) mus[b] = b < B ? a.mu_f[b] : 0.f;
+  named_sync();
+  int64_t c = it.c0;
+  for (; c < it.c1; ++c, ++q) {
+    const int s = q % S;
     int ok = 1;
-    if (lane == 0) ok = mbar_wait(&sy->full[s], (c / S) & 1, &sy->abort) ? 1 : 0;
+    if (lane == 0) ok = mbar_wait(&sy->full[s], (q / S) & 1, &sy->abort) ? 1 : 0;
     ok = __shfl_sync(kFull, ok, 0);
     if (!named_and(ok)) break;
-    const int64_t p0 = (c_begin + c) * kPc;
+    const int64_t p0 = c * kPc;
     const int cp = (int)((N - p0) < kPc ? (N - p0) : kPc);
-    const unsigned char* st = stages + (size_t)s * a.stage_bytes;
+    const unsigned char* st = stages + (size_t)s * stage_bytes;
     float4 a0[KQ], a1[KQ];
 #pragma unroll
     for (int q = 0; q < KQ; ++q) { a0[q] = make_float4(0.f, 0.f, 0.f, 0.f); a1[q] = a0[q]; }
@@ -202,9 +253,11 @@ k_project(const __grid_constant__ CUtensorMap tmap, const ProjArgs a) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&sy->empty[s]);   // this warp is done with the stage
     } else {
-      // bands 4u .. 4u+3 for u = h, h + 8, ...: at most kMaxU groups per part,
-      // read four groups at a time; the stage is released after the reads of
-      // the last four
+      // bands 4u .. 4u+3 for u = h, h + 8, ...: read four groups at a time.
+      // The stage is released only after the last values read from it have
+      // been used: an arrive right after the loads let the next copy into the
+      // stage overwrite values still being read (wrong projections seen on
+      // the GPU when B was a multiple of 32).
       const In* sp = reinterpret_cast<const In*>(st);
       const size_t copied = (((size_t)cp * B * sizeof(In)) & ~(size_t)15) / sizeof(In);
       const bool whole = cp == kPc && copied == (size_t)kPc * B;
@@ -237,10 +290,6 @@ k_project(const __grid_constant__ CUtensorMap tmap, const ProjArgs a) {
             y1[i][e] = v1;
           }
         }
-        if (i0 + 4 >= mine) {
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sy->empty[s]);
-        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
 #pragma unroll
@@ -251,6 +300,10 @@ k_project(const __grid_constant__ CUtensorMap tmap, const ProjArgs a) {
               fma_band<KQ>(y0[i][e] - m, y1[i][e] - m, vs + (size_t)b * KQ, a0, a1);
             }
           }
+        }
+        if (i0 + 4 >= mine) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sy->empty[s]);
         }
       }
     }
@@ -276,12 +329,18 @@ k_project(const __grid_constant__ CUtensorMap tmap, const ProjArgs a) {
     }
     named_sync();
   }
-  if (c < nch) {
-    // a bounded wait gave up: make the rest of this CTA's range visibly invalid
-    const int64_t o0 = (c_begin + c) * kPc * k;
-    const int64_t o1 = (c_end * kPc < N ? c_end * kPc : N) * k;
-    for (int64_t o = o0 + tid; o < o1; o += kCompute) a.proj[o] = __int_as_float(0x7fc00000);
-    if (tid == 0 && a.hdr) set_status(a.hdr, PCA_ERR_TIMEOUT);
+  if (c < it.c1) {
+    // a bounded wait gave up: make the rest of this CTA's work visibly invalid
+    stop = true;
+    for (int j = i; j < nitems; ++j) {
+      const PItem rest = proj_item(one, &tmap, T, maps, items, cta_items, j);
+      const int64_t c0 = j == i ? c : rest.c0;
+      const int64_t o0 = c0 * kPc * rest.a.k;
+      const int64_t o1 = (rest.c1 * kPc < rest.a.N ? rest.c1 * kPc : rest.a.N) * rest.a.k;
+      for (int64_t o = o0 + tid; o < o1; o += kCompute) rest.a.proj[o] = __int_as_float(0x7fc00000);
+      if (tid == 0 && rest.a.hdr) set_status(rest.a.hdr, PCA_ERR_TIMEOUT);
+    }
+  }
   }
 }
 
@@ -309,64 +368,107 @@ template <> constexpr CUtensorMapDataType tmap_type<float>() { return CU_TENSOR_
 template <> constexpr CUtensorMapDataType tmap_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
 template <> constexpr CUtensorMapDataType tmap_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 
+// 2-D map of a cube [N][B] for the swizzled tiled load: boxes of 128 bytes x
+// kPc pixels.  False when the rows are not whole 16-byte units or encoding fails.
+template <typename In>
+bool encode_map(const void* cube, int64_t N, int B, CUtensorMap* map) {
+  memset(map, 0, sizeof(*map));
+  if ((B * sizeof(In)) % 16 != 0 || ((uintptr_t)cube % 16) != 0 || N >= (1ll << 31) ||
+      encode_fn() == nullptr)
+    return false;
+  const cuuint64_t gdim[2] = {(cuuint64_t)B, (cuuint64_t)N};
+  const cuuint64_t gstride[1] = {(cuuint64_t)B * sizeof(In)};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / sizeof(In)), (cuuint32_t)kPc};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode_fn()(map, tmap_type<In>(), 2, const_cast<void*>(cube), gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename In, int KQ>
-cudaError_t project_kq(const In* cube, int64_t N, int B, int k, const float* mu_f, const float* vk,
-                       float* proj, DevHeader* hdr, cudaStream_t st) {
-  CUtensorMap tmap;
-  memset(&tmap, 0, sizeof(tmap));
-  bool tiled = (B * sizeof(In)) % 16 == 0 && ((uintptr_t)cube % 16) == 0 && N < (1ll << 31) &&
-               encode_fn() != nullptr;
-  if (tiled) {
-    const cuuint64_t gdim[2] = {(cuuint64_t)B, (cuuint64_t)N};
-    const cuuint64_t gstride[1] = {(cuuint64_t)B * sizeof(In)};
-    const cuuint32_t box[2] = {(cuuint32_t)(128 / sizeof(In)), (cuuint32_t)kPc};
-    const cuuint32_t estr[2] = {1, 1};
-    tiled = encode_fn()(&tmap, tmap_type<In>(), 2, const_cast<In*>(cube), gdim, gstride, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-  }
-  const int B8 = (B + 7) & ~7;
-  const int nbox = (B * (int)sizeof(In) + 127) / 128;
+cudaError_t project_launch(bool tiled, const CUtensorMap& tmap, const ProjArgs& one,
+                           const TileDesc* T, const CUtensorMap* maps, const ProjItem* items,
+                           const int* cta_items, int ctas, int maxB, int maxk, cudaStream_t st) {
+  const int B8 = (maxB + 7) & ~7;
+  const int nbox = (maxB * (int)sizeof(In) + 127) / 128;
   const int stage_bytes = tiled ? nbox * kPc * 128
-                                : (int)((((size_t)kPc * B * sizeof(In)) + 1023) & ~(size_t)1023);
-  const size_t fixed = (size_t)B8 * KQ * 16 + (size_t)B8 * 4 + (size_t)kParts * kPc * k * 4 +
+                                : (int)((((size_t)kPc * maxB * sizeof(In)) + 1023) & ~(size_t)1023);
+  const size_t fixed = (size_t)B8 * KQ * 16 + (size_t)B8 * 4 + (size_t)kParts * kPc * maxk * 4 +
                        sizeof(ProjSync) + 1024;
   const size_t budget = 227 * 1024;
   int stages = (int)((budget - fixed) / stage_bytes);
   stages = stages > kMaxStages ? kMaxStages : stages;
   if (stages < 2) return cudaErrorInvalidValue;
   const size_t smem = fixed + (size_t)stages * stage_bytes;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t nch = (N + kPc - 1) / kPc;
-  const int grid = (int)(nch < sms ? nch : sms);
-  ProjArgs a{cube, N, B, k, mu_f, vk, proj, stages, stage_bytes, hdr};
   auto kern = tiled ? k_project<In, KQ, true> : k_project<In, KQ, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThreadsP, smem, st>>>(tmap, a);
+  kern<<<ctas, kThreadsP, smem, st>>>(tmap, one, T, maps, items, cta_items, maxB, maxk, stages,
+                                      stage_bytes);
   return cudaGetLastError();
+}
+
+template <typename In>
+cudaError_t project_any(bool tiled, const CUtensorMap& tmap, const ProjArgs& one, const TileDesc* T,
+                        const CUtensorMap* maps, const ProjItem* items, const int* cta_items,
+                        int ctas, int maxB, int maxk, cudaStream_t st) {
+  switch ((maxk + 3) / 4) {
+#define GB_PROJ_CASE(q) \
+    case q: return project_launch<In, q>(tiled, tmap, one, T, maps, items, cta_items, ctas, maxB, maxk, st);
+    GB_PROJ_CASE(1) GB_PROJ_CASE(2) GB_PROJ_CASE(3) GB_PROJ_CASE(4)
+    GB_PROJ_CASE(5) GB_PROJ_CASE(6) GB_PROJ_CASE(7) GB_PROJ_CASE(8)
+#undef GB_PROJ_CASE
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename In>
 cudaError_t project_typed(const In* cube, int64_t N, int B, int k, const float* mu_f,
                           const float* vk, float* proj, DevHeader* hdr, cudaStream_t st) {
-  switch ((k + 3) / 4) {
-    case 1: return project_kq<In, 1>(cube, N, B, k, mu_f, vk, proj, hdr, st);
-    case 2: return project_kq<In, 2>(cube, N, B, k, mu_f, vk, proj, hdr, st);
-    case 3: return project_kq<In, 3>(cube, N, B, k, mu_f, vk, proj, hdr, st);
-    case 4: return project_kq<In, 4>(cube, N, B, k, mu_f, vk, proj, hdr, st);
-    case 5: return project_kq<In, 5>(cube, N, B, k, mu_f, vk, proj, hdr, st);
-    case 6: return project_kq<In, 6>(cube, N, B, k, mu_f, vk, proj, hdr, st);
-    case 7: return project_kq<In, 7>(cube, N, B, k, mu_f, vk, proj, hdr, st);
-    case 8: return project_kq<In, 8>(cube, N, B, k, mu_f, vk, proj, hdr, st);
-  }
-  return cudaErrorInvalidValue;
+  CUtensorMap tmap;
+  const bool tiled = encode_map<In>(cube, N, B, &tmap);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nch = (N + kPc - 1) / kPc;
+  const int grid = (int)(nch < sms ? nch : sms);
+  const ProjArgs one{cube, N, B, k, mu_f, vk, proj, hdr};
+  return project_any<In>(tiled, tmap, one, nullptr, nullptr, nullptr, nullptr, grid, B, k, st);
 }
 
 }  // namespace
+
+bool encode_cube_map(pca_dtype dt, const void* cube, int64_t N, int B, void* map) {
+  CUtensorMap* m = static_cast<CUtensorMap*>(map);
+  switch (dt) {
+    case PCA_F32: return encode_map<float>(cube, N, B, m);
+    case PCA_BF16: return encode_map<__nv_bfloat16>(cube, N, B, m);
+    case PCA_F16: return encode_map<__half>(cube, N, B, m);
+  }
+  return false;
+}
+
+cudaError_t launch_project_grouped(const TileDesc* T, const void* maps, const ProjItem* items,
+                                   const int* cta_items, int ctas, int maxB, int maxk,
+                                   pca_dtype dt, cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  const ProjArgs one{};
+  const CUtensorMap* m = static_cast<const CUtensorMap*>(maps);
+  switch (dt) {
+    case PCA_F32:
+      return project_any<float>(m != nullptr, none, one, T, m, items, cta_items, ctas, maxB, maxk, st);
+    case PCA_BF16:
+      return project_any<__nv_bfloat16>(m != nullptr, none, one, T, m, items, cta_items, ctas, maxB,
+                                        maxk, st);
+    case PCA_F16:
+      return project_any<__half>(m != nullptr, none, one, T, m, items, cta_items, ctas, maxB, maxk,
+                                 st);
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_project(const void* cube, pca_dtype dt, int64_t N, int B, int k,
                            const float* mu_f, const float* vk, float* proj, cudaStream_t st,

@@ -68,15 +68,15 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
 // their partial sums are added at the end (enough warps per SM to hide the
 // dependent chains of the error-free transformations).
 template <bool kTransA>
-__global__ void __launch_bounds__(kTh * 4)
-k_dfgemm(const float2* __restrict__ A, const float2* __restrict__ Bm,
-         const float2* __restrict__ X, float2* __restrict__ D, int n) {
+__device__ __forceinline__ void dfgemm_tile(const float2* __restrict__ A,
+                                            const float2* __restrict__ Bm,
+                                            const float2* __restrict__ X, float2* __restrict__ D,
+                                            int n, int r0, int c0) {
   __shared__ float2 as[4][kT][kT + 1];  // as[group][k][row]
   __shared__ float2 bs[4][kT][kT + 1];  // bs[group][k][col]
   __shared__ float2 red[3][kT * kT];
   const int grp = threadIdx.x / kTh, t = threadIdx.x % kTh;
   const int tx = t & 7, ty = t >> 3;
-  const int r0 = blockIdx.y * kT, c0 = blockIdx.x * kT;
   float2 acc[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -141,6 +141,35 @@ k_dfgemm(const float2* __restrict__ A, const float2* __restrict__ Bm,
   }
 }
 
+template <bool kTransA>
+__global__ void __launch_bounds__(kTh * 4)
+k_dfgemm(const float2* __restrict__ A, const float2* __restrict__ Bm,
+         const float2* __restrict__ X, float2* __restrict__ D, int n) {
+  dfgemm_tile<kTransA>(A, Bm, X, D, n, blockIdx.y * kT, blockIdx.x * kT);
+}
+
+// The products of one refinement iteration / orthogonalisation step for
+// every tile of a batch (tile = blockIdx.z); v is vc, or w when flip.
+enum BatchedProduct { kCV = 0, kVtW = 1, kVtV = 2, kVEpV = 3 };
+template <bool kTransA>
+__global__ void __launch_bounds__(kTh * 4)
+k_dfgemm_batched(const TileDesc* __restrict__ T, int product, int flip) {
+  const TileDesc& t = T[blockIdx.z];
+  const int n = t.B;
+  if ((int)blockIdx.y * kT >= n || (int)blockIdx.x * kT >= n) return;
+  const float2* v = flip ? t.w : t.vc;
+  float2* vout = flip ? t.vc : t.w;
+  const float2 *A, *Bm, *X = nullptr;
+  float2* D;
+  switch (product) {
+    case kCV: A = t.cdf; Bm = v; D = vout; break;             // W = C V (in vout)
+    case kVtW: A = v; Bm = vout; D = t.s; break;              // S = V^T W
+    case kVtV: A = v; Bm = v; D = t.g; break;                 // G = V^T V
+    default: A = v; Bm = t.e; X = v; D = vout; break;         // V' = V E + V
+  }
+  dfgemm_tile<kTransA>(A, Bm, X, D, n, blockIdx.y * kT, blockIdx.x * kT);
+}
+
 void dfgemm(bool transA, const float2* A, const float2* Bm, const float2* X, float2* D, int n,
             cudaStream_t st) {
   const dim3 grid((n + kT - 1) / kT, (n + kT - 1) / kT);
@@ -154,11 +183,10 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
 }
 
 // E_ij and lam~_i = S_ii / G_ii (written by the diagonal entries), FP64.
-__global__ void k_refine_E(const float2* __restrict__ S, const float2* __restrict__ G, int n,
-                           float2* __restrict__ E, double* __restrict__ lam,
-                           DevHeader* __restrict__ hdr, double inv_max_angle) {
-  const int i = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void refine_E_row(int i, int j, const float2* __restrict__ S,
+                                             const float2* __restrict__ G, int n,
+                                             float2* __restrict__ E, double* __restrict__ lam,
+                                             DevHeader* __restrict__ hdr, double inv_max_angle) {
   double e = 0.0;
   if (j < n) {
     const double li = df_to_d(S[(size_t)i * n + i]) / df_to_d(G[(size_t)i * n + i]);
@@ -167,9 +195,12 @@ __global__ void k_refine_E(const float2* __restrict__ S, const float2* __restric
     const double sij = df_to_d(S[(size_t)i * n + j]);
     const double num = sij + lj * rij;
     const double gap = lj - li;
-    // classified the same way from (i, j) and (j, i), so that E_ij + E_ji = R_ij
+    // classified the same way from (i, j) and (j, i), so that E_ij + E_ji = R_ij;
+    // gaps at FP64 rounding level of ||A||_F (e.g. the null space of a
+    // rank-deficient covariance) count as clustered too
     const double size = fabs(sij) + fmax(fabs(li), fabs(lj)) * fabs(rij);
-    if (i != j && fabs(gap) > inv_max_angle * size) e = num / gap;
+    const double floor = 64.0 * 2.220446049250313e-16 * hdr->fro;
+    if (i != j && fabs(gap) > inv_max_angle * size && fabs(gap) > floor) e = num / gap;
     else e = 0.5 * rij;
     E[(size_t)i * n + j] = d_to_df(e);
     if (i == j) lam[i] = li;
@@ -181,21 +212,50 @@ __global__ void k_refine_E(const float2* __restrict__ S, const float2* __restric
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_pos(&hdr->refine_res, m);
 }
+__global__ void k_refine_E(const float2* __restrict__ S, const float2* __restrict__ G, int n,
+                           float2* __restrict__ E, double* __restrict__ lam,
+                           DevHeader* __restrict__ hdr, double inv_max_angle) {
+  refine_E_row(blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, S, G, n, E, lam, hdr,
+               inv_max_angle);
+}
+__global__ void k_refine_E_batched(const TileDesc* __restrict__ T, double inv_max_angle) {
+  const TileDesc& t = T[blockIdx.z];
+  if ((int)blockIdx.y >= t.B || (int)blockIdx.x * (int)blockDim.x >= t.B) return;
+  refine_E_row(blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, t.s, t.g, t.B, t.e, t.lam, t.hdr,
+               inv_max_angle);
+}
+__global__ void k_reset_res_batched(TileDesc* __restrict__ T, int ntiles) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ntiles) T[i].hdr->refine_res = 0.0;
+}
 
 // E = (I - G) / 2: one Newton-Schulz step V <- V (3I - V^T V)/2 = V + V E.
-__global__ void k_ns_E(const float2* __restrict__ G, int n, float2* __restrict__ E) {
-  const int i = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void ns_E_entry(int i, int j, const float2* __restrict__ G, int n,
+                                           float2* __restrict__ E) {
   if (j >= n) return;
   const float2 g = G[(size_t)i * n + j];
   const float2 r = i == j ? df_add(make_float2(1.f, 0.f), make_float2(-g.x, -g.y))
                           : make_float2(-g.x, -g.y);
   E[(size_t)i * n + j] = make_float2(0.5f * r.x, 0.5f * r.y);
 }
+__global__ void k_ns_E(const float2* __restrict__ G, int n, float2* __restrict__ E) {
+  ns_E_entry(blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, G, n, E);
+}
+__global__ void k_ns_E_batched(const TileDesc* __restrict__ T) {
+  const TileDesc& t = T[blockIdx.z];
+  if ((int)blockIdx.y >= t.B) return;
+  ns_E_entry(blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, t.g, t.B, t.e);
+}
 
 __global__ void k_to_df(const double* __restrict__ src, float2* __restrict__ dst, int count) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
     dst[e] = d_to_df(src[e]);
+}
+__global__ void k_to_df_batched(const TileDesc* __restrict__ T) {
+  const TileDesc& t = T[blockIdx.y];
+  const int count = t.B * t.B;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+    t.cdf[e] = d_to_df(t.C[e]);
 }
 
 }  // namespace
@@ -222,6 +282,40 @@ cudaError_t launch_refine(const float2* C, int B, const float2* v, float2* vout,
   cudaMemsetAsync(&hdr->refine_res, 0, sizeof(double), st);
   k_refine_E<<<dim3((B + 127) / 128, B), 128, 0, st>>>(s, g, B, e, lam, hdr, 1.0 / max_angle);
   dfgemm(false, v, e, v, vout, B, st);        // V' = V E + V
+  return cudaGetLastError();
+}
+
+void dfgemm_batched(bool transA, const TileDesc* T, int ntiles, int maxB, int product, bool flip,
+                    cudaStream_t st) {
+  const dim3 grid((maxB + kT - 1) / kT, (maxB + kT - 1) / kT, ntiles);
+  if (transA) k_dfgemm_batched<true><<<grid, kTh * 4, 0, st>>>(T, product, flip ? 1 : 0);
+  else k_dfgemm_batched<false><<<grid, kTh * 4, 0, st>>>(T, product, flip ? 1 : 0);
+}
+
+cudaError_t launch_to_df_batched(const TileDesc* T, int ntiles, int maxB, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  k_to_df_batched<<<dim3((maxB * maxB + 1023) / 1024, ntiles), 256, 0, st>>>(T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_batched(const TileDesc* T, int ntiles, int maxB, bool flip,
+                                  double max_angle, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  dfgemm_batched(false, T, ntiles, maxB, kCV, flip, st);
+  dfgemm_batched(true, T, ntiles, maxB, kVtW, flip, st);
+  dfgemm_batched(true, T, ntiles, maxB, kVtV, flip, st);
+  k_reset_res_batched<<<(ntiles + 127) / 128, 128, 0, st>>>(const_cast<TileDesc*>(T), ntiles);
+  k_refine_E_batched<<<dim3((maxB + 127) / 128, maxB, ntiles), 128, 0, st>>>(T, 1.0 / max_angle);
+  dfgemm_batched(false, T, ntiles, maxB, kVEpV, flip, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orthonormalize_batched(const TileDesc* T, int ntiles, int maxB, bool flip,
+                                          cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  dfgemm_batched(true, T, ntiles, maxB, kVtV, flip, st);
+  k_ns_E_batched<<<dim3((maxB + 127) / 128, maxB, ntiles), 128, 0, st>>>(T);
+  dfgemm_batched(false, T, ntiles, maxB, kVEpV, flip, st);
   return cudaGetLastError();
 }
 

@@ -49,3 +49,26 @@ def test_binding_refuses_cpu_tensors():
     import paper_2403_18321_gb300 as g
     with pytest.raises(TypeError):
         g.fit(torch.zeros(10, 4), 2)
+
+
+def test_batch_workspace_size_is_host_only_and_checks_every_tile():
+    """pca_batch_workspace_size lays out a batch on the host: positive for valid
+    tiles, 0 as soon as one tile is invalid, growing with the tiles."""
+    import paper_2403_18321_gb300 as g
+    lib = g.load(build_if_missing=True)
+
+    def tiles(shapes):
+        arr = (g.Tile * len(shapes))()
+        for i, (N, B, k) in enumerate(shapes):
+            arr[i] = g.Tile(None, N, B, k, None, None, None, None)
+        return arr
+
+    ok = [(4096, 64, 8), (100, 7, 3), (262144, 256, 8), (2, 2, 1)]
+    for prec in (0, 1, 2):
+        one = lib.pca_batch_workspace_size(1, tiles(ok[:1]), 0, prec)
+        four = lib.pca_batch_workspace_size(4, tiles(ok), 0, prec)
+        assert one > 0 and four > one
+    assert lib.pca_batch_workspace_size(2, tiles([(4096, 64, 8), (100, 257, 3)]), 0, 1) == 0
+    assert lib.pca_batch_workspace_size(2, tiles([(4096, 64, 8), (1, 8, 3)]), 0, 1) == 0
+    assert lib.pca_batch_workspace_size(2, tiles([(4096, 64, 8), (100, 8, 9)]), 0, 1) == 0
+    assert lib.pca_batch_workspace_size(0, tiles(ok), 0, 1) == 0

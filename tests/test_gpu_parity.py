@@ -31,7 +31,8 @@ def skip_if_unsupported(g, form, B):
 @pytest.mark.gpu
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("shape", [(37, 41, 64, 4), (61, 34, 103, 10), (23, 29, 7, 3),
-                                   (50, 51, 128, 5), (17, 11, 2, 1), (9, 7, 3, 2)])
+                                   (50, 51, 128, 5), (17, 11, 2, 1), (9, 7, 3, 2),
+                                   (1, 2, 16, 1)])
 def test_linear_mixing_small(gbpca_lib, form, shape):
     rows, cols, B, k = shape
     skip_if_unsupported(gbpca_lib, form, B)
