@@ -48,6 +48,8 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default="mix")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched form (256 tiles, 15.9 M pixels)")
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the differentiation form (forward + backward on 512 x 512 x 200)")
     ap.add_argument("--ncu-case", choices=["scenes", "big"], default=None,
@@ -217,6 +219,128 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ profiler case
+BATCH_WORKLOAD = ("256 tiles, N log-uniform in [4096, 262144], B uniform in "
+                  "{64,96,128,160,200,224,256}, 3-15 endmember FP32 mixtures (seed 3), k=8, "
+                  "tol 1e-8, 30 sweeps max")
+
+
+def run_batched(args, dev, peaks, peak_src):
+    """The batched form on the 256-tile workload: the batched MIX and P32 forms
+    (plain launches and a replayed CUDA graph) against fitting the tiles one by
+    one with the plain FP32 form, plus per-stage times and errors of sampled
+    tiles against the oracle.  Inputs (10 GB) exceed the L2, so no flush."""
+    import torch
+
+    import paper_2403_18321_gb300 as g
+    import synth
+    specs = synth.tile_batch_specs(seed=3)
+    cubes = [synth.tile_device(sp, dev) for sp in specs]
+    Ys = [c.Y for c in cubes]
+    units = sum(c.N * c.B for c in cubes)
+    nbytes = sum(c.N * c.B * 4 for c in cubes)
+    steps = max(3, min(args.steps, 10))
+    out = {"workload": BATCH_WORKLOAD, "tiles": len(cubes),
+           "pixels": sum(c.N for c in cubes), "values": units, "cube_GB": nbytes / 1e9,
+           "l2": "inputs (10 GB) larger than L2; no flush", "forms": {}}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    keep = {}
+    for prec in ("mix", "p32"):
+        b = g.Batch(Ys, 8, tol=1e-8, sweeps_max=30, precision=prec)
+        for _ in range(args.warmup):
+            b.run()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            e0.record()
+            b.run()
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1) / 1e3
+        ms = tot / steps * 1e3
+        g.profile(True)
+        b.run()
+        torch.cuda.synchronize()
+        stage = g.profile_collect()[0]
+        g.profile(False)
+        # the same run captured once into a CUDA graph and replayed
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            b.run(stream=side)
+        stream.wait_stream(side)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        tg = 0.0
+        for _ in range(steps):
+            e0.record()
+            graph.replay()
+            e1.record()
+            e1.synchronize()
+            tg += e0.elapsed_time(e1) / 1e3
+        status, infos = b.info()
+        sw = [i["sweeps"] for i in infos]
+        cov_ms, proj_ms = stage["covariance"], stage["project"]
+        proj_bytes = nbytes + sum(c.N * 8 * 4 for c in cubes)
+        out["forms"][prec] = {
+            "ms": ms, "value": units / (ms / 1e3) / 1e6, "unit": UNIT,
+            "graph_ms": tg / steps * 1e3, "graph_value": units / (tg / steps) / 1e6,
+            "kernel_launches": b.kernel_launches(), "status": status,
+            "sweeps_min": min(sw), "sweeps_max": max(sw), "sweeps_mean": float(np.mean(sw)),
+            "stage_ms": stage,
+            "covariance_GB/s": nbytes / (cov_ms / 1e3) / 1e9 if cov_ms > 0 else None,
+            "covariance_frac": (nbytes / (cov_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if cov_ms > 0 else None,
+            "project_GB/s": proj_bytes / (proj_ms / 1e3) / 1e9 if proj_ms > 0 else None,
+            "project_frac": (proj_bytes / (proj_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if proj_ms > 0 else None,
+            "peak_basis": peak_src}
+        keep[prec] = b
+        del graph
+    # the plain FP32 form, tile after tile on one stream
+    wss = [g.make_workspace(c.N, c.B, 8, 0, "p32", dev) for c in cubes]
+    outs = [(torch.empty(c.B, dtype=torch.float64, device=dev),
+             torch.empty(c.B, dtype=torch.float64, device=dev),
+             torch.empty(c.B, c.B, dtype=torch.float64, device=dev),
+             torch.empty(c.N, 8, dtype=torch.float32, device=dev)) for c in cubes]
+
+    def sequential():
+        for c, w, o in zip(cubes, wss, outs):
+            g.fit(c.Y, 8, tol=1e-8, sweeps_max=30, precision="p32", out=o, workspace=w, sync=False)
+    sequential()
+    torch.cuda.synchronize()
+    reps = 2
+    e0.record()
+    for _ in range(reps):
+        sequential()
+    e1.record()
+    e1.synchronize()
+    ms_seq = e0.elapsed_time(e1) / reps
+    out["sequential_p32"] = {"ms": ms_seq, "value": units / (ms_seq / 1e3) / 1e6, "unit": UNIT,
+                             "how": "pca_fit (P32) per tile, one stream"}
+    for prec in ("mix", "p32"):
+        out["forms"][prec]["speedup_vs_sequential_p32"] = ms_seq / out["forms"][prec]["ms"]
+    # errors of sampled tiles against the FP64 oracle (smallest, median, largest N)
+    import oracle
+    oracle.set_threads(0)
+    order = np.argsort([c.N for c in cubes])
+    sample = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    errs = {}
+    for prec, b in keep.items():
+        e_rel, e_l1 = [], []
+        for t in sample:
+            ref = oracle.pca_fit(cubes[t].Y.cpu().numpy(), 8, tol=1e-14)
+            lam = b.results[t][1].cpu().numpy()
+            err = np.abs(lam[:8] - ref["lam"][:8])
+            e_rel.append(float((err / np.abs(ref["lam"][:8])).max()))
+            e_l1.append(float(err.max() / abs(ref["lam"][0])))
+        errs[prec] = {"eig_rel_err_topk_max": max(e_rel), "eig_err_topk_over_lam1": max(e_l1)}
+        b.close()
+    out["errors_sampled_tiles"] = {"tiles": [cubes[t].name for t in sample], **errs}
+    return out
+
+
 def run_ncu_case(args):
     """Fits without timing, for ncu captures of single kernels (-k/-s/-c select them)."""
     import torch
@@ -491,6 +615,10 @@ def main(argv=None):
                 "backward_bytes": 2 * gc.N * gc.B * 4 + 2 * gc.N * gc.k * 4 + gc.N * gc.B * 4,
                 "backward_GB/s": (2 * gc.N * gc.B * 4 + 2 * gc.N * gc.k * 4 + gc.N * gc.B * 4) / tb / 1e9}
 
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = run_batched(args, dev, peaks, peak_src)
+
     launches = g.kernel_launches(args.precision, True) * len(cubes) * args.steps
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_mix / args.steps * 1e3,
@@ -508,7 +636,7 @@ def main(argv=None):
                               "sweeps": [i["sweeps"] for i in infos_p32], **errors.get("p32", {})}},
             "stage_ms_per_step": stage_ms, "roofline": roof, "hbm_kernels": hbm,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "differentiation": diff}
+            "differentiation": diff, "batched": batched}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

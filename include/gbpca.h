@@ -231,9 +231,10 @@ int pca_backward(const void *cube, pca_dtype dtype, int64_t N, int B, int k, con
  *     to *bad_tile when not NULL), lays out the workspace, encodes the
  *     tensor maps of the cubes and writes the work lists and per-tile
  *     descriptors into the workspace with one synchronous host-to-device
- *     copy.  The plan lives in host memory and owns four CUDA streams and
- *     five events (no device memory); the tiles' pointers and the workspace
- *     must stay valid for its life.  Returns PCA_OK, PCA_ERR_ARG,
+ *     copy.  The plan lives in host memory and owns a CUDA stream and an
+ *     event per Jacobi cluster shape (at most 24) plus one event (no device
+ *     memory); the tiles' pointers and the workspace must stay valid for its
+ *     life.  Returns PCA_OK, PCA_ERR_ARG,
  *     PCA_ERR_WORKSPACE or PCA_ERR_CUDA.
  * pca_batch_run  enqueues the fit of every tile on `stream`.  It launches
  *     kernels and records events only -- no allocation, copy or
@@ -295,8 +296,9 @@ int pca_batch_kernel_launches(const pca_batch *plan);
 int pca_jacobi_sms(int B);
 
 /*
- * Per-stage timing.  pca_profile(1) makes every later pca_fit on the calling
- * host thread record CUDA events on its stream around its eight stages
+ * Per-stage timing.  pca_profile(1) makes every later pca_fit (and
+ * pca_batch_run, one record per run) on the calling host thread record CUDA
+ * events on its stream around its eight stages
  * (covariance, covariance finalisation, Jacobi, a fourth slot that is always
  * 0 because the Jacobi kernel rotates V itself, compaction, refinement,
  * sort/sign, projection), up to 256 fits; pca_profile(0) stops.

@@ -25,6 +25,12 @@ __global__ void k_header_init(DevHeader* h, int refine_iters, float tol32) {
 
 }  // namespace
 
+// 64 chunks = 2048 pixels per slot: on 256 mixture tiles the eigenvalue error
+// relative to lam_1 grew linearly with the slot length (about 1.0e-5 at 64
+// chunks, 2.0e-5 at 128, 4.9e-4 with one slot per CTA of up to 170 k pixels),
+// while each halving of the length cost about 7% more covariance time.
+int tc_slot_chunks() { return 64; }
+
 int device_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
@@ -59,20 +65,20 @@ struct ProfState {
 };
 thread_local ProfState g_prof;
 
-struct StageMark {
-  cudaStream_t st;
-  int rec;
-  explicit StageMark(cudaStream_t s) : st(s), rec(-1) {
-    if (g_prof.on && g_prof.nrec < kProfRecords) rec = g_prof.nrec++;
-  }
-  void mark(int i) {
-    if (rec < 0) return;
-    cudaEvent_t& e = g_prof.ev[rec][i];
-    if (!e) cudaEventCreate(&e);
-    cudaEventRecord(e, st);
-    g_prof.used[rec][i] = true;
-  }
-};
+}  // namespace
+
+StageMark::StageMark(cudaStream_t s) : st(s), rec(-1) {
+  if (g_prof.on && g_prof.nrec < kProfRecords) rec = g_prof.nrec++;
+}
+void StageMark::mark(int i) {
+  if (rec < 0) return;
+  cudaEvent_t& e = g_prof.ev[rec][i];
+  if (!e) cudaEventCreate(&e);
+  cudaEventRecord(e, st);
+  g_prof.used[rec][i] = true;
+}
+
+namespace {
 
 }  // namespace
 
@@ -81,7 +87,9 @@ Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, in
   Layout L{};
   const int Bp = round_even(B);
   if (prec == PCA_PREC_MIX) {
-    L.partials = (int)std::min<int64_t>(num_sms, std::max<int64_t>(1, (N + 127) / 128));
+    L.tc_ctas = (int)std::min<int64_t>(num_sms, std::max<int64_t>(1, (N + 127) / 128));
+    const int64_t nchunk = (N + 31) / 32, cap = tc_slot_chunks();
+    L.partials = (int)std::max<int64_t>(L.tc_ctas, (nchunk + cap - 1) / cap);
     L.s2_bytes_el = 4;
   } else {
     L.partials = (int)std::min<int64_t>(kMaxPartials, std::max<int64_t>(1, (N + 255) / 256));
@@ -243,8 +251,8 @@ cudaError_t run_cov(const void* cube, pca_dtype dt, int64_t N, int B, pca_precis
   cudaError_t e;
   pm.mark(0);
   if (prec == PCA_PREC_MIX) {
-    e = launch_syrk_tc(cube, dt, N, B, P.shift, P.escale, P.s1p, (float*)P.s2p, L.partials, P.hdr,
-                       st);
+    e = launch_syrk_tc(cube, dt, N, B, P.shift, P.escale, P.s1p, (float*)P.s2p, L.partials,
+                       L.tc_ctas, P.hdr, st);
     if (e != cudaSuccess) return e;
     // a value outside the scaled FP16 range: the SIMT form recomputes the partials
     // (its CTAs return at once when the flag is clear)

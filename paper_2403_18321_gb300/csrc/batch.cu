@@ -26,7 +26,6 @@ namespace {
 
 constexpr int kCovChunk = 32;    // pixel granularity of covariance items
 constexpr int kProjChunk = 64;   // pixel granularity of projection items
-constexpr int kBuckets = 4;      // Jacobi cluster shapes
 constexpr int kSimtItemsPerSm = 4;
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -43,31 +42,45 @@ __global__ void k_header_init_batched(TileDesc* __restrict__ T, int ntiles, int 
   *T[i].hdr = z;
 }
 
-// Splits the tiles' chunks (weight B per chunk, i.e. bytes) into `ctas`
-// contiguous ranges of equal weight; every (tile, range) piece is one item.
-// Returns the items grouped by CTA and the number of items of every tile.
+// Cost of one chunk of a tile with B bands, in arbitrary units, fitted to the
+// measured times of the streaming kernels on this GPU: a fixed part per chunk
+// (barrier round trips, the MMA/epilogue cadence) plus a part per band; the
+// SIMT covariance grows with the B^2/2 products per pixel.
+enum class Cost { kTensorCov, kSimtCov, kProject };
+double chunk_cost(Cost c, int B) {
+  switch (c) {
+    case Cost::kTensorCov: return 464.0 + B;         // ~1.16 us + 2.5 ns per band (32 pixels)
+    case Cost::kSimtCov: return 13900.0 + (double)B * B;
+    case Cost::kProject: return 223.0 + B;           // ~1.07 us + 4.8 ns per band (64 pixels)
+  }
+  return B;
+}
+
+// Splits the tiles' chunks into `ctas` contiguous ranges of equal cost; every
+// (tile, range) piece is one item.  Returns the items grouped by CTA and the
+// number of items of every tile.
 struct Split {
   std::vector<std::vector<CovItem>> per_cta;
   std::vector<int> parts;
 };
-Split split_chunks(const std::vector<pca_tile>& tiles, int chunk, int ctas) {
+Split split_chunks(const std::vector<pca_tile>& tiles, int chunk, int ctas, Cost cost) {
   Split sp;
   const int n = (int)tiles.size();
   sp.per_cta.assign(ctas, {});
   sp.parts.assign(n, 0);
   long double total = 0;
-  for (const pca_tile& t : tiles) total += (long double)((t.N + chunk - 1) / chunk) * t.B;
+  for (const pca_tile& t : tiles) total += (long double)((t.N + chunk - 1) / chunk) * chunk_cost(cost, t.B);
   long double w0 = 0;  // weight before the current tile
   int g = 0;
   for (int ti = 0; ti < n; ++ti) {
     const int64_t nch = (tiles[ti].N + chunk - 1) / chunk;
-    const int B = tiles[ti].B;
+    const double wc = chunk_cost(cost, tiles[ti].B);  // cost of one chunk
     int64_t c = 0;
     while (c < nch) {
       int64_t cend = nch;
       if (g < ctas - 1) {
         const long double end = total * (g + 1) / ctas;  // weight at which CTA g stops
-        const long double x = (end - w0) / B;
+        const long double x = (end - w0) / wc;
         cend = x <= 0 ? 0 : std::min<int64_t>(nch, (int64_t)std::ceil((double)x));
         if (cend <= c) { ++g; continue; }
       }
@@ -79,7 +92,7 @@ Split split_chunks(const std::vector<pca_tile>& tiles, int chunk, int ctas) {
       sp.per_cta[g].push_back(it);
       c = cend;
     }
-    w0 += (long double)nch * B;
+    w0 += (long double)nch * wc;
   }
   return sp;
 }
@@ -106,15 +119,18 @@ struct pca_batch {
   int* proj_off = nullptr;
   int proj_ctas = 0;
   void* maps = nullptr;           // device CUtensorMap[ntiles] or null (untiled loads)
-  // Jacobi lists
+  // Jacobi lists, one per cluster shape (V width, CTAs per cluster), each
+  // launched on its own stream
   struct Bucket {
-    void* list = nullptr;         // device
+    void* list = nullptr;         // device, `count` parameter entries
     int count = 0;
     size_t smem = 0;
     std::vector<unsigned char> first;  // host copy of the first entry (launch shape)
-  } bucket[kBuckets];
-  cudaStream_t aux[kBuckets] = {};
-  cudaEvent_t fork = nullptr, join[kBuckets] = {};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t join = nullptr;
+  };
+  std::vector<Bucket> buckets;
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -127,7 +143,7 @@ bool tile_ok(const pca_tile& t, pca_dtype dt, pca_precision prec, double tol, in
 // Workspace layout of a batch.  With descs != nullptr the per-tile
 // descriptors are filled in, pointing into the workspace at `base`.
 struct BatchLayout {
-  size_t tiles, hdrs, cov_items, cov_off, proj_items, proj_off, maps, lists[kBuckets];
+  size_t tiles, hdrs, cov_items, cov_off, proj_items, proj_off, maps, lists;
   size_t total;
   Split cov, proj;
 };
@@ -140,12 +156,32 @@ BatchLayout batch_layout(const std::vector<pca_tile>& tiles, pca_dtype dt, pca_p
   const bool mix = prec == PCA_PREC_MIX, p64 = prec == PCA_PREC_P64;
   const bool refine = refine_iterations(prec) > 0;
   const int cov_ctas = mix ? sms : kSimtItemsPerSm * sms;
-  L.cov = split_chunks(tiles, kCovChunk, cov_ctas);
+  L.cov = split_chunks(tiles, kCovChunk, cov_ctas, mix ? Cost::kTensorCov : Cost::kSimtCov);
+  if (mix) {  // bound the tensor-core accumulation: long items become several slots
+    const int64_t cap = tc_slot_chunks();
+    std::vector<int> slot_of(n, 0);
+    for (auto& v : L.cov.per_cta) {
+      std::vector<CovItem> split;
+      for (const CovItem& it : v) {
+        const int64_t c0 = it.p0 / kCovChunk, c1 = (it.p1 + kCovChunk - 1) / kCovChunk;
+        const int64_t pieces = (c1 - c0 + cap - 1) / cap;
+        for (int64_t q = 0; q < pieces; ++q) {
+          CovItem x = it;
+          x.p0 = (c0 + (c1 - c0) * q / pieces) * kCovChunk;
+          x.p1 = std::min<int64_t>(it.p1, (c0 + (c1 - c0) * (q + 1) / pieces) * kCovChunk);
+          x.slot = slot_of[it.tile]++;
+          split.push_back(x);
+        }
+      }
+      v.swap(split);
+    }
+    L.cov.parts = slot_of;
+  }
   std::vector<pca_tile> ptiles;
   std::vector<int> pmap;
   for (int i = 0; i < n; ++i)
     if (tiles[i].proj) { ptiles.push_back(tiles[i]); pmap.push_back(i); }
-  L.proj = split_chunks(ptiles, kProjChunk, sms);
+  L.proj = split_chunks(ptiles, kProjChunk, sms, Cost::kProject);
   for (auto& v : L.proj.per_cta)
     for (auto& it : v) it.tile = pmap[it.tile];
   int ncov = 0, nproj = 0;
@@ -160,7 +196,7 @@ BatchLayout batch_layout(const std::vector<pca_tile>& tiles, pca_dtype dt, pca_p
   L.proj_items = take(sizeof(ProjItem) * std::max(nproj, 1));
   L.proj_off = take(sizeof(int) * (sms + 1));
   L.maps = take(128 * (size_t)n);
-  for (int b = 0; b < kBuckets; ++b) L.lists[b] = take(jacobi_params_bytes() * n);
+  L.lists = take(jacobi_params_bytes() * n);
   if (descs) descs->assign(n, TileDesc{});
   for (int i = 0; i < n; ++i) {
     const pca_tile& t = tiles[i];
@@ -261,7 +297,7 @@ int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dt
   b->hdrs = reinterpret_cast<DevHeader*>(ws + L.hdrs);
 
   // the table region [0, end of the Jacobi lists) is built on the host and copied once
-  const size_t table = L.lists[kBuckets - 1] + jacobi_params_bytes() * ntiles;
+  const size_t table = L.lists + jacobi_params_bytes() * ntiles;
   std::vector<unsigned char> img(table, 0);
   std::memcpy(img.data() + L.tiles, descs.data(), sizeof(TileDesc) * ntiles);
   {  // covariance items, CTA by CTA
@@ -303,29 +339,40 @@ int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dt
       if (v[i].proj) all = encode_cube_map(dtype, v[i].cube, v[i].N, v[i].B, img.data() + L.maps + 128 * (size_t)i);
     b->maps = all ? ws + L.maps : nullptr;
   }
-  {  // Jacobi lists: one per cluster shape, largest matrices first
+  {  // Jacobi lists.  Throughput over latency: each matrix gets the fewest
+     // CTAs that hold its V (a cluster per matrix; the clusters of one shape
+     // share a launch), and within a shape the largest matrices start first.
     std::vector<int> order(ntiles);
     for (int i = 0; i < ntiles; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return v[a].B > v[c].B; });
+    auto key = [&](int i) { return jacobi_width(v[i].B) * 16 + jacobi_min_ctas(v[i].B); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+      return key(a) != key(c) ? key(a) > key(c) : v[a].B > v[c].B;
+    });
     const size_t pb = jacobi_params_bytes();
-    for (int i : order) {
-      const int bk = jacobi_bucket(v[i].B);
-      pca_batch::Bucket& bu = b->bucket[bk];
-      unsigned char* dst = img.data() + L.lists[bk] + pb * bu.count;
+    int prev = -1;
+    for (int pos = 0; pos < ntiles; ++pos) {
+      const int i = order[pos];
+      if (key(i) != prev) {
+        b->buckets.emplace_back();
+        b->buckets.back().list = ws + L.lists + pb * pos;
+        prev = key(i);
+      }
+      pca_batch::Bucket& bu = b->buckets.back();
+      unsigned char* dst = img.data() + L.lists + pb * pos;
       const size_t smem = jacobi_fill_params(dst, descs[i].C, v[i].B, b->tol32, sweeps_max,
                                              relative_stop(prec), descs[i].diag32, descs[i].v32,
-                                             descs[i].hdr);
+                                             descs[i].hdr, jacobi_min_ctas(v[i].B));
       bu.smem = std::max(bu.smem, smem);
       if (bu.count == 0) bu.first.assign(dst, dst + pb);
       ++bu.count;
     }
-    for (int bk = 0; bk < kBuckets; ++bk) b->bucket[bk].list = ws + L.lists[bk];
   }
   bool ok = cudaMemcpy(ws, img.data(), table, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
-  for (int bk = 0; bk < kBuckets && ok; ++bk) {
-    ok = cudaStreamCreateWithFlags(&b->aux[bk], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&b->join[bk], cudaEventDisableTiming) == cudaSuccess;
+  for (pca_batch::Bucket& bu : b->buckets) {
+    if (!ok) break;
+    ok = cudaStreamCreateWithFlags(&bu.stream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&bu.join, cudaEventDisableTiming) == cudaSuccess;
   }
   if (!ok) {
     pca_batch_destroy(b);
@@ -341,9 +388,11 @@ int pca_batch_run(pca_batch* b, void* stream) {
   const int n = b->ntiles, maxB = b->maxB;
   const pca_precision prec = b->prec;
   const int iters = refine_iterations(prec), ortho = ortho_steps(prec);
+  StageMark pm(st);
   k_header_init_batched<<<(n + 127) / 128, 128, 0, st>>>(b->T, n, iters, b->tol32);
   GB_CK(cudaGetLastError());
   // stages 2-3: band means and covariance
+  pm.mark(0);
   if (prec == PCA_PREC_MIX) {
     GB_CK(launch_syrk_tc_grouped(b->T, b->cov_items, b->cov_off, b->cov_ctas, maxB, b->dt, st));
     GB_CK(launch_syrk_simt_grouped(b->T, b->cov_items, b->cov_nitems, maxB, b->dt, false, true, st));
@@ -351,29 +400,34 @@ int pca_batch_run(pca_batch* b, void* stream) {
     GB_CK(launch_syrk_simt_grouped(b->T, b->cov_items, b->cov_nitems, maxB, b->dt,
                                    prec == PCA_PREC_P64, false, st));
   }
+  pm.mark(1);
   GB_CK(launch_cov_finalize_batched(b->T, n, maxB, prec == PCA_PREC_P64, prec == PCA_PREC_MIX, st));
   // stage 4: one Jacobi launch per cluster shape, side by side
+  pm.mark(2);
   GB_CK(cudaEventRecord(b->fork, st));
-  for (int bk = 0; bk < kBuckets; ++bk) {
-    pca_batch::Bucket& bu = b->bucket[bk];
-    if (bu.count == 0) continue;
-    GB_CK(cudaStreamWaitEvent(b->aux[bk], b->fork, 0));
-    GB_CK(launch_jacobi_cluster_list(bu.first.data(), bu.list, bu.count, bu.smem, b->aux[bk]));
-    GB_CK(cudaEventRecord(b->join[bk], b->aux[bk]));
+  for (pca_batch::Bucket& bu : b->buckets) {
+    GB_CK(cudaStreamWaitEvent(bu.stream, b->fork, 0));
+    GB_CK(launch_jacobi_cluster_list(bu.first.data(), bu.list, bu.count, bu.smem, bu.stream));
+    GB_CK(cudaEventRecord(bu.join, bu.stream));
   }
-  for (int bk = 0; bk < kBuckets; ++bk)
-    if (b->bucket[bk].count > 0) GB_CK(cudaStreamWaitEvent(st, b->join[bk], 0));
+  for (pca_batch::Bucket& bu : b->buckets) GB_CK(cudaStreamWaitEvent(st, bu.join, 0));
+  pm.mark(3);
+  pm.mark(4);
   GB_CK(launch_compact_batched(b->T, n, maxB, st));
+  pm.mark(5);
   bool in_w = false;  // V alternates between vc and w
   if (iters > 0) GB_CK(launch_to_df_batched(b->T, n, maxB, st));
   for (int it = 0; it < iters; ++it, in_w = !in_w)
     GB_CK(launch_refine_batched(b->T, n, maxB, in_w, refine_max_angle(prec), st));
   for (int it = 0; it < ortho; ++it, in_w = !in_w)
     GB_CK(launch_orthonormalize_batched(b->T, n, maxB, in_w, st));
+  pm.mark(6);
   GB_CK(launch_sort_sign_batched(b->T, n, maxB, in_w, st));
   // stages 5-6: projection
+  pm.mark(7);
   GB_CK(launch_project_grouped(b->T, b->maps, b->proj_items, b->proj_off, b->proj_ctas, maxB,
                                b->maxk, b->dt, st));
+  pm.mark(8);
   return PCA_OK;
 }
 
@@ -405,7 +459,7 @@ int pca_batch_kernel_launches(const pca_batch* b) {
   if (!b) return 0;
   const int iters = refine_iterations(b->prec), ortho = ortho_steps(b->prec);
   int n = 1 + (b->prec == PCA_PREC_MIX ? 2 : 1) + 2;  // header, covariance, finalisation
-  for (int bk = 0; bk < kBuckets; ++bk) n += b->bucket[bk].count > 0 ? 1 : 0;
+  n += (int)b->buckets.size();
   n += 1;                                              // compaction
   n += (iters > 0 ? 1 : 0) + 6 * iters + 3 * ortho;    // refinement
   n += 2;                                              // rank/sign, scatter
@@ -415,9 +469,9 @@ int pca_batch_kernel_launches(const pca_batch* b) {
 
 void pca_batch_destroy(pca_batch* b) {
   if (!b) return;
-  for (int bk = 0; bk < kBuckets; ++bk) {
-    if (b->aux[bk]) cudaStreamDestroy(b->aux[bk]);
-    if (b->join[bk]) cudaEventDestroy(b->join[bk]);
+  for (pca_batch::Bucket& bu : b->buckets) {
+    if (bu.stream) cudaStreamDestroy(bu.stream);
+    if (bu.join) cudaEventDestroy(bu.join);
   }
   if (b->fork) cudaEventDestroy(b->fork);
   delete b;

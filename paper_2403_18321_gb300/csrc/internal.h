@@ -38,6 +38,7 @@ struct Layout {
   size_t hdr, shift, escale, s1_part, s2_part, dvec, cov, cdf, rank, sgn, diag32, v32, lam, vc, w, s, r, e, vk, muf;
   size_t total;
   int partials;      // number of covariance partial slots the SYRK uses
+  int tc_ctas;       // MIX: CTAs of the tensor-core pass (partials spread over them)
   int s2_elems;      // packed upper-triangle entries per partial: B(B+1)/2
   int s2_bytes_el;   // 4 (FP32 partials) or 8 (FP64 partials)
 };
@@ -80,6 +81,16 @@ inline bool relative_stop(pca_precision prec) { return prec != PCA_PREC_MIX; }
 bool args_ok(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol,
              int sweeps_max, pca_precision prec);
 int device_sms();
+
+// Optional per-stage CUDA-event timing (pca_profile): one record per fit, marks
+// 0..8 around the stages covariance, finalisation, Jacobi, (empty), compaction,
+// refinement, sort/sign, projection.  Inactive unless profiling is on.
+struct StageMark {
+  cudaStream_t st;
+  int rec;
+  explicit StageMark(cudaStream_t s);
+  void mark(int i);
+};
 
 // ---------------------------------------------------------------- batched form
 // One tile of a batch: its input, the caller's outputs and its workspace
@@ -144,8 +155,11 @@ cudaError_t launch_syrk_simt(const void* cube, pca_dtype dt, int64_t N, int B, b
 // partials are unscaled, S2 partials stay scaled by 2^(e_i + e_j).  A value
 // outside the FP16 range after scaling sets hdr->cov_range.
 cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
-                           int* escale, double* s1_part, float* s2_part, int partials,
+                           int* escale, double* s1_part, float* s2_part, int partials, int ctas,
                            DevHeader* hdr, cudaStream_t st);
+// Longest run of 32-pixel chunks one tensor-core partial slot accumulates: the
+// FP32 accumulation in tensor memory loses accuracy in proportion to its length.
+int tc_slot_chunks();
 bool syrk_tc_supported(int B);
 
 // Sums the partials, applies the shift correction, writes mu (FP64), C (FP64, full
@@ -240,14 +254,17 @@ cudaError_t launch_syrk_tc_grouped(const TileDesc* T, const CovItem* items, cons
                                    int ctas, int maxB, pca_dtype dt, cudaStream_t st);
 cudaError_t launch_cov_finalize_batched(const TileDesc* T, int ntiles, int maxB, bool fp64,
                                         bool escaled, cudaStream_t st);
-// Jacobi parameter lists: matrices of one bucket (equal cluster shape) run in
-// one launch, one cluster each.
-int jacobi_bucket(int B);  // 0..3
+// Jacobi parameter lists: matrices of one shape (equal V width and cluster
+// size) run in one launch, one cluster each.
+int jacobi_width(int B);     // V values per lane of a V row (kernel variant)
+int jacobi_min_ctas(int B);  // fewest CTAs per cluster for B bands
 size_t jacobi_params_bytes();
-// Writes the parameters of one matrix to dst (host); returns the dynamic
-// shared memory its cluster needs.
+// Writes the parameters of one matrix to dst (host) for a cluster of nA CTAs
+// (0: the latency-oriented default of the single-matrix form); returns the
+// dynamic shared memory its cluster needs.
 size_t jacobi_fill_params(void* dst, const double* C, int B, float tol32, int sweeps_max,
-                          bool relative_stop, float* diag32, float* v32, DevHeader* hdr);
+                          bool relative_stop, float* diag32, float* v32, DevHeader* hdr, int nA);
+int jacobi_params_ctas(const void* params);
 cudaError_t launch_jacobi_cluster_list(const void* host_first, const void* dev_list, int count,
                                        size_t smem, cudaStream_t st);
 cudaError_t launch_compact_batched(const TileDesc* T, int ntiles, int maxB, cudaStream_t st);

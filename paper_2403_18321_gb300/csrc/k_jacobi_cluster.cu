@@ -586,7 +586,7 @@ namespace {
 
 // Parameters of one matrix, and the dynamic shared memory its cluster needs.
 size_t make_params(const double* C, int B, float tol32, int sweeps_max, bool relative_stop,
-                   float* diag32, float* v32, DevHeader* hdr, Params* out) {
+                   float* diag32, float* v32, DevHeader* hdr, int nA, Params* out) {
   const int Bp = round_even(B), P = Bp / 2;
   Params prm{};
   prm.C = C;
@@ -596,6 +596,7 @@ size_t make_params(const double* C, int B, float tol32, int sweeps_max, bool rel
   prm.relative_stop = relative_stop ? 1 : 0;
   int nV = 0;
   jacobi_cluster_shape(B, &prm.nA, &nV);
+  if (nA > 0) prm.nA = nA;
   if (prm.nA > P) prm.nA = P;
   // rows: balance the blocks (I, J >= I) of the even steps
   const long total = (long)P * (P + 1) / 2;
@@ -657,22 +658,29 @@ cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweep
                                   bool relative_stop, float* diag32, float* v32, DevHeader* hdr,
                                   cudaStream_t st) {
   Params prm;
-  const size_t smem = make_params(C, B, tol32, sweeps_max, relative_stop, diag32, v32, hdr, &prm);
+  const size_t smem =
+      make_params(C, B, tol32, sweeps_max, relative_stop, diag32, v32, hdr, 0, &prm);
   return launch_clusters(v_width(round_even(B)), prm, nullptr, 1, smem, st);
 }
 
-int jacobi_bucket(int B) {
-  const int Bp = round_even(B);
-  return Bp <= 32 ? 0 : (Bp <= 64 ? 1 : (Bp <= 128 ? 2 : 3));
+int jacobi_width(int B) { return v_width(round_even(B)); }
+
+// Fewest CTAs that hold the rows of V in registers: kVRows rows per bulk warp.
+int jacobi_min_ctas(int B) {
+  const int Bp = round_even(B), per = kVRows * kBulkWarps;
+  const int n = (Bp + per - 1) / per;
+  return n < 1 ? 1 : (n > kMaxCl ? kMaxCl : n);
 }
 
 size_t jacobi_params_bytes() { return sizeof(Params); }
 
 size_t jacobi_fill_params(void* dst, const double* C, int B, float tol32, int sweeps_max,
-                          bool relative_stop, float* diag32, float* v32, DevHeader* hdr) {
-  return make_params(C, B, tol32, sweeps_max, relative_stop, diag32, v32, hdr,
+                          bool relative_stop, float* diag32, float* v32, DevHeader* hdr, int nA) {
+  return make_params(C, B, tol32, sweeps_max, relative_stop, diag32, v32, hdr, nA,
                      static_cast<Params*>(dst));
 }
+
+int jacobi_params_ctas(const void* params) { return static_cast<const Params*>(params)->nA; }
 
 cudaError_t launch_jacobi_cluster_list(const void* host_first, const void* dev_list, int count,
                                        size_t smem, cudaStream_t st) {

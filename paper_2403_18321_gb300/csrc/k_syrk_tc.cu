@@ -136,6 +136,7 @@ struct TcTile {
   const void* cube;
   int64_t N;
   int B;
+  int slots;          // single cube: partial slots, split evenly over the CTAs
   float* shift;       // written by the CTA holding partial slot 0
   int* escale;
   double* s1_part;    // [slots][B]
@@ -154,14 +155,16 @@ __device__ __forceinline__ TcItem tc_item(const TcTile& one, const TileDesc* __r
                                           const CovItem* __restrict__ items,
                                           const int* __restrict__ cta_items, int i) {
   TcItem it;
-  if (T == nullptr) {  // single cube: CTA g takes its share of the 32-pixel chunks
+  if (T == nullptr) {  // single cube: CTA g takes its share of the slots, slot s
+                       // its share of the 32-pixel chunks
     const int G = gridDim.x, g = blockIdx.x;
+    const int s = (int)((int64_t)one.slots * g / G) + i;
     const int64_t nchunk = (one.N + kKC - 1) / kKC;
     it.t = one;
-    it.p0 = nchunk * g / G * kKC;
-    it.p1 = nchunk * (g + 1) / G * kKC;
+    it.p0 = nchunk * s / one.slots * kKC;
+    it.p1 = nchunk * (s + 1) / one.slots * kKC;
     if (it.p1 > one.N) it.p1 = one.N;
-    it.slot = g;
+    it.slot = s;
   } else {
     const CovItem ci = items[cta_items[blockIdx.x] + i];
     const TileDesc& d = T[ci.tile];
@@ -196,7 +199,10 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
   SyncBlock* sb = reinterpret_cast<SyncBlock*>(pmax + 2 * kRows);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nitems = T == nullptr ? 1 : cta_items[blockIdx.x + 1] - cta_items[blockIdx.x];
+  const int nitems =
+      T == nullptr ? (int)((int64_t)one.slots * (blockIdx.x + 1) / gridDim.x -
+                           (int64_t)one.slots * blockIdx.x / gridDim.x)
+                   : cta_items[blockIdx.x + 1] - cta_items[blockIdx.x];
 
   // ---- set-up
   for (int i = tid; i < kOpStages * 2 * kOpBytes / 16; i += kThreads)
@@ -530,10 +536,10 @@ cudaError_t syrk_tc_launch(const TcTile& one, const TileDesc* T, const CovItem* 
 
 template <typename In>
 cudaError_t syrk_tc_typed(const void* cube, int64_t N, int B, float* shift, int* escale,
-                          double* s1_part, float* s2_part, int partials, DevHeader* hdr,
+                          double* s1_part, float* s2_part, int partials, int ctas, DevHeader* hdr,
                           cudaStream_t st) {
-  TcTile one{cube, N, B, shift, escale, s1_part, s2_part, hdr};
-  return syrk_tc_launch<In>(one, nullptr, nullptr, nullptr, partials, B, st);
+  TcTile one{cube, N, B, partials, shift, escale, s1_part, s2_part, hdr};
+  return syrk_tc_launch<In>(one, nullptr, nullptr, nullptr, ctas, B, st);
 }
 
 }  // namespace
@@ -541,16 +547,19 @@ cudaError_t syrk_tc_typed(const void* cube, int64_t N, int B, float* shift, int*
 bool syrk_tc_supported(int B) { return B >= 2 && B <= kMaxB; }
 
 cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
-                           int* escale, double* s1_part, float* s2_part, int partials,
+                           int* escale, double* s1_part, float* s2_part, int partials, int ctas,
                            DevHeader* hdr, cudaStream_t st) {
+  if (ctas < 1 || ctas > partials) return cudaErrorInvalidValue;
   switch (dt) {
     case PCA_F32:
-      return syrk_tc_typed<float>(cube, N, B, shift, escale, s1_part, s2_part, partials, hdr, st);
+      return syrk_tc_typed<float>(cube, N, B, shift, escale, s1_part, s2_part, partials, ctas, hdr,
+                                  st);
     case PCA_BF16:
       return syrk_tc_typed<__nv_bfloat16>(cube, N, B, shift, escale, s1_part, s2_part, partials,
-                                          hdr, st);
+                                          ctas, hdr, st);
     case PCA_F16:
-      return syrk_tc_typed<__half>(cube, N, B, shift, escale, s1_part, s2_part, partials, hdr, st);
+      return syrk_tc_typed<__half>(cube, N, B, shift, escale, s1_part, s2_part, partials, ctas, hdr,
+                                   st);
   }
   return cudaErrorInvalidValue;
 }

@@ -20,6 +20,7 @@ Workloads (pixels x bands, component count k):
                     1e-3 floor, values in [0, 1] rounded to bf16 (or fp16), k=20
   tile_batch        256 tiles, N log-uniform in [4096, 262144],
                     B in {64,96,128,160,200,224,256}, 3-15 endmembers, k=8
+                    (tile: numpy on the host; tile_device: torch on a GPU)
   gradient_cube     512x512 x 200 planted spectrum (s_i = 0.9^(i-1), i <= 11,
                     0.05 floor), upstream gradient N(0,1), k=10
 """
@@ -165,6 +166,24 @@ def tile(spec, k: int = 8, tol: float = 1e-8, sweeps_max: int = 30) -> Cube:
     M = rng.uniform(0.0, 1.0, size=(e, B))
     A = _dirichlet(rng, np.ones(e), N)
     Y = (A @ M + 0.01 * rng.standard_normal((N, B))).astype(np.float32)
+    return Cube(f"tile_{N}x{B}_e{e}", Y, k, tol, sweeps_max, (), dict(seed=sd, endmembers=e))
+
+
+def tile_device(spec, device, k: int = 8, tol: float = 1e-8, sweeps_max: int = 30) -> Cube:
+    """The same recipe as ``tile`` (U[0,1] endmembers, Dirichlet(1) abundances as
+    normalised exponential draws, 0.01 Gaussian noise, FP32) drawn on a CUDA
+    device with a torch generator seeded by the tile seed -- for full-size
+    batches whose 10 GB would take minutes to draw on the host.  The values
+    differ from ``tile``'s (another generator); the distribution is the same."""
+    import torch
+    N, B, e, sd = spec
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(sd))
+    M = torch.rand(e, B, generator=gen, device=device, dtype=torch.float32)
+    A = torch.empty(N, e, device=device, dtype=torch.float32).exponential_(generator=gen)
+    A /= A.sum(dim=1, keepdim=True)
+    Y = torch.randn(N, B, generator=gen, device=device, dtype=torch.float32).mul_(0.01)
+    Y.addmm_(A, M)
     return Cube(f"tile_{N}x{B}_e{e}", Y, k, tol, sweeps_max, (), dict(seed=sd, endmembers=e))
 
 
