@@ -344,7 +344,7 @@ int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dt
      // share a launch), and within a shape the largest matrices start first.
     std::vector<int> order(ntiles);
     for (int i = 0; i < ntiles; ++i) order[i] = i;
-    auto key = [&](int i) { return jacobi_width(v[i].B) * 16 + jacobi_min_ctas(v[i].B); };
+    auto key = [&](int i) { return jacobi_width(v[i].B) * 16 + jacobi_batch_ctas(v[i].B); };
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
       return key(a) != key(c) ? key(a) > key(c) : v[a].B > v[c].B;
     });
@@ -361,7 +361,7 @@ int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dt
       unsigned char* dst = img.data() + L.lists + pb * pos;
       const size_t smem = jacobi_fill_params(dst, descs[i].C, v[i].B, b->tol32, sweeps_max,
                                              relative_stop(prec), descs[i].diag32, descs[i].v32,
-                                             descs[i].hdr, jacobi_min_ctas(v[i].B));
+                                             descs[i].hdr, jacobi_batch_ctas(v[i].B));
       bu.smem = std::max(bu.smem, smem);
       if (bu.count == 0) bu.first.assign(dst, dst + pb);
       ++bu.count;

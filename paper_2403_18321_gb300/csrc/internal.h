@@ -257,7 +257,8 @@ cudaError_t launch_cov_finalize_batched(const TileDesc* T, int ntiles, int maxB,
 // Jacobi parameter lists: matrices of one shape (equal V width and cluster
 // size) run in one launch, one cluster each.
 int jacobi_width(int B);     // V values per lane of a V row (kernel variant)
-int jacobi_min_ctas(int B);  // fewest CTAs per cluster for B bands
+int jacobi_min_ctas(int B);  // fewest CTAs per cluster of the default kernel variant
+int jacobi_batch_ctas(int B);  // fewest CTAs per cluster of any variant (batched form)
 size_t jacobi_params_bytes();
 // Writes the parameters of one matrix to dst (host) for a cluster of nA CTAs
 // (0: the latency-oriented default of the single-matrix form); returns the

@@ -40,6 +40,7 @@
 // and broadcast), so every CTA reaches every cluster barrier.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -54,8 +55,10 @@ constexpr int kThreads = 640;
 constexpr int kBandWarps = 4;
 constexpr int kBulkWarps = kThreads / 32 - kBandWarps;
 constexpr int kBulkLanes = kBulkWarps * 32;
-constexpr int kMaxItems = 4;      // bulk blocks per lane per parity (checked)
-constexpr int kVRows = 2;         // V rows per bulk warp (checked)
+constexpr int kMaxItems = 4;      // bulk blocks per lane per parity (checked), default variant
+constexpr int kVRows = 2;         // V rows per bulk warp (checked), default variant
+constexpr int kWideVRows = 3;     // the same for the fewer-CTA variant
+constexpr int kWideItems = 3;
 constexpr int kMaxCl = 8;
 constexpr int kSlots = 3;
 constexpr int kRecs = 128;        // records per slot: 32 lanes x W/2 pairs, W <= 8
@@ -174,7 +177,7 @@ __device__ __forceinline__ const Params& par(const Params& one, const Params* li
 
 // One matrix per cluster: `one` when list is null, else list[cluster index]
 // (every entry of a list has the cluster size one.nA).
-template <int W>
+template <int W, int VR, int MI>
 __global__ void __launch_bounds__(kThreads, 1)
 k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ list) {
   constexpr int H = W / 2;                 // pairs per lane in a V row
@@ -235,10 +238,10 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
   if (tid == 0) { sh.ovf = 0; sh.flag = 0; }
 
   // ---- V rows in registers: bulk warp bw holds rows V0 + bw + kBulkWarps*k
-  float v[kVRows][W];
-  int vrow[kVRows];
+  float v[VR][W];
+  int vrow[VR];
 #pragma unroll
-  for (int k = 0; k < kVRows; ++k) {
+  for (int k = 0; k < VR; ++k) {
     vrow[k] = band ? -1 : V0 + bw + kBulkWarps * k;
     if (vrow[k] >= V1) vrow[k] = -1;
 #pragma unroll
@@ -246,21 +249,21 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
   }
 
   // ---- bulk block lists (blocks (I, J >= I+2) of this CTA's row pairs)
-  uint32_t lst[2][kMaxItems];
+  uint32_t lst[2][MI];
   uint32_t xitem = kNone;   // odd steps: one row-0 or last-column item
   int overflow = 0;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     const int np = P - e;
 #pragma unroll
-    for (int t = 0; t < kMaxItems; ++t) lst[e][t] = kNone;
+    for (int t = 0; t < MI; ++t) lst[e][t] = kNone;
     if (!band) {
       const int Ihi = min(I_hi, np - 2);  // rows that hold a block with J >= I + 2
       int total = 0;
       for (int I = I_lo; I < Ihi; ++I) total += np - 2 - I;
-      if (total > kMaxItems * kBulkLanes) overflow = 1;
+      if (total > MI * kBulkLanes) overflow = 1;
 #pragma unroll
-      for (int t = 0; t < kMaxItems; ++t) {
+      for (int t = 0; t < MI; ++t) {
         const int idx = lid + t * kBulkLanes;
         if (idx < total) {
           int rem = idx, I = I_lo;
@@ -286,7 +289,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
       if (I != P - 2) xitem = (1u << 31) | (uint32_t)I;
     }
   }
-  if (V1 - V0 > kVRows * kBulkWarps || P > 32 * H) overflow = 1;
+  if (V1 - V0 > VR * kBulkWarps || P > 32 * H) overflow = 1;
   overflow = __syncthreads_or(overflow);
   cl.sync();  // every CTA's flags and records are initialised before remote writes
   if (overflow && tid == 0)
@@ -443,7 +446,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
         }
       } else {
 #pragma unroll
-        for (int t = 0; t < kMaxItems; ++t) {
+        for (int t = 0; t < MI; ++t) {
           const uint32_t w = lst[e][t];
           if (w == kNone) continue;
           const int I = (int)(w >> 24), J = (int)((w >> 16) & 0xff);
@@ -503,7 +506,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
         for (int t = 0; t < H; ++t) g[t] = cs_of(rc[t * 32 + lane]);
         if (e == 0) {
 #pragma unroll
-          for (int k = 0; k < kVRows; ++k) {
+          for (int k = 0; k < VR; ++k) {
             if (vrow[k] < 0) continue;
 #pragma unroll
             for (int t = 0; t < H; ++t) {
@@ -518,7 +521,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
           // pair J0-1 straddles this lane and the previous one
           const float2 gp = lane > 0 ? cs_of(rc[(H - 1) * 32 + lane - 1]) : make_float2(1.f, 0.f);
 #pragma unroll
-          for (int k = 0; k < kVRows; ++k) {
+          for (int k = 0; k < VR; ++k) {
             if (vrow[k] < 0) continue;        // uniform over the warp
             const float yn = __shfl_down_sync(kFull, v[k][0], 1);     // next lane's first
             const float xp = __shfl_up_sync(kFull, v[k][W - 1], 1);   // previous lane's last
@@ -560,7 +563,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
     }
   }
 #pragma unroll
-  for (int k = 0; k < kVRows; ++k) {
+  for (int k = 0; k < VR; ++k) {
     if (vrow[k] < 0) continue;
 #pragma unroll
     for (int c = 0; c < W; ++c) {
@@ -625,13 +628,17 @@ size_t make_params(const double* C, int B, float tol32, int sweeps_max, bool rel
   return (size_t)maxrows * Bp * sizeof(float);
 }
 
+// Kernel variant: the default holds kVRows rows of V per bulk warp; clusters
+// with fewer CTAs than that needs (the batched form's throughput shapes) hold
+// kWideVRows rows and up to kWideItems bulk blocks per lane.
 cudaError_t launch_clusters(int w, const Params& one, const Params* list, int count, size_t smem,
                             cudaStream_t st) {
   void (*kern)(const Params, const Params*);
+  const bool wide = one.nA < jacobi_min_ctas(one.B);
   switch (w) {
-    case 2: kern = k_jacobi_cluster<2>; break;
-    case 4: kern = k_jacobi_cluster<4>; break;
-    default: kern = k_jacobi_cluster<8>; break;
+    case 2: kern = wide ? k_jacobi_cluster<2, kWideVRows, kWideItems> : k_jacobi_cluster<2, kVRows, kMaxItems>; break;
+    case 4: kern = wide ? k_jacobi_cluster<4, kWideVRows, kWideItems> : k_jacobi_cluster<4, kVRows, kMaxItems>; break;
+    default: kern = wide ? k_jacobi_cluster<8, kWideVRows, kWideItems> : k_jacobi_cluster<8, kVRows, kMaxItems>; break;
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -664,6 +671,32 @@ cudaError_t launch_jacobi_cluster(const double* C, int B, float tol32, int sweep
 }
 
 int jacobi_width(int B) { return v_width(round_even(B)); }
+
+// Fewest CTAs whose kernel variant holds the matrix: every CTA's rows of V
+// and bulk blocks of both parities within the variant's capacity (the same
+// counts the kernel checks).
+int jacobi_batch_ctas(int B) {
+  const int Bp = round_even(B), P = Bp / 2;
+  for (int n = 1; n <= kMaxCl; ++n) {
+    Params prm;
+    make_params(nullptr, B, 1.f, 1, true, nullptr, nullptr, nullptr, n, &prm);
+    const bool wide = prm.nA < jacobi_min_ctas(B);
+    const int vr = wide ? kWideVRows : kVRows, mi = wide ? kWideItems : kMaxItems;
+    bool fits = P <= 32 * (v_width(Bp) / 2);
+    for (int r = 0; r < prm.nA && fits; ++r) {
+      const int V0 = (int)((long)Bp * r / prm.nA), V1 = (int)((long)Bp * (r + 1) / prm.nA);
+      if (V1 - V0 > vr * kBulkWarps) fits = false;
+      for (int e = 0; e < 2 && fits; ++e) {
+        const int np = P - e, hi = std::min(prm.rp[r + 1], np - 2);
+        long total = 0;
+        for (int I = prm.rp[r]; I < hi; ++I) total += np - 2 - I;
+        if (total > (long)mi * kBulkLanes) fits = false;
+      }
+    }
+    if (fits) return prm.nA;
+  }
+  return jacobi_min_ctas(B);
+}
 
 // Fewest CTAs that hold the rows of V in registers: kVRows rows per bulk warp.
 int jacobi_min_ctas(int B) {
