@@ -52,10 +52,13 @@ def parse_args(argv=None):
                     help="skip the batched form (256 tiles, 15.9 M pixels)")
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the differentiation form (forward + backward on 512 x 512 x 200)")
-    ap.add_argument("--ncu-case", choices=["scenes", "big"], default=None,
+    ap.add_argument("--ncu-case", choices=["scenes", "big", "batched", "batched-small"],
+                    default=None,
                     help="untimed fits for profiler captures: 'scenes' = the bench cubes, "
-                         "'big' = one 1024x400x224 scene cube (367 MB, larger than L2); "
-                         "runs --warmup + --steps fits and prints no JSON line")
+                         "'big' = one 1024x400x224 scene cube (367 MB, larger than L2), "
+                         "'batched' = the 256-tile batch (10 GB), 'batched-small' = its first "
+                         "48 tiles with N / 4 (about 0.5 GB); runs --warmup + --steps fits "
+                         "and prints no JSON line")
     return ap.parse_args(argv)
 
 
@@ -348,6 +351,20 @@ def run_ncu_case(args):
     import paper_2403_18321_gb300 as g
     import synth
     g.load()
+    if args.ncu_case in ("batched", "batched-small"):
+        specs = synth.tile_batch_specs(seed=3)
+        if args.ncu_case == "batched-small":
+            specs = [(max(4096, n // 4), b, e, sd) for n, b, e, sd in specs[:48]]
+        dev = torch.device("cuda")
+        Ys = [synth.tile_device(sp, dev).Y for sp in specs]
+        b = g.Batch(Ys, 8, tol=1e-8, sweeps_max=30, precision=args.precision)
+        for _ in range(args.warmup + args.steps):
+            b.run()
+        status, infos = b.info()
+        print(f"{len(Ys)} tiles, {sum(y.numel() for y in Ys) * 4 / 1e9:.2f} GB: status {status}, "
+              f"{b.kernel_launches()} launches per run")
+        b.close()
+        return 0
     if args.ncu_case == "big":
         cubes = [synth.paper_scene(2, 1024, 400, 224)]
     else:

@@ -436,12 +436,12 @@ int pca_version(void) { return 100; }
 int pca_kernel_launches(pca_precision prec, int with_projection) {
   // header init, covariance (MIX: tensor-core pass + guarded SIMT
   // re-computation), band-sum reduce, covariance finalise, Jacobi (with
-  // V), compact, 5 per refinement iteration (four products and the angle
-  // kernel), 1 conversion, 3 per orthogonalisation step, rank/sign +
-  // scatter, projection
+  // V), compact, 6 per refinement iteration (four products, the eigenvalue
+  // and the angle kernels), 1 conversion, 3 per orthogonalisation step,
+  // rank/sign + scatter, projection
   const int it = refine_iterations(prec);
   const int cov = prec == PCA_PREC_MIX ? 2 : 1;
-  return 5 + cov + 5 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
+  return 5 + cov + 6 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
 }
 
 int pca_jacobi_sms(int B) {

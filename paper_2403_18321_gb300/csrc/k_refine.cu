@@ -141,10 +141,13 @@ __device__ __forceinline__ void dfgemm_tile(const float2* __restrict__ A,
   }
 }
 
+// sym: D is symmetric (V^T W, V^T V) -- only the tiles on or above the
+// diagonal are formed, and readers take entry (min(i,j), max(i,j)).
 template <bool kTransA>
 __global__ void __launch_bounds__(kTh * 4)
 k_dfgemm(const float2* __restrict__ A, const float2* __restrict__ Bm,
-         const float2* __restrict__ X, float2* __restrict__ D, int n) {
+         const float2* __restrict__ X, float2* __restrict__ D, int n, int sym) {
+  if (sym && blockIdx.y > blockIdx.x) return;
   dfgemm_tile<kTransA>(A, Bm, X, D, n, blockIdx.y * kT, blockIdx.x * kT);
 }
 
@@ -157,6 +160,7 @@ k_dfgemm_batched(const TileDesc* __restrict__ T, int product, int flip) {
   const TileDesc& t = T[blockIdx.z];
   const int n = t.B;
   if ((int)blockIdx.y * kT >= n || (int)blockIdx.x * kT >= n) return;
+  if ((product == kVtW || product == kVtV) && blockIdx.y > blockIdx.x) return;  // symmetric
   const float2* v = flip ? t.w : t.vc;
   float2* vout = flip ? t.vc : t.w;
   const float2 *A, *Bm, *X = nullptr;
@@ -171,10 +175,10 @@ k_dfgemm_batched(const TileDesc* __restrict__ T, int product, int flip) {
 }
 
 void dfgemm(bool transA, const float2* A, const float2* Bm, const float2* X, float2* D, int n,
-            cudaStream_t st) {
+            bool sym, cudaStream_t st) {
   const dim3 grid((n + kT - 1) / kT, (n + kT - 1) / kT);
-  if (transA) k_dfgemm<true><<<grid, kTh * 4, 0, st>>>(A, Bm, X, D, n);
-  else k_dfgemm<false><<<grid, kTh * 4, 0, st>>>(A, Bm, X, D, n);
+  if (transA) k_dfgemm<true><<<grid, kTh * 4, 0, st>>>(A, Bm, X, D, n, sym ? 1 : 0);
+  else k_dfgemm<false><<<grid, kTh * 4, 0, st>>>(A, Bm, X, D, n, sym ? 1 : 0);
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
@@ -182,17 +186,42 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// E_ij and lam~_i = S_ii / G_ii (written by the diagonal entries), FP64.
+// num / den in FP64 without the FP64 divider (slow on this GPU): an FP32
+// reciprocal as the seed, one Newton-Raphson step r <- r (2 - den r), the
+// quotient q = num r, and one residual correction q <- q + r (num - den q)
+// (Markstein's scheme), all in FP64.  Denominators outside the FP32 normal
+// range take the plain division.
+__device__ __forceinline__ double quotient(double num, double den) {
+  const float df = (float)den;
+  if (!(fabsf(df) >= 1.17549435e-38f) || !(fabsf(df) <= 3.0e38f)) return num / den;
+  double r = (double)__frcp_rn(df);
+  r = r * fma(-den, r, 2.0);
+  double q = num * r;
+  return fma(r, fma(-den, q, num), q);
+}
+
+// lam~_i = S_ii / G_ii, once per eigen-pair, and the residual word reset
+// before k_refine_E maximises into it.
+__device__ __forceinline__ void refine_lam_entry(int i, const float2* __restrict__ S,
+                                                 const float2* __restrict__ G, int n,
+                                                 double* __restrict__ lam,
+                                                 DevHeader* __restrict__ hdr) {
+  if (i < n) lam[i] = df_to_d(S[(size_t)i * n + i]) / df_to_d(G[(size_t)i * n + i]);
+  if (i == 0) hdr->refine_res = 0.0;
+}
+
+// E_ij from the upper triangles of S and G (both symmetric), FP64.
 __device__ __forceinline__ void refine_E_row(int i, int j, const float2* __restrict__ S,
                                              const float2* __restrict__ G, int n,
-                                             float2* __restrict__ E, double* __restrict__ lam,
+                                             float2* __restrict__ E,
+                                             const double* __restrict__ lam,
                                              DevHeader* __restrict__ hdr, double inv_max_angle) {
   double e = 0.0;
   if (j < n) {
-    const double li = df_to_d(S[(size_t)i * n + i]) / df_to_d(G[(size_t)i * n + i]);
-    const double lj = df_to_d(S[(size_t)j * n + j]) / df_to_d(G[(size_t)j * n + j]);
-    const double rij = (i == j ? 1.0 : 0.0) - df_to_d(G[(size_t)i * n + j]);
-    const double sij = df_to_d(S[(size_t)i * n + j]);
+    const size_t u = i <= j ? (size_t)i * n + j : (size_t)j * n + i;
+    const double li = lam[i], lj = lam[j];
+    const double rij = (i == j ? 1.0 : 0.0) - df_to_d(G[u]);
+    const double sij = df_to_d(S[u]);
     const double num = sij + lj * rij;
     const double gap = lj - li;
     // classified the same way from (i, j) and (j, i), so that E_ij + E_ji = R_ij;
@@ -200,10 +229,9 @@ __device__ __forceinline__ void refine_E_row(int i, int j, const float2* __restr
     // rank-deficient covariance) count as clustered too
     const double size = fabs(sij) + fmax(fabs(li), fabs(lj)) * fabs(rij);
     const double floor = 64.0 * 2.220446049250313e-16 * hdr->fro;
-    if (i != j && fabs(gap) > inv_max_angle * size && fabs(gap) > floor) e = num / gap;
+    if (i != j && fabs(gap) > inv_max_angle * size && fabs(gap) > floor) e = quotient(num, gap);
     else e = 0.5 * rij;
     E[(size_t)i * n + j] = d_to_df(e);
-    if (i == j) lam[i] = li;
   }
   // largest |E_ij|: one atomic per warp (one max over all B^2 entries on a
   // single word would serialise)
@@ -212,8 +240,16 @@ __device__ __forceinline__ void refine_E_row(int i, int j, const float2* __restr
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_pos(&hdr->refine_res, m);
 }
+__global__ void k_refine_lam(const float2* __restrict__ S, const float2* __restrict__ G, int n,
+                             double* __restrict__ lam, DevHeader* __restrict__ hdr) {
+  refine_lam_entry(blockIdx.x * blockDim.x + threadIdx.x, S, G, n, lam, hdr);
+}
+__global__ void k_refine_lam_batched(const TileDesc* __restrict__ T) {
+  const TileDesc& t = T[blockIdx.y];
+  refine_lam_entry(blockIdx.x * blockDim.x + threadIdx.x, t.s, t.g, t.B, t.lam, t.hdr);
+}
 __global__ void k_refine_E(const float2* __restrict__ S, const float2* __restrict__ G, int n,
-                           float2* __restrict__ E, double* __restrict__ lam,
+                           float2* __restrict__ E, const double* __restrict__ lam,
                            DevHeader* __restrict__ hdr, double inv_max_angle) {
   refine_E_row(blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, S, G, n, E, lam, hdr,
                inv_max_angle);
@@ -224,16 +260,12 @@ __global__ void k_refine_E_batched(const TileDesc* __restrict__ T, double inv_ma
   refine_E_row(blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, t.s, t.g, t.B, t.e, t.lam, t.hdr,
                inv_max_angle);
 }
-__global__ void k_reset_res_batched(TileDesc* __restrict__ T, int ntiles) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < ntiles) T[i].hdr->refine_res = 0.0;
-}
 
 // E = (I - G) / 2: one Newton-Schulz step V <- V (3I - V^T V)/2 = V + V E.
 __device__ __forceinline__ void ns_E_entry(int i, int j, const float2* __restrict__ G, int n,
                                            float2* __restrict__ E) {
   if (j >= n) return;
-  const float2 g = G[(size_t)i * n + j];
+  const float2 g = G[i <= j ? (size_t)i * n + j : (size_t)j * n + i];  // upper triangle
   const float2 r = i == j ? df_add(make_float2(1.f, 0.f), make_float2(-g.x, -g.y))
                           : make_float2(-g.x, -g.y);
   E[(size_t)i * n + j] = make_float2(0.5f * r.x, 0.5f * r.y);
@@ -267,21 +299,21 @@ cudaError_t launch_to_df(const double* src, float2* dst, int count, cudaStream_t
 
 cudaError_t launch_orthonormalize(const float2* v, float2* vout, int B, float2* g, float2* e,
                                   cudaStream_t st) {
-  dfgemm(true, v, v, nullptr, g, B, st);                         // G = V^T V
+  dfgemm(true, v, v, nullptr, g, B, true, st);                   // G = V^T V (upper)
   k_ns_E<<<dim3((B + 127) / 128, B), 128, 0, st>>>(g, B, e);
-  dfgemm(false, v, e, v, vout, B, st);                           // V' = V E + V
+  dfgemm(false, v, e, v, vout, B, false, st);                    // V' = V E + V
   return cudaGetLastError();
 }
 
 cudaError_t launch_refine(const float2* C, int B, const float2* v, float2* vout, double* lam,
                           float2* s, float2* g, float2* e, DevHeader* hdr, double max_angle,
                           cudaStream_t st) {
-  dfgemm(false, C, v, nullptr, vout, B, st);  // W = C V (in vout, free until the last product)
-  dfgemm(true, v, vout, nullptr, s, B, st);   // S = V^T W
-  dfgemm(true, v, v, nullptr, g, B, st);      // G = V^T V
-  cudaMemsetAsync(&hdr->refine_res, 0, sizeof(double), st);
+  dfgemm(false, C, v, nullptr, vout, B, false, st);  // W = C V (in vout until the last product)
+  dfgemm(true, v, vout, nullptr, s, B, true, st);    // S = V^T W (upper)
+  dfgemm(true, v, v, nullptr, g, B, true, st);       // G = V^T V (upper)
+  k_refine_lam<<<(B + 127) / 128, 128, 0, st>>>(s, g, B, lam, hdr);
   k_refine_E<<<dim3((B + 127) / 128, B), 128, 0, st>>>(s, g, B, e, lam, hdr, 1.0 / max_angle);
-  dfgemm(false, v, e, v, vout, B, st);        // V' = V E + V
+  dfgemm(false, v, e, v, vout, B, false, st);        // V' = V E + V
   return cudaGetLastError();
 }
 
@@ -304,7 +336,7 @@ cudaError_t launch_refine_batched(const TileDesc* T, int ntiles, int maxB, bool 
   dfgemm_batched(false, T, ntiles, maxB, kCV, flip, st);
   dfgemm_batched(true, T, ntiles, maxB, kVtW, flip, st);
   dfgemm_batched(true, T, ntiles, maxB, kVtV, flip, st);
-  k_reset_res_batched<<<(ntiles + 127) / 128, 128, 0, st>>>(const_cast<TileDesc*>(T), ntiles);
+  k_refine_lam_batched<<<dim3((maxB + 127) / 128, ntiles), 128, 0, st>>>(T);
   k_refine_E_batched<<<dim3((maxB + 127) / 128, maxB, ntiles), 128, 0, st>>>(T, 1.0 / max_angle);
   dfgemm_batched(false, T, ntiles, maxB, kVEpV, flip, st);
   return cudaGetLastError();
