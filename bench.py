@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched form (256 tiles, 15.9 M pixels)")
+    ap.add_argument("--no-paper-shapes", action="store_true",
+                    help="skip the k=1 fits at the shapes of the paper's tables")
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the differentiation form (forward + backward on 512 x 512 x 200)")
     ap.add_argument("--ncu-case", choices=["scenes", "big", "batched", "batched-small"],
@@ -344,6 +346,57 @@ def run_batched(args, dev, peaks, peak_src):
     return out
 
 
+# the shapes of the paper's Tables 4 and 5 (k = 1) and its GTX 680 times (ms, FP32,
+# PCIe copies included) -- context only, another machine's numbers
+PAPER_SHAPES = [("Jasper-shaped 512x614x224", 512, 614, 224, 216.78, "Table 5"),
+                ("Cuprite-large-shaped 350x350x188", 350, 350, 188, 166.48, "Table 5"),
+                ("Cuprite-small-shaped 250x191x188", 250, 191, 188, 148.68, "Table 5"),
+                ("synthetic 100x100x50", 100, 100, 50, 69.19, "Table 4"),
+                ("synthetic 500x500x50", 500, 500, 50, 89.25, "Table 4"),
+                ("synthetic 300x300x100", 300, 300, 100, 87.68, "Table 4"),
+                ("synthetic 300x300x200", 300, 300, 200, 160.48, "Table 4")]
+
+
+def run_paper_shapes(args, dev):
+    """k = 1 fits (the paper's setting) on scene-like cubes of the paper's shapes,
+    FP32: device-resident and end to end from pinned host memory (the paper's times
+    include the host-device copies)."""
+    import torch
+
+    import paper_2403_18321_gb300 as g
+    import synth
+    rows = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(args.steps, 10))
+    for i, (name, r, c, B, paper_ms, src) in enumerate(PAPER_SHAPES):
+        cube = synth.paper_scene(60 + i, r, c, B, k=1, name=name)
+        Yh = torch.from_numpy(cube.Y).pin_memory()
+        Y = Yh.to(dev)
+        row = {"workload": name, "N": cube.N, "B": B, "k": 1, "paper_ms": paper_ms,
+               "paper_source": src, "paper_hardware": "GTX 680, FP32"}
+        for prec in ("mix", "p32"):
+            ws = g.make_workspace(cube.N, B, 1, 0, prec, dev)
+            for _ in range(3):
+                g.fit(Y, 1, precision=prec, workspace=ws, sync=False)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                g.fit(Y, 1, precision=prec, workspace=ws, sync=False)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            # end to end: copy in, fit, copy the results out, synchronise
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                g.fit_host(Yh, 1, precision=prec, workspace=ws, device=dev)
+            ms_e2e = (time.perf_counter() - t0) / reps * 1e3
+            row[prec] = {"ms": ms, "Mpixel-bands/s": cube.N * B / (ms / 1e3) / 1e6,
+                         "ms_e2e": ms_e2e, "cubes_per_s_e2e": 1e3 / ms_e2e}
+        rows.append(row)
+    return rows
+
+
 def run_ncu_case(args):
     """Fits without timing, for ncu captures of single kernels (-k/-s/-c select them)."""
     import torch
@@ -632,6 +685,10 @@ def main(argv=None):
                 "backward_bytes": 2 * gc.N * gc.B * 4 + 2 * gc.N * gc.k * 4 + gc.N * gc.B * 4,
                 "backward_GB/s": (2 * gc.N * gc.B * 4 + 2 * gc.N * gc.k * 4 + gc.N * gc.B * 4) / tb / 1e9}
 
+    shapes = None
+    if not args.no_paper_shapes and rank == 0:
+        shapes = run_paper_shapes(args, dev)
+
     batched = None
     if not args.no_batched and rank == 0:
         batched = run_batched(args, dev, peaks, peak_src)
@@ -653,7 +710,7 @@ def main(argv=None):
                               "sweeps": [i["sweeps"] for i in infos_p32], **errors.get("p32", {})}},
             "stage_ms_per_step": stage_ms, "roofline": roof, "hbm_kernels": hbm,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "differentiation": diff, "batched": batched}
+            "differentiation": diff, "batched": batched, "paper_shapes_k1": shapes}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -35,7 +35,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, ERR_ARG, ERR_NOCONV, ERR_NONFINITE = 0, 1, 2, 3
-ROW_CYCLIC, ROUND_ROBIN, ODD_EVEN = 0, 1, 2
+ROW_CYCLIC, ROUND_ROBIN, ODD_EVEN, CLASSICAL, GREEDY = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -64,6 +64,8 @@ def _bind(lib):
     lib.oracle_project.argtypes = [P, l, i, P, P, i, P]
     lib.oracle_pca_fit.argtypes = [P, l, i, i, d, i, i, P, P, P, P, P, P, P]
     lib.oracle_backward.argtypes = [P, l, i, i, P, P, P, P, P, d, P]
+    lib.oracle_jacobi_steps.argtypes = [P, i, i, i, d, P]
+    lib.oracle_jacobi_steps.restype = l
     return lib
 
 
@@ -177,6 +179,19 @@ def jacobi(A, tol=1e-14, sweeps_max=60, ordering=ROW_CYCLIC):
                                ctypes.byref(sw), ctypes.byref(off), ctypes.byref(nrot))
     _check(st, (OK, ERR_NOCONV))
     return A, V, dict(status=st, sweeps=sw.value, off_rel=off.value, rotations=nrot.value)
+
+
+def jacobi_steps(A, ordering, steps, thr=0.0):
+    """The first `steps` steps of the classical (one rotation each) or greedy
+    (one iteration of disjoint pairs above thr each) ordering, no stop test.
+    Returns (A, V, rotations)."""
+    A = as_f64(A).copy()
+    B = A.shape[0]
+    V = np.empty((B, B))
+    n = _load().oracle_jacobi_steps(_p(A), B, int(ordering), int(steps), float(thr), _p(V))
+    if n < 0:
+        raise ValueError("oracle_jacobi_steps rejected its arguments")
+    return A, V, int(n)
 
 
 def sort_sign(lam, V):

@@ -195,6 +195,48 @@ static void norms(const double *A, int B, double *off, double *fro) {
 #define ORD_ROW_CYCLIC 0
 #define ORD_ROUND_ROBIN 1
 #define ORD_ODD_EVEN 2
+#define ORD_CLASSICAL 3
+#define ORD_GREEDY 4
+
+/*
+ * Classical pivot (Sec. 4.2 stage 4.1): the off-diagonal element of largest
+ * magnitude in the upper triangle, the first in row-major order on ties.
+ * Returns 0 when every off-diagonal element is 0.
+ */
+static int classical_pivot(const double *A, int B, int *pp, int *pq) {
+  double best = 0.0;
+  int found = 0;
+  for (int i = 0; i < B - 1; ++i)
+    for (int j = i + 1; j < B; ++j) {
+      double a = fabs(A[(size_t)i * B + j]);
+      if (a > best) { best = a; *pp = i; *pq = j; found = 1; }
+    }
+  return found;
+}
+
+/*
+ * One iteration of the manycore's greedy selection (Sec. 5, Code 5.3.1): scan
+ * the upper triangle row by row and take (i, j) when |a_ij| > thr, (i, j) has
+ * not been zeroed yet in this sweep, and neither i nor j is already used in
+ * this iteration; the taken pairs share no index, so their rotations commute
+ * (Sec. 2) and are applied one after the other.  zeroed[B*B] marks the pairs
+ * of the sweep; used[B] is scratch.  Returns the number of pairs rotated.
+ */
+static int greedy_iteration(double *A, double *V, int B, double thr, unsigned char *zeroed,
+                            unsigned char *used, long *nrot) {
+  memset(used, 0, (size_t)B);
+  int taken = 0;
+  for (int i = 0; i < B - 1; ++i)
+    for (int j = i + 1; j < B; ++j) {
+      if (used[i] || used[j] || zeroed[(size_t)i * B + j]) continue;
+      if (!(fabs(A[(size_t)i * B + j]) > thr)) continue;
+      used[i] = used[j] = 1;
+      zeroed[(size_t)i * B + j] = 1;
+      *nrot += rotate_pair(A, V, B, i, j);
+      ++taken;
+    }
+  return taken;
+}
 
 /*
  * Cyclic Jacobi (Sec. 2, Eqs. 6-10; cyclic ordering chosen in Sec. 2 over
@@ -211,7 +253,15 @@ static void norms(const double *A, int B, double *off, double *fro) {
  *     applied one after the other;
  *   2 odd-even: B' rounds; even rounds pair positions (0,1),(2,3),...,
  *     odd rounds (1,2),(3,4),...; after each rotation the two indices swap
- *     positions, so every index pair meets exactly once per sweep.
+ *     positions, so every index pair meets exactly once per sweep;
+ *   3 classical (the GPU host loop of Sec. 4.2 stage 4.1): every rotation
+ *     zeroes the largest off-diagonal element; a "sweep" is B(B-1)/2
+ *     rotations (fewer when the matrix is already diagonal);
+ *   4 greedy (the manycore's Code 5.3.1): iterations of disjoint pairs chosen
+ *     row by row among the elements above thr = tol ||A||_F / sqrt(B(B-1))
+ *     not yet zeroed in the sweep; a sweep ends when an iteration finds none.
+ *     The per-element threshold is the one at which every element below it
+ *     implies the stop test off(A) <= tol ||A||_F.
  * The stop test runs before each sweep: off(A) <= tol * ||A||_F, or
  * ||A||_F == 0.  *sweeps = sweeps run, *off_rel = final off(A)/||A||_F,
  * *rotations = rotations applied.  Returns ORC_ERR_NOCONV if sweeps_max
@@ -226,7 +276,9 @@ int oracle_jacobi(double *A, int B, double tol, int sweeps_max, int ordering,
   for (int i = 0; i < B; ++i) V[(size_t)i * B + i] = 1.0;
   const int Bp = B + (B & 1);
   int *pos = (int *)malloc(sizeof(int) * (size_t)Bp);
-  if (!pos) return ORC_ERR_ARG;
+  unsigned char *zeroed = (unsigned char *)malloc((size_t)B * B + 1);
+  unsigned char *used = (unsigned char *)malloc((size_t)B + 1);
+  if (!pos || !zeroed || !used) { free(pos); free(zeroed); free(used); return ORC_ERR_ARG; }
   long nrot = 0;
   int sw = 0, status = ORC_ERR_NOCONV;
   double off, fro;
@@ -259,17 +311,60 @@ int oracle_jacobi(double *A, int B, double tol, int sweeps_max, int ordering,
           pos[s0 + 1] = a;
         }
       }
+    } else if (ordering == ORD_CLASSICAL) {
+      const long m = (long)B * (B - 1) / 2;
+      for (long r = 0; r < m; ++r) {
+        int p = 0, q = 0;
+        if (!classical_pivot(A, B, &p, &q)) break;
+        nrot += rotate_pair(A, V, B, p, q);
+      }
+    } else if (ordering == ORD_GREEDY) {
+      const double thr = B > 1 ? tol * fro / sqrt((double)B * (B - 1)) : 0.0;
+      memset(zeroed, 0, (size_t)B * B);
+      while (greedy_iteration(A, V, B, thr, zeroed, used, &nrot) > 0) {
+      }
     } else {
-      free(pos);
+      free(pos); free(zeroed); free(used);
       return ORC_ERR_ARG;
     }
     ++sw;
   }
   free(pos);
+  free(zeroed);
+  free(used);
   *sweeps = sw;
   *off_rel = (fro == 0.0) ? 0.0 : off / fro;
   *rotations = nrot;
   return status;
+}
+
+/*
+ * The first `steps` steps of an ordering, without any stop test, for the pins
+ * of the orderings: a step is one rotation (classical) or one iteration of
+ * disjoint pairs (greedy, threshold thr, all in one sweep).  V starts from the
+ * identity.  Returns the number of rotations applied (< 0 on bad arguments).
+ */
+long oracle_jacobi_steps(double *A, int B, int ordering, int steps, double thr, double *V) {
+  if (B < 1 || steps < 0 || (ordering != ORD_CLASSICAL && ordering != ORD_GREEDY)) return -1;
+  memset(V, 0, sizeof(double) * (size_t)B * B);
+  for (int i = 0; i < B; ++i) V[(size_t)i * B + i] = 1.0;
+  long nrot = 0;
+  if (ordering == ORD_CLASSICAL) {
+    for (int s = 0; s < steps; ++s) {
+      int p = 0, q = 0;
+      if (!classical_pivot(A, B, &p, &q)) break;
+      nrot += rotate_pair(A, V, B, p, q);
+    }
+    return nrot;
+  }
+  unsigned char *zeroed = (unsigned char *)calloc((size_t)B * B + 1, 1);
+  unsigned char *used = (unsigned char *)malloc((size_t)B + 1);
+  if (!zeroed || !used) { free(zeroed); free(used); return -1; }
+  for (int s = 0; s < steps; ++s)
+    if (greedy_iteration(A, V, B, thr, zeroed, used, &nrot) == 0) break;
+  free(zeroed);
+  free(used);
+  return nrot;
 }
 
 /*

@@ -166,7 +166,8 @@ def test_3x3_against_characteristic_polynomial(seed):
 # ---------------------------------------------------------------- invariants
 
 @pytest.mark.parametrize("B", [5, 16, 33, 64])
-@pytest.mark.parametrize("ordering", [oracle.ROW_CYCLIC, oracle.ROUND_ROBIN, oracle.ODD_EVEN])
+@pytest.mark.parametrize("ordering", [oracle.ROW_CYCLIC, oracle.ROUND_ROBIN, oracle.ODD_EVEN,
+                                      oracle.CLASSICAL, oracle.GREEDY])
 def test_jacobi_invariants(B, ordering):
     rng = np.random.default_rng(100 + B)
     A, lam_true = rand_sym(rng, B)
@@ -185,10 +186,51 @@ def test_orderings_agree():
     rng = np.random.default_rng(7)
     Y = rng.standard_normal((400, 21)) @ rng.standard_normal((21, 21))
     r0 = oracle.pca_fit(Y, 5)
-    for o in (oracle.ROUND_ROBIN, oracle.ODD_EVEN):
+    for o in (oracle.ROUND_ROBIN, oracle.ODD_EVEN, oracle.CLASSICAL, oracle.GREEDY):
         r = oracle.pca_fit(Y, 5, ordering=o)
         assert np.allclose(r["lam"], r0["lam"], rtol=1e-12, atol=1e-13 * r0["lam"][0])
         assert np.allclose(r["V"], r0["V"], atol=1e-10)
+
+
+def test_classical_rotation_zeroes_the_largest_element_and_off_drops_by_twice_its_square():
+    """Classical pivot (Sec. 4.2 stage 4.1): each rotation zeroes the largest
+    off-diagonal element, and a Jacobi rotation lowers off(A)^2 by exactly 2 a_pq^2
+    (the textbook identity of the Jacobi method)."""
+    rng = np.random.default_rng(31)
+    A, _ = rand_sym(rng, 9)
+    cur = A.copy()
+    off2 = lambda M: float((M ** 2).sum() - (np.diag(M) ** 2).sum())
+    for step in range(6):
+        iu = np.triu_indices(9, 1)
+        k = int(np.argmax(np.abs(cur[iu])))
+        p, q = iu[0][k], iu[1][k]
+        big = cur[p, q]
+        nxt, V, nrot = oracle.jacobi_steps(cur, oracle.CLASSICAL, 1)
+        assert nrot == 1
+        assert nxt[p, q] == 0.0 and nxt[q, p] == 0.0
+        assert abs(off2(cur) - off2(nxt) - 2 * big * big) <= 1e-13 * (A ** 2).sum()
+        assert np.linalg.norm(V.T @ V - np.eye(9)) <= 1e-14
+        cur = nxt
+
+
+def test_greedy_iteration_takes_row_wise_disjoint_pairs_above_threshold():
+    """Greedy selection (Code 5.3.1): one iteration takes, row by row, the pairs
+    above the threshold whose indices are still free -- here (0,1), (2,3), (4,5) --
+    and leaves rows and columns 6, 7 untouched; the next iteration may take a
+    pair it skipped, but never a pair zeroed earlier in the sweep."""
+    B = 8
+    A = np.diag(np.arange(1.0, B + 1.0)) + 0.01
+    for (i, j, v) in [(0, 1, 5.0), (0, 2, 4.0), (2, 3, 3.0), (4, 5, 2.0), (1, 3, 1.5)]:
+        A[i, j] = A[j, i] = v
+    A1, V, nrot = oracle.jacobi_steps(A, oracle.GREEDY, 1, thr=1.0)
+    assert nrot == 3
+    for (i, j) in [(0, 1), (2, 3), (4, 5)]:
+        assert A1[i, j] == 0.0
+    assert A1[6, 7] == A[6, 7] and A1[6, 6] == A[6, 6] and A1[7, 7] == A[7, 7]
+    assert abs(A1[0, 2]) > 1.0                      # rotated, not yet taken
+    A2, _, nrot2 = oracle.jacobi_steps(A, oracle.GREEDY, 2, thr=1.0)
+    assert nrot2 > 3
+    assert A2[6, 7] == A[6, 7]
 
 
 # ---------------------------------------------------------------- planted spectrum
@@ -349,6 +391,12 @@ def test_nonfinite_input_is_reported():
 # ---------------------------------------------------------------- the pins catch mistakes
 
 MUTANTS = {
+    "classical pivot takes the smallest element": (
+        "if (a > best) { best = a; *pp = i; *pq = j; found = 1; }",
+        "if (a > 0.0 && (!found || a < best)) { best = a; *pp = i; *pq = j; found = 1; }"),
+    "greedy ignores used indices": (
+        "if (used[i] || used[j] || zeroed[(size_t)i * B + j]) continue;",
+        "if (zeroed[(size_t)i * B + j]) continue;"),
     "row update sign": ("A[(size_t)p * B + k] = c * apk - s * aqk;",
                         "A[(size_t)p * B + k] = c * apk + s * aqk;"),
     "column update sign": ("A[(size_t)k * B + q] = s * akp + c * akq;",
@@ -449,6 +497,10 @@ def _pins_pass() -> bool:
         for seed in range(2):
             test_3x3_against_characteristic_polynomial(seed)
         test_jacobi_invariants(16, oracle.ROW_CYCLIC)
+        test_jacobi_invariants(16, oracle.CLASSICAL)
+        test_jacobi_invariants(16, oracle.GREEDY)
+        test_classical_rotation_zeroes_the_largest_element_and_off_drops_by_twice_its_square()
+        test_greedy_iteration_takes_row_wise_disjoint_pairs_above_threshold()
         test_planted_spectrum_recovered_exactly()
         test_projection_properties()
         test_sort_is_descending_with_ties_by_index_and_sign_rule()
