@@ -138,8 +138,9 @@ int pca_fit(const void *cube, pca_dtype dtype, int64_t N, int B, int k, double t
  *   covariance form (P64: FP64 accumulation; P32: FP32 SIMT; MIX: split-FP16
  *   tensor cores on per-band shifted and power-of-two scaled values).
  * pca_eigh -- Algorithm 1 stage 4 on a given symmetric matrix A [B][B] FP64
- *   (device): cyclic Jacobi (Eqs. 2-10), FP64 refinement (P32: none, MIX:
- *   one iteration, P64: three), descending sort and sign rule; eigvals [B],
+ *   (device): cyclic Jacobi (Eqs. 2-10), FP64 refinement (P32: none; MIX: two
+ *   iterations and one orthogonalisation step; P64: three and two),
+ *   descending sort and sign rule; eigvals [B],
  *   eigvecs [B][B] as in pca_fit.  The workspace is that of pca_fit with
  *   N = 2 (any N works).
  * pca_project -- Algorithm 1 stages 5-6: proj [N][k] FP32 = (Y - 1 mu^T) V[:, :k]
@@ -154,6 +155,22 @@ int pca_eigh(const double *A, int B, double tol, int sweeps_max, pca_precision p
 int pca_project(const void *cube, pca_dtype dtype, int64_t N, int B, int k, const double *mu,
                 const double *eigvecs, float *proj, void *workspace, size_t ws_bytes,
                 void *stream);
+
+/*
+ * pca_combine_moments -- pooled band means and covariance of a cube whose
+ * pixels are split into `parts` shards (one per GPU of a multi-GPU fit, or
+ * several calls on one GPU); the exchange step of a pixel-sharded fit, which
+ * the paper's manycore version performs over its two I/O halves (Sec. 5).
+ * Shard g has n[g] >= 1 pixels (host array), mean mu_parts[g][B] and
+ * covariance C_parts[g][B][B] (FP64, device, as pca_covariance returns them;
+ * divided by n[g] - 1).  Writes mu [B] and C [B][B] (device) of the union by
+ * the rule of Chan, Golub and LeVeque, in FP64, shards added in index order
+ * (equal inputs give equal bits on every GPU).  1 <= parts <= 256,
+ * 1 <= B <= 256, sum n >= 2, else PCA_ERR_ARG.  No workspace; enqueued on
+ * `stream`, no synchronisation.
+ */
+int pca_combine_moments(int parts, const int64_t *n, const double *mu_parts,
+                        const double *C_parts, int B, double *mu, double *C, void *stream);
 
 /*
  * pca_project_noalloc -- pca_project for callers that cannot allocate.  (No

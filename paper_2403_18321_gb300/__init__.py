@@ -19,7 +19,8 @@ from dataclasses import dataclass
 
 from . import _build
 
-__all__ = ["fit", "fit_host", "fit_batched", "Batch", "workspace_size", "load", "Info", "PCAError",
+__all__ = ["fit", "fit_host", "fit_batched", "fit_sharded", "Batch", "workspace_size", "load",
+           "Info", "PCAError",
            "PREC_P64", "PREC_P32", "PREC_MIX", "STATUS"]
 
 PREC_P64, PREC_P32, PREC_MIX = 0, 1, 2
@@ -31,7 +32,8 @@ EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_p
            "pca_kernel_launches", "pca_profile", "pca_profile_collect", "pca_project_noalloc",
            "pca_jacobi_sms", "pca_backward", "pca_backward_workspace_size",
            "pca_batch_workspace_size", "pca_batch_create", "pca_batch_run", "pca_batch_read_info",
-           "pca_batch_destroy", "pca_fit_batched", "pca_batch_kernel_launches")
+           "pca_batch_destroy", "pca_fit_batched", "pca_batch_kernel_launches",
+           "pca_combine_moments")
 STAGES = ("covariance", "cov_finalize", "jacobi", "empty", "compact", "refine", "sort_sign",
           "project")
 
@@ -119,6 +121,8 @@ def load(build_if_missing: bool = False):
     lib.pca_batch_kernel_launches.restype = i
     lib.pca_fit_batched.argtypes = [i, TP, i, d, i, i, P, sz, P, ctypes.POINTER(Info)]
     lib.pca_fit_batched.restype = i
+    lib.pca_combine_moments.argtypes = [i, ctypes.POINTER(i64), P, P, i, P, P, P]
+    lib.pca_combine_moments.restype = i
     _lib = lib
     return lib
 
@@ -433,6 +437,89 @@ def fit_batched(cubes, k, tol: float = 1e-10, sweeps_max: int = 30, precision="m
     status, infos = b.info()
     b.close()
     return b.results, status, infos
+
+
+def combine_moments(counts, mus, Cs, stream=None):
+    """Pooled (mu [B], C [B, B]) of shards with pixel counts `counts` (ints),
+    means mus [G, B] and covariances Cs [G, B, B] (float64, device)."""
+    import torch
+    mus = mus.to(torch.float64).contiguous()
+    Cs = Cs.to(torch.float64).contiguous()
+    G, B = mus.shape
+    mu = torch.empty(B, dtype=torch.float64, device=mus.device)
+    C = torch.empty(B, B, dtype=torch.float64, device=mus.device)
+    n = (ctypes.c_int64 * G)(*[int(c) for c in counts])
+    st = stream if stream is not None else torch.cuda.current_stream(mus.device)
+    _check_rc(load().pca_combine_moments(G, n, ctypes.c_void_p(mus.data_ptr()),
+                                         ctypes.c_void_p(Cs.data_ptr()), B,
+                                         ctypes.c_void_p(mu.data_ptr()),
+                                         ctypes.c_void_p(C.data_ptr()),
+                                         ctypes.c_void_p(st.cuda_stream)))
+    return mu, C
+
+
+class _LibraryOps:
+    """The stages of a pixel-sharded fit, on this rank's GPU."""
+
+    def __init__(self, precision, tol, sweeps_max):
+        self.precision, self.tol, self.sweeps_max = precision, tol, sweeps_max
+
+    def moments(self, cube):
+        mu, C, _ = covariance(cube, self.precision)
+        return mu, C
+
+    def combine(self, counts, mus, Cs):
+        return combine_moments(counts, mus, Cs)
+
+    def eigh(self, C):
+        ev, V, info = eigh(C, self.tol, self.sweeps_max, self.precision)
+        return ev, V, info
+
+    def project(self, cube, mu, V, k):
+        return project(cube, mu, V, k)
+
+
+def fit_sharded(cube, k: int, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
+                group=None, ops=None):
+    """PCA of a cube whose pixels are split over the ranks of a torch.distributed
+    group: `cube` is this rank's [N_r, B] slice (contiguous and 16-byte aligned,
+    N_r >= 2; clone a slice of a larger cube whose first row does not start on a
+    16-byte boundary).  Each rank computes its band
+    means and covariance; the ranks all-gather (N_r, mu_r, C_r) and pool them
+    (pca_combine_moments); rank 0 of the group solves the pooled covariance and
+    broadcasts eigenvalues and eigenvectors, so that every rank holds the same
+    bits; each rank projects its own pixels.  Returns (mu, eigvals, eigvecs,
+    proj of this rank's pixels, info of the eigen-solve on rank 0 or None).
+    `ops` replaces the four stages (used to test the exchange on CPU ranks)."""
+    import torch
+    import torch.distributed as dist
+    ops = ops if ops is not None else _LibraryOps(precision, tol, sweeps_max)
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    N, B = cube.shape
+    mu_r, C_r = ops.moments(cube)
+    dev = mu_r.device
+    n_r = torch.tensor([N], dtype=torch.int64, device=dev)
+    ns = [torch.empty_like(n_r) for _ in range(world)]
+    mus = [torch.empty_like(mu_r) for _ in range(world)]
+    Cs = [torch.empty_like(C_r) for _ in range(world)]
+    dist.all_gather(ns, n_r, group=group)
+    dist.all_gather(mus, mu_r.contiguous(), group=group)
+    dist.all_gather(Cs, C_r.contiguous(), group=group)
+    counts = [int(x.item()) for x in ns]
+    mu, C = ops.combine(counts, torch.stack(mus), torch.stack(Cs))
+    root = dist.get_global_rank(group, 0) if group is not None else 0
+    info = None
+    if rank == 0:
+        ev, V, info = ops.eigh(C)
+        ev, V = ev.contiguous(), V.contiguous()
+    else:
+        ev = torch.empty(B, dtype=torch.float64, device=dev)
+        V = torch.empty(B, B, dtype=torch.float64, device=dev)
+    dist.broadcast(ev, root, group=group)
+    dist.broadcast(V, root, group=group)
+    Q = ops.project(cube, mu, V, k)
+    return mu, ev, V, Q, info
 
 
 def _autograd_function():
