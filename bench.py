@@ -689,6 +689,34 @@ def main(argv=None):
     if not args.no_paper_shapes and rank == 0:
         shapes = run_paper_shapes(args, dev)
 
+    # band-sequential input (the paper's GPU layout): the conversion to the
+    # pixel-major layout, one read and one write of each scene cube
+    bsq = None
+    if rank == 0:
+        Bq = [y.t().contiguous() for y in Yd]
+        for _ in range(3):
+            for y in Bq:
+                g.bsq_to_bip(y)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps, tot = 10, 0.0
+        for _ in range(reps):
+            flush.fill_(1)        # the cubes (53 MB) would otherwise stay in L2
+            e0.record()
+            for y in Bq:
+                g.bsq_to_bip(y)
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / reps
+        moved = sum(2 * y.numel() * 4 for y in Bq)
+        bsq = {"what": "pca_bsq_to_bip of both scene cubes (read + write), L2 flushed before "
+                       "each repetition", "ms": ms,
+               "GB/s": moved / (ms / 1e3) / 1e9, "frac": moved / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+               "peak_basis": peak_src}
+        del Bq
+
     batched = None
     if not args.no_batched and rank == 0:
         batched = run_batched(args, dev, peaks, peak_src)
@@ -710,7 +738,8 @@ def main(argv=None):
                               "sweeps": [i["sweeps"] for i in infos_p32], **errors.get("p32", {})}},
             "stage_ms_per_step": stage_ms, "roofline": roof, "hbm_kernels": hbm,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "differentiation": diff, "batched": batched, "paper_shapes_k1": shapes}
+            "differentiation": diff, "batched": batched, "paper_shapes_k1": shapes,
+            "bsq_input": bsq}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -157,6 +157,17 @@ int pca_project(const void *cube, pca_dtype dtype, int64_t N, int B, int k, cons
                 void *stream);
 
 /*
+ * pca_bsq_to_bip -- band-sequential input.  The paper's GPU code stores each
+ * band contiguously (Sec. 4.2, data initialisation: value (n, b) at
+ * bsq[b*N + n]); every other entry point takes the pixel-major layout.  This
+ * writes bip[n*B + b] = bsq[b*N + n] (both device arrays of `dtype`, N x B
+ * elements, no alignment requirement, not overlapping), enqueued on `stream`;
+ * the result is a cube for pca_fit.  Returns PCA_ERR_ARG for null pointers,
+ * N < 1 or B < 1.
+ */
+int pca_bsq_to_bip(const void *bsq, pca_dtype dtype, int64_t N, int B, void *bip, void *stream);
+
+/*
  * pca_combine_moments -- pooled band means and covariance of a cube whose
  * pixels are split into `parts` shards (one per GPU of a multi-GPU fit, or
  * several calls on one GPU); the exchange step of a pixel-sharded fit, which

@@ -33,7 +33,7 @@ EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_p
            "pca_jacobi_sms", "pca_backward", "pca_backward_workspace_size",
            "pca_batch_workspace_size", "pca_batch_create", "pca_batch_run", "pca_batch_read_info",
            "pca_batch_destroy", "pca_fit_batched", "pca_batch_kernel_launches",
-           "pca_combine_moments")
+           "pca_combine_moments", "pca_bsq_to_bip")
 STAGES = ("covariance", "cov_finalize", "jacobi", "empty", "compact", "refine", "sort_sign",
           "project")
 
@@ -123,6 +123,8 @@ def load(build_if_missing: bool = False):
     lib.pca_fit_batched.restype = i
     lib.pca_combine_moments.argtypes = [i, ctypes.POINTER(i64), P, P, i, P, P, P]
     lib.pca_combine_moments.restype = i
+    lib.pca_bsq_to_bip.argtypes = [P, i, i64, i, P, P]
+    lib.pca_bsq_to_bip.restype = i
     _lib = lib
     return lib
 
@@ -167,10 +169,29 @@ def _ws_ptr(ws: Workspace) -> int:
     return (p + 255) & ~255
 
 
+def bsq_to_bip(cube_bsq, stream=None):
+    """A band-sequential device cube [B, N] (each band contiguous, the paper's GPU
+    layout) as the pixel-major [N, B] cube the fit reads (pca_bsq_to_bip)."""
+    import torch
+    if not isinstance(cube_bsq, torch.Tensor) or not cube_bsq.is_cuda:
+        raise TypeError("cube must be a CUDA tensor")
+    if cube_bsq.dim() != 2 or not cube_bsq.is_contiguous():
+        raise ValueError("cube must be a contiguous [B, N] tensor")
+    B, N = cube_bsq.shape
+    out = torch.empty(N, B, dtype=cube_bsq.dtype, device=cube_bsq.device)
+    st = stream if stream is not None else torch.cuda.current_stream(cube_bsq.device)
+    _check_rc(load().pca_bsq_to_bip(ctypes.c_void_p(cube_bsq.data_ptr()), _dtype_code(cube_bsq),
+                                    N, B, ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
 def fit(cube, k: int, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
         out=None, workspace: Workspace | None = None, project: bool = True,
-        sync: bool = True, stream=None):
-    """PCA of a device cube [N, B] (float32/bfloat16/float16, pixel-major).
+        sync: bool = True, stream=None, layout: str = "bip"):
+    """PCA of a device cube (float32/bfloat16/float16): [N, B] pixel-major
+    (layout "bip"), or [B, N] band-sequential (layout "bsq", converted first by
+    pca_bsq_to_bip).
 
     Returns (mu [B] f64, eigvals [B] f64, eigvecs [B, B] f64, proj [N, k] f32 or None,
     info dict or None).  With sync=False nothing waits for the GPU and info is None.
@@ -179,7 +200,13 @@ def fit(cube, k: int, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
     if not isinstance(cube, torch.Tensor) or not cube.is_cuda:
         raise TypeError("cube must be a CUDA tensor")
     if cube.dim() != 2 or not cube.is_contiguous():
-        raise ValueError("cube must be a contiguous [N, B] tensor")
+        raise ValueError("cube must be a contiguous 2-D tensor")
+    if layout == "bsq":
+        cube = bsq_to_bip(cube, stream)
+        if stream is not None:
+            cube.record_stream(stream)   # the converted copy stays alive for that stream
+    elif layout != "bip":
+        raise ValueError("layout must be 'bip' or 'bsq'")
     N, B = cube.shape
     dt = _dtype_code(cube)
     prec = _prec_code(precision)
