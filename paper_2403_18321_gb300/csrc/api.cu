@@ -88,8 +88,10 @@ Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, in
   const int Bp = round_even(B);
   if (prec == PCA_PREC_MIX) {
     L.tc_ctas = (int)std::min<int64_t>(num_sms, std::max<int64_t>(1, (N + 127) / 128));
+    // every CTA gets the same number of slots, each at most tc_slot_chunks() long
     const int64_t nchunk = (N + 31) / 32, cap = tc_slot_chunks();
-    L.partials = (int)std::max<int64_t>(L.tc_ctas, (nchunk + cap - 1) / cap);
+    const int64_t per_cta = (nchunk + L.tc_ctas - 1) / L.tc_ctas;
+    L.partials = L.tc_ctas * (int)((per_cta + cap - 1) / cap);
     L.s2_bytes_el = 4;
   } else {
     L.partials = (int)std::min<int64_t>(kMaxPartials, std::max<int64_t>(1, (N + 255) / 256));

@@ -13,7 +13,7 @@
 //               both computed by every CTA from the same pixels), split into
 //               FP16 hi = fp16(x), lo = fp16(x - hi) -- 22 significant bits
 //               of x -- written transposed ([band][pixel], K-major core-
-//               matrix layout) into a 2-stage operand ring, and keep the
+//               matrix layout) into a 3-stage operand ring, and keep the
 //               band sums S1 = sum x of the values they converted (FP32 over
 //               16 chunks, then FP64);
 //   warp 1      MMA issuer (one thread): D += hi hi^T + hi lo^T + lo hi^T
@@ -38,7 +38,7 @@ namespace {
 
 constexpr int kKC = 32;                 // pixels per chunk (K of one stage)
 constexpr int kMaxStages = 12;          // TMA ring depth: as many stages as shared memory holds
-constexpr int kOpStages = 2;            // FP16 operand ring depth
+constexpr int kOpStages = 3;            // FP16 operand ring depth
 constexpr int kRows = 256;              // operand rows (bands, padded to 16)
 constexpr int kConvWarps = 16;
 constexpr int kThreads = (2 + kConvWarps) * 32;
