@@ -68,8 +68,8 @@ typedef enum { PCA_F32 = 0, PCA_BF16 = 1, PCA_F16 = 2 } pca_dtype;
  *     split of the cube, shifted by a sampled band mean and scaled per band
  *     by a power of two (three products, FP32 accumulation in tensor
  *     memory), FP32 Jacobi stopped on the Frobenius test at
- *     max(tol, 1e-5), two refinement iterations and one orthogonalisation
- *     step in double-float/FP64.  The
+ *     max(tol, 1e-5), one refinement iteration and two orthogonalisation
+ *     steps in double-float/FP64.  The
  *     split keeps 22 bits of every value; the remaining covariance error
  *     comes from the tensor cores' FP32 accumulation.  A value that leaves
  *     the scaled FP16 range makes the covariance be recomputed in FP32 on
@@ -138,8 +138,8 @@ int pca_fit(const void *cube, pca_dtype dtype, int64_t N, int B, int k, double t
  *   covariance form (P64: FP64 accumulation; P32: FP32 SIMT; MIX: split-FP16
  *   tensor cores on per-band shifted and power-of-two scaled values).
  * pca_eigh -- Algorithm 1 stage 4 on a given symmetric matrix A [B][B] FP64
- *   (device): cyclic Jacobi (Eqs. 2-10), FP64 refinement (P32: none; MIX: two
- *   iterations and one orthogonalisation step; P64: three and two),
+ *   (device): cyclic Jacobi (Eqs. 2-10), FP64 refinement (P32: none; MIX: one
+ *   iteration and two orthogonalisation steps; P64: three and two),
  *   descending sort and sign rule; eigvals [B],
  *   eigvecs [B][B] as in pca_fit.  The workspace is that of pca_fit with
  *   N = 2 (any N works).

