@@ -622,14 +622,29 @@ def main(argv=None):
         h2d = sum(y.numel() * 4 for y in Yh)
         d2h = sum(sum(t.numel() * t.element_size() for t in o) for o in outs)
 
+        Yin = [torch.empty(y.shape, dtype=y.dtype, device=dev) for y in Yh]
+
         def e2e_step():
-            Ys = [y.to(dev, non_blocking=True) for y in Yh]
-            step(args.precision, ws, outs, Ys)
-            # the copies back wait for both cubes' streams (joined into the current stream)
-            for o, h in zip(outs, host_out):
-                for t, th in zip(o, h):
-                    th.copy_(t, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+            # each cube on its own stream: copy in, fit, copy the results out, so
+            # one cube's copies overlap the other cube's kernels
+            main = torch.cuda.current_stream(dev)
+            fork = torch.cuda.Event()
+            fork.record(main)
+            joins = []
+            for c, yh, yd, w, o, h, st in zip(cubes, Yh, Yin, ws, outs, host_out, side):
+                st.wait_event(fork)
+                with torch.cuda.stream(st):
+                    yd.copy_(yh, non_blocking=True)
+                    g.fit(yd, c.k, tol=c.tol, sweeps_max=c.sweeps_max, precision=args.precision,
+                          out=o, workspace=w, sync=False, stream=st)
+                    for t, th in zip(o, h):
+                        th.copy_(t, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(st)
+                joins.append(ev)
+            for ev in joins:
+                main.wait_event(ev)
+            main.synchronize()
 
         for _ in range(args.warmup):
             e2e_step()

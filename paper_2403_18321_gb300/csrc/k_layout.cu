@@ -1,17 +1,17 @@
 // k_layout.cu -- band-sequential (BSQ) input: the paper's GPU code keeps each
 // band contiguous (Sec. 4.2, data initialisation: image[b*PIXELS + n]); the
 // fit reads pixel-major cubes (band interleaved by pixel, the manycore layout
-// of Sec. 5).  pca_bsq_to_bip transposes one into the other: 32-band x 64-pixel
-// tiles staged in shared memory, read along pixels and written along bands,
-// so both sides move whole 32-byte sectors; one read and one write of the
-// cube (HBM-bound).
+// of Sec. 5).  pca_bsq_to_bip transposes one into the other: 32-band x
+// 128-pixel tiles staged in shared memory, read along pixels and written along
+// bands, so both sides move whole 32-byte sectors, 16 independent loads in
+// flight per thread; one read and one write of the cube (HBM-bound).
 #include "common.cuh"
 
 namespace gbpca {
 namespace {
 
 constexpr int kTb = 32;   // bands per tile
-constexpr int kTp = 64;   // pixels per tile
+constexpr int kTp = 128;  // pixels per tile
 
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -19,13 +19,15 @@ k_bsq_to_bip(const T* __restrict__ bsq, int64_t N, int B, T* __restrict__ bip) {
   __shared__ T tile[kTb][kTp + 1];
   const int64_t p0 = (int64_t)blockIdx.x * kTp;
   const int b0 = blockIdx.y * kTb;
-  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 64 x 4
-  for (int b = ty; b < kTb; b += 4) {
+  const int tx = threadIdx.x & 127, ty = threadIdx.x >> 7;  // 128 x 2
+#pragma unroll
+  for (int b = ty; b < kTb; b += 2) {
     const int64_t p = p0 + tx;
     if (b0 + b < B && p < N) tile[b][tx] = bsq[(int64_t)(b0 + b) * N + p];
   }
   __syncthreads();
   const int lb = threadIdx.x & 31, lp = threadIdx.x >> 5;  // 32 x 8
+#pragma unroll
   for (int p = lp; p < kTp; p += 8) {
     const int64_t n = p0 + p;
     if (b0 + lb < B && n < N) bip[n * B + b0 + lb] = tile[lb][p];

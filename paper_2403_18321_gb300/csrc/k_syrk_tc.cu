@@ -298,6 +298,8 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
     // ---------------------------------------------------------- converters
     const int ct = tid - 64;
     int qs = 0;                       // ring / operand-ring position, continued across items
+    const void* probed = nullptr;     // the cube (and pixel count) whose shift and
+    int64_t probed_n = -1;            // scale are in shs / sesc
     for (int i = 0; i < nitems; ++i) {
       const TcItem it = tc_item(one, T, items, cta_items, i);
       const In* cube = static_cast<const In*>(it.t.cube);
@@ -311,8 +313,11 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
       // so that the sampled deviations scale into (2^5, 2^6] and a scaled value
       // leaves the FP16 range (65504) only if it lies about a thousand times
       // further from the shift than every sampled one.  A degenerate sample
-      // falls back to |shift_b|, then to scale 1.
-      {
+      // falls back to |shift_b|, then to scale 1.  Consecutive items of one
+      // cube (slots of one tile) reuse the values.
+      if (it.t.cube != probed || N != probed_n) {
+        probed = it.t.cube;
+        probed_n = N;
         const int Sp = (int)(N < kProbe ? N : kProbe);
         const int b = ct % kRows, half = ct / kRows;     // 512 threads: two halves of the sample
         double sum = 0.0;
