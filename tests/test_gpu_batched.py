@@ -138,3 +138,40 @@ def test_batch_bad_tile_is_rejected(gbpca_lib):
     assert e.value.status == 1 and "tile 1" in str(e.value)
     with pytest.raises(g.PCAError):
         g.Batch([torch.zeros(64, 257, device="cuda")], 2)
+
+
+@pytest.mark.gpu
+def test_batch_range_guard_recomputes_only_the_flagged_tile(gbpca_lib):
+    """A tile with one value far outside its sampled spread leaves the scaled
+    FP16 range: that tile (and only that one) is recomputed on the SIMT path,
+    and every tile still matches the oracle (the flagged one at P32 accuracy)."""
+    g = gbpca_lib
+    cubes = _cubes(SHAPES[4:9], seed0=600)
+    Ys = [c.Y.copy() for c in cubes]
+    assert Ys[2].shape[0] > 1024
+    Ys[2][1, 7] = 5e6                          # the data lie in [0, 1]
+    dev = [torch.as_tensor(y).cuda() for y in Ys]
+    results, status, infos = g.fit_batched(dev, [c.k for c in cubes], precision="mix")
+    assert status == 0
+    assert [i["cov_fallback"] for i in infos] == [0, 0, 1, 0, 0]
+    for t, (c, y, (mu, ev, V, Q)) in enumerate(zip(cubes, Ys, results)):
+        ref = oracle.pca_fit(y, c.k, tol=1e-14)
+        compare((_host(mu), _host(ev), _host(V), _host(Q)), ref, c.k, "p32" if t == 2 else "mix")
+
+
+@pytest.mark.gpu
+def test_batch_nonfinite_tile_is_reported_alone(gbpca_lib):
+    """A NaN in one tile gives that tile PCA_ERR_NONFINITE; the others fit."""
+    g = gbpca_lib
+    cubes = _cubes(SHAPES[5:8], seed0=700)
+    Ys = [c.Y.copy() for c in cubes]
+    Ys[1][3, 2] = np.nan
+    dev = [torch.as_tensor(y).cuda() for y in Ys]
+    for form in ("mix", "p32"):
+        results, status, infos = g.fit_batched(dev, [c.k for c in cubes], precision=form)
+        assert status == 3
+        assert [i["status"] for i in infos] == [0, 3, 0]
+        for t in (0, 2):
+            ref = oracle.pca_fit(cubes[t].Y, cubes[t].k, tol=1e-14)
+            mu, ev, V, Q = results[t]
+            compare((_host(mu), _host(ev), _host(V), _host(Q)), ref, cubes[t].k, form)
