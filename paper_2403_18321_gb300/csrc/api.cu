@@ -128,7 +128,8 @@ Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, in
 namespace {
 
 struct BwdLayout {
-  size_t hdr, dv_part, dqs_part, dVk, Gk, dA, S32, vk32, mdq, mu32, total;
+  size_t hdr, dv_part, dqs_part, dVk, Gk, dA, S32, vk32, mdq, mu32, xmax_part, dqmax_part, ascale,
+      anshift, bop, fcol, total;
   int parts;
 };
 
@@ -147,6 +148,13 @@ BwdLayout make_bwd_layout(int64_t N, int B, int k, int num_sms) {
   L.vk32 = take(sizeof(float) * (size_t)B * k);
   L.mdq = take(sizeof(float) * (size_t)k);
   L.mu32 = take(sizeof(float) * (size_t)B);
+  L.xmax_part = take(sizeof(float) * (size_t)L.parts * B);
+  L.dqmax_part = take(sizeof(float) * (size_t)L.parts * k);
+  const int B32 = (B + 31) & ~31;                 // the dQ segment of K starts here
+  L.ascale = take(sizeof(float) * (size_t)(B32 + k));
+  L.anshift = take(sizeof(float) * (size_t)(B32 + k));
+  L.bop = take(bwd_bop_bytes(B, k));
+  L.fcol = take(sizeof(float) * (size_t)2 * B);
   L.total = o;
   return L;
 }
@@ -423,6 +431,12 @@ int pca_backward(const void* cube, pca_dtype dt, int64_t N, int B, int k, const 
   w.vk32 = reinterpret_cast<float*>(ws + L.vk32);
   w.mdq = reinterpret_cast<float*>(ws + L.mdq);
   w.mu32 = reinterpret_cast<float*>(ws + L.mu32);
+  w.xmax_part = reinterpret_cast<float*>(ws + L.xmax_part);
+  w.dqmax_part = reinterpret_cast<float*>(ws + L.dqmax_part);
+  w.ascale = reinterpret_cast<float*>(ws + L.ascale);
+  w.anshift = reinterpret_cast<float*>(ws + L.anshift);
+  w.bop = ws + L.bop;
+  w.fcol = reinterpret_cast<float*>(ws + L.fcol);
   DevHeader* hdr = reinterpret_cast<DevHeader*>(ws + L.hdr);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   k_header_init<<<1, 1, 0, st>>>(hdr, 0, 0.f);

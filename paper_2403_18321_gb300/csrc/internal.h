@@ -232,7 +232,23 @@ struct BwdPtrs {
   float* vk32;
   float* mdq;
   float* mu32;
+  float* xmax_part;      // [parts][B] largest |x_b| per CTA
+  float* dqmax_part;     // [parts][k] largest |dq_j| per CTA
+  float* ascale;         // [B32 + k] power-of-two scales of the A operand of dY (B32 = B
+                         // rounded up to 32, where the dQ segment of K starts)
+  float* anshift;        // [B32 + k] -shift * scale
+  unsigned char* bop;    // B operand of dY: FP16 hi/lo planes per 32-wide K block
+  float* fcol;           // [2][B] column scales 2^-f_c of the two K segments
 };
+// Bytes of the B operand planes of the tensor-core dY product.
+size_t bwd_bop_bytes(int B, int k);
+// dY = [X | dQ'] [S'; V_k^T] on the tensor cores (with its scale and operand
+// preparation kernels).
+cudaError_t launch_bwd_dy_tc(const void* cube, pca_dtype dt, const float* dq, int64_t N, int B,
+                             int k, const float* xmax_part, const float* dqmax_part, int parts,
+                             const float* mu32, const float* mdq, const float* S32,
+                             const float* vk32, float* ascale, float* anshift, unsigned char* bop,
+                             float* fcol, float* dY, DevHeader* hdr, cudaStream_t st);
 
 // dY = (dQ - 1 mean dQ) V_k^T + 2/(N-1) X S (the adjoint of the projection
 // layer; dlam nullable).
@@ -282,8 +298,11 @@ cudaError_t launch_sort_sign_batched(const TileDesc* T, int ntiles, int maxB, bo
 // Streamed projection of every item; maps (nullable, 64-byte aligned, one per
 // tile) are 2-D tensor maps of the cubes for the swizzled tiled load.
 // Encodes the 2-D tensor map (CUtensorMap, 128 bytes, 64-byte aligned) of a cube
-// for the tiled projection load; false when the cube does not qualify.
-bool encode_cube_map(pca_dtype dt, const void* cube, int64_t N, int B, void* map);
+// [N][B]: boxes of 128 bytes of a row x box_rows rows, 128-byte swizzle (the
+// tiled projection load uses 64 rows); false when the cube does not qualify
+// (rows not a whole number of 16-byte units, base not 16-byte aligned).
+bool encode_cube_map(pca_dtype dt, const void* cube, int64_t N, int B, void* map,
+                     int box_rows = 64);
 cudaError_t launch_project_grouped(const TileDesc* T, const void* maps, const ProjItem* items,
                                    const int* cta_items, int ctas, int maxB, int maxk,
                                    pca_dtype dt, cudaStream_t st);

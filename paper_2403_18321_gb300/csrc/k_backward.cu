@@ -11,10 +11,12 @@
 //   k_bwd_dv     one streaming pass over cube and dQ (TMA bulk copies of
 //                64-pixel chunks): per-CTA partial sums of X^T dQ and of the
 //                columns of dQ (FP32), thread = band;
+//                the same pass records the largest |x_b| and |dq_j| (the
+//                operand scales of the dY product);
 //   k_bwd_reduce / k_bwd_m / k_bwd_s / k_bwd_sym   the B x B algebra in
 //                FP64 (the FP32 partials added in FP64);
-//   k_bwd_dy     dY as a register-tiled SIMT product [X | dQ'] [S'; V_k^T]
-//                over 128-pixel x 64-band tiles, X centred while staged.
+//   dY           the product [X | dQ'] [S'; V_k^T] on the tensor cores
+//                (k_bwd_dy_tc.cu).
 #include "tma.cuh"
 
 namespace gbpca {
@@ -52,7 +54,8 @@ template <typename In, int KQ>
 __global__ void __launch_bounds__(kDvThreads, 1)
 k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, int B, int k,
          const double* __restrict__ mu, float* __restrict__ dv_part, float* __restrict__ dqs_part,
-         int cube_stage, int dq_stage, DevHeader* __restrict__ hdr) {
+         float* __restrict__ xmax_part, float* __restrict__ dqmax_part, int cube_stage,
+         int dq_stage, DevHeader* __restrict__ hdr) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* cst = smem;                                        // [S][cube_stage]
   float* dqst = reinterpret_cast<float*>(smem + kDvStages * cube_stage);  // [S][dq_stage/4]
@@ -93,6 +96,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
 #pragma unroll
   for (int q = 0; q < KQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   float csum = 0.f;                     // column sum of dQ (threads j < k)
+  float xmax = 0.f, dmax = 0.f;         // largest |x_b| and |dq_j| (operand scales of dY)
   const float m = b < B ? mus[b] : 0.f;
   int c = 0;
   for (; c < nch; ++c) {
@@ -136,6 +140,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
           dv[j] = j < k ? (ed < copied_d ? ds[ed] : dq[p0 * k + ed]) : 0.f;
         }
       }
+      xmax = fmaxf(xmax, fabsf(x));
 #pragma unroll
       for (int q = 0; q < KQ; ++q) {
         acc[q].x = fmaf(x, dv[4 * q], acc[q].x);
@@ -143,7 +148,11 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
         acc[q].z = fmaf(x, dv[4 * q + 2], acc[q].z);
         acc[q].w = fmaf(x, dv[4 * q + 3], acc[q].w);
       }
-      if (tid < k) csum += reinterpret_cast<const float*>(dqp)[p * KQ * 4 + tid];
+      if (tid < k) {
+        const float d = reinterpret_cast<const float*>(dqp)[p * KQ * 4 + tid];
+        csum += d;
+        dmax = fmaxf(dmax, fabsf(d));
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&sy->empty[s]);
@@ -159,7 +168,11 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
         if (4 * q + t < k) out[4 * q + t] = v[t];
     }
   }
-  if (tid < k) dqs_part[(size_t)g * k + tid] = csum;
+  if (tid < k) {
+    dqs_part[(size_t)g * k + tid] = csum;
+    dqmax_part[(size_t)g * k + tid] = dmax;
+  }
+  if (b < B) xmax_part[(size_t)g * B + b] = xmax;
 }
 
 // ------------------------------------------------------------------ k_bwd_reduce
@@ -270,109 +283,10 @@ __global__ void k_bwd_sym(const double* __restrict__ dA, int64_t N, int B, float
   S32[(size_t)a * B + c] = (float)(f * 0.5 * (dA[(size_t)a * B + c] + dA[(size_t)c * B + a]));
 }
 
-// ------------------------------------------------------------------ k_bwd_dy
-// dY[n][c] = sum_b x_nb S'_bc + sum_j (dq_nj - mdq_j) V_cj: the product
-// [X | dQ'] [S'; V_k^T] over 128-pixel x 128-band output tiles (256 threads,
-// 8 x 8 outputs each: pixels {4ty..4ty+3, 64+4ty..}, bands {4tx.., 64+4tx..},
-// read as 16-byte shared-memory vectors), K in steps of 8 with the next step's
-// tiles held in registers while the current one is multiplied; the cube is
-// centred while it is staged.  The band tiles of one pixel block are
-// consecutive blocks of the grid, so that they reuse its cube rows from L2.
-constexpr int kTM = 128, kTN = 128, kTK = 8;
-
-template <typename In>
-__global__ void __launch_bounds__(256, 2)
-k_bwd_dy(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, int B, int k,
-         const float* __restrict__ mu32, const float* __restrict__ mdq, const float* __restrict__ S32,
-         const float* __restrict__ vk32, float* __restrict__ dY) {
-  __shared__ __align__(16) float As[2][kTK][kTM + 4];
-  __shared__ __align__(16) float Bs[2][kTK][kTN + 4];
-  const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
-  const int nbt = (B + kTN - 1) / kTN;
-  const int c0 = (int)(blockIdx.x % nbt) * kTN;
-  const int64_t n0 = (int64_t)(blockIdx.x / nbt) * kTM;
-  const int KT = B + k;
-  // staging roles: A -- pixel ar = tid / 2, columns ak0 .. ak0 + 3;
-  //                B -- row br = tid / 32, bands bc0 .. bc0 + 3
-  const int ar = tid >> 1, ak0 = (tid & 1) * 4;
-  const int br = tid >> 5, bc0 = (tid & 31) * 4;
-  const int64_t an = n0 + ar;
-  float ra[4], rb[4];
-  auto load = [&](int kk) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int col = kk + ak0 + e;
-      float v = 0.f;
-      if (an < N) {
-        if (col < B) v = to_f32<In>(cube[an * B + col]) - mu32[col];
-        else if (col < KT) v = dq[an * k + (col - B)] - mdq[col - B];
-      }
-      ra[e] = v;
-    }
-    const int row = kk + br;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int c = c0 + bc0 + e;
-      float v = 0.f;
-      if (c < B) {
-        if (row < B) v = S32[(size_t)row * B + c];
-        else if (row < KT) v = vk32[(size_t)c * k + (row - B)];
-      }
-      rb[e] = v;
-    }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) As[buf][ak0 + e][ar] = ra[e];
-    *reinterpret_cast<float4*>(&Bs[buf][br][bc0]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
-  };
-  float acc[8][8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  load(0);
-  store(0);
-  __syncthreads();
-  int buf = 0;
-  for (int kk = 0; kk < KT; kk += kTK) {
-    const bool more = kk + kTK < KT;
-    if (more) load(kk + kTK);
-#pragma unroll
-    for (int q = 0; q < kTK; ++q) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][q][4 * ty]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][q][64 + 4 * ty]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][q][4 * tx]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][q][64 + 4 * tx]);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
-    }
-    if (more) {
-      store(buf ^ 1);
-      __syncthreads();
-      buf ^= 1;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int64_t n = n0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + (i - 4));
-    if (n >= N) continue;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = c0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + (j - 4));
-      if (c < B) dY[n * B + c] = acc[i][j];
-    }
-  }
-}
-
 template <typename In, int KQ>
 cudaError_t dv_kq(const In* cube, const float* dq, int64_t N, int B, int k, const double* mu,
-                  float* dv_part, float* dqs_part, int parts, DevHeader* hdr, cudaStream_t st) {
+                  float* dv_part, float* dqs_part, float* xmax_part, float* dqmax_part, int parts,
+                  DevHeader* hdr, cudaStream_t st) {
   const int cube_stage = (int)((((size_t)kDvPx * B * sizeof(In)) + 127) & ~(size_t)127);
   const int dq_stage = (int)((((size_t)kDvPx * k * 4) + 127) & ~(size_t)127);
   const size_t smem = (size_t)kDvStages * (cube_stage + dq_stage) + 256 * 4 +
@@ -380,35 +294,23 @@ cudaError_t dv_kq(const In* cube, const float* dq, int64_t N, int B, int k, cons
   auto kern = k_bwd_dv<In, KQ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<parts, kDvThreads, smem, st>>>(cube, dq, N, B, k, mu, dv_part, dqs_part, cube_stage,
-                                        dq_stage, hdr);
+  kern<<<parts, kDvThreads, smem, st>>>(cube, dq, N, B, k, mu, dv_part, dqs_part, xmax_part,
+                                        dqmax_part, cube_stage, dq_stage, hdr);
   return cudaGetLastError();
 }
 
 template <typename In>
 cudaError_t dv_typed(const In* cube, const float* dq, int64_t N, int B, int k, const double* mu,
-                     float* dv_part, float* dqs_part, int parts, DevHeader* hdr, cudaStream_t st) {
+                     const BwdPtrs& w, DevHeader* hdr, cudaStream_t st) {
   switch ((k + 3) / 4) {
-    case 1: return dv_kq<In, 1>(cube, dq, N, B, k, mu, dv_part, dqs_part, parts, hdr, st);
-    case 2: return dv_kq<In, 2>(cube, dq, N, B, k, mu, dv_part, dqs_part, parts, hdr, st);
-    case 3: return dv_kq<In, 3>(cube, dq, N, B, k, mu, dv_part, dqs_part, parts, hdr, st);
-    case 4: return dv_kq<In, 4>(cube, dq, N, B, k, mu, dv_part, dqs_part, parts, hdr, st);
-    case 5: return dv_kq<In, 5>(cube, dq, N, B, k, mu, dv_part, dqs_part, parts, hdr, st);
-    case 6: return dv_kq<In, 6>(cube, dq, N, B, k, mu, dv_part, dqs_part, parts, hdr, st);
-    case 7: return dv_kq<In, 7>(cube, dq, N, B, k, mu, dv_part, dqs_part, parts, hdr, st);
-    case 8: return dv_kq<In, 8>(cube, dq, N, B, k, mu, dv_part, dqs_part, parts, hdr, st);
+#define GB_DV_CASE(q) \
+    case q: return dv_kq<In, q>(cube, dq, N, B, k, mu, w.dv_part, w.dqs_part, w.xmax_part, \
+                                w.dqmax_part, w.parts, hdr, st);
+    GB_DV_CASE(1) GB_DV_CASE(2) GB_DV_CASE(3) GB_DV_CASE(4)
+    GB_DV_CASE(5) GB_DV_CASE(6) GB_DV_CASE(7) GB_DV_CASE(8)
+#undef GB_DV_CASE
   }
   return cudaErrorInvalidValue;
-}
-
-template <typename In>
-cudaError_t dy_typed(const In* cube, const float* dq, int64_t N, int B, int k, const float* mu32,
-                     const float* mdq, const float* S32, const float* vk32, float* dY,
-                     cudaStream_t st) {
-  const int64_t tiles = (int64_t)((B + kTN - 1) / kTN) * ((N + kTM - 1) / kTM);
-  if (tiles > 0x7fffffffll) return cudaErrorInvalidValue;
-  k_bwd_dy<In><<<(unsigned)tiles, 256, 0, st>>>(cube, dq, N, B, k, mu32, mdq, S32, vk32, dY);
-  return cudaGetLastError();
 }
 
 }  // namespace
@@ -419,16 +321,9 @@ cudaError_t launch_backward(const void* cube, pca_dtype dt, int64_t N, int B, in
                             const BwdPtrs& w, DevHeader* hdr, cudaStream_t st) {
   cudaError_t e;
   switch (dt) {
-    case PCA_F32:
-      e = dv_typed((const float*)cube, dq, N, B, k, mu, w.dv_part, w.dqs_part, w.parts, hdr, st);
-      break;
-    case PCA_BF16:
-      e = dv_typed((const __nv_bfloat16*)cube, dq, N, B, k, mu, w.dv_part, w.dqs_part, w.parts, hdr,
-                   st);
-      break;
-    case PCA_F16:
-      e = dv_typed((const __half*)cube, dq, N, B, k, mu, w.dv_part, w.dqs_part, w.parts, hdr, st);
-      break;
+    case PCA_F32: e = dv_typed((const float*)cube, dq, N, B, k, mu, w, hdr, st); break;
+    case PCA_BF16: e = dv_typed((const __nv_bfloat16*)cube, dq, N, B, k, mu, w, hdr, st); break;
+    case PCA_F16: e = dv_typed((const __half*)cube, dq, N, B, k, mu, w, hdr, st); break;
     default:
       return cudaErrorInvalidValue;
   }
@@ -438,15 +333,9 @@ cudaError_t launch_backward(const void* cube, pca_dtype dt, int64_t N, int B, in
   k_bwd_s<<<B, 256, 0, st>>>(V, w.Gk, dlam, N, B, k, w.dA, w.vk32);
   k_bwd_sym<<<dim3((B + 127) / 128, B), 128, 0, st>>>(w.dA, N, B, w.S32);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  switch (dt) {
-    case PCA_F32:
-      return dy_typed((const float*)cube, dq, N, B, k, w.mu32, w.mdq, w.S32, w.vk32, dY, st);
-    case PCA_BF16:
-      return dy_typed((const __nv_bfloat16*)cube, dq, N, B, k, w.mu32, w.mdq, w.S32, w.vk32, dY, st);
-    case PCA_F16:
-      return dy_typed((const __half*)cube, dq, N, B, k, w.mu32, w.mdq, w.S32, w.vk32, dY, st);
-  }
-  return cudaErrorInvalidValue;
+  // dY on the tensor cores (k_bwd_dy_tc.cu)
+  return launch_bwd_dy_tc(cube, dt, dq, N, B, k, w.xmax_part, w.dqmax_part, w.parts, w.mu32,
+                          w.mdq, w.S32, w.vk32, w.ascale, w.anshift, w.bop, w.fcol, dY, hdr, st);
 }
 
 }  // namespace gbpca

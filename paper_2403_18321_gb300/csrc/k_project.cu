@@ -371,14 +371,14 @@ template <> constexpr CUtensorMapDataType tmap_type<__half>() { return CU_TENSOR
 // 2-D map of a cube [N][B] for the swizzled tiled load: boxes of 128 bytes x
 // kPc pixels.  False when the rows are not whole 16-byte units or encoding fails.
 template <typename In>
-bool encode_map(const void* cube, int64_t N, int B, CUtensorMap* map) {
+bool encode_map(const void* cube, int64_t N, int B, CUtensorMap* map, int box_rows = kPc) {
   memset(map, 0, sizeof(*map));
   if ((B * sizeof(In)) % 16 != 0 || ((uintptr_t)cube % 16) != 0 || N >= (1ll << 31) ||
       encode_fn() == nullptr)
     return false;
   const cuuint64_t gdim[2] = {(cuuint64_t)B, (cuuint64_t)N};
   const cuuint64_t gstride[1] = {(cuuint64_t)B * sizeof(In)};
-  const cuuint32_t box[2] = {(cuuint32_t)(128 / sizeof(In)), (cuuint32_t)kPc};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / sizeof(In)), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return encode_fn()(map, tmap_type<In>(), 2, const_cast<void*>(cube), gdim, gstride, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -439,12 +439,12 @@ cudaError_t project_typed(const In* cube, int64_t N, int B, int k, const float* 
 
 }  // namespace
 
-bool encode_cube_map(pca_dtype dt, const void* cube, int64_t N, int B, void* map) {
+bool encode_cube_map(pca_dtype dt, const void* cube, int64_t N, int B, void* map, int box_rows) {
   CUtensorMap* m = static_cast<CUtensorMap*>(map);
   switch (dt) {
-    case PCA_F32: return encode_map<float>(cube, N, B, m);
-    case PCA_BF16: return encode_map<__nv_bfloat16>(cube, N, B, m);
-    case PCA_F16: return encode_map<__half>(cube, N, B, m);
+    case PCA_F32: return encode_map<float>(cube, N, B, m, box_rows);
+    case PCA_BF16: return encode_map<__nv_bfloat16>(cube, N, B, m, box_rows);
+    case PCA_F16: return encode_map<__half>(cube, N, B, m, box_rows);
   }
   return false;
 }

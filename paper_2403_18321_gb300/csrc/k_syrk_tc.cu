@@ -30,7 +30,7 @@
 // finalised by k_cov.cu.  Every mbarrier wait is bounded (one second of
 // globaltimer); on time-out the CTA records PCA_ERR_TIMEOUT, drains its MMAs,
 // frees TMEM and returns.
-#include "tma.cuh"
+#include "tc.cuh"
 
 namespace gbpca {
 
@@ -61,57 +61,8 @@ struct __align__(8) SyncBlock {
   int abort;
 };
 
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// K-major, no swizzle: core matrix = 8 rows x 16 bytes; LBO = K stride, SBO = row-group stride.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((kSBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-// kind::f16 instruction descriptor: D F32, A/B F16 (format 0), both K-major,
-// M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_f16(int n) {
-  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   su32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
-  uint32_t r;  // low half = a, high half = b
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
-  return r;
-}
-__device__ __forceinline__ void unpack_f16x2(uint32_t v, float& a, float& b) {
-  a = __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
-  b = __half2float(__ushort_as_half((unsigned short)(v >> 16)));
-}
+// K-major operand descriptor of the ring layout (kLBO, kSBO)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) { return sdesc_kmajor(addr, kLBO, kSBO); }
 
 template <typename In>
 __device__ __forceinline__ float elem(const In* p) { return to_f32<In>(*p); }
