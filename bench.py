@@ -54,13 +54,14 @@ def parse_args(argv=None):
                     help="skip the k=1 fits at the shapes of the paper's tables")
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the differentiation form (forward + backward on 512 x 512 x 200)")
-    ap.add_argument("--ncu-case", choices=["scenes", "big", "batched", "batched-small"],
+    ap.add_argument("--ncu-case", choices=["scenes", "big", "batched", "batched-small", "backward"],
                     default=None,
                     help="untimed fits for profiler captures: 'scenes' = the bench cubes, "
                          "'big' = one 1024x400x224 scene cube (367 MB, larger than L2), "
                          "'batched' = the 256-tile batch (10 GB), 'batched-small' = its first "
-                         "48 tiles with N / 4 (about 0.5 GB); runs --warmup + --steps fits "
-                         "and prints no JSON line")
+                         "48 tiles with N / 4 (about 0.5 GB), 'backward' = the adjoint on the "
+                         "512x512x200 gradient cube; runs --warmup + --steps fits (or "
+                         "backward passes) and prints no JSON line")
     return ap.parse_args(argv)
 
 
@@ -404,6 +405,16 @@ def run_ncu_case(args):
     import paper_2403_18321_gb300 as g
     import synth
     g.load()
+    if args.ncu_case == "backward":
+        gc = synth.gradient_cube()
+        Y = torch.from_numpy(gc.Y).cuda()
+        dQ = torch.from_numpy(gc.meta["dQ"]).cuda()
+        mu, ev, V, _, _ = g.fit(Y, gc.k, precision=args.precision)
+        for _ in range(args.warmup + args.steps):
+            dY = g.backward(Y, mu, ev, V, dQ)
+        torch.cuda.synchronize()
+        print(f"backward {gc.N}x{gc.B} k={gc.k}: |dY| max {dY.abs().max().item():.3e}")
+        return 0
     if args.ncu_case in ("batched", "batched-small"):
         specs = synth.tile_batch_specs(seed=3)
         if args.ncu_case == "batched-small":
