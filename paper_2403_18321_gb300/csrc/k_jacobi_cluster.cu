@@ -28,22 +28,34 @@
 //     (distributed shared memory), so a step needs no CTA-local barrier.
 //   * Whoever rotates the diagonal block of a pair of the next step writes
 //     one 16-byte record (c, s, new a_pp, new a_qq) into every CTA of the
-//     cluster.  Records rotate through three slots by global step number,
-//     so the diagonal of the last two steps stays readable and the V
-//     rotations of a step can run after the cluster-barrier arrive.
+//     cluster.  Records rotate through four slots by global step number.
 //   * V rows live in registers: lane l of a warp holds positions
 //     [W l, W l + W) of a row.  Even-step pairs are lane-local; an odd-step
 //     pair that straddles two lanes is completed by both lanes from one
 //     shuffle each way.
-//   * One cluster barrier (arrive.release / wait.acquire) per step.
+//   * No cluster barrier inside a sweep.  Records and handed-over row
+//     values travel as st.async stores that complete on the receiver's
+//     mbarrier of the step they feed (one per record slot); each CTA's
+//     mbarrier of step s+1 also takes one arrival per local warp (its
+//     shared-memory writes of step s), with the byte count of the records
+//     and row values it will receive.  A CTA starts step s+1 when that
+//     phase completes, so no CTA runs more than one step ahead of another:
+//     when a CTA pushes the records of step s+2, every CTA has at least
+//     entered step s and reads slots s-1 and s only (four slots suffice),
+//     and a handed-over row is written only after its holder sent its own
+//     values of that row for the previous step (after its last read).
 // Control flow is identical in every CTA (the stop decision is made by CTA 0
-// and broadcast), so every CTA reaches every cluster barrier.
+// and broadcast), so every CTA reaches every cluster barrier (three per
+// sweep, at its start).  Every mbarrier wait is bounded; a CTA that gives up
+// stops waiting and the sweep's stop test ends the solve with
+// PCA_ERR_TIMEOUT.
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -60,7 +72,7 @@ constexpr int kVRows = 2;         // V rows per bulk warp (checked), default var
 constexpr int kWideVRows = 3;     // the same for the fewer-CTA variant
 constexpr int kWideItems = 3;
 constexpr int kMaxCl = 8;
-constexpr int kSlots = 3;
+constexpr int kSlots = 4;
 constexpr int kRecs = 128;        // records per slot: 32 lanes x W/2 pairs, W <= 8
 constexpr uint32_t kNone = 0xffffffffu;
 
@@ -127,10 +139,15 @@ __device__ __forceinline__ void rot_block(float2 csI, float2 csJ, float& m00, fl
 }
 
 struct Shared {
+  uint64_t mbar[kSlots];  // step s+1 completes on mbar[(s + 1) % kSlots]
   float4 rec[kSlots][kRecs];
   float dg[kMaxB];        // diagonal at the sweep boundary
   double part_o[kMaxCl], part_d[kMaxCl];
   int part_v[kMaxCl];
+  int part_a[kMaxCl];
+  int abort;
+  uint32_t halo_a, first_a;  // handed-over rows in the neighbours' windows
+  uint32_t halo_bytes[2];    // row-value bytes received after even / odd steps
   double wred[2][32];
   int wviol[32];
   int flag;
@@ -145,6 +162,7 @@ __device__ __forceinline__ int rix(int J) { return (J % H) * 32 + J / H; }
 
 __device__ __forceinline__ float2 cs_of(const float4& r) { return make_float2(r.x, r.y); }
 
+// Plain remote stores, ordered by the cluster barrier that follows (sweep start).
 template <int H>
 __device__ __forceinline__ void push_record(cg::cluster_group& cl, Shared* sh, int ncl, int slot,
                                             int J, float4 r) {
@@ -152,11 +170,60 @@ __device__ __forceinline__ void push_record(cg::cluster_group& cl, Shared* sh, i
   for (int q = 0; q < ncl; ++q) cl.map_shared_rank(sh, q)->rec[slot][i] = r;
 }
 
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+// Shared-memory address a (this CTA's window) in the window of CTA `rank`.
+__device__ __forceinline__ uint32_t mapa(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
 }
-__device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+// Stores into a CTA of the cluster that complete-tx their bytes on that
+// CTA's mbarrier `bar` (both addresses in the receiver's window).
+__device__ __forceinline__ void st_async(uint32_t a, float4 v, uint32_t bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(a),
+      "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t a, float x, float y, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(a),
+               "f"(x), "f"(y), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t a, float x, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(a),
+               "f"(x), "r"(bar)
+               : "memory");
+}
+// A record of the next step into every CTA (slot and mbarrier of that step).
+template <int H>
+__device__ __forceinline__ void push_record_async(Shared* sh, int ncl, int slot, int J, float4 r) {
+  const uint32_t a = su32(&sh->rec[slot][rix<H>(J)]), bar = su32(&sh->mbar[slot]);
+  for (int q = 0; q < ncl; ++q) st_async(mapa(a, q), r, mapa(bar, q));
+}
+// Phase wait with cluster-scope acquire (the st.async data of other CTAs).
+__device__ __forceinline__ bool mbar_try_cluster(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+static __device__ __noinline__ void mbar_wait_cluster_slow(uint64_t* b, uint32_t parity, int* abort) {
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    if (*(volatile int*)abort) return;
+    if (mbar_try_cluster(b, parity)) return;
+    if (gtimer() - t0 > kWaitNs) {
+      atomicExch(abort, 1);
+      return;
+    }
+  }
+}
+__device__ __forceinline__ void mbar_wait_cluster(uint64_t* b, uint32_t parity, int* abort) {
+  if (!mbar_try_cluster(b, parity)) mbar_wait_cluster_slow(b, parity, abort);
 }
 
 // Diagonal position x after an odd step (records in slot so) preceded by an
@@ -207,9 +274,9 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
   const int V0 = (int)((long)Bp * rank / ncl), V1 = (int)((long)Bp * (rank + 1) / ncl);
   // remote copies a handed-over row goes to: the previous CTA's halo row
   // (after even steps) and the next CTA's first row (after odd steps)
-  float* halo_prev =
-      rank > 0 ? cl.map_shared_rank(rows, rank - 1) + (size_t)(2 * (I_lo - prev_lo)) * Bp : nullptr;
-  float* first_next = rank + 1 < ncl ? cl.map_shared_rank(rows, rank + 1) : nullptr;
+  // (kept in shared memory: they are used by few threads, and registers are full)
+  const bool has_prev = rank > 0, has_next = rank + 1 < ncl;
+  const int halo_row = 2 * (I_lo - prev_lo);  // in the previous CTA's rows
 
   // ---- uniform early exit (every CTA reads the same header word)
   if (par(one, list).hdr->nonfinite) {
@@ -225,17 +292,31 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
   }
 
   // ---- matrix rows, and records that reproduce the initial diagonal as the
-  //      state after an odd step (slot 2) preceded by an even step (slot 1)
+  //      state after an odd step (slot 3) preceded by an even step (slot 2)
   for (int e = tid; e < nrows * Bp; e += kThreads) {
     const int i = R0 + e / Bp, j = e % Bp;
     rows[e] = (i < B && j < B) ? (float)C[(size_t)i * B + j] : 0.f;
   }
   auto d0 = [&](int i) { return i < B ? (float)C[(size_t)i * B + i] : 0.f; };
   for (int J = tid; J < P; J += kThreads) {
-    sh.rec[1][rix<H>(J)] = make_float4(1.f, 0.f, d0(2 * J), d0(2 * J + 1));
-    sh.rec[2][rix<H>(J)] = make_float4(1.f, 0.f, d0(2 * J + 1), J + 1 < P ? d0(2 * J + 2) : 0.f);
+    sh.rec[2][rix<H>(J)] = make_float4(1.f, 0.f, d0(2 * J), d0(2 * J + 1));
+    sh.rec[3][rix<H>(J)] = make_float4(1.f, 0.f, d0(2 * J + 1), J + 1 < P ? d0(2 * J + 2) : 0.f);
   }
-  if (tid == 0) { sh.ovf = 0; sh.flag = 0; }
+  if (tid == 0) {
+    sh.ovf = 0;
+    sh.flag = 0;
+    sh.abort = 0;
+    sh.halo_a = has_prev ? mapa(su32(rows) + 4u * (uint32_t)(halo_row * Bp), rank - 1) : 0u;
+    sh.first_a = has_next ? mapa(su32(rows), rank + 1) : 0u;
+    // bytes of handed-over row values this CTA receives per step: after an
+    // even step the next CTA's first row from column 2 I_hi + 2 on (its
+    // blocks J = I_hi + 1 .. P - 1); after an odd step columns 2 I_lo + 1 ..
+    // B' - 1 of this CTA's first row, from the previous CTA
+    sh.halo_bytes[0] = has_next ? 8u * (uint32_t)max(0, P - 1 - I_hi) : 0u;
+    sh.halo_bytes[1] = has_prev ? 4u * (uint32_t)(2 * max(0, P - 1 - I_lo) + 1) : 0u;
+    for (int k = 0; k < kSlots; ++k) mbar_init(&sh.mbar[k], kThreads / 32);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
 
   // ---- V rows in registers: bulk warp bw holds rows V0 + bw + kBulkWarps*k
   float v[VR][W];
@@ -299,12 +380,12 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
   if (ovf && rank == 0 && tid == 0) set_status(par(one, list).hdr, PCA_ERR_ARG);
 
   int sweep = 0, status = PCA_OK;
-  int gs = 0;                    // global step number; step gs uses record slot gs % 3
+  int gs = 0;                    // global step number; step gs uses record slot gs % 4
   const float tol2 = par(one, list).tol32 * par(one, list).tol32;
   for (; !ovf;) {
     // ---------------- diagonal at the sweep boundary (after the last odd step)
     {
-      const int so = (gs + 2) % kSlots, se = (gs + 1) % kSlots;
+      const int so = (gs + 3) % kSlots, se = (gs + 2) % kSlots;
       for (int x = tid; x < Bp; x += kThreads) sh.dg[x] = diag_after_odd<H>(&sh, so, se, x, Bp);
     }
     __syncthreads();
@@ -343,18 +424,25 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
           s0->part_o[rank] = o;
           s0->part_d[rank] = d;
           s0->part_v[rank] = anyv;
+          s0->part_a[rank] = *(volatile int*)&sh.abort;
         }
       }
     }
     cl.sync();
     if (rank == 0 && tid == 0) {
       double o = 0.0, d = 0.0;
-      int anyv = 0;
-      for (int r = 0; r < ncl; ++r) { o += sh.part_o[r]; d += sh.part_d[r]; anyv |= sh.part_v[r]; }
+      int anyv = 0, anya = 0;
+      for (int r = 0; r < ncl; ++r) {
+        o += sh.part_o[r];
+        d += sh.part_d[r];
+        anyv |= sh.part_v[r];
+        anya |= sh.part_a[r];
+      }
       const double off = sqrt(2.0 * o), fro = sqrt(2.0 * o + d);
       const bool conv = par(one, list).relative_stop ? !anyv : off <= (double)par(one, list).tol32 * fro;
       int flag = 0;
-      if (fro == 0.0 || conv) flag = 1;
+      if (anya) flag = 3;
+      else if (fro == 0.0 || conv) flag = 1;
       else if (sweep >= par(one, list).sweeps_max) flag = 2;
       for (int r = 0; r < ncl; ++r) cl.map_shared_rank(&sh, r)->flag = flag;
       sh.off_rel = fro == 0.0 ? 0.0 : off / fro;
@@ -362,7 +450,10 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
     }
     cl.sync();
     const int flag = sh.flag;
-    if (flag) { status = flag == 1 ? PCA_OK : PCA_ERR_NOCONV; break; }
+    if (flag) {
+      status = flag == 1 ? PCA_OK : (flag == 2 ? PCA_ERR_NOCONV : PCA_ERR_TIMEOUT);
+      break;
+    }
 
     // ---------------- the first (even) step's pairs: rotate their diagonal blocks
     if (tid < I_hi - I_lo) {
@@ -370,14 +461,20 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
       float* apq = rows + (p - R0) * Bp + p + 1;
       push_record<H>(cl, &sh, ncl, gs % kSlots, I, pair_record(sh.dg[p], sh.dg[p + 1], *apq));
       *apq = 0.f;
-      if (I == I_lo && halo_prev) halo_prev[p + 1] = 0.f;
+      if (I == I_lo && has_prev) cl.map_shared_rank(rows, rank - 1)[(size_t)halo_row * Bp + p + 1] = 0.f;
     }
     cl.sync();
 
     auto step_body = [&](auto E_, bool last) {
       constexpr int e = decltype(E_)::value;
       const int np = P - e;
-      const int cur = gs % kSlots, nxt = (gs + 1) % kSlots, prv = (gs + 2) % kSlots;
+      const int cur = gs % kSlots, nxt = (gs + 1) % kSlots, prv = (gs + 3) % kSlots;
+      const uint32_t bar_nxt = su32(&sh.mbar[nxt]);
+      // stores into the previous CTA's halo row / the next CTA's first row
+      auto to_prev = [&](int col, float x, float y) {
+        st_async(sh.halo_a + 4u * col, x, y, mapa(bar_nxt, rank - 1));
+      };
+      auto to_next = [&](int col, float x) { st_async(sh.first_a + 4u * col, x, mapa(bar_nxt, rank + 1)); };
       const float4* rc = sh.rec[cur];
       if (band) {
         // super-diagonal blocks (I, I+1) of this CTA's row pairs
@@ -398,17 +495,19 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
           const float4 gI = rc[rix<H>(I)], gJ = rc[rix<H>(I + 1)];
           rot_block(cs_of(gI), cs_of(gJ), m00, m01, m10, m11);
           if (!last) {  // (q_I, p_{I+1}) is the off-diagonal of a next-step pair
-            push_record<H>(cl, &sh, ncl, nxt, e == 0 ? I : I + 1, pair_record(gI.w, gJ.z, m10));
+            push_record_async<H>(&sh, ncl, nxt, e == 0 ? I : I + 1, pair_record(gI.w, gJ.z, m10));
             m10 = 0.f;
           }
           if (e == 0) {
             *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
             *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
-            if (I == I_lo && halo_prev)
-              *reinterpret_cast<float2*>(halo_prev + pI + 2) = make_float2(m00, m01);
+            if (I == I_lo && has_prev) to_prev(pI + 2, m00, m01);
           } else {
             r0[0] = m00; r0[1] = m01; r1[0] = m10; r1[1] = m11;
-            if (I == I_hi - 1 && first_next) { first_next[pI + 2] = m10; first_next[pI + 3] = m11; }
+            if (I == I_hi - 1 && has_next) {
+              to_next(pI + 2, m10);
+              to_next(pI + 3, m11);
+            }
           }
         }
         if (e) {
@@ -422,7 +521,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
             float n0 = fmaf(x, g.y, y * g.x);
             const float n1 = fmaf(x, g.x, -y * g.y);
             if (!last) {
-              push_record<H>(cl, &sh, ncl, nxt, 0, pair_record(sh.rec[prv][rix<H>(0)].z, g.z, n0));
+              push_record_async<H>(&sh, ncl, nxt, 0, pair_record(sh.rec[prv][rix<H>(0)].z, g.z, n0));
               n0 = 0.f;
             }
             a[0] = n0;
@@ -435,13 +534,13 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
             const float n0 = fmaf(g.y, x, g.x * y);
             float n1 = fmaf(g.x, x, -g.y * y);
             if (!last) {
-              push_record<H>(cl, &sh, ncl, nxt, P - 1,
-                             pair_record(g.w, sh.rec[prv][rix<H>(P - 1)].w, n1));
+              push_record_async<H>(&sh, ncl, nxt, P - 1,
+                                   pair_record(g.w, sh.rec[prv][rix<H>(P - 1)].w, n1));
               n1 = 0.f;
             }
             a[0] = n0;
             a[Bp] = n1;
-            if (P - 2 == I_hi - 1 && first_next) first_next[Bp - 1] = n1;
+            if (P - 2 == I_hi - 1 && has_next) to_next(Bp - 1, n1);
           }
         }
       } else {
@@ -465,13 +564,12 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
           if (e == 0) {
             *reinterpret_cast<float2*>(r0) = make_float2(m00, m01);
             *reinterpret_cast<float2*>(r1) = make_float2(m10, m11);
-            if (I == I_lo && halo_prev)
-              *reinterpret_cast<float2*>(halo_prev + 2 * J) = make_float2(m00, m01);
+            if (I == I_lo && has_prev) to_prev(2 * J, m00, m01);
           } else {
             r0[0] = m00; r0[1] = m01; r1[0] = m10; r1[1] = m11;
-            if (I == I_hi - 1 && first_next) {
-              first_next[2 * J + 1] = m10;
-              first_next[2 * J + 2] = m11;
+            if (I == I_hi - 1 && has_next) {
+              to_next(2 * J + 1, m10);
+              to_next(2 * J + 2, m11);
             }
           }
         }
@@ -491,14 +589,21 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
             const float n1 = fmaf(g.x, x, -g.y * y);
             a[0] = fmaf(g.y, x, g.x * y);
             a[Bp] = n1;
-            if (I == I_hi - 1 && first_next) first_next[Bp - 1] = n1;
+            if (I == I_hi - 1 && has_next) to_next(Bp - 1, n1);
           }
         }
       }
-      cluster_arrive();
+      // this warp's shared-memory writes of the step are done: arrive on the
+      // next step's mbarrier (warp 0 with the bytes this CTA will receive)
+      __syncwarp();
+      if (lane == 0) {
+        if (warp == 0)
+          mbar_expect_tx(&sh.mbar[nxt], (last ? 0u : 16u * (uint32_t)(P - 1 + e)) + sh.halo_bytes[e]);
+        else
+          mbar_arrive(&sh.mbar[nxt]);
+      }
       // V rows: (v_p, v_q) <- (v_p, v_q) G for every pair of this step.  The
-      // records of this slot are rewritten only after every CTA has arrived
-      // at the next step's barrier, which this CTA does after these lines.
+      // records of this slot are rewritten only three steps later.
       if (!band && vrow[0] >= 0) {
         const int J0 = H * lane;
         float2 g[H];
@@ -539,7 +644,8 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
           }
         }
       }
-      cluster_wait();
+      // steps gs = 4j + 3, 4j, 4j + 1, 4j + 2 complete phase j of slots 0..3
+      mbar_wait_cluster(&sh.mbar[nxt], (uint32_t)(gs >> 2) & 1u, &sh.abort);
       ++gs;
     };
     for (int step = 0; step < Bp; step += 2) {
@@ -550,7 +656,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
   }
 
   if (rank == 0) {
-    const int so = (gs + 2) % kSlots, se = (gs + 1) % kSlots;
+    const int so = (gs + 3) % kSlots, se = (gs + 2) % kSlots;
     for (int x = tid; x < Bp; x += kThreads)
       par(one, list).diag32[x] = ovf ? 0.f : diag_after_odd<H>(&sh, so, se, x, Bp);
     if (tid == 0) {
@@ -569,6 +675,13 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
     for (int c = 0; c < W; ++c) {
       const int pos = W * lane + c;
       if (pos < Bp) par(one, list).v32[(size_t)vrow[k] * Bp + pos] = v[k][c];
+    }
+  }
+  if (status == PCA_ERR_TIMEOUT) {
+    // an abandoned wait may leave stores of other CTAs in flight: give them
+    // time to land before any CTA of the cluster leaves
+    const unsigned long long t0 = gtimer();
+    while (gtimer() - t0 < 100000ull) {
     }
   }
   cl.sync();  // no CTA leaves while others may still write its shared memory
