@@ -27,8 +27,9 @@
 //     changes holder also write it straight into the other holder's copy
 //     (distributed shared memory), so a step needs no CTA-local barrier.
 //   * Whoever rotates the diagonal block of a pair of the next step writes
-//     one 16-byte record (c, s, new a_pp, new a_qq) into every CTA of the
-//     cluster.  Records rotate through four slots by global step number.
+//     one record (c, s) + (new a_pp, new a_qq) into every CTA of the
+//     cluster, as two 8-byte halves in separate arrays (the rotations read
+//     only (c, s)).  Records rotate through four slots by global step number.
 //   * V rows live in registers: lane l of a warp holds positions
 //     [W l, W l + W) of a row.  Even-step pairs are lane-local; an odd-step
 //     pair that straddles two lanes is completed by both lanes from one
@@ -140,7 +141,8 @@ __device__ __forceinline__ void rot_block(float2 csI, float2 csJ, float& m00, fl
 
 struct Shared {
   uint64_t mbar[kSlots];  // step s+1 completes on mbar[(s + 1) % kSlots]
-  float4 rec[kSlots][kRecs];
+  float2 cs[kSlots][kRecs];  // (c, s) of the pairs of a step
+  float2 dd[kSlots][kRecs];  // the pairs' two diagonal values after the step
   float dg[kMaxB];        // diagonal at the sweep boundary
   double part_o[kMaxCl], part_d[kMaxCl];
   int part_v[kMaxCl];
@@ -155,19 +157,27 @@ struct Shared {
   double off_rel, fro;
 };
 
-// Record index of pair J: lane l of a V warp reads the records of its pairs
-// l*H .. l*H+H-1 as H conflict-free 16-byte loads (index t*32 + l).
+// Record index of pair J = H q + t: row t of a 32-wide table, column q
+// XOR t*32/H.  Lane l of a V warp reads its pairs l*H + t (t < H) as H
+// loads of 32 distinct columns; 32 consecutive pairs (a bulk warp) fall on
+// 32 distinct columns too, so both 8-byte access patterns are free of bank
+// conflicts.
 template <int H>
-__device__ __forceinline__ int rix(int J) { return (J % H) * 32 + J / H; }
-
-__device__ __forceinline__ float2 cs_of(const float4& r) { return make_float2(r.x, r.y); }
+__device__ __forceinline__ int rix(int J) {
+  const int t = J % H, q = J / H;
+  return t * 32 + (q ^ (t * (32 / H)));
+}
 
 // Plain remote stores, ordered by the cluster barrier that follows (sweep start).
 template <int H>
 __device__ __forceinline__ void push_record(cg::cluster_group& cl, Shared* sh, int ncl, int slot,
                                             int J, float4 r) {
   const int i = rix<H>(J);
-  for (int q = 0; q < ncl; ++q) cl.map_shared_rank(sh, q)->rec[slot][i] = r;
+  for (int q = 0; q < ncl; ++q) {
+    Shared* d = cl.map_shared_rank(sh, q);
+    d->cs[slot][i] = make_float2(r.x, r.y);
+    d->dd[slot][i] = make_float2(r.z, r.w);
+  }
 }
 
 // Shared-memory address a (this CTA's window) in the window of CTA `rank`.
@@ -178,12 +188,6 @@ __device__ __forceinline__ uint32_t mapa(uint32_t a, int rank) {
 }
 // Stores into a CTA of the cluster that complete-tx their bytes on that
 // CTA's mbarrier `bar` (both addresses in the receiver's window).
-__device__ __forceinline__ void st_async(uint32_t a, float4 v, uint32_t bar) {
-  asm volatile(
-      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(a),
-      "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
-      : "memory");
-}
 __device__ __forceinline__ void st_async(uint32_t a, float x, float y, uint32_t bar) {
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(a),
                "f"(x), "f"(y), "r"(bar)
@@ -197,8 +201,20 @@ __device__ __forceinline__ void st_async(uint32_t a, float x, uint32_t bar) {
 // A record of the next step into every CTA (slot and mbarrier of that step).
 template <int H>
 __device__ __forceinline__ void push_record_async(Shared* sh, int ncl, int slot, int J, float4 r) {
-  const uint32_t a = su32(&sh->rec[slot][rix<H>(J)]), bar = su32(&sh->mbar[slot]);
-  for (int q = 0; q < ncl; ++q) st_async(mapa(a, q), r, mapa(bar, q));
+  const int i = rix<H>(J);
+  const uint32_t a = su32(&sh->cs[slot][i]), b = su32(&sh->dd[slot][i]), bar = su32(&sh->mbar[slot]);
+  for (int q = 0; q < ncl; ++q) {
+    const uint32_t bq = mapa(bar, q);
+    st_async(mapa(a, q), r.x, r.y, bq);
+    st_async(mapa(b, q), r.z, r.w, bq);
+  }
+}
+// The whole record of pair J in a slot: (c, s, new a_pp, new a_qq).
+template <int H>
+__device__ __forceinline__ float4 rec4(const Shared* sh, int slot, int J) {
+  const int i = rix<H>(J);
+  const float2 a = sh->cs[slot][i], b = sh->dd[slot][i];
+  return make_float4(a.x, a.y, b.x, b.y);
 }
 // Phase wait with cluster-scope acquire (the st.async data of other CTAs).
 __device__ __forceinline__ bool mbar_try_cluster(uint64_t* b, uint32_t parity) {
@@ -231,9 +247,9 @@ __device__ __forceinline__ void mbar_wait_cluster(uint64_t* b, uint32_t parity, 
 template <int H>
 __device__ __forceinline__ float diag_after_odd(const Shared* sh, int so, int se, int x, int Bp) {
   const int P = Bp / 2;
-  if (x == 0) return sh->rec[se][rix<H>(0)].z;
-  if (x == Bp - 1) return sh->rec[se][rix<H>(P - 1)].w;
-  return (x & 1) ? sh->rec[so][rix<H>((x - 1) >> 1)].z : sh->rec[so][rix<H>((x - 2) >> 1)].w;
+  if (x == 0) return sh->dd[se][rix<H>(0)].x;
+  if (x == Bp - 1) return sh->dd[se][rix<H>(P - 1)].y;
+  return (x & 1) ? sh->dd[so][rix<H>((x - 1) >> 1)].x : sh->dd[so][rix<H>((x - 2) >> 1)].y;
 }
 
 // The parameters of this CTA's matrix, read in place (parameter space or global
@@ -299,8 +315,9 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
   }
   auto d0 = [&](int i) { return i < B ? (float)C[(size_t)i * B + i] : 0.f; };
   for (int J = tid; J < P; J += kThreads) {
-    sh.rec[2][rix<H>(J)] = make_float4(1.f, 0.f, d0(2 * J), d0(2 * J + 1));
-    sh.rec[3][rix<H>(J)] = make_float4(1.f, 0.f, d0(2 * J + 1), J + 1 < P ? d0(2 * J + 2) : 0.f);
+    sh.cs[2][rix<H>(J)] = sh.cs[3][rix<H>(J)] = make_float2(1.f, 0.f);
+    sh.dd[2][rix<H>(J)] = make_float2(d0(2 * J), d0(2 * J + 1));
+    sh.dd[3][rix<H>(J)] = make_float2(d0(2 * J + 1), J + 1 < P ? d0(2 * J + 2) : 0.f);
   }
   if (tid == 0) {
     sh.ovf = 0;
@@ -475,7 +492,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
         st_async(sh.halo_a + 4u * col, x, y, mapa(bar_nxt, rank - 1));
       };
       auto to_next = [&](int col, float x) { st_async(sh.first_a + 4u * col, x, mapa(bar_nxt, rank + 1)); };
-      const float4* rc = sh.rec[cur];
+      const float2* rc = sh.cs[cur];
       if (band) {
         // super-diagonal blocks (I, I+1) of this CTA's row pairs
         const int I = I_lo + tid;
@@ -492,8 +509,8 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
           } else {
             m00 = r0[0]; m01 = r0[1]; m10 = r1[0]; m11 = r1[1];
           }
-          const float4 gI = rc[rix<H>(I)], gJ = rc[rix<H>(I + 1)];
-          rot_block(cs_of(gI), cs_of(gJ), m00, m01, m10, m11);
+          const float4 gI = rec4<H>(&sh, cur, I), gJ = rec4<H>(&sh, cur, I + 1);
+          rot_block(make_float2(gI.x, gI.y), make_float2(gJ.x, gJ.y), m00, m01, m10, m11);
           if (!last) {  // (q_I, p_{I+1}) is the off-diagonal of a next-step pair
             push_record_async<H>(&sh, ncl, nxt, e == 0 ? I : I + 1, pair_record(gI.w, gJ.z, m10));
             m10 = 0.f;
@@ -515,27 +532,27 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
           // pair, each on a thread of its own: (0, 1) -> pair 0 (CTA 0) and
           // (B'-2, B'-1) -> pair P-1 (the CTA that holds odd pair P-2)
           if (tid == kBandWarps * 32 - 1 && rank == 0 && P >= 2) {
-            const float4 g = rc[rix<H>(0)];
+            const float4 g = rec4<H>(&sh, cur, 0);
             float* a = rows + 1;                     // (0, 1), (0, 2)
             const float x = a[0], y = a[1];
             float n0 = fmaf(x, g.y, y * g.x);
             const float n1 = fmaf(x, g.x, -y * g.y);
             if (!last) {
-              push_record_async<H>(&sh, ncl, nxt, 0, pair_record(sh.rec[prv][rix<H>(0)].z, g.z, n0));
+              push_record_async<H>(&sh, ncl, nxt, 0, pair_record(sh.dd[prv][rix<H>(0)].x, g.z, n0));
               n0 = 0.f;
             }
             a[0] = n0;
             a[1] = n1;
           }
           if (tid == kBandWarps * 32 - 2 && P >= 2 && I_lo <= P - 2 && P - 2 < I_hi) {
-            const float4 g = rc[rix<H>(P - 2)];
+            const float4 g = rec4<H>(&sh, cur, P - 2);
             float* a = rows + (Bp - 3 - R0) * Bp + (Bp - 1);  // (B'-3, L), (B'-2, L)
             const float x = a[0], y = a[Bp];
             const float n0 = fmaf(g.y, x, g.x * y);
             float n1 = fmaf(g.x, x, -g.y * y);
             if (!last) {
               push_record_async<H>(&sh, ncl, nxt, P - 1,
-                                   pair_record(g.w, sh.rec[prv][rix<H>(P - 1)].w, n1));
+                                   pair_record(g.w, sh.dd[prv][rix<H>(P - 1)].y, n1));
               n1 = 0.f;
             }
             a[0] = n0;
@@ -549,7 +566,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
           const uint32_t w = lst[e][t];
           if (w == kNone) continue;
           const int I = (int)(w >> 24), J = (int)((w >> 16) & 0xff);
-          const float2 csI = cs_of(rc[rix<H>(I)]), csJ = cs_of(rc[rix<H>(J)]);
+          const float2 csI = rc[rix<H>(I)], csJ = rc[rix<H>(J)];
           float* r0 = rows + (w & 0xffff);
           float* r1 = r0 + Bp;
           float m00, m01, m10, m11;
@@ -576,14 +593,14 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
         if (e && xitem != kNone) {
           if (!(xitem >> 31)) {        // (0, p), (0, q) against column pair w
             const int wp = (int)(xitem & 0xffff);
-            const float2 g = cs_of(rc[rix<H>(wp)]);
+            const float2 g = rc[rix<H>(wp)];
             float* a = rows + 2 * wp + 1;
             const float x = a[0], y = a[1];
             a[0] = fmaf(x, g.y, y * g.x);
             a[1] = fmaf(x, g.x, -y * g.y);
           } else {                     // (p, L), (q, L) against row pair I
             const int I = (int)(xitem & 0xffff);
-            const float2 g = cs_of(rc[rix<H>(I)]);
+            const float2 g = rc[rix<H>(I)];
             float* a = rows + (2 * I + 1 - R0) * Bp + (Bp - 1);
             const float x = a[0], y = a[Bp];
             const float n1 = fmaf(g.x, x, -g.y * y);
@@ -608,7 +625,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
         const int J0 = H * lane;
         float2 g[H];
 #pragma unroll
-        for (int t = 0; t < H; ++t) g[t] = cs_of(rc[t * 32 + lane]);
+        for (int t = 0; t < H; ++t) g[t] = rc[rix<H>(H * lane + t)];
         if (e == 0) {
 #pragma unroll
           for (int k = 0; k < VR; ++k) {
@@ -624,7 +641,7 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
           }
         } else {
           // pair J0-1 straddles this lane and the previous one
-          const float2 gp = lane > 0 ? cs_of(rc[(H - 1) * 32 + lane - 1]) : make_float2(1.f, 0.f);
+          const float2 gp = lane > 0 ? rc[rix<H>(H * lane - 1)] : make_float2(1.f, 0.f);
 #pragma unroll
           for (int k = 0; k < VR; ++k) {
             if (vrow[k] < 0) continue;        // uniform over the warp
