@@ -10,7 +10,10 @@
 // Three stages:
 //   k_bwd_dv     one streaming pass over cube and dQ (TMA bulk copies of
 //                64-pixel chunks): per-CTA partial sums of X^T dQ and of the
-//                columns of dQ (FP32), thread = band;
+//                columns of dQ (FP32), thread = band in each of two groups
+//                that take alternate pixels (two warps per band slice keep
+//                the shared-memory loads of one in flight while the other
+//                computes), their sums added at the end;
 //                the same pass records the largest |x_b| and |dq_j| (the
 //                operand scales of the dY product);
 //   k_bwd_reduce / k_bwd_m / k_bwd_s / k_bwd_sym   the B x B algebra in
@@ -25,9 +28,10 @@ namespace {
 
 // ------------------------------------------------------------------ k_bwd_dv
 constexpr int kDvPx = 64;                 // pixels per chunk
-constexpr int kDvWarps = 8;               // thread = band (B <= 256)
+constexpr int kDvGroups = 2;              // pixel groups (alternate pixels)
+constexpr int kDvWarps = 8 * kDvGroups;   // thread = band within a group (B <= 256)
 constexpr int kDvThreads = kDvWarps * 32 + 32;
-constexpr int kDvStages = 3;
+constexpr int kDvStages = 3;              // most stages; fewer when shared memory is short
 
 __device__ __forceinline__ void dv_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kDvWarps * 32) : "memory");
@@ -44,10 +48,13 @@ __device__ __forceinline__ int dv_and(int v) {
   return r;
 }
 
-struct __align__(8) DvSync {
+struct __align__(16) DvSync {
   uint64_t full[kDvStages];
   uint64_t empty[kDvStages];
   int abort;
+  int pad[3];
+  float4 comb[256];          // the second group's sums, one column quad at a time
+  float combv[3][256];       // its xmax (by band), column sums and |dq| maxima
 };
 
 template <typename In, int KQ>
@@ -55,11 +62,11 @@ __global__ void __launch_bounds__(kDvThreads, 1)
 k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, int B, int k,
          const double* __restrict__ mu, float* __restrict__ dv_part, float* __restrict__ dqs_part,
          float* __restrict__ xmax_part, float* __restrict__ dqmax_part, int cube_stage,
-         int dq_stage, DevHeader* __restrict__ hdr) {
+         int dq_stage, int nst, DevHeader* __restrict__ hdr) {
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* cst = smem;                                        // [S][cube_stage]
-  float* dqst = reinterpret_cast<float*>(smem + kDvStages * cube_stage);  // [S][dq_stage/4]
-  float* mus = dqst + kDvStages * dq_stage / 4;                     // [256]
+  unsigned char* cst = smem;                                        // [nst][cube_stage]
+  float* dqst = reinterpret_cast<float*>(smem + nst * cube_stage);  // [nst][dq_stage/4]
+  float* mus = dqst + nst * dq_stage / 4;                           // [256]
   float4* dqpad = reinterpret_cast<float4*>(mus + 256);              // [2][kDvPx][KQ]
   DvSync* sy = reinterpret_cast<DvSync*>(dqpad + 2 * kDvPx * KQ);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -69,7 +76,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
   const int nch = (int)(c_end - c_begin);
   for (int b = tid; b < 256; b += kDvThreads) mus[b] = b < B ? (float)mu[b] : 0.f;
   if (tid == 0) {
-    for (int s = 0; s < kDvStages; ++s) { mbar_init(&sy->full[s], 1); mbar_init(&sy->empty[s], kDvWarps); }
+    for (int s = 0; s < nst; ++s) { mbar_init(&sy->full[s], 1); mbar_init(&sy->empty[s], kDvWarps); }
     sy->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -77,8 +84,8 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
   if (warp == kDvWarps) {
     if (lane == 0) {
       for (int c = 0; c < nch; ++c) {
-        const int s = c % kDvStages;
-        if (!mbar_wait(&sy->empty[s], ((c / kDvStages) & 1) ^ 1, &sy->abort)) break;
+        const int s = c % nst;
+        if (!mbar_wait(&sy->empty[s], ((c / nst) & 1) ^ 1, &sy->abort)) break;
         const int64_t p0 = (c_begin + c) * kDvPx;
         const int cp = (int)((N - p0) < kDvPx ? (N - p0) : kDvPx);
         const uint32_t cb = (uint32_t)((size_t)cp * B * sizeof(In)) & ~15u;
@@ -91,7 +98,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
     }
     return;
   }
-  const int b = tid;                    // this thread's band
+  const int grp = tid / 256, b = tid % 256;  // pixel group, this thread's band
   float4 acc[KQ];
 #pragma unroll
   for (int q = 0; q < KQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -100,9 +107,9 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
   const float m = b < B ? mus[b] : 0.f;
   int c = 0;
   for (; c < nch; ++c) {
-    const int s = c % kDvStages;
+    const int s = c % nst;
     int ok = 1;
-    if (lane == 0) ok = mbar_wait(&sy->full[s], (c / kDvStages) & 1, &sy->abort) ? 1 : 0;
+    if (lane == 0) ok = mbar_wait(&sy->full[s], (c / nst) & 1, &sy->abort) ? 1 : 0;
     ok = __shfl_sync(kFull, ok, 0);
     if (!dv_and(ok)) break;
     const int64_t p0 = (c_begin + c) * kDvPx;
@@ -121,7 +128,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
       reinterpret_cast<float*>(dqp)[e] = j < k ? (ed < copied_d ? ds[ed] : dq[p0 * k + ed]) : 0.f;
     }
     dv_sync();
-    for (int p = 0; p < cp; ++p) {
+    for (int p = grp; p < cp; p += kDvGroups) {
       float x = 0.f;
       float dv[KQ * 4];
       if (whole) {
@@ -148,8 +155,8 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
         acc[q].z = fmaf(x, dv[4 * q + 2], acc[q].z);
         acc[q].w = fmaf(x, dv[4 * q + 3], acc[q].w);
       }
-      if (tid < k) {
-        const float d = reinterpret_cast<const float*>(dqp)[p * KQ * 4 + tid];
+      if (b < k) {
+        const float d = reinterpret_cast<const float*>(dqp)[p * KQ * 4 + b];
         csum += d;
         dmax = fmaxf(dmax, fabsf(d));
       }
@@ -158,21 +165,33 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
     if (lane == 0) mbar_arrive(&sy->empty[s]);
   }
   if (c < nch && tid == 0 && hdr) set_status(hdr, PCA_ERR_TIMEOUT);
-  if (b < B) {
-    float* out = dv_part + ((size_t)g * B + b) * k;
+  // the second group hands its sums to the first through shared memory
+  if (grp == 1) {
+    sy->combv[0][b] = xmax;
+    sy->combv[1][b] = csum;
+    sy->combv[2][b] = dmax;
+  }
+  float* out = dv_part + ((size_t)g * B + b) * k;
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-      const float v[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
+  for (int q = 0; q < KQ; ++q) {
+    if (grp == 1) sy->comb[b] = acc[q];
+    dv_sync();
+    if (grp == 0 && b < B) {
+      const float4 o = sy->comb[b];
+      const float v[4] = {acc[q].x + o.x, acc[q].y + o.y, acc[q].z + o.z, acc[q].w + o.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         if (4 * q + t < k) out[4 * q + t] = v[t];
     }
+    dv_sync();
   }
-  if (tid < k) {
-    dqs_part[(size_t)g * k + tid] = csum;
-    dqmax_part[(size_t)g * k + tid] = dmax;
+  if (grp == 0) {
+    if (b < k) {
+      dqs_part[(size_t)g * k + b] = csum + sy->combv[1][b];
+      dqmax_part[(size_t)g * k + b] = fmaxf(dmax, sy->combv[2][b]);
+    }
+    if (b < B) xmax_part[(size_t)g * B + b] = fmaxf(xmax, sy->combv[0][b]);
   }
-  if (b < B) xmax_part[(size_t)g * B + b] = xmax;
 }
 
 // ------------------------------------------------------------------ k_bwd_reduce
@@ -289,13 +308,18 @@ cudaError_t dv_kq(const In* cube, const float* dq, int64_t N, int B, int k, cons
                   DevHeader* hdr, cudaStream_t st) {
   const int cube_stage = (int)((((size_t)kDvPx * B * sizeof(In)) + 127) & ~(size_t)127);
   const int dq_stage = (int)((((size_t)kDvPx * k * 4) + 127) & ~(size_t)127);
-  const size_t smem = (size_t)kDvStages * (cube_stage + dq_stage) + 256 * 4 +
-                      (size_t)2 * kDvPx * KQ * 16 + sizeof(DvSync);
+  // three stages where they fit in the 227 KB a CTA may use (all but the
+  // largest FP32 shapes), else two
+  auto bytes = [&](int n) {
+    return (size_t)n * (cube_stage + dq_stage) + 256 * 4 + (size_t)2 * kDvPx * KQ * 16 + sizeof(DvSync);
+  };
+  const int nst = bytes(kDvStages) <= (size_t)227 * 1024 ? kDvStages : 2;
+  const size_t smem = bytes(nst);
   auto kern = k_bwd_dv<In, KQ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<parts, kDvThreads, smem, st>>>(cube, dq, N, B, k, mu, dv_part, dqs_part, xmax_part,
-                                        dqmax_part, cube_stage, dq_stage, hdr);
+                                        dqmax_part, cube_stage, dq_stage, nst, hdr);
   return cudaGetLastError();
 }
 

@@ -36,7 +36,10 @@ def _check(gbpca, Y, k, dQ, dlam=None, dtype=torch.float32, gap_eps=1e-9):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("side,bands,k", [(16, 24, 5), (21, 33, 6), (20, 48, 10), (13, 7, 3)])
+# (9, 256, 32): the largest B and k of the ABI (two pipeline stages in the
+# X^T dQ pass, the widest tensor-core dY product)
+@pytest.mark.parametrize("side,bands,k", [(16, 24, 5), (21, 33, 6), (20, 48, 10), (13, 7, 3),
+                                          (9, 256, 32)])
 def test_backward_matches_oracle(gbpca_lib, side, bands, k):
     Y, k, dQ = _case(side * 3 + bands, side, bands, k)
     err = _check(gbpca_lib, Y, k, dQ)
