@@ -635,17 +635,24 @@ def main(argv=None):
 
         Yin = [torch.empty(y.shape, dtype=y.dtype, device=dev) for y in Yh]
 
+        # the cube with the longest fit (most bands: Jacobi steps grow with B)
+        # is copied in first, with the link to itself; the next cube's copy
+        # starts when it is done and overlaps the first cube's kernels
+        order = sorted(range(len(cubes)), key=lambda i: -cubes[i].B)
+
         def e2e_step():
-            # each cube on its own stream: copy in, fit, copy the results out, so
-            # one cube's copies overlap the other cube's kernels
+            # each cube on its own stream: copy in, fit, copy the results out
             main = torch.cuda.current_stream(dev)
-            fork = torch.cuda.Event()
-            fork.record(main)
+            prev = torch.cuda.Event()
+            prev.record(main)
             joins = []
-            for c, yh, yd, w, o, h, st in zip(cubes, Yh, Yin, ws, outs, host_out, side):
-                st.wait_event(fork)
+            for i in order:
+                c, yh, yd, w, o, h, st = cubes[i], Yh[i], Yin[i], ws[i], outs[i], host_out[i], side[i]
+                st.wait_event(prev)
                 with torch.cuda.stream(st):
                     yd.copy_(yh, non_blocking=True)
+                    prev = torch.cuda.Event()
+                    prev.record(st)
                     g.fit(yd, c.k, tol=c.tol, sweeps_max=c.sweeps_max, precision=args.precision,
                           out=o, workspace=w, sync=False, stream=st)
                     for t, th in zip(o, h):
