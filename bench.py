@@ -483,8 +483,13 @@ def main(argv=None):
                  torch.empty(c.N, c.k, dtype=torch.float32, device=dev)) for c in cubes]
         return ws, outs
 
-    # the cubes are independent problems: each gets its own stream, joined per step
-    side = [torch.cuda.Stream(device=dev) for _ in cubes]
+    # the cubes are independent problems: each gets its own stream, joined per
+    # step; the cube with the longest fit (most bands: the Jacobi steps grow
+    # with B) gets the higher priority, so that its launches take the SMs first
+    # when both cubes' kernels are pending
+    longest = max(range(len(cubes)), key=lambda i: cubes[i].B)
+    side = [torch.cuda.Stream(device=dev, priority=-1 if i == longest else 0)
+            for i in range(len(cubes))]
 
     def step(prec, ws, outs, Ys=None):
         Ys = Yd if Ys is None else Ys
