@@ -55,9 +55,13 @@ __host__ __device__ inline int64_t packed_index(int i, int j, int B) {  // i <= 
 }
 
 // ---------------------------------------------------------------- precision policy
-// FP64 refinement iterations after the FP32 sweeps.
+// FP64 refinement iterations after the FP32 sweeps.  P64 runs five: pairs just
+// outside a cluster (first-order angles a little below the cluster bound)
+// converge slowly, and on a spectrum with a large cluster (the 16-bit rounding
+// floor of a 2048 x 2048 x 224 BF16 cube) three iterations left eigenvector
+// residuals of 1e-10 ||C||, five leave 3e-12.
 inline int refine_iterations(pca_precision prec) {
-  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 3);
+  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 1 : 5);
 }
 // Lowest stop threshold of the FP32 sweeps.  MIX hands the eigen-pairs to its
 // quadratically convergent refinement once off(A) <= 1e-5 ||A||_F: on the
@@ -70,9 +74,10 @@ inline float stop_floor(pca_precision prec) {
 }
 // Largest first-order angle the refinement applies (pairs above it count as clustered).
 inline double refine_max_angle(pca_precision prec) { (void)prec; return 1.0 / 64; }
-// Closing Newton-Schulz orthogonalisation steps.
+// Closing Newton-Schulz orthogonalisation steps (P64: one more, for the
+// non-orthogonality a large last update leaves, ~1e-3 in the case above).
 inline int ortho_steps(pca_precision prec) {
-  return prec == PCA_PREC_P32 ? 0 : 2;
+  return prec == PCA_PREC_P32 ? 0 : (prec == PCA_PREC_MIX ? 2 : 3);
 }
 // MIX stops its FP32 sweeps on the Frobenius test (the refinement resolves what
 // the element-wise test would still demand); P32 and P64 use the element-wise test.
