@@ -58,10 +58,12 @@ typedef enum { PCA_F32 = 0, PCA_BF16 = 1, PCA_F16 = 2 } pca_dtype;
 /*
  * Precision forms.
  *   PCA_PREC_P64: covariance accumulated in FP64 from exact products;
- *     FP32 Jacobi followed by three FP64 refinement iterations (eigen-pairs
- *     separated from the rest of the spectrum by more than about 1e-6 of
- *     ||C|| come out FP64-accurate; tighter clusters keep FP32-level
- *     accuracy of the cluster, at least 1e-7 ||C|| absolute).
+ *     FP32 Jacobi followed by five FP64 refinement iterations and three
+ *     orthogonalisation steps (eigen-pairs separated from the rest of the
+ *     spectrum by more than about 1e-5 of ||C|| come out FP64-accurate --
+ *     eigenvalues below about 1e-3 ||C|| to about 1e-13 ||C|| absolute, the
+ *     precision of the double-float products; tighter clusters keep
+ *     FP32-level accuracy within the cluster, at least 1e-7 ||C|| absolute).
  *   PCA_PREC_P32: plain FP32 on the GPU (SIMT covariance, FP32 Jacobi, no
  *     refinement).
  *   PCA_PREC_MIX: covariance on the tensor cores from a two-term FP16
@@ -139,7 +141,7 @@ int pca_fit(const void *cube, pca_dtype dtype, int64_t N, int B, int k, double t
  *   tensor cores on per-band shifted and power-of-two scaled values).
  * pca_eigh -- Algorithm 1 stage 4 on a given symmetric matrix A [B][B] FP64
  *   (device): cyclic Jacobi (Eqs. 2-10), FP64 refinement (P32: none; MIX: one
- *   iteration and two orthogonalisation steps; P64: three and two),
+ *   iteration and two orthogonalisation steps; P64: five and three),
  *   descending sort and sign rule; eigvals [B],
  *   eigvecs [B][B] as in pca_fit.  The workspace is that of pca_fit with
  *   N = 2 (any N works).
