@@ -175,3 +175,35 @@ def test_batch_nonfinite_tile_is_reported_alone(gbpca_lib):
             ref = oracle.pca_fit(cubes[t].Y, cubes[t].k, tol=1e-14)
             mu, ev, V, Q = results[t]
             compare((_host(mu), _host(ev), _host(V), _host(Q)), ref, cubes[t].k, form)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", ["mix", "p32"])
+def test_batch_full_size_workload(gbpca_lib, form):
+    """The batched workload at full size: 256 tiles (N log-uniform in [4096,
+    262144], B from the seven band counts, 3-15 endmembers, k = 8, tol 1e-8;
+    15.25 M pixels, 9.9 GB FP32 drawn on the GPU).  Every tile: status, descending
+    eigenvalues, orthonormal eigenvectors; four tiles (smallest and largest N, the
+    median, the largest B) against the oracle in full."""
+    g = gbpca_lib
+    specs = synth.tile_batch_specs(seed=3)
+    cubes = [synth.tile_device(s, "cuda") for s in specs]
+    assert len(cubes) == 256
+    results, status, infos = g.fit_batched([c.Y for c in cubes], 8, tol=1e-8, precision=form)
+    torch.cuda.synchronize()
+    assert status == 0 and all(i["status"] == 0 for i in infos)
+    orth_tol = {"mix": 1e-6, "p32": 1e-4}[form]
+    for (mu, ev, V, Q) in results:
+        lam = ev.cpu().numpy()
+        assert np.all(np.diff(lam) <= 0)
+        Vh = V.cpu().numpy()
+        assert np.abs(Vh.T @ Vh - np.eye(Vh.shape[0])).max() <= orth_tol
+    order = np.argsort([c.N for c in cubes])
+    sample = {int(order[0]), int(order[len(order) // 2]), int(order[-1]),
+              int(np.argmax([c.B for c in cubes]))}
+    oracle.set_threads(0)
+    for t in sorted(sample):
+        c = cubes[t]
+        ref = oracle.pca_fit(c.Y.cpu().numpy(), 8, tol=1e-14)
+        mu, ev, V, Q = results[t]
+        compare((_host(mu), _host(ev), _host(V), _host(Q)), ref, 8, form)

@@ -132,3 +132,21 @@ def test_paper_scenes_full_size(gbpca_lib, form):
         out, info = run(gbpca_lib, cube.Y, cube.k, form)
         assert info["status"] == 0, info
         compare(out, ref, cube.k, form)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", FORMS)
+def test_plain_pca_config_exact(gbpca_lib, form):
+    """Plain PCA exactly as specified: 100 x 100 pixels x 128 bands, 5 endmembers
+    (U[0,1] spectra, Dirichlet(1) abundances, 0.01 Gaussian noise), seed 0, k = 5,
+    tol 1e-10, 30 sweeps; whole outputs against the oracle."""
+    cube = synth.linear_mixing()
+    assert (cube.N, cube.B, cube.k) == (10000, 128, 5)
+    ref = oracle.pca_fit(cube.Y, cube.k, tol=1e-14)
+    out, info = run(gbpca_lib, cube.Y, cube.k, form, tol=cube.tol, sweeps_max=cube.sweeps_max)
+    assert info["status"] == 0, info
+    # P64 at FP64 accuracy for the signal components (endmembers - 1 of them);
+    # the noise eigenvalues beyond form a cluster (include/gbpca.h)
+    kc = min(cube.k, 4) if form == "p64" else cube.k
+    mu, lam, V, Q = out
+    compare((mu, lam, V, Q[:, :kc]), ref, kc, form)
