@@ -96,38 +96,49 @@ def aggregate(units_per_rank_step: float, steps: int, max_seconds: float, world:
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons, sampled every interval_ms from one
+    process started before the first timed region; `with sampler:` marks a timed
+    region, and only samples whose timestamps fall inside a region are kept."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.idx = gpu_index
-        self.proc = None
-        self.path = None
-
-    def __enter__(self):
+    def __init__(self, gpu_index: int, interval_ms: int = 20):
+        self.regions = []
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
-        return self
+        import atexit
+        atexit.register(self._stop)          # never leave the sampler running
+        time.sleep(0.5)                      # let the first samples arrive
 
-    def __exit__(self, *exc):
+    def _stop(self):
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+            self.proc = None
+
+    def __enter__(self):
+        self.regions.append([time.time(), None])
+        return self
+
+    def __exit__(self, *exc):
+        self.regions[-1][1] = time.time()
         return False
 
     def summary(self):
-        if not self.path or not os.path.exists(self.path):
+        import datetime
+        self._stop()
+        if not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi"]}
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -136,10 +147,14 @@ class ClockSampler:
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                t = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                clk, mx = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
+            if not any(r0 <= t <= r1 for r0, r1 in self.regions if r1 is not None):
+                continue
+            sm.append(clk)
+            smax.append(mx)
             for n, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
@@ -147,7 +162,8 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "regions": len(self.regions)}
 
 
 # ------------------------------------------------------------------ helpers
@@ -546,7 +562,7 @@ def main(argv=None):
     t_mix, stages, infos_mix, res_mix = timed(args.precision, args.steps, args.warmup, True, sampler)
     t_mix = max_over_ranks(t_mix, world)
     value = aggregate(units, args.steps, t_mix, world)
-    t_p32, _, infos_p32, res_p32 = timed("p32", args.steps, args.warmup)
+    t_p32, _, infos_p32, res_p32 = timed("p32", args.steps, args.warmup, False, sampler)
     t_p32 = max_over_ranks(t_p32, world)
     value_p32 = aggregate(units, args.steps, t_p32, world)
 
@@ -557,7 +573,6 @@ def main(argv=None):
                 for s in g.STAGES}
     dom = max(stage_ms, key=stage_ms.get)
     roof = None
-    clocks = sampler.summary()
     if dom == "jacobi":
         # one launch per cube; report the larger-B cube's launch (the dominant one)
         j = int(np.argmax([c.B for c in cubes]))
@@ -701,13 +716,14 @@ def main(argv=None):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         total = 0.0
-        for _ in range(args.steps):
-            flush.fill_(1)
-            e0.record()
-            e2e_step()
-            e1.record()
-            e1.synchronize()
-            total += e0.elapsed_time(e1) / 1e3
+        with sampler:
+            for _ in range(args.steps):
+                flush.fill_(1)
+                e0.record()
+                e2e_step()
+                e1.record()
+                e1.synchronize()
+                total += e0.elapsed_time(e1) / 1e3
         total = max_over_ranks(total, world)
         e2e = {"value": aggregate(units, args.steps, total, world), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -801,7 +817,7 @@ def main(argv=None):
                       "p32": {"value": value_p32, "ms_per_step": t_p32 / args.steps * 1e3,
                               "sweeps": [i["sweeps"] for i in infos_p32], **errors.get("p32", {})}},
             "stage_ms_per_step": stage_ms, "roofline": roof, "hbm_kernels": hbm,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
             "differentiation": diff, "batched": batched, "paper_shapes_k1": shapes,
             "bsq_input": bsq}
     if rank == 0:
