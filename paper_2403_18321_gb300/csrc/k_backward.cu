@@ -10,10 +10,11 @@
 // Three stages:
 //   k_bwd_dv     one streaming pass over cube and dQ (TMA bulk copies of
 //                64-pixel chunks): per-CTA partial sums of X^T dQ and of the
-//                columns of dQ (FP32), thread = band in each of two groups
-//                that take alternate pixels (two warps per band slice keep
-//                the shared-memory loads of one in flight while the other
-//                computes), their sums added at the end;
+//                columns of dQ (FP32), thread = band in each of three
+//                groups (two for k > 16, where the registers of 800 threads
+//                run out) that take alternate pixels, so that several warps
+//                per band slice keep shared-memory loads in flight while
+//                others compute; their sums are added at the end;
 //                the same pass records the largest |x_b| and |dq_j| (the
 //                operand scales of the dY product);
 //   k_bwd_reduce / k_bwd_m / k_bwd_s / k_bwd_sym   the B x B algebra in
@@ -28,22 +29,26 @@ namespace {
 
 // ------------------------------------------------------------------ k_bwd_dv
 constexpr int kDvPx = 64;                 // pixels per chunk
-constexpr int kDvGroups = 2;              // pixel groups (alternate pixels)
-constexpr int kDvWarps = 8 * kDvGroups;   // thread = band within a group (B <= 256)
-constexpr int kDvThreads = kDvWarps * 32 + 32;
+// pixel groups (alternate pixels; thread = band within a group, B <= 256):
+// three while the registers of 800 threads allow it (k <= 16), else two
+__host__ __device__ constexpr int dv_groups(int KQ) { return KQ <= 4 ? 3 : 2; }
+__host__ __device__ constexpr int dv_compute(int KQ) { return dv_groups(KQ) * 256; }
+__host__ __device__ constexpr int dv_threads(int KQ) { return dv_compute(KQ) + 32; }
 constexpr int kDvStages = 3;              // most stages; fewer when shared memory is short
 
+template <int NT>
 __device__ __forceinline__ void dv_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kDvWarps * 32) : "memory");
+  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
 }
 // AND of a flag over the compute warps (they leave the chunk loop together)
+template <int NT>
 __device__ __forceinline__ int dv_and(int v) {
   int r;
   asm volatile(
       "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
       " selp.s32 %0, 1, 0, q;\n}\n"
       : "=r"(r)
-      : "r"(v), "n"(kDvWarps * 32)
+      : "r"(v), "n"(NT)
       : "memory");
   return r;
 }
@@ -58,7 +63,7 @@ struct __align__(16) DvSync {
 };
 
 template <typename In, int KQ>
-__global__ void __launch_bounds__(kDvThreads, 1)
+__global__ void __launch_bounds__(dv_threads(KQ), 1)
 k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, int B, int k,
          const double* __restrict__ mu, float* __restrict__ dv_part, float* __restrict__ dqs_part,
          float* __restrict__ xmax_part, float* __restrict__ dqmax_part, int cube_stage,
@@ -74,14 +79,15 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
   const int64_t nch_total = (N + kDvPx - 1) / kDvPx;
   const int64_t c_begin = nch_total * g / G, c_end = nch_total * (g + 1) / G;
   const int nch = (int)(c_end - c_begin);
-  for (int b = tid; b < 256; b += kDvThreads) mus[b] = b < B ? (float)mu[b] : 0.f;
+  constexpr int kGroups = dv_groups(KQ), kComp = dv_compute(KQ), kWarps = kComp / 32;
+  for (int b = tid; b < 256; b += dv_threads(KQ)) mus[b] = b < B ? (float)mu[b] : 0.f;
   if (tid == 0) {
-    for (int s = 0; s < nst; ++s) { mbar_init(&sy->full[s], 1); mbar_init(&sy->empty[s], kDvWarps); }
+    for (int s = 0; s < nst; ++s) { mbar_init(&sy->full[s], 1); mbar_init(&sy->empty[s], kWarps); }
     sy->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (warp == kDvWarps) {
+  if (warp == kWarps) {
     if (lane == 0) {
       for (int c = 0; c < nch; ++c) {
         const int s = c % nst;
@@ -111,7 +117,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
     int ok = 1;
     if (lane == 0) ok = mbar_wait(&sy->full[s], (c / nst) & 1, &sy->abort) ? 1 : 0;
     ok = __shfl_sync(kFull, ok, 0);
-    if (!dv_and(ok)) break;
+    if (!dv_and<kComp>(ok)) break;
     const int64_t p0 = (c_begin + c) * kDvPx;
     const int cp = (int)((N - p0) < kDvPx ? (N - p0) : kDvPx);
     const In* xs = reinterpret_cast<const In*>(cst + (size_t)s * cube_stage);
@@ -122,13 +128,13 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
     // dQ rows of this chunk padded to 16-byte rows (two buffers by chunk
     // parity), so that every pixel's row is read as KQ vectors
     float4* dqp = dqpad + (size_t)(c & 1) * kDvPx * KQ;
-    for (int e = tid; e < cp * KQ * 4; e += kDvWarps * 32) {
+    for (int e = tid; e < cp * KQ * 4; e += kComp) {
       const int pp = e / (KQ * 4), j = e - pp * (KQ * 4);
       const int ed = pp * k + j;
       reinterpret_cast<float*>(dqp)[e] = j < k ? (ed < copied_d ? ds[ed] : dq[p0 * k + ed]) : 0.f;
     }
-    dv_sync();
-    for (int p = grp; p < cp; p += kDvGroups) {
+    dv_sync<kComp>();
+    for (int p = grp; p < cp; p += kGroups) {
       float x = 0.f;
       float dv[KQ * 4];
       if (whole) {
@@ -165,32 +171,47 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
     if (lane == 0) mbar_arrive(&sy->empty[s]);
   }
   if (c < nch && tid == 0 && hdr) set_status(hdr, PCA_ERR_TIMEOUT);
-  // the second group hands its sums to the first through shared memory
-  if (grp == 1) {
-    sy->combv[0][b] = xmax;
-    sy->combv[1][b] = csum;
-    sy->combv[2][b] = dmax;
-  }
+  // the other groups hand their sums to the first through shared memory, one
+  // group and one column quad at a time
   float* out = dv_part + ((size_t)g * B + b) * k;
 #pragma unroll
   for (int q = 0; q < KQ; ++q) {
-    if (grp == 1) sy->comb[b] = acc[q];
-    dv_sync();
+    for (int h = 1; h < kGroups; ++h) {
+      if (grp == h) sy->comb[b] = acc[q];
+      dv_sync<kComp>();
+      if (grp == 0) {
+        const float4 o = sy->comb[b];
+        acc[q].x += o.x; acc[q].y += o.y; acc[q].z += o.z; acc[q].w += o.w;
+      }
+      dv_sync<kComp>();
+    }
     if (grp == 0 && b < B) {
-      const float4 o = sy->comb[b];
-      const float v[4] = {acc[q].x + o.x, acc[q].y + o.y, acc[q].z + o.z, acc[q].w + o.w};
+      const float v[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         if (4 * q + t < k) out[4 * q + t] = v[t];
     }
-    dv_sync();
+  }
+  for (int h = 1; h < kGroups; ++h) {
+    if (grp == h) {
+      sy->combv[0][b] = xmax;
+      sy->combv[1][b] = csum;
+      sy->combv[2][b] = dmax;
+    }
+    dv_sync<kComp>();
+    if (grp == 0) {
+      xmax = fmaxf(xmax, sy->combv[0][b]);
+      csum += sy->combv[1][b];
+      dmax = fmaxf(dmax, sy->combv[2][b]);
+    }
+    dv_sync<kComp>();
   }
   if (grp == 0) {
     if (b < k) {
-      dqs_part[(size_t)g * k + b] = csum + sy->combv[1][b];
-      dqmax_part[(size_t)g * k + b] = fmaxf(dmax, sy->combv[2][b]);
+      dqs_part[(size_t)g * k + b] = csum;
+      dqmax_part[(size_t)g * k + b] = dmax;
     }
-    if (b < B) xmax_part[(size_t)g * B + b] = fmaxf(xmax, sy->combv[0][b]);
+    if (b < B) xmax_part[(size_t)g * B + b] = xmax;
   }
 }
 
@@ -318,7 +339,7 @@ cudaError_t dv_kq(const In* cube, const float* dq, int64_t N, int B, int k, cons
   auto kern = k_bwd_dv<In, KQ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<parts, kDvThreads, smem, st>>>(cube, dq, N, B, k, mu, dv_part, dqs_part, xmax_part,
+  kern<<<parts, dv_threads(KQ), smem, st>>>(cube, dq, N, B, k, mu, dv_part, dqs_part, xmax_part,
                                         dqmax_part, cube_stage, dq_stage, nst, hdr);
   return cudaGetLastError();
 }
