@@ -11,15 +11,12 @@
 //            group for each of eight consecutive pixels;
 //   untiled: otherwise, as one contiguous bulk copy (the odd row stride then
 //            spreads consecutive pixels over the banks by itself).
-// A group of eight compute warps takes a chunk: each warp one eighth of the
-// bands for the same 64 pixels (two pixels per lane), accumulating x * V_k in
-// registers with V_k and mu read as broadcasts from shared memory; the eight
-// partial sums are added through shared memory before the chunk's k columns
-// are stored.  Two groups take alternate chunks when shared memory leaves
-// room for their two reduction buffers and three stages (the chunk work is
-// latency-bound: a second group keeps a second chunk in flight), else one.
-// Every wait is bounded; a chunk whose data did not arrive gets NaN outputs,
-// and PCA_ERR_TIMEOUT is recorded when a header is given.
+// Warps 0-7 each take one eighth of the bands for the same 64 pixels (two
+// pixels per lane), accumulate x * V_k in registers with V_k and mu read as
+// broadcasts from shared memory, and the eight partial sums are added through
+// shared memory before the chunk's k columns are stored.  Every wait is
+// bounded; on time-out the CTA fills the rest of its output range with NaN
+// and records PCA_ERR_TIMEOUT when a header is given.
 #include "tma.cuh"
 
 namespace gbpca {
@@ -27,10 +24,9 @@ namespace gbpca {
 namespace {
 
 constexpr int kPc = 64;                  // pixels per chunk
-constexpr int kParts = 8;                // compute warps (band parts) of a group
-constexpr int kCompute = kParts * 32;    // threads of a group
-// two groups where a thread's registers allow 544 threads (up to 12 components)
-__host__ __device__ constexpr int max_groups(int KQ) { return KQ <= 3 ? 2 : 1; }
+constexpr int kParts = 8;                // compute warps (band parts)
+constexpr int kCompute = kParts * 32;
+constexpr int kThreadsP = kCompute + 32;
 constexpr int kMaxStages = 8;
 
 struct __align__(8) ProjSync {
@@ -39,22 +35,18 @@ struct __align__(8) ProjSync {
   int abort;
 };
 
-// barrier of one group (id 1 + group), and of all compute threads (id 3)
-__device__ __forceinline__ void group_sync(int grp) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "n"(kCompute) : "memory");
+__device__ __forceinline__ void named_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kCompute) : "memory");
 }
-__device__ __forceinline__ int group_and(int grp, int v) {
+__device__ __forceinline__ int named_and(int v) {
   int r;
   asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n"
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
       " selp.s32 %0, 1, 0, q;\n}\n"
       : "=r"(r)
-      : "r"(v), "r"(1 + grp), "n"(kCompute)
+      : "r"(v), "n"(kCompute)
       : "memory");
   return r;
-}
-__device__ __forceinline__ void compute_sync(int n) {
-  asm volatile("bar.sync 3, %0;" ::"r"(n) : "memory");
 }
 
 template <typename In>
@@ -146,8 +138,8 @@ __device__ __forceinline__ PItem proj_item(const ProjArgs& one, const CUtensorMa
 
 // maxB, maxk: the largest bands and components of the items (shared-memory
 // sizing); the single-cube form takes its cube as `one` with map `tmap`.
-template <typename In, int KQ, bool kTiled, int G>
-__global__ void __launch_bounds__(G * kCompute + 32, 1)
+template <typename In, int KQ, bool kTiled>
+__global__ void __launch_bounds__(kThreadsP, 1)
 k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ ProjArgs one,
           const TileDesc* __restrict__ T, const CUtensorMap* __restrict__ maps,
           const ProjItem* __restrict__ items, const int* __restrict__ cta_items, int maxB,
@@ -161,8 +153,8 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
   unsigned char* stages = smem;
   float4* vs = reinterpret_cast<float4*>(stages + (size_t)S * stage_bytes);  // [B8][KQ]
   float* mus = reinterpret_cast<float*>(vs + (size_t)B8m * KQ);              // [B8]
-  float* red_all = mus + B8m;                                      // [G][kParts][kPc][maxk]
-  ProjSync* sy = reinterpret_cast<ProjSync*>(red_all + (size_t)G * kParts * kPc * maxk);
+  float* red = mus + B8m;                                                    // [kParts][kPc][k]
+  ProjSync* sy = reinterpret_cast<ProjSync*>(red + (size_t)kParts * kPc * maxk);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nitems = T == nullptr ? 1 : cta_items[blockIdx.x + 1] - cta_items[blockIdx.x];
@@ -174,7 +166,7 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
   }
   __syncthreads();
 
-  if (warp == G * kParts) {
+  if (warp == kParts) {
     // ------------------------------------------------------------ producer
     // streams every item's chunks through one ring, ahead of the compute warps
     if (lane == 0) {
@@ -209,12 +201,11 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
   }
 
   // -------------------------------------------------------------- compute
-  const int grp = warp / kParts, h = warp % kParts, gt = tid - grp * kCompute;
-  const int nComp = G * kCompute;
-  float* red = red_all + (size_t)grp * kParts * kPc * maxk;
+  const int h = warp;
   const int pa = lane, pb = lane + 32;
-  int q = 0;   // chunk sequence number over all items: group grp takes q % G == grp
-  for (int i = 0; i < nitems; ++i) {
+  int q = 0;
+  bool stop = false;
+  for (int i = 0; i < nitems && !stop; ++i) {
   const PItem it = proj_item(one, &tmap, T, maps, items, cta_items, i);
   const ProjArgs& a = it.a;
   const In* cube = static_cast<const In*>(a.cube);
@@ -222,28 +213,22 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
   const int B = a.B, k = a.k;
   const int B8 = (B + 7) & ~7;
   // V_k and mu of this item's cube (the producer is already streaming)
-  if (i > 0) compute_sync(nComp);   // every warp is done with the previous item's V_k
-  for (int e = tid; e < B8 * KQ * 4; e += nComp) {
+  if (i > 0) named_sync();   // every warp is done with the previous item's V_k
+  for (int e = tid; e < B8 * KQ * 4; e += kCompute) {
     const int b = e / (KQ * 4), j = e - b * (KQ * 4);
     reinterpret_cast<float*>(vs)[e] = (b < B && j < k) ? a.vk[(size_t)b * k + j] : 0.f;
   }
-  for (int b = tid; b < B8; b += nComp) mus[b] = b < B ? a.mu_f[b] : 0.f;
-  compute_sync(nComp);
-  for (int64_t c = it.c0; c < it.c1; ++c, ++q) {
-    if (q % G != grp) continue;
+  for (int b = tid; b < B8; b += kCompute) mus[b] = b < B ? a.mu_f[b] : 0.f;
+  named_sync();
+  int64_t c = it.c0;
+  for (; c < it.c1; ++c, ++q) {
     const int s = q % S;
     int ok = 1;
     if (lane == 0) ok = mbar_wait(&sy->full[s], (q / S) & 1, &sy->abort) ? 1 : 0;
     ok = __shfl_sync(kFull, ok, 0);
+    if (!named_and(ok)) break;
     const int64_t p0 = c * kPc;
     const int cp = (int)((N - p0) < kPc ? (N - p0) : kPc);
-    if (!group_and(grp, ok)) {
-      // a bounded wait gave up: this chunk's outputs are made visibly invalid
-      // (the waits of the remaining chunks return at once)
-      for (int o = gt; o < cp * k; o += kCompute) a.proj[p0 * k + o] = __int_as_float(0x7fc00000);
-      if (gt == 0 && a.hdr) set_status(a.hdr, PCA_ERR_TIMEOUT);
-      continue;
-    }
     const unsigned char* st = stages + (size_t)s * stage_bytes;
     float4 a0[KQ], a1[KQ];
 #pragma unroll
@@ -334,15 +319,27 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
         if (j < k) { rp[pa * k + j] = v0[t]; rp[pb * k + j] = v1[t]; }
       }
     }
-    group_sync(grp);
+    named_sync();
     float* out = a.proj + p0 * k;
-    for (int o = gt; o < cp * k; o += kCompute) {
+    for (int o = tid; o < cp * k; o += kCompute) {
       float sum = 0.f;
 #pragma unroll
       for (int hh = 0; hh < kParts; ++hh) sum += red[(size_t)hh * kPc * k + o];
       out[o] = sum;
     }
-    group_sync(grp);
+    named_sync();
+  }
+  if (c < it.c1) {
+    // a bounded wait gave up: make the rest of this CTA's work visibly invalid
+    stop = true;
+    for (int j = i; j < nitems; ++j) {
+      const PItem rest = proj_item(one, &tmap, T, maps, items, cta_items, j);
+      const int64_t c0 = j == i ? c : rest.c0;
+      const int64_t o0 = c0 * kPc * rest.a.k;
+      const int64_t o1 = (rest.c1 * kPc < rest.a.N ? rest.c1 * kPc : rest.a.N) * rest.a.k;
+      for (int64_t o = o0 + tid; o < o1; o += kCompute) rest.a.proj[o] = __int_as_float(0x7fc00000);
+      if (tid == 0 && rest.a.hdr) set_status(rest.a.hdr, PCA_ERR_TIMEOUT);
+    }
   }
   }
 }
@@ -397,27 +394,18 @@ cudaError_t project_launch(bool tiled, const CUtensorMap& tmap, const ProjArgs& 
   const int nbox = (maxB * (int)sizeof(In) + 127) / 128;
   const int stage_bytes = tiled ? nbox * kPc * 128
                                 : (int)((((size_t)kPc * maxB * sizeof(In)) + 1023) & ~(size_t)1023);
+  const size_t fixed = (size_t)B8 * KQ * 16 + (size_t)B8 * 4 + (size_t)kParts * kPc * maxk * 4 +
+                       sizeof(ProjSync) + 1024;
   const size_t budget = 227 * 1024;
-  // two groups (two reduction buffers) while three stages still fit, else one
-  auto fixed = [&](int G) {
-    return (size_t)B8 * KQ * 16 + (size_t)B8 * 4 + (size_t)G * kParts * kPc * maxk * 4 +
-           sizeof(ProjSync) + 1024;
-  };
-  auto stages_for = [&](int G) {
-    const int n = fixed(G) < budget ? (int)((budget - fixed(G)) / stage_bytes) : 0;
-    return n > kMaxStages ? kMaxStages : n;
-  };
-  const int G = max_groups(KQ) > 1 && stages_for(max_groups(KQ)) >= 3 ? max_groups(KQ) : 1;
-  const int stages = stages_for(G);
+  int stages = (int)((budget - fixed) / stage_bytes);
+  stages = stages > kMaxStages ? kMaxStages : stages;
   if (stages < 2) return cudaErrorInvalidValue;
-  const size_t smem = fixed(G) + (size_t)stages * stage_bytes;
-  constexpr int G2 = max_groups(KQ);   // the instantiated group counts: 1 and G2
-  auto kern = tiled ? (G == 1 ? k_project<In, KQ, true, 1> : k_project<In, KQ, true, G2>)
-                    : (G == 1 ? k_project<In, KQ, false, 1> : k_project<In, KQ, false, G2>);
+  const size_t smem = fixed + (size_t)stages * stage_bytes;
+  auto kern = tiled ? k_project<In, KQ, true> : k_project<In, KQ, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<ctas, G * kCompute + 32, smem, st>>>(tmap, one, T, maps, items, cta_items, maxB, maxk,
-                                               stages, stage_bytes);
+  kern<<<ctas, kThreadsP, smem, st>>>(tmap, one, T, maps, items, cta_items, maxB, maxk, stages,
+                                      stage_bytes);
   return cudaGetLastError();
 }
 
