@@ -203,6 +203,10 @@ int pca_combine_moments(int parts, const int64_t *n, const double *mu_parts,
  *   - All calls share the array.  Every call rewrites what it reads before
  *     reading it, but calls whose GPU work overlaps (other streams, other
  *     host threads) race on it: serialise them.
+ *   - There is no workspace, hence no device status word: if a bounded wait
+ *     of the projection kernel gives up (PCA_ERR_TIMEOUT in the other entry
+ *     points), the rows it had not written are filled with NaN and the call
+ *     still returns PCA_OK.  NaN in proj is the only sign of it.
  */
 int pca_project_noalloc(const void *cube, pca_dtype dtype, int64_t N, int B, int k,
                         const double *mu, const double *eigvecs, float *proj, void *stream);

@@ -12,9 +12,10 @@ import torch
 
 import oracle
 import synth
-from parity import LAM_TOL, ORTH_TOL, rel_gaps, sign_norm
+from parity import E_COV, LAM_TOL, ORTH_TOL, rel_gaps, sign_norm
 
-# covariance: max_ij |C - C*| / max_ij |C*|
+# covariance: max_ij |C - C*| / max_ij |C*|; in the spectral norm relative to
+# lambda_1, E_COV (the bound every later comparison builds on)
 COV_TOL = {"p64": 1e-13, "p32": 2e-6, "mix": 2e-5}
 MU_TOL = {"p64": 1e-13, "p32": 1e-6, "mix": 1e-6}
 
@@ -38,9 +39,12 @@ def test_covariance_stage(gbpca_lib, form):
         C_ref = oracle.covariance(cube.Y, mu_ref)
         mu_err = np.abs(mu.cpu().numpy() - mu_ref).max() / np.abs(mu_ref).max()
         cov_err = np.abs(C.cpu().numpy() - C_ref).max() / np.abs(C_ref).max()
-        print(f"{cube.name} {form} mu_err={mu_err:.3e} cov_err={cov_err:.3e}")
+        cov_norm = np.linalg.norm(C.cpu().numpy() - C_ref, 2) / np.linalg.norm(C_ref, 2)
+        print(f"{cube.name} {form} mu_err={mu_err:.3e} cov_err={cov_err:.3e} "
+              f"||dC||_2/lam1={cov_norm:.3e}")
         assert mu_err <= MU_TOL[form]
         assert cov_err <= COV_TOL[form]
+        assert cov_norm <= E_COV[form], cov_norm
         assert np.array_equal(C.cpu().numpy(), C.cpu().numpy().T)
 
 

@@ -427,13 +427,26 @@ MUTANTS = {
 
 # ---------------------------------------------------------------- adjoint of the path
 
+FD_SIDE, FD_BANDS, FD_K = 32, 48, 10      # the separately generated FD sub-cube
+
+
 def _adjoint_case(seed=5):
+    """A 32 x 32 pixel x 48 band planted cube (s_i = 0.9^(i-1) over 11
+    components above a 0.05 floor) with its upstream gradients.  Central
+    differences only pin the adjoint where the eigen-pairs it differentiates
+    are simple, so the realised gaps of the top k + 1 eigenvalues are asserted
+    to be at least 1e-3 of lambda_1 (first-order perturbation theory divides
+    by them)."""
     import synth
-    c = synth.gradient_cube(seed=seed, side=16, bands=24, comps=7, k=5)
+    c = synth.gradient_cube(seed=seed, side=FD_SIDE, bands=FD_BANDS, comps=FD_K + 1, k=FD_K)
+    Y = c.Y.astype(np.float64)
+    lam = oracle.pca_fit(Y, c.k, tol=1e-14, project_q=False)["lam"]
+    gaps = (lam[:c.k + 1] - lam[1:c.k + 2]) / lam[0]
+    assert gaps.min() >= 1e-3, gaps
     rng = np.random.default_rng(seed + 100)
     dQ = rng.standard_normal((c.N, c.k))
     dl = rng.standard_normal(c.B)
-    return c.Y.astype(np.float64), c.k, dQ, dl
+    return Y, c.k, dQ, dl
 
 
 def _loss(Y, k, dQ, dl):
@@ -441,29 +454,42 @@ def _loss(Y, k, dQ, dl):
     return float(np.sum(dQ * r["Q"]) + np.dot(dl, r["lam"]))
 
 
-def test_adjoint_matches_central_differences():
+def _fd_check(entries, directions, seed=5):
     """dL/dY of L = <dQ, Q(Y)> + <dlam, lam(Y)> against central finite
-    differences (h = 1e-6, FP64) on sampled entries and random directions of a
-    planted cube whose top k+2 eigenvalues are 10% apart."""
-    Y, k, dQ, dl = _adjoint_case()
+    differences (h = 1e-6, FP64) at `entries` distinct random entries and along
+    `directions` random directions.  The forward pass's sign rule is the same
+    on both sides of every difference (no column's largest entry changes rank
+    at this step size), so the differences see one smooth branch."""
+    Y, k, dQ, dl = _adjoint_case(seed)
     r = oracle.pca_fit(Y, k, tol=1e-14)
     adj = oracle.backward(Y, k, r["mu"], r["lam"], r["V"], dQ, dl, gap_eps=1e-9)
     scale = np.abs(adj).max()
     h = 1e-6
     rng = np.random.default_rng(7)
     N, B = Y.shape
-    for _ in range(12):
-        n, b = int(rng.integers(N)), int(rng.integers(B))
+    flat = rng.choice(N * B, size=entries, replace=False)
+    worst = 0.0
+    for e in flat:
+        n, b = divmod(int(e), B)
         Yp, Ym = Y.copy(), Y.copy()
         Yp[n, b] += h
         Ym[n, b] -= h
         fd = (_loss(Yp, k, dQ, dl) - _loss(Ym, k, dQ, dl)) / (2 * h)
-        assert abs(fd - adj[n, b]) <= 2e-6 * scale, (n, b, fd, adj[n, b])
-    for _ in range(2):
+        worst = max(worst, abs(fd - adj[n, b]) / scale)
+        assert abs(fd - adj[n, b]) <= 2e-7 * scale, (n, b, fd, adj[n, b])
+    for _ in range(directions):
         D = rng.standard_normal(Y.shape)
         fd = (_loss(Y + h * D, k, dQ, dl) - _loss(Y - h * D, k, dQ, dl)) / (2 * h)
         # error bound on the scale of |<adj, D>| <= ||adj|| ||D|| (Cauchy-Schwarz)
         assert abs(fd - np.sum(adj * D)) <= 1e-6 * np.linalg.norm(adj) * np.linalg.norm(D), fd
+    return worst
+
+
+def test_adjoint_matches_central_differences():
+    """The adjoint pin at full size: 256 entries and 8 directional derivatives
+    of the 32 x 32 x 48 sub-cube."""
+    worst = _fd_check(entries=256, directions=8)
+    print(f"largest entry error / max|dY|: {worst:.2e}")
 
 
 def test_adjoint_special_cases():
@@ -509,7 +535,7 @@ def _pins_pass() -> bool:
         test_rank_one_cube()
         test_stop_rule_is_relative_to_the_norm()
         test_adjoint_special_cases()
-        test_adjoint_matches_central_differences()
+        _fd_check(entries=24, directions=2)
     except (AssertionError, oracle.OracleError):
         return False
     return True

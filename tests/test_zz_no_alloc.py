@@ -14,12 +14,13 @@ import oracle
 import synth
 
 
-def _inputs(cube):
-    ref = oracle.pca_fit(cube.Y, cube.k, tol=1e-14, project_q=False)
-    Y = torch.from_numpy(cube.Y).cuda()
+def _inputs(cube, dtype=torch.float32):
+    Yt = torch.from_numpy(cube.Y).to(dtype)         # the oracle sees the same values
+    ref = oracle.pca_fit(Yt, cube.k, tol=1e-14)
+    Y = Yt.cuda()
     mu = torch.from_numpy(ref["mu"]).cuda()
     V = torch.from_numpy(ref["V"]).cuda()
-    return Y, mu, V
+    return Y, mu, V, ref["Q"]
 
 
 @pytest.mark.gpu
@@ -28,16 +29,21 @@ def test_noalloc_projection_matches_pca_project_on_consecutive_calls(gbpca_lib):
     cubes = [synth.linear_mixing(seed=31, rows=41, cols=43, bands=96, endmembers=6, k=6),
              synth.linear_mixing(seed=32, rows=29, cols=31, bands=256, endmembers=8, k=32),
              synth.linear_mixing(seed=33, rows=17, cols=19, bands=7, endmembers=3, k=2)]
-    for cube in cubes:                       # consecutive calls share the array
-        Y, mu, V = _inputs(cube)
+    cases = [(cubes[0], torch.float32), (cubes[1], torch.float32), (cubes[2], torch.float32),
+             (cubes[0], torch.bfloat16), (cubes[1], torch.float16)]
+    for cube, dtype in cases:                # consecutive calls share the array
+        Y, mu, V, Q_oracle = _inputs(cube, dtype)
         Q_ref = g.project(Y, mu, V, cube.k)  # pca_project, with a workspace
         Q = g.project_noalloc(Y, mu, V, cube.k)
         torch.cuda.synchronize()
         a = Q.cpu().numpy().astype(np.float64)
         b = Q_ref.cpu().numpy().astype(np.float64)
         for j in range(cube.k):
+            scale = max(np.abs(Q_oracle[:, j]).max(), 1e-30)
             err = np.abs(a[:, j] - b[:, j]).max() / max(np.abs(b[:, j]).max(), 1e-30)
-            assert err <= 1e-5, (cube.name, j, err)
+            assert err <= 1e-5, (cube.name, dtype, j, err)
+            err_o = np.abs(a[:, j] - Q_oracle[:, j]).max() / scale
+            assert err_o <= 1e-5, (cube.name, dtype, j, err_o)
 
 
 @pytest.mark.gpu
