@@ -306,6 +306,49 @@ int pca_fit_batched(int ntiles, const pca_tile *tiles, pca_dtype dtype, double t
                     pca_info *infos);
 
 /*
+ * Tuning (no counterpart in the paper): process-wide parameters that trade
+ * speed against accuracy (the accumulation run of the tensor-core covariance)
+ * or shape the batched form's work split, chosen by the package's autotuner
+ * and otherwise left at measured defaults.  They are read when a workspace is
+ * sized, when pca_fit enqueues its work and when pca_batch_create plans a
+ * batch (a plan keeps what it read); change them before sizing a workspace,
+ * or a fit may find its workspace too small (PCA_ERR_WORKSPACE).  Host only.
+ *
+ * tc_slot_chunks   MIX covariance: the longest run of 32-pixel chunks that one
+ *                  tensor-memory accumulator sums in FP32 before it is written
+ *                  out and added in FP64 (1..1024, default 64).  The FP32
+ *                  accumulation error grows with the run; shorter runs write
+ *                  more partials.
+ * batch_jacobi_ctas[i]  batched form: CTAs of the Jacobi cluster of a tile
+ *                  with 32i < B' <= 32(i+1) bands (B' = B rounded up to even);
+ *                  0 = the fewest that hold the matrix (default), otherwise
+ *                  raised to the fewest that hold it, at most 8.
+ * batch_cov_tc_fixed, batch_proj_fixed  batched form: fixed cost of one
+ *                  32-pixel covariance chunk (MIX) / one 64-pixel projection
+ *                  chunk, in units of the per-band cost of a chunk; the work
+ *                  is split over the CTAs by this cost model (defaults 464 and
+ *                  223, measured).
+ * batch_cov_simt_fixed  the same for the SIMT covariance (P32, P64), in units
+ *                  of one product per pixel (default 13900).
+ * batch_simt_items_per_sm  SIMT covariance work items per SM (1..64, default 4).
+ *
+ * pca_tuning_defaults fills *t with the defaults.  pca_set_tuning installs *t
+ * (NULL: the defaults); PCA_ERR_ARG, and no change, for a value out of range.
+ * pca_get_tuning copies the current values.
+ */
+typedef struct {
+  int tc_slot_chunks;
+  int batch_jacobi_ctas[8];
+  double batch_cov_tc_fixed;
+  double batch_proj_fixed;
+  double batch_cov_simt_fixed;
+  int batch_simt_items_per_sm;
+} pca_tuning;
+void pca_tuning_defaults(pca_tuning *t);
+int pca_set_tuning(const pca_tuning *t);
+int pca_get_tuning(pca_tuning *t);
+
+/*
  * Waits for `stream` and copies the device-side outcome of the last
  * pca_fit (or pca_backward) that used `workspace` into *info.  Returns
  * info->status.
@@ -328,6 +371,20 @@ int pca_batch_kernel_launches(const pca_batch *plan);
 
 /* SMs (CTAs of one cluster) the Jacobi stage occupies for B bands; 0 if B is invalid. */
 int pca_jacobi_sms(int B);
+
+/* The shape of the plan pca_batch_create would make for these tiles under the
+ * current tuning, without a workspace or a device: counts[0] covariance work
+ * items, counts[1] projection work items, counts[2] Jacobi launches (one per
+ * cluster shape), counts[3] CTAs of the largest Jacobi cluster.  Returns
+ * PCA_ERR_ARG for invalid tiles (no pointer of a tile is read; every tile
+ * counts as projected). */
+int pca_batch_plan_counts(int ntiles, const pca_tile *tiles, pca_dtype dtype, pca_precision prec,
+                          int *counts);
+
+/* CTAs of the batched form's Jacobi cluster for a B-band tile when the tuning
+ * asks for `request` (0: the fewest that hold the matrix; else raised to the
+ * fewest that hold it, at most 8); 0 if B or request is invalid. */
+int pca_batch_jacobi_ctas(int B, int request);
 
 /*
  * Per-stage timing.  pca_profile(1) makes every later pca_fit (and

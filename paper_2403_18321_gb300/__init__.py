@@ -33,7 +33,8 @@ EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_p
            "pca_jacobi_sms", "pca_backward", "pca_backward_workspace_size",
            "pca_batch_workspace_size", "pca_batch_create", "pca_batch_run", "pca_batch_read_info",
            "pca_batch_destroy", "pca_fit_batched", "pca_batch_kernel_launches",
-           "pca_combine_moments", "pca_bsq_to_bip")
+           "pca_combine_moments", "pca_bsq_to_bip", "pca_tuning_defaults", "pca_set_tuning",
+           "pca_get_tuning", "pca_batch_jacobi_ctas", "pca_batch_plan_counts")
 STAGES = ("covariance", "cov_finalize", "jacobi", "empty", "compact", "refine", "sort_sign",
           "project")
 
@@ -52,6 +53,36 @@ class Info(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    """pca_tuning of include/gbpca.h."""
+    _fields_ = [("tc_slot_chunks", ctypes.c_int), ("batch_jacobi_ctas", ctypes.c_int * 8),
+                ("batch_cov_tc_fixed", ctypes.c_double), ("batch_proj_fixed", ctypes.c_double),
+                ("batch_cov_simt_fixed", ctypes.c_double),
+                ("batch_simt_items_per_sm", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["batch_jacobi_ctas"] = list(self.batch_jacobi_ctas)
+        return d
+
+    @classmethod
+    def from_dict(cls, d):
+        t = cls()
+        load().pca_tuning_defaults(ctypes.byref(t))
+        for f, _ in cls._fields_:
+            if f not in d:
+                continue
+            if f == "batch_jacobi_ctas":
+                v = list(d[f])
+                if len(v) != 8:
+                    raise ValueError("batch_jacobi_ctas needs 8 entries")
+                for i in range(8):
+                    t.batch_jacobi_ctas[i] = int(v[i])
+            else:
+                setattr(t, f, d[f])
+        return t
 
 
 class Tile(ctypes.Structure):
@@ -125,8 +156,41 @@ def load(build_if_missing: bool = False):
     lib.pca_combine_moments.restype = i
     lib.pca_bsq_to_bip.argtypes = [P, i, i64, i, P, P]
     lib.pca_bsq_to_bip.restype = i
+    TuP = ctypes.POINTER(Tuning)
+    lib.pca_tuning_defaults.argtypes = [TuP]
+    lib.pca_tuning_defaults.restype = None
+    lib.pca_set_tuning.argtypes = [TuP]
+    lib.pca_set_tuning.restype = i
+    lib.pca_get_tuning.argtypes = [TuP]
+    lib.pca_get_tuning.restype = i
+    lib.pca_batch_jacobi_ctas.argtypes = [i, i]
+    lib.pca_batch_jacobi_ctas.restype = i
+    lib.pca_batch_plan_counts.argtypes = [i, TP, i, i, ctypes.POINTER(i)]
+    lib.pca_batch_plan_counts.restype = i
     _lib = lib
     return lib
+
+
+def tuning() -> dict:
+    """The library's current tuning parameters (pca_get_tuning)."""
+    t = Tuning()
+    _check_rc(load().pca_get_tuning(ctypes.byref(t)))
+    return t.as_dict()
+
+
+def tuning_defaults() -> dict:
+    t = Tuning()
+    load().pca_tuning_defaults(ctypes.byref(t))
+    return t.as_dict()
+
+
+def set_tuning(params: dict | None = None) -> dict:
+    """Installs tuning parameters (missing keys take the defaults; None: all
+    defaults) and returns the previous ones (pca_set_tuning)."""
+    prev = tuning()
+    t = Tuning.from_dict(params or {})
+    _check_rc(load().pca_set_tuning(ctypes.byref(t)))
+    return prev
 
 
 def _dtype_code(t):
@@ -322,6 +386,25 @@ def jacobi_sms(B: int) -> int:
     return int(load().pca_jacobi_sms(int(B)))
 
 
+def batch_plan_counts(shapes, precision="mix", dtype_code: int = 0) -> dict:
+    """The plan pca_batch_create would make under the current tuning for tiles of
+    shapes [(N, B, k), ...], computed on the host (no device, no workspace)."""
+    tiles = (Tile * len(shapes))()
+    for t, (N, B, k) in enumerate(shapes):
+        tiles[t] = Tile(None, int(N), int(B), int(k), None, None, None, None)
+    c = (ctypes.c_int * 4)()
+    _check_rc(load().pca_batch_plan_counts(len(shapes), tiles, int(dtype_code),
+                                           _prec_code(precision), c))
+    return {"cov_items": c[0], "proj_items": c[1], "jacobi_launches": c[2],
+            "widest_cluster": c[3]}
+
+
+def batch_jacobi_ctas(B: int, request: int = 0) -> int:
+    """CTAs the batched form gives the Jacobi cluster of a B-band tile when the
+    tuning asks for `request` (0: the fewest that hold the matrix)."""
+    return int(load().pca_batch_jacobi_ctas(int(B), int(request)))
+
+
 def profile(enable: bool) -> None:
     load().pca_profile(1 if enable else 0)
 
@@ -384,8 +467,14 @@ class Batch:
     graph); ``info()`` waits and returns (worst status, per-tile info dicts)."""
 
     def __init__(self, cubes, k, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
-                 project: bool = True):
+                 project: bool = True, tuning="auto"):
+        """tuning: "auto" installs the autotuner's cached parameters for this
+        device, dtype and precision while planning (the library defaults when
+        nothing is cached); a dict installs those; None plans with whatever the
+        library holds."""
         import torch
+
+        from . import tune
         if not cubes:
             raise ValueError("no cubes")
         ks = list(k) if isinstance(k, (list, tuple)) else [int(k)] * len(cubes)
@@ -411,6 +500,14 @@ class Batch:
                             V.data_ptr(), Q.data_ptr() if Q is not None else None)
         self._tiles = tiles
         lib = load()
+        if tuning == "auto":
+            tuning = tune.lookup(tune.device_key(dev, dt, self.precision))
+        self.tuning = tuning
+        with tune.applied(tuning):
+            self._plan_batch(lib, cubes, tiles, dt, tol, sweeps_max, dev)
+
+    def _plan_batch(self, lib, cubes, tiles, dt, tol, sweeps_max, dev):
+        import torch
         n = lib.pca_batch_workspace_size(len(cubes), tiles, dt, self.precision)
         if n == 0:
             bad = next(t for t in range(len(cubes))

@@ -25,11 +25,11 @@ __global__ void k_header_init(DevHeader* h, int refine_iters, float tol32) {
 
 }  // namespace
 
-// 64 chunks = 2048 pixels per slot: on 256 mixture tiles the eigenvalue error
-// relative to lam_1 grew linearly with the slot length (about 1.0e-5 at 64
+// Default 64 chunks = 2048 pixels per slot: on 256 mixture tiles the eigenvalue
+// error relative to lam_1 grew linearly with the slot length (about 1.0e-5 at 64
 // chunks, 2.0e-5 at 128, 4.9e-4 with one slot per CTA of up to 170 k pixels),
 // while each halving of the length cost about 7% more covariance time.
-int tc_slot_chunks() { return 64; }
+int tc_slot_chunks() { return tuning().tc_slot_chunks; }
 
 int device_sms() {
   int dev = 0, sms = 0;
@@ -466,6 +466,11 @@ int pca_jacobi_sms(int B) {
   jacobi_cluster_shape(B, &nA, &nV);
   const int P = round_even(B) / 2;
   return (nA > P ? P : nA) + nV;
+}
+
+int pca_batch_jacobi_ctas(int B, int request) {
+  if (B < 2 || B > kMaxB || request < 0 || request > 8) return 0;
+  return jacobi_ctas_at_least(B, request);
 }
 
 int pca_profile(int enable) {

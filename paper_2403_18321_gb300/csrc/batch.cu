@@ -26,7 +26,6 @@ namespace {
 
 constexpr int kCovChunk = 32;    // pixel granularity of covariance items
 constexpr int kProjChunk = 64;   // pixel granularity of projection items
-constexpr int kSimtItemsPerSm = 4;
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -45,15 +44,24 @@ __global__ void k_header_init_batched(TileDesc* __restrict__ T, int ntiles, int 
 // Cost of one chunk of a tile with B bands, in arbitrary units, fitted to the
 // measured times of the streaming kernels on this GPU: a fixed part per chunk
 // (barrier round trips, the MMA/epilogue cadence) plus a part per band; the
-// SIMT covariance grows with the B^2/2 products per pixel.
+// SIMT covariance grows with the B^2/2 products per pixel.  The fixed parts
+// are tuning parameters (defaults: ~1.16 us + 2.5 ns per band per 32-pixel
+// covariance chunk, ~1.07 us + 4.8 ns per band per 64-pixel projection chunk).
 enum class Cost { kTensorCov, kSimtCov, kProject };
-double chunk_cost(Cost c, int B) {
+double chunk_cost(const pca_tuning& tu, Cost c, int B) {
   switch (c) {
-    case Cost::kTensorCov: return 464.0 + B;         // ~1.16 us + 2.5 ns per band (32 pixels)
-    case Cost::kSimtCov: return 13900.0 + (double)B * B;
-    case Cost::kProject: return 223.0 + B;           // ~1.07 us + 4.8 ns per band (64 pixels)
+    case Cost::kTensorCov: return tu.batch_cov_tc_fixed + B;
+    case Cost::kSimtCov: return tu.batch_cov_simt_fixed + (double)B * B;
+    case Cost::kProject: return tu.batch_proj_fixed + B;
   }
   return B;
+}
+
+// CTAs of the batched Jacobi cluster of a B-band tile under the tuning.
+int batch_cluster_ctas(const pca_tuning& tu, int B) {
+  const int bucket = (round_even(B) - 1) / 32;
+  const int want = tu.batch_jacobi_ctas[bucket < 0 ? 0 : (bucket > 7 ? 7 : bucket)];
+  return jacobi_ctas_at_least(B, want);
 }
 
 // Splits the tiles' chunks into `ctas` contiguous ranges of equal cost; every
@@ -63,18 +71,20 @@ struct Split {
   std::vector<std::vector<CovItem>> per_cta;
   std::vector<int> parts;
 };
-Split split_chunks(const std::vector<pca_tile>& tiles, int chunk, int ctas, Cost cost) {
+Split split_chunks(const std::vector<pca_tile>& tiles, int chunk, int ctas, Cost cost,
+                   const pca_tuning& tu) {
   Split sp;
   const int n = (int)tiles.size();
   sp.per_cta.assign(ctas, {});
   sp.parts.assign(n, 0);
   long double total = 0;
-  for (const pca_tile& t : tiles) total += (long double)((t.N + chunk - 1) / chunk) * chunk_cost(cost, t.B);
+  for (const pca_tile& t : tiles)
+    total += (long double)((t.N + chunk - 1) / chunk) * chunk_cost(tu, cost, t.B);
   long double w0 = 0;  // weight before the current tile
   int g = 0;
   for (int ti = 0; ti < n; ++ti) {
     const int64_t nch = (tiles[ti].N + chunk - 1) / chunk;
-    const double wc = chunk_cost(cost, tiles[ti].B);  // cost of one chunk
+    const double wc = chunk_cost(tu, cost, tiles[ti].B);  // cost of one chunk
     int64_t c = 0;
     while (c < nch) {
       int64_t cend = nch;
@@ -149,16 +159,16 @@ struct BatchLayout {
 };
 
 BatchLayout batch_layout(const std::vector<pca_tile>& tiles, pca_dtype dt, pca_precision prec,
-                         int sms, std::vector<TileDesc>* descs, char* base) {
+                         int sms, const pca_tuning& tu, std::vector<TileDesc>* descs, char* base) {
   (void)dt;
   BatchLayout L{};
   const int n = (int)tiles.size();
   const bool mix = prec == PCA_PREC_MIX, p64 = prec == PCA_PREC_P64;
   const bool refine = refine_iterations(prec) > 0;
-  const int cov_ctas = mix ? sms : kSimtItemsPerSm * sms;
-  L.cov = split_chunks(tiles, kCovChunk, cov_ctas, mix ? Cost::kTensorCov : Cost::kSimtCov);
+  const int cov_ctas = mix ? sms : tu.batch_simt_items_per_sm * sms;
+  L.cov = split_chunks(tiles, kCovChunk, cov_ctas, mix ? Cost::kTensorCov : Cost::kSimtCov, tu);
   if (mix) {  // bound the tensor-core accumulation: long items become several slots
-    const int64_t cap = tc_slot_chunks();
+    const int64_t cap = tu.tc_slot_chunks;
     std::vector<int> slot_of(n, 0);
     for (auto& v : L.cov.per_cta) {
       std::vector<CovItem> split;
@@ -181,7 +191,7 @@ BatchLayout batch_layout(const std::vector<pca_tile>& tiles, pca_dtype dt, pca_p
   std::vector<int> pmap;
   for (int i = 0; i < n; ++i)
     if (tiles[i].proj) { ptiles.push_back(tiles[i]); pmap.push_back(i); }
-  L.proj = split_chunks(ptiles, kProjChunk, sms, Cost::kProject);
+  L.proj = split_chunks(ptiles, kProjChunk, sms, Cost::kProject, tu);
   for (auto& v : L.proj.per_cta)
     for (auto& it : v) it.tile = pmap[it.tile];
   int ncov = 0, nproj = 0;
@@ -264,7 +274,37 @@ size_t pca_batch_workspace_size(int ntiles, const pca_tile* tiles, pca_dtype dty
     if (!args_ok(kDummy, dtype, t.N, t.B, t.k, 1.0, 1, prec)) return 0;
     t.cube = kDummy;
   }
-  return batch_layout(v, dtype, prec, device_sms(), nullptr, nullptr).total;
+  return batch_layout(v, dtype, prec, device_sms(), tuning(), nullptr, nullptr).total;
+}
+
+int pca_batch_plan_counts(int ntiles, const pca_tile* tiles, pca_dtype dtype, pca_precision prec,
+                          int* counts) {
+  static const float kDummy[4] = {0.f, 0.f, 0.f, 0.f};
+  if (ntiles < 1 || !tiles || !counts) return PCA_ERR_ARG;
+  std::vector<pca_tile> v = as_vector(ntiles, tiles);
+  for (pca_tile& t : v) {
+    if (!args_ok(kDummy, dtype, t.N, t.B, t.k, 1.0, 1, prec)) return PCA_ERR_ARG;
+    t.cube = kDummy;
+    t.proj = const_cast<float*>(kDummy);   // every tile counted as projected
+  }
+  const pca_tuning tu = tuning();
+  const BatchLayout L = batch_layout(v, dtype, prec, device_sms(), tu, nullptr, nullptr);
+  int ncov = 0, nproj = 0;
+  for (const auto& c : L.cov.per_cta) ncov += (int)c.size();
+  for (const auto& c : L.proj.per_cta) nproj += (int)c.size();
+  std::vector<int> shapes;
+  int widest = 0;
+  for (const pca_tile& t : v) {
+    const int n = batch_cluster_ctas(tu, t.B);
+    shapes.push_back(jacobi_width(t.B) * 16 + n);
+    widest = std::max(widest, n);
+  }
+  std::sort(shapes.begin(), shapes.end());
+  counts[0] = ncov;
+  counts[1] = nproj;
+  counts[2] = (int)(std::unique(shapes.begin(), shapes.end()) - shapes.begin());
+  counts[3] = widest;
+  return PCA_OK;
 }
 
 int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dtype dtype,
@@ -283,7 +323,8 @@ int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dt
   const int sms = device_sms();
   char* ws = static_cast<char*>(workspace);
   std::vector<TileDesc> descs;
-  const BatchLayout L = batch_layout(v, dtype, prec, sms, &descs, ws);
+  const pca_tuning tu = tuning();
+  const BatchLayout L = batch_layout(v, dtype, prec, sms, tu, &descs, ws);
   if (ws_bytes < L.total) return PCA_ERR_WORKSPACE;
 
   pca_batch* b = new (std::nothrow) pca_batch;
@@ -344,7 +385,7 @@ int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dt
      // share a launch), and within a shape the largest matrices start first.
     std::vector<int> order(ntiles);
     for (int i = 0; i < ntiles; ++i) order[i] = i;
-    auto key = [&](int i) { return jacobi_width(v[i].B) * 16 + jacobi_batch_ctas(v[i].B); };
+    auto key = [&](int i) { return jacobi_width(v[i].B) * 16 + batch_cluster_ctas(tu, v[i].B); };
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
       return key(a) != key(c) ? key(a) > key(c) : v[a].B > v[c].B;
     });
@@ -361,7 +402,7 @@ int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dt
       unsigned char* dst = img.data() + L.lists + pb * pos;
       const size_t smem = jacobi_fill_params(dst, descs[i].C, v[i].B, b->tol32, sweeps_max,
                                              relative_stop(prec), descs[i].diag32, descs[i].v32,
-                                             descs[i].hdr, jacobi_batch_ctas(v[i].B));
+                                             descs[i].hdr, batch_cluster_ctas(tu, v[i].B));
       bu.smem = std::max(bu.smem, smem);
       if (bu.count == 0) bu.first.assign(dst, dst + pb);
       ++bu.count;

@@ -83,6 +83,9 @@ inline int ortho_steps(pca_precision prec) {
 // the element-wise test would still demand); P32 and P64 use the element-wise test.
 inline bool relative_stop(pca_precision prec) { return prec != PCA_PREC_MIX; }
 
+// The current tuning parameters (pca_set_tuning; measured defaults otherwise).
+pca_tuning tuning();
+
 // Argument checks shared by the entry points; SMs of the current device.
 bool args_ok(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol,
              int sweeps_max, pca_precision prec);
@@ -281,6 +284,9 @@ cudaError_t launch_cov_finalize_batched(const TileDesc* T, int ntiles, int maxB,
 int jacobi_width(int B);     // V values per lane of a V row (kernel variant)
 int jacobi_min_ctas(int B);  // fewest CTAs per cluster of the default kernel variant
 int jacobi_batch_ctas(int B);  // fewest CTAs per cluster of any variant (batched form)
+// The fewest CTAs, at least n, whose cluster holds a matrix of B bands (some
+// variant fits); n <= 0 gives jacobi_batch_ctas(B).
+int jacobi_ctas_at_least(int B, int n);
 size_t jacobi_params_bytes();
 // Writes the parameters of one matrix to dst (host) for a cluster of nA CTAs
 // (0: the latency-oriented default of the single-matrix form); returns the

@@ -805,9 +805,11 @@ int jacobi_width(int B) { return v_width(round_even(B)); }
 // Fewest CTAs whose kernel variant holds the matrix: every CTA's rows of V
 // and bulk blocks of both parities within the variant's capacity (the same
 // counts the kernel checks).
-int jacobi_batch_ctas(int B) {
+int jacobi_batch_ctas(int B) { return jacobi_ctas_at_least(B, 1); }
+
+int jacobi_ctas_at_least(int B, int n0) {
   const int Bp = round_even(B), P = Bp / 2;
-  for (int n = 1; n <= kMaxCl; ++n) {
+  for (int n = n0 < 1 ? 1 : n0; n <= kMaxCl; ++n) {
     Params prm;
     make_params(nullptr, B, 1.f, 1, true, nullptr, nullptr, nullptr, n, &prm);
     const bool wide = prm.nA < jacobi_min_ctas(B);

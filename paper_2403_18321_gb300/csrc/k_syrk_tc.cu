@@ -15,11 +15,17 @@
 //               of x -- written transposed ([band][pixel], K-major core-
 //               matrix layout) into a 3-stage operand ring, and keep the
 //               band sums S1 = sum x of the values they converted (FP32 over
-//               16 chunks, then FP64);
+//               16 chunks, then FP64); each warp also flags whether any lo of
+//               its values is non-zero;
 //   warp 1      MMA issuer (one thread): D += hi hi^T + hi lo^T + lo hi^T
 //               for the upper block-triangle (row tile 0: bands 0-127 x all;
 //               row tile 1: bands 128-255 x bands 128-255) with FP32
-//               accumulation in TMEM;
+//               accumulation in TMEM.  A chunk whose lo parts are all zero
+//               gets the first product only: the other two are exactly zero.
+//               That is the rule for 16-bit cubes, whose shift is rounded to
+//               the input type: y - s then has at most the bits of the
+//               input's grid, which a single FP16 holds as long as the
+//               pixel's deviation stays within 2^11 grid steps;
 //   warps 2-5   epilogue: TMEM -> registers -> the item's partial slot
 //               (packed upper triangle, FP32, still scaled by 2^(e_i+e_j));
 //               the converters write S1 (FP64, unscaled).
@@ -57,6 +63,7 @@ struct __align__(8) SyncBlock {
   uint64_t done;       // the MMAs of an item finished (one phase per item)
   uint64_t tfree;      // the epilogue has read the item's accumulators out of TMEM
   uint64_t drain;      // every MMA of the CTA finished (teardown)
+  int lo_nz[kOpStages][kConvWarps];  // per operand stage and converter warp: a lo part is non-zero
   uint32_t tmem_base;
   int abort;
 };
@@ -66,6 +73,21 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) { return sdesc_kmajor(a
 
 template <typename In>
 __device__ __forceinline__ float elem(const In* p) { return to_f32<In>(*p); }
+
+// The band shift on the input's own grid (16-bit cubes), so that y - s is exact
+// in FP32 and carries no more bits than the input does.
+template <typename In>
+__device__ __forceinline__ float on_grid(float m);
+template <>
+__device__ __forceinline__ float on_grid<float>(float m) { return m; }
+template <>
+__device__ __forceinline__ float on_grid<__nv_bfloat16>(float m) {
+  return __bfloat162float(__float2bfloat16_rn(m));
+}
+template <>
+__device__ __forceinline__ float on_grid<__half>(float m) {
+  return fabsf(m) <= 65504.f ? __half2float(__float2half_rn(m)) : m;
+}
 
 // barriers among the converter warps only (the producer and MMA warps are busy)
 __device__ __forceinline__ void conv_sync() {
@@ -223,20 +245,28 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
           tc_fence_after();
           const uint32_t hi = ops_base + (uint32_t)(o * 2) * kOpBytes;
           const uint32_t lo = hi + kOpBytes;
+          // the converters' flags (written before their arrivals on opfull)
+          int nz = 0;
+#pragma unroll
+          for (int w = 0; w < kConvWarps; ++w) nz |= ((volatile int*)sb->lo_nz[o])[w];
 #pragma unroll
           for (int kk = 0; kk < kKC / 16; ++kk) {
             const uint32_t ko = kk * 2 * kLBO;
             const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;
             // tile 0: rows 0..127 (A) x rows 0..N0-1 (B)
             mma_f16(tbase, sdesc(hi + ko), sdesc(hi + ko), id0, acc0);
-            mma_f16(tbase, sdesc(hi + ko), sdesc(lo + ko), id0, 1u);
-            mma_f16(tbase, sdesc(lo + ko), sdesc(hi + ko), id0, 1u);
+            if (nz) {
+              mma_f16(tbase, sdesc(hi + ko), sdesc(lo + ko), id0, 1u);
+              mma_f16(tbase, sdesc(lo + ko), sdesc(hi + ko), id0, 1u);
+            }
             if (two_tiles) {
               const uint32_t r128 = (128 / 8) * kSBO;
               const uint32_t t1 = tbase + (uint32_t)N0;
               mma_f16(t1, sdesc(hi + r128 + ko), sdesc(hi + r128 + ko), id1, acc0);
-              mma_f16(t1, sdesc(hi + r128 + ko), sdesc(lo + r128 + ko), id1, 1u);
-              mma_f16(t1, sdesc(lo + r128 + ko), sdesc(hi + r128 + ko), id1, 1u);
+              if (nz) {
+                mma_f16(t1, sdesc(hi + r128 + ko), sdesc(lo + r128 + ko), id1, 1u);
+                mma_f16(t1, sdesc(lo + r128 + ko), sdesc(hi + r128 + ko), id1, 1u);
+              }
             }
           }
           first = false;
@@ -300,7 +330,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
             const double tot = psum[b] + psum[kRows + b];
             lo = fminf(pmin[b], pmin[kRows + b]);
             hi = fmaxf(pmax[b], pmax[kRows + b]);
-            m = (float)(tot / (double)Sp);
+            m = on_grid<In>((float)(tot / (double)Sp));
             double dev = fmax((double)hi - (double)m, (double)m - (double)lo);
             if (!isfinite(m) || !isfinite(dev)) { m = 0.f; dev = 0.0; }
             if (!(dev > 0.0)) dev = fabs((double)m);
@@ -334,6 +364,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         isc[u] = ldexpf(1.f, sesc[row]);
       }
       int out_of_range = 0;   // a scaled value of this item left the FP16 range
+      const int cw = warp - 2;  // converter warp index
       int c = 0;
       for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ++c, ++qs) {
         const int s = qs % S, o = qs % kOpStages;
@@ -353,6 +384,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         const In* gsrc = cube + p0 * B;
         unsigned char* hi = ops + (size_t)(o * 2) * kOpBytes;
         unsigned char* lo = hi + kOpBytes;
+        uint32_t lo_bits = 0;    // OR of this thread's lo parts in this chunk
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const int pg = ipg[u], b = ib[u];
@@ -384,13 +416,19 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
             float a, bb;
             unpack_f16x2(h[k], a, bb);
             l[k] = pack_f16x2(x[2 * k] - a, x[2 * k + 1] - bb);
+            lo_bits |= l[k];
           }
           *reinterpret_cast<uint4*>(hi + ioff[u]) = make_uint4(h[0], h[1], h[2], h[3]);
           *reinterpret_cast<uint4*>(lo + ioff[u]) = make_uint4(l[0], l[1], l[2], l[3]);
         }
+        const int any_lo = __any_sync(kFull, lo_bits != 0u);
         fence_proxy_async();
         __syncwarp();
-        if (lane == 0) { mbar_arrive(&sb->opfull[o]); mbar_arrive(&sb->empty[s]); }
+        if (lane == 0) {
+          sb->lo_nz[o][cw] = any_lo;   // published by the release of the arrival below
+          mbar_arrive(&sb->opfull[o]);
+          mbar_arrive(&sb->empty[s]);
+        }
         if ((c + 1) % kS1Flush == 0) {
 #pragma unroll
           for (int u = 0; u < 2; ++u) { s1d[u] += (double)s1f[u]; s1f[u] = 0.f; }

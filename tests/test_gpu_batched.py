@@ -207,3 +207,31 @@ def test_batch_full_size_workload(gbpca_lib, form):
         ref = oracle.pca_fit(c.Y.cpu().numpy(), 8, tol=1e-14)
         mu, ev, V, Q = results[t]
         compare((_host(mu), _host(ev), _host(V), _host(Q)), ref, 8, form)
+
+
+@pytest.mark.gpu
+def test_autotuned_batch_keeps_parity(gbpca_lib, tmp_path):
+    """The autotuner times its candidates on a small batch, caches the fastest
+    parameters, and a batch planned from the cache (other cluster shapes and
+    work splits) still matches the oracle tile by tile."""
+    from paper_2403_18321_gb300 import tune
+    g = gbpca_lib
+    cubes = _cubes(SHAPES[3:12], seed0=400)
+    dev = [torch.as_tensor(c.Y).cuda() for c in cubes]
+    ks = [c.k for c in cubes]
+    path = str(tmp_path / "tuning.json")
+    res = tune.tune_batch(dev, ks, precision="mix", tol=1e-10, warmup=1, reps=3, path=path)
+    assert len(res["trials"]) > 3 and res["ms"] <= res["default_ms"]
+    params = tune.lookup(res["key"], path)
+    assert params == {k: v for k, v in res["params"].items() if k in tune.SPEED_KEYS}
+    # force a non-default shape so that the check covers a tuned plan either way
+    params = dict(params, batch_jacobi_ctas=[8] * 8, batch_cov_tc_fixed=232.0)
+    b = g.Batch(dev, ks, tol=1e-10, precision="mix", tuning=params)
+    b.run()
+    status, infos = b.info()
+    assert status == 0, infos
+    assert g.tuning() == g.tuning_defaults()          # planning restored the defaults
+    for c, (mu, ev, V, Q) in zip(cubes, b.results):
+        ref = oracle.pca_fit(c.Y, c.k, tol=1e-14)
+        compare((_host(mu), _host(ev), _host(V), _host(Q)), ref, c.k, "mix")
+    b.close()
