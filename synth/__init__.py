@@ -18,6 +18,7 @@ Workloads (pixels x bands, component count k):
                     Poisson-like noise, k=10
   planted_spectrum  2048x2048 x 224, s_i = 0.7^(i-1) over 20 components,
                     1e-3 floor, values in [0, 1] rounded to bf16 (or fp16), k=20
+                    (planted_spectrum_device: the same recipe drawn on a GPU)
   tile_batch        256 tiles, N log-uniform in [4096, 262144],
                     B in {64,96,128,160,200,224,256}, 3-15 endmembers, k=8
                     (tile: numpy on the host; tile_device: torch on a GPU)
@@ -125,17 +126,20 @@ def orthonormal_basis(rng, B: int) -> np.ndarray:
 def planted_spectrum(seed: int = 20, side: int = 2048, bands: int = 224, comps: int = 20,
                      ratio: float = 0.7, floor: float = 1e-3, dtype: str = "bf16",
                      k: int = 20, tol: float = 1e-10, sweeps_max: int = 30,
-                     chunk: int = 1 << 18, name: str = "planted_spectrum"):
+                     chunk: int = 1 << 18, name: str = "planted_spectrum",
+                     pixels: int | None = None):
     """Y = clip(0.5 + 0.08 U diag(s) W^T, 0, 1) rounded to bf16 or fp16, U ~ N(0,1),
     W orthonormal, s_i = ratio^(i-1) for i <= comps, floor otherwise.
-    Returns a Cube whose Y is a torch tensor of the requested 16-bit dtype (CPU)."""
+    Returns a Cube whose Y is a torch tensor of the requested 16-bit dtype (CPU).
+    pixels: only the first `pixels` rows of the side x side cube (the same values
+    the whole cube has there; a bounded sample for a slow consumer)."""
     import torch
     rng = np.random.default_rng(seed)
     W = orthonormal_basis(rng, bands)
     s = np.full(bands, floor)
     s[:comps] = ratio ** np.arange(comps)
     Ms = (s[:, None] * W.T).astype(np.float32)          # diag(s) W^T
-    N = side * side
+    N = side * side if pixels is None else min(side * side, int(pixels))
     tdt = torch.bfloat16 if dtype == "bf16" else torch.float16
     out = torch.empty((N, bands), dtype=tdt)
     for n0 in range(0, N, chunk):
@@ -145,6 +149,35 @@ def planted_spectrum(seed: int = 20, side: int = 2048, bands: int = 224, comps: 
         out[n0:n1] = torch.from_numpy(blk).to(tdt)
     return Cube(name, out, k, tol, sweeps_max, (side, side),
                 dict(seed=seed, s=s, W=W, dtype=dtype))
+
+
+def planted_spectrum_device(device, seed: int = 20, side: int = 2048, bands: int = 224,
+                            comps: int = 20, ratio: float = 0.7, floor: float = 1e-3,
+                            dtype: str = "bf16", k: int = 20, tol: float = 1e-10,
+                            sweeps_max: int = 30, chunk: int = 1 << 20,
+                            name: str = "planted_spectrum"):
+    """The recipe of ``planted_spectrum`` (same W and s from the same numpy seed)
+    with U ~ N(0, 1) drawn on a CUDA device by a torch generator seeded with
+    `seed`, for the full-size cube that would take long to draw on the host.
+    The values differ from ``planted_spectrum``'s (another generator of U); the
+    distribution is the same.  Y is a device tensor of the 16-bit dtype."""
+    import torch
+    rng = np.random.default_rng(seed)
+    W = orthonormal_basis(rng, bands)
+    s = np.full(bands, floor)
+    s[:comps] = ratio ** np.arange(comps)
+    Ms = torch.from_numpy((s[:, None] * W.T).astype(np.float32)).to(device)
+    N = side * side
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float16
+    out = torch.empty((N, bands), dtype=tdt, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    for n0 in range(0, N, chunk):
+        n1 = min(N, n0 + chunk)
+        U = torch.randn(n1 - n0, bands, generator=gen, device=device, dtype=torch.float32)
+        out[n0:n1] = (U @ Ms).mul_(0.08).add_(0.5).clamp_(0.0, 1.0).to(tdt)
+    return Cube(name, out, k, tol, sweeps_max, (side, side),
+                dict(seed=seed, s=s, W=W, dtype=dtype, generator="torch-device"))
 
 
 TILE_BANDS = (64, 96, 128, 160, 200, 224, 256)
