@@ -314,11 +314,17 @@ int pca_fit_batched(int ntiles, const pca_tile *tiles, pca_dtype dtype, double t
  * batch (a plan keeps what it read); change them before sizing a workspace,
  * or a fit may find its workspace too small (PCA_ERR_WORKSPACE).  Host only.
  *
- * tc_slot_chunks   MIX covariance: the longest run of 32-pixel chunks that one
- *                  tensor-memory accumulator sums in FP32 before it is written
- *                  out and added in FP64 (1..1024, default 64).  The FP32
- *                  accumulation error grows with the run; shorter runs write
- *                  more partials.
+ * tc_slot_chunks   MIX covariance of FP32 cubes: the longest run of 32-pixel
+ *                  chunks that one tensor-memory accumulator sums in FP32
+ *                  before it is written out and added in FP64 (1..1024,
+ *                  default 8).  The FP32 accumulation error grows linearly with
+ *                  the run (measured ||dC||_2 / lambda_1 on the 610x340x103
+ *                  scene: 3.0e-7 at 2 chunks, 1.2e-6 at 8, 2.5e-6 at 16, 8.0e-6
+ *                  at 64); shorter runs write more partials.
+ * tc_slot_chunks_16bit  the same for BF16 and FP16 cubes (default 64).  Their
+ *                  shifted values fit one FP16 each, the products are exact and
+ *                  so are the FP32 sums while they stay below 2^24 units of the
+ *                  product grid, which 64 chunks of centred data do.
  * batch_jacobi_ctas[i]  batched form: CTAs of the Jacobi cluster of a tile
  *                  with 32i < B' <= 32(i+1) bands (B' = B rounded up to even);
  *                  0 = the fewest that hold the matrix (default), otherwise
@@ -338,6 +344,7 @@ int pca_fit_batched(int ntiles, const pca_tile *tiles, pca_dtype dtype, double t
  */
 typedef struct {
   int tc_slot_chunks;
+  int tc_slot_chunks_16bit;
   int batch_jacobi_ctas[8];
   double batch_cov_tc_fixed;
   double batch_proj_fixed;

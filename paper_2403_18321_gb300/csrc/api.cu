@@ -25,11 +25,15 @@ __global__ void k_header_init(DevHeader* h, int refine_iters, float tol32) {
 
 }  // namespace
 
-// Default 64 chunks = 2048 pixels per slot: on 256 mixture tiles the eigenvalue
-// error relative to lam_1 grew linearly with the slot length (about 1.0e-5 at 64
-// chunks, 2.0e-5 at 128, 4.9e-4 with one slot per CTA of up to 170 k pixels),
-// while each halving of the length cost about 7% more covariance time.
-int tc_slot_chunks() { return tuning().tc_slot_chunks; }
+// FP32 cubes: 8 chunks = 256 pixels per slot by default.  The covariance error
+// grows linearly with the slot length (||dC||_2 / lambda_1 on the 103-band scene:
+// 1.2e-6 at 8 chunks, about the plain FP32 form's, 8.0e-6 at 64), at about 50%
+// more covariance time than 64 chunks there.  16-bit cubes: 64 chunks, their
+// products and sums are exact (||dC||_2 = 2e-13 lambda_1 on the planted cube).
+int tc_slot_chunks(pca_dtype dt) {
+  const pca_tuning t = tuning();
+  return dt == PCA_F32 ? t.tc_slot_chunks : t.tc_slot_chunks_16bit;
+}
 
 int device_sms() {
   int dev = 0, sms = 0;
@@ -83,13 +87,12 @@ namespace {
 }  // namespace
 
 Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, int num_sms) {
-  (void)dt;
   Layout L{};
   const int Bp = round_even(B);
   if (prec == PCA_PREC_MIX) {
     L.tc_ctas = (int)std::min<int64_t>(num_sms, std::max<int64_t>(1, (N + 127) / 128));
     // every CTA gets the same number of slots, each at most tc_slot_chunks() long
-    const int64_t nchunk = (N + 31) / 32, cap = tc_slot_chunks();
+    const int64_t nchunk = (N + 31) / 32, cap = tc_slot_chunks(dt);
     const int64_t per_cta = (nchunk + L.tc_ctas - 1) / L.tc_ctas;
     L.partials = L.tc_ctas * (int)((per_cta + cap - 1) / cap);
     L.s2_bytes_el = 4;

@@ -160,7 +160,6 @@ struct BatchLayout {
 
 BatchLayout batch_layout(const std::vector<pca_tile>& tiles, pca_dtype dt, pca_precision prec,
                          int sms, const pca_tuning& tu, std::vector<TileDesc>* descs, char* base) {
-  (void)dt;
   BatchLayout L{};
   const int n = (int)tiles.size();
   const bool mix = prec == PCA_PREC_MIX, p64 = prec == PCA_PREC_P64;
@@ -168,7 +167,7 @@ BatchLayout batch_layout(const std::vector<pca_tile>& tiles, pca_dtype dt, pca_p
   const int cov_ctas = mix ? sms : tu.batch_simt_items_per_sm * sms;
   L.cov = split_chunks(tiles, kCovChunk, cov_ctas, mix ? Cost::kTensorCov : Cost::kSimtCov, tu);
   if (mix) {  // bound the tensor-core accumulation: long items become several slots
-    const int64_t cap = tu.tc_slot_chunks;
+    const int64_t cap = dt == PCA_F32 ? tu.tc_slot_chunks : tu.tc_slot_chunks_16bit;
     std::vector<int> slot_of(n, 0);
     for (auto& v : L.cov.per_cta) {
       std::vector<CovItem> split;

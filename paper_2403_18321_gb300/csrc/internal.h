@@ -166,9 +166,10 @@ cudaError_t launch_syrk_simt(const void* cube, pca_dtype dt, int64_t N, int B, b
 cudaError_t launch_syrk_tc(const void* cube, pca_dtype dt, int64_t N, int B, float* shift,
                            int* escale, double* s1_part, float* s2_part, int partials, int ctas,
                            DevHeader* hdr, cudaStream_t st);
-// Longest run of 32-pixel chunks one tensor-core partial slot accumulates: the
-// FP32 accumulation in tensor memory loses accuracy in proportion to its length.
-int tc_slot_chunks();
+// Longest run of 32-pixel chunks one tensor-core partial slot accumulates for a
+// cube of this type: the FP32 accumulation in tensor memory loses accuracy in
+// proportion to its length (FP32 cubes); 16-bit cubes sum exact products.
+int tc_slot_chunks(pca_dtype dt);
 bool syrk_tc_supported(int B);
 
 // Sums the partials, applies the shift correction, writes mu (FP64), C (FP64, full

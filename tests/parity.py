@@ -36,8 +36,10 @@ import numpy as np
 
 EPS = {"p64": 1e-15, "mix": 1e-7, "p32": 1e-6}
 LAM_TOL = {"p64": 1e-10, "mix": 2e-5, "p32": 2e-3}
-# ||C - C*||_2 / lam_1 of each covariance form (asserted by the covariance stage test)
-E_COV = {"p64": 1e-13, "mix": 2e-5, "p32": 2e-6}
+# ||C - C*||_2 / lam_1 of each covariance form (asserted by the covariance stage
+# test).  MIX: FP32 accumulation runs of 8 chunks on FP32 cubes, measured up to
+# 1.5e-6 (exact products and sums on 16-bit cubes); P32: FP32 SIMT partials.
+E_COV = {"p64": 1e-13, "mix": 5e-6, "p32": 2e-6}
 MU_TOL = {"p64": 1e-12, "mix": 1e-6, "p32": 1e-6}
 LAM_ALL_TOL = {"p64": 1e-7, "mix": 1e-4, "p32": 2e-3}
 ORTH_TOL = {"p64": 1e-11, "mix": 1e-6, "p32": 1e-4}
