@@ -103,7 +103,7 @@ size_t pca_workspace_size(int64_t N, int B, int k, pca_dtype dtype, pca_precisio
  * cube       [N][B] device array of `dtype`, 16-byte aligned.
  * N          pixels, N >= 2 (C is divided by N-1, Sec. 4.2 stage 3).
  * B          bands, 2 <= B <= 256.
- * k          components to project onto, 1 <= k <= min(B, 32).
+ * k          components to project onto, 1 <= k <= B.
  * tol        Jacobi stop factor (Sec. 2, "until all off-diagonal elements are
  *            smaller than the stop factor").  The FP32 Jacobi applies
  *            tau = max(tol, 2^-22) for P32 and P64, which stop when every
@@ -196,7 +196,8 @@ int pca_combine_moments(int parts, const int64_t *n, const double *mu_parts,
  * 256 + 256*32 floats (33,792 bytes), held on every GPU that loads the
  * library until the process exits.  It allocates and frees nothing.
  *   - Arguments as pca_project, without workspace; B*(k+1) above the array
- *     size (impossible for valid B <= 256, k <= 32) returns PCA_ERR_ARG.
+ *     size (8,448 floats: up to 32 components at 256 bands, 131 at 64 bands)
+ *     returns PCA_ERR_ARG.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
@@ -254,7 +255,7 @@ int pca_backward(const void *cube, pca_dtype dtype, int64_t N, int B, int k, con
  * persistent projection launch walks (tile, pixel range) items.
  *
  * pca_tile   cube [N][B] device array of the batch's dtype, 16-byte aligned;
- *            N >= 2, 2 <= B <= 256, 1 <= k <= min(B, 32); device outputs
+ *            N >= 2, 2 <= B <= 256, 1 <= k <= B; device outputs
  *            mu [B], eigvals [B], eigvecs [B][B] (FP64, as pca_fit) and
  *            proj [N][k] FP32 (NULL: no projection for this tile).
  * All tiles share dtype, precision, tol and sweeps_max (as in pca_fit).

@@ -48,7 +48,7 @@ bool args_ok(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol
   if (!cube) return false;
   if (dt != PCA_F32 && dt != PCA_BF16 && dt != PCA_F16) return false;
   if (prec != PCA_PREC_P64 && prec != PCA_PREC_P32 && prec != PCA_PREC_MIX) return false;
-  if (N < 2 || B < 2 || B > kMaxB || k < 1 || k > B || k > kMaxK) return false;
+  if (N < 2 || B < 2 || B > kMaxB || k < 1 || k > B) return false;
   if (!(tol > 0.0) || !std::isfinite(tol)) return false;
   if (sweeps_max < 1 || sweeps_max > kMaxSweeps) return false;
   if (((uintptr_t)cube) % 16 != 0) return false;

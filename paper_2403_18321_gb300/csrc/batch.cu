@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kCovChunk = 32;    // pixel granularity of covariance items
 constexpr int kProjChunk = 64;   // pixel granularity of projection items
+constexpr int kProjCols = 32;    // columns of one projection pass
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -186,13 +187,23 @@ BatchLayout batch_layout(const std::vector<pca_tile>& tiles, pca_dtype dt, pca_p
     }
     L.cov.parts = slot_of;
   }
+  // one projection "tile" per projected tile and group of 32 columns (the
+  // projection kernel's pass width); CovItem.slot carries the column group
   std::vector<pca_tile> ptiles;
-  std::vector<int> pmap;
+  std::vector<int> pmap, gmap;
   for (int i = 0; i < n; ++i)
-    if (tiles[i].proj) { ptiles.push_back(tiles[i]); pmap.push_back(i); }
+    if (tiles[i].proj)
+      for (int grp = 0; grp * kProjCols < tiles[i].k; ++grp) {
+        ptiles.push_back(tiles[i]);
+        pmap.push_back(i);
+        gmap.push_back(grp);
+      }
   L.proj = split_chunks(ptiles, kProjChunk, sms, Cost::kProject, tu);
   for (auto& v : L.proj.per_cta)
-    for (auto& it : v) it.tile = pmap[it.tile];
+    for (auto& it : v) {
+      it.slot = gmap[it.tile];
+      it.tile = pmap[it.tile];
+    }
   int ncov = 0, nproj = 0;
   for (auto& v : L.cov.per_cta) ncov += (int)v.size();
   for (auto& v : L.proj.per_cta) nproj += (int)v.size();
@@ -361,6 +372,7 @@ int pca_batch_create(pca_batch** plan, int ntiles, const pca_tile* tiles, pca_dt
       for (const CovItem& it : c) {
         ProjItem p{};
         p.tile = it.tile;
+        p.pad = it.slot;               // column group
         p.c0 = it.p0 / kProjChunk;
         p.c1 = (it.p1 + kProjChunk - 1) / kProjChunk;
         items.push_back(p);

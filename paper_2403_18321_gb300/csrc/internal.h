@@ -11,7 +11,6 @@
 namespace gbpca {
 
 constexpr int kMaxB = 256;          // two 128-row tensor-core tiles; 8 Jacobi CTAs x 32 V rows
-constexpr int kMaxK = 32;
 constexpr int kMaxPartials = 320;   // per-CTA covariance partial slots
 constexpr float kJacobiFloor = 2.384185791015625e-07f;  // 2^-22: FP32 Jacobi stop floor
 constexpr float kMixJacobiFloor = 1e-5f;                 // MIX: refinement takes over from here
@@ -140,7 +139,7 @@ struct CovItem {
   int tile, slot;
   int64_t p0, p1;
 };
-// 64-pixel chunks [c0, c1) of one tile.
+// 64-pixel chunks [c0, c1) of one tile, columns [32 pad, 32 pad + 32) of its V_k.
 struct ProjItem {
   int tile, pad;
   int64_t c0, c1;

@@ -8,7 +8,8 @@
 //   S    = sym(V G V^T)
 //   dY   = (dQ - 1 mean_n dQ) V_k^T + 2/(N-1) X S.
 // Three stages:
-//   k_bwd_dv     one streaming pass over cube and dQ (TMA bulk copies of
+//   k_bwd_dv     one streaming pass over cube and dQ per group of 32
+//                columns of dQ (TMA bulk copies of
 //                64-pixel chunks): per-CTA partial sums of X^T dQ and of the
 //                columns of dQ (FP32), thread = band in each of three
 //                groups (two for k > 16, where the registers of 800 threads
@@ -62,12 +63,17 @@ struct __align__(16) DvSync {
   float combv[3][256];       // its xmax (by band), column sums and |dq| maxima
 };
 
+// One pass covers dQ columns [j0, j0 + k) (k <= 32) of a dQ whose rows are ld
+// floats long; the partials are written at the same column offset.  dQ rows
+// are bulk-copied with the cube chunk when the pass covers all columns
+// (ld == k), else read straight from dQ.
 template <typename In, int KQ>
 __global__ void __launch_bounds__(dv_threads(KQ), 1)
 k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, int B, int k,
-         const double* __restrict__ mu, float* __restrict__ dv_part, float* __restrict__ dqs_part,
-         float* __restrict__ xmax_part, float* __restrict__ dqmax_part, int cube_stage,
-         int dq_stage, int nst, DevHeader* __restrict__ hdr) {
+         int j0, int ld, const double* __restrict__ mu, float* __restrict__ dv_part,
+         float* __restrict__ dqs_part, float* __restrict__ xmax_part,
+         float* __restrict__ dqmax_part, int cube_stage, int dq_stage, int nst,
+         DevHeader* __restrict__ hdr) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* cst = smem;                                        // [nst][cube_stage]
   float* dqst = reinterpret_cast<float*>(smem + nst * cube_stage);  // [nst][dq_stage/4]
@@ -95,7 +101,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
         const int64_t p0 = (c_begin + c) * kDvPx;
         const int cp = (int)((N - p0) < kDvPx ? (N - p0) : kDvPx);
         const uint32_t cb = (uint32_t)((size_t)cp * B * sizeof(In)) & ~15u;
-        const uint32_t db = (uint32_t)((size_t)cp * k * 4) & ~15u;
+        const uint32_t db = ld == k ? (uint32_t)((size_t)cp * k * 4) & ~15u : 0u;
         mbar_expect_tx(&sy->full[s], cb + db);
         if (cb) bulk_g2s(cst + (size_t)s * cube_stage, cube + p0 * B, cb, &sy->full[s]);
         if (db) bulk_g2s(reinterpret_cast<unsigned char*>(dqst) + (size_t)s * dq_stage, dq + p0 * k, db,
@@ -123,15 +129,16 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
     const In* xs = reinterpret_cast<const In*>(cst + (size_t)s * cube_stage);
     const float* ds = dqst + (size_t)s * dq_stage / 4;
     const int copied_x = (int)((((size_t)cp * B * sizeof(In)) & ~(size_t)15) / sizeof(In));
-    const int copied_d = (int)((((size_t)cp * k * 4) & ~(size_t)15) / 4);
-    const bool whole = copied_x == cp * B && copied_d == cp * k;
+    const int copied_d = ld == k ? (int)((((size_t)cp * k * 4) & ~(size_t)15) / 4) : 0;
+    const bool whole = copied_x == cp * B;
     // dQ rows of this chunk padded to 16-byte rows (two buffers by chunk
     // parity), so that every pixel's row is read as KQ vectors
     float4* dqp = dqpad + (size_t)(c & 1) * kDvPx * KQ;
     for (int e = tid; e < cp * KQ * 4; e += kComp) {
       const int pp = e / (KQ * 4), j = e - pp * (KQ * 4);
       const int ed = pp * k + j;
-      reinterpret_cast<float*>(dqp)[e] = j < k ? (ed < copied_d ? ds[ed] : dq[p0 * k + ed]) : 0.f;
+      reinterpret_cast<float*>(dqp)[e] =
+          j < k ? (ed < copied_d ? ds[ed] : dq[(p0 + pp) * ld + j0 + j]) : 0.f;
     }
     dv_sync<kComp>();
     for (int p = grp; p < cp; p += kGroups) {
@@ -139,19 +146,14 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
       float dv[KQ * 4];
       if (whole) {
         if (b < B) x = to_f32<In>(xs[p * B + b]) - m;
-#pragma unroll
-        for (int q = 0; q < KQ; ++q) {
-          const float4 v = dqp[p * KQ + q];
-          dv[4 * q] = v.x; dv[4 * q + 1] = v.y; dv[4 * q + 2] = v.z; dv[4 * q + 3] = v.w;
-        }
       } else {
         const int ex = p * B + b;
         if (b < B) x = (ex < copied_x ? to_f32<In>(xs[ex]) : to_f32<In>(cube[p0 * B + ex])) - m;
+      }
 #pragma unroll
-        for (int j = 0; j < KQ * 4; ++j) {
-          const int ed = p * k + j;
-          dv[j] = j < k ? (ed < copied_d ? ds[ed] : dq[p0 * k + ed]) : 0.f;
-        }
+      for (int q = 0; q < KQ; ++q) {
+        const float4 v = dqp[p * KQ + q];
+        dv[4 * q] = v.x; dv[4 * q + 1] = v.y; dv[4 * q + 2] = v.z; dv[4 * q + 3] = v.w;
       }
       xmax = fmaxf(xmax, fabsf(x));
 #pragma unroll
@@ -173,7 +175,7 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
   if (c < nch && tid == 0 && hdr) set_status(hdr, PCA_ERR_TIMEOUT);
   // the other groups hand their sums to the first through shared memory, one
   // group and one column quad at a time
-  float* out = dv_part + ((size_t)g * B + b) * k;
+  float* out = dv_part + ((size_t)g * B + b) * ld + j0;
 #pragma unroll
   for (int q = 0; q < KQ; ++q) {
     for (int h = 1; h < kGroups; ++h) {
@@ -208,17 +210,18 @@ k_bwd_dv(const In* __restrict__ cube, const float* __restrict__ dq, int64_t N, i
   }
   if (grp == 0) {
     if (b < k) {
-      dqs_part[(size_t)g * k + b] = csum;
-      dqmax_part[(size_t)g * k + b] = dmax;
+      dqs_part[(size_t)g * ld + j0 + b] = csum;
+      dqmax_part[(size_t)g * ld + j0 + b] = dmax;
     }
     if (b < B) xmax_part[(size_t)g * B + b] = xmax;
   }
 }
 
 // ------------------------------------------------------------------ k_bwd_reduce
-// dVk[b][j] = sum over the partials (FP64), FP32 copy of mu; CTA 0 also forms
-// the column means of dQ.  One CTA per band: warp w adds the partials
-// w, w + 8, ... for every column (lane = column), then the eight warp sums.
+// dVk[b][j] = sum over the partials (FP64), FP32 copy of mu; the CTAs of band 0
+// also form the column means of dQ.  One CTA per band and group of 32 columns:
+// warp w adds the partials w, w + 8, ... for every column (lane = column), then
+// the eight warp sums.
 constexpr int kRedWarps = 8;
 
 __global__ void __launch_bounds__(kRedWarps * 32)
@@ -227,47 +230,50 @@ k_bwd_reduce(const float* __restrict__ dv_part, const float* __restrict__ dqs_pa
              float* __restrict__ mdq, float* __restrict__ mu32) {
   __shared__ double red[2][kRedWarps][32];
   const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = 32 * blockIdx.y + lane;
   double s = 0.0, t = 0.0;
-  if (lane < k) {
+  if (j < k) {
     for (int gg = warp; gg < parts; gg += kRedWarps) {
-      s += (double)dv_part[((size_t)gg * B + b) * k + lane];
-      if (b == 0) t += (double)dqs_part[(size_t)gg * k + lane];
+      s += (double)dv_part[((size_t)gg * B + b) * k + j];
+      if (b == 0) t += (double)dqs_part[(size_t)gg * k + j];
     }
   }
   red[0][warp][lane] = s;
   red[1][warp][lane] = t;
   __syncthreads();
-  if (warp == 0 && lane < k) {
+  if (warp == 0 && j < k) {
     double a = 0.0, c = 0.0;
 #pragma unroll
     for (int w = 0; w < kRedWarps; ++w) { a += red[0][w][lane]; c += red[1][w][lane]; }
-    dVk[(size_t)b * k + lane] = a;
-    if (b == 0) mdq[lane] = (float)(c / (double)N);
+    dVk[(size_t)b * k + j] = a;
+    if (b == 0) mdq[j] = (float)(c / (double)N);
   }
-  if (threadIdx.x == 0) mu32[b] = (float)mu[b];
+  if (threadIdx.x == 0 && blockIdx.y == 0) mu32[b] = (float)mu[b];
 }
 
 // ------------------------------------------------------------------ k_bwd_m
 // G_ij = F_ij (V^T dVk)_ij for j < k (i != j), G_jj = dlam_j.  One CTA per
-// row i; thread = band b, the k products summed by shuffles and shared memory.
+// row i and group of 32 columns; thread = band b, the products summed by
+// shuffles and shared memory.
 __global__ void __launch_bounds__(256)
 k_bwd_m(int B, int k, const double* __restrict__ lam, const double* __restrict__ V,
         const double* __restrict__ dVk, const double* __restrict__ dlam, double gap_eps,
         double* __restrict__ Gk) {
   __shared__ double part[8][32];
   const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int jc = 32 * blockIdx.y, nj = k - jc < 32 ? k - jc : 32;
   const double v = tid < B ? V[(size_t)tid * B + i] : 0.0;
-  for (int j = 0; j < k; ++j) {
-    double m = tid < B ? v * dVk[(size_t)tid * k + j] : 0.0;
+  for (int jj = 0; jj < nj; ++jj) {
+    double m = tid < B ? v * dVk[(size_t)tid * k + jc + jj] : 0.0;
     m = warp_sum(m);
-    if (lane == 0) part[warp][j] = m;
+    if (lane == 0) part[warp][jj] = m;
   }
   __syncthreads();
-  if (tid < k) {
-    const int j = tid;
+  if (tid < nj) {
+    const int j = jc + tid;
     double m = 0.0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) m += part[w][j];
+    for (int w = 0; w < 8; ++w) m += part[w][tid];
     double gval;
     if (i == j) {
       gval = dlam ? dlam[i] : 0.0;
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(256)
 k_bwd_s(const double* __restrict__ V, const double* __restrict__ Gk, const double* __restrict__ dlam,
         int64_t N, int B, int k, double* __restrict__ dA, float* __restrict__ vk32) {
   __shared__ double T[256];
-  __shared__ double part[8][32];
+  __shared__ double part[8][256];
   const int a = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double vai = tid < B ? V[(size_t)a * B + tid] : 0.0;   // thread = i
   for (int j = 0; j < k; ++j) {
@@ -324,11 +330,11 @@ __global__ void k_bwd_sym(const double* __restrict__ dA, int64_t N, int B, float
 }
 
 template <typename In, int KQ>
-cudaError_t dv_kq(const In* cube, const float* dq, int64_t N, int B, int k, const double* mu,
-                  float* dv_part, float* dqs_part, float* xmax_part, float* dqmax_part, int parts,
-                  DevHeader* hdr, cudaStream_t st) {
+cudaError_t dv_kq(const In* cube, const float* dq, int64_t N, int B, int k, int j0, int ld,
+                  const double* mu, float* dv_part, float* dqs_part, float* xmax_part,
+                  float* dqmax_part, int parts, DevHeader* hdr, cudaStream_t st) {
   const int cube_stage = (int)((((size_t)kDvPx * B * sizeof(In)) + 127) & ~(size_t)127);
-  const int dq_stage = (int)((((size_t)kDvPx * k * 4) + 127) & ~(size_t)127);
+  const int dq_stage = ld == k ? (int)((((size_t)kDvPx * k * 4) + 127) & ~(size_t)127) : 0;
   // three stages where they fit in the 227 KB a CTA may use (all but the
   // largest FP32 shapes), else two
   auto bytes = [&](int n) {
@@ -339,23 +345,29 @@ cudaError_t dv_kq(const In* cube, const float* dq, int64_t N, int B, int k, cons
   auto kern = k_bwd_dv<In, KQ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<parts, dv_threads(KQ), smem, st>>>(cube, dq, N, B, k, mu, dv_part, dqs_part, xmax_part,
-                                        dqmax_part, cube_stage, dq_stage, nst, hdr);
+  kern<<<parts, dv_threads(KQ), smem, st>>>(cube, dq, N, B, k, j0, ld, mu, dv_part, dqs_part,
+                                            xmax_part, dqmax_part, cube_stage, dq_stage, nst, hdr);
   return cudaGetLastError();
 }
 
+// X^T dQ in passes of at most 32 columns (the accumulators live in registers)
 template <typename In>
 cudaError_t dv_typed(const In* cube, const float* dq, int64_t N, int B, int k, const double* mu,
                      const BwdPtrs& w, DevHeader* hdr, cudaStream_t st) {
-  switch ((k + 3) / 4) {
+  for (int j0 = 0; j0 < k; j0 += 32) {
+    const int kk = k - j0 < 32 ? k - j0 : 32;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch ((kk + 3) / 4) {
 #define GB_DV_CASE(q) \
-    case q: return dv_kq<In, q>(cube, dq, N, B, k, mu, w.dv_part, w.dqs_part, w.xmax_part, \
-                                w.dqmax_part, w.parts, hdr, st);
-    GB_DV_CASE(1) GB_DV_CASE(2) GB_DV_CASE(3) GB_DV_CASE(4)
-    GB_DV_CASE(5) GB_DV_CASE(6) GB_DV_CASE(7) GB_DV_CASE(8)
+      case q: e = dv_kq<In, q>(cube, dq, N, B, kk, j0, k, mu, w.dv_part, w.dqs_part, w.xmax_part, \
+                               w.dqmax_part, w.parts, hdr, st); break;
+      GB_DV_CASE(1) GB_DV_CASE(2) GB_DV_CASE(3) GB_DV_CASE(4)
+      GB_DV_CASE(5) GB_DV_CASE(6) GB_DV_CASE(7) GB_DV_CASE(8)
 #undef GB_DV_CASE
+    }
+    if (e != cudaSuccess) return e;
   }
-  return cudaErrorInvalidValue;
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -373,8 +385,10 @@ cudaError_t launch_backward(const void* cube, pca_dtype dt, int64_t N, int B, in
       return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
-  k_bwd_reduce<<<B, kRedWarps * 32, 0, st>>>(w.dv_part, w.dqs_part, w.parts, N, B, k, mu, w.dVk, w.mdq, w.mu32);
-  k_bwd_m<<<B, 256, 0, st>>>(B, k, lam, V, w.dVk, dlam, gap_eps, w.Gk);
+  const int kg = (k + 31) / 32;   // groups of 32 columns
+  k_bwd_reduce<<<dim3(B, kg), kRedWarps * 32, 0, st>>>(w.dv_part, w.dqs_part, w.parts, N, B, k,
+                                                       mu, w.dVk, w.mdq, w.mu32);
+  k_bwd_m<<<dim3(B, kg), 256, 0, st>>>(B, k, lam, V, w.dVk, dlam, gap_eps, w.Gk);
   k_bwd_s<<<B, 256, 0, st>>>(V, w.Gk, dlam, N, B, k, w.dA, w.vk32);
   k_bwd_sym<<<dim3((B + 127) / 128, B), 128, 0, st>>>(w.dA, N, B, w.S32);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -44,7 +44,7 @@ constexpr uint32_t kLBO = 128;                 // K-adjacent core matrices
 constexpr uint32_t kSBO = (kKB / 8) * 128;     // 8-row groups: 512 B
 constexpr int kAPlane = kM * kKB * 2;          // one FP16 plane of an A block: 8 KB
 constexpr int kXStage = kM * 128;              // a staged FP32 cube block: 128 rows x 128 B
-constexpr int kMaxKdim = 256 + 32;
+constexpr int kMaxKdim = 256 + 256;   // bands (rounded to 32) + dQ columns
 constexpr int kEpiWarps = 8;     // epilogue warps: two per TMEM lane quarter, each half the columns
 
 struct __align__(8) DySync {
@@ -390,11 +390,11 @@ __global__ void k_bwd_scales(const float* __restrict__ xmax_part, const float* _
 // segment, the column scaled so that its largest entry lies below 2^14;
 // written as FP16 hi and lo planes of each 32-wide K block in core-matrix
 // order.  fcol[s * B + c] = 2^-f of segment s.
-__global__ void __launch_bounds__(320)
+__global__ void __launch_bounds__(512)
 k_bwd_bop(const float* __restrict__ S32, const float* __restrict__ vk32, int B, int k,
           const float* __restrict__ ascale, unsigned char* __restrict__ bop,
           float* __restrict__ fcol) {
-  __shared__ float red[2][10];
+  __shared__ float red[2][16];
   const int c = blockIdx.x, kk = threadIdx.x, lane = kk & 31, warp = kk >> 5;
   const int R16 = (B + 15) & ~15, B32 = (B + kKB - 1) & ~(kKB - 1);
   const int K = B32 + k, KB = (K + kKB - 1) / kKB;
@@ -409,7 +409,7 @@ k_bwd_bop(const float* __restrict__ S32, const float* __restrict__ vk32, int B, 
   __syncthreads();
   float m = 0.f;
 #pragma unroll
-  for (int w = 0; w < 10; ++w) m = fmaxf(m, red[seg2 ? 1 : 0][w]);
+  for (int w = 0; w < 16; ++w) m = fmaxf(m, red[seg2 ? 1 : 0][w]);
   const float f = ldexpf(1.f, scale_exp(m));
   if ((kk == 0 || kk == B32) && c < B) fcol[(seg2 ? B : 0) + c] = 1.f / f;  // exact
   if (kk < KB * kKB) {
@@ -468,7 +468,7 @@ cudaError_t launch_bwd_dy_tc(const void* cube, pca_dtype dt, const float* dq, in
   if (((B + kKB - 1) & ~(kKB - 1)) + k > kMaxKdim) return cudaErrorInvalidValue;
   k_bwd_scales<<<((B + kKB - 1) & ~(kKB - 1)) + k, 32, 0, st>>>(xmax_part, dqmax_part, parts, B, k,
                                                                  mu32, mdq, ascale, anshift);
-  k_bwd_bop<<<(B + 15) & ~15, 320, 0, st>>>(S32, vk32, B, k, ascale, bop, fcol);
+  k_bwd_bop<<<(B + 15) & ~15, 512, 0, st>>>(S32, vk32, B, k, ascale, bop, fcol);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   switch (dt) {

@@ -14,7 +14,9 @@
 // Warps 0-7 each take one eighth of the bands for the same 64 pixels (two
 // pixels per lane), accumulate x * V_k in registers with V_k and mu read as
 // broadcasts from shared memory, and the eight partial sums are added through
-// shared memory before the chunk's k columns are stored.  Every wait is
+// shared memory before the chunk's columns are stored.  One pass handles up to
+// 32 columns; more components take one pass per group of 32 (the batched form:
+// one work item per tile, chunk range and column group).  Every wait is
 // bounded; on time-out the CTA fills the rest of its output range with NaN
 // and records PCA_ERR_TIMEOUT when a header is given.
 #include "tma.cuh"
@@ -28,6 +30,7 @@ constexpr int kParts = 8;                // compute warps (band parts)
 constexpr int kCompute = kParts * 32;
 constexpr int kThreadsP = kCompute + 32;
 constexpr int kMaxStages = 8;
+constexpr int kColGroup = 32;            // columns of V_k per pass (registers per thread)
 
 struct __align__(8) ProjSync {
   uint64_t full[kMaxStages];
@@ -88,6 +91,8 @@ __device__ __forceinline__ void fma_band(float x0, float x1, const float4* __res
   }
 }
 
+// One pass projects columns [j0, j0 + k) of V_k (k <= 32): vk and proj point at
+// column j0 of their matrices, whose rows are vk_ld and q_ld floats apart.
 struct ProjArgs {
   const void* cube;
   int64_t N;
@@ -96,6 +101,7 @@ struct ProjArgs {
   const float* vk;
   float* proj;
   DevHeader* hdr;
+  int vk_ld, q_ld;
 };
 
 // One work item: chunks [c0, c1) of one cube and its tensor map.
@@ -121,14 +127,17 @@ __device__ __forceinline__ PItem proj_item(const ProjArgs& one, const CUtensorMa
   } else {
     const ProjItem pi = items[cta_items[blockIdx.x] + i];
     const TileDesc& d = T[pi.tile];
+    const int j0 = kColGroup * pi.pad;     // this item's column group
     it.a.cube = d.cube;
     it.a.N = d.N;
     it.a.B = d.B;
-    it.a.k = d.k;
+    it.a.k = d.k - j0 < kColGroup ? d.k - j0 : kColGroup;
     it.a.mu_f = d.muf;
-    it.a.vk = d.vk;
-    it.a.proj = d.proj;
+    it.a.vk = d.vk + j0;
+    it.a.proj = d.proj + j0;
     it.a.hdr = d.hdr;
+    it.a.vk_ld = d.k;
+    it.a.q_ld = d.k;
     it.map = maps != nullptr ? maps + pi.tile : nullptr;
     it.c0 = pi.c0;
     it.c1 = pi.c1;
@@ -216,7 +225,7 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
   if (i > 0) named_sync();   // every warp is done with the previous item's V_k
   for (int e = tid; e < B8 * KQ * 4; e += kCompute) {
     const int b = e / (KQ * 4), j = e - b * (KQ * 4);
-    reinterpret_cast<float*>(vs)[e] = (b < B && j < k) ? a.vk[(size_t)b * k + j] : 0.f;
+    reinterpret_cast<float*>(vs)[e] = (b < B && j < k) ? a.vk[(size_t)b * a.vk_ld + j] : 0.f;
   }
   for (int b = tid; b < B8; b += kCompute) mus[b] = b < B ? a.mu_f[b] : 0.f;
   named_sync();
@@ -320,12 +329,13 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
       }
     }
     named_sync();
-    float* out = a.proj + p0 * k;
+    float* out = a.proj + p0 * a.q_ld;
     for (int o = tid; o < cp * k; o += kCompute) {
       float sum = 0.f;
 #pragma unroll
       for (int hh = 0; hh < kParts; ++hh) sum += red[(size_t)hh * kPc * k + o];
-      out[o] = sum;
+      const int row = o / k;
+      out[(size_t)row * a.q_ld + (o - row * k)] = sum;
     }
     named_sync();
   }
@@ -335,9 +345,11 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
     for (int j = i; j < nitems; ++j) {
       const PItem rest = proj_item(one, &tmap, T, maps, items, cta_items, j);
       const int64_t c0 = j == i ? c : rest.c0;
-      const int64_t o0 = c0 * kPc * rest.a.k;
-      const int64_t o1 = (rest.c1 * kPc < rest.a.N ? rest.c1 * kPc : rest.a.N) * rest.a.k;
-      for (int64_t o = o0 + tid; o < o1; o += kCompute) rest.a.proj[o] = __int_as_float(0x7fc00000);
+      const int64_t kk = rest.a.k;
+      const int64_t o0 = c0 * kPc * kk;
+      const int64_t o1 = (rest.c1 * kPc < rest.a.N ? rest.c1 * kPc : rest.a.N) * kk;
+      for (int64_t o = o0 + tid; o < o1; o += kCompute)
+        rest.a.proj[(o / kk) * rest.a.q_ld + o % kk] = __int_as_float(0x7fc00000);
       if (tid == 0 && rest.a.hdr) set_status(rest.a.hdr, PCA_ERR_TIMEOUT);
     }
   }
@@ -433,8 +445,15 @@ cudaError_t project_typed(const In* cube, int64_t N, int B, int k, const float* 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t nch = (N + kPc - 1) / kPc;
   const int grid = (int)(nch < sms ? nch : sms);
-  const ProjArgs one{cube, N, B, k, mu_f, vk, proj, hdr};
-  return project_any<In>(tiled, tmap, one, nullptr, nullptr, nullptr, nullptr, grid, B, k, st);
+  // one pass per group of at most kColGroup columns
+  for (int j0 = 0; j0 < k; j0 += kColGroup) {
+    const int kk = k - j0 < kColGroup ? k - j0 : kColGroup;
+    const ProjArgs one{cube, N, B, kk, mu_f, vk + j0, proj + j0, hdr, k, k};
+    const cudaError_t e =
+        project_any<In>(tiled, tmap, one, nullptr, nullptr, nullptr, nullptr, grid, B, kk, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -457,6 +476,7 @@ cudaError_t launch_project_grouped(const TileDesc* T, const void* maps, const Pr
   memset(&none, 0, sizeof(none));
   const ProjArgs one{};
   const CUtensorMap* m = static_cast<const CUtensorMap*>(maps);
+  if (maxk > kColGroup) maxk = kColGroup;   // items carry one column group each
   switch (dt) {
     case PCA_F32:
       return project_any<float>(m != nullptr, none, one, T, m, items, cta_items, ctas, maxB, maxk, st);

@@ -10,9 +10,9 @@
 // keeps those intermediates in a fixed array in device memory that belongs
 // to this library instead, so it neither allocates nor needs a workspace.
 //
-// The array holds kNoAllocFloats floats (B + B*k <= 256 + 256*32 = 8,448
-// floats, 33,792 bytes) and stays allocated on every GPU that loads the
-// library until the process exits.  All calls share it, and each call
+// The array holds kNoAllocFloats = 8,448 floats (33,792 bytes: B + B*k for
+// 256 bands and 32 components, or fewer bands with more components) and stays
+// allocated on every GPU that loads the library until the process exits.  All calls share it, and each call
 // rewrites every entry it reads before reading it, so nothing has to start
 // at zero -- but two calls whose work overlaps on the GPU (different streams,
 // or different host threads) race on it and must be serialised by the caller.
@@ -23,7 +23,7 @@
 namespace gbpca {
 namespace {
 
-constexpr int kNoAllocFloats = kMaxB + kMaxB * kMaxK;
+constexpr int kNoAllocFloats = 256 + 256 * 32;
 constexpr int kMaxDevices = 64;
 
 // File-scope device array.  In host code its name is only a host-side handle
@@ -61,7 +61,7 @@ extern "C" int pca_project_noalloc(const void* cube, pca_dtype dtype, int64_t N,
                                    void* stream) {
   if (!cube || !mu || !eigvecs || !proj) return PCA_ERR_ARG;
   if (dtype != PCA_F32 && dtype != PCA_BF16 && dtype != PCA_F16) return PCA_ERR_ARG;
-  if (N < 1 || B < 2 || B > kMaxB || k < 1 || k > B || k > kMaxK) return PCA_ERR_ARG;
+  if (N < 1 || B < 2 || B > kMaxB || k < 1 || k > B) return PCA_ERR_ARG;
   if (((uintptr_t)cube) % 16 != 0) return PCA_ERR_ARG;
   if ((int64_t)B + (int64_t)B * k > kNoAllocFloats) return PCA_ERR_ARG;  // beyond the array
   float* scratch = nullptr;

@@ -72,3 +72,16 @@ def test_batch_workspace_size_is_host_only_and_checks_every_tile():
     assert lib.pca_batch_workspace_size(2, tiles([(4096, 64, 8), (1, 8, 3)]), 0, 1) == 0
     assert lib.pca_batch_workspace_size(2, tiles([(4096, 64, 8), (100, 8, 9)]), 0, 1) == 0
     assert lib.pca_batch_workspace_size(0, tiles(ok), 0, 1) == 0
+
+
+def test_workspace_sizes_accept_every_k_up_to_B():
+    """1 <= k <= B (Algorithm 1 stages 5-6 project onto any number of
+    components); sizes are computed on the host."""
+    import paper_2403_18321_gb300 as g
+    lib = g.load(build_if_missing=True)
+    for prec in (0, 1, 2):
+        for B, k in ((256, 256), (224, 33), (103, 103), (2, 2)):
+            assert lib.pca_workspace_size(1000, B, k, 0, prec) > 0, (B, k, prec)
+        assert lib.pca_workspace_size(1000, 64, 65, 0, prec) == 0
+    assert lib.pca_backward_workspace_size(1000, 256, 256) > 0
+    assert lib.pca_backward_workspace_size(1000, 256, 257) == 0

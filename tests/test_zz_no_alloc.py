@@ -55,3 +55,10 @@ def test_noalloc_projection_rejects_bad_sizes(gbpca_lib):
     with pytest.raises(g.PCAError) as e:
         g.project_noalloc(Y, mu, V, 9)       # k > B
     assert e.value.status == 1
+    # within the ABI (k <= B) but beyond the library's fixed array: B + B k > 8448
+    Y = torch.zeros(64, 256, device="cuda")
+    mu = torch.zeros(256, dtype=torch.float64, device="cuda")
+    V = torch.eye(256, dtype=torch.float64, device="cuda")
+    with pytest.raises(g.PCAError) as e:
+        g.project_noalloc(Y, mu, V, 33)
+    assert e.value.status == 1
