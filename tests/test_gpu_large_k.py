@@ -4,9 +4,9 @@ and the adjoint, at k = 33, 64, 128 and k = B, up to B = k = 256.
 Where the eigen-pairs are individually defined the comparison rules of
 parity.compare apply; every column of the projection (including those in
 the noise cluster, whose vectors are not individually pinned) is checked
-against the FP64 projection of the cube onto the GPU's own eigenvectors
-(the projection stage's own arithmetic, 1e-5 of the column's scale), and
-the adjoint against the oracle adjoint (2e-5 of max |dY|)."""
+against the FP64 projection of the cube onto the GPU's own eigenvectors,
+within the rounding-error bound of an FP32 dot product, and the adjoint
+against the oracle adjoint (2e-5 of max |dY|)."""
 import numpy as np
 import pytest
 import torch
@@ -20,10 +20,21 @@ CASES = [(40, 41, 64, 33), (30, 33, 96, 64), (25, 27, 160, 128), (21, 23, 96, 96
 
 
 def _projection_stage_err(Y, mu, V, Q, k):
-    """max over columns of |Q_j - (Y - mu) V_j| / max |(Y - mu) V_j|, FP64."""
+    """|Q - (Y - mu) V_k| against the rounding-error bound of an FP32 dot
+    product of B terms computed from FP32 copies of mu and V (Higham's
+    gamma_n = n u / (1 - n u), n = B + 3 roundings per term path, u = 2^-24):
+        |Q_nj - R_nj| <= gamma_{B+3} sum_b (|x_nb| + |mu_b|) |v_bj|,
+    which holds whatever the summation order and however much the terms
+    cancel (the noise-floor columns).  Returns the largest ratio of the error
+    to its bound (<= 1 passes)."""
+    B = Y.shape[1]
     X = Y.astype(np.float64) - mu[None, :]
-    R = X @ V[:, :k]
-    return float(np.max(np.abs(Q - R).max(axis=0) / np.maximum(np.abs(R).max(axis=0), 1e-300)))
+    Vk = V[:, :k]
+    R = X @ Vk
+    S = (np.abs(X) + np.abs(mu)[None, :]) @ np.abs(Vk)
+    u = 2.0 ** -24
+    gamma = (B + 3) * u / (1 - (B + 3) * u)
+    return float(np.max(np.abs(Q - R) / np.maximum(gamma * S, 1e-300)))
 
 
 @pytest.mark.gpu
@@ -42,7 +53,7 @@ def test_fit_with_many_components(gbpca_lib, form, rows, cols, B, k):
     kc = min(k, 8) if form == "p64" else k
     compare((host[0], host[1], host[2], host[3][:, :kc]), ref, kc, form)
     err = _projection_stage_err(c.Y, host[0], host[2], host[3], k)
-    assert err <= 1e-5, err
+    assert err <= 1.0, err
 
 
 @pytest.mark.gpu
@@ -59,7 +70,7 @@ def test_batched_with_many_components(gbpca_lib, form):
         host = [t.cpu().numpy().astype(np.float64) for t in (mu, ev, V, Q)]
         compare((host[0], host[1], host[2], host[3]), ref, c.k, form)
         err = _projection_stage_err(c.Y, host[0], host[2], host[3], c.k)
-        assert err <= 1e-5, (c.name, err)
+        assert err <= 1.0, (c.name, err)
 
 
 @pytest.mark.gpu
