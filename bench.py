@@ -1072,7 +1072,7 @@ def main(argv=None):
     if not args.no_batched and rank == 0:
         batched = run_batched(args, dev, peaks, peak_src)
 
-    launches = g.kernel_launches(args.precision, True) * args.steps
+    launches = g.kernel_launches(args.precision, c2["k"]) * args.steps
     forms = c2["forms"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_head / args.steps * 1e3,

@@ -71,11 +71,15 @@ typedef enum { PCA_F32 = 0, PCA_BF16 = 1, PCA_F16 = 2 } pca_dtype;
  *     by a power of two (three products, FP32 accumulation in tensor
  *     memory), FP32 Jacobi stopped on the Frobenius test at
  *     max(tol, 1e-5), one refinement iteration and two orthogonalisation
- *     steps in double-float/FP64.  The
- *     split keeps 22 bits of every value; the remaining covariance error
- *     comes from the tensor cores' FP32 accumulation.  A value that leaves
- *     the scaled FP16 range makes the covariance be recomputed in FP32 on
- *     the SIMT cores (pca_info.cov_fallback).
+ *     steps in double-float/FP64, and the projection on the tensor cores
+ *     (the centred cube split the same way, V_k split into FP16 hi + lo,
+ *     FP32 accumulation).  The split keeps 22 bits of every value; the
+ *     remaining covariance error comes from the tensor cores' FP32
+ *     accumulation, and vanishes for BF16/FP16 cubes, whose shifted values
+ *     fit one FP16 and whose products and sums are then exact.  A value that
+ *     leaves the scaled FP16 range makes the covariance (or the projection)
+ *     be recomputed in FP32 on the SIMT cores (pca_info.cov_fallback,
+ *     proj_fallback).
  */
 typedef enum { PCA_PREC_P64 = 0, PCA_PREC_P32 = 1, PCA_PREC_MIX = 2 } pca_precision;
 
@@ -89,6 +93,7 @@ typedef struct {
   double refine_res; /* largest |E_ij| of the last refinement correction (0 if none) */
   int cov_fallback;  /* MIX only: 1 if a scaled value left the FP16 range and the
                         covariance was recomputed in FP32 on the SIMT cores     */
+  int proj_fallback; /* MIX only: the same for the tensor-core projection       */
 } pca_info;
 
 /*
@@ -371,8 +376,9 @@ int pca_version(void);
 
 /* ---- instrumentation (no counterpart in the paper; used by the benchmark) */
 
-/* Number of kernels one pca_fit enqueues for this precision form. */
-int pca_kernel_launches(pca_precision prec, int with_projection);
+/* Number of kernels one pca_fit enqueues for this precision form when it
+ * projects onto k components (k = 0: no projection). */
+int pca_kernel_launches(pca_precision prec, int k);
 
 /* Number of kernels one pca_batch_run of this plan enqueues. */
 int pca_batch_kernel_launches(const pca_batch *plan);

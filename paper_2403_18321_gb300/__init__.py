@@ -49,7 +49,8 @@ class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("sweeps", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("steps", ctypes.c_int),
                 ("off_rel", ctypes.c_double), ("tol_used", ctypes.c_double),
-                ("refine_res", ctypes.c_double), ("cov_fallback", ctypes.c_int)]
+                ("refine_res", ctypes.c_double), ("cov_fallback", ctypes.c_int),
+                ("proj_fallback", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -379,8 +380,9 @@ def project_noalloc(cube, mu, eigvecs, k: int, stream=None):
     return Q
 
 
-def kernel_launches(precision="mix", project: bool = True) -> int:
-    return int(load().pca_kernel_launches(_prec_code(precision), 1 if project else 0))
+def kernel_launches(precision="mix", k: int = 1) -> int:
+    """Kernels one fit enqueues when it projects onto k components (0: none)."""
+    return int(load().pca_kernel_launches(_prec_code(precision), int(k)))
 
 
 def jacobi_sms(B: int) -> int:

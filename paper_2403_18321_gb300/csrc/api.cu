@@ -124,6 +124,11 @@ Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, in
   L.e = take(BB8);
   L.vk = take(sizeof(float) * (size_t)B * k);
   L.muf = take(sizeof(float) * B);
+  L.ptc_shift = take(sizeof(float) * 256);
+  L.ptc_escale = take(sizeof(int) * 256);
+  L.ptc_planes = take(project_tc_planes_bytes(B, k));
+  L.ptc_colscale = take(sizeof(float) * 128);
+  L.ptc_corr = take(sizeof(float) * 128);
   L.total = o;
   return L;
 }
@@ -201,6 +206,7 @@ int pca_read_info(const void* workspace, void* stream, pca_info* info) {
   info->tol_used = h.tol_used;
   info->refine_res = h.refine_res;
   info->cov_fallback = h.cov_range != 0 ? 1 : 0;
+  info->proj_fallback = h.proj_range != 0 ? 1 : 0;
   return info->status;
 }
 
@@ -230,6 +236,11 @@ struct Ptrs {
   float2* e;
   float* vk;
   float* muf;
+  float* ptc_shift;
+  int* ptc_escale;
+  unsigned char* ptc_planes;
+  float* ptc_colscale;
+  float* ptc_corr;
 };
 
 Ptrs carve(void* workspace, const Layout& L) {
@@ -255,6 +266,11 @@ Ptrs carve(void* workspace, const Layout& L) {
   p.e = reinterpret_cast<float2*>(ws + L.e);
   p.vk = reinterpret_cast<float*>(ws + L.vk);
   p.muf = reinterpret_cast<float*>(ws + L.muf);
+  p.ptc_shift = reinterpret_cast<float*>(ws + L.ptc_shift);
+  p.ptc_escale = reinterpret_cast<int*>(ws + L.ptc_escale);
+  p.ptc_planes = reinterpret_cast<unsigned char*>(ws + L.ptc_planes);
+  p.ptc_colscale = reinterpret_cast<float*>(ws + L.ptc_colscale);
+  p.ptc_corr = reinterpret_cast<float*>(ws + L.ptc_corr);
   return p;
 }
 
@@ -333,9 +349,16 @@ int pca_fit(const void* cube, pca_dtype dt, int64_t N, int B, int k, double tol,
   GB_CK(cudaGetLastError());
   GB_CK(run_cov(cube, dt, N, B, prec, L, P, mu, st, pm));
   GB_CK(run_eigh(P.C, B, tol32, sweeps_max, prec, k, P, eigvals, eigvecs, st, pm));
-  // stages 5-6: projection onto the first k eigenvectors
+  // stages 5-6: projection onto the first k eigenvectors (MIX: tensor cores, with
+  // the FP32 SIMT form as the guarded fallback for values outside their range)
   pm.mark(7);
-  if (proj) GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st, P.hdr));
+  if (proj && prec == PCA_PREC_MIX) {
+    GB_CK(launch_project_tc(cube, dt, N, B, k, mu, eigvecs, proj, P.ptc_shift, P.ptc_escale,
+                            P.ptc_planes, P.ptc_colscale, P.ptc_corr, P.hdr, st));
+    GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st, P.hdr, &P.hdr->proj_range));
+  } else if (proj) {
+    GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st, P.hdr));
+  }
   pm.mark(8);
   if (info) return pca_read_info(workspace, stream, info);
   return PCA_OK;
@@ -452,15 +475,22 @@ int pca_backward(const void* cube, pca_dtype dt, int64_t N, int B, int k, const 
 
 int pca_version(void) { return 100; }
 
-int pca_kernel_launches(pca_precision prec, int with_projection) {
+int pca_kernel_launches(pca_precision prec, int k) {
   // header init, covariance (MIX: tensor-core pass + guarded SIMT
   // re-computation), band-sum reduce, covariance finalise, Jacobi (with
   // V), compact, 6 per refinement iteration (four products, the eigenvalue
   // and the angle kernels), 1 conversion, 3 per orthogonalisation step,
-  // rank/sign + scatter, projection
+  // rank/sign + scatter, projection: one SIMT pass per 32 columns (MIX: band
+  // constants, then operand preparation + tensor-core pass per 128 columns,
+  // and the guarded SIMT passes)
   const int it = refine_iterations(prec);
   const int cov = prec == PCA_PREC_MIX ? 2 : 1;
-  return 5 + cov + 6 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + (with_projection ? 1 : 0);
+  int proj = 0;
+  if (k > 0) {
+    proj = (k + 31) / 32;
+    if (prec == PCA_PREC_MIX) proj += 1 + 2 * ((k + 127) / 128);
+  }
+  return 4 + cov + 6 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + proj;
 }
 
 int pca_jacobi_sms(int B) {

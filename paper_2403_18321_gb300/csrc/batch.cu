@@ -503,6 +503,7 @@ int pca_batch_read_info(pca_batch* b, void* stream, pca_info* infos) {
     o.tol_used = h[i].tol_used;
     o.refine_res = h[i].refine_res;
     o.cov_fallback = h[i].cov_range != 0 ? 1 : 0;
+    o.proj_fallback = h[i].proj_range != 0 ? 1 : 0;
   }
   return worst;
 }

@@ -24,7 +24,7 @@ struct DevHeader {
   int nonfinite;
   int dummy_slot;    // slot of the padding index when B is odd, else -1
   int cov_range;     // tensor-core covariance met a value outside its scaled FP16 range
-  int pad1;
+  int proj_range;    // tensor-core projection met a value outside its scaled FP16 range
   double off_rel;
   double fro;
   double tol_used;
@@ -35,6 +35,7 @@ struct DevHeader {
 // Offsets (bytes) of every workspace region; all 256-byte aligned.
 struct Layout {
   size_t hdr, shift, escale, s1_part, s2_part, dvec, cov, cdf, rank, sgn, diag32, v32, lam, vc, w, s, r, e, vk, muf;
+  size_t ptc_shift, ptc_escale, ptc_planes, ptc_colscale, ptc_corr;   // tensor-core projection
   size_t total;
   int partials;      // number of covariance partial slots the SYRK uses
   int tc_ctas;       // MIX: CTAs of the tensor-core pass (partials spread over them)
@@ -221,9 +222,21 @@ cudaError_t launch_narrow_inputs(const double* mu, const double* eigvecs, int B,
 
 // Q = (Y - 1 mu^T) V_k, FP32 (TMA-streamed).  hdr (nullable) receives
 // PCA_ERR_TIMEOUT if a bounded wait gives up (the output range is then NaN).
+// With guard != nullptr every CTA returns at once unless *guard != 0.
 cudaError_t launch_project(const void* cube, pca_dtype dt, int64_t N, int B, int k,
                            const float* mu_f, const float* vk, float* proj, cudaStream_t st,
-                           DevHeader* hdr = nullptr);
+                           DevHeader* hdr = nullptr, const int* guard = nullptr);
+
+// Q = (Y - 1 mu^T) V_k on the tensor cores from mu [B] and V [B][B] (FP64,
+// device; the first k columns of V), FP32 accumulation; workspace: shift [256]
+// (FP32), escale [256] (int), planes of project_tc_planes_bytes(B, k) bytes,
+// colscale [128], corr [128] (FP32).  A scaled value outside the FP16 range
+// sets hdr->proj_range (the caller then recomputes Q on the SIMT path).
+size_t project_tc_planes_bytes(int B, int k);
+cudaError_t launch_project_tc(const void* cube, pca_dtype dt, int64_t N, int B, int k,
+                              const double* mu, const double* V, float* proj, float* shift,
+                              int* escale, unsigned char* planes, float* colscale, float* corr,
+                              DevHeader* hdr, cudaStream_t st);
 
 // Scratch of the backward pass (all device pointers, inside the caller's
 // workspace): parts per-CTA partials of X^T dQ [parts][B][k] and of the column

@@ -102,6 +102,7 @@ struct ProjArgs {
   float* proj;
   DevHeader* hdr;
   int vk_ld, q_ld;
+  const int* guard;    // single cube: run only when *guard != 0 (nullable)
 };
 
 // One work item: chunks [c0, c1) of one cube and its tensor map.
@@ -167,6 +168,7 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nitems = T == nullptr ? 1 : cta_items[blockIdx.x + 1] - cta_items[blockIdx.x];
+  if (T == nullptr && one.guard != nullptr && *(volatile const int*)one.guard == 0) return;
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&sy->full[s], 1); mbar_init(&sy->empty[s], kParts); }
@@ -437,7 +439,8 @@ cudaError_t project_any(bool tiled, const CUtensorMap& tmap, const ProjArgs& one
 
 template <typename In>
 cudaError_t project_typed(const In* cube, int64_t N, int B, int k, const float* mu_f,
-                          const float* vk, float* proj, DevHeader* hdr, cudaStream_t st) {
+                          const float* vk, float* proj, DevHeader* hdr, const int* guard,
+                          cudaStream_t st) {
   CUtensorMap tmap;
   const bool tiled = encode_map<In>(cube, N, B, &tmap);
   int dev = 0, sms = 148;
@@ -448,7 +451,7 @@ cudaError_t project_typed(const In* cube, int64_t N, int B, int k, const float* 
   // one pass per group of at most kColGroup columns
   for (int j0 = 0; j0 < k; j0 += kColGroup) {
     const int kk = k - j0 < kColGroup ? k - j0 : kColGroup;
-    const ProjArgs one{cube, N, B, kk, mu_f, vk + j0, proj + j0, hdr, k, k};
+    const ProjArgs one{cube, N, B, kk, mu_f, vk + j0, proj + j0, hdr, k, k, guard};
     const cudaError_t e =
         project_any<In>(tiled, tmap, one, nullptr, nullptr, nullptr, nullptr, grid, B, kk, st);
     if (e != cudaSuccess) return e;
@@ -492,15 +495,15 @@ cudaError_t launch_project_grouped(const TileDesc* T, const void* maps, const Pr
 
 cudaError_t launch_project(const void* cube, pca_dtype dt, int64_t N, int B, int k,
                            const float* mu_f, const float* vk, float* proj, cudaStream_t st,
-                           DevHeader* hdr) {
+                           DevHeader* hdr, const int* guard) {
   if (N < 1) return cudaSuccess;
   switch (dt) {
     case PCA_F32:
-      return project_typed((const float*)cube, N, B, k, mu_f, vk, proj, hdr, st);
+      return project_typed((const float*)cube, N, B, k, mu_f, vk, proj, hdr, guard, st);
     case PCA_BF16:
-      return project_typed((const __nv_bfloat16*)cube, N, B, k, mu_f, vk, proj, hdr, st);
+      return project_typed((const __nv_bfloat16*)cube, N, B, k, mu_f, vk, proj, hdr, guard, st);
     case PCA_F16:
-      return project_typed((const __half*)cube, N, B, k, mu_f, vk, proj, hdr, st);
+      return project_typed((const __half*)cube, N, B, k, mu_f, vk, proj, hdr, guard, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -1,0 +1,501 @@
+// k_project_tc.cu -- the projection Q = (Y - 1 mu^T) V_k (Algorithm 1 stages
+// 5-6) on the 5th-generation tensor cores, for the mixed-precision form.
+//
+// Q is a skinny GEMM: M = pixels (128 per tile), K = bands, N = components.
+// The cube is pixel-major, so a pixel's bands are the K-contiguous rows of the
+// A operand: the converters read 16 consecutive bands of a pixel with vector
+// loads and write them, shifted, scaled and split into FP16 hi + lo, as rows of
+// K-major core matrices -- no transpose.  V_k is the B operand (K-major, a
+// component's bands contiguous), prepared once per fit by two small kernels:
+//   k_ptc_bands  per band a shift s_b (the band mean rounded to the input's
+//                type, so that y - s_b is exact for 16-bit cubes) and a
+//                power-of-two scale 2^e_b (the deviations of 32 sampled
+//                pixels scaled into (2^5, 2^6], as in the covariance);
+//   k_ptc_vop    per column j the entries v_bj 2^-e_b scaled by 2^f_j into
+//                [2^13, 2^14), split into FP16 hi + lo planes in core-matrix
+//                order, and the centring correction c_j = sum_b (mu_b - s_b)
+//                v_bj (FP64), so that Q_nj = 2^-f_j sum_b x_nb w_bj - c_j with
+//                x_nb = (y_nb - s_b) 2^e_b.
+// Products hi hi + hi lo + lo hi (the third only when a chunk has a non-zero
+// lo part: never for 16-bit cubes within 2^11 grid steps of the shift), FP32
+// accumulation in TMEM, one accumulator per 64-band chunk (up to four, so
+// that no accumulator sums more than 12 products), double-buffered by tile.
+// One persistent CTA per SM walks its 128-pixel tiles:
+//   warps 2-17   converters: per 64-band chunk each thread takes one pixel and
+//                16 bands (the next chunk's loads in flight while it converts);
+//   warp 1       MMA issuer (one thread) and TMEM owner;
+//   warps 18-21  epilogue: TMEM -> registers (the chunk accumulators added in
+//                FP32) -> column scale and correction -> Q rows.
+// At most 128 columns per launch; more components take a second launch.  A
+// scaled value outside the FP16 range sets hdr->proj_range and the caller's
+// guarded SIMT projection recomputes Q.  Every wait is bounded (one second);
+// on time-out the CTA records PCA_ERR_TIMEOUT, drains its MMAs and frees TMEM.
+#include "tc.cuh"
+
+namespace gbpca {
+
+namespace {
+
+constexpr int kTM = 128;                 // pixels per tile (MMA M)
+constexpr int kKC = 64;                  // bands per K-chunk (one operand stage)
+constexpr int kMaxSt = 4;                // operand ring depth (as shared memory allows)
+constexpr int kConvW = 16;               // converter warps
+constexpr int kEpiW = 4;                 // epilogue warps (one per TMEM lane quarter)
+constexpr int kThr = (2 + kConvW + kEpiW) * 32;
+constexpr int kPlane = kTM * kKC * 2;    // one FP16 plane of an A stage: 16 KB
+constexpr uint32_t kLBO = 128;           // K-adjacent core matrices
+constexpr uint32_t kASBO = (kKC / 8) * 128;   // A: 8-row groups, 1 KB
+constexpr int kMaxCols = 128;            // columns of one launch
+constexpr int kProbe = 32;
+
+struct __align__(8) PtcSync {
+  uint64_t opfull[kMaxSt];
+  uint64_t opempty[kMaxSt];
+  uint64_t tdone[2];   // the MMAs of a tile finished (per TMEM buffer)
+  uint64_t tfree[2];   // the epilogue has read a TMEM buffer
+  uint64_t drain;
+  int lo_nz[kMaxSt][kConvW];
+  uint32_t tmem_base;
+  int abort;
+};
+
+template <typename In>
+__device__ __forceinline__ float on_grid(float m);
+template <>
+__device__ __forceinline__ float on_grid<float>(float m) { return m; }
+template <>
+__device__ __forceinline__ float on_grid<__nv_bfloat16>(float m) {
+  return __bfloat162float(__float2bfloat16_rn(m));
+}
+template <>
+__device__ __forceinline__ float on_grid<__half>(float m) {
+  return fabsf(m) <= 65504.f ? __half2float(__float2half_rn(m)) : m;
+}
+
+// ------------------------------------------------------------------ k_ptc_bands
+// Band shifts and scales (one CTA, thread = band): s_b = mu_b on the input's
+// grid; e_b from the largest |y - s_b| over 32 pixels spread through the cube.
+template <typename In>
+__global__ void __launch_bounds__(256)
+k_ptc_bands(const In* __restrict__ cube, int64_t N, int B, const double* __restrict__ mu,
+            float* __restrict__ shift, int* __restrict__ escale) {
+  const int b = threadIdx.x;
+  if (b >= B) return;
+  const float s = on_grid<In>((float)mu[b]);
+  const int Sp = (int)(N < kProbe ? N : kProbe);
+  float dev = 0.f;
+  for (int i = 0; i < Sp; ++i) {
+    const float y = to_f32<In>(cube[((int64_t)i * N / Sp) * B + b]);
+    dev = fmaxf(dev, fabsf(y - s));
+  }
+  if (!(dev > 0.f) || !isfinite(dev)) dev = fabsf(s);
+  int e = 0;
+  if (dev > 0.f && isfinite(dev)) {
+    int E;
+    frexpf(dev, &E);        // dev < 2^E
+    e = 6 - E;
+    e = e < -120 ? -120 : (e > 120 ? 120 : e);
+  }
+  shift[b] = s;
+  escale[b] = e;
+}
+
+// ------------------------------------------------------------------ k_ptc_vop
+// The B operand of one launch, one CTA per column j < N16 (thread = band):
+// hi and lo FP16 planes [N16][B16] in K-major core-matrix order (8 columns x
+// 8 bands per core matrix; bands in 128-byte steps, 8-column groups in
+// (B16/8)*128-byte steps), the column scale 2^-f_j and the correction c_j.
+__global__ void __launch_bounds__(256)
+k_ptc_vop(const double* __restrict__ V, int B, int j0, int k, const double* __restrict__ mu,
+          const float* __restrict__ shift, const int* __restrict__ escale,
+          unsigned char* __restrict__ planes, float* __restrict__ colscale,
+          float* __restrict__ corr) {
+  __shared__ float wmax[8];
+  __shared__ double csum[8];
+  const int j = blockIdx.x, b = threadIdx.x, lane = b & 31, warp = b >> 5;
+  const int B16 = (B + 15) & ~15, N16 = gridDim.x;
+  const bool live = b < B && j < k;
+  const double v = live ? V[(size_t)b * B + j0 + j] : 0.0;
+  const float w = live ? ldexpf((float)v, -escale[b]) : 0.f;
+  const double c = live ? (mu[b] - (double)shift[b]) * v : 0.0;
+  float m = warp_max(fabsf(w));
+  const double cs = warp_sum(c);
+  if (lane == 0) { wmax[warp] = m; csum[warp] = cs; }
+  __syncthreads();
+  m = 0.f;
+  double ct = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { m = fmaxf(m, wmax[i]); ct += csum[i]; }
+  int f = 0;
+  if (m > 0.f && isfinite(m)) {
+    int E;
+    frexpf(m, &E);
+    f = 14 - E;
+    f = f < -100 ? -100 : (f > 100 ? 100 : f);
+  }
+  if (b == 0) {
+    colscale[j] = ldexpf(1.f, -f);
+    corr[j] = (float)ct;
+  }
+  if (b < B16) {
+    const float x = ldexpf(w, f);
+    const __half hi = __float2half_rn(x);
+    const __half lo = __float2half_rn(x - __half2float(hi));
+    const size_t plane = (size_t)N16 * B16 * 2;
+    const size_t off = (size_t)(j >> 3) * (B16 / 8) * 128 + (size_t)(b >> 3) * 128 +
+                       (size_t)(j & 7) * 16 + (size_t)(b & 7) * 2;
+    *reinterpret_cast<__half*>(planes + off) = hi;
+    *reinterpret_cast<__half*>(planes + plane + off) = lo;
+  }
+}
+
+// Sixteen raw values (bands b0 .. b0+15 of pixel n; 0 outside the cube).
+template <typename In>
+__device__ __forceinline__ void load16(const In* __restrict__ cube, int64_t n, int64_t N, int B,
+                                       int b0, bool vec, float* r) {
+  if (n < N && vec && b0 + 16 <= B) {
+    const In* src = cube + n * B + b0;
+    if constexpr (sizeof(In) == 4) {
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 a = __ldg(s4 + i);
+        r[4 * i] = a.x; r[4 * i + 1] = a.y; r[4 * i + 2] = a.z; r[4 * i + 3] = a.w;
+      }
+    } else {
+      const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const uint4 u = __ldg(s4 + i);
+        const In* h = reinterpret_cast<const In*>(&u);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r[8 * i + e] = to_f32<In>(h[e]);
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int e = 0; e < 16; ++e) r[e] = (n < N && b0 + e < B) ? to_f32<In>(cube[n * B + b0 + e]) : 0.f;
+}
+
+struct PtcArgs {
+  const void* cube;
+  int64_t N;
+  int B;
+  int k;               // columns of this launch
+  int N16;             // k rounded up to 16
+  int q_ld;            // floats between rows of proj
+  float* proj;         // column 0 of this launch
+  const float* shift;
+  const int* escale;
+  const unsigned char* planes;
+  const float* colscale;
+  const float* corr;
+  DevHeader* hdr;
+};
+
+template <typename In>
+__global__ void __launch_bounds__(kThr, 1)
+k_project_tc(const __grid_constant__ PtcArgs a, int S, int nacc) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
+  const int B = a.B, N16 = a.N16;
+  const int B16 = (B + 15) & ~15;
+  const int KC = (B16 + kKC - 1) / kKC;                    // K-chunks per tile
+  const int vplane = N16 * B16 * 2;                        // one FP16 plane of V
+  unsigned char* vs = smem;                                // [hi|lo][vplane]
+  unsigned char* ops = vs + 2 * ((vplane + 1023) & ~1023); // [S][hi|lo][kPlane]
+  float* shs = reinterpret_cast<float*>(ops + (size_t)S * 2 * kPlane);   // [256] shift
+  float* scs = shs + 256;                                                 // [256] 2^e
+  float* cls = scs + 256;                                                 // [128] 2^-f
+  float* crs = cls + kMaxCols;                                            // [128] c_j
+  PtcSync* sy = reinterpret_cast<PtcSync*>(crs + kMaxCols);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const In* cube = static_cast<const In*>(a.cube);
+  const int64_t N = a.N;
+  const int64_t ntiles = (N + kTM - 1) / kTM;
+  const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int nt = (int)(t1 - t0);
+
+  // ---- set-up: V planes, band and column constants, barriers, TMEM
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.planes);
+    const int n16 = vplane / 16;
+    for (int i = tid; i < 2 * n16; i += kThr) {
+      const int p = i / n16, r = i - p * n16;
+      reinterpret_cast<uint4*>(vs + (size_t)p * ((vplane + 1023) & ~1023))[r] = src[i];
+    }
+  }
+  for (int b = tid; b < 256; b += kThr) {
+    shs[b] = b < B ? a.shift[b] : 0.f;
+    scs[b] = b < B ? ldexpf(1.f, a.escale[b]) : 0.f;
+  }
+  for (int j = tid; j < kMaxCols; j += kThr) {
+    cls[j] = j < a.k ? a.colscale[j] : 0.f;
+    crs[j] = j < a.k ? a.corr[j] : 0.f;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) { mbar_init(&sy->opfull[s], kConvW); mbar_init(&sy->opempty[s], 1); }
+    for (int i = 0; i < 2; ++i) { mbar_init(&sy->tdone[i], 1); mbar_init(&sy->tfree[i], kEpiW); }
+    mbar_init(&sy->drain, 1);
+    sy->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&sy->tmem_base)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = sy->tmem_base;
+  const int accw = nacc * N16;            // TMEM columns of one tile buffer
+
+  if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t ops_base = su32(ops), vhi = su32(vs);
+      const uint32_t vlo = vhi + (uint32_t)((vplane + 1023) & ~1023);
+      const uint32_t vsbo = (uint32_t)(B16 / 8) * 128;
+      const uint32_t idesc = idesc_f16(N16);
+      int q = 0;
+      bool ok = true;
+      for (int i = 0; i < nt && ok; ++i) {
+        const int bf = i & 1;
+        // the epilogue has read this buffer's previous tile (i - 2)
+        if (i >= 2 && !mbar_wait(&sy->tfree[bf], ((i - 2) >> 1) & 1, &sy->abort)) break;
+        tc_fence_after();
+        const uint32_t acc0 = tbase + (uint32_t)(bf * accw);
+        for (int c = 0; c < KC; ++c, ++q) {
+          const int o = q % S;
+          if (!mbar_wait(&sy->opfull[o], (q / S) & 1, &sy->abort)) { ok = false; break; }
+          tc_fence_after();
+          int nz = 0;
+#pragma unroll
+          for (int w = 0; w < kConvW; ++w) nz |= ((volatile int*)sy->lo_nz[o])[w];
+          const uint32_t ahi = ops_base + (uint32_t)(o * 2) * kPlane, alo = ahi + kPlane;
+          const int ksteps = (B16 - c * kKC) < kKC ? (B16 - c * kKC) / 16 : kKC / 16;
+          const uint32_t acc = acc0 + (uint32_t)((c % nacc) * N16);
+          for (int kk = 0; kk < ksteps; ++kk) {
+            const uint32_t ka = (uint32_t)kk * 2 * kLBO;
+            const uint32_t kb = (uint32_t)((c * kKC + kk * 16) / 8) * 128;
+            const uint32_t first = (c < nacc && kk == 0) ? 0u : 1u;
+            mma_f16(acc, sdesc_kmajor(ahi + ka, kLBO, kASBO), sdesc_kmajor(vhi + kb, kLBO, vsbo),
+                    idesc, first);
+            mma_f16(acc, sdesc_kmajor(ahi + ka, kLBO, kASBO), sdesc_kmajor(vlo + kb, kLBO, vsbo),
+                    idesc, 1u);
+            if (nz)
+              mma_f16(acc, sdesc_kmajor(alo + ka, kLBO, kASBO), sdesc_kmajor(vhi + kb, kLBO, vsbo),
+                      idesc, 1u);
+          }
+          mma_commit(&sy->opempty[o]);
+        }
+        if (ok) mma_commit(&sy->tdone[bf]);
+      }
+    }
+  } else if (warp >= 2 && warp < 2 + kConvW) {
+    // ------------------------------------------------------------ converters
+    const int ct = tid - 64, cw = warp - 2;
+    const int pr = ct % kTM, gp = ct / kTM;   // pixel row of the tile; 16-band group of a chunk
+    const bool vec = (B * (int)sizeof(In)) % 16 == 0;
+    const int Q = nt * KC;
+    float cur[16], nxt[16];
+    auto load_q = [&](int qq, float* r) {
+      const int64_t tile = t0 + qq / KC;
+      const int c = qq % KC;
+      load16<In>(cube, tile * kTM + pr, N, B, c * kKC + gp * 16, vec, r);
+    };
+    if (Q > 0) load_q(0, cur);
+    int bad = 0;
+    for (int q = 0; q < Q; ++q) {
+      const int o = q % S;
+      if (q + 1 < Q) load_q(q + 1, nxt);
+      const int b0 = (q % KC) * kKC + gp * 16;
+      const bool row = (t0 + q / KC) * kTM + pr < N;    // rows past the cube stay 0
+      uint32_t h[8], l[8];
+      uint32_t lo_bits = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int bb = b0 + 2 * e;
+        const float x0 = row && bb < B ? (cur[2 * e] - shs[bb]) * scs[bb] : 0.f;
+        const float x1 = row && bb + 1 < B ? (cur[2 * e + 1] - shs[bb + 1]) * scs[bb + 1] : 0.f;
+        bad |= !(fabsf(x0) <= 65504.f) | !(fabsf(x1) <= 65504.f);
+        h[e] = pack_f16x2(x0, x1);
+        float r0, r1;
+        unpack_f16x2(h[e], r0, r1);
+        l[e] = pack_f16x2(x0 - r0, x1 - r1);
+        lo_bits |= l[e];
+      }
+      const int any_lo = __any_sync(kFull, lo_bits != 0u);
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&sy->opempty[o], ((q / S) & 1) ^ 1, &sy->abort) ? 1 : 0;
+      ok = __shfl_sync(kFull, ok, 0);
+      if (!ok) break;
+      // row pr of the A stage, bands gp*16 .. +15 = core matrices 2gp, 2gp+1
+      unsigned char* hi = ops + (size_t)(o * 2) * kPlane;
+      unsigned char* lo = hi + kPlane;
+      const uint32_t off = (uint32_t)(pr >> 3) * kASBO + (uint32_t)(2 * gp) * kLBO + (pr & 7) * 16;
+      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(hi + off + kLBO) = make_uint4(h[4], h[5], h[6], h[7]);
+      *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+      *reinterpret_cast<uint4*>(lo + off + kLBO) = make_uint4(l[4], l[5], l[6], l[7]);
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        sy->lo_nz[o][cw] = any_lo;   // published by the release of the arrival below
+        mbar_arrive(&sy->opfull[o]);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) cur[e] = nxt[e];
+    }
+    if (__any_sync(kFull, bad) && lane == 0 && a.hdr) atomicOr(&a.hdr->proj_range, 1);
+  } else if (warp >= 2 + kConvW) {
+    // ------------------------------------------------------------ epilogue
+    const int q4 = warp & 3;
+    const int r = q4 * 32 + lane;
+    const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
+    const int nused = nacc < KC ? nacc : KC;
+    const bool v4 = (a.q_ld & 3) == 0 && (a.k & 3) == 0 &&
+                    (reinterpret_cast<uintptr_t>(a.proj) & 15) == 0;
+    bool ok = true;
+    for (int i = 0; i < nt; ++i) {
+      const int bf = i & 1;
+      int okw = 0;
+      if (lane == 0) okw = mbar_wait(&sy->tdone[bf], (i >> 1) & 1, &sy->abort) ? 1 : 0;
+      ok = __shfl_sync(kFull, okw, 0) != 0;
+      if (!ok) break;
+      tc_fence_after();
+      const int64_t n = (t0 + i) * kTM + r;
+      float* out = a.proj + n * a.q_ld;
+      for (int j0 = 0; j0 < N16; j0 += 16) {
+        float v[16], w[16];
+        tmem_ld16(tbase + lane_off + (uint32_t)(bf * accw + j0), v);
+        for (int ac = 1; ac < nused; ++ac) {
+          tmem_ld16(tbase + lane_off + (uint32_t)(bf * accw + ac * N16 + j0), w);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] += w[e];
+        }
+        if (n < N) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = v[e] * cls[j0 + e] - crs[j0 + e];
+          if (v4 && j0 + 16 <= a.k) {
+#pragma unroll
+            for (int e = 0; e < 16; e += 4)
+              *reinterpret_cast<float4*>(out + j0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (j0 + e < a.k) out[j0 + e] = v[e];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sy->tfree[bf]);
+    }
+    if (!ok) {
+      // a bounded wait gave up: this CTA's remaining rows are invalid
+      for (int64_t n = (t0 * kTM) + r; n < t1 * kTM && n < N; n += kTM)
+        for (int j = 0; j < a.k; ++j) a.proj[n * a.q_ld + j] = __int_as_float(0x7fc00000);
+      if (lane == 0 && a.hdr) set_status(a.hdr, PCA_ERR_TIMEOUT);
+    }
+  }
+  // teardown: every MMA of this CTA has finished before TMEM is released
+  if (warp == 1 && lane == 0) {
+    mma_commit(&sy->drain);
+    const unsigned long long tw = gtimer();
+    while (!mbar_try(&sy->drain, 0) && gtimer() - tw < kWaitNs) {
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512)
+                 : "memory");
+  }
+}
+
+size_t ptc_smem(int B, int N16, int S) {
+  const int B16 = (B + 15) & ~15;
+  const size_t vplane = (size_t)((N16 * B16 * 2 + 1023) & ~1023);
+  return 1024 + 2 * vplane + (size_t)S * 2 * kPlane + (256 * 2 + 2 * kMaxCols) * 4 +
+         sizeof(PtcSync);
+}
+
+template <typename In>
+cudaError_t ptc_typed(const PtcArgs& a, cudaStream_t st) {
+  int S = kMaxSt;
+  while (S >= 2 && ptc_smem(a.B, a.N16, S) > (size_t)227 * 1024) --S;
+  if (S < 2) return cudaErrorInvalidValue;
+  const int B16 = (a.B + 15) & ~15;
+  const int KC = (B16 + kKC - 1) / kKC;
+  int nacc = 256 / a.N16;          // accumulators per tile buffer (two buffers in 512 columns)
+  nacc = nacc > KC ? KC : nacc;
+  nacc = nacc < 1 ? 1 : nacc;
+  const size_t smem = ptc_smem(a.B, a.N16, S);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ntiles = (a.N + kTM - 1) / kTM;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  auto kern = k_project_tc<In>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThr, smem, st>>>(a, S, nacc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t project_tc_planes_bytes(int B, int k) {
+  const int B16 = (B + 15) & ~15;
+  const int N16 = ((k < kMaxCols ? k : kMaxCols) + 15) & ~15;
+  return (size_t)2 * N16 * B16 * 2;
+}
+
+cudaError_t launch_project_tc(const void* cube, pca_dtype dt, int64_t N, int B, int k,
+                              const double* mu, const double* V, float* proj, float* shift,
+                              int* escale, unsigned char* planes, float* colscale, float* corr,
+                              DevHeader* hdr, cudaStream_t st) {
+  if (N < 1) return cudaSuccess;
+  switch (dt) {
+    case PCA_F32:
+      k_ptc_bands<float><<<1, 256, 0, st>>>((const float*)cube, N, B, mu, shift, escale);
+      break;
+    case PCA_BF16:
+      k_ptc_bands<__nv_bfloat16><<<1, 256, 0, st>>>((const __nv_bfloat16*)cube, N, B, mu, shift,
+                                                     escale);
+      break;
+    case PCA_F16:
+      k_ptc_bands<__half><<<1, 256, 0, st>>>((const __half*)cube, N, B, mu, shift, escale);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // one launch per group of at most 128 columns (the V operand in shared memory)
+  for (int j0 = 0; j0 < k; j0 += kMaxCols) {
+    const int kk = k - j0 < kMaxCols ? k - j0 : kMaxCols;
+    const int N16 = (kk + 15) & ~15;
+    k_ptc_vop<<<N16, 256, 0, st>>>(V, B, j0, kk, mu, shift, escale, planes, colscale, corr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const PtcArgs a{cube, N, B, kk, N16, k, proj + j0, shift, escale, planes, colscale, corr, hdr};
+    switch (dt) {
+      case PCA_F32: e = ptc_typed<float>(a, st); break;
+      case PCA_BF16: e = ptc_typed<__nv_bfloat16>(a, st); break;
+      case PCA_F16: e = ptc_typed<__half>(a, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace gbpca
