@@ -21,8 +21,14 @@
 // accumulation in TMEM, one accumulator per 64-band chunk (up to four, so
 // that no accumulator sums more than 12 products), double-buffered by tile.
 // One persistent CTA per SM walks its 128-pixel tiles:
+//   warp 0       TMA producer: when a pixel row is a whole number of 16-byte
+//                units, 128-pixel x 128-byte boxes of a 2-D tensor map
+//                (128-byte swizzle; one box per 64-band chunk of a 16-bit
+//                cube, two of an FP32 one) into a ring of raw stages -- many
+//                chunks in flight, which direct loads by the converters cannot
+//                keep up (other cubes: the converters load directly);
 //   warps 2-17   converters: per 64-band chunk each thread takes one pixel and
-//                16 bands (the next chunk's loads in flight while it converts);
+//                16 bands;
 //   warp 1       MMA issuer (one thread) and TMEM owner;
 //   warps 18-21  epilogue: TMEM -> registers (the chunk accumulators added in
 //                FP32) -> column scale and correction -> Q rows.
@@ -30,6 +36,9 @@
 // scaled value outside the FP16 range sets hdr->proj_range and the caller's
 // guarded SIMT projection recomputes Q.  Every wait is bounded (one second);
 // on time-out the CTA records PCA_ERR_TIMEOUT, drains its MMAs and frees TMEM.
+#include <cstring>
+#include <type_traits>
+
 #include "tc.cuh"
 
 namespace gbpca {
@@ -39,6 +48,7 @@ namespace {
 constexpr int kTM = 128;                 // pixels per tile (MMA M)
 constexpr int kKC = 64;                  // bands per K-chunk (one operand stage)
 constexpr int kMaxSt = 4;                // operand ring depth (as shared memory allows)
+constexpr int kMaxRaw = 8;               // raw-chunk ring depth of the TMA path
 constexpr int kConvW = 16;               // converter warps
 constexpr int kEpiW = 4;                 // epilogue warps (one per TMEM lane quarter)
 constexpr int kThr = (2 + kConvW + kEpiW) * 32;
@@ -49,6 +59,8 @@ constexpr int kMaxCols = 128;            // columns of one launch
 constexpr int kProbe = 32;
 
 struct __align__(8) PtcSync {
+  uint64_t rfull[kMaxRaw];
+  uint64_t rempty[kMaxRaw];
   uint64_t opfull[kMaxSt];
   uint64_t opempty[kMaxSt];
   uint64_t tdone[2];   // the MMAs of a tile finished (per TMEM buffer)
@@ -194,16 +206,24 @@ struct PtcArgs {
   DevHeader* hdr;
 };
 
+// Raw bytes of one 64-band chunk of a tile in the TMA ring: 128 rows of 128
+// bytes per box, one box (16-bit) or two (FP32).
 template <typename In>
+constexpr int raw_chunk_bytes() { return kTM * 128 * (sizeof(In) == 4 ? 2 : 1); }
+
+template <typename In, bool kTiled>
 __global__ void __launch_bounds__(kThr, 1)
-k_project_tc(const __grid_constant__ PtcArgs a, int S, int nacc) {
+k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ PtcArgs a, int S,
+             int R, int nacc) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int B = a.B, N16 = a.N16;
   const int B16 = (B + 15) & ~15;
   const int KC = (B16 + kKC - 1) / kKC;                    // K-chunks per tile
   const int vplane = N16 * B16 * 2;                        // one FP16 plane of V
-  unsigned char* vs = smem;                                // [hi|lo][vplane]
+  constexpr int kRaw = raw_chunk_bytes<In>();
+  unsigned char* raw = smem;                               // [R][kRaw] (TMA path)
+  unsigned char* vs = raw + (size_t)R * kRaw;              // [hi|lo][vplane]
   unsigned char* ops = vs + 2 * ((vplane + 1023) & ~1023); // [S][hi|lo][kPlane]
   float* shs = reinterpret_cast<float*>(ops + (size_t)S * 2 * kPlane);   // [256] shift
   float* scs = shs + 256;                                                 // [256] 2^e
@@ -236,6 +256,7 @@ k_project_tc(const __grid_constant__ PtcArgs a, int S, int nacc) {
     crs[j] = j < a.k ? a.corr[j] : 0.f;
   }
   if (tid == 0) {
+    for (int s = 0; s < R; ++s) { mbar_init(&sy->rfull[s], 1); mbar_init(&sy->rempty[s], kConvW); }
     for (int s = 0; s < S; ++s) { mbar_init(&sy->opfull[s], kConvW); mbar_init(&sy->opempty[s], 1); }
     for (int i = 0; i < 2; ++i) { mbar_init(&sy->tdone[i], 1); mbar_init(&sy->tfree[i], kEpiW); }
     mbar_init(&sy->drain, 1);
@@ -256,7 +277,21 @@ k_project_tc(const __grid_constant__ PtcArgs a, int S, int nacc) {
   const uint32_t tbase = sy->tmem_base;
   const int accw = nacc * N16;            // TMEM columns of one tile buffer
 
-  if (warp == 1) {
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (kTiled && lane == 0) {
+      const int Q = nt * KC;
+      for (int q = 0; q < Q; ++q) {
+        const int s = q % R;
+        if (!mbar_wait(&sy->rempty[s], ((q / R) & 1) ^ 1, &sy->abort)) break;
+        const int y = (int)((t0 + q / KC) * kTM), x = (q % KC) * kKC;
+        unsigned char* dst = raw + (size_t)s * kRaw;
+        mbar_expect_tx(&sy->rfull[s], (uint32_t)kRaw);
+        tma_load_2d(dst, &xmap, x, y, &sy->rfull[s]);
+        if (sizeof(In) == 4) tma_load_2d(dst + kTM * 128, &xmap, x + 32, y, &sy->rfull[s]);
+      }
+    }
+  } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t ops_base = su32(ops), vhi = su32(vs);
@@ -310,11 +345,35 @@ k_project_tc(const __grid_constant__ PtcArgs a, int S, int nacc) {
       const int c = qq % KC;
       load16<In>(cube, tile * kTM + pr, N, B, c * kKC + gp * 16, vec, r);
     };
-    if (Q > 0) load_q(0, cur);
+    if (!kTiled && Q > 0) load_q(0, cur);
     int bad = 0;
     for (int q = 0; q < Q; ++q) {
       const int o = q % S;
-      if (q + 1 < Q) load_q(q + 1, nxt);
+      if constexpr (kTiled) {
+        // bands gp*16 .. +15 of row pr: 16-byte units of the swizzled box row
+        const int s = q % R;
+        int okr = 1;
+        if (lane == 0) okr = mbar_wait(&sy->rfull[s], (q / R) & 1, &sy->abort) ? 1 : 0;
+        okr = __shfl_sync(kFull, okr, 0);
+        if (!okr) break;
+        const unsigned char* box = raw + (size_t)s * kRaw;
+        constexpr int E = 16 / (int)sizeof(In);          // elements per 16-byte unit
+        constexpr int U = 16 / E;                        // units of 16 bands
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int unit = gp * U + u;                   // unit of the chunk (8 per box)
+          const unsigned char* bx = box + (size_t)(unit >> 3) * kTM * 128;
+          const uint4 v = *reinterpret_cast<const uint4*>(
+              bx + pr * 128 + (((unit & 7) ^ (pr & 7)) << 4));
+          const In* h = reinterpret_cast<const In*>(&v);
+#pragma unroll
+          for (int e = 0; e < E; ++e) cur[u * E + e] = to_f32<In>(h[e]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sy->rempty[s]);
+      } else {
+        if (q + 1 < Q) load_q(q + 1, nxt);
+      }
       const int b0 = (q % KC) * kKC + gp * 16;
       const bool row = (t0 + q / KC) * kTM + pr < N;    // rows past the cube stay 0
       uint32_t h[8], l[8];
@@ -350,8 +409,10 @@ k_project_tc(const __grid_constant__ PtcArgs a, int S, int nacc) {
         sy->lo_nz[o][cw] = any_lo;   // published by the release of the arrival below
         mbar_arrive(&sy->opfull[o]);
       }
+      if constexpr (!kTiled) {
 #pragma unroll
-      for (int e = 0; e < 16; ++e) cur[e] = nxt[e];
+        for (int e = 0; e < 16; ++e) cur[e] = nxt[e];
+      }
     }
     if (__any_sync(kFull, bad) && lane == 0 && a.hdr) atomicOr(&a.hdr->proj_range, 1);
   } else if (warp >= 2 + kConvW) {
@@ -421,33 +482,52 @@ k_project_tc(const __grid_constant__ PtcArgs a, int S, int nacc) {
   }
 }
 
-size_t ptc_smem(int B, int N16, int S) {
+size_t ptc_smem(int B, int N16, int S, int R, int raw_bytes) {
   const int B16 = (B + 15) & ~15;
   const size_t vplane = (size_t)((N16 * B16 * 2 + 1023) & ~1023);
-  return 1024 + 2 * vplane + (size_t)S * 2 * kPlane + (256 * 2 + 2 * kMaxCols) * 4 +
-         sizeof(PtcSync);
+  return 1024 + (size_t)R * raw_bytes + 2 * vplane + (size_t)S * 2 * kPlane +
+         (256 * 2 + 2 * kMaxCols) * 4 + sizeof(PtcSync);
 }
 
 template <typename In>
 cudaError_t ptc_typed(const PtcArgs& a, cudaStream_t st) {
-  int S = kMaxSt;
-  while (S >= 2 && ptc_smem(a.B, a.N16, S) > (size_t)227 * 1024) --S;
-  if (S < 2) return cudaErrorInvalidValue;
+  // the tensor-map path when the rows are whole 16-byte units
+  CUtensorMap xmap;
+  bool tiled = encode_cube_map(sizeof(In) == 4 ? PCA_F32 : (std::is_same<In, __half>::value
+                                                              ? PCA_F16 : PCA_BF16),
+                               a.cube, a.N, a.B, &xmap, kTM);
+  const int rb = raw_chunk_bytes<In>();
+  const size_t budget = (size_t)227 * 1024;
+  auto fits = [&](int s_, int r_) { return ptc_smem(a.B, a.N16, s_, r_, rb) <= budget; };
+  // tensor-map path: 3 operand stages if they fit (else 2), then as many raw
+  // stages as fit (2..8); when not even 2 + 2 fit, the direct-load path
+  int S = 2, R = 0;
+  if (tiled && !fits(2, 2)) tiled = false;
+  if (tiled) {
+    S = fits(3, 2) ? 3 : 2;
+    R = 2;
+    while (R < kMaxRaw && fits(S, R + 1)) ++R;
+  } else {
+    S = kMaxSt;
+    while (S > 2 && !fits(S, 0)) --S;
+    if (!fits(S, 0)) return cudaErrorInvalidValue;
+    memset(&xmap, 0, sizeof(xmap));
+  }
   const int B16 = (a.B + 15) & ~15;
   const int KC = (B16 + kKC - 1) / kKC;
   int nacc = 256 / a.N16;          // accumulators per tile buffer (two buffers in 512 columns)
   nacc = nacc > KC ? KC : nacc;
   nacc = nacc < 1 ? 1 : nacc;
-  const size_t smem = ptc_smem(a.B, a.N16, S);
+  const size_t smem = ptc_smem(a.B, a.N16, S, R, rb);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (a.N + kTM - 1) / kTM;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
-  auto kern = k_project_tc<In>;
+  auto kern = tiled ? k_project_tc<In, true> : k_project_tc<In, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThr, smem, st>>>(a, S, nacc);
+  kern<<<grid, kThr, smem, st>>>(xmap, a, S, R, nacc);
   return cudaGetLastError();
 }
 
