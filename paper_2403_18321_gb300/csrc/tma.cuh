@@ -41,12 +41,25 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same test, but a thread whose phase is not complete is suspended until it
+// completes or `ns` nanoseconds pass, instead of returning at once: a waiting
+// warp then takes no issue slots from the warps doing the work.
+__device__ __forceinline__ bool mbar_try_suspend(uint64_t* b, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait; false on time-out or when another role already aborted.
 static __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* abort) {
   if (mbar_try(b, parity)) return true;
   const unsigned long long t0 = gtimer();
   for (;;) {
-    if (mbar_try(b, parity)) return true;
+    if (mbar_try_suspend(b, parity, 1000000u)) return true;
     if (*(volatile int*)abort) return false;
     if (gtimer() - t0 > kWaitNs) {
       atomicExch(abort, 1);
