@@ -225,9 +225,8 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   unsigned char* raw = smem;                               // [R][kRaw] (TMA path)
   unsigned char* vs = raw + (size_t)R * kRaw;              // [hi|lo][vplane]
   unsigned char* ops = vs + 2 * ((vplane + 1023) & ~1023); // [S][hi|lo][kPlane]
-  float* shs = reinterpret_cast<float*>(ops + (size_t)S * 2 * kPlane);   // [256] shift
-  float* scs = shs + 256;                                                 // [256] 2^e
-  float* cls = scs + 256;                                                 // [128] 2^-f
+  float2* cst = reinterpret_cast<float2*>(ops + (size_t)S * 2 * kPlane);  // [256] (2^e, -s 2^e)
+  float* cls = reinterpret_cast<float*>(cst + 256);                       // [128] 2^-f
   float* crs = cls + kMaxCols;                                            // [128] c_j
   PtcSync* sy = reinterpret_cast<PtcSync*>(crs + kMaxCols);
 
@@ -247,9 +246,11 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       reinterpret_cast<uint4*>(vs + (size_t)p * ((vplane + 1023) & ~1023))[r] = src[i];
     }
   }
+  // x = (y - s) 2^e as one FMA: y 2^e is exact (a power of two) and the sum is
+  // rounded once, as (y - s) would be before the exact scaling
   for (int b = tid; b < 256; b += kThr) {
-    shs[b] = b < B ? a.shift[b] : 0.f;
-    scs[b] = b < B ? ldexpf(1.f, a.escale[b]) : 0.f;
+    const float sc = b < B ? ldexpf(1.f, a.escale[b]) : 0.f;
+    cst[b] = make_float2(sc, b < B ? -a.shift[b] * sc : 0.f);
   }
   for (int j = tid; j < kMaxCols; j += kThr) {
     cls[j] = j < a.k ? a.colscale[j] : 0.f;
@@ -346,7 +347,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       load16<In>(cube, tile * kTM + pr, N, B, c * kKC + gp * 16, vec, r);
     };
     if (!kTiled && Q > 0) load_q(0, cur);
-    int bad = 0;
+    float mx = 0.f;           // largest |x|: above the FP16 range (or NaN) -> fallback
     for (int q = 0; q < Q; ++q) {
       const int o = q % S;
       if constexpr (kTiled) {
@@ -376,18 +377,31 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       }
       const int b0 = (q % KC) * kKC + gp * 16;
       const bool row = (t0 + q / KC) * kTM + pr < N;    // rows past the cube stay 0
+      // the 16 bands' constants (broadcast reads: every lane of the warp has the same b0)
+      float2 kc[16];
+#pragma unroll
+      for (int e = 0; e < 16; e += 2) {
+        const float4 t = *reinterpret_cast<const float4*>(cst + b0 + e);
+        kc[e] = make_float2(t.x, t.y);
+        kc[e + 1] = make_float2(t.z, t.w);
+      }
+      float x[16];
+      if (row && b0 + 16 <= B) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) x[e] = fmaf(cur[e], kc[e].x, kc[e].y);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) x[e] = row && b0 + e < B ? fmaf(cur[e], kc[e].x, kc[e].y) : 0.f;
+      }
       uint32_t h[8], l[8];
       uint32_t lo_bits = 0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const int bb = b0 + 2 * e;
-        const float x0 = row && bb < B ? (cur[2 * e] - shs[bb]) * scs[bb] : 0.f;
-        const float x1 = row && bb + 1 < B ? (cur[2 * e + 1] - shs[bb + 1]) * scs[bb + 1] : 0.f;
-        bad |= !(fabsf(x0) <= 65504.f) | !(fabsf(x1) <= 65504.f);
-        h[e] = pack_f16x2(x0, x1);
+        mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
+        h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
         float r0, r1;
         unpack_f16x2(h[e], r0, r1);
-        l[e] = pack_f16x2(x0 - r0, x1 - r1);
+        l[e] = pack_f16x2(x[2 * e] - r0, x[2 * e + 1] - r1);
         lo_bits |= l[e];
       }
       const int any_lo = __any_sync(kFull, lo_bits != 0u);
@@ -414,6 +428,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
         for (int e = 0; e < 16; ++e) cur[e] = nxt[e];
       }
     }
+    const int bad = !(mx <= 65504.f);
     if (__any_sync(kFull, bad) && lane == 0 && a.hdr) atomicOr(&a.hdr->proj_range, 1);
   } else if (warp >= 2 + kConvW) {
     // ------------------------------------------------------------ epilogue
@@ -486,7 +501,7 @@ size_t ptc_smem(int B, int N16, int S, int R, int raw_bytes) {
   const int B16 = (B + 15) & ~15;
   const size_t vplane = (size_t)((N16 * B16 * 2 + 1023) & ~1023);
   return 1024 + (size_t)R * raw_bytes + 2 * vplane + (size_t)S * 2 * kPlane +
-         (256 * 2 + 2 * kMaxCols) * 4 + sizeof(PtcSync);
+         (256 * 2 + 2 * kMaxCols) * 4 + sizeof(PtcSync);   // cst[256] float2 + cls + crs
 }
 
 template <typename In>
