@@ -343,6 +343,10 @@ int pca_fit_batched(int ntiles, const pca_tile *tiles, pca_dtype dtype, double t
  * batch_cov_simt_fixed  the same for the SIMT covariance (P32, P64), in units
  *                  of one product per pixel (default 13900).
  * batch_simt_items_per_sm  SIMT covariance work items per SM (1..64, default 4).
+ * proj_tc_stages, proj_tc_raw_stages  tensor-core projection (MIX): depth of
+ *                  the converted-operand ring (2..6) and of the TMA ring of raw
+ *                  cube chunks (2..8); 0 = as many as shared memory holds, with
+ *                  3 operand stages first (default).
  *
  * pca_tuning_defaults fills *t with the defaults.  pca_set_tuning installs *t
  * (NULL: the defaults); PCA_ERR_ARG, and no change, for a value out of range.
@@ -356,6 +360,8 @@ typedef struct {
   double batch_proj_fixed;
   double batch_cov_simt_fixed;
   int batch_simt_items_per_sm;
+  int proj_tc_stages;
+  int proj_tc_raw_stages;
 } pca_tuning;
 void pca_tuning_defaults(pca_tuning *t);
 int pca_set_tuning(const pca_tuning *t);

@@ -47,7 +47,7 @@ namespace {
 
 constexpr int kTM = 128;                 // pixels per tile (MMA M)
 constexpr int kKC = 64;                  // bands per K-chunk (one operand stage)
-constexpr int kMaxSt = 4;                // operand ring depth (as shared memory allows)
+constexpr int kMaxSt = 6;                // operand ring depth (as shared memory allows)
 constexpr int kMaxRaw = 8;               // raw-chunk ring depth of the TMA path
 constexpr int kConvW = 16;               // converter warps
 constexpr int kEpiW = 4;                 // epilogue warps (one per TMEM lane quarter)
@@ -299,6 +299,10 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       const uint32_t vlo = vhi + (uint32_t)((vplane + 1023) & ~1023);
       const uint32_t vsbo = (uint32_t)(B16 / 8) * 128;
       const uint32_t idesc = idesc_f16(N16);
+      // descriptors of the operand bases; an offset of d bytes adds d >> 4 to
+      // the start-address field (every address stays below 256 KB)
+      const uint64_t dA = sdesc_kmajor(ops_base, kLBO, kASBO);
+      const uint64_t dVh = sdesc_kmajor(vhi, kLBO, vsbo), dVl = sdesc_kmajor(vlo, kLBO, vsbo);
       int q = 0;
       bool ok = true;
       for (int i = 0; i < nt && ok; ++i) {
@@ -314,20 +318,15 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
           int nz = 0;
 #pragma unroll
           for (int w = 0; w < kConvW; ++w) nz |= ((volatile int*)sy->lo_nz[o])[w];
-          const uint32_t ahi = ops_base + (uint32_t)(o * 2) * kPlane, alo = ahi + kPlane;
+          const uint64_t ahi = dA + (uint64_t)((o * 2 * kPlane) >> 4), alo = ahi + (kPlane >> 4);
           const int ksteps = (B16 - c * kKC) < kKC ? (B16 - c * kKC) / 16 : kKC / 16;
           const uint32_t acc = acc0 + (uint32_t)((c % nacc) * N16);
+          const uint64_t kb0 = (uint64_t)(c * (kKC / 8) * 128 >> 4);
           for (int kk = 0; kk < ksteps; ++kk) {
-            const uint32_t ka = (uint32_t)kk * 2 * kLBO;
-            const uint32_t kb = (uint32_t)((c * kKC + kk * 16) / 8) * 128;
-            const uint32_t first = (c < nacc && kk == 0) ? 0u : 1u;
-            mma_f16(acc, sdesc_kmajor(ahi + ka, kLBO, kASBO), sdesc_kmajor(vhi + kb, kLBO, vsbo),
-                    idesc, first);
-            mma_f16(acc, sdesc_kmajor(ahi + ka, kLBO, kASBO), sdesc_kmajor(vlo + kb, kLBO, vsbo),
-                    idesc, 1u);
-            if (nz)
-              mma_f16(acc, sdesc_kmajor(alo + ka, kLBO, kASBO), sdesc_kmajor(vhi + kb, kLBO, vsbo),
-                      idesc, 1u);
+            const uint64_t ka = (uint64_t)(kk * 2 * kLBO >> 4), kb = kb0 + (uint64_t)(kk * 2 * 128 >> 4);
+            mma_f16(acc, ahi + ka, dVh + kb, idesc, (c < nacc && kk == 0) ? 0u : 1u);
+            mma_f16(acc, ahi + ka, dVl + kb, idesc, 1u);
+            if (nz) mma_f16(acc, alo + ka, dVh + kb, idesc, 1u);
           }
           mma_commit(&sy->opempty[o]);
         }
@@ -516,12 +515,16 @@ cudaError_t ptc_typed(const PtcArgs& a, cudaStream_t st) {
   auto fits = [&](int s_, int r_) { return ptc_smem(a.B, a.N16, s_, r_, rb) <= budget; };
   // tensor-map path: 3 operand stages if they fit (else 2), then as many raw
   // stages as fit (2..8); when not even 2 + 2 fit, the direct-load path
+  const pca_tuning tu = tuning();
   int S = 2, R = 0;
   if (tiled && !fits(2, 2)) tiled = false;
   if (tiled) {
     S = fits(3, 2) ? 3 : 2;
+    if (tu.proj_tc_stages >= 2 && tu.proj_tc_stages <= kMaxSt && fits(tu.proj_tc_stages, 2))
+      S = tu.proj_tc_stages;
     R = 2;
-    while (R < kMaxRaw && fits(S, R + 1)) ++R;
+    while (R < kMaxRaw && fits(S, R + 1) && (tu.proj_tc_raw_stages == 0 || R < tu.proj_tc_raw_stages))
+      ++R;
   } else {
     S = kMaxSt;
     while (S > 2 && !fits(S, 0)) --S;

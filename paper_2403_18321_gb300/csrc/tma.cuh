@@ -54,9 +54,10 @@ __device__ __forceinline__ bool mbar_try_suspend(uint64_t* b, uint32_t parity, u
       : "memory");
   return ok != 0;
 }
-// Bounded wait; false on time-out or when another role already aborted.
-static __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* abort) {
-  if (mbar_try(b, parity)) return true;
+// Bounded wait; false on time-out or when another role already aborted.  The
+// first test is inline (the common case of a phase already complete costs no
+// call); the loop is out of line.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity, int* abort) {
   const unsigned long long t0 = gtimer();
   for (;;) {
     if (mbar_try_suspend(b, parity, 1000000u)) return true;
@@ -66,6 +67,9 @@ static __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int*
       return false;
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* abort) {
+  return mbar_try(b, parity) || mbar_wait_slow(b, parity, abort);
 }
 // 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

@@ -19,6 +19,8 @@ pca_tuning defaults() {
   t.batch_proj_fixed = 223.0;
   t.batch_cov_simt_fixed = 13900.0;
   t.batch_simt_items_per_sm = 4;
+  t.proj_tc_stages = 0;
+  t.proj_tc_raw_stages = 0;
   return t;
 }
 
@@ -32,6 +34,9 @@ bool valid(const pca_tuning& t) {
     if (t.batch_jacobi_ctas[i] < 0 || t.batch_jacobi_ctas[i] > 8) return false;
   auto ok = [](double v) { return std::isfinite(v) && v >= 0.0 && v <= 1e9; };
   if (!ok(t.batch_cov_tc_fixed) || !ok(t.batch_proj_fixed) || !ok(t.batch_cov_simt_fixed))
+    return false;
+  if (t.proj_tc_stages != 0 && (t.proj_tc_stages < 2 || t.proj_tc_stages > 6)) return false;
+  if (t.proj_tc_raw_stages != 0 && (t.proj_tc_raw_stages < 2 || t.proj_tc_raw_stages > 8))
     return false;
   return t.batch_simt_items_per_sm >= 1 && t.batch_simt_items_per_sm <= 64;
 }
