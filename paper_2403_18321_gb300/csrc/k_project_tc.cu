@@ -66,7 +66,7 @@ struct __align__(8) PtcSync {
   uint64_t tdone[2];   // the MMAs of a tile finished (per TMEM buffer)
   uint64_t tfree[2];   // the epilogue has read a TMEM buffer
   uint64_t drain;
-  int lo_nz[kMaxSt][kConvW];
+  unsigned char lo_nz[kMaxSt][kConvW];   // per converter warp: a lo part is non-zero
   uint32_t tmem_base;
   int abort;
 };
@@ -315,9 +315,11 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
           const int o = q % S;
           if (!mbar_wait(&sy->opfull[o], (q / S) & 1, &sy->abort)) { ok = false; break; }
           tc_fence_after();
-          int nz = 0;
-#pragma unroll
-          for (int w = 0; w < kConvW; ++w) nz |= ((volatile int*)sy->lo_nz[o])[w];
+          uint32_t f0, f1, f2, f3;   // the 16 warps' flags in one 16-byte load
+          asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(f0), "=r"(f1), "=r"(f2), "=r"(f3)
+                       : "r"(su32(sy->lo_nz[o])));
+          const uint32_t nz = (f0 | f1) | (f2 | f3);
           const uint64_t ahi = dA + (uint64_t)((o * 2 * kPlane) >> 4), alo = ahi + (kPlane >> 4);
           const int ksteps = (B16 - c * kKC) < kKC ? (B16 - c * kKC) / 16 : kKC / 16;
           const uint32_t acc = acc0 + (uint32_t)((c % nacc) * N16);
@@ -419,7 +421,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) {
-        sy->lo_nz[o][cw] = any_lo;   // published by the release of the arrival below
+        sy->lo_nz[o][cw] = (unsigned char)any_lo;   // published by the release of the arrival below
         mbar_arrive(&sy->opfull[o]);
       }
       if constexpr (!kTiled) {
@@ -448,12 +450,26 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       const int64_t n = (t0 + i) * kTM + r;
       float* out = a.proj + n * a.q_ld;
       for (int j0 = 0; j0 < N16; j0 += 16) {
-        float v[16], w[16];
-        tmem_ld16(tbase + lane_off + (uint32_t)(bf * accw + j0), v);
-        for (int ac = 1; ac < nused; ++ac) {
-          tmem_ld16(tbase + lane_off + (uint32_t)(bf * accw + ac * N16 + j0), w);
+        float v[16], w[16], x2[16], y2[16];
+        const uint32_t t = tbase + lane_off + (uint32_t)(bf * accw + j0);
+        // accumulators two at a time (two loads in flight per wait)
+        if (nused >= 2) {
+          tmem_ld16x2(t, t + (uint32_t)N16, v, w);
 #pragma unroll
           for (int e = 0; e < 16; ++e) v[e] += w[e];
+        } else {
+          tmem_ld16(t, v);
+        }
+        for (int ac = 2; ac < nused; ac += 2) {
+          if (ac + 1 < nused) {
+            tmem_ld16x2(t + (uint32_t)(ac * N16), t + (uint32_t)((ac + 1) * N16), x2, y2);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] += x2[e] + y2[e];
+          } else {
+            tmem_ld16(t + (uint32_t)(ac * N16), x2);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] += x2[e];
+          }
         }
         if (n < N) {
 #pragma unroll
