@@ -36,6 +36,7 @@
 // scaled value outside the FP16 range sets hdr->proj_range and the caller's
 // guarded SIMT projection recomputes Q.  Every wait is bounded (one second);
 // on time-out the CTA records PCA_ERR_TIMEOUT, drains its MMAs and frees TMEM.
+#include <cstddef>
 #include <cstring>
 #include <type_traits>
 
@@ -58,7 +59,7 @@ constexpr uint32_t kASBO = (kKC / 8) * 128;   // A: 8-row groups, 1 KB
 constexpr int kMaxCols = 128;            // columns of one launch
 constexpr int kProbe = 32;
 
-struct __align__(8) PtcSync {
+struct __align__(16) PtcSync {
   uint64_t rfull[kMaxRaw];
   uint64_t rempty[kMaxRaw];
   uint64_t opfull[kMaxSt];
@@ -66,10 +67,15 @@ struct __align__(8) PtcSync {
   uint64_t tdone[2];   // the MMAs of a tile finished (per TMEM buffer)
   uint64_t tfree[2];   // the epilogue has read a TMEM buffer
   uint64_t drain;
-  unsigned char lo_nz[kMaxSt][kConvW];   // per converter warp: a lo part is non-zero
+  // per converter warp: a lo part is non-zero; each stage's 16 flags are one
+  // 16-byte aligned row (the MMA thread reads a row with one vector load)
+  alignas(16) unsigned char lo_nz[kMaxSt][kConvW];
   uint32_t tmem_base;
   int abort;
 };
+
+static_assert(offsetof(PtcSync, lo_nz) % 16 == 0 && kConvW == 16,
+              "each stage's flags must be one aligned 16-byte row");
 
 template <typename In>
 __device__ __forceinline__ float on_grid(float m);
@@ -228,7 +234,8 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   float2* cst = reinterpret_cast<float2*>(ops + (size_t)S * 2 * kPlane);  // [256] (2^e, -s 2^e)
   float* cls = reinterpret_cast<float*>(cst + 256);                       // [128] 2^-f
   float* crs = cls + kMaxCols;                                            // [128] c_j
-  PtcSync* sy = reinterpret_cast<PtcSync*>(crs + kMaxCols);
+  PtcSync* sy = reinterpret_cast<PtcSync*>((reinterpret_cast<uintptr_t>(crs + kMaxCols) + 15) &
+                                            ~static_cast<uintptr_t>(15));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const In* cube = static_cast<const In*>(a.cube);
@@ -516,7 +523,7 @@ size_t ptc_smem(int B, int N16, int S, int R, int raw_bytes) {
   const int B16 = (B + 15) & ~15;
   const size_t vplane = (size_t)((N16 * B16 * 2 + 1023) & ~1023);
   return 1024 + (size_t)R * raw_bytes + 2 * vplane + (size_t)S * 2 * kPlane +
-         (256 * 2 + 2 * kMaxCols) * 4 + sizeof(PtcSync);   // cst[256] float2 + cls + crs
+         (256 * 2 + 2 * kMaxCols) * 4 + sizeof(PtcSync) + 16;   // cst[256] float2 + cls + crs
 }
 
 template <typename In>
