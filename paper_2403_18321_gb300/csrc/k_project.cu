@@ -181,7 +181,7 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
     // ------------------------------------------------------------ producer
     // streams every item's chunks through one ring, ahead of the compute warps
     if (lane == 0) {
-      int q = 0;
+      Ring rq(S);
       bool ok = true;
       for (int i = 0; i < nitems && ok; ++i) {
         const PItem it = proj_item(one, &tmap, T, maps, items, cta_items, i);
@@ -189,9 +189,9 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
         const int64_t N = it.a.N;
         const int B = it.a.B;
         const int nbox = (B * (int)sizeof(In) + 127) / 128;
-        for (int64_t c = it.c0; c < it.c1; ++c, ++q) {
-          const int s = q % S;
-          if (!mbar_wait(&sy->empty[s], ((q / S) & 1) ^ 1, &sy->abort)) { ok = false; break; }
+        for (int64_t c = it.c0; c < it.c1; ++c, rq.next()) {
+          const int s = rq.idx;
+          if (!mbar_wait(&sy->empty[s], rq.phase ^ 1u, &sy->abort)) { ok = false; break; }
           const int64_t p0 = c * kPc;
           unsigned char* dst = stages + (size_t)s * stage_bytes;
           if constexpr (kTiled) {
@@ -214,7 +214,7 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
   // -------------------------------------------------------------- compute
   const int h = warp;
   const int pa = lane, pb = lane + 32;
-  int q = 0;
+  Ring rq(S);
   bool stop = false;
   for (int i = 0; i < nitems && !stop; ++i) {
   const PItem it = proj_item(one, &tmap, T, maps, items, cta_items, i);
@@ -232,10 +232,10 @@ k_project(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Proj
   for (int b = tid; b < B8; b += kCompute) mus[b] = b < B ? a.mu_f[b] : 0.f;
   named_sync();
   int64_t c = it.c0;
-  for (; c < it.c1; ++c, ++q) {
-    const int s = q % S;
+  for (; c < it.c1; ++c, rq.next()) {
+    const int s = rq.idx;
     int ok = 1;
-    if (lane == 0) ok = mbar_wait(&sy->full[s], (q / S) & 1, &sy->abort) ? 1 : 0;
+    if (lane == 0) ok = mbar_wait(&sy->full[s], rq.phase, &sy->abort) ? 1 : 0;
     ok = __shfl_sync(kFull, ok, 0);
     if (!named_and(ok)) break;
     const int64_t p0 = c * kPc;

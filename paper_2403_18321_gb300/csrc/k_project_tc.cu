@@ -288,15 +288,18 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (kTiled && lane == 0) {
-      const int Q = nt * KC;
-      for (int q = 0; q < Q; ++q) {
-        const int s = q % R;
-        if (!mbar_wait(&sy->rempty[s], ((q / R) & 1) ^ 1, &sy->abort)) break;
-        const int y = (int)((t0 + q / KC) * kTM), x = (q % KC) * kKC;
-        unsigned char* dst = raw + (size_t)s * kRaw;
-        mbar_expect_tx(&sy->rfull[s], (uint32_t)kRaw);
-        tma_load_2d(dst, &xmap, x, y, &sy->rfull[s]);
-        if (sizeof(In) == 4) tma_load_2d(dst + kTM * 128, &xmap, x + 32, y, &sy->rfull[s]);
+      Ring rs(R);
+      bool go = true;
+      for (int i = 0; i < nt && go; ++i) {
+        const int y = (int)((t0 + i) * kTM);
+        for (int c = 0; c < KC; ++c, rs.next()) {
+          if (!mbar_wait(&sy->rempty[rs.idx], rs.phase ^ 1u, &sy->abort)) { go = false; break; }
+          unsigned char* dst = raw + (size_t)rs.idx * kRaw;
+          mbar_expect_tx(&sy->rfull[rs.idx], (uint32_t)kRaw);
+          tma_load_2d(dst, &xmap, c * kKC, y, &sy->rfull[rs.idx]);
+          if (sizeof(In) == 4)
+            tma_load_2d(dst + kTM * 128, &xmap, c * kKC + 32, y, &sy->rfull[rs.idx]);
+        }
       }
     }
   } else if (warp == 1) {
@@ -310,7 +313,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       // the start-address field (every address stays below 256 KB)
       const uint64_t dA = sdesc_kmajor(ops_base, kLBO, kASBO);
       const uint64_t dVh = sdesc_kmajor(vhi, kLBO, vsbo), dVl = sdesc_kmajor(vlo, kLBO, vsbo);
-      int q = 0;
+      Ring ro(S);
       bool ok = true;
       for (int i = 0; i < nt && ok; ++i) {
         const int bf = i & 1;
@@ -318,9 +321,9 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
         if (i >= 2 && !mbar_wait(&sy->tfree[bf], ((i - 2) >> 1) & 1, &sy->abort)) break;
         tc_fence_after();
         const uint32_t acc0 = tbase + (uint32_t)(bf * accw);
-        for (int c = 0; c < KC; ++c, ++q) {
-          const int o = q % S;
-          if (!mbar_wait(&sy->opfull[o], (q / S) & 1, &sy->abort)) { ok = false; break; }
+        for (int c = 0; c < KC; ++c, ro.next()) {
+          const int o = ro.idx;
+          if (!mbar_wait(&sy->opfull[o], ro.phase, &sy->abort)) { ok = false; break; }
           tc_fence_after();
           uint32_t f0, f1, f2, f3;   // the 16 warps' flags in one 16-byte load
           asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -349,20 +352,21 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
     const bool vec = (B * (int)sizeof(In)) % 16 == 0;
     const int Q = nt * KC;
     float cur[16], nxt[16];
-    auto load_q = [&](int qq, float* r) {
-      const int64_t tile = t0 + qq / KC;
-      const int c = qq % KC;
-      load16<In>(cube, tile * kTM + pr, N, B, c * kKC + gp * 16, vec, r);
-    };
-    if (!kTiled && Q > 0) load_q(0, cur);
+    // (tile, chunk) of the chunk being converted and of the next one
+    int64_t tile = t0, ntile = t0;
+    int c = 0, nc = 0;
+    auto advance = [&](int64_t& t, int& cc) { if (++cc == KC) { cc = 0; ++t; } };
+    if (!kTiled && Q > 0) load16<In>(cube, t0 * kTM + pr, N, B, gp * 16, vec, cur);
+    advance(ntile, nc);
     float mx = 0.f;           // largest |x|: above the FP16 range (or NaN) -> fallback
-    for (int q = 0; q < Q; ++q) {
-      const int o = q % S;
+    Ring ro(S), rs(R > 0 ? R : 1);
+    for (int q = 0; q < Q; ++q, ro.next(), rs.next()) {
+      const int o = ro.idx;
       if constexpr (kTiled) {
         // bands gp*16 .. +15 of row pr: 16-byte units of the swizzled box row
-        const int s = q % R;
+        const int s = rs.idx;
         int okr = 1;
-        if (lane == 0) okr = mbar_wait(&sy->rfull[s], (q / R) & 1, &sy->abort) ? 1 : 0;
+        if (lane == 0) okr = mbar_wait(&sy->rfull[s], rs.phase, &sy->abort) ? 1 : 0;
         okr = __shfl_sync(kFull, okr, 0);
         if (!okr) break;
         const unsigned char* box = raw + (size_t)s * kRaw;
@@ -381,10 +385,10 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
         __syncwarp();
         if (lane == 0) mbar_arrive(&sy->rempty[s]);
       } else {
-        if (q + 1 < Q) load_q(q + 1, nxt);
+        if (q + 1 < Q) load16<In>(cube, ntile * kTM + pr, N, B, nc * kKC + gp * 16, vec, nxt);
       }
-      const int b0 = (q % KC) * kKC + gp * 16;
-      const bool row = (t0 + q / KC) * kTM + pr < N;    // rows past the cube stay 0
+      const int b0 = c * kKC + gp * 16;
+      const bool row = tile * kTM + pr < N;    // rows past the cube stay 0
       // the 16 bands' constants (broadcast reads: every lane of the warp has the same b0)
       float2 kc[16];
 #pragma unroll
@@ -414,7 +418,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       }
       const int any_lo = __any_sync(kFull, lo_bits != 0u);
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(&sy->opempty[o], ((q / S) & 1) ^ 1, &sy->abort) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(&sy->opempty[o], ro.phase ^ 1u, &sy->abort) ? 1 : 0;
       ok = __shfl_sync(kFull, ok, 0);
       if (!ok) break;
       // row pr of the A stage, bands gp*16 .. +15 = core matrices 2gp, 2gp+1
@@ -435,6 +439,8 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
 #pragma unroll
         for (int e = 0; e < 16; ++e) cur[e] = nxt[e];
       }
+      advance(tile, c);
+      advance(ntile, nc);
     }
     const int bad = !(mx <= 65504.f);
     if (__any_sync(kFull, bad) && lane == 0 && a.hdr) atomicOr(&a.hdr->proj_range, 1);

@@ -205,15 +205,15 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
   if (warp == 0) {
     // ---------------------------------------------------------- TMA producer
     if (lane == 0) {
-      int q = 0;  // ring position, continued across items
+      Ring rq(S);  // ring position, continued across items
       bool ok = true;
       for (int i = 0; i < nitems && ok; ++i) {
         const TcItem it = tc_item(one, T, items, cta_items, i);
         const In* cube = static_cast<const In*>(it.t.cube);
         const int B = it.t.B;
-        for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ++q) {
-          const int s = q % S;
-          if (!mbar_wait(&sb->empty[s], ((q / S) & 1) ^ 1, &sb->abort)) { ok = false; break; }
+        for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, rq.next()) {
+          const int s = rq.idx;
+          if (!mbar_wait(&sb->empty[s], rq.phase ^ 1u, &sb->abort)) { ok = false; break; }
           const int cp = (int)((it.p1 - p0) < kKC ? (it.p1 - p0) : kKC);
           const uint32_t bytes = (uint32_t)(cp * B * (int)sizeof(In)) & ~15u;
           mbar_expect_tx(&sb->full[s], bytes);
@@ -225,7 +225,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const uint32_t ops_base = su32(ops);
-      int q = 0;  // operand-ring position, continued across items
+      Ring ro(kOpStages);  // operand-ring position, continued across items
       bool ok = true;
       for (int i = 0; i < nitems && ok; ++i) {
         const TcItem it = tc_item(one, T, items, cta_items, i);
@@ -239,9 +239,9 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         if (i > 0 && !mbar_wait(&sb->tfree, (i - 1) & 1, &sb->abort)) break;
         tc_fence_after();
         bool first = true;
-        for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ++q) {
-          const int o = q % kOpStages;
-          if (!mbar_wait(&sb->opfull[o], (q / kOpStages) & 1, &sb->abort)) { ok = false; break; }
+        for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ro.next()) {
+          const int o = ro.idx;
+          if (!mbar_wait(&sb->opfull[o], ro.phase, &sb->abort)) { ok = false; break; }
           tc_fence_after();
           const uint32_t hi = ops_base + (uint32_t)(o * 2) * kOpBytes;
           const uint32_t lo = hi + kOpBytes;
@@ -278,7 +278,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
   } else {
     // ---------------------------------------------------------- converters
     const int ct = tid - 64;
-    int qs = 0;                       // ring / operand-ring position, continued across items
+    Ring rs(S), ro(kOpStages);        // ring / operand-ring positions, continued across items
     const void* probed = nullptr;     // the cube (and pixel count) whose shift and
     int64_t probed_n = -1;            // scale are in shs / sesc
     for (int i = 0; i < nitems; ++i) {
@@ -366,14 +366,14 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
       int out_of_range = 0;   // a scaled value of this item left the FP16 range
       const int cw = warp - 2;  // converter warp index
       int c = 0;
-      for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ++c, ++qs) {
-        const int s = qs % S, o = qs % kOpStages;
+      for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ++c, rs.next(), ro.next()) {
+        const int s = rs.idx, o = ro.idx;
         // one lane per warp polls the barriers (the others would only add
         // shared-memory traffic), then the warp proceeds together
         int ok = 1;
         if (lane == 0) {
-          ok = mbar_wait(&sb->full[s], (qs / S) & 1, &sb->abort) ? 1 : 0;
-          if (ok) ok = mbar_wait(&sb->opempty[o], ((qs / kOpStages) & 1) ^ 1, &sb->abort) ? 1 : 0;
+          ok = mbar_wait(&sb->full[s], rs.phase, &sb->abort) ? 1 : 0;
+          if (ok) ok = mbar_wait(&sb->opempty[o], ro.phase ^ 1u, &sb->abort) ? 1 : 0;
         }
         ok = __shfl_sync(kFull, ok, 0);
         if (!ok) break;

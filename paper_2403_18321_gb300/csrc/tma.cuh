@@ -12,6 +12,17 @@ namespace gbpca {
 
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s bound on every wait
 
+// A position in a ring of n stages -- the stage and the parity of its current
+// phase -- advanced one slot at a time (no division in the per-chunk loops).
+struct Ring {
+  int n, idx;
+  uint32_t phase;
+  __device__ explicit Ring(int n_) : n(n_), idx(0), phase(0u) {}
+  __device__ __forceinline__ void next() {
+    if (++idx == n) { idx = 0; phase ^= 1u; }
+  }
+};
+
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
