@@ -16,10 +16,11 @@
 //                order, and the centring correction c_j = sum_b (mu_b - s_b)
 //                v_bj (FP64), so that Q_nj = 2^-f_j sum_b x_nb w_bj - c_j with
 //                x_nb = (y_nb - s_b) 2^e_b.
-// Products hi hi + hi lo + lo hi (the third only when a chunk has a non-zero
-// lo part: never for 16-bit cubes within 2^11 grid steps of the shift), FP32
-// accumulation in TMEM, one accumulator per 64-band chunk (up to four, so
-// that no accumulator sums more than 12 products), double-buffered by tile.
+// Products x_hi [V_hi | V_lo] (one MMA of 2 N16 columns) and x_lo V_hi (only
+// when a chunk has a non-zero lo part: never for 16-bit cubes within 2^11 grid
+// steps of the shift), FP32 accumulation in TMEM; the K-steps of a tile rotate
+// over up to eight accumulators, so that consecutive MMAs are independent and
+// none sums more than a few products; double-buffered by tile.
 // One persistent CTA per SM walks its 128-pixel tiles:
 //   warp 0       TMA producer: when a pixel row is a whole number of 16-byte
 //                units, 128-pixel x 128-byte boxes of a 2-D tensor map
@@ -229,8 +230,10 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   const int vplane = N16 * B16 * 2;                        // one FP16 plane of V
   constexpr int kRaw = raw_chunk_bytes<In>();
   unsigned char* raw = smem;                               // [R][kRaw] (TMA path)
+  // V: the lo plane right after the hi plane, so that [V_hi | V_lo] is one B
+  // operand of 2 N16 rows (one MMA gives both products of a K-step)
   unsigned char* vs = raw + (size_t)R * kRaw;              // [hi|lo][vplane]
-  unsigned char* ops = vs + 2 * ((vplane + 1023) & ~1023); // [S][hi|lo][kPlane]
+  unsigned char* ops = vs + ((2 * vplane + 1023) & ~1023); // [S][hi|lo][kPlane]
   float2* cst = reinterpret_cast<float2*>(ops + (size_t)S * 2 * kPlane);  // [256] (2^e, -s 2^e)
   float* cls = reinterpret_cast<float*>(cst + 256);                       // [128] 2^-f
   float* crs = cls + kMaxCols;                                            // [128] c_j
@@ -247,11 +250,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   // ---- set-up: V planes, band and column constants, barriers, TMEM
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.planes);
-    const int n16 = vplane / 16;
-    for (int i = tid; i < 2 * n16; i += kThr) {
-      const int p = i / n16, r = i - p * n16;
-      reinterpret_cast<uint4*>(vs + (size_t)p * ((vplane + 1023) & ~1023))[r] = src[i];
-    }
+    for (int i = tid; i < 2 * vplane / 16; i += kThr) reinterpret_cast<uint4*>(vs)[i] = src[i];
   }
   // x = (y - s) 2^e as one FMA: y 2^e is exact (a power of two) and the sum is
   // rounded once, as (y - s) would be before the exact scaling
@@ -283,7 +282,10 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = sy->tmem_base;
-  const int accw = nacc * N16;            // TMEM columns of one tile buffer
+  // nacc accumulators of 2 N16 columns per tile buffer, the K-steps of a tile
+  // rotating over them (consecutive MMAs do not wait for each other): columns
+  // [0, N16) sum x_hi V_hi (+ x_lo V_hi), [N16, 2 N16) sum x_hi V_lo
+  const int accw = nacc * 2 * N16;        // TMEM columns of one tile buffer
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -306,13 +308,12 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t ops_base = su32(ops), vhi = su32(vs);
-      const uint32_t vlo = vhi + (uint32_t)((vplane + 1023) & ~1023);
       const uint32_t vsbo = (uint32_t)(B16 / 8) * 128;
-      const uint32_t idesc = idesc_f16(N16);
+      const uint32_t id_both = idesc_f16(2 * N16), id_hi = idesc_f16(N16);
       // descriptors of the operand bases; an offset of d bytes adds d >> 4 to
       // the start-address field (every address stays below 256 KB)
       const uint64_t dA = sdesc_kmajor(ops_base, kLBO, kASBO);
-      const uint64_t dVh = sdesc_kmajor(vhi, kLBO, vsbo), dVl = sdesc_kmajor(vlo, kLBO, vsbo);
+      const uint64_t dVh = sdesc_kmajor(vhi, kLBO, vsbo);   // [V_hi | V_lo] from here
       Ring ro(S);
       bool ok = true;
       for (int i = 0; i < nt && ok; ++i) {
@@ -321,6 +322,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
         if (i >= 2 && !mbar_wait(&sy->tfree[bf], ((i - 2) >> 1) & 1, &sy->abort)) break;
         tc_fence_after();
         const uint32_t acc0 = tbase + (uint32_t)(bf * accw);
+        int ai = 0, ks = 0;      // rotating accumulator, K-step of the tile
         for (int c = 0; c < KC; ++c, ro.next()) {
           const int o = ro.idx;
           if (!mbar_wait(&sy->opfull[o], ro.phase, &sy->abort)) { ok = false; break; }
@@ -332,13 +334,13 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
           const uint32_t nz = (f0 | f1) | (f2 | f3);
           const uint64_t ahi = dA + (uint64_t)((o * 2 * kPlane) >> 4), alo = ahi + (kPlane >> 4);
           const int ksteps = (B16 - c * kKC) < kKC ? (B16 - c * kKC) / 16 : kKC / 16;
-          const uint32_t acc = acc0 + (uint32_t)((c % nacc) * N16);
           const uint64_t kb0 = (uint64_t)(c * (kKC / 8) * 128 >> 4);
-          for (int kk = 0; kk < ksteps; ++kk) {
+          for (int kk = 0; kk < ksteps; ++kk, ++ks) {
             const uint64_t ka = (uint64_t)(kk * 2 * kLBO >> 4), kb = kb0 + (uint64_t)(kk * 2 * 128 >> 4);
-            mma_f16(acc, ahi + ka, dVh + kb, idesc, (c < nacc && kk == 0) ? 0u : 1u);
-            mma_f16(acc, ahi + ka, dVl + kb, idesc, 1u);
-            if (nz) mma_f16(acc, alo + ka, dVh + kb, idesc, 1u);
+            const uint32_t acc = acc0 + (uint32_t)(ai * 2 * N16);
+            mma_f16(acc, ahi + ka, dVh + kb, id_both, ks < nacc ? 0u : 1u);
+            if (nz) mma_f16(acc, alo + ka, dVh + kb, id_hi, 1u);
+            ai = ai + 1 == nacc ? 0 : ai + 1;
           }
           mma_commit(&sy->opempty[o]);
         }
@@ -449,7 +451,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
     const int q4 = warp & 3;
     const int r = q4 * 32 + lane;
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-    const int nused = nacc < KC ? nacc : KC;
+    const int nused = nacc < B16 / 16 ? nacc : B16 / 16;   // accumulators a tile writes
     const bool v4 = (a.q_ld & 3) == 0 && (a.k & 3) == 0 &&
                     (reinterpret_cast<uintptr_t>(a.proj) & 15) == 0;
     bool ok = true;
@@ -463,26 +465,18 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       const int64_t n = (t0 + i) * kTM + r;
       float* out = a.proj + n * a.q_ld;
       for (int j0 = 0; j0 < N16; j0 += 16) {
-        float v[16], w[16], x2[16], y2[16];
+        float v[16], w[16];
         const uint32_t t = tbase + lane_off + (uint32_t)(bf * accw + j0);
-        // accumulators two at a time (two loads in flight per wait)
-        if (nused >= 2) {
-          tmem_ld16x2(t, t + (uint32_t)N16, v, w);
+        // both halves of every accumulator (two loads in flight per wait)
+        tmem_ld16x2(t, t + (uint32_t)N16, v, w);
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] += w[e];
-        } else {
-          tmem_ld16(t, v);
-        }
-        for (int ac = 2; ac < nused; ac += 2) {
-          if (ac + 1 < nused) {
-            tmem_ld16x2(t + (uint32_t)(ac * N16), t + (uint32_t)((ac + 1) * N16), x2, y2);
+        for (int e = 0; e < 16; ++e) v[e] += w[e];
+        for (int ac = 1; ac < nused; ++ac) {
+          float x2[16], y2[16];
+          const uint32_t ta = t + (uint32_t)(ac * 2 * N16);
+          tmem_ld16x2(ta, ta + (uint32_t)N16, x2, y2);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] += x2[e] + y2[e];
-          } else {
-            tmem_ld16(t + (uint32_t)(ac * N16), x2);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] += x2[e];
-          }
+          for (int e = 0; e < 16; ++e) v[e] += x2[e] + y2[e];
         }
         if (n < N) {
 #pragma unroll
@@ -527,8 +521,8 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
 
 size_t ptc_smem(int B, int N16, int S, int R, int raw_bytes) {
   const int B16 = (B + 15) & ~15;
-  const size_t vplane = (size_t)((N16 * B16 * 2 + 1023) & ~1023);
-  return 1024 + (size_t)R * raw_bytes + 2 * vplane + (size_t)S * 2 * kPlane +
+  const size_t vplanes = (size_t)((2 * N16 * B16 * 2 + 1023) & ~1023);
+  return 1024 + (size_t)R * raw_bytes + vplanes + (size_t)S * 2 * kPlane +
          (256 * 2 + 2 * kMaxCols) * 4 + sizeof(PtcSync) + 16;   // cst[256] float2 + cls + crs
 }
 
@@ -562,8 +556,9 @@ cudaError_t ptc_typed(const PtcArgs& a, cudaStream_t st) {
   }
   const int B16 = (a.B + 15) & ~15;
   const int KC = (B16 + kKC - 1) / kKC;
-  int nacc = 256 / a.N16;          // accumulators per tile buffer (two buffers in 512 columns)
-  nacc = nacc > KC ? KC : nacc;
+  // accumulators of 2 N16 columns per tile buffer (two buffers in 512 columns)
+  int nacc = 256 / (2 * a.N16);
+  nacc = nacc > B16 / 16 ? B16 / 16 : nacc;
   nacc = nacc < 1 ? 1 : nacc;
   const size_t smem = ptc_smem(a.B, a.N16, S, R, rb);
   int dev = 0, sms = 148;
