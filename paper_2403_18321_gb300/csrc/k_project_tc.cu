@@ -555,7 +555,6 @@ cudaError_t ptc_typed(const PtcArgs& a, cudaStream_t st) {
     memset(&xmap, 0, sizeof(xmap));
   }
   const int B16 = (a.B + 15) & ~15;
-  const int KC = (B16 + kKC - 1) / kKC;
   // accumulators of 2 N16 columns per tile buffer (two buffers in 512 columns)
   int nacc = 256 / (2 * a.N16);
   nacc = nacc > B16 / 16 ? B16 / 16 : nacc;
