@@ -55,8 +55,8 @@ constexpr int kConvW = 16;               // converter warps
 constexpr int kEpiW = 4;                 // epilogue warps (one per TMEM lane quarter)
 constexpr int kThr = (2 + kConvW + kEpiW) * 32;
 constexpr int kPlane = kTM * kKC * 2;    // one FP16 plane of an A stage: 16 KB
-constexpr uint32_t kLBO = 128;           // K-adjacent core matrices
-constexpr uint32_t kASBO = (kKC / 8) * 128;   // A: 8-row groups, 1 KB
+// Operands in the 128-byte swizzled K-major layout: one 64-band chunk is one
+// row of 128 bytes per pixel (A) or per column of [V_hi | V_lo] (B).
 constexpr int kMaxCols = 128;            // columns of one launch
 constexpr int kProbe = 32;
 
@@ -121,9 +121,10 @@ k_ptc_bands(const In* __restrict__ cube, int64_t N, int B, const double* __restr
 
 // ------------------------------------------------------------------ k_ptc_vop
 // The B operand of one launch, one CTA per column j < N16 (thread = band):
-// hi and lo FP16 planes [N16][B16] in K-major core-matrix order (8 columns x
-// 8 bands per core matrix; bands in 128-byte steps, 8-column groups in
-// (B16/8)*128-byte steps), the column scale 2^-f_j and the correction c_j.
+// per 64-band chunk c a block of 2 N16 rows of 128 bytes -- row j = V_hi
+// column j, row N16 + j = V_lo column j -- in the 128-byte swizzled K-major
+// layout (unit u of row n at u ^ (n mod 8)); the column scale 2^-f_j and the
+// correction c_j.
 __global__ void __launch_bounds__(256)
 k_ptc_vop(const double* __restrict__ V, int B, int j0, int k, const double* __restrict__ mu,
           const float* __restrict__ shift, const int* __restrict__ escale,
@@ -156,15 +157,15 @@ k_ptc_vop(const double* __restrict__ V, int B, int j0, int k, const double* __re
     colscale[j] = ldexpf(1.f, -f);
     corr[j] = (float)ct;
   }
-  if (b < B16) {
+  if (b < ((B16 + 63) & ~63)) {   // every band of the chunks (0 past B)
     const float x = ldexpf(w, f);
     const __half hi = __float2half_rn(x);
     const __half lo = __float2half_rn(x - __half2float(hi));
-    const size_t plane = (size_t)N16 * B16 * 2;
-    const size_t off = (size_t)(j >> 3) * (B16 / 8) * 128 + (size_t)(b >> 3) * 128 +
-                       (size_t)(j & 7) * 16 + (size_t)(b & 7) * 2;
-    *reinterpret_cast<__half*>(planes + off) = hi;
-    *reinterpret_cast<__half*>(planes + plane + off) = lo;
+    const int c = b >> 6, u = (b & 63) >> 3;
+    unsigned char* blk = planes + (size_t)c * (2 * N16) * 128;
+    const int nh = j, nl = N16 + j;
+    *reinterpret_cast<__half*>(blk + nh * 128 + ((u ^ (nh & 7)) << 4) + (b & 7) * 2) = hi;
+    *reinterpret_cast<__half*>(blk + nl * 128 + ((u ^ (nl & 7)) << 4) + (b & 7) * 2) = lo;
   }
 }
 
@@ -227,13 +228,13 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   const int B = a.B, N16 = a.N16;
   const int B16 = (B + 15) & ~15;
   const int KC = (B16 + kKC - 1) / kKC;                    // K-chunks per tile
-  const int vplane = N16 * B16 * 2;                        // one FP16 plane of V
+  const int vbytes = KC * 2 * N16 * 128;                   // [V_hi | V_lo], all chunks
   constexpr int kRaw = raw_chunk_bytes<In>();
   unsigned char* raw = smem;                               // [R][kRaw] (TMA path)
   // V: the lo plane right after the hi plane, so that [V_hi | V_lo] is one B
   // operand of 2 N16 rows (one MMA gives both products of a K-step)
-  unsigned char* vs = raw + (size_t)R * kRaw;              // [hi|lo][vplane]
-  unsigned char* ops = vs + ((2 * vplane + 1023) & ~1023); // [S][hi|lo][kPlane]
+  unsigned char* vs = raw + (size_t)R * kRaw;              // [KC][2 N16][128]
+  unsigned char* ops = vs + ((vbytes + 1023) & ~1023);     // [S][hi|lo][kPlane]
   float2* cst = reinterpret_cast<float2*>(ops + (size_t)S * 2 * kPlane);  // [256] (2^e, -s 2^e)
   float* cls = reinterpret_cast<float*>(cst + 256);                       // [128] 2^-f
   float* crs = cls + kMaxCols;                                            // [128] c_j
@@ -250,7 +251,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   // ---- set-up: V planes, band and column constants, barriers, TMEM
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.planes);
-    for (int i = tid; i < 2 * vplane / 16; i += kThr) reinterpret_cast<uint4*>(vs)[i] = src[i];
+    for (int i = tid; i < vbytes / 16; i += kThr) reinterpret_cast<uint4*>(vs)[i] = src[i];
   }
   // x = (y - s) 2^e as one FMA: y 2^e is exact (a power of two) and the sum is
   // rounded once, as (y - s) would be before the exact scaling
@@ -308,12 +309,11 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t ops_base = su32(ops), vhi = su32(vs);
-      const uint32_t vsbo = (uint32_t)(B16 / 8) * 128;
       const uint32_t id_both = idesc_f16(2 * N16), id_hi = idesc_f16(N16);
       // descriptors of the operand bases; an offset of d bytes adds d >> 4 to
       // the start-address field (every address stays below 256 KB)
-      const uint64_t dA = sdesc_kmajor(ops_base, kLBO, kASBO);
-      const uint64_t dVh = sdesc_kmajor(vhi, kLBO, vsbo);   // [V_hi | V_lo] from here
+      const uint64_t dA = sdesc_sw128(ops_base);
+      const uint64_t dV = sdesc_sw128(vhi);   // chunk c: [V_hi | V_lo] at c * 2 N16 * 128
       Ring ro(S);
       bool ok = true;
       for (int i = 0; i < nt && ok; ++i) {
@@ -334,12 +334,12 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
           const uint32_t nz = (f0 | f1) | (f2 | f3);
           const uint64_t ahi = dA + (uint64_t)((o * 2 * kPlane) >> 4), alo = ahi + (kPlane >> 4);
           const int ksteps = (B16 - c * kKC) < kKC ? (B16 - c * kKC) / 16 : kKC / 16;
-          const uint64_t kb0 = (uint64_t)(c * (kKC / 8) * 128 >> 4);
+          const uint64_t vc = dV + (uint64_t)((c * 2 * N16 * 128) >> 4);
           for (int kk = 0; kk < ksteps; ++kk, ++ks) {
-            const uint64_t ka = (uint64_t)(kk * 2 * kLBO >> 4), kb = kb0 + (uint64_t)(kk * 2 * 128 >> 4);
+            const uint64_t kofs = (uint64_t)(kk * 32 >> 4);     // 16 K-values = 32 bytes
             const uint32_t acc = acc0 + (uint32_t)(ai * 2 * N16);
-            mma_f16(acc, ahi + ka, dVh + kb, id_both, ks < nacc ? 0u : 1u);
-            if (nz) mma_f16(acc, alo + ka, dVh + kb, id_hi, 1u);
+            mma_f16(acc, ahi + kofs, vc + kofs, id_both, ks < nacc ? 0u : 1u);
+            if (nz) mma_f16(acc, alo + kofs, vc + kofs, id_hi, 1u);
             ai = ai + 1 == nacc ? 0 : ai + 1;
           }
           mma_commit(&sy->opempty[o]);
@@ -426,11 +426,13 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       // row pr of the A stage, bands gp*16 .. +15 = core matrices 2gp, 2gp+1
       unsigned char* hi = ops + (size_t)(o * 2) * kPlane;
       unsigned char* lo = hi + kPlane;
-      const uint32_t off = (uint32_t)(pr >> 3) * kASBO + (uint32_t)(2 * gp) * kLBO + (pr & 7) * 16;
-      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<uint4*>(hi + off + kLBO) = make_uint4(h[4], h[5], h[6], h[7]);
-      *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-      *reinterpret_cast<uint4*>(lo + off + kLBO) = make_uint4(l[4], l[5], l[6], l[7]);
+      // row pr, units 2 gp and 2 gp + 1, swizzled
+      const uint32_t o0 = (uint32_t)pr * 128 + ((uint32_t)((2 * gp) ^ (pr & 7)) << 4);
+      const uint32_t o1 = (uint32_t)pr * 128 + ((uint32_t)((2 * gp + 1) ^ (pr & 7)) << 4);
+      *reinterpret_cast<uint4*>(hi + o0) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(hi + o1) = make_uint4(h[4], h[5], h[6], h[7]);
+      *reinterpret_cast<uint4*>(lo + o0) = make_uint4(l[0], l[1], l[2], l[3]);
+      *reinterpret_cast<uint4*>(lo + o1) = make_uint4(l[4], l[5], l[6], l[7]);
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) {
@@ -520,8 +522,8 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
 }
 
 size_t ptc_smem(int B, int N16, int S, int R, int raw_bytes) {
-  const int B16 = (B + 15) & ~15;
-  const size_t vplanes = (size_t)((2 * N16 * B16 * 2 + 1023) & ~1023);
+  const int KC = (((B + 15) & ~15) + kKC - 1) / kKC;
+  const size_t vplanes = (size_t)((KC * 2 * N16 * 128 + 1023) & ~1023);
   return 1024 + (size_t)R * raw_bytes + vplanes + (size_t)S * 2 * kPlane +
          (256 * 2 + 2 * kMaxCols) * 4 + sizeof(PtcSync) + 16;   // cst[256] float2 + cls + crs
 }
@@ -575,9 +577,9 @@ cudaError_t ptc_typed(const PtcArgs& a, cudaStream_t st) {
 }  // namespace
 
 size_t project_tc_planes_bytes(int B, int k) {
-  const int B16 = (B + 15) & ~15;
+  const int KC = (((B + 15) & ~15) + kKC - 1) / kKC;
   const int N16 = ((k < kMaxCols ? k : kMaxCols) + 15) & ~15;
-  return (size_t)2 * N16 * B16 * 2;
+  return (size_t)KC * 2 * N16 * 128;
 }
 
 cudaError_t launch_project_tc(const void* cube, pca_dtype dt, int64_t N, int B, int k,

@@ -22,6 +22,14 @@ __device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t addr, uint32_t lbo, ui
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
+// Shared-memory operand descriptor, K-major with the 128-byte swizzle: rows of
+// 128 bytes (64 FP16 K-values), the 16-byte units of row r stored at unit
+// index u ^ (r mod 8), 8-row groups 1024 bytes apart (the atom must be 1024-byte
+// aligned).  A K-step of 16 values inside the atom adds 32 bytes to the start.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
 // kind::f16 instruction descriptor: D F32, A/B F16 (format 0), both K-major,
 // M = 128, N = n.
 __device__ __forceinline__ uint32_t idesc_f16(int n) {
