@@ -307,46 +307,53 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      const uint32_t ops_base = su32(ops), vhi = su32(vs);
-      const uint32_t id_both = idesc_f16(2 * N16), id_hi = idesc_f16(N16);
-      // descriptors of the operand bases; an offset of d bytes adds d >> 4 to
-      // the start-address field (every address stays below 256 KB)
-      const uint64_t dA = sdesc_sw128(ops_base);
-      const uint64_t dV = sdesc_sw128(vhi);   // chunk c: [V_hi | V_lo] at c * 2 N16 * 128
-      Ring ro(S);
-      bool ok = true;
-      for (int i = 0; i < nt && ok; ++i) {
-        const int bf = i & 1;
-        // the epilogue has read this buffer's previous tile (i - 2)
-        if (i >= 2 && !mbar_wait(&sy->tfree[bf], ((i - 2) >> 1) & 1, &sy->abort)) break;
-        tc_fence_after();
-        const uint32_t acc0 = tbase + (uint32_t)(bf * accw);
-        int ai = 0, ks = 0;      // rotating accumulator, K-step of the tile
-        for (int c = 0; c < KC; ++c, ro.next()) {
-          const int o = ro.idx;
-          if (!mbar_wait(&sy->opfull[o], ro.phase, &sy->abort)) { ok = false; break; }
-          tc_fence_after();
-          uint32_t f0, f1, f2, f3;   // the 16 warps' flags in one 16-byte load
-          asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                       : "=r"(f0), "=r"(f1), "=r"(f2), "=r"(f3)
-                       : "r"(su32(sy->lo_nz[o])));
-          const uint32_t nz = (f0 | f1) | (f2 | f3);
-          const uint64_t ahi = dA + (uint64_t)((o * 2 * kPlane) >> 4), alo = ahi + (kPlane >> 4);
-          const int ksteps = (B16 - c * kKC) < kKC ? (B16 - c * kKC) / 16 : kKC / 16;
-          const uint64_t vc = dV + (uint64_t)((c * 2 * N16 * 128) >> 4);
-          for (int kk = 0; kk < ksteps; ++kk, ++ks) {
-            const uint64_t kofs = (uint64_t)(kk * 32 >> 4);     // 16 K-values = 32 bytes
-            const uint32_t acc = acc0 + (uint32_t)(ai * 2 * N16);
-            mma_f16(acc, ahi + kofs, vc + kofs, id_both, ks < nacc ? 0u : 1u);
-            if (nz) mma_f16(acc, alo + kofs, vc + kofs, id_hi, 1u);
-            ai = ai + 1 == nacc ? 0 : ai + 1;
-          }
-          mma_commit(&sy->opempty[o]);
-        }
-        if (ok) mma_commit(&sy->tdone[bf]);
+    // The whole warp runs this loop (uniform control flow); lane 0 waits on the
+    // barriers and broadcasts the outcome, one elected lane issues each MMA.
+    const uint32_t ops_base = su32(ops), vhi = su32(vs);
+    const uint32_t id_both = idesc_f16(2 * N16), id_hi = idesc_f16(N16);
+    // descriptors of the operand bases; an offset of d bytes adds d >> 4 to
+    // the start-address field (every address stays below 256 KB)
+    const uint64_t dA = sdesc_sw128(ops_base);
+    const uint64_t dV = sdesc_sw128(vhi);   // chunk c: [V_hi | V_lo] at c * 2 N16 * 128
+    Ring ro(S);
+    bool ok = true;
+    for (int i = 0; i < nt && ok; ++i) {
+      const int bf = i & 1;
+      // the epilogue has read this buffer's previous tile (i - 2)
+      if (i >= 2) {
+        int w = 1;
+        if (lane == 0) w = mbar_wait(&sy->tfree[bf], ((i - 2) >> 1) & 1, &sy->abort) ? 1 : 0;
+        if (!__shfl_sync(kFull, w, 0)) break;
       }
+      tc_fence_after();
+      const uint32_t acc0 = tbase + (uint32_t)(bf * accw);
+      int ai = 0, ks = 0;      // rotating accumulator, K-step of the tile
+      for (int c = 0; c < KC; ++c, ro.next()) {
+        const int o = ro.idx;
+        int w = 1;
+        if (lane == 0) w = mbar_wait(&sy->opfull[o], ro.phase, &sy->abort) ? 1 : 0;
+        if (!__shfl_sync(kFull, w, 0)) { ok = false; break; }
+        tc_fence_after();
+        uint32_t f0, f1, f2, f3;   // the 16 warps' flags in one 16-byte load
+        asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(f0), "=r"(f1), "=r"(f2), "=r"(f3)
+                     : "r"(su32(sy->lo_nz[o])));
+        const uint32_t nz = (f0 | f1) | (f2 | f3);
+        const uint64_t ahi = dA + (uint64_t)((o * 2 * kPlane) >> 4), alo = ahi + (kPlane >> 4);
+        const int ksteps = (B16 - c * kKC) < kKC ? (B16 - c * kKC) / 16 : kKC / 16;
+        const uint64_t vc = dV + (uint64_t)((c * 2 * N16 * 128) >> 4);
+        for (int kk = 0; kk < ksteps; ++kk, ++ks) {
+          const uint64_t kofs = (uint64_t)(kk * 32 >> 4);     // 16 K-values = 32 bytes
+          const uint32_t acc = acc0 + (uint32_t)(ai * 2 * N16);
+          mma_f16_warp(acc, ahi + kofs, vc + kofs, id_both, ks < nacc ? 0u : 1u);
+          if (nz) mma_f16_warp(acc, alo + kofs, vc + kofs, id_hi, 1u);
+          ai = ai + 1 == nacc ? 0 : ai + 1;
+        }
+        mma_commit_warp(&sy->opempty[o]);
+      }
+      if (ok) mma_commit_warp(&sy->tdone[bf]);
     }
+    __syncwarp();
   } else if (warp >= 2 && warp < 2 + kConvW) {
     // ------------------------------------------------------------ converters
     const int ct = tid - 64, cw = warp - 2;
