@@ -223,58 +223,67 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      const uint32_t ops_base = su32(ops);
-      Ring ro(kOpStages);  // operand-ring position, continued across items
-      bool ok = true;
-      for (int i = 0; i < nitems && ok; ++i) {
-        const TcItem it = tc_item(one, T, items, cta_items, i);
-        const int B = it.t.B;
-        const int R16 = (B + 15) & ~15;               // bands padded to the 16-row MMA granule
-        const bool two_tiles = B > 128;
-        const int N0 = R16;                           // tile 0 columns: bands 0..R16-1
-        const int N1 = two_tiles ? (R16 - 128) : 0;   // tile 1 columns: bands 128..R16-1
-        const uint32_t id0 = idesc_f16(N0), id1 = idesc_f16(N1 > 0 ? N1 : 16);
-        // the accumulators are free once the previous item's epilogue read them
-        if (i > 0 && !mbar_wait(&sb->tfree, (i - 1) & 1, &sb->abort)) break;
+    // The whole warp runs this loop (uniform control flow keeps the
+    // descriptors in uniform registers); lane 0 waits on the barriers and
+    // broadcasts the outcome, one elected lane issues each MMA.
+    const uint32_t ops_base = su32(ops);
+    const uint64_t d0 = sdesc(ops_base);   // an offset of d bytes adds d >> 4
+    Ring ro(kOpStages);  // operand-ring position, continued across items
+    bool ok = true;
+    for (int i = 0; i < nitems && ok; ++i) {
+      const TcItem it = tc_item(one, T, items, cta_items, i);
+      const int B = it.t.B;
+      const int R16 = (B + 15) & ~15;               // bands padded to the 16-row MMA granule
+      const bool two_tiles = B > 128;
+      const int N0 = R16;                           // tile 0 columns: bands 0..R16-1
+      const int N1 = two_tiles ? (R16 - 128) : 0;   // tile 1 columns: bands 128..R16-1
+      const uint32_t id0 = idesc_f16(N0), id1 = idesc_f16(N1 > 0 ? N1 : 16);
+      // the accumulators are free once the previous item's epilogue read them
+      if (i > 0) {
+        int w = 1;
+        if (lane == 0) w = mbar_wait(&sb->tfree, (i - 1) & 1, &sb->abort) ? 1 : 0;
+        if (!__shfl_sync(kFull, w, 0)) break;
+      }
+      tc_fence_after();
+      bool first = true;
+      const uint32_t t1 = tbase + (uint32_t)N0;
+      constexpr uint64_t r128 = (uint64_t)((128 / 8) * kSBO) >> 4;   // tile 1 rows
+      for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ro.next()) {
+        const int o = ro.idx;
+        int w = 1;
+        if (lane == 0) w = mbar_wait(&sb->opfull[o], ro.phase, &sb->abort) ? 1 : 0;
+        if (!__shfl_sync(kFull, w, 0)) { ok = false; break; }
         tc_fence_after();
-        bool first = true;
-        for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ro.next()) {
-          const int o = ro.idx;
-          if (!mbar_wait(&sb->opfull[o], ro.phase, &sb->abort)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t hi = ops_base + (uint32_t)(o * 2) * kOpBytes;
-          const uint32_t lo = hi + kOpBytes;
-          // the converters' flags (written before their arrivals on opfull)
-          int nz = 0;
+        // the converters' flags (written before their arrivals on opfull)
+        int nz = 0;
 #pragma unroll
-          for (int w = 0; w < kConvWarps; ++w) nz |= ((volatile int*)sb->lo_nz[o])[w];
+        for (int cw = 0; cw < kConvWarps; ++cw) nz |= ((volatile int*)sb->lo_nz[o])[cw];
+        const uint64_t hi = d0 + (uint64_t)(((uint32_t)(o * 2) * kOpBytes) >> 4);
+        const uint64_t lo = hi + (uint64_t)(kOpBytes >> 4);
 #pragma unroll
-          for (int kk = 0; kk < kKC / 16; ++kk) {
-            const uint32_t ko = kk * 2 * kLBO;
-            const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;
-            // tile 0: rows 0..127 (A) x rows 0..N0-1 (B)
-            mma_f16(tbase, sdesc(hi + ko), sdesc(hi + ko), id0, acc0);
+        for (int kk = 0; kk < kKC / 16; ++kk) {
+          const uint64_t ko = (uint64_t)((kk * 2 * kLBO) >> 4);
+          const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;
+          // tile 0: rows 0..127 (A) x rows 0..N0-1 (B)
+          mma_f16_warp(tbase, hi + ko, hi + ko, id0, acc0);
+          if (nz) {
+            mma_f16_warp(tbase, hi + ko, lo + ko, id0, 1u);
+            mma_f16_warp(tbase, lo + ko, hi + ko, id0, 1u);
+          }
+          if (two_tiles) {
+            mma_f16_warp(t1, hi + r128 + ko, hi + r128 + ko, id1, acc0);
             if (nz) {
-              mma_f16(tbase, sdesc(hi + ko), sdesc(lo + ko), id0, 1u);
-              mma_f16(tbase, sdesc(lo + ko), sdesc(hi + ko), id0, 1u);
-            }
-            if (two_tiles) {
-              const uint32_t r128 = (128 / 8) * kSBO;
-              const uint32_t t1 = tbase + (uint32_t)N0;
-              mma_f16(t1, sdesc(hi + r128 + ko), sdesc(hi + r128 + ko), id1, acc0);
-              if (nz) {
-                mma_f16(t1, sdesc(hi + r128 + ko), sdesc(lo + r128 + ko), id1, 1u);
-                mma_f16(t1, sdesc(lo + r128 + ko), sdesc(hi + r128 + ko), id1, 1u);
-              }
+              mma_f16_warp(t1, hi + r128 + ko, lo + r128 + ko, id1, 1u);
+              mma_f16_warp(t1, lo + r128 + ko, hi + r128 + ko, id1, 1u);
             }
           }
-          first = false;
-          mma_commit(&sb->opempty[o]);  // operand stage free once these MMAs finished
         }
-        mma_commit(&sb->done);          // this item's MMAs finished
+        first = false;
+        mma_commit_warp(&sb->opempty[o]);  // operand stage free once these MMAs finished
       }
+      mma_commit_warp(&sb->done);          // this item's MMAs finished
     }
+    __syncwarp();
   } else {
     // ---------------------------------------------------------- converters
     const int ct = tid - 64;
