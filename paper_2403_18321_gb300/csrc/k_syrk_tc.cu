@@ -49,8 +49,12 @@ constexpr int kRows = 256;              // operand rows (bands, padded to 16)
 constexpr int kConvWarps = 16;
 constexpr int kThreads = (2 + kConvWarps) * 32;
 constexpr int kOpBytes = kRows * kKC * 2;        // one FP16 operand (hi or lo): 16 KB
-constexpr uint32_t kLBO = 128;                   // K-adjacent core matrices
-constexpr uint32_t kSBO = (kKC / 8) * 128;       // 8-row groups: 512 B
+// Operands in the MN-major layout with the 128-byte swizzle, in the cube's own
+// order: per pixel (K) a row of 64 bands (MN) = 128 bytes; 8 pixel rows form a
+// 1 KB swizzle atom; the 4 atoms of a 32-pixel chunk make a 4 KB block of 64
+// bands; the blocks of bands 0-63, 64-127, ... follow each other.
+constexpr uint32_t kMnSBO = 1024;                // next 8 pixels (K)
+constexpr uint32_t kMnLBO = (kKC / 8) * 1024;    // next 64 bands (MN): 4 KB
 constexpr int kTmemCols = 512;
 constexpr int kProbe = 32;               // pixels of the band probe
 constexpr int kS1Flush = 16;             // chunks summed in FP32 before the FP64 add
@@ -68,8 +72,13 @@ struct __align__(8) SyncBlock {
   int abort;
 };
 
-// K-major operand descriptor of the ring layout (kLBO, kSBO)
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) { return sdesc_kmajor(addr, kLBO, kSBO); }
+// MN-major 128-byte swizzled operand descriptor of the ring layout
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(kMnLBO >> 4) << 16) |
+         ((uint64_t)(kMnSBO >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+// kind::f16 instruction descriptor with both operands MN-major
+__device__ __forceinline__ uint32_t idesc_mn(int n) { return idesc_f16(n) | (1u << 15) | (1u << 16); }
 
 template <typename In>
 __device__ __forceinline__ float elem(const In* p) { return to_f32<In>(*p); }
@@ -237,7 +246,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
       const bool two_tiles = B > 128;
       const int N0 = R16;                           // tile 0 columns: bands 0..R16-1
       const int N1 = two_tiles ? (R16 - 128) : 0;   // tile 1 columns: bands 128..R16-1
-      const uint32_t id0 = idesc_f16(N0), id1 = idesc_f16(N1 > 0 ? N1 : 16);
+      const uint32_t id0 = idesc_mn(N0), id1 = idesc_mn(N1 > 0 ? N1 : 16);
       // the accumulators are free once the previous item's epilogue read them
       if (i > 0) {
         int w = 1;
@@ -247,7 +256,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
       tc_fence_after();
       bool first = true;
       const uint32_t t1 = tbase + (uint32_t)N0;
-      constexpr uint64_t r128 = (uint64_t)((128 / 8) * kSBO) >> 4;   // tile 1 rows
+      constexpr uint64_t r128 = (uint64_t)(2 * kMnLBO) >> 4;   // tile 1: bands 128..
       for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ro.next()) {
         const int o = ro.idx;
         int w = 1;
@@ -262,7 +271,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         const uint64_t lo = hi + (uint64_t)(kOpBytes >> 4);
 #pragma unroll
         for (int kk = 0; kk < kKC / 16; ++kk) {
-          const uint64_t ko = (uint64_t)((kk * 2 * kLBO) >> 4);
+          const uint64_t ko = (uint64_t)((kk * 2 * kMnSBO) >> 4);   // pixels 16 kk ..
           const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;
           // tile 0: rows 0..127 (A) x rows 0..N0-1 (B)
           mma_f16_warp(tbase, hi + ko, hi + ko, id0, acc0);
@@ -356,23 +365,44 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         }
         conv_sync();
       }
-      // Item = (band, 8-pixel group); a thread owns the same items in every
-      // chunk (at most two for B <= 256), so their decode happens once.
-      const int nitm = B * (kKC / 8);
-      int ib[2], ipg[2], ioff[2];
-      float ish[2], isc[2], s1f[2] = {0.f, 0.f};
-      double s1d[2] = {0.0, 0.0};
+      // Per-band constants of this cube as (2^e, -s 2^e) pairs, x = y 2^e - s 2^e
+      // in one FMA (y 2^e is exact), laid out [k][group] as float4 of bands
+      // 8 group + 2k and + 1, so that the lanes of a warp (consecutive groups)
+      // read consecutive 16-byte units; the band sums restart at zero.
+      const int G8 = (B + 7) >> 3;                  // 8-band groups
+      float4* cstT = reinterpret_cast<float4*>(pmin);   // [4][32] (pmin/pmax: probe only)
+      for (int e = ct; e < 4 * 32; e += kConvWarps * 32) {
+        const int kq = e >> 5, gq = e & 31, b0 = 8 * gq + 2 * kq;
+        const float sa = b0 < B ? ldexpf(1.f, sesc[b0]) : 0.f;
+        const float sb2 = b0 + 1 < B ? ldexpf(1.f, sesc[b0 + 1]) : 0.f;
+        cstT[e] = make_float4(sa, b0 < B ? -shs[b0] * sa : 0.f, sb2,
+                              b0 + 1 < B ? -shs[b0 + 1] * sb2 : 0.f);
+      }
+      for (int b = ct; b < kRows; b += kConvWarps * 32) psum[b] = 0.0;
+      conv_sync();
+      // Units (pixel p of the chunk, 8-band group gu): a thread owns the same
+      // two units in every chunk (32 x G8 <= 1024 units).  Its values are
+      // written as one 16-byte row unit of the MN-major operand with the
+      // 128-byte swizzle: 64-band blocks 4 KB apart, 8-pixel groups 1 KB apart
+      // inside a block, unit gu mod 8 of pixel row p at (gu ^ p) mod 8.
+      int up[2], ug[2];
+      uint32_t uoff[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int w = ct + u * kConvWarps * 32;
-        ipg[u] = w < nitm ? w / B : -1;
-        ib[u] = w < nitm ? w - ipg[u] * B : 0;
-        const int row = ib[u];
-        ioff[u] = (row >> 3) * (int)kSBO + (ipg[u] < 0 ? 0 : ipg[u]) * 128 + (row & 7) * 16;
-        ish[u] = shs[row];
-        isc[u] = ldexpf(1.f, sesc[row]);
+        up[u] = w < 32 * G8 ? w / G8 : -1;
+        ug[u] = w < 32 * G8 ? w - up[u] * G8 : 0;
+        const int pp = up[u] < 0 ? 0 : up[u];
+        uoff[u] = (uint32_t)(ug[u] >> 3) * kMnLBO + (uint32_t)(pp >> 3) * kMnSBO + (pp & 7) * 128 +
+                  ((uint32_t)((ug[u] & 7) ^ (pp & 7)) << 4);
       }
-      int out_of_range = 0;   // a scaled value of this item left the FP16 range
+      const bool vec = (B * (int)sizeof(In)) % 16 == 0;
+      float s1f[2][8];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) s1f[u][e] = 0.f;
+      float mx = 0.f;           // largest |x| of this item: above the FP16 range -> SIMT pass
       const int cw = warp - 2;  // converter warp index
       int c = 0;
       for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ++c, rs.next(), ro.next()) {
@@ -396,39 +426,54 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         uint32_t lo_bits = 0;    // OR of this thread's lo parts in this chunk
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          const int pg = ipg[u], b = ib[u];
-          if (pg < 0) continue;
-          uint32_t h[4], l[4];
-          const float sh = ish[u], sc = isc[u];
-          float x[8];
-          if (full) {
-            const In* src = st + pg * 8 * B + b;
+          const int pp = up[u], gu = ug[u];
+          if (pp < 0) continue;
+          const int b0 = 8 * gu;
+          float y[8];
+          if (full && vec && b0 + 8 <= B) {
+            const In* src = st + pp * B + b0;
+            if constexpr (sizeof(In) == 4) {
+              const float4 a0 = *reinterpret_cast<const float4*>(src);
+              const float4 a1 = *reinterpret_cast<const float4*>(src + 4);
+              y[0] = a0.x; y[1] = a0.y; y[2] = a0.z; y[3] = a0.w;
+              y[4] = a1.x; y[5] = a1.y; y[6] = a1.z; y[7] = a1.w;
+            } else {
+              const uint4 v = *reinterpret_cast<const uint4*>(src);
+              const In* h8 = reinterpret_cast<const In*>(&v);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) x[k] = (elem(src + k * B) - sh) * sc;
+              for (int e = 0; e < 8; ++e) y[e] = to_f32<In>(h8[e]);
+            }
           } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const int p = pg * 8 + k;
-              const int e = p * B + b;
-              float v = 0.f;
-              if (p < cp) v = ((e < copied ? elem(st + e) : elem(gsrc + e)) - sh) * sc;
-              x[k] = v;
+            for (int e = 0; e < 8; ++e) {
+              const int el = pp * B + b0 + e;
+              y[e] = (pp < cp && b0 + e < B)
+                         ? (el < copied ? elem(st + el) : elem(gsrc + el)) : 0.f;
             }
           }
-          // NaN compares false, so it counts as out of range too
+          float x[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) out_of_range |= !(fabsf(x[k]) <= 65504.f);
-          s1f[u] += ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            h[k] = pack_f16x2(x[2 * k], x[2 * k + 1]);
-            float a, bb;
-            unpack_f16x2(h[k], a, bb);
-            l[k] = pack_f16x2(x[2 * k] - a, x[2 * k + 1] - bb);
-            lo_bits |= l[k];
+          for (int kq = 0; kq < 4; ++kq) {
+            const float4 k4 = cstT[kq * 32 + gu];
+            // bands past B and pixels past the chunk contribute 0
+            const bool v0 = pp < cp && b0 + 2 * kq < B, v1 = pp < cp && b0 + 2 * kq + 1 < B;
+            x[2 * kq] = v0 ? fmaf(y[2 * kq], k4.x, k4.y) : 0.f;
+            x[2 * kq + 1] = v1 ? fmaf(y[2 * kq + 1], k4.z, k4.w) : 0.f;
           }
-          *reinterpret_cast<uint4*>(hi + ioff[u]) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(lo + ioff[u]) = make_uint4(l[0], l[1], l[2], l[3]);
+          uint32_t h[4], l[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
+            s1f[u][2 * e] += x[2 * e];
+            s1f[u][2 * e + 1] += x[2 * e + 1];
+            h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
+            float a, bb;
+            unpack_f16x2(h[e], a, bb);
+            l[e] = pack_f16x2(x[2 * e] - a, x[2 * e + 1] - bb);
+            lo_bits |= l[e];
+          }
+          *reinterpret_cast<uint4*>(hi + uoff[u]) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>(lo + uoff[u]) = make_uint4(l[0], l[1], l[2], l[3]);
         }
         const int any_lo = __any_sync(kFull, lo_bits != 0u);
         fence_proxy_async();
@@ -438,21 +483,30 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
           mbar_arrive(&sb->opfull[o]);
           mbar_arrive(&sb->empty[s]);
         }
-        if ((c + 1) % kS1Flush == 0) {
+        if ((c + 1) % kS1Flush == 0) {   // FP32 sums of 16 chunks into the FP64 band sums
 #pragma unroll
-          for (int u = 0; u < 2; ++u) { s1d[u] += (double)s1f[u]; s1f[u] = 0.f; }
+          for (int u = 0; u < 2; ++u)
+            if (up[u] >= 0)
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                if (8 * ug[u] + e < B) atomicAdd(&psum[8 * ug[u] + e], (double)s1f[u][e]);
+                s1f[u][e] = 0.f;
+              }
         }
       }
-      if (__any_sync(kFull, out_of_range) && lane == 0) atomicOr(&it.t.hdr->cov_range, 1);
-      // band sums: the four 8-pixel groups of a band meet in shared memory
+      // NaN compares false: a non-finite value is reported by the finalisation
+      if (__any_sync(kFull, !(mx <= 65504.f) && mx == mx) && lane == 0)
+        atomicOr(&it.t.hdr->cov_range, 1);
 #pragma unroll
       for (int u = 0; u < 2; ++u)
-        if (ipg[u] >= 0) psum[ipg[u] * kRows + ib[u]] = s1d[u] + (double)s1f[u];
+        if (up[u] >= 0)
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (8 * ug[u] + e < B) atomicAdd(&psum[8 * ug[u] + e], (double)s1f[u][e]);
       // barrier, and a uniform decision to stop after an abandoned wait
       const bool aborted = conv_or(*(volatile int*)&sb->abort) != 0;
       for (int b = ct; b < B; b += kConvWarps * 32)
-        it.t.s1_part[(size_t)g * B + b] = ldexp(
-            (psum[b] + psum[kRows + b]) + (psum[2 * kRows + b] + psum[3 * kRows + b]), -sesc[b]);
+        it.t.s1_part[(size_t)g * B + b] = ldexp(psum[b], -sesc[b]);
       // ---------------------------------------------------------- epilogue
       if (warp >= 2 && warp < 6) {
         int okw = 0;
