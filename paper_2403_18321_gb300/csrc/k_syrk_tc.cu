@@ -12,11 +12,13 @@
 //               pixels spread through the cube and e a power-of-two scale,
 //               both computed by every CTA from the same pixels), split into
 //               FP16 hi = fp16(x), lo = fp16(x - hi) -- 22 significant bits
-//               of x -- written transposed ([band][pixel], K-major core-
-//               matrix layout) into a 3-stage operand ring, and keep the
-//               band sums S1 = sum x of the values they converted (FP32 over
-//               16 chunks, then FP64); each warp also flags whether any lo of
-//               its values is non-zero;
+//               of x -- written in the cube's own [pixel][band] order as
+//               MN-major operands with the 128-byte swizzle (16-byte vector
+//               loads and stores) into a 3-stage operand ring, and keep the
+//               band sums S1 = sum x of the values they converted (FP32 per
+//               thread over 16 chunks, added by FP32 shared atomics into the
+//               item's row); each warp also flags whether any lo of its values
+//               is non-zero;
 //   warp 1      MMA issuer (one thread): D += hi hi^T + hi lo^T + lo hi^T
 //               for the upper block-triangle (row tile 0: bands 0-127 x all;
 //               row tile 1: bands 128-255 x bands 128-255) with FP32
@@ -378,7 +380,12 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         cstT[e] = make_float4(sa, b0 < B ? -shs[b0] * sa : 0.f, sb2,
                               b0 + 1 < B ? -shs[b0 + 1] * sb2 : 0.f);
       }
-      for (int b = ct; b < kRows; b += kConvWarps * 32) psum[b] = 0.0;
+      // band sums: each thread's FP32 partials of 16 chunks are added with native
+      // FP32 shared atomics into one row of the item's band sums, read after the
+      // barrier at the end of the item (no barrier inside the chunk loop, which
+      // a warp may leave early after an abandoned wait)
+      float* s1row = reinterpret_cast<float*>(pmax);   // [kRows] (pmax: probe only otherwise)
+      for (int b = ct; b < kRows; b += kConvWarps * 32) s1row[b] = 0.f;
       conv_sync();
       // Units (pixel p of the chunk, 8-band group gu): a thread owns the same
       // two units in every chunk (32 x G8 <= 1024 units).  Its values are
@@ -483,13 +490,13 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
           mbar_arrive(&sb->opfull[o]);
           mbar_arrive(&sb->empty[s]);
         }
-        if ((c + 1) % kS1Flush == 0) {   // FP32 sums of 16 chunks into the FP64 band sums
+        if ((c + 1) % kS1Flush == 0) {   // FP32 partials of 16 chunks into the item's row
 #pragma unroll
           for (int u = 0; u < 2; ++u)
             if (up[u] >= 0)
 #pragma unroll
               for (int e = 0; e < 8; ++e) {
-                if (8 * ug[u] + e < B) atomicAdd(&psum[8 * ug[u] + e], (double)s1f[u][e]);
+                if (8 * ug[u] + e < B) atomicAdd(&s1row[8 * ug[u] + e], s1f[u][e]);
                 s1f[u][e] = 0.f;
               }
         }
@@ -502,11 +509,11 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         if (up[u] >= 0)
 #pragma unroll
           for (int e = 0; e < 8; ++e)
-            if (8 * ug[u] + e < B) atomicAdd(&psum[8 * ug[u] + e], (double)s1f[u][e]);
+            if (8 * ug[u] + e < B) atomicAdd(&s1row[8 * ug[u] + e], s1f[u][e]);
       // barrier, and a uniform decision to stop after an abandoned wait
       const bool aborted = conv_or(*(volatile int*)&sb->abort) != 0;
       for (int b = ct; b < B; b += kConvWarps * 32)
-        it.t.s1_part[(size_t)g * B + b] = ldexp(psum[b], -sesc[b]);
+        it.t.s1_part[(size_t)g * B + b] = ldexp((double)s1row[b], -sesc[b]);
       // ---------------------------------------------------------- epilogue
       if (warp >= 2 && warp < 6) {
         int okw = 0;
