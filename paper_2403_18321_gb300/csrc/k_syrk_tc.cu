@@ -16,9 +16,9 @@
 //               MN-major operands with the 128-byte swizzle (16-byte vector
 //               loads and stores) into a 3-stage operand ring, and keep the
 //               band sums S1 = sum x of the values they converted (FP32 per
-//               thread over 16 chunks, added by FP32 shared atomics into the
-//               item's row); each warp also flags whether any lo of its values
-//               is non-zero;
+//               thread over the item -- at most 64 chunks, exact for 16-bit
+//               cubes -- then FP64 over the 32 pixel rows in a fixed order);
+//               each warp also flags whether any lo of its values is non-zero;
 //   warp 1      MMA issuer (one thread): D += hi hi^T + hi lo^T + lo hi^T
 //               for the upper block-triangle (row tile 0: bands 0-127 x all;
 //               row tile 1: bands 128-255 x bands 128-255) with FP32
@@ -59,7 +59,6 @@ constexpr uint32_t kMnSBO = 1024;                // next 8 pixels (K)
 constexpr uint32_t kMnLBO = (kKC / 8) * 1024;    // next 64 bands (MN): 4 KB
 constexpr int kTmemCols = 512;
 constexpr int kProbe = 32;               // pixels of the band probe
-constexpr int kS1Flush = 16;             // chunks summed in FP32 before the FP64 add
 
 struct __align__(8) SyncBlock {
   uint64_t full[kMaxStages];
@@ -380,12 +379,6 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         cstT[e] = make_float4(sa, b0 < B ? -shs[b0] * sa : 0.f, sb2,
                               b0 + 1 < B ? -shs[b0 + 1] * sb2 : 0.f);
       }
-      // band sums: each thread's FP32 partials of 16 chunks are added with native
-      // FP32 shared atomics into one row of the item's band sums, read after the
-      // barrier at the end of the item (no barrier inside the chunk loop, which
-      // a warp may leave early after an abandoned wait)
-      float* s1row = reinterpret_cast<float*>(pmax);   // [kRows] (pmax: probe only otherwise)
-      for (int b = ct; b < kRows; b += kConvWarps * 32) s1row[b] = 0.f;
       conv_sync();
       // Units (pixel p of the chunk, 8-band group gu): a thread owns the same
       // two units in every chunk (32 x G8 <= 1024 units).  Its values are
@@ -490,30 +483,31 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
           mbar_arrive(&sb->opfull[o]);
           mbar_arrive(&sb->empty[s]);
         }
-        if ((c + 1) % kS1Flush == 0) {   // FP32 partials of 16 chunks into the item's row
-#pragma unroll
-          for (int u = 0; u < 2; ++u)
-            if (up[u] >= 0)
-#pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                if (8 * ug[u] + e < B) atomicAdd(&s1row[8 * ug[u] + e], s1f[u][e]);
-                s1f[u][e] = 0.f;
-              }
-        }
       }
       // NaN compares false: a non-finite value is reported by the finalisation
       if (__any_sync(kFull, !(mx <= 65504.f) && mx == mx) && lane == 0)
         atomicOr(&it.t.hdr->cov_range, 1);
+      // band sums: the 32 pixel rows' FP32 partials of every band meet in the
+      // probe buffer, 8 rows at a time, and are added in FP64 in a fixed order
+      // (the same bits on every run); the barriers are outside the chunk loop
+      float* s1buf = reinterpret_cast<float*>(psum);   // [8][kRows] (psum: probe only otherwise)
+      double s1tot = 0.0;                              // band ct (ct < B)
+      for (int r = 0; r < 4; ++r) {
+        conv_sync();
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
-        if (up[u] >= 0)
+        for (int u = 0; u < 2; ++u)
+          if (up[u] >= 8 * r && up[u] < 8 * r + 8)
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            if (8 * ug[u] + e < B) atomicAdd(&s1row[8 * ug[u] + e], s1f[u][e]);
+            for (int e = 0; e < 8; ++e)
+              s1buf[(up[u] - 8 * r) * kRows + 8 * ug[u] + e] = s1f[u][e];
+        conv_sync();
+        if (ct < B)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) s1tot += (double)s1buf[q * kRows + ct];
+      }
       // barrier, and a uniform decision to stop after an abandoned wait
       const bool aborted = conv_or(*(volatile int*)&sb->abort) != 0;
-      for (int b = ct; b < B; b += kConvWarps * 32)
-        it.t.s1_part[(size_t)g * B + b] = ldexp((double)s1row[b], -sesc[b]);
+      if (ct < B) it.t.s1_part[(size_t)g * B + ct] = ldexp(s1tot, -sesc[ct]);
       // ---------------------------------------------------------- epilogue
       if (warp >= 2 && warp < 6) {
         int okw = 0;
