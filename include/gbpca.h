@@ -327,10 +327,13 @@ int pca_fit_batched(int ntiles, const pca_tile *tiles, pca_dtype dtype, double t
  *                  the run (measured ||dC||_2 / lambda_1 on the 610x340x103
  *                  scene: 3.0e-7 at 2 chunks, 1.2e-6 at 8, 2.5e-6 at 16, 8.0e-6
  *                  at 64); shorter runs write more partials.
- * tc_slot_chunks_16bit  the same for BF16 and FP16 cubes (default 64).  Their
- *                  shifted values fit one FP16 each, the products are exact and
- *                  so are the FP32 sums while they stay below 2^24 units of the
- *                  product grid, which 64 chunks of centred data do.
+ * tc_slot_chunks_f16, tc_slot_chunks_bf16  the same for FP16 and BF16 cubes
+ *                  (defaults 64 and 1024).  Their shifted values fit one FP16
+ *                  each, the products are exact, and so are the FP32 sums while
+ *                  they stay below 2^24 units of the product grid: measured on
+ *                  the 2048 x 2048 x 224 planted cube against the FP64
+ *                  covariance, BF16 (8-bit values) is exact at every run length,
+ *                  FP16 (11-bit values) at 64 chunks but not at 256 (3e-7).
  * batch_jacobi_ctas[i]  batched form: CTAs of the Jacobi cluster of a tile
  *                  with 32i < B' <= 32(i+1) bands (B' = B rounded up to even);
  *                  0 = the fewest that hold the matrix (default), otherwise
@@ -354,7 +357,8 @@ int pca_fit_batched(int ntiles, const pca_tile *tiles, pca_dtype dtype, double t
  */
 typedef struct {
   int tc_slot_chunks;
-  int tc_slot_chunks_16bit;
+  int tc_slot_chunks_f16;
+  int tc_slot_chunks_bf16;
   int batch_jacobi_ctas[8];
   double batch_cov_tc_fixed;
   double batch_proj_fixed;

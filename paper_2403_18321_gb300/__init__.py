@@ -58,7 +58,8 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     """pca_tuning of include/gbpca.h."""
-    _fields_ = [("tc_slot_chunks", ctypes.c_int), ("tc_slot_chunks_16bit", ctypes.c_int),
+    _fields_ = [("tc_slot_chunks", ctypes.c_int), ("tc_slot_chunks_f16", ctypes.c_int),
+                ("tc_slot_chunks_bf16", ctypes.c_int),
                 ("batch_jacobi_ctas", ctypes.c_int * 8),
                 ("batch_cov_tc_fixed", ctypes.c_double), ("batch_proj_fixed", ctypes.c_double),
                 ("batch_cov_simt_fixed", ctypes.c_double),

@@ -28,11 +28,13 @@ __global__ void k_header_init(DevHeader* h, int refine_iters, float tol32) {
 // FP32 cubes: 8 chunks = 256 pixels per slot by default.  The covariance error
 // grows linearly with the slot length (||dC||_2 / lambda_1 on the 103-band scene:
 // 1.2e-6 at 8 chunks, about the plain FP32 form's, 8.0e-6 at 64), at about 50%
-// more covariance time than 64 chunks there.  16-bit cubes: 64 chunks, their
-// products and sums are exact (||dC||_2 = 2e-13 lambda_1 on the planted cube).
+// more covariance time than 64 chunks there.  16-bit cubes: products and sums
+// are exact while the sums stay within FP32's 24 bits -- FP16 64 chunks, BF16
+// (8-bit values) 1024 chunks (equal to the FP64 covariance on the planted cube).
 int tc_slot_chunks(pca_dtype dt) {
   const pca_tuning t = tuning();
-  return dt == PCA_F32 ? t.tc_slot_chunks : t.tc_slot_chunks_16bit;
+  return dt == PCA_F32 ? t.tc_slot_chunks
+                       : (dt == PCA_F16 ? t.tc_slot_chunks_f16 : t.tc_slot_chunks_bf16);
 }
 
 int device_sms() {

@@ -13,7 +13,8 @@ namespace {
 pca_tuning defaults() {
   pca_tuning t{};
   t.tc_slot_chunks = 8;
-  t.tc_slot_chunks_16bit = 64;
+  t.tc_slot_chunks_f16 = 64;
+  t.tc_slot_chunks_bf16 = 1024;
   for (int i = 0; i < 8; ++i) t.batch_jacobi_ctas[i] = 0;
   t.batch_cov_tc_fixed = 464.0;
   t.batch_proj_fixed = 223.0;
@@ -29,7 +30,8 @@ pca_tuning g_tuning = defaults();
 
 bool valid(const pca_tuning& t) {
   if (t.tc_slot_chunks < 1 || t.tc_slot_chunks > 1024) return false;
-  if (t.tc_slot_chunks_16bit < 1 || t.tc_slot_chunks_16bit > 1024) return false;
+  if (t.tc_slot_chunks_f16 < 1 || t.tc_slot_chunks_f16 > 1024) return false;
+  if (t.tc_slot_chunks_bf16 < 1 || t.tc_slot_chunks_bf16 > 1024) return false;
   for (int i = 0; i < 8; ++i)
     if (t.batch_jacobi_ctas[i] < 0 || t.batch_jacobi_ctas[i] > 8) return false;
   auto ok = [](double v) { return std::isfinite(v) && v >= 0.0 && v <= 1e9; };

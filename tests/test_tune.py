@@ -38,7 +38,8 @@ def test_applied_installs_and_restores(cache):
         t = g.tuning()
         assert t["batch_jacobi_ctas"] == [8] * 8 and t["batch_proj_fixed"] == 100.0
         assert t["tc_slot_chunks"] == default["tc_slot_chunks"]
-        assert t["tc_slot_chunks_16bit"] == default["tc_slot_chunks_16bit"]
+        assert t["tc_slot_chunks_f16"] == default["tc_slot_chunks_f16"]
+        assert t["tc_slot_chunks_bf16"] == default["tc_slot_chunks_bf16"]
     assert g.tuning() == default
 
 
