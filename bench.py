@@ -208,8 +208,8 @@ def profiled_traffic(kernel: str, workload: str):
 
 
 def jacobi_flops(B: int, sweeps: int) -> float:
-    """Algorithmic FP32 flops of the cyclic Jacobi on a symmetric B x B matrix by
-    the survey's count: 6 B^3 per sweep (every rotation of a pair updates two
+    """Algorithmic FP32 flops of the cyclic Jacobi on a symmetric B x B matrix:
+    6 B^3 per sweep (every rotation of a pair updates two
     rows and two columns of the symmetric matrix, 6 flops per entry pair, and a
     sweep rotates B(B-1)/2 pairs)."""
     return 6.0 * float(sweeps) * float(B) ** 3
@@ -807,9 +807,8 @@ def roofline_of(g, c2, peaks, peak_src, prec):
 
 # ------------------------------------------------------------------ scene cubes and the mixing cube
 def run_scenes(args, g, dev, peaks, peak_src, world, rank):
-    """The two scene-shaped FP32 cubes fitted side by side on two streams (the
-    round-1 headline workload), every form, with errors and per-kernel HBM
-    fractions; L2 flushed before each step."""
+    """The two scene-shaped FP32 cubes fitted side by side on two streams, every
+    form, with errors and per-kernel HBM fractions; L2 flushed before each step."""
     import torch
 
     import oracle

@@ -14,11 +14,13 @@
 //               FP16 hi = fp16(x), lo = fp16(x - hi) -- 22 significant bits
 //               of x -- written in the cube's own [pixel][band] order as
 //               MN-major operands with the 128-byte swizzle (16-byte vector
-//               loads and stores) into a 3-stage operand ring, and keep the
-//               band sums S1 = sum x of the values they converted (FP32 per
-//               thread over the item -- at most 64 chunks, exact for 16-bit
-//               cubes -- then FP64 over the 32 pixel rows in a fixed order);
-//               each warp also flags whether any lo of its values is non-zero;
+//               loads and stores) into a 3-stage operand ring; a thread owns
+//               8 bands of two pixel rows, keeps their constants in
+//               registers and their band sums S1 = sum x (FP32 over the item,
+//               exact for 16-bit cubes, then added over the 16 row pairs in
+//               a fixed order); a lo unit is stored only when it is non-zero
+//               or was non-zero the last time; each warp flags whether any
+//               lo of its values is non-zero;
 //   warp 1      MMA issuer (one thread): D += hi hi^T + hi lo^T + lo hi^T
 //               for the upper block-triangle (row tile 0: bands 0-127 x all;
 //               row tile 1: bands 128-255 x bands 128-255) with FP32
@@ -28,9 +30,10 @@
 //               the input type: y - s then has at most the bits of the
 //               input's grid, which a single FP16 holds as long as the
 //               pixel's deviation stays within 2^11 grid steps;
-//   warps 2-5   epilogue: TMEM -> registers -> the item's partial slot
-//               (packed upper triangle, FP32, still scaled by 2^(e_i+e_j));
-//               the converters write S1 (FP64, unscaled).
+//   then, after the item's last chunk, the same 16 warps are the epilogue:
+//               TMEM -> registers -> the item's partial slot (packed upper
+//               triangle, FP32, still scaled by 2^(e_i+e_j)) and S1 (FP64,
+//               unscaled).
 // The rings continue across items; the MMAs of an item start once the
 // epilogue of the previous one has read the accumulators out of TMEM.
 // A scaled value outside the FP16 range sets hdr->cov_range; the caller then
@@ -194,7 +197,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
     for (int s = 0; s < S; ++s) { mbar_init(&sb->full[s], 1); mbar_init(&sb->empty[s], kConvWarps); }
     for (int s = 0; s < kOpStages; ++s) { mbar_init(&sb->opfull[s], kConvWarps); mbar_init(&sb->opempty[s], 1); }
     mbar_init(&sb->done, 1);
-    mbar_init(&sb->tfree, 4);
+    mbar_init(&sb->tfree, kConvWarps);
     mbar_init(&sb->drain, 1);
     sb->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -300,12 +303,15 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
     Ring rs(S), ro(kOpStages);        // ring / operand-ring positions, continued across items
     const void* probed = nullptr;     // the cube (and pixel count) whose shift and
     int64_t probed_n = -1;            // scale are in shs / sesc
+    int mapB = -1;                    // the band count of the current unit layout
+    int pr = 0, gq = 0;               // this thread's pixel-row pair and band group
+    uint32_t uoff[2] = {0u, 0u};      // its units' byte offsets in an operand
+    uint32_t dirty = 0;               // bit 2 o + u: lo unit u of operand stage o is non-zero
     for (int i = 0; i < nitems; ++i) {
       const TcItem it = tc_item(one, T, items, cta_items, i);
       const In* cube = static_cast<const In*>(it.t.cube);
       const int64_t N = it.t.N;
       const int B = it.t.B;
-      const int g = it.slot;
       conv_sync();  // the previous item's band sums have been read out of psum
       // Band probe (every CTA computes the same values from the same pixels):
       // over S = min(N, 32) pixels spread evenly through the cube, per band b
@@ -359,53 +365,59 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
               e = 6 - E;
               e = e < -120 ? -120 : (e > 120 ? 120 : e);
             }
-            if (g == 0) { it.t.shift[b] = m; it.t.escale[b] = e; }
+            if (it.slot == 0) { it.t.shift[b] = m; it.t.escale[b] = e; }
           }
           shs[b] = m;
           sesc[b] = e;
         }
         conv_sync();
       }
-      // Per-band constants of this cube as (2^e, -s 2^e) pairs, x = y 2^e - s 2^e
-      // in one FMA (y 2^e is exact), laid out [k][group] as float4 of bands
-      // 8 group + 2k and + 1, so that the lanes of a warp (consecutive groups)
-      // read consecutive 16-byte units; the band sums restart at zero.
+      // Units: thread ct owns the 8-band group gq of pixel rows pr and pr + 16
+      // of every chunk (16 G8 <= 512 threads; the others only take part in the
+      // barriers), so the per-band constants of its bands stay in registers:
+      // x = y 2^e - s 2^e in one FMA (y 2^e and s 2^e are exact); bands past B
+      // get 0, 0.  Its values are written as one 16-byte row unit of the
+      // MN-major operand with the 128-byte swizzle: 64-band blocks 4 KB apart,
+      // 8-pixel groups 1 KB apart inside a block, unit gq mod 8 of pixel row p
+      // at (gq ^ p) mod 8.
       const int G8 = (B + 7) >> 3;                  // 8-band groups
-      float4* cstT = reinterpret_cast<float4*>(pmin);   // [4][32] (pmin/pmax: probe only)
-      for (int e = ct; e < 4 * 32; e += kConvWarps * 32) {
-        const int kq = e >> 5, gq = e & 31, b0 = 8 * gq + 2 * kq;
-        const float sa = b0 < B ? ldexpf(1.f, sesc[b0]) : 0.f;
-        const float sb2 = b0 + 1 < B ? ldexpf(1.f, sesc[b0 + 1]) : 0.f;
-        cstT[e] = make_float4(sa, b0 < B ? -shs[b0] * sa : 0.f, sb2,
-                              b0 + 1 < B ? -shs[b0 + 1] * sb2 : 0.f);
+      if (B != mapB) {
+        // A new unit layout: the lo units this thread left non-zero under the
+        // old one are cleared first (every MMA of the previous item finished
+        // before its epilogue, which the barrier above follows).
+        for (int o = 0; o < kOpStages; ++o)
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (dirty & (1u << (2 * o + u)))
+              *reinterpret_cast<uint4*>(ops + (size_t)(o * 2 + 1) * kOpBytes + uoff[u]) =
+                  make_uint4(0, 0, 0, 0);
+        dirty = 0;
+        mapB = B;
+        pr = ct / G8;
+        gq = ct - pr * G8;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int pp = pr < 16 ? pr + 16 * u : 0;
+          uoff[u] = (uint32_t)(gq >> 3) * kMnLBO + (uint32_t)(pp >> 3) * kMnSBO + (pp & 7) * 128 +
+                    ((uint32_t)((gq & 7) ^ (pp & 7)) << 4);
+        }
       }
-      conv_sync();
-      // Units (pixel p of the chunk, 8-band group gu): a thread owns the same
-      // two units in every chunk (32 x G8 <= 1024 units).  Its values are
-      // written as one 16-byte row unit of the MN-major operand with the
-      // 128-byte swizzle: 64-band blocks 4 KB apart, 8-pixel groups 1 KB apart
-      // inside a block, unit gu mod 8 of pixel row p at (gu ^ p) mod 8.
-      int up[2], ug[2];
-      uint32_t uoff[2];
+      const bool act = pr < 16;
+      const int b0 = 8 * gq;
+      float sc[8], sh[8];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int w = ct + u * kConvWarps * 32;
-        up[u] = w < 32 * G8 ? w / G8 : -1;
-        ug[u] = w < 32 * G8 ? w - up[u] * G8 : 0;
-        const int pp = up[u] < 0 ? 0 : up[u];
-        uoff[u] = (uint32_t)(ug[u] >> 3) * kMnLBO + (uint32_t)(pp >> 3) * kMnSBO + (pp & 7) * 128 +
-                  ((uint32_t)((ug[u] & 7) ^ (pp & 7)) << 4);
+      for (int e = 0; e < 8; ++e) {
+        const int b = b0 + e;
+        sc[e] = (act && b < B) ? ldexpf(1.f, sesc[b]) : 0.f;
+        sh[e] = (act && b < B) ? -shs[b] * sc[e] : 0.f;
       }
-      const bool vec = (B * (int)sizeof(In)) % 16 == 0;
-      float s1f[2][8];
+      const bool vec = (B * (int)sizeof(In)) % 16 == 0 && b0 + 8 <= B;
+      float s1f[8];              // band sums of this thread's pixel rows over the item
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int e = 0; e < 8; ++e) s1f[u][e] = 0.f;
+      for (int e = 0; e < 8; ++e) s1f[e] = 0.f;
       float mx = 0.f;           // largest |x| of this item: above the FP16 range -> SIMT pass
       const int cw = warp - 2;  // converter warp index
-      int c = 0;
-      for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, ++c, rs.next(), ro.next()) {
+      for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, rs.next(), ro.next()) {
         const int s = rs.idx, o = ro.idx;
         // one lane per warp polls the barriers (the others would only add
         // shared-memory traffic), then the warp proceeds together
@@ -418,62 +430,66 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         if (!ok) break;
         const int cp = (int)((it.p1 - p0) < kKC ? (it.p1 - p0) : kKC);
         const int copied = (int)(((uint32_t)(cp * B * (int)sizeof(In)) & ~15u) / sizeof(In));
-        const bool full = cp == kKC && copied == kKC * B;
+        const bool fast = vec && cp == kKC && copied == kKC * B;
         const In* st = reinterpret_cast<const In*>(stages + s * stage_stride);
         const In* gsrc = cube + p0 * B;
         unsigned char* hi = ops + (size_t)(o * 2) * kOpBytes;
         unsigned char* lo = hi + kOpBytes;
         uint32_t lo_bits = 0;    // OR of this thread's lo parts in this chunk
+        if (act) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int pp = up[u], gu = ug[u];
-          if (pp < 0) continue;
-          const int b0 = 8 * gu;
-          float y[8];
-          if (full && vec && b0 + 8 <= B) {
-            const In* src = st + pp * B + b0;
-            if constexpr (sizeof(In) == 4) {
-              const float4 a0 = *reinterpret_cast<const float4*>(src);
-              const float4 a1 = *reinterpret_cast<const float4*>(src + 4);
-              y[0] = a0.x; y[1] = a0.y; y[2] = a0.z; y[3] = a0.w;
-              y[4] = a1.x; y[5] = a1.y; y[6] = a1.z; y[7] = a1.w;
+          for (int u = 0; u < 2; ++u) {
+            const int pp = pr + 16 * u;
+            float x[8];
+            if (fast) {
+              const In* src = st + pp * B + b0;
+              float y[8];
+              if constexpr (sizeof(In) == 4) {
+                const float4 a0 = *reinterpret_cast<const float4*>(src);
+                const float4 a1 = *reinterpret_cast<const float4*>(src + 4);
+                y[0] = a0.x; y[1] = a0.y; y[2] = a0.z; y[3] = a0.w;
+                y[4] = a1.x; y[5] = a1.y; y[6] = a1.z; y[7] = a1.w;
+              } else {
+                const uint4 v = *reinterpret_cast<const uint4*>(src);
+                const In* h8 = reinterpret_cast<const In*>(&v);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) y[e] = to_f32<In>(h8[e]);
+              }
+#pragma unroll
+              for (int e = 0; e < 8; ++e) x[e] = fmaf(y[e], sc[e], sh[e]);
             } else {
-              const uint4 v = *reinterpret_cast<const uint4*>(src);
-              const In* h8 = reinterpret_cast<const In*>(&v);
+              // partial chunk, a ragged pixel row or the last band group: pixels
+              // past the chunk and bands past B contribute 0
 #pragma unroll
-              for (int e = 0; e < 8; ++e) y[e] = to_f32<In>(h8[e]);
+              for (int e = 0; e < 8; ++e) {
+                const int el = pp * B + b0 + e;
+                const bool v = pp < cp && b0 + e < B;
+                const float y = v ? (el < copied ? elem(st + el) : elem(gsrc + el)) : 0.f;
+                x[e] = v ? fmaf(y, sc[e], sh[e]) : 0.f;
+              }
             }
-          } else {
+            uint32_t h[4], l[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int el = pp * B + b0 + e;
-              y[e] = (pp < cp && b0 + e < B)
-                         ? (el < copied ? elem(st + el) : elem(gsrc + el)) : 0.f;
+            for (int e = 0; e < 4; ++e) {
+              mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
+              s1f[2 * e] += x[2 * e];
+              s1f[2 * e + 1] += x[2 * e + 1];
+              h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
+              float a, bb;
+              unpack_f16x2(h[e], a, bb);
+              l[e] = pack_f16x2(x[2 * e] - a, x[2 * e + 1] - bb);
             }
+            *reinterpret_cast<uint4*>(hi + uoff[u]) = make_uint4(h[0], h[1], h[2], h[3]);
+            // the lo unit is stored when it is non-zero, or to clear what this
+            // thread left there before; a unit that is and stays zero is skipped
+            const uint32_t lu = (l[0] | l[1]) | (l[2] | l[3]);
+            const uint32_t bit = 1u << (2 * o + u);
+            if (lu != 0u || (dirty & bit)) {
+              *reinterpret_cast<uint4*>(lo + uoff[u]) = make_uint4(l[0], l[1], l[2], l[3]);
+              dirty = lu != 0u ? (dirty | bit) : (dirty & ~bit);
+            }
+            lo_bits |= lu;
           }
-          float x[8];
-#pragma unroll
-          for (int kq = 0; kq < 4; ++kq) {
-            const float4 k4 = cstT[kq * 32 + gu];
-            // bands past B and pixels past the chunk contribute 0
-            const bool v0 = pp < cp && b0 + 2 * kq < B, v1 = pp < cp && b0 + 2 * kq + 1 < B;
-            x[2 * kq] = v0 ? fmaf(y[2 * kq], k4.x, k4.y) : 0.f;
-            x[2 * kq + 1] = v1 ? fmaf(y[2 * kq + 1], k4.z, k4.w) : 0.f;
-          }
-          uint32_t h[4], l[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
-            s1f[u][2 * e] += x[2 * e];
-            s1f[u][2 * e + 1] += x[2 * e + 1];
-            h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
-            float a, bb;
-            unpack_f16x2(h[e], a, bb);
-            l[e] = pack_f16x2(x[2 * e] - a, x[2 * e + 1] - bb);
-            lo_bits |= l[e];
-          }
-          *reinterpret_cast<uint4*>(hi + uoff[u]) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(lo + uoff[u]) = make_uint4(l[0], l[1], l[2], l[3]);
         }
         const int any_lo = __any_sync(kFull, lo_bits != 0u);
         fence_proxy_async();
@@ -484,68 +500,71 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
           mbar_arrive(&sb->empty[s]);
         }
       }
+      // the item's outputs, fetched again (not kept live through the chunk loop)
+      const TcItem io = tc_item(one, T, items, cta_items, i);
       // NaN compares false: a non-finite value is reported by the finalisation
       if (__any_sync(kFull, !(mx <= 65504.f) && mx == mx) && lane == 0)
-        atomicOr(&it.t.hdr->cov_range, 1);
-      // band sums: the 32 pixel rows' FP32 partials of every band meet in the
-      // probe buffer, 8 rows at a time, and are added in FP64 in a fixed order
-      // (the same bits on every run); the barriers are outside the chunk loop
+        atomicOr(&io.t.hdr->cov_range, 1);
+      // band sums: the 16 pixel-row pairs' FP32 partials of every band meet in
+      // the probe buffer, 8 at a time, and are added in a fixed order (the same
+      // bits on every run): pairs in FP32 (exact for 16-bit cubes), the rest in
+      // FP64; the barriers are outside the chunk loop
       float* s1buf = reinterpret_cast<float*>(psum);   // [8][kRows] (psum: probe only otherwise)
       double s1tot = 0.0;                              // band ct (ct < B)
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < 2; ++r) {
         conv_sync();
+        if (act && pr >= 8 * r && pr < 8 * r + 8)
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-          if (up[u] >= 8 * r && up[u] < 8 * r + 8)
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              s1buf[(up[u] - 8 * r) * kRows + 8 * ug[u] + e] = s1f[u][e];
+          for (int e = 0; e < 8; ++e) s1buf[(pr - 8 * r) * kRows + b0 + e] = s1f[e];
         conv_sync();
-        if (ct < B)
+        if (ct < B) {
+          double t = 0.0;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) s1tot += (double)s1buf[q * kRows + ct];
+          for (int q = 0; q < 8; q += 2) t += (double)(s1buf[q * kRows + ct] + s1buf[(q + 1) * kRows + ct]);
+          s1tot += t;
+        }
       }
       // barrier, and a uniform decision to stop after an abandoned wait
       const bool aborted = conv_or(*(volatile int*)&sb->abort) != 0;
-      if (ct < B) it.t.s1_part[(size_t)g * B + ct] = ldexp(s1tot, -sesc[ct]);
+      if (ct < B) io.t.s1_part[(size_t)io.slot * B + ct] = ldexp(s1tot, -sesc[ct]);
       // ---------------------------------------------------------- epilogue
-      if (warp >= 2 && warp < 6) {
+      // All 16 converter warps: warp w reads TMEM lane quarter w mod 4 (the
+      // quarter it may access) and every fourth 16-column block, from block
+      // (w - 2) / 4 on.
+      {
         int okw = 0;
         if (lane == 0) okw = (!aborted && mbar_wait(&sb->done, i & 1, &sb->abort) && !*(volatile int*)&sb->abort) ? 1 : 0;
         const bool ok = __shfl_sync(kFull, okw, 0) != 0;
-        const bool any = it.p1 > it.p0;   // an empty item leaves the accumulators unwritten
+        const bool any = io.p1 > io.p0;   // an empty item leaves the accumulators unwritten
         tc_fence_after();
         const int R16 = (B + 15) & ~15;
         const int N0 = R16, N1 = B > 128 ? R16 - 128 : 0;
         const int q4 = warp & 3;          // TMEM lane quarter this warp may read
+        const int part = cw >> 2;         // 0..3: which blocks of the quarter
         const int r = q4 * 32 + lane;     // accumulator row
         const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-        float* out = it.t.s2_part + (size_t)g * (B * (B + 1) / 2);
-        // tile 0: row r = band r, column j = band j (j < R16)
-        for (int j0 = 0; j0 < N0; j0 += 16) {
+        float* out = io.t.s2_part + (size_t)io.slot * (B * (B + 1) / 2);
+        const int nb0 = N0 >> 4, nb = nb0 + (N1 >> 4);
+        for (int bk = part; bk < nb; bk += 4) {
+          const bool t1 = bk >= nb0;
+          const int j0 = (t1 ? bk - nb0 : bk) << 4;       // column within the tile
           float v[16];
-          if (ok && any) tmem_ld16(tbase + lane_off + (uint32_t)j0, v);
+          if (ok && any) tmem_ld16(tbase + lane_off + (uint32_t)(t1 ? N0 + j0 : j0), v);
           else
-            for (int k = 0; k < 16; ++k) v[k] = 0.f;
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int j = j0 + k;
-            if (r < B && r < 128 && j < B && j >= r) out[packed_index(r, j, B)] = v[k];
+            for (int k = 0; k < 16; ++k) v[k] = 0.f;
+          // tile 0: row r = band r, column j = band j; tile 1: bands 128 + r, 128 + j
+          const int band = t1 ? 128 + r : r;
+          const int jb0 = t1 ? 128 + j0 : j0;
+          if (band < B && (t1 || r < 128)) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int jb = jb0 + k;
+              if (jb < B && jb >= band) out[packed_index(band, jb, B)] = v[k];
+            }
           }
         }
-        // tile 1: row r = band 128 + r, column j = band 128 + j
-        for (int j0 = 0; j0 < N1; j0 += 16) {
-          float v[16];
-          if (ok && any) tmem_ld16(tbase + lane_off + (uint32_t)(N0 + j0), v);
-          else
-            for (int k = 0; k < 16; ++k) v[k] = 0.f;
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int band = 128 + r, jb = 128 + j0 + k;
-            if (band < B && jb < B && jb >= band) out[packed_index(band, jb, B)] = v[k];
-          }
-        }
-        if (!ok && lane == 0) set_status(it.t.hdr, PCA_ERR_TIMEOUT);
+        if (!ok && lane == 0) set_status(io.t.hdr, PCA_ERR_TIMEOUT);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sb->tfree);
