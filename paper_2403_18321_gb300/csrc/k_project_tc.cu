@@ -248,16 +248,36 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
   const int nt = (int)(t1 - t0);
 
-  // ---- set-up: V planes, band and column constants, barriers, TMEM
+  // ---- set-up: V planes, zero lo planes, band and column constants, barriers, TMEM
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.planes);
     for (int i = tid; i < vbytes / 16; i += kThr) reinterpret_cast<uint4*>(vs)[i] = src[i];
+    // the converters store a lo unit only when it is (or was) non-zero
+    for (int i = tid; i < S * (kPlane / 16); i += kThr) {
+      const int st = i / (kPlane / 16), u = i - st * (kPlane / 16);
+      reinterpret_cast<uint4*>(ops + (size_t)(st * 2 + 1) * kPlane)[u] = make_uint4(0, 0, 0, 0);
+    }
   }
   // x = (y - s) 2^e as one FMA: y 2^e is exact (a power of two) and the sum is
   // rounded once, as (y - s) would be before the exact scaling
-  for (int b = tid; b < 256; b += kThr) {
-    const float sc = b < B ? ldexpf(1.f, a.escale[b]) : 0.f;
-    cst[b] = make_float2(sc, b < B ? -a.shift[b] * sc : 0.f);
+  // BF16 cubes read through the tensor map: the raw pairs enter the FMA
+  constexpr bool kBf16 = std::is_same<In, __nv_bfloat16>::value && kTiled;
+  if constexpr (kBf16) {
+    // BF16 cubes: [256] shifts -s 2^e (FP32), then [128] packed BF16 scale pairs
+    float* shf = reinterpret_cast<float*>(cst);
+    uint32_t* scb = reinterpret_cast<uint32_t*>(shf + 256);
+    for (int b = tid; b < 256; b += kThr)
+      shf[b] = b < B ? -a.shift[b] * ldexpf(1.f, a.escale[b]) : 0.f;
+    for (int b2 = tid; b2 < 128; b2 += kThr) {
+      const int b = 2 * b2;
+      scb[b2] = (b < B ? bf16_pow2(a.escale[b]) : 0u) |
+                ((b + 1 < B ? bf16_pow2(a.escale[b + 1]) : 0u) << 16);
+    }
+  } else {
+    for (int b = tid; b < 256; b += kThr) {
+      const float sc = b < B ? ldexpf(1.f, a.escale[b]) : 0.f;
+      cst[b] = make_float2(sc, b < B ? -a.shift[b] * sc : 0.f);
+    }
   }
   for (int j = tid; j < kMaxCols; j += kThr) {
     cls[j] = j < a.k ? a.colscale[j] : 0.f;
@@ -361,6 +381,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
     const bool vec = (B * (int)sizeof(In)) % 16 == 0;
     const int Q = nt * KC;
     float cur[16], nxt[16];
+    uint32_t raw16[8];       // BF16 path: the 16 values as 8 packed pairs
     // (tile, chunk) of the chunk being converted and of the next one
     int64_t tile = t0, ntile = t0;
     int c = 0, nc = 0;
@@ -368,6 +389,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
     if (!kTiled && Q > 0) load16<In>(cube, t0 * kTM + pr, N, B, gp * 16, vec, cur);
     advance(ntile, nc);
     float mx = 0.f;           // largest |x|: above the FP16 range (or NaN) -> fallback
+    uint32_t dirty = 0u;      // bit o: this thread's lo units of operand stage o are non-zero
     Ring ro(S), rs(R > 0 ? R : 1);
     for (int q = 0; q < Q; ++q, ro.next(), rs.next()) {
       const int o = ro.idx;
@@ -387,9 +409,13 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
           const unsigned char* bx = box + (size_t)(unit >> 3) * kTM * 128;
           const uint4 v = *reinterpret_cast<const uint4*>(
               bx + pr * 128 + (((unit & 7) ^ (pr & 7)) << 4));
-          const In* h = reinterpret_cast<const In*>(&v);
+          if constexpr (kBf16) {
+            raw16[4 * u] = v.x; raw16[4 * u + 1] = v.y; raw16[4 * u + 2] = v.z; raw16[4 * u + 3] = v.w;
+          } else {
+            const In* h = reinterpret_cast<const In*>(&v);
 #pragma unroll
-          for (int e = 0; e < E; ++e) cur[u * E + e] = to_f32<In>(h[e]);
+            for (int e = 0; e < E; ++e) cur[u * E + e] = to_f32<In>(h[e]);
+          }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sy->rempty[s]);
@@ -398,21 +424,46 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       }
       const int b0 = c * kKC + gp * 16;
       const bool row = tile * kTM + pr < N;    // rows past the cube stay 0
-      // the 16 bands' constants (broadcast reads: every lane of the warp has the same b0)
-      float2 kc[16];
-#pragma unroll
-      for (int e = 0; e < 16; e += 2) {
-        const float4 t = *reinterpret_cast<const float4*>(cst + b0 + e);
-        kc[e] = make_float2(t.x, t.y);
-        kc[e + 1] = make_float2(t.z, t.w);
-      }
       float x[16];
-      if (row && b0 + 16 <= B) {
+      if constexpr (kBf16) {
+        // the BF16 pairs enter the FMA as they are; constants: 16 shifts and
+        // 8 scale pairs (broadcast reads: the lanes of a warp share b0)
+        const float* shf = reinterpret_cast<const float*>(cst);
+        const uint32_t* scb = reinterpret_cast<const uint32_t*>(shf + 256);
+        float sh[16];
+        uint32_t sp[8];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) x[e] = fmaf(cur[e], kc[e].x, kc[e].y);
+        for (int e = 0; e < 16; e += 4) {
+          const float4 t = *reinterpret_cast<const float4*>(shf + b0 + e);
+          sh[e] = t.x; sh[e + 1] = t.y; sh[e + 2] = t.z; sh[e + 3] = t.w;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; e += 4) {
+          const uint4 t = *reinterpret_cast<const uint4*>(scb + (b0 >> 1) + e);
+          sp[e] = t.x; sp[e + 1] = t.y; sp[e + 2] = t.z; sp[e + 3] = t.w;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) fma_bf16x2_f32(raw16[e], sp[e], sh[2 * e], sh[2 * e + 1], x[2 * e], x[2 * e + 1]);
+        if (!(row && b0 + 16 <= B)) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) x[e] = row && b0 + e < B ? x[e] : 0.f;
+        }
       } else {
+        // the 16 bands' constants (broadcast reads: every lane of the warp has the same b0)
+        float2 kc[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) x[e] = row && b0 + e < B ? fmaf(cur[e], kc[e].x, kc[e].y) : 0.f;
+        for (int e = 0; e < 16; e += 2) {
+          const float4 t = *reinterpret_cast<const float4*>(cst + b0 + e);
+          kc[e] = make_float2(t.x, t.y);
+          kc[e + 1] = make_float2(t.z, t.w);
+        }
+        if (row && b0 + 16 <= B) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) x[e] = fmaf(cur[e], kc[e].x, kc[e].y);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) x[e] = row && b0 + e < B ? fmaf(cur[e], kc[e].x, kc[e].y) : 0.f;
+        }
       }
       uint32_t h[8], l[8];
       uint32_t lo_bits = 0;
@@ -421,8 +472,14 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
         mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
         h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
         float r0, r1;
-        unpack_f16x2(h[e], r0, r1);
-        l[e] = pack_f16x2(x[2 * e] - r0, x[2 * e + 1] - r1);
+        if constexpr (kBf16) {
+          resid_f16x2(h[e], x[2 * e], x[2 * e + 1], r0, r1);
+        } else {
+          unpack_f16x2(h[e], r0, r1);
+          r0 = x[2 * e] - r0;
+          r1 = x[2 * e + 1] - r1;
+        }
+        l[e] = pack_f16x2(r0, r1);
         lo_bits |= l[e];
       }
       const int any_lo = __any_sync(kFull, lo_bits != 0u);
@@ -438,8 +495,13 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       const uint32_t o1 = (uint32_t)pr * 128 + ((uint32_t)((2 * gp + 1) ^ (pr & 7)) << 4);
       *reinterpret_cast<uint4*>(hi + o0) = make_uint4(h[0], h[1], h[2], h[3]);
       *reinterpret_cast<uint4*>(hi + o1) = make_uint4(h[4], h[5], h[6], h[7]);
-      *reinterpret_cast<uint4*>(lo + o0) = make_uint4(l[0], l[1], l[2], l[3]);
-      *reinterpret_cast<uint4*>(lo + o1) = make_uint4(l[4], l[5], l[6], l[7]);
+      // lo units: stored when non-zero, or to clear what this thread left
+      // there before; units that are and stay zero are skipped
+      if (lo_bits != 0u || (dirty & (1u << o))) {
+        *reinterpret_cast<uint4*>(lo + o0) = make_uint4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint4*>(lo + o1) = make_uint4(l[4], l[5], l[6], l[7]);
+        dirty = lo_bits != 0u ? (dirty | (1u << o)) : (dirty & ~(1u << o));
+      }
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) {

@@ -41,6 +41,8 @@
 // finalised by k_cov.cu.  Every mbarrier wait is bounded (one second of
 // globaltimer); on time-out the CTA records PCA_ERR_TIMEOUT, drains its MMAs,
 // frees TMEM and returns.
+#include <type_traits>
+
 #include "tc.cuh"
 
 namespace gbpca {
@@ -405,12 +407,17 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
       const bool act = pr < 16;
       const int b0 = 8 * gq;
       float sc[8], sh[8];
+      uint32_t sc16[4];          // BF16 cubes: the scales as packed BF16 pairs
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int b = b0 + e;
         sc[e] = (act && b < B) ? ldexpf(1.f, sesc[b]) : 0.f;
         sh[e] = (act && b < B) ? -shs[b] * sc[e] : 0.f;
       }
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        sc16[e] = (sc[2 * e] != 0.f ? bf16_pow2(sesc[b0 + 2 * e]) : 0u) |
+                  ((sc[2 * e + 1] != 0.f ? bf16_pow2(sesc[b0 + 2 * e + 1]) : 0u) << 16);
       const bool vec = (B * (int)sizeof(In)) % 16 == 0 && b0 + 8 <= B;
       float s1f[8];              // band sums of this thread's pixel rows over the item
 #pragma unroll
@@ -443,20 +450,29 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
             float x[8];
             if (fast) {
               const In* src = st + pp * B + b0;
-              float y[8];
-              if constexpr (sizeof(In) == 4) {
-                const float4 a0 = *reinterpret_cast<const float4*>(src);
-                const float4 a1 = *reinterpret_cast<const float4*>(src + 4);
-                y[0] = a0.x; y[1] = a0.y; y[2] = a0.z; y[3] = a0.w;
-                y[4] = a1.x; y[5] = a1.y; y[6] = a1.z; y[7] = a1.w;
-              } else {
+              if constexpr (std::is_same<In, __nv_bfloat16>::value) {
+                // the BF16 pairs enter the FMA as they are
                 const uint4 v = *reinterpret_cast<const uint4*>(src);
-                const In* h8 = reinterpret_cast<const In*>(&v);
+                fma_bf16x2_f32(v.x, sc16[0], sh[0], sh[1], x[0], x[1]);
+                fma_bf16x2_f32(v.y, sc16[1], sh[2], sh[3], x[2], x[3]);
+                fma_bf16x2_f32(v.z, sc16[2], sh[4], sh[5], x[4], x[5]);
+                fma_bf16x2_f32(v.w, sc16[3], sh[6], sh[7], x[6], x[7]);
+              } else {
+                float y[8];
+                if constexpr (sizeof(In) == 4) {
+                  const float4 a0 = *reinterpret_cast<const float4*>(src);
+                  const float4 a1 = *reinterpret_cast<const float4*>(src + 4);
+                  y[0] = a0.x; y[1] = a0.y; y[2] = a0.z; y[3] = a0.w;
+                  y[4] = a1.x; y[5] = a1.y; y[6] = a1.z; y[7] = a1.w;
+                } else {
+                  const uint4 v = *reinterpret_cast<const uint4*>(src);
+                  const In* h8 = reinterpret_cast<const In*>(&v);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) y[e] = to_f32<In>(h8[e]);
+                  for (int e = 0; e < 8; ++e) y[e] = to_f32<In>(h8[e]);
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = fmaf(y[e], sc[e], sh[e]);
               }
-#pragma unroll
-              for (int e = 0; e < 8; ++e) x[e] = fmaf(y[e], sc[e], sh[e]);
             } else {
               // partial chunk, a ragged pixel row or the last band group: pixels
               // past the chunk and bands past B contribute 0
@@ -465,7 +481,12 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
                 const int el = pp * B + b0 + e;
                 const bool v = pp < cp && b0 + e < B;
                 const float y = v ? (el < copied ? elem(st + el) : elem(gsrc + el)) : 0.f;
-                x[e] = v ? fmaf(y, sc[e], sh[e]) : 0.f;
+                if constexpr (std::is_same<In, __nv_bfloat16>::value) {
+                  const float c = v ? ldexpf(1.f, sesc[b0 + e]) : 0.f;   // as sc, sh
+                  x[e] = v ? fmaf(y, c, -shs[b0 + e] * c) : 0.f;
+                } else {
+                  x[e] = v ? fmaf(y, sc[e], sh[e]) : 0.f;
+                }
               }
             }
             uint32_t h[4], l[4];
@@ -475,9 +496,15 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
               s1f[2 * e] += x[2 * e];
               s1f[2 * e + 1] += x[2 * e + 1];
               h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
-              float a, bb;
-              unpack_f16x2(h[e], a, bb);
-              l[e] = pack_f16x2(x[2 * e] - a, x[2 * e + 1] - bb);
+              float r0, r1;
+              if constexpr (std::is_same<In, __nv_bfloat16>::value) {
+                resid_f16x2(h[e], x[2 * e], x[2 * e + 1], r0, r1);
+              } else {
+                unpack_f16x2(h[e], r0, r1);
+                r0 = x[2 * e] - r0;
+                r1 = x[2 * e + 1] - r1;
+              }
+              l[e] = pack_f16x2(r0, r1);
             }
             *reinterpret_cast<uint4*>(hi + uoff[u]) = make_uint4(h[0], h[1], h[2], h[3]);
             // the lo unit is stored when it is non-zero, or to clear what this

@@ -111,5 +111,27 @@ __device__ __forceinline__ void unpack_f16x2(uint32_t v, float& a, float& b) {
   b = __half2float(__ushort_as_half((unsigned short)(v >> 16)));
 }
 
+// x = y s + c for a packed BF16 pair y (low half first) and packed BF16 scales
+// s, with FP32 c and results: the product is exact (the scales are powers of
+// two), the sum rounded once -- fmaf on the widened operands, without them.
+__device__ __forceinline__ void fma_bf16x2_f32(uint32_t y, uint32_t s, float c0, float c1,
+                                               float& x0, float& x1) {
+  asm("{\n .reg .b16 y0, y1, s0, s1;\n mov.b32 {y0, y1}, %2;\n mov.b32 {s0, s1}, %3;\n"
+      " fma.rn.f32.bf16 %0, y0, s0, %4;\n fma.rn.f32.bf16 %1, y1, s1, %5;\n}"
+      : "=f"(x0), "=f"(x1)
+      : "r"(y), "r"(s), "f"(c0), "f"(c1));
+}
+// r = x - hi for a packed FP16 pair hi (low half first): exact, since hi is x
+// rounded to FP16.
+__device__ __forceinline__ void resid_f16x2(uint32_t hi, float x0, float x1, float& r0,
+                                            float& r1) {
+  asm("{\n .reg .b16 h0, h1, m;\n mov.b32 {h0, h1}, %2;\n mov.b16 m, 0xbc00;\n"
+      " fma.rn.f32.f16 %0, h0, m, %3;\n fma.rn.f32.f16 %1, h1, m, %4;\n}"
+      : "=f"(r0), "=f"(r1)
+      : "r"(hi), "f"(x0), "f"(x1));
+}
+// BF16 bits of 2^e (|e| <= 126)
+__device__ __forceinline__ uint32_t bf16_pow2(int e) { return (uint32_t)(e + 127) << 7; }
+
 
 }  // namespace gbpca
