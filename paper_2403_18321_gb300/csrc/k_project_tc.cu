@@ -388,7 +388,12 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
     auto advance = [&](int64_t& t, int& cc) { if (++cc == KC) { cc = 0; ++t; } };
     if (!kTiled && Q > 0) load16<In>(cube, t0 * kTM + pr, N, B, gp * 16, vec, cur);
     advance(ntile, nc);
-    float mx = 0.f;           // largest |x|: above the FP16 range (or NaN) -> fallback
+    // a value beyond the FP16 range -> fallback.  FP32 cubes track the largest
+    // |x|; for 16-bit cubes (whose lo parts are nearly always zero) an
+    // infinite lo part is the sign of it, checked where lo is stored
+    constexpr bool k16 = sizeof(In) == 2;
+    float mx = 0.f;
+    int rng = 0;
     uint32_t dirty = 0u;      // bit o: this thread's lo units of operand stage o are non-zero
     Ring ro(S), rs(R > 0 ? R : 1);
     for (int q = 0; q < Q; ++q, ro.next(), rs.next()) {
@@ -469,7 +474,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       uint32_t lo_bits = 0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
+        if constexpr (!k16) mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
         h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
         float r0, r1;
         if constexpr (kBf16) {
@@ -501,6 +506,12 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
         *reinterpret_cast<uint4*>(lo + o0) = make_uint4(l[0], l[1], l[2], l[3]);
         *reinterpret_cast<uint4*>(lo + o1) = make_uint4(l[4], l[5], l[6], l[7]);
         dirty = lo_bits != 0u ? (dirty | (1u << o)) : (dirty & ~(1u << o));
+        if constexpr (k16) {
+          bool inf = false;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) inf |= f16x2_has_inf(l[e]);
+          rng |= inf ? 1 : 0;
+        }
       }
       fence_proxy_async();
       __syncwarp();
@@ -515,7 +526,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       advance(tile, c);
       advance(ntile, nc);
     }
-    const int bad = !(mx <= 65504.f);
+    const int bad = !(mx <= 65504.f) || rng != 0;
     if (__any_sync(kFull, bad) && lane == 0 && a.hdr) atomicOr(&a.hdr->proj_range, 1);
   } else if (warp >= 2 + kConvW) {
     // ------------------------------------------------------------ epilogue

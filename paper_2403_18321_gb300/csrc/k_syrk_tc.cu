@@ -15,16 +15,15 @@
 //               of x -- written in the cube's own [pixel][band] order as
 //               MN-major operands with the 128-byte swizzle (16-byte vector
 //               loads and stores) into a 3-stage operand ring; a thread owns
-//               8 bands of two pixel rows, keeps their constants in
-//               registers and their band sums S1 = sum x (FP32 over the item,
-//               exact for 16-bit cubes, then added over the 16 row pairs in
-//               a fixed order); a lo unit is stored only when it is non-zero
-//               or was non-zero the last time; each warp flags whether any
-//               lo of its values is non-zero;
+//               8 bands of two pixel rows and keeps their constants in
+//               registers; a lo unit is stored only when it is non-zero or
+//               was non-zero the last time; each warp flags whether any lo of
+//               its values is non-zero;
 //   warp 1      MMA issuer (one thread): D += hi hi^T + hi lo^T + lo hi^T
 //               for the upper block-triangle (row tile 0: bands 0-127 x all;
 //               row tile 1: bands 128-255 x bands 128-255) with FP32
-//               accumulation in TMEM.  A chunk whose lo parts are all zero
+//               accumulation in TMEM, and the band sums S1 = (hi + lo)^T 1
+//               against a constant operand of ones (N = 16, column 0).  A chunk whose lo parts are all zero
 //               gets the first product only: the other two are exactly zero.
 //               That is the rule for 16-bit cubes, whose shift is rounded to
 //               the input type: y - s then has at most the bits of the
@@ -33,7 +32,8 @@
 //   then, after the item's last chunk, the same 16 warps are the epilogue:
 //               TMEM -> registers -> the item's partial slot (packed upper
 //               triangle, FP32, still scaled by 2^(e_i+e_j)) and S1 (FP64,
-//               unscaled).
+//               unscaled).  S1 shares the covariance entries' accumulation:
+//               exact for 16-bit cubes within their runs, FP32 runs otherwise.
 // The rings continue across items; the MMAs of an item start once the
 // epilogue of the previous one has read the accumulators out of TMEM.
 // A scaled value outside the FP16 range sets hdr->cov_range; the caller then
@@ -63,6 +63,8 @@ constexpr int kOpBytes = kRows * kKC * 2;        // one FP16 operand (hi or lo):
 constexpr uint32_t kMnSBO = 1024;                // next 8 pixels (K)
 constexpr uint32_t kMnLBO = (kKC / 8) * 1024;    // next 64 bands (MN): 4 KB
 constexpr int kTmemCols = 512;
+constexpr int kOnesBytes = 16 * 128;     // B operand of the band sums: 16 rows x 128 bytes
+constexpr uint32_t kS1Col = 384;         // TMEM columns of the band sums (tile 0; tile 1 at +16)
 constexpr int kProbe = 32;               // pixels of the band probe
 
 struct __align__(8) SyncBlock {
@@ -85,6 +87,21 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 }
 // kind::f16 instruction descriptor with both operands MN-major
 __device__ __forceinline__ uint32_t idesc_mn(int n) { return idesc_f16(n) | (1u << 15) | (1u << 16); }
+
+// The band sums S1 come out of the tensor cores.  Up to 248 bands, operand row
+// ob = 8 G8 (the first 8-band group past the data) holds 1.0 for every pixel,
+// so accumulator column ob sums each band's values, hi + lo, like any
+// covariance entry; wider cubes have no free row below 256 and take S1 from
+// extra MMAs against a separate operand of ones.
+__device__ __forceinline__ int ones_band(int B) {
+  const int ob = ((B + 7) >> 3) << 3;
+  return ob < kRows ? ob : -1;
+}
+// operand rows (bands, and the ones row) padded to the 16-row MMA granule
+__device__ __forceinline__ int mma_rows(int B) {
+  const int ob = ones_band(B);
+  return ob >= 0 ? (ob + 16) & ~15 : (B + 15) & ~15;
+}
 
 template <typename In>
 __device__ __forceinline__ float elem(const In* p) { return to_f32<In>(*p); }
@@ -178,11 +195,12 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
           int stage_stride) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* ops = smem;                                        // [kOpStages][hi|lo][kOpBytes]
-  unsigned char* stages = smem + kOpStages * 2 * kOpBytes;          // [S][stage_stride]
+  unsigned char* ones = smem + kOpStages * 2 * kOpBytes;            // [16][128 B], row 0 = 1.0
+  unsigned char* stages = ones + kOnesBytes;                        // [S][stage_stride]
   float* shs = reinterpret_cast<float*>(stages + S * stage_stride);        // [kRows] shift
   int* sesc = reinterpret_cast<int*>(shs + kRows);                         // [kRows] exponent
-  double* psum = reinterpret_cast<double*>(sesc + kRows);                  // [4][kRows]
-  float* pmin = reinterpret_cast<float*>(psum + 4 * kRows);                // [2][kRows]
+  double* psum = reinterpret_cast<double*>(sesc + kRows);                  // [2][kRows]
+  float* pmin = reinterpret_cast<float*>(psum + 2 * kRows);                // [2][kRows]
   float* pmax = pmin + 2 * kRows;                                          // [2][kRows]
   SyncBlock* sb = reinterpret_cast<SyncBlock*>(pmax + 2 * kRows);
 
@@ -195,6 +213,13 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
   // ---- set-up
   for (int i = tid; i < kOpStages * 2 * kOpBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(ops)[i] = make_uint4(0, 0, 0, 0);
+  // the ones operand: K-major (pixels contiguous), row 0 = FP16 1.0 for every
+  // pixel, rows 1-15 zero (the 128-byte swizzle only permutes 16-byte units
+  // inside a row, so it leaves this pattern as it is)
+  for (int i = tid; i < kOnesBytes / 16; i += kThreads) {
+    const uint32_t w = i < 8 ? 0x3c003c00u : 0u;
+    reinterpret_cast<uint4*>(ones)[i] = make_uint4(w, w, w, w);
+  }
   if (tid == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&sb->full[s], 1); mbar_init(&sb->empty[s], kConvWarps); }
     for (int s = 0; s < kOpStages; ++s) { mbar_init(&sb->opfull[s], kConvWarps); mbar_init(&sb->opempty[s], 1); }
@@ -243,12 +268,16 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
     // broadcasts the outcome, one elected lane issues each MMA.
     const uint32_t ops_base = su32(ops);
     const uint64_t d0 = sdesc(ops_base);   // an offset of d bytes adds d >> 4
+    const uint64_t d1s = sdesc_sw128(su32(ones));
+    // band sums S1 = x^T 1: A = the tile's rows (MN-major), B = the ones (K-major), N = 16
+    const uint32_t id_s1 = idesc_f16(16) | (1u << 15);
     Ring ro(kOpStages);  // operand-ring position, continued across items
     bool ok = true;
     for (int i = 0; i < nitems && ok; ++i) {
       const TcItem it = tc_item(one, T, items, cta_items, i);
       const int B = it.t.B;
-      const int R16 = (B + 15) & ~15;               // bands padded to the 16-row MMA granule
+      const int R16 = mma_rows(B);                  // bands (and the ones row), padded
+      const bool s1mma = ones_band(B) < 0;          // S1 from the separate ones operand
       const bool two_tiles = B > 128;
       const int N0 = R16;                           // tile 0 columns: bands 0..R16-1
       const int N1 = two_tiles ? (R16 - 128) : 0;   // tile 1 columns: bands 128..R16-1
@@ -292,6 +321,15 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
               mma_f16_warp(t1, lo + r128 + ko, hi + r128 + ko, id1, 1u);
             }
           }
+          if (s1mma) {
+            // band sums: (hi + lo)^T 1, column 0 of a 16-column accumulator per tile
+            mma_f16_warp(tbase + kS1Col, hi + ko, d1s, id_s1, acc0);
+            if (nz) mma_f16_warp(tbase + kS1Col, lo + ko, d1s, id_s1, 1u);
+            if (two_tiles) {
+              mma_f16_warp(tbase + kS1Col + 16, hi + r128 + ko, d1s, id_s1, acc0);
+              if (nz) mma_f16_warp(tbase + kS1Col + 16, lo + r128 + ko, d1s, id_s1, 1u);
+            }
+          }
         }
         first = false;
         mma_commit_warp(&sb->opempty[o]);  // operand stage free once these MMAs finished
@@ -314,7 +352,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
       const In* cube = static_cast<const In*>(it.t.cube);
       const int64_t N = it.t.N;
       const int B = it.t.B;
-      conv_sync();  // the previous item's band sums have been read out of psum
+      conv_sync();  // the previous item's epilogue is over (every MMA of it finished)
       // Band probe (every CTA computes the same values from the same pixels):
       // over S = min(N, 32) pixels spread evenly through the cube, per band b
       //   shift_b = sample mean,  escale_b = 6 - E with max |y - shift_b| <= 2^E,
@@ -394,6 +432,23 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
               *reinterpret_cast<uint4*>(ops + (size_t)(o * 2 + 1) * kOpBytes + uoff[u]) =
                   make_uint4(0, 0, 0, 0);
         dirty = 0;
+        // the ones row of the new layout in the hi plane of every stage (and
+        // the old one cleared): unit G8 of each of the 32 pixel rows
+        const int ob_old = mapB > 0 ? ones_band(mapB) : -1, ob_new = ones_band(B);
+        if (ct < kOpStages * kKC) {
+          const int o = ct / kKC, k = ct - o * kKC;
+          unsigned char* hp = ops + (size_t)(o * 2) * kOpBytes + (k >> 3) * kMnSBO + (k & 7) * 128;
+          if (ob_old >= 0 && ob_old != ob_new) {
+            const int gu = ob_old >> 3;
+            *reinterpret_cast<uint4*>(hp + (gu >> 3) * kMnLBO + (((gu & 7) ^ (k & 7)) << 4)) =
+                make_uint4(0, 0, 0, 0);
+          }
+          if (ob_new >= 0) {
+            const int gu = ob_new >> 3;
+            *reinterpret_cast<uint4*>(hp + (gu >> 3) * kMnLBO + (((gu & 7) ^ (k & 7)) << 4)) =
+                make_uint4(0x3c00u, 0, 0, 0);   // FP16 1.0 at band ob, 0 at ob+1..ob+7
+          }
+        }
         mapB = B;
         pr = ct / G8;
         gq = ct - pr * G8;
@@ -419,10 +474,12 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         sc16[e] = (sc[2 * e] != 0.f ? bf16_pow2(sesc[b0 + 2 * e]) : 0u) |
                   ((sc[2 * e + 1] != 0.f ? bf16_pow2(sesc[b0 + 2 * e + 1]) : 0u) << 16);
       const bool vec = (B * (int)sizeof(In)) % 16 == 0 && b0 + 8 <= B;
-      float s1f[8];              // band sums of this thread's pixel rows over the item
-#pragma unroll
-      for (int e = 0; e < 8; ++e) s1f[e] = 0.f;
-      float mx = 0.f;           // largest |x| of this item: above the FP16 range -> SIMT pass
+      // a value beyond the FP16 range -> SIMT pass.  FP32 cubes track the
+      // largest |x|; for 16-bit cubes (whose lo parts are nearly always zero)
+      // an infinite lo part is the sign of it, checked where lo is stored
+      constexpr bool k16 = sizeof(In) == 2;
+      float mx = 0.f;
+      int rng = 0;
       const int cw = warp - 2;  // converter warp index
       for (int64_t p0 = it.p0; p0 < it.p1; p0 += kKC, rs.next(), ro.next()) {
         const int s = rs.idx, o = ro.idx;
@@ -492,9 +549,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
             uint32_t h[4], l[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
-              s1f[2 * e] += x[2 * e];
-              s1f[2 * e + 1] += x[2 * e + 1];
+              if constexpr (!k16) mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
               h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
               float r0, r1;
               if constexpr (std::is_same<In, __nv_bfloat16>::value) {
@@ -514,6 +569,9 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
             if (lu != 0u || (dirty & bit)) {
               *reinterpret_cast<uint4*>(lo + uoff[u]) = make_uint4(l[0], l[1], l[2], l[3]);
               dirty = lu != 0u ? (dirty | bit) : (dirty & ~bit);
+              if constexpr (k16)
+                rng |= (f16x2_has_inf(l[0]) | f16x2_has_inf(l[1]) | f16x2_has_inf(l[2]) |
+                        f16x2_has_inf(l[3])) ? 1 : 0;
             }
             lo_bits |= lu;
           }
@@ -529,31 +587,12 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
       }
       // the item's outputs, fetched again (not kept live through the chunk loop)
       const TcItem io = tc_item(one, T, items, cta_items, i);
-      // NaN compares false: a non-finite value is reported by the finalisation
-      if (__any_sync(kFull, !(mx <= 65504.f) && mx == mx) && lane == 0)
+      // NaN compares false (and gives a NaN lo part, not an infinite one): a
+      // non-finite value is reported by the finalisation
+      if (__any_sync(kFull, (!(mx <= 65504.f) && mx == mx) || rng != 0) && lane == 0)
         atomicOr(&io.t.hdr->cov_range, 1);
-      // band sums: the 16 pixel-row pairs' FP32 partials of every band meet in
-      // the probe buffer, 8 at a time, and are added in a fixed order (the same
-      // bits on every run): pairs in FP32 (exact for 16-bit cubes), the rest in
-      // FP64; the barriers are outside the chunk loop
-      float* s1buf = reinterpret_cast<float*>(psum);   // [8][kRows] (psum: probe only otherwise)
-      double s1tot = 0.0;                              // band ct (ct < B)
-      for (int r = 0; r < 2; ++r) {
-        conv_sync();
-        if (act && pr >= 8 * r && pr < 8 * r + 8)
-#pragma unroll
-          for (int e = 0; e < 8; ++e) s1buf[(pr - 8 * r) * kRows + b0 + e] = s1f[e];
-        conv_sync();
-        if (ct < B) {
-          double t = 0.0;
-#pragma unroll
-          for (int q = 0; q < 8; q += 2) t += (double)(s1buf[q * kRows + ct] + s1buf[(q + 1) * kRows + ct]);
-          s1tot += t;
-        }
-      }
       // barrier, and a uniform decision to stop after an abandoned wait
       const bool aborted = conv_or(*(volatile int*)&sb->abort) != 0;
-      if (ct < B) io.t.s1_part[(size_t)io.slot * B + ct] = ldexp(s1tot, -sesc[ct]);
       // ---------------------------------------------------------- epilogue
       // All 16 converter warps: warp w reads TMEM lane quarter w mod 4 (the
       // quarter it may access) and every fourth 16-column block, from block
@@ -564,8 +603,9 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         const bool ok = __shfl_sync(kFull, okw, 0) != 0;
         const bool any = io.p1 > io.p0;   // an empty item leaves the accumulators unwritten
         tc_fence_after();
-        const int R16 = (B + 15) & ~15;
+        const int R16 = mma_rows(B);
         const int N0 = R16, N1 = B > 128 ? R16 - 128 : 0;
+        const int ob = ones_band(B);      // accumulator column of the band sums (-1: separate)
         const int q4 = warp & 3;          // TMEM lane quarter this warp may read
         const int part = cw >> 2;         // 0..3: which blocks of the quarter
         const int r = q4 * 32 + lane;     // accumulator row
@@ -589,6 +629,25 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
               const int jb = jb0 + k;
               if (jb < B && jb >= band) out[packed_index(band, jb, B)] = v[k];
             }
+          }
+        }
+        // band sums (FP64, unscaled): column ob of the tiles' accumulators, or
+        // column 0 of the separate ones accumulators
+        if (part == 0) {
+          for (int t = 0; t < (B > 128 ? 2 : 1); ++t) {
+            const uint32_t col = ob >= 0 ? (uint32_t)(t == 0 ? (ob & ~15) : N0 + ((ob - 128) & ~15))
+                                         : kS1Col + 16u * (uint32_t)t;
+            const int kk = ob >= 0 ? (ob & 15) : 0;   // the same for both tiles (128 = 0 mod 16)
+            float v[16];
+            if (ok && any) tmem_ld16(tbase + lane_off + col, v);
+            else
+#pragma unroll
+              for (int k = 0; k < 16; ++k) v[k] = 0.f;
+            float sv = v[0];
+#pragma unroll
+            for (int k = 1; k < 16; ++k) sv = k == kk ? v[k] : sv;
+            const int band = 128 * t + r;
+            if (band < B) io.t.s1_part[(size_t)io.slot * B + band] = ldexp((double)sv, -sesc[band]);
           }
         }
         if (!ok && lane == 0) set_status(io.t.hdr, PCA_ERR_TIMEOUT);
@@ -618,8 +677,8 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
 
 // shared memory: operand ring, TMA ring of S stages, probe and sync blocks
 size_t tc_fixed_smem() {
-  return 1024 + (size_t)kOpStages * 2 * kOpBytes + kRows * (sizeof(float) + sizeof(int)) +
-         kRows * (4 * sizeof(double) + 4 * sizeof(float)) + sizeof(SyncBlock);
+  return 1024 + (size_t)kOpStages * 2 * kOpBytes + kOnesBytes + kRows * (sizeof(float) + sizeof(int)) +
+         kRows * (2 * sizeof(double) + 4 * sizeof(float)) + sizeof(SyncBlock);
 }
 
 template <typename In>

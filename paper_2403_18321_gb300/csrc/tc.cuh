@@ -130,6 +130,12 @@ __device__ __forceinline__ void resid_f16x2(uint32_t hi, float x0, float x1, flo
       : "=f"(r0), "=f"(r1)
       : "r"(hi), "f"(x0), "f"(x1));
 }
+// Whether either half of a packed FP16 pair is an infinity.  When x leaves
+// the FP16 range, hi = fp16(x) is an infinity and so is lo = fp16(x - hi).
+__device__ __forceinline__ bool f16x2_has_inf(uint32_t v) {
+  const uint32_t a = v & 0x7fff7fffu;
+  return (a & 0xffffu) == 0x7c00u || (a >> 16) == 0x7c00u;
+}
 // BF16 bits of 2^e (|e| <= 126)
 __device__ __forceinline__ uint32_t bf16_pow2(int e) { return (uint32_t)(e + 127) << 7; }
 

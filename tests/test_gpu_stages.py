@@ -12,7 +12,7 @@ import torch
 
 import oracle
 import synth
-from parity import E_COV, LAM_TOL, ORTH_TOL, rel_gaps, sign_norm
+from parity import E_COV, compare, LAM_TOL, ORTH_TOL, rel_gaps, sign_norm
 
 # covariance: max_ij |C - C*| / max_ij |C*|; in the spectral norm relative to
 # lambda_1, E_COV (the bound every later comparison builds on)
@@ -119,6 +119,29 @@ def test_project_stage(gbpca_lib, dtype, bands):
     for j in range(cube.k):
         err = np.abs(Qn[:, j] - ref["Q"][:, j]).max() / np.abs(ref["Q"][:, j]).max()
         assert err <= 1e-5, (j, err)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype,big", [(torch.bfloat16, 5e6), (torch.float16, 6e4)])
+def test_mix_range_guard_16bit_cubes(gbpca_lib, dtype, big):
+    """16-bit cubes: the converters see a value beyond the FP16 range through
+    its infinite hi and lo parts; the covariance and the projection are then
+    recomputed on the SIMT path and match the oracle at P32 accuracy, while
+    the same cube without the outlier stays on the tensor cores."""
+    g = gbpca_lib
+    cube = synth.linear_mixing(seed=21, rows=61, cols=67, bands=48, endmembers=5)
+    assert cube.N > 1024          # pixel 1 is then outside the strided sample
+    Yd = torch.from_numpy(cube.Y).to(dtype)
+    *_, info = g.fit(Yd.cuda(), cube.k, precision="mix")
+    assert info["status"] == 0 and info["cov_fallback"] == 0 and info["proj_fallback"] == 0
+    Yd[1, 7] = big                # the data lie in [0, 1]
+    Yh = Yd.float().numpy().astype(np.float64)
+    mu, ev, V, Q, info = g.fit(Yd.cuda(), cube.k, precision="mix")
+    torch.cuda.synchronize()
+    assert info["status"] == 0 and info["cov_fallback"] == 1 and info["proj_fallback"] == 1, info
+    ref = oracle.pca_fit(Yh, cube.k, tol=1e-14)
+    compare((mu.cpu().numpy(), ev.cpu().numpy(), V.cpu().numpy(),
+             Q.cpu().numpy().astype(np.float64)), ref, cube.k, "p32")
 
 
 @pytest.mark.gpu
