@@ -492,7 +492,7 @@ int pca_kernel_launches(pca_precision prec, int k) {
     proj = (k + 31) / 32;
     if (prec == PCA_PREC_MIX) proj += 1 + 2 * ((k + 127) / 128);
   }
-  return 4 + cov + 6 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + proj;
+  return 5 + cov + 6 * it + (it > 0 ? 1 : 0) + 3 * ortho_steps(prec) + 2 + proj;
 }
 
 int pca_jacobi_sms(int B) {
