@@ -454,11 +454,21 @@ def run_paper_shapes(args, dev):
             e1.record()
             e1.synchronize()
             ms = e0.elapsed_time(e1) / reps
-            # end to end: copy in, fit, copy the results out, synchronise
+            # end to end through pca_fit_host: pinned host cube in, results out
+            hb = g.HostFit(cube.N, B, 1, Yh.dtype, prec, dev)
+            hout = (torch.empty(B, dtype=torch.float64).pin_memory(),
+                    torch.empty(B, dtype=torch.float64).pin_memory(),
+                    torch.empty(B, B, dtype=torch.float64).pin_memory(),
+                    torch.empty(cube.N, 1, dtype=torch.float32).pin_memory())
+            for _ in range(2):
+                g.fit_host(Yh, 1, precision=prec, buffers=hb, out=hout, sync=False)
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(reps):
-                g.fit_host(Yh, 1, precision=prec, workspace=ws, device=dev)
+                g.fit_host(Yh, 1, precision=prec, buffers=hb, out=hout, sync=False)
+                torch.cuda.current_stream(dev).synchronize()
             ms_e2e = (time.perf_counter() - t0) / reps * 1e3
+            del hb
             row[prec] = {"ms": ms, "Mpixel-bands/s": cube.N * B / (ms / 1e3) / 1e6,
                          "ms_e2e": ms_e2e, "cubes_per_s_e2e": 1e3 / ms_e2e}
         rows.append(row)
@@ -719,26 +729,22 @@ def run_c2(args, g, dev, peaks, peak_src, sampler, world, rank):
         props["mu_err"] = float(np.abs(host16[0] - mu_ex).max() / np.abs(mu_ex).max())
         errors["full_size_fp16_mix"] = props
     del c16
-    # end to end through the public API from pinned host memory
+    # end to end through the C ABI with host buffers (pca_fit_host): the pinned
+    # host cube goes in, the results come back to pinned host memory
     e2e = None
     if not args.no_e2e:
         Yh = Y.cpu().pin_memory()
-        ws = g.make_workspace(N, B, k, 1, args.precision, dev)
-        Yin = torch.empty_like(Y)
-        outs = (torch.empty(B, dtype=torch.float64, device=dev),
-                torch.empty(B, dtype=torch.float64, device=dev),
-                torch.empty(B, B, dtype=torch.float64, device=dev),
-                torch.empty(N, k, dtype=torch.float32, device=dev))
-        hout = tuple(torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs)
+        hb = g.HostFit(N, B, k, Yh.dtype, args.precision, dev)
+        hout = (torch.empty(B, dtype=torch.float64).pin_memory(),
+                torch.empty(B, dtype=torch.float64).pin_memory(),
+                torch.empty(B, B, dtype=torch.float64).pin_memory(),
+                torch.empty(N, k, dtype=torch.float32).pin_memory())
         h2d = Yh.numel() * Yh.element_size()
-        d2h = sum(o.numel() * o.element_size() for o in outs)
+        d2h = sum(o.numel() * o.element_size() for o in hout)
 
         def e2e_step():
-            Yin.copy_(Yh, non_blocking=True)
-            g.fit(Yin, k, tol=1e-10, sweeps_max=30, precision=args.precision, out=outs,
-                  workspace=ws, sync=False)
-            for o, h in zip(outs, hout):
-                h.copy_(o, non_blocking=True)
+            g.fit_host(Yh, k, tol=1e-10, sweeps_max=30, precision=args.precision, buffers=hb,
+                       out=hout, sync=False)
             torch.cuda.current_stream(dev).synchronize()
 
         for _ in range(args.warmup):
@@ -758,9 +764,38 @@ def run_c2(args, g, dev, peaks, peak_src, sampler, world, rank):
         e2e = {"value": aggregate(units, args.steps, total, world), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": total / args.steps * 1e3,
-               "how": "pinned host cube -> device copy, pca_fit, results -> pinned host, "
-                      "synchronise; one stream"}
-        del Yh, Yin, ws
+               "how": "pca_fit_host: pinned host cube copied in 16 pixel ranges, each range's "
+                      "covariance as its copy lands, the ranges' moments pooled, eigen stage, "
+                      "each range's projection copied back while the next is projected; "
+                      "synchronise"}
+        # the same through the device-resident API with the copies around it, one stream
+        Yin = torch.empty_like(Y)
+        ws = g.make_workspace(N, B, k, 1, args.precision, dev)
+        outs = (torch.empty(B, dtype=torch.float64, device=dev),
+                torch.empty(B, dtype=torch.float64, device=dev),
+                torch.empty(B, B, dtype=torch.float64, device=dev),
+                torch.empty(N, k, dtype=torch.float32, device=dev))
+
+        def serial_step():
+            Yin.copy_(Yh, non_blocking=True)
+            g.fit(Yin, k, tol=1e-10, sweeps_max=30, precision=args.precision, out=outs,
+                  workspace=ws, sync=False)
+            for o, h in zip(outs, hout):
+                h.copy_(o, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+
+        for _ in range(args.warmup):
+            serial_step()
+        t_serial = 0.0
+        for _ in range(args.steps):
+            e0.record()
+            serial_step()
+            e1.record()
+            e1.synchronize()
+            t_serial += e0.elapsed_time(e1) / 1e3
+        t_serial = max_over_ranks(t_serial, world)
+        e2e["serial_copies_ms_per_step"] = t_serial / args.steps * 1e3
+        del Yh, Yin, ws, hb
     res.update({"forms": forms, "hbm": hbm, "errors": errors, "e2e": e2e, "N": N, "B": B, "k": k,
                 "units": units})
     return res

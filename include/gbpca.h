@@ -164,6 +164,43 @@ int pca_project(const void *cube, pca_dtype dtype, int64_t N, int B, int k, cons
                 void *stream);
 
 /*
+ * pca_fit_host -- pca_fit of a cube that lives in host memory, with the
+ * transfers overlapped with the stages.  (The paper's GPU code copies the
+ * whole image before its first stage, Sec. 4.2 stage 1, and its times include
+ * that copy.)  The cube is copied to the device in pixel ranges (at most 16,
+ * each a multiple of 128 pixels and at least 65,536 pixels); the covariance of
+ * a range runs as soon as its copy has landed, the ranges' means and
+ * covariances are pooled exactly in FP64 (the rule of pca_combine_moments),
+ * then the eigen-decomposition runs as in pca_fit, and the projection of each
+ * range is copied back while the next range is projected.  The results equal
+ * pca_fit's within its error bounds, not bit for bit (each range has its own
+ * shift and accumulation runs).
+ *   cube_host  [N][B] of dtype in host memory.  Page-locked memory
+ *              (cudaHostAlloc, or torch's pin_memory) lets the copies run
+ *              asynchronously; pageable memory works but makes them blocking.
+ *   mu [B], eigvals [B], eigvecs [B][B] (FP64) and proj [N][k] (FP32): host
+ *              memory, written as pca_fit writes them; proj may be NULL
+ *              (no projection).
+ *   cube_dev   device buffer of N*B elements of dtype, 16-byte aligned,
+ *              receives the cube (its contents afterwards: the cube).
+ *   proj_dev   device buffer of N*k floats, 16-byte aligned, receives the
+ *              projection before it is copied back (NULL when proj is NULL).
+ *   workspace  device, at least pca_fit_host_workspace_size() bytes, 256-byte
+ *              aligned.
+ * Everything is enqueued on `stream`; an internal copy stream joins it before
+ * the call's last operation, so `stream` completes after every copy.  The host
+ * buffers must stay valid (and cube_host unchanged) until then.  With info
+ * non-NULL the call waits for `stream` and fills it (as pca_fit).  Return
+ * codes as pca_fit; PCA_ERR_ARG also for a misaligned proj_dev or a NULL one
+ * with proj given.
+ */
+size_t pca_fit_host_workspace_size(int64_t N, int B, int k, pca_dtype dtype, pca_precision prec);
+int pca_fit_host(const void *cube_host, pca_dtype dtype, int64_t N, int B, int k, double tol,
+                 int sweeps_max, pca_precision prec, double *mu, double *eigvals, double *eigvecs,
+                 float *proj, void *cube_dev, float *proj_dev, void *workspace, size_t ws_bytes,
+                 void *stream, pca_info *info);
+
+/*
  * pca_bsq_to_bip -- band-sequential input.  The paper's GPU code stores each
  * band contiguously (Sec. 4.2, data initialisation: value (n, b) at
  * bsq[b*N + n]); every other entry point takes the pixel-major layout.  This

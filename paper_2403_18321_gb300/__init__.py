@@ -34,7 +34,8 @@ EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_p
            "pca_batch_workspace_size", "pca_batch_create", "pca_batch_run", "pca_batch_read_info",
            "pca_batch_destroy", "pca_fit_batched", "pca_batch_kernel_launches",
            "pca_combine_moments", "pca_bsq_to_bip", "pca_tuning_defaults", "pca_set_tuning",
-           "pca_get_tuning", "pca_batch_jacobi_ctas", "pca_batch_plan_counts")
+           "pca_get_tuning", "pca_batch_jacobi_ctas", "pca_batch_plan_counts",
+           "pca_fit_host_workspace_size", "pca_fit_host")
 STAGES = ("covariance", "cov_finalize", "jacobi", "empty", "compact", "refine", "sort_sign",
           "project")
 
@@ -120,6 +121,11 @@ def load(build_if_missing: bool = False):
     lib.pca_eigh.restype = i
     lib.pca_project.argtypes = [P, i, i64, i, i, P, P, P, P, sz, P]
     lib.pca_project.restype = i
+    lib.pca_fit_host_workspace_size.argtypes = [i64, i, i, i, i]
+    lib.pca_fit_host_workspace_size.restype = sz
+    lib.pca_fit_host.argtypes = [P, i, i64, i, i, d, i, i, P, P, P, P, P, P, P, sz, P,
+                                 ctypes.POINTER(Info)]
+    lib.pca_fit_host.restype = i
     lib.pca_project_noalloc.argtypes = [P, i, i64, i, i, P, P, P, P]
     lib.pca_project_noalloc.restype = i
     lib.pca_backward_workspace_size.argtypes = [i64, i, i]
@@ -421,15 +427,69 @@ def profile_collect(max_records: int = 256):
     return [{s: float(buf[r * len(STAGES) + i]) for i, s in enumerate(STAGES)} for r in range(n)]
 
 
+class HostFit:
+    """Device buffers for repeated pca_fit_host calls of one problem shape: the
+    device copy of the cube, the device projection and the workspace."""
+
+    def __init__(self, N: int, B: int, k: int, dtype, precision="mix", device="cuda",
+                 project: bool = True):
+        import torch
+        self.shape, self.k, self.dtype, self.precision = (int(N), int(B)), int(k), dtype, precision
+        dt = _dtype_code(torch.empty(0, dtype=dtype))
+        n = int(load().pca_fit_host_workspace_size(N, B, k, dt, _prec_code(precision)))
+        if n == 0:
+            raise PCAError(1, "pca_fit_host_workspace_size rejected the shape")
+        self.workspace = Workspace(torch.empty(n + 256, dtype=torch.uint8, device=device), n)
+        self.cube_dev = torch.empty(N, B, dtype=dtype, device=device)
+        self.proj_dev = torch.empty(N, k, dtype=torch.float32, device=device) if project else None
+
+
 def fit_host(cube_host, k: int, tol: float = 1e-10, sweeps_max: int = 30, precision="mix",
-             workspace: Workspace | None = None, device="cuda"):
-    """End-to-end from a (pinned) host cube: H2D copy, pca_fit, D2H of the results."""
+             buffers: HostFit | None = None, out=None, project: bool = True, sync: bool = True,
+             stream=None, device="cuda"):
+    """PCA of a host cube [N, B] (float32/bfloat16/float16, pinned memory for
+    overlapped copies) through pca_fit_host: the upload overlaps the covariance,
+    the download of the projection overlaps the projection.  Returns host
+    tensors (mu, eigvals, eigvecs, proj or None, info or None); with
+    sync=False nothing waits and info is None (the results are valid once
+    `stream` has finished)."""
     import torch
-    d = cube_host.to(device, non_blocking=True)
-    mu, ev, V, Q, _ = fit(d, k, tol, sweeps_max, precision, workspace=workspace, sync=False)
-    outs = [t.to("cpu", non_blocking=True) for t in (mu, ev, V, Q) if t is not None]
-    torch.cuda.current_stream(d.device).synchronize()
-    return outs
+    if not isinstance(cube_host, torch.Tensor) or cube_host.is_cuda:
+        raise TypeError("cube_host must be a host tensor")
+    if cube_host.dim() != 2 or not cube_host.is_contiguous():
+        raise ValueError("cube_host must be a contiguous 2-D tensor")
+    N, B = cube_host.shape
+    dt = _dtype_code(cube_host)
+    if buffers is None:
+        buffers = HostFit(N, B, k, cube_host.dtype, precision, device, project)
+    if buffers.shape != (N, B) or buffers.k != k or buffers.dtype != cube_host.dtype:
+        raise ValueError("buffers were made for another problem shape")
+    pin = cube_host.is_pinned()
+    if out is None:
+        mu = torch.empty(B, dtype=torch.float64, pin_memory=pin)
+        ev = torch.empty(B, dtype=torch.float64, pin_memory=pin)
+        V = torch.empty(B, B, dtype=torch.float64, pin_memory=pin)
+        Q = torch.empty(N, k, dtype=torch.float32, pin_memory=pin) if project else None
+    else:
+        mu, ev, V, Q = out
+    if Q is not None and buffers.proj_dev is None:
+        raise ValueError("buffers were made without a projection")
+    dev = buffers.cube_dev.device
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    info = Info() if sync else None
+    rc = load().pca_fit_host(ctypes.c_void_p(cube_host.data_ptr()), dt, N, B, int(k), float(tol),
+                             int(sweeps_max), _prec_code(precision),
+                             ctypes.c_void_p(mu.data_ptr()), ctypes.c_void_p(ev.data_ptr()),
+                             ctypes.c_void_p(V.data_ptr()),
+                             ctypes.c_void_p(Q.data_ptr()) if Q is not None else None,
+                             ctypes.c_void_p(buffers.cube_dev.data_ptr()),
+                             ctypes.c_void_p(buffers.proj_dev.data_ptr()) if Q is not None else None,
+                             ctypes.c_void_p(_ws_ptr(buffers.workspace)), buffers.workspace.nbytes,
+                             ctypes.c_void_p(st.cuda_stream),
+                             ctypes.byref(info) if info is not None else None)
+    if rc not in (0, 2) and not (rc == 3 and info is not None):
+        raise PCAError(rc, load().pca_status_string(rc).decode())
+    return mu, ev, V, Q, (info.as_dict() if info is not None else None)
 
 
 def backward(cube, mu, eigvals, eigvecs, dproj, deigvals=None, gap_eps: float = 1e-6,

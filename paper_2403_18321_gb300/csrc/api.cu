@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -417,6 +418,158 @@ int pca_project(const void* cube, pca_dtype dt, int64_t N, int B, int k, const d
   GB_CK(launch_narrow_inputs(mu, eigvecs, B, k, P.muf, P.vk, st));
   GB_CK(launch_project(cube, dt, N, B, k, P.muf, P.vk, proj, st, P.hdr));
   return PCA_OK;
+}
+
+}  // extern "C"
+
+namespace gbpca {
+namespace {
+
+// ---- host-resident cubes: the pixel ranges whose copies overlap the stages
+constexpr int kHostRanges = 16;
+constexpr int64_t kHostMinRange = 65536;
+
+struct HostLayout {
+  int64_t range = 0;     // pixels per range (the last one takes the rest)
+  int parts = 0;
+  Layout L{};            // the fit's layout, sized for the largest range
+  size_t mu_parts = 0, C_parts = 0, mu = 0, ev = 0, V = 0, total = 0;
+};
+
+HostLayout make_host_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, int sms) {
+  HostLayout H;
+  int64_t r = std::max<int64_t>((N + kHostRanges - 1) / kHostRanges, kHostMinRange);
+  r = (r + 127) & ~int64_t(127);            // 16-byte aligned range starts
+  H.range = std::min(r, N);
+  H.parts = (int)((N + H.range - 1) / H.range);
+  if (H.parts > 1 && N - (int64_t)(H.parts - 1) * H.range < 2) --H.parts;   // no 1-pixel range
+  const int64_t last = N - (int64_t)(H.parts - 1) * H.range;
+  H.L = make_layout(std::max(H.range, last), B, k, dt, prec, sms);
+  size_t o = align256(H.L.total);
+  auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
+  H.mu_parts = take(sizeof(double) * (size_t)H.parts * B);
+  H.C_parts = take(sizeof(double) * (size_t)H.parts * B * B);
+  H.mu = take(sizeof(double) * B);
+  H.ev = take(sizeof(double) * B);
+  H.V = take(sizeof(double) * (size_t)B * B);
+  H.total = o;
+  return H;
+}
+
+}  // namespace
+}  // namespace gbpca
+
+extern "C" {
+
+size_t pca_fit_host_workspace_size(int64_t N, int B, int k, pca_dtype dtype, pca_precision prec) {
+  static const float kDummy[4] = {0.f, 0.f, 0.f, 0.f};
+  if (!args_ok(kDummy, dtype, N, B, k, 1.0, 1, prec)) return 0;
+  return make_host_layout(N, B, k, dtype, prec, device_sms()).total;
+}
+
+int pca_fit_host(const void* cube_host, pca_dtype dt, int64_t N, int B, int k, double tol,
+                 int sweeps_max, pca_precision prec, double* mu, double* eigvals, double* eigvecs,
+                 float* proj, void* cube_dev, float* proj_dev, void* workspace, size_t ws_bytes,
+                 void* stream, pca_info* info) {
+  if (!cube_host || !args_ok(cube_dev, dt, N, B, k, tol, sweeps_max, prec)) return PCA_ERR_ARG;
+  if (!mu || !eigvals || !eigvecs) return PCA_ERR_ARG;
+  if (proj && (!proj_dev || ((uintptr_t)proj_dev) % 16 != 0)) return PCA_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace) % 256 != 0) return PCA_ERR_WORKSPACE;
+  const HostLayout H = make_host_layout(N, B, k, dt, prec, device_sms());
+  if (ws_bytes < H.total) return PCA_ERR_WORKSPACE;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  const Ptrs P = carve(workspace, H.L);
+  double* mu_parts = reinterpret_cast<double*>(ws + H.mu_parts);
+  double* C_parts = reinterpret_cast<double*>(ws + H.C_parts);
+  double* mu_d = reinterpret_cast<double*>(ws + H.mu);
+  double* ev_d = reinterpret_cast<double*>(ws + H.ev);
+  double* V_d = reinterpret_cast<double*>(ws + H.V);
+  const size_t el = dt == PCA_F32 ? 4 : 2;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the copies run on a stream of their own, ordered against `st` by events
+  cudaStream_t cs = nullptr;
+  GB_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  std::vector<cudaEvent_t> evs;
+  auto event = [&](cudaEvent_t* e) {
+    const cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+    if (r == cudaSuccess) evs.push_back(*e);
+    return r;
+  };
+  // the events and the copy stream are released once their work is done
+  auto finish = [&](int rc) {
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    cudaStreamDestroy(cs);
+    return rc;
+  };
+#define GB_HK(x)                                            \
+  do {                                                      \
+    if ((x) != cudaSuccess) return finish(PCA_ERR_CUDA);    \
+  } while (0)
+  const float tol32 = std::max((float)tol, stop_floor(prec));
+  StageMark pm(st);
+  cudaEvent_t start;
+  GB_HK(event(&start));
+  GB_HK(cudaEventRecord(start, st));          // the copies follow earlier work on `st`
+  GB_HK(cudaStreamWaitEvent(cs, start, 0));
+  k_header_init<<<1, 1, 0, st>>>(P.hdr, refine_iterations(prec), tol32);
+  GB_HK(cudaGetLastError());
+  // stages 1-3 per pixel range, each as soon as its bytes are on the device
+  std::vector<int64_t> counts((size_t)H.parts);
+  for (int c = 0; c < H.parts; ++c) {
+    const int64_t p0 = (int64_t)c * H.range;
+    const int64_t n = c + 1 < H.parts ? H.range : N - p0;
+    counts[(size_t)c] = n;
+    const unsigned char* src = static_cast<const unsigned char*>(cube_host) + (size_t)p0 * B * el;
+    unsigned char* dst = static_cast<unsigned char*>(cube_dev) + (size_t)p0 * B * el;
+    GB_HK(cudaMemcpyAsync(dst, src, (size_t)n * B * el, cudaMemcpyHostToDevice, cs));
+    cudaEvent_t in;
+    GB_HK(event(&in));
+    GB_HK(cudaEventRecord(in, cs));
+    GB_HK(cudaStreamWaitEvent(st, in, 0));
+    const Layout Lc = make_layout(n, B, k, dt, prec, device_sms());
+    Ptrs Pc = carve(workspace, Lc);
+    Pc.C = C_parts + (size_t)c * B * B;
+    GB_HK(run_cov(dst, dt, n, B, prec, Lc, Pc, mu_parts + (size_t)c * B, st, pm));
+  }
+  // the ranges' moments pooled exactly (Chan, Golub and LeVeque), then stage 4
+  if (pca_combine_moments(H.parts, counts.data(), mu_parts, C_parts, B, mu_d, P.C, st) != PCA_OK)
+    return finish(PCA_ERR_CUDA);
+  GB_HK(run_eigh(P.C, B, tol32, sweeps_max, prec, k, P, ev_d, V_d, st, pm));
+  GB_HK(launch_narrow_inputs(mu_d, V_d, B, k, P.muf, P.vk, st));
+  GB_HK(cudaMemcpyAsync(mu, mu_d, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  GB_HK(cudaMemcpyAsync(eigvals, ev_d, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  GB_HK(cudaMemcpyAsync(eigvecs, V_d, sizeof(double) * B * B, cudaMemcpyDeviceToHost, st));
+  // stages 5-6 per range, each range's rows copied back while the next is projected
+  pm.mark(7);
+  if (proj) {
+    for (int c = 0; c < H.parts; ++c) {
+      const int64_t p0 = (int64_t)c * H.range, n = counts[(size_t)c];
+      const unsigned char* cube_c = static_cast<const unsigned char*>(cube_dev) + (size_t)p0 * B * el;
+      float* q = proj_dev + (size_t)p0 * k;
+      if (prec == PCA_PREC_MIX) {
+        GB_HK(launch_project_tc(cube_c, dt, n, B, k, mu_d, V_d, q, P.ptc_shift, P.ptc_escale,
+                                P.ptc_planes, P.ptc_colscale, P.ptc_corr, P.hdr, st));
+        GB_HK(launch_project(cube_c, dt, n, B, k, P.muf, P.vk, q, st, P.hdr, &P.hdr->proj_range));
+      } else {
+        GB_HK(launch_project(cube_c, dt, n, B, k, P.muf, P.vk, q, st, P.hdr));
+      }
+      cudaEvent_t out;
+      GB_HK(event(&out));
+      GB_HK(cudaEventRecord(out, st));
+      GB_HK(cudaStreamWaitEvent(cs, out, 0));
+      GB_HK(cudaMemcpyAsync(proj + (size_t)p0 * k, q, sizeof(float) * (size_t)n * k,
+                            cudaMemcpyDeviceToHost, cs));
+    }
+  }
+  pm.mark(8);
+  cudaEvent_t done;
+  GB_HK(event(&done));
+  GB_HK(cudaEventRecord(done, cs));
+  GB_HK(cudaStreamWaitEvent(st, done, 0));     // `st` completes after the last copy
+#undef GB_HK
+  const int rc = finish(PCA_OK);
+  if (rc == PCA_OK && info) return pca_read_info(workspace, stream, info);
+  return rc;
 }
 
 const char* pca_status_string(int status) {

@@ -53,8 +53,16 @@ constexpr int kKC = 32;                 // pixels per chunk (K of one stage)
 constexpr int kMaxStages = 12;          // TMA ring depth: as many stages as shared memory holds
 constexpr int kOpStages = 3;            // FP16 operand ring depth
 constexpr int kRows = 256;              // operand rows (bands, padded to 16)
-constexpr int kConvWarps = 16;
+#ifndef GBPCA_COV_CONV_WARPS
+#define GBPCA_COV_CONV_WARPS 16
+#endif
+constexpr int kConvWarps = GBPCA_COV_CONV_WARPS;   // 8 or 16
 constexpr int kThreads = (2 + kConvWarps) * 32;
+constexpr int kConvThreads = kConvWarps * 32;
+constexpr int kRowsPT = 32 * 32 / kConvThreads;  // pixel rows of a chunk per converter thread
+constexpr int kRowStep = 32 / kRowsPT;           // a thread's rows: pr, pr + kRowStep, ...
+constexpr int kProbeHalves = kConvThreads / 256; // threads per band in the probe
+static_assert(kConvWarps == 8 || kConvWarps == 16, "8 or 16 converter warps");
 constexpr int kOpBytes = kRows * kKC * 2;        // one FP16 operand (hi or lo): 16 KB
 // Operands in the MN-major layout with the 128-byte swizzle, in the cube's own
 // order: per pixel (K) a row of 64 bands (MN) = 128 bytes; 8 pixel rows form a
@@ -344,9 +352,9 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
     const void* probed = nullptr;     // the cube (and pixel count) whose shift and
     int64_t probed_n = -1;            // scale are in shs / sesc
     int mapB = -1;                    // the band count of the current unit layout
-    int pr = 0, gq = 0;               // this thread's pixel-row pair and band group
-    uint32_t uoff[2] = {0u, 0u};      // its units' byte offsets in an operand
-    uint32_t dirty = 0;               // bit 2 o + u: lo unit u of operand stage o is non-zero
+    int pr = 0, gq = 0;               // this thread's first pixel row and band group
+    uint32_t uoff[kRowsPT] = {};      // its units' byte offsets in an operand
+    uint32_t dirty = 0;               // bit kRowsPT o + u: lo unit u of operand stage o is non-zero
     for (int i = 0; i < nitems; ++i) {
       const TcItem it = tc_item(one, T, items, cta_items, i);
       const In* cube = static_cast<const In*>(it.t.cube);
@@ -365,19 +373,20 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         probed = it.t.cube;
         probed_n = N;
         const int Sp = (int)(N < kProbe ? N : kProbe);
-        const int b = ct % kRows, half = ct / kRows;     // 512 threads: two halves of the sample
+        const int b = ct % kRows, half = ct / kRows;     // kProbeHalves threads per band
         double sum = 0.0;
         float lo = INFINITY, hi = -INFINITY;
         if (b < B) {
-          float y[kProbe / 2];
+          constexpr int kPer = kProbe / kProbeHalves;
+          float y[kPer];
 #pragma unroll
-          for (int u = 0; u < kProbe / 2; ++u) {
-            const int pi = half + 2 * u;
+          for (int u = 0; u < kPer; ++u) {
+            const int pi = half + kProbeHalves * u;
             y[u] = pi < Sp ? elem(cube + ((int64_t)pi * N / Sp) * B + b) : 0.f;
           }
 #pragma unroll
-          for (int u = 0; u < kProbe / 2; ++u) {
-            if (half + 2 * u < Sp) {
+          for (int u = 0; u < kPer; ++u) {
+            if (half + kProbeHalves * u < Sp) {
               sum += (double)y[u];
               lo = fminf(lo, y[u]);
               hi = fmaxf(hi, y[u]);
@@ -392,9 +401,14 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
           float m = 0.f;
           int e = 0;
           if (b < B) {
-            const double tot = psum[b] + psum[kRows + b];
-            lo = fminf(pmin[b], pmin[kRows + b]);
-            hi = fmaxf(pmax[b], pmax[kRows + b]);
+            double tot = psum[b];
+            lo = pmin[b];
+            hi = pmax[b];
+            if (kProbeHalves > 1) {
+              tot += psum[kRows + b];
+              lo = fminf(lo, pmin[kRows + b]);
+              hi = fmaxf(hi, pmax[kRows + b]);
+            }
             m = on_grid<In>((float)(tot / (double)Sp));
             double dev = fmax((double)hi - (double)m, (double)m - (double)lo);
             if (!isfinite(m) || !isfinite(dev)) { m = 0.f; dev = 0.0; }
@@ -412,9 +426,9 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         }
         conv_sync();
       }
-      // Units: thread ct owns the 8-band group gq of pixel rows pr and pr + 16
-      // of every chunk (16 G8 <= 512 threads; the others only take part in the
-      // barriers), so the per-band constants of its bands stay in registers:
+      // Units: thread ct owns the 8-band group gq of pixel rows pr, pr + kRowStep,
+      // ... of every chunk (kRowStep G8 <= kConvThreads; the others only take
+      // part in the barriers), so the per-band constants of its bands stay in registers:
       // x = y 2^e - s 2^e in one FMA (y 2^e and s 2^e are exact); bands past B
       // get 0, 0.  Its values are written as one 16-byte row unit of the
       // MN-major operand with the 128-byte swizzle: 64-band blocks 4 KB apart,
@@ -427,8 +441,8 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         // before its epilogue, which the barrier above follows).
         for (int o = 0; o < kOpStages; ++o)
 #pragma unroll
-          for (int u = 0; u < 2; ++u)
-            if (dirty & (1u << (2 * o + u)))
+          for (int u = 0; u < kRowsPT; ++u)
+            if (dirty & (1u << (kRowsPT * o + u)))
               *reinterpret_cast<uint4*>(ops + (size_t)(o * 2 + 1) * kOpBytes + uoff[u]) =
                   make_uint4(0, 0, 0, 0);
         dirty = 0;
@@ -453,13 +467,13 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         pr = ct / G8;
         gq = ct - pr * G8;
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int pp = pr < 16 ? pr + 16 * u : 0;
+        for (int u = 0; u < kRowsPT; ++u) {
+          const int pp = pr < kRowStep ? pr + kRowStep * u : 0;
           uoff[u] = (uint32_t)(gq >> 3) * kMnLBO + (uint32_t)(pp >> 3) * kMnSBO + (pp & 7) * 128 +
                     ((uint32_t)((gq & 7) ^ (pp & 7)) << 4);
         }
       }
-      const bool act = pr < 16;
+      const bool act = pr < kRowStep;
       const int b0 = 8 * gq;
       float sc[8], sh[8];
       uint32_t sc16[4];          // BF16 cubes: the scales as packed BF16 pairs
@@ -502,8 +516,8 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         uint32_t lo_bits = 0;    // OR of this thread's lo parts in this chunk
         if (act) {
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int pp = pr + 16 * u;
+          for (int u = 0; u < kRowsPT; ++u) {
+            const int pp = pr + kRowStep * u;
             float x[8];
             if (fast) {
               const In* src = st + pp * B + b0;
@@ -565,7 +579,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
             // the lo unit is stored when it is non-zero, or to clear what this
             // thread left there before; a unit that is and stays zero is skipped
             const uint32_t lu = (l[0] | l[1]) | (l[2] | l[3]);
-            const uint32_t bit = 1u << (2 * o + u);
+            const uint32_t bit = 1u << (kRowsPT * o + u);
             if (lu != 0u || (dirty & bit)) {
               *reinterpret_cast<uint4*>(lo + uoff[u]) = make_uint4(l[0], l[1], l[2], l[3]);
               dirty = lu != 0u ? (dirty | bit) : (dirty & ~bit);
@@ -594,7 +608,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
       // barrier, and a uniform decision to stop after an abandoned wait
       const bool aborted = conv_or(*(volatile int*)&sb->abort) != 0;
       // ---------------------------------------------------------- epilogue
-      // All 16 converter warps: warp w reads TMEM lane quarter w mod 4 (the
+      // All converter warps: warp w reads TMEM lane quarter w mod 4 (the
       // quarter it may access) and every fourth 16-column block, from block
       // (w - 2) / 4 on.
       {
@@ -607,12 +621,12 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         const int N0 = R16, N1 = B > 128 ? R16 - 128 : 0;
         const int ob = ones_band(B);      // accumulator column of the band sums (-1: separate)
         const int q4 = warp & 3;          // TMEM lane quarter this warp may read
-        const int part = cw >> 2;         // 0..3: which blocks of the quarter
+        const int part = cw >> 2;         // which blocks of the quarter (kConvWarps / 4 parts)
         const int r = q4 * 32 + lane;     // accumulator row
         const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
         float* out = io.t.s2_part + (size_t)io.slot * (B * (B + 1) / 2);
         const int nb0 = N0 >> 4, nb = nb0 + (N1 >> 4);
-        for (int bk = part; bk < nb; bk += 4) {
+        for (int bk = part; bk < nb; bk += kConvWarps / 4) {
           const bool t1 = bk >= nb0;
           const int j0 = (t1 ? bk - nb0 : bk) << 4;       // column within the tile
           float v[16];

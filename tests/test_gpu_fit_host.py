@@ -1,0 +1,53 @@
+"""pca_fit_host (host cube in, host results out, copies overlapped with the
+stages in pixel ranges) against the FP64 oracle, through the C ABI: several
+ranges with a ragged last one, a last range that would hold one pixel, BF16
+input, pageable input memory, and no projection."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity import compare
+
+
+def _cube(N, B, seed, dtype):
+    c = synth.linear_mixing(seed=seed, rows=1, cols=N, bands=B, endmembers=6)
+    Y = torch.from_numpy(c.Y).to(dtype)
+    return c, Y
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,dtype,N,pinned", [
+    ("mix", torch.float32, 200_003, True),      # 4 ranges, the last ragged
+    ("p32", torch.float32, 65_537, True),       # the 1-pixel tail joins the only range
+    ("mix", torch.bfloat16, 140_000, True),
+    ("p64", torch.float32, 70_000, False),      # pageable host memory
+])
+def test_fit_host_against_oracle(gbpca_lib, precision, dtype, N, pinned):
+    g = gbpca_lib
+    c, Y = _cube(N, 40, 31, dtype)
+    Yh = Y.pin_memory() if pinned else Y
+    k = 6
+    mu, ev, V, Q, info = g.fit_host(Yh, k, tol=1e-12, precision=precision)
+    assert info["status"] == 0, info
+    ref = oracle.pca_fit(Y.float().numpy().astype(np.float64), k, tol=1e-14)
+    m = compare((mu.numpy(), ev.numpy(), V.numpy(), Q.numpy().astype(np.float64)), ref, k,
+                precision)
+    print(precision, dtype, N, m)
+    # the device copy of the cube is the cube
+    hb = g.HostFit(N, 40, k, dtype, precision)
+    g.fit_host(Yh, k, tol=1e-12, precision=precision, buffers=hb)
+    assert torch.equal(hb.cube_dev.cpu(), Y)
+
+
+@pytest.mark.gpu
+def test_fit_host_matches_fit_and_skips_projection(gbpca_lib):
+    g = gbpca_lib
+    c, Y = _cube(150_000, 64, 32, torch.float32)
+    Yh = Y.pin_memory()
+    mu, ev, V, Q, info = g.fit_host(Yh, 5, precision="p32", project=False)
+    assert Q is None and info["status"] == 0
+    mu2, ev2, V2, _, _ = g.fit(Y.cuda(), 5, precision="p32")
+    assert np.abs(mu.numpy() - mu2.cpu().numpy()).max() <= 1e-6 * np.abs(mu2.cpu().numpy()).max()
+    assert np.abs(ev.numpy()[:5] - ev2.cpu().numpy()[:5]).max() <= 2e-5 * ev2[0].item()

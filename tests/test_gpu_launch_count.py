@@ -42,7 +42,7 @@ def test_kernel_launches_match_a_captured_fit(gbpca_lib, precision, k, bands):
     outs = (torch.empty(B, dtype=torch.float64, device="cuda"),
             torch.empty(B, dtype=torch.float64, device="cuda"),
             torch.empty(B, B, dtype=torch.float64, device="cuda"),
-            torch.empty(N, max(k, 1), dtype=torch.float32, device="cuda"))
+            torch.empty(N, max(k, 1), dtype=torch.float32, device="cuda") if k > 0 else None)
     kw = dict(precision=precision, out=outs, workspace=ws, project=k > 0)
     g.fit(Y, max(k, 1), **kw)            # first call: one-time set-up outside the capture
     torch.cuda.synchronize()
