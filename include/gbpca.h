@@ -360,10 +360,15 @@ int pca_fit_batched(int ntiles, const pca_tile *tiles, pca_dtype dtype, double t
  * tc_slot_chunks   MIX covariance of FP32 cubes: the longest run of 32-pixel
  *                  chunks that one tensor-memory accumulator sums in FP32
  *                  before it is written out and added in FP64 (1..1024,
- *                  default 8).  The FP32 accumulation error grows linearly with
+ *                  default 4).  The FP32 accumulation error grows linearly with
  *                  the run (measured ||dC||_2 / lambda_1 on the 610x340x103
- *                  scene: 3.0e-7 at 2 chunks, 1.2e-6 at 8, 2.5e-6 at 16, 8.0e-6
- *                  at 64); shorter runs write more partials.
+ *                  scene: 3.0e-7 at 2 chunks, 6.1e-7 at 4, 1.2e-6 at 8, 2.5e-6
+ *                  at 16, 8.0e-6 at 64); shorter runs write more partials.  At
+ *                  4 chunks every top-10 eigenvalue of the two paper-shaped
+ *                  scene cubes is within 1.2e-5 of its own size (2.6e-5 at 8).
+ * tc_slot_chunks_batch  the same for the FP32 tiles of the batched form
+ *                  (default 8: its tiles' top eigenvalues stay within 1.1e-6
+ *                  there, and shorter runs cost it 20% more time).
  * tc_slot_chunks_f16, tc_slot_chunks_bf16  the same for FP16 and BF16 cubes
  *                  (defaults 64 and 1024).  Their shifted values fit one FP16
  *                  each, the products are exact, and so are the FP32 sums while
@@ -403,6 +408,7 @@ typedef struct {
   int batch_simt_items_per_sm;
   int proj_tc_stages;
   int proj_tc_raw_stages;
+  int tc_slot_chunks_batch;
 } pca_tuning;
 void pca_tuning_defaults(pca_tuning *t);
 int pca_set_tuning(const pca_tuning *t);

@@ -26,10 +26,11 @@ __global__ void k_header_init(DevHeader* h, int refine_iters, float tol32) {
 
 }  // namespace
 
-// FP32 cubes: 8 chunks = 256 pixels per slot by default.  The covariance error
+// FP32 cubes: 4 chunks = 128 pixels per slot by default.  The covariance error
 // grows linearly with the slot length (||dC||_2 / lambda_1 on the 103-band scene:
-// 1.2e-6 at 8 chunks, about the plain FP32 form's, 8.0e-6 at 64), at about 50%
-// more covariance time than 64 chunks there.  16-bit cubes: products and sums
+// 6.1e-7 at 4 chunks, half the plain FP32 form's, 1.2e-6 at 8, 8.0e-6 at 64); at
+// 4 chunks every top-10 eigenvalue of both paper-shaped scenes is within 2e-5
+// of its own size.  16-bit cubes: products and sums
 // are exact while the sums stay within FP32's 24 bits -- FP16 64 chunks, BF16
 // (8-bit values) 1024 chunks (equal to the FP64 covariance on the planted cube).
 int tc_slot_chunks(pca_dtype dt) {

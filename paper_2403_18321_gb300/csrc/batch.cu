@@ -168,7 +168,7 @@ BatchLayout batch_layout(const std::vector<pca_tile>& tiles, pca_dtype dt, pca_p
   const int cov_ctas = mix ? sms : tu.batch_simt_items_per_sm * sms;
   L.cov = split_chunks(tiles, kCovChunk, cov_ctas, mix ? Cost::kTensorCov : Cost::kSimtCov, tu);
   if (mix) {  // bound the tensor-core accumulation: long items become several slots
-    const int64_t cap = dt == PCA_F32 ? tu.tc_slot_chunks
+    const int64_t cap = dt == PCA_F32 ? tu.tc_slot_chunks_batch
                                       : (dt == PCA_F16 ? tu.tc_slot_chunks_f16 : tu.tc_slot_chunks_bf16);
     std::vector<int> slot_of(n, 0);
     for (auto& v : L.cov.per_cta) {

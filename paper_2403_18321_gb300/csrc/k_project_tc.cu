@@ -102,11 +102,15 @@ k_ptc_bands(const In* __restrict__ cube, int64_t N, int B, const double* __restr
   if (b >= B) return;
   const float s = on_grid<In>((float)mu[b]);
   const int Sp = (int)(N < kProbe ? N : kProbe);
+  // all sampled loads in flight at once (a loop of dependent loads costs
+  // kProbe memory latencies)
+  float y[kProbe];
+#pragma unroll
+  for (int i = 0; i < kProbe; ++i)
+    y[i] = i < Sp ? to_f32<In>(cube[((int64_t)i * N / Sp) * B + b]) : s;
   float dev = 0.f;
-  for (int i = 0; i < Sp; ++i) {
-    const float y = to_f32<In>(cube[((int64_t)i * N / Sp) * B + b]);
-    dev = fmaxf(dev, fabsf(y - s));
-  }
+#pragma unroll
+  for (int i = 0; i < kProbe; ++i) dev = fmaxf(dev, fabsf(y[i] - s));
   if (!(dev > 0.f) || !isfinite(dev)) dev = fabsf(s);
   int e = 0;
   if (dev > 0.f && isfinite(dev)) {

@@ -12,9 +12,10 @@ namespace {
 
 pca_tuning defaults() {
   pca_tuning t{};
-  t.tc_slot_chunks = 8;
+  t.tc_slot_chunks = 4;
   t.tc_slot_chunks_f16 = 64;
   t.tc_slot_chunks_bf16 = 1024;
+  t.tc_slot_chunks_batch = 8;
   for (int i = 0; i < 8; ++i) t.batch_jacobi_ctas[i] = 0;
   t.batch_cov_tc_fixed = 464.0;
   t.batch_proj_fixed = 223.0;
@@ -30,6 +31,7 @@ pca_tuning g_tuning = defaults();
 
 bool valid(const pca_tuning& t) {
   if (t.tc_slot_chunks < 1 || t.tc_slot_chunks > 1024) return false;
+  if (t.tc_slot_chunks_batch < 1 || t.tc_slot_chunks_batch > 1024) return false;
   if (t.tc_slot_chunks_f16 < 1 || t.tc_slot_chunks_f16 > 1024) return false;
   if (t.tc_slot_chunks_bf16 < 1 || t.tc_slot_chunks_bf16 > 1024) return false;
   for (int i = 0; i < 8; ++i)

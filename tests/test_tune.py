@@ -40,6 +40,7 @@ def test_applied_installs_and_restores(cache):
         assert t["tc_slot_chunks"] == default["tc_slot_chunks"]
         assert t["tc_slot_chunks_f16"] == default["tc_slot_chunks_f16"]
         assert t["tc_slot_chunks_bf16"] == default["tc_slot_chunks_bf16"]
+        assert t["tc_slot_chunks_batch"] == default["tc_slot_chunks_batch"]
     assert g.tuning() == default
 
 
