@@ -448,9 +448,10 @@ int pca_batch_run(pca_batch* b, void* stream) {
   pm.mark(0);
   if (prec == PCA_PREC_MIX) {
     GB_CK(launch_syrk_tc_grouped(b->T, b->cov_items, b->cov_off, b->cov_ctas, maxB, b->dt, st));
-    GB_CK(launch_syrk_simt_grouped(b->T, b->cov_items, b->cov_nitems, maxB, b->dt, false, true, st));
+    GB_CK(launch_syrk_simt_grouped(b->T, b->cov_items, b->cov_nitems, maxB, n, b->dt, false, true,
+                                   st));
   } else {
-    GB_CK(launch_syrk_simt_grouped(b->T, b->cov_items, b->cov_nitems, maxB, b->dt,
+    GB_CK(launch_syrk_simt_grouped(b->T, b->cov_items, b->cov_nitems, maxB, n, b->dt,
                                    prec == PCA_PREC_P64, false, st));
   }
   pm.mark(1);

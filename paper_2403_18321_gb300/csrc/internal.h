@@ -283,9 +283,10 @@ cudaError_t launch_header_init_batched(TileDesc* T, int ntiles, int refine_iters
                                        cudaStream_t st);
 // SIMT partials of every item (grid: items x band-tile groups of the largest B).
 // guarded: a tile is skipped unless its hdr->cov_range is set, and a run then
-// zeroes its escale.
+// zeroes its escale; the launch is a small grid that returns at once when no
+// tile of the ntiles is flagged.
 cudaError_t launch_syrk_simt_grouped(const TileDesc* T, const CovItem* items, int nitems,
-                                     int maxB, pca_dtype dt, bool fp64, bool guarded,
+                                     int maxB, int ntiles, pca_dtype dt, bool fp64, bool guarded,
                                      cudaStream_t st);
 // Tensor-core partials: CTA g walks items [cta_items[g], cta_items[g+1]).
 cudaError_t launch_syrk_tc_grouped(const TileDesc* T, const CovItem* items, const int* cta_items,

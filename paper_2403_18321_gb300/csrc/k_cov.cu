@@ -111,82 +111,117 @@ __device__ __forceinline__ void syrk_simt_cta(const In* __restrict__ cube, int B
   }
 }
 
-// Grid: x = partial slot (pixel range), y = band-tile group.
-template <typename In, typename Acc, int TM>
+// Grid: x walks the partial slots g (pixel ranges N g / parts ..), y = band-tile
+// group.  The guarded form (the re-computation after an out-of-range
+// tensor-core pass) runs on a small grid that returns at once when the flag is
+// clear, instead of one CTA per slot.
+template <typename In, typename Acc, int TM, bool kGuarded>
 __global__ void __launch_bounds__(kSyrkThreads)
-k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, float* __restrict__ shift_out,
+k_syrk_simt(const In* __restrict__ cube, int64_t N, int B, int parts, float* __restrict__ shift_out,
             double* __restrict__ s1_part, Acc* __restrict__ s2_part,
             const int* __restrict__ guard, int* __restrict__ escale) {
-  // guarded form: the re-computation after an out-of-range tensor-core pass
-  if (guard != nullptr && *(volatile const int*)guard == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int G = gridDim.x, g = blockIdx.x;
-  syrk_simt_cta<In, Acc, TM>(cube, B, N * g / G, N * (g + 1) / G, g, blockIdx.y, shift_out,
-                             s1_part, s2_part, escale, smem_raw);
+  if constexpr (kGuarded) {
+    if (*(volatile const int*)guard == 0) return;
+    for (int g = blockIdx.x; g < parts; g += gridDim.x) {
+      syrk_simt_cta<In, Acc, TM>(cube, B, N * g / parts, N * (g + 1) / parts, g, blockIdx.y,
+                                 shift_out, s1_part, s2_part, escale, smem_raw);
+      __syncthreads();   // the CTA's shared staging is reused by the next slot
+    }
+  } else {   // one slot per CTA
+    const int g = blockIdx.x;
+    syrk_simt_cta<In, Acc, TM>(cube, B, N * g / parts, N * (g + 1) / parts, g, blockIdx.y,
+                               shift_out, s1_part, s2_part, nullptr, smem_raw);
+  }
 }
 
-// Grid: x = item, y = band-tile group (groups beyond the item's tile return).
-template <typename In, typename Acc, int TM>
+// Grid: x walks the items (item x, x + gridDim.x, ...), y = band-tile group
+// (groups beyond an item's tile skip it).  The guarded form runs on a small
+// grid whose CTAs first look at every tile's range flag together and return
+// when none is set, so that the common case costs a few microseconds, not one
+// CTA per item.
+template <typename In, typename Acc, int TM, bool kGuarded>
 __global__ void __launch_bounds__(kSyrkThreads)
-k_syrk_simt_grouped(const TileDesc* __restrict__ T, const CovItem* __restrict__ items,
-                    int guarded) {
+k_syrk_simt_grouped(const TileDesc* __restrict__ T, const CovItem* __restrict__ items, int nitems,
+                    int ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const CovItem it = items[blockIdx.x];
-  const TileDesc& t = T[it.tile];
-  const int B = t.B, Bt = (B + TM - 1) / TM;
-  if ((int)blockIdx.y * kSyrkThreads >= Bt * (Bt + 1) / 2) return;
-  if (guarded && *(volatile const int*)&t.hdr->cov_range == 0) return;
-  syrk_simt_cta<In, Acc, TM>(static_cast<const In*>(t.cube), B, it.p0, it.p1, it.slot, blockIdx.y,
-                             t.shift, t.s1p, static_cast<Acc*>(t.s2p), guarded ? t.escale : nullptr,
-                             smem_raw);
+  if constexpr (kGuarded) {
+    int any = 0;
+    for (int i = threadIdx.x; i < ntiles; i += kSyrkThreads)
+      any |= *(volatile const int*)&T[i].hdr->cov_range;
+    if (!__syncthreads_or(any)) return;
+    for (int x = blockIdx.x; x < nitems; x += gridDim.x) {
+      const CovItem it = items[x];
+      const TileDesc& t = T[it.tile];
+      const int B = t.B, Bt = (B + TM - 1) / TM;
+      if ((int)blockIdx.y * kSyrkThreads >= Bt * (Bt + 1) / 2) continue;
+      if (*(volatile const int*)&t.hdr->cov_range == 0) continue;
+      syrk_simt_cta<In, Acc, TM>(static_cast<const In*>(t.cube), B, it.p0, it.p1, it.slot,
+                                 blockIdx.y, t.shift, t.s1p, static_cast<Acc*>(t.s2p), t.escale,
+                                 smem_raw);
+      __syncthreads();   // the CTA's shared staging is reused by the next item
+    }
+  } else {   // one item per CTA
+    const CovItem it = items[blockIdx.x];
+    const TileDesc& t = T[it.tile];
+    const int B = t.B, Bt = (B + TM - 1) / TM;
+    if ((int)blockIdx.y * kSyrkThreads >= Bt * (Bt + 1) / 2) return;
+    syrk_simt_cta<In, Acc, TM>(static_cast<const In*>(t.cube), B, it.p0, it.p1, it.slot,
+                               blockIdx.y, t.shift, t.s1p, static_cast<Acc*>(t.s2p), nullptr,
+                               smem_raw);
+  }
 }
 
 template <typename In>
 cudaError_t syrk_simt_typed(const In* cube, int64_t N, int B, bool fp64, float* shift,
                             double* s1_part, void* s2_part, int partials, cudaStream_t st,
                             const int* guard, int* escale) {
+  const int gx = guard != nullptr ? std::min(partials, 4 * device_sms()) : partials;
   if (fp64) {
     constexpr int TM = 4;
     const int Bt = (B + TM - 1) / TM, ntiles = Bt * (Bt + 1) / 2;
     const int groups = (ntiles + kSyrkThreads - 1) / kSyrkThreads;
     const size_t smem = (size_t)kChunk * Bt * TM * sizeof(double) + Bt * TM * sizeof(float);
-    auto kern = k_syrk_simt<In, double, TM>;
+    auto kern = guard != nullptr ? k_syrk_simt<In, double, TM, true> : k_syrk_simt<In, double, TM, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(cube, N, B, shift, s1_part,
-                                                             (double*)s2_part, guard, escale);
+    kern<<<dim3(gx, groups), kSyrkThreads, smem, st>>>(cube, N, B, partials, shift, s1_part,
+                                                       (double*)s2_part, guard, escale);
   } else {
     constexpr int TM = 8;
     const int Bt = (B + TM - 1) / TM, ntiles = Bt * (Bt + 1) / 2;
     const int groups = (ntiles + kSyrkThreads - 1) / kSyrkThreads;
     const size_t smem = (size_t)kChunk * Bt * TM * sizeof(float) + Bt * TM * sizeof(float);
-    auto kern = k_syrk_simt<In, float, TM>;
+    auto kern = guard != nullptr ? k_syrk_simt<In, float, TM, true> : k_syrk_simt<In, float, TM, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<dim3(partials, groups), kSyrkThreads, smem, st>>>(cube, N, B, shift, s1_part,
-                                                             (float*)s2_part, guard, escale);
+    kern<<<dim3(gx, groups), kSyrkThreads, smem, st>>>(cube, N, B, partials, shift, s1_part,
+                                                       (float*)s2_part, guard, escale);
   }
   return cudaGetLastError();
 }
 
 template <typename In>
 cudaError_t syrk_simt_grouped_typed(const TileDesc* T, const CovItem* items, int nitems, int maxB,
-                                    bool fp64, bool guarded, cudaStream_t st) {
+                                    int ntiles, bool fp64, bool guarded, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
+  const int gx = guarded ? std::min(nitems, 4 * device_sms()) : nitems;
   if (fp64) {
     constexpr int TM = 4;
     const int Bt = (maxB + TM - 1) / TM, groups = (Bt * (Bt + 1) / 2 + kSyrkThreads - 1) / kSyrkThreads;
     const size_t smem = (size_t)kChunk * Bt * TM * sizeof(double) + Bt * TM * sizeof(float);
-    auto kern = k_syrk_simt_grouped<In, double, TM>;
+    auto kern = guarded ? k_syrk_simt_grouped<In, double, TM, true>
+                        : k_syrk_simt_grouped<In, double, TM, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(nitems, groups), kSyrkThreads, smem, st>>>(T, items, guarded ? 1 : 0);
+    kern<<<dim3(gx, groups), kSyrkThreads, smem, st>>>(T, items, nitems, ntiles);
   } else {
     constexpr int TM = 8;
     const int Bt = (maxB + TM - 1) / TM, groups = (Bt * (Bt + 1) / 2 + kSyrkThreads - 1) / kSyrkThreads;
     const size_t smem = (size_t)kChunk * Bt * TM * sizeof(float) + Bt * TM * sizeof(float);
-    auto kern = k_syrk_simt_grouped<In, float, TM>;
+    auto kern = guarded ? k_syrk_simt_grouped<In, float, TM, true>
+                        : k_syrk_simt_grouped<In, float, TM, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(nitems, groups), kSyrkThreads, smem, st>>>(T, items, guarded ? 1 : 0);
+    kern<<<dim3(gx, groups), kSyrkThreads, smem, st>>>(T, items, nitems, ntiles);
   }
   return cudaGetLastError();
 }
@@ -328,15 +363,16 @@ cudaError_t launch_cov_finalize(const float* shift, const double* s1_part, const
 }
 
 cudaError_t launch_syrk_simt_grouped(const TileDesc* T, const CovItem* items, int nitems,
-                                     int maxB, pca_dtype dt, bool fp64, bool guarded,
+                                     int maxB, int ntiles, pca_dtype dt, bool fp64, bool guarded,
                                      cudaStream_t st) {
   switch (dt) {
     case PCA_F32:
-      return syrk_simt_grouped_typed<float>(T, items, nitems, maxB, fp64, guarded, st);
+      return syrk_simt_grouped_typed<float>(T, items, nitems, maxB, ntiles, fp64, guarded, st);
     case PCA_BF16:
-      return syrk_simt_grouped_typed<__nv_bfloat16>(T, items, nitems, maxB, fp64, guarded, st);
+      return syrk_simt_grouped_typed<__nv_bfloat16>(T, items, nitems, maxB, ntiles, fp64, guarded,
+                                                    st);
     case PCA_F16:
-      return syrk_simt_grouped_typed<__half>(T, items, nitems, maxB, fp64, guarded, st);
+      return syrk_simt_grouped_typed<__half>(T, items, nitems, maxB, ntiles, fp64, guarded, st);
   }
   return cudaErrorInvalidValue;
 }
