@@ -264,18 +264,24 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
   }
   // x = (y - s) 2^e as one FMA: y 2^e is exact (a power of two) and the sum is
   // rounded once, as (y - s) would be before the exact scaling
-  // BF16 cubes read through the tensor map: the raw pairs enter the FMA
-  constexpr bool kBf16 = std::is_same<In, __nv_bfloat16>::value && kTiled;
-  if constexpr (kBf16) {
-    // BF16 cubes: [256] shifts -s 2^e (FP32), then [128] packed BF16 scale pairs
+  // 16-bit cubes read through the tensor map: the raw pairs enter the FMA,
+  // the scales as pairs of the input type (FP16: when every band's scale is
+  // in FP16's normal range)
+  constexpr bool kMix16 = sizeof(In) == 2 && kTiled;
+  constexpr bool kBf = std::is_same<In, __nv_bfloat16>::value;
+  bool in_range = true;
+  for (int b = tid; b < B; b += kThr) in_range &= kBf || (a.escale[b] >= -14 && a.escale[b] <= 15);
+  const bool mix_ok = kMix16 && __syncthreads_and(in_range);
+  if (mix_ok) {
+    // [256] shifts -s 2^e (FP32), then [128] packed scale pairs
     float* shf = reinterpret_cast<float*>(cst);
     uint32_t* scb = reinterpret_cast<uint32_t*>(shf + 256);
     for (int b = tid; b < 256; b += kThr)
       shf[b] = b < B ? -a.shift[b] * ldexpf(1.f, a.escale[b]) : 0.f;
+    auto pw = [&](int e) { return kBf ? bf16_pow2(e) : f16_pow2(e); };
     for (int b2 = tid; b2 < 128; b2 += kThr) {
       const int b = 2 * b2;
-      scb[b2] = (b < B ? bf16_pow2(a.escale[b]) : 0u) |
-                ((b + 1 < B ? bf16_pow2(a.escale[b + 1]) : 0u) << 16);
+      scb[b2] = (b < B ? pw(a.escale[b]) : 0u) | ((b + 1 < B ? pw(a.escale[b + 1]) : 0u) << 16);
     }
   } else {
     for (int b = tid; b < 256; b += kThr) {
@@ -418,7 +424,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
           const unsigned char* bx = box + (size_t)(unit >> 3) * kTM * 128;
           const uint4 v = *reinterpret_cast<const uint4*>(
               bx + pr * 128 + (((unit & 7) ^ (pr & 7)) << 4));
-          if constexpr (kBf16) {
+          if constexpr (kMix16) {
             raw16[4 * u] = v.x; raw16[4 * u + 1] = v.y; raw16[4 * u + 2] = v.z; raw16[4 * u + 3] = v.w;
           } else {
             const In* h = reinterpret_cast<const In*>(&v);
@@ -434,8 +440,15 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
       const int b0 = c * kKC + gp * 16;
       const bool row = tile * kTM + pr < N;    // rows past the cube stay 0
       float x[16];
-      if constexpr (kBf16) {
-        // the BF16 pairs enter the FMA as they are; constants: 16 shifts and
+      if constexpr (kMix16) {
+        if (!mix_ok) {   // FP16 scales out of range: widen the raw values
+          const In* h16 = reinterpret_cast<const In*>(raw16);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) cur[e] = to_f32<In>(h16[e]);
+        }
+      }
+      if (kMix16 && mix_ok) {
+        // the 16-bit pairs enter the FMA as they are; constants: 16 shifts and
         // 8 scale pairs (broadcast reads: the lanes of a warp share b0)
         const float* shf = reinterpret_cast<const float*>(cst);
         const uint32_t* scb = reinterpret_cast<const uint32_t*>(shf + 256);
@@ -452,7 +465,10 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
           sp[e] = t.x; sp[e + 1] = t.y; sp[e + 2] = t.z; sp[e + 3] = t.w;
         }
 #pragma unroll
-        for (int e = 0; e < 8; ++e) fma_bf16x2_f32(raw16[e], sp[e], sh[2 * e], sh[2 * e + 1], x[2 * e], x[2 * e + 1]);
+        for (int e = 0; e < 8; ++e) {
+          if constexpr (kBf) fma_bf16x2_f32(raw16[e], sp[e], sh[2 * e], sh[2 * e + 1], x[2 * e], x[2 * e + 1]);
+          else fma_f16x2_f32(raw16[e], sp[e], sh[2 * e], sh[2 * e + 1], x[2 * e], x[2 * e + 1]);
+        }
         if (!(row && b0 + 16 <= B)) {
 #pragma unroll
           for (int e = 0; e < 16; ++e) x[e] = row && b0 + e < B ? x[e] : 0.f;
@@ -481,7 +497,7 @@ k_project_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ P
         if constexpr (!k16) mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
         h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
         float r0, r1;
-        if constexpr (kBf16) {
+        if constexpr (kMix16) {
           resid_f16x2(h[e], x[2 * e], x[2 * e + 1], r0, r1);
         } else {
           unpack_f16x2(h[e], r0, r1);

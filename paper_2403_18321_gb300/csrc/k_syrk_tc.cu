@@ -475,23 +475,29 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
       }
       const bool act = pr < kRowStep;
       const int b0 = 8 * gq;
+      constexpr bool k16 = sizeof(In) == 2;
+      constexpr bool kBf = std::is_same<In, __nv_bfloat16>::value;
       float sc[8], sh[8];
-      uint32_t sc16[4];          // BF16 cubes: the scales as packed BF16 pairs
+      uint32_t sc16[4];          // 16-bit cubes: the scales as packed pairs of the input type
+      bool mixfma = k16;         // FP16 cubes: scales within FP16's normal range
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int b = b0 + e;
         sc[e] = (act && b < B) ? ldexpf(1.f, sesc[b]) : 0.f;
         sh[e] = (act && b < B) ? -shs[b] * sc[e] : 0.f;
+        if (!kBf && act && b < B && (sesc[b] < -14 || sesc[b] > 15)) mixfma = false;
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        sc16[e] = (sc[2 * e] != 0.f ? bf16_pow2(sesc[b0 + 2 * e]) : 0u) |
-                  ((sc[2 * e + 1] != 0.f ? bf16_pow2(sesc[b0 + 2 * e + 1]) : 0u) << 16);
+      for (int e = 0; e < 4; ++e) {
+        const int e0 = sesc[b0 + 2 * e & 255], e1 = sesc[b0 + 2 * e + 1 & 255];
+        const uint32_t p0 = sc[2 * e] == 0.f ? 0u : (kBf ? bf16_pow2(e0) : f16_pow2(e0));
+        const uint32_t p1 = sc[2 * e + 1] == 0.f ? 0u : (kBf ? bf16_pow2(e1) : f16_pow2(e1));
+        sc16[e] = p0 | (p1 << 16);
+      }
       const bool vec = (B * (int)sizeof(In)) % 16 == 0 && b0 + 8 <= B;
       // a value beyond the FP16 range -> SIMT pass.  FP32 cubes track the
       // largest |x|; for 16-bit cubes (whose lo parts are nearly always zero)
       // an infinite lo part is the sign of it, checked where lo is stored
-      constexpr bool k16 = sizeof(In) == 2;
       float mx = 0.f;
       int rng = 0;
       const int cw = warp - 2;  // converter warp index
@@ -521,13 +527,20 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
             float x[8];
             if (fast) {
               const In* src = st + pp * B + b0;
-              if constexpr (std::is_same<In, __nv_bfloat16>::value) {
-                // the BF16 pairs enter the FMA as they are
+              if (k16 && mixfma) {
+                // the 16-bit pairs enter the FMA as they are
                 const uint4 v = *reinterpret_cast<const uint4*>(src);
-                fma_bf16x2_f32(v.x, sc16[0], sh[0], sh[1], x[0], x[1]);
-                fma_bf16x2_f32(v.y, sc16[1], sh[2], sh[3], x[2], x[3]);
-                fma_bf16x2_f32(v.z, sc16[2], sh[4], sh[5], x[4], x[5]);
-                fma_bf16x2_f32(v.w, sc16[3], sh[6], sh[7], x[6], x[7]);
+                if constexpr (kBf) {
+                  fma_bf16x2_f32(v.x, sc16[0], sh[0], sh[1], x[0], x[1]);
+                  fma_bf16x2_f32(v.y, sc16[1], sh[2], sh[3], x[2], x[3]);
+                  fma_bf16x2_f32(v.z, sc16[2], sh[4], sh[5], x[4], x[5]);
+                  fma_bf16x2_f32(v.w, sc16[3], sh[6], sh[7], x[6], x[7]);
+                } else {
+                  fma_f16x2_f32(v.x, sc16[0], sh[0], sh[1], x[0], x[1]);
+                  fma_f16x2_f32(v.y, sc16[1], sh[2], sh[3], x[2], x[3]);
+                  fma_f16x2_f32(v.z, sc16[2], sh[4], sh[5], x[4], x[5]);
+                  fma_f16x2_f32(v.w, sc16[3], sh[6], sh[7], x[6], x[7]);
+                }
               } else {
                 float y[8];
                 if constexpr (sizeof(In) == 4) {
@@ -566,7 +579,7 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
               if constexpr (!k16) mx = fmaxf(mx, fmaxf(fabsf(x[2 * e]), fabsf(x[2 * e + 1])));
               h[e] = pack_f16x2(x[2 * e], x[2 * e + 1]);
               float r0, r1;
-              if constexpr (std::is_same<In, __nv_bfloat16>::value) {
+              if constexpr (k16) {
                 resid_f16x2(h[e], x[2 * e], x[2 * e + 1], r0, r1);
               } else {
                 unpack_f16x2(h[e], r0, r1);

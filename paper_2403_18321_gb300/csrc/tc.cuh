@@ -136,6 +136,16 @@ __device__ __forceinline__ bool f16x2_has_inf(uint32_t v) {
   const uint32_t a = v & 0x7fff7fffu;
   return (a & 0xffffu) == 0x7c00u || (a >> 16) == 0x7c00u;
 }
+// The same for a packed FP16 pair y and packed FP16 scales s.
+__device__ __forceinline__ void fma_f16x2_f32(uint32_t y, uint32_t s, float c0, float c1,
+                                              float& x0, float& x1) {
+  asm("{\n .reg .b16 y0, y1, s0, s1;\n mov.b32 {y0, y1}, %2;\n mov.b32 {s0, s1}, %3;\n"
+      " fma.rn.f32.f16 %0, y0, s0, %4;\n fma.rn.f32.f16 %1, y1, s1, %5;\n}"
+      : "=f"(x0), "=f"(x1)
+      : "r"(y), "r"(s), "f"(c0), "f"(c1));
+}
+// FP16 bits of 2^e (-14 <= e <= 15: the normal range)
+__device__ __forceinline__ uint32_t f16_pow2(int e) { return (uint32_t)(e + 15) << 10; }
 // BF16 bits of 2^e (|e| <= 126)
 __device__ __forceinline__ uint32_t bf16_pow2(int e) { return (uint32_t)(e + 127) << 7; }
 

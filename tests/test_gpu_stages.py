@@ -164,3 +164,24 @@ def test_mix_range_guard_recomputes_on_simt(gbpca_lib):
     C_ref = oracle.covariance(Y, mu_ref)
     assert np.abs(mu.cpu().numpy() - mu_ref).max() / np.abs(mu_ref).max() <= MU_TOL["p32"]
     assert np.abs(C.cpu().numpy() - C_ref).max() / np.abs(C_ref).max() <= COV_TOL["p32"]
+
+
+@pytest.mark.gpu
+def test_mix_fp16_band_with_tiny_spread(gbpca_lib):
+    """An FP16 band whose values differ only in the last bits of 0.5 gets a
+    power-of-two scale beyond FP16's normal range (2^16 and more): the
+    converters then widen those values instead of scaling them in FP16, and
+    the fit still matches the oracle."""
+    g = gbpca_lib
+    cube = synth.linear_mixing(seed=23, rows=41, cols=43, bands=48, endmembers=5)
+    Y = cube.Y.copy()
+    rng = np.random.default_rng(5)
+    Y[:, 9] = 0.5 + 2.0 ** -11 * rng.integers(-1, 2, size=Y.shape[0])   # three FP16 values
+    Yd = torch.from_numpy(Y).to(torch.float16)
+    Yh = Yd.float().numpy().astype(np.float64)
+    mu, ev, V, Q, info = g.fit(Yd.cuda(), cube.k, precision="mix")
+    torch.cuda.synchronize()
+    assert info["status"] == 0 and info["cov_fallback"] == 0 and info["proj_fallback"] == 0, info
+    ref = oracle.pca_fit(Yh, cube.k, tol=1e-14)
+    compare((mu.cpu().numpy(), ev.cpu().numpy(), V.cpu().numpy(),
+             Q.cpu().numpy().astype(np.float64)), ref, cube.k, "mix")
