@@ -222,7 +222,10 @@ k_bwd_dy_tc(const __grid_constant__ CUtensorMap xmap, int xtma, const In* __rest
   } else {
     // ------------------------------------------------------------ converters
     const int ct = tid - 64;
-    const int r = ct >> 2, kg = ct & 3;                  // pixel row, 8-wide K group
+    // pixel row and 8-wide K group: the 8 lanes of a quarter warp take eight
+    // rows of one K group, so that their 16-byte stores fill one core matrix
+    // (all 32 banks) and their reads of a swizzled row hit 8 distinct units
+    const int r = ((ct >> 5) << 3) | (ct & 7), kg = (ct >> 3) & 3;
     const uint32_t aoff = (uint32_t)((r >> 3) * (int)kSBO + kg * 128 + (r & 7) * 16);
     int q = 0, tl = 0;
     bool ok = true;
