@@ -228,6 +228,35 @@ int pca_combine_moments(int parts, const int64_t *n, const double *mu_parts,
                         const double *C_parts, int B, double *mu, double *C, void *stream);
 
 /*
+ * pca_shifted_sums / pca_moments_from_sums -- the same exchange as ONE sum of
+ * a vector whose length does not grow with the number of shards, so that a
+ * pixel-sharded fit needs a single all-reduce (the manycore version of the
+ * paper likewise adds the partial products of its two I/O halves, Sec. 5).
+ * Every shard uses the same shift s [B] (e.g. the mean of shard 0, sent to
+ * the others first), which keeps the sums free of cancellation.
+ *   sums layout (FP64, device, PCA_SUMS_LEN(B) = 1 + B + B(B+1)/2 values):
+ *     sums[0]            n, the shard's pixel count (exact up to 2^53)
+ *     sums[1 + b]        S1_b  = n (mu_b - s_b)
+ *     sums[1 + B + t]    S2_ij = (n - 1) C_ij + n (mu_i - s_i)(mu_j - s_j),
+ *                        t running over i <= j row by row (upper triangle)
+ *   Summed over the shards these are n, sum (y - s) and sum (y - s)(y - s)^T of
+ *   the whole cube.
+ * pca_shifted_sums: n >= 1 (host), mu [B], C [B][B] (full symmetric, as
+ *   pca_covariance returns them; 0 for a one-pixel shard) and s [B], all FP64
+ *   on the device; writes sums.
+ * pca_moments_from_sums: from the summed vector and the same s, writes
+ *   mu = s + S1/n and C = (S2 - S1 S1^T / n) / (n - 1), full symmetric [B][B]
+ *   (C is 0 when the summed n is below 2).
+ * Outputs must not overlap the inputs.  1 <= B <= 256 and non-NULL pointers,
+ * else PCA_ERR_ARG.  No workspace; enqueued on `stream`, no synchronisation.
+ */
+#define PCA_SUMS_LEN(B) (1 + (B) + (B) * ((B) + 1) / 2)
+int pca_shifted_sums(int64_t n, const double *mu, const double *C, const double *s, int B,
+                     double *sums, void *stream);
+int pca_moments_from_sums(const double *sums, const double *s, int B, double *mu, double *C,
+                          void *stream);
+
+/*
  * pca_project_noalloc -- pca_project for callers that cannot allocate.  (No
  * counterpart in the paper.)  Some callers cannot hand the library a
  * workspace: code running while a CUDA graph is captured, plug-ins whose

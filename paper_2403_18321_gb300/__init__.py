@@ -35,7 +35,8 @@ EXPORTS = ("pca_workspace_size", "pca_fit", "pca_covariance", "pca_eigh", "pca_p
            "pca_batch_destroy", "pca_fit_batched", "pca_batch_kernel_launches",
            "pca_combine_moments", "pca_bsq_to_bip", "pca_tuning_defaults", "pca_set_tuning",
            "pca_get_tuning", "pca_batch_jacobi_ctas", "pca_batch_plan_counts",
-           "pca_fit_host_workspace_size", "pca_fit_host")
+           "pca_fit_host_workspace_size", "pca_fit_host", "pca_shifted_sums",
+           "pca_moments_from_sums")
 STAGES = ("covariance", "cov_finalize", "jacobi", "empty", "compact", "refine", "sort_sign",
           "project")
 
@@ -164,6 +165,10 @@ def load(build_if_missing: bool = False):
     lib.pca_fit_batched.restype = i
     lib.pca_combine_moments.argtypes = [i, ctypes.POINTER(i64), P, P, i, P, P, P]
     lib.pca_combine_moments.restype = i
+    lib.pca_shifted_sums.argtypes = [i64, P, P, P, i, P, P]
+    lib.pca_shifted_sums.restype = i
+    lib.pca_moments_from_sums.argtypes = [P, P, i, P, P, P]
+    lib.pca_moments_from_sums.restype = i
     lib.pca_bsq_to_bip.argtypes = [P, i, i64, i, P, P]
     lib.pca_bsq_to_bip.restype = i
     TuP = ctypes.POINTER(Tuning)
@@ -647,6 +652,45 @@ def combine_moments(counts, mus, Cs, stream=None):
     return mu, C
 
 
+def sums_length(B: int) -> int:
+    """Length of the vector pca_shifted_sums writes: 1 + B + B(B+1)/2."""
+    return 1 + B + B * (B + 1) // 2
+
+
+def shifted_sums(n, mu, C, s, stream=None):
+    """(n, S1, S2 upper) of one shard about the common shift s, as one FP64
+    vector of sums_length(B) values on the device (pca_shifted_sums)."""
+    import torch
+    mu, C, s = (t.to(torch.float64).contiguous() for t in (mu, C, s))
+    B = mu.shape[0]
+    sums = torch.empty(sums_length(B), dtype=torch.float64, device=mu.device)
+    st = stream if stream is not None else torch.cuda.current_stream(mu.device)
+    _check_rc(load().pca_shifted_sums(int(n), ctypes.c_void_p(mu.data_ptr()),
+                                      ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(s.data_ptr()),
+                                      B, ctypes.c_void_p(sums.data_ptr()),
+                                      ctypes.c_void_p(st.cuda_stream)))
+    return sums
+
+
+def moments_from_sums(sums, s, stream=None):
+    """(mu [B], C [B, B]) of the cube from the shards' summed shifted sums
+    (pca_moments_from_sums)."""
+    import torch
+    sums, s = sums.to(torch.float64).contiguous(), s.to(torch.float64).contiguous()
+    B = s.shape[0]
+    if sums.numel() != sums_length(B):
+        raise ValueError("sums has the wrong length for B")
+    mu = torch.empty(B, dtype=torch.float64, device=s.device)
+    C = torch.empty(B, B, dtype=torch.float64, device=s.device)
+    st = stream if stream is not None else torch.cuda.current_stream(s.device)
+    _check_rc(load().pca_moments_from_sums(ctypes.c_void_p(sums.data_ptr()),
+                                           ctypes.c_void_p(s.data_ptr()), B,
+                                           ctypes.c_void_p(mu.data_ptr()),
+                                           ctypes.c_void_p(C.data_ptr()),
+                                           ctypes.c_void_p(st.cuda_stream)))
+    return mu, C
+
+
 class _LibraryOps:
     """The stages of a pixel-sharded fit, on this rank's GPU."""
 
@@ -657,8 +701,11 @@ class _LibraryOps:
         mu, C, _ = covariance(cube, self.precision)
         return mu, C
 
-    def combine(self, counts, mus, Cs):
-        return combine_moments(counts, mus, Cs)
+    def shifted_sums(self, n, mu, C, s):
+        return shifted_sums(n, mu, C, s)
+
+    def from_sums(self, sums, s):
+        return moments_from_sums(sums, s)
 
     def eigh(self, C):
         ev, V, info = eigh(C, self.tol, self.sweeps_max, self.precision)
@@ -673,31 +720,29 @@ def fit_sharded(cube, k: int, tol: float = 1e-10, sweeps_max: int = 30, precisio
     """PCA of a cube whose pixels are split over the ranks of a torch.distributed
     group: `cube` is this rank's [N_r, B] slice (contiguous and 16-byte aligned,
     N_r >= 2; clone a slice of a larger cube whose first row does not start on a
-    16-byte boundary).  Each rank computes its band
-    means and covariance; the ranks all-gather (N_r, mu_r, C_r) and pool them
-    (pca_combine_moments); rank 0 of the group solves the pooled covariance and
-    broadcasts eigenvalues and eigenvectors, so that every rank holds the same
-    bits; each rank projects its own pixels.  Returns (mu, eigvals, eigvecs,
-    proj of this rank's pixels, info of the eigen-solve on rank 0 or None).
-    `ops` replaces the four stages (used to test the exchange on CPU ranks)."""
+    16-byte boundary).  Each rank computes its band means and covariance; rank 0
+    of the group sends its mean as the common shift s; every rank turns its
+    moments into (n, S1, S2) about s (pca_shifted_sums) and ONE all-reduce sums
+    them -- 1 + B + B(B+1)/2 FP64 values whatever the number of ranks; every rank
+    recovers the pooled mean and covariance (pca_moments_from_sums).  Rank 0
+    solves the pooled covariance and broadcasts eigenvalues and eigenvectors, so
+    that every rank holds the same bits; each rank projects its own pixels.
+    Returns (mu, eigvals, eigvecs, proj of this rank's pixels, info of the
+    eigen-solve on rank 0 or None).  `ops` replaces the stages (used to test the
+    exchange on CPU ranks)."""
     import torch
     import torch.distributed as dist
     ops = ops if ops is not None else _LibraryOps(precision, tol, sweeps_max)
-    world = dist.get_world_size(group)
     rank = dist.get_rank(group)
     N, B = cube.shape
     mu_r, C_r = ops.moments(cube)
     dev = mu_r.device
-    n_r = torch.tensor([N], dtype=torch.int64, device=dev)
-    ns = [torch.empty_like(n_r) for _ in range(world)]
-    mus = [torch.empty_like(mu_r) for _ in range(world)]
-    Cs = [torch.empty_like(C_r) for _ in range(world)]
-    dist.all_gather(ns, n_r, group=group)
-    dist.all_gather(mus, mu_r.contiguous(), group=group)
-    dist.all_gather(Cs, C_r.contiguous(), group=group)
-    counts = [int(x.item()) for x in ns]
-    mu, C = ops.combine(counts, torch.stack(mus), torch.stack(Cs))
     root = dist.get_global_rank(group, 0) if group is not None else 0
+    s = mu_r.clone() if rank == 0 else torch.empty(B, dtype=torch.float64, device=dev)
+    dist.broadcast(s, root, group=group)
+    sums = ops.shifted_sums(N, mu_r, C_r, s)
+    dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=group)
+    mu, C = ops.from_sums(sums, s)
     info = None
     if rank == 0:
         ev, V, info = ops.eigh(C)

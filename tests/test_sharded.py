@@ -1,8 +1,9 @@
-"""Pixel-sharded fit (fit_sharded): the exchange of per-rank moments, the
-pooled eigen-solve on rank 0 and its broadcast, on CPU ranks (gloo, world
-sizes 2 and 3, uneven shards including a one-pixel shard).  The four stages
-are the FP64 oracle's here, so every rank must reproduce the oracle's fit of
-the whole cube; the GPU pooling kernel has its own test in
+"""Pixel-sharded fit (fit_sharded): the exchange of per-rank moments (the
+common shift from rank 0, one all-reduce of shifted sums), the pooled
+eigen-solve on rank 0 and its broadcast, on CPU ranks (gloo, world sizes 2
+and 3, uneven shards including a one-pixel shard).  The stages are the FP64
+oracle's here, so every rank must reproduce the oracle's fit of the whole
+cube; the GPU kernels of the exchange have their own tests in
 test_gpu_sharded.py."""
 import os
 import socket
@@ -32,15 +33,23 @@ class OracleOps:
         C = oracle.covariance(Y) if Y.shape[0] > 1 else np.zeros((Y.shape[1], Y.shape[1]))
         return torch.from_numpy(mu), torch.from_numpy(C)
 
-    def combine(self, counts, mus, Cs):
-        # the pooling rule written out for the CPU ranks
+    def shifted_sums(self, n, mu, C, s):
+        # (n, S1, S2 upper) about the common shift, written out for the CPU ranks
         import torch
-        n = np.asarray(counts, dtype=np.float64)
-        M, S = mus.numpy(), Cs.numpy()
-        mu = (n[:, None] * M).sum(0) / n.sum()
-        D = M - mu[None, :]
-        C = (((n - 1.0)[:, None, None] * S).sum(0) + np.einsum("g,gi,gj->ij", n, D, D)) / (n.sum() - 1.0)
-        return torch.from_numpy(mu), torch.from_numpy(C)
+        d = mu.numpy() - s.numpy()
+        S2 = (n - 1.0) * C.numpy() + n * np.outer(d, d)
+        iu = np.triu_indices(len(d))
+        return torch.from_numpy(np.concatenate([[float(n)], n * d, S2[iu]]))
+
+    def from_sums(self, sums, s):
+        import torch
+        v, sv = sums.numpy(), s.numpy()
+        B = len(sv)
+        n, S1 = v[0], v[1:1 + B]
+        S2 = np.zeros((B, B))
+        S2[np.triu_indices(B)] = v[1 + B:]
+        S2 = S2 + np.triu(S2, 1).T
+        return torch.from_numpy(sv + S1 / n), torch.from_numpy((S2 - np.outer(S1, S1) / n) / (n - 1.0))
 
     def eigh(self, C):
         import torch
