@@ -520,14 +520,18 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
         unsigned char* hi = ops + (size_t)(o * 2) * kOpBytes;
         unsigned char* lo = hi + kOpBytes;
         uint32_t lo_bits = 0;    // OR of this thread's lo parts in this chunk
-        if (act) {
+        // the units of this chunk; FM: the common case (a full chunk of a 16-bit
+        // cube whose scales FP16 holds) compiled on its own, without the
+        // per-unit tests of the other paths
+        auto units = [&](auto FM_) {
+          constexpr bool FM = decltype(FM_)::value;
 #pragma unroll
           for (int u = 0; u < kRowsPT; ++u) {
             const int pp = pr + kRowStep * u;
             float x[8];
-            if (fast) {
+            if (FM || fast) {
               const In* src = st + pp * B + b0;
-              if (k16 && mixfma) {
+              if (FM || (k16 && mixfma)) {
                 // the 16-bit pairs enter the FMA as they are
                 const uint4 v = *reinterpret_cast<const uint4*>(src);
                 if constexpr (kBf) {
@@ -602,6 +606,10 @@ k_syrk_tc(const __grid_constant__ TcTile one, const TileDesc* __restrict__ T,
             }
             lo_bits |= lu;
           }
+        };
+        if (act) {
+          if (k16 && fast && mixfma) units(std::integral_constant<bool, true>{});
+          else units(std::integral_constant<bool, false>{});
         }
         const int any_lo = __any_sync(kFull, lo_bits != 0u);
         fence_proxy_async();
