@@ -747,28 +747,9 @@ def run_c2(args, g, dev, peaks, peak_src, sampler, world, rank):
                        out=hout, sync=False)
             torch.cuda.current_stream(dev).synchronize()
 
-        for _ in range(args.warmup):
-            e2e_step()
-        barrier(world)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        total = 0.0
-        with sampler:
-            for _ in range(args.steps):
-                e0.record()
-                e2e_step()
-                e1.record()
-                e1.synchronize()
-                total += e0.elapsed_time(e1) / 1e3
-        total = max_over_ranks(total, world)
-        e2e = {"value": aggregate(units, args.steps, total, world), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": total / args.steps * 1e3,
-               "how": "pca_fit_host: pinned host cube copied in 16 pixel ranges, each range's "
-                      "covariance as its copy lands, the ranges' moments pooled, eigen stage, "
-                      "each range's projection copied back while the next is projected; "
-                      "synchronise"}
-        # the same through the device-resident API with the copies around it, one stream
+        # the same through the device-resident API with the copies around it, one
+        # stream; timed step by step in alternation with the pca_fit_host steps, so
+        # that both see the same state of the (shared) host memory path
         Yin = torch.empty_like(Y)
         ws = g.make_workspace(N, B, k, 1, args.precision, dev)
         outs = (torch.empty(B, dtype=torch.float64, device=dev),
@@ -785,14 +766,32 @@ def run_c2(args, g, dev, peaks, peak_src, sampler, world, rank):
             torch.cuda.current_stream(dev).synchronize()
 
         for _ in range(args.warmup):
+            e2e_step()
             serial_step()
-        t_serial = 0.0
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        total, t_serial = 0.0, 0.0
         for _ in range(args.steps):
+            with sampler:
+                e0.record()
+                e2e_step()
+                e1.record()
+                e1.synchronize()
+            total += e0.elapsed_time(e1) / 1e3
             e0.record()
             serial_step()
             e1.record()
             e1.synchronize()
             t_serial += e0.elapsed_time(e1) / 1e3
+        total = max_over_ranks(total, world)
+        e2e = {"value": aggregate(units, args.steps, total, world), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": total / args.steps * 1e3,
+               "how": "pca_fit_host: pinned host cube copied in 16 pixel ranges, each range's "
+                      "covariance as its copy lands, the ranges' moments pooled, eigen stage, "
+                      "each range's projection copied back while the next is projected; "
+                      "synchronise"}
         t_serial = max_over_ranks(t_serial, world)
         e2e["serial_copies_ms_per_step"] = t_serial / args.steps * 1e3
         del Yh, Yin, ws, hb
