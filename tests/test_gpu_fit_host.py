@@ -1,7 +1,8 @@
 """pca_fit_host (host cube in, host results out, copies overlapped with the
 stages in pixel ranges) against the FP64 oracle, through the C ABI: several
 ranges with a ragged last one, a last range that would hold one pixel, BF16
-input, pageable input memory, and no projection."""
+input, pageable input memory, and no projection; two calls in flight on two
+streams (each with its own buffers) give the results of calls made one by one."""
 import numpy as np
 import pytest
 import torch
@@ -51,3 +52,30 @@ def test_fit_host_matches_fit_and_skips_projection(gbpca_lib):
     mu2, ev2, V2, _, _ = g.fit(Y.cuda(), 5, precision="p32")
     assert np.abs(mu.numpy() - mu2.cpu().numpy()).max() <= 1e-6 * np.abs(mu2.cpu().numpy()).max()
     assert np.abs(ev.numpy()[:5] - ev2.cpu().numpy()[:5]).max() <= 2e-5 * ev2[0].item()
+
+
+@pytest.mark.gpu
+def test_two_fits_in_flight_on_two_streams(gbpca_lib):
+    """Cubes of a stream of scenes: calls alternate between two CUDA streams with
+    their own device buffers and host outputs and nothing waits in between, so
+    the copies of one call overlap the other's stages.  Every call must give the
+    bits a call made on its own gives."""
+    g = gbpca_lib
+    cubes = [_cube(150_000, 48, 40 + i, torch.bfloat16)[1].pin_memory() for i in range(2)]
+    k = 6
+    ref = [g.fit_host(Yh, k, tol=1e-12, precision="mix") for Yh in cubes]
+    streams = (torch.cuda.Stream(), torch.cuda.Stream())
+    bufs = [g.HostFit(150_000, 48, k, torch.bfloat16, "mix") for _ in range(2)]
+    outs = [(torch.empty(48, dtype=torch.float64, pin_memory=True),
+             torch.empty(48, dtype=torch.float64, pin_memory=True),
+             torch.empty(48, 48, dtype=torch.float64, pin_memory=True),
+             torch.empty(150_000, k, dtype=torch.float32, pin_memory=True)) for _ in range(2)]
+    for rnd in range(3):
+        for i in range(2):
+            g.fit_host(cubes[i], k, tol=1e-12, precision="mix", buffers=bufs[i], out=outs[i],
+                       sync=False, stream=streams[i])
+        for s in streams:
+            s.synchronize()
+        for i in range(2):
+            for a, b in zip(outs[i], ref[i][:4]):
+                assert torch.equal(a, b), (rnd, i)
