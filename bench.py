@@ -635,15 +635,26 @@ def timed_fits(g, Y, k, prec, steps, warmup, world=1, sampler=None, profile=Fals
     e1 = torch.cuda.Event(enable_timing=True)
     total = 0.0
     with (sampler if sampler is not None else _Null()):
-        for _ in range(steps):
-            if flush is not None:
-                flush.fill_(1)
+        if flush is None:
+            # the K steps back to back between two synchronisations (inputs
+            # larger than L2)
             e0.record()
-            g.fit(Y, k, tol=tol, sweeps_max=sweeps_max, precision=prec, out=out, workspace=ws,
-                  sync=False)
+            for _ in range(steps):
+                g.fit(Y, k, tol=tol, sweeps_max=sweeps_max, precision=prec, out=out, workspace=ws,
+                      sync=False)
             e1.record()
             e1.synchronize()
-            total += e0.elapsed_time(e1) / 1e3
+            total = e0.elapsed_time(e1) / 1e3
+        else:
+            # an L2 flush before each step, outside the timed interval
+            for _ in range(steps):
+                flush.fill_(1)
+                e0.record()
+                g.fit(Y, k, tol=tol, sweeps_max=sweeps_max, precision=prec, out=out,
+                      workspace=ws, sync=False)
+                e1.record()
+                e1.synchronize()
+                total += e0.elapsed_time(e1) / 1e3
     stages = g.profile_collect() if profile else []
     if profile:
         g.profile(False)
@@ -654,6 +665,53 @@ def timed_fits(g, Y, k, prec, steps, warmup, world=1, sampler=None, profile=Fals
     host = tuple(t.cpu().numpy().astype(np.float64) for t in out)
     del ws
     return total, stages, info, host
+
+
+def two_in_flight(g, Y, k, prec, steps, warmup, tol=1e-10, sweeps_max=30):
+    """A stream of fits of resident cubes with two in flight: fits alternate
+    between two CUDA streams, each with its own workspace and outputs, and
+    nothing waits between them, so one fit's Jacobi (one thread-block cluster)
+    runs beside the other's streaming kernels.  Returns seconds for `steps`
+    fits (CUDA events: the start on the current stream, the later of the two
+    streams' ends)."""
+    import torch
+    N, B = Y.shape
+    dev = Y.device
+    dt = g._dtype_code(Y)
+    sets = []
+    for _ in range(2):
+        ws = g.make_workspace(N, B, k, dt, prec, dev)
+        out = (torch.empty(B, dtype=torch.float64, device=dev),
+               torch.empty(B, dtype=torch.float64, device=dev),
+               torch.empty(B, B, dtype=torch.float64, device=dev),
+               torch.empty(N, k, dtype=torch.float32, device=dev))
+        sets.append((ws, out))
+    streams = (torch.cuda.Stream(dev), torch.cuda.Stream(dev))
+
+    def run(n):
+        cur = torch.cuda.current_stream(dev)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p0.record(cur)
+        for s_ in streams:
+            s_.wait_event(p0)
+        for i in range(n):
+            ws, out = sets[i % 2]
+            g.fit(Y, k, tol=tol, sweeps_max=sweeps_max, precision=prec, out=out, workspace=ws,
+                  sync=False, stream=streams[i % 2])
+        ends = []
+        for s_ in streams:
+            pe = torch.cuda.Event(enable_timing=True)
+            pe.record(s_)
+            ends.append(pe)
+        for pe in ends:
+            pe.synchronize()
+        return max(p0.elapsed_time(pe) for pe in ends) / 1e3
+
+    run(warmup)
+    torch.cuda.synchronize()
+    t = run(steps)
+    del sets
+    return t
 
 
 def mean_stages(g, stages):
@@ -676,8 +734,12 @@ def run_c2(args, g, dev, peaks, peak_src, sampler, world, rank):
     units = N * B
     s_in = 2
     res = {}
-    t, stages, info, host = timed_fits(g, Y, k, args.precision, args.steps, args.warmup, world,
-                                       sampler, profile=True)
+    # stage times from a profiled pass (CUDA events between the stages), the
+    # step time from a pass without them
+    _, stages, _, _ = timed_fits(g, Y, k, args.precision, args.steps, args.warmup, world,
+                                 None, profile=True)
+    t, _, info, host = timed_fits(g, Y, k, args.precision, args.steps, args.warmup, world,
+                                  sampler, profile=False)
     t = max_over_ranks(t, world)
     res["headline"] = {"seconds": t, "stages": stages, "info": info, "host": host}
     forms = {args.precision: {"ms": t / args.steps * 1e3,
@@ -693,6 +755,24 @@ def run_c2(args, g, dev, peaks, peak_src, sampler, world, rank):
         forms[prec] = {"ms": tp / steps * 1e3, "value": aggregate(units, steps, tp, world),
                        "sweeps": inf["sweeps"], "steps_timed": steps,
                        "stage_ms": mean_stages(g, st)}
+    # a stream of resident cubes, two fits in flight, without and with the SMs
+    # that the streaming kernels leave to the other fit's Jacobi cluster
+    tif = {}
+    for reserve in (0, g.jacobi_sms(B)):
+        prev = g.set_tuning({**g.tuning(), "stream_sms_reserve": int(reserve)})
+        try:
+            t2 = two_in_flight(g, Y, k, args.precision, args.steps, args.warmup)
+        finally:
+            g.set_tuning(prev)
+        t2 = max_over_ranks(t2, world)
+        tif[f"sms_reserved_{reserve}"] = {"ms_per_fit": t2 / args.steps * 1e3,
+                                          "value": aggregate(units, args.steps, t2, world)}
+    res["two_in_flight"] = {"unit": UNIT, **tif,
+                            "how": "fits of the resident cube alternate between two CUDA streams, "
+                                   "each with its own workspace and outputs, nothing waits "
+                                   "between them; the tensor-core covariance and projection "
+                                   "optionally leave the Jacobi cluster's SMs free "
+                                   "(stream_sms_reserve)"}
     # the FP16 variant of the cube (mixed form)
     c16 = synth.planted_spectrum_device(dev, dtype="fp16")
     tf, st, inf, host16 = timed_fits(g, c16.Y, k, "mix", args.steps, 2, world, profile=True)
@@ -1168,6 +1248,7 @@ def main(argv=None):
             "step_hbm_frac": (2 * c2["N"] * c2["B"] * 2 + 4 * c2["N"] * c2["k"])
             / (t_head / args.steps) / 1e9 / peaks["hbm_gbs"],
             "cpu_baseline": cpu, "oracle_timings": timings, "e2e": c2["e2e"],
+            "two_in_flight": c2.get("two_in_flight"),
             "gpu_launches": launches, "clocks": sampler.summary(),
             "scenes": scenes, "mixing_100x100x128": c0, "differentiation": diff,
             "batched": batched, "paper_shapes_k1": shapes}

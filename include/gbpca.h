@@ -421,6 +421,14 @@ int pca_fit_batched(int ntiles, const pca_tile *tiles, pca_dtype dtype, double t
  *                  the converted-operand ring (2..6) and of the TMA ring of raw
  *                  cube chunks (2..8); 0 = as many as shared memory holds, with
  *                  3 operand stages first (default).
+ * stream_sms_reserve  SMs (0..64, default 0) that the single-cube tensor-core
+ *                  covariance and projection (MIX) leave free: their persistent
+ *                  grids hold one CTA per SM and would otherwise wait for the
+ *                  SMs a Jacobi cluster of a second fit, enqueued on another
+ *                  stream, holds (8 for more than 128 bands).  Set it when fits
+ *                  run two at a time, before sizing their workspaces
+ *                  (pca_workspace_size reads it; a smaller workspace gives
+ *                  PCA_ERR_WORKSPACE).
  *
  * pca_tuning_defaults fills *t with the defaults.  pca_set_tuning installs *t
  * (NULL: the defaults); PCA_ERR_ARG, and no change, for a value out of range.
@@ -438,6 +446,7 @@ typedef struct {
   int proj_tc_stages;
   int proj_tc_raw_stages;
   int tc_slot_chunks_batch;
+  int stream_sms_reserve;
 } pca_tuning;
 void pca_tuning_defaults(pca_tuning *t);
 int pca_set_tuning(const pca_tuning *t);

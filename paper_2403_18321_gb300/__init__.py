@@ -66,7 +66,8 @@ class Tuning(ctypes.Structure):
                 ("batch_cov_tc_fixed", ctypes.c_double), ("batch_proj_fixed", ctypes.c_double),
                 ("batch_cov_simt_fixed", ctypes.c_double),
                 ("batch_simt_items_per_sm", ctypes.c_int), ("proj_tc_stages", ctypes.c_int),
-                ("proj_tc_raw_stages", ctypes.c_int), ("tc_slot_chunks_batch", ctypes.c_int)]
+                ("proj_tc_raw_stages", ctypes.c_int), ("tc_slot_chunks_batch", ctypes.c_int),
+                ("stream_sms_reserve", ctypes.c_int)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -94,7 +94,9 @@ Layout make_layout(int64_t N, int B, int k, pca_dtype dt, pca_precision prec, in
   Layout L{};
   const int Bp = round_even(B);
   if (prec == PCA_PREC_MIX) {
-    L.tc_ctas = (int)std::min<int64_t>(num_sms, std::max<int64_t>(1, (N + 127) / 128));
+    // one persistent CTA per SM, less the SMs left to a concurrent fit's Jacobi
+    const int use = std::max(1, num_sms - tuning().stream_sms_reserve);
+    L.tc_ctas = (int)std::min<int64_t>(use, std::max<int64_t>(1, (N + 127) / 128));
     // every CTA gets the same number of slots, each at most tc_slot_chunks() long
     const int64_t nchunk = (N + 31) / 32, cap = tc_slot_chunks(dt);
     const int64_t per_cta = (nchunk + L.tc_ctas - 1) / L.tc_ctas;

@@ -665,6 +665,7 @@ cudaError_t ptc_typed(const PtcArgs& a, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  sms = sms - tu.stream_sms_reserve > 1 ? sms - tu.stream_sms_reserve : 1;  // SMs left to a concurrent fit
   const int64_t ntiles = (a.N + kTM - 1) / kTM;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
   auto kern = tiled ? k_project_tc<In, true> : k_project_tc<In, false>;

@@ -23,6 +23,7 @@ pca_tuning defaults() {
   t.batch_simt_items_per_sm = 4;
   t.proj_tc_stages = 0;
   t.proj_tc_raw_stages = 0;
+  t.stream_sms_reserve = 0;
   return t;
 }
 
@@ -42,6 +43,7 @@ bool valid(const pca_tuning& t) {
   if (t.proj_tc_stages != 0 && (t.proj_tc_stages < 2 || t.proj_tc_stages > 6)) return false;
   if (t.proj_tc_raw_stages != 0 && (t.proj_tc_raw_stages < 2 || t.proj_tc_raw_stages > 8))
     return false;
+  if (t.stream_sms_reserve < 0 || t.stream_sms_reserve > 64) return false;
   return t.batch_simt_items_per_sm >= 1 && t.batch_simt_items_per_sm <= 64;
 }
 

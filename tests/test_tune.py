@@ -61,7 +61,28 @@ def test_invalid_tuning_is_rejected_and_leaves_the_old_values():
         g.set_tuning({"batch_jacobi_ctas": [9] * 8})
     with pytest.raises(g.PCAError):
         g.set_tuning({"tc_slot_chunks": 0})
+    for bad in (-1, 65):
+        with pytest.raises(g.PCAError):
+            g.set_tuning({"stream_sms_reserve": bad})
     assert g.tuning() == before
+
+
+def test_sm_reserve_shrinks_the_streaming_grid_in_the_workspace_plan():
+    """stream_sms_reserve takes SMs from the persistent covariance grid: a BF16
+    cube of this size gives every CTA one accumulation run (at most 1024 chunks),
+    so the grid's CTA count is its count of partial slots, which the workspace
+    size reads (host only, no GPU)."""
+    assert g.tuning()["stream_sms_reserve"] == 0
+    N, B, k = 4_194_304, 224, 20
+    base = g.workspace_size(N, B, k, 1, "mix")
+    try:
+        g.set_tuning({"stream_sms_reserve": 8})
+        assert g.tuning()["stream_sms_reserve"] == 8
+        reserved = g.workspace_size(N, B, k, 1, "mix")
+    finally:
+        g.set_tuning(None)
+    assert reserved < base
+    assert g.workspace_size(N, B, k, 1, "mix") == base
 
 
 def test_cluster_request_is_raised_to_a_shape_that_holds_the_matrix():
