@@ -14,6 +14,11 @@ cube, and the FP16 variant of the cube, each with its error against the FP64
 oracle.  The same line carries the scene-shaped cubes (610x340x103 and
 512x217x224, FP32, k = 10), the 100x100x128 mixing cube, the batched form
 (256 tiles), the differentiation form and the paper's k = 1 table shapes.
+`value` fits one cube at a time (the K steps back to back between two
+synchronisations); `two_in_flight` gives the same fits two at a time on two
+streams, and `e2e` the fits of a stream of host-resident cubes through
+pca_fit_host with two calls in flight (with the one-at-a-time figure beside
+it), every step copying its cube in and its results out.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
