@@ -55,27 +55,36 @@ def test_fit_host_matches_fit_and_skips_projection(gbpca_lib):
 
 
 @pytest.mark.gpu
-def test_two_fits_in_flight_on_two_streams(gbpca_lib):
+@pytest.mark.parametrize("reserve", [0, 8])
+def test_two_fits_in_flight_on_two_streams(gbpca_lib, reserve):
     """Cubes of a stream of scenes: calls alternate between two CUDA streams with
     their own device buffers and host outputs and nothing waits in between, so
     the copies of one call overlap the other's stages.  Every call must give the
-    bits a call made on its own gives."""
+    bits a call made on its own gives (also with SMs left to the other call's
+    Jacobi, stream_sms_reserve)."""
     g = gbpca_lib
-    cubes = [_cube(150_000, 48, 40 + i, torch.bfloat16)[1].pin_memory() for i in range(2)]
-    k = 6
-    ref = [g.fit_host(Yh, k, tol=1e-12, precision="mix") for Yh in cubes]
-    streams = (torch.cuda.Stream(), torch.cuda.Stream())
-    bufs = [g.HostFit(150_000, 48, k, torch.bfloat16, "mix") for _ in range(2)]
-    outs = [(torch.empty(48, dtype=torch.float64, pin_memory=True),
-             torch.empty(48, dtype=torch.float64, pin_memory=True),
-             torch.empty(48, 48, dtype=torch.float64, pin_memory=True),
-             torch.empty(150_000, k, dtype=torch.float32, pin_memory=True)) for _ in range(2)]
-    for rnd in range(3):
-        for i in range(2):
-            g.fit_host(cubes[i], k, tol=1e-12, precision="mix", buffers=bufs[i], out=outs[i],
-                       sync=False, stream=streams[i])
-        for s in streams:
-            s.synchronize()
-        for i in range(2):
-            for a, b in zip(outs[i], ref[i][:4]):
-                assert torch.equal(a, b), (rnd, i)
+    N, B, k = 150_000, 160, 6
+    cubes = [_cube(N, B, 40 + i, torch.bfloat16)[1].pin_memory() for i in range(2)]
+    prev = g.set_tuning({**g.tuning(), "stream_sms_reserve": reserve})
+    try:
+        ref = [g.fit_host(Yh, k, tol=1e-12, precision="mix") for Yh in cubes]
+        streams = (torch.cuda.Stream(), torch.cuda.Stream())
+        bufs = [g.HostFit(N, B, k, torch.bfloat16, "mix") for _ in range(2)]
+        outs = [(torch.empty(B, dtype=torch.float64, pin_memory=True),
+                 torch.empty(B, dtype=torch.float64, pin_memory=True),
+                 torch.empty(B, B, dtype=torch.float64, pin_memory=True),
+                 torch.empty(N, k, dtype=torch.float32, pin_memory=True)) for _ in range(2)]
+        for rnd in range(3):
+            for i in range(2):
+                g.fit_host(cubes[i], k, tol=1e-12, precision="mix", buffers=bufs[i], out=outs[i],
+                           sync=False, stream=streams[i])
+            for s in streams:
+                s.synchronize()
+            for i in range(2):
+                for a, b in zip(outs[i], ref[i][:4]):
+                    assert torch.equal(a, b), (rnd, i)
+    finally:
+        g.set_tuning(prev)
+    Y0 = cubes[0].float().numpy().astype(np.float64)
+    compare(tuple(t.numpy().astype(np.float64) for t in ref[0][:4]),
+            oracle.pca_fit(Y0, k, tol=1e-14), k, "mix")
