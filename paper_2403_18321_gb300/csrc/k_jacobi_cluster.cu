@@ -110,9 +110,25 @@ __device__ __forceinline__ float sqrt_est(float x) {
 // tau = (aqq - app)/(2 apq); an off-diagonal below 2^-24 sqrt(|app aqq|) is
 // dropped without rotating (c = 1, s = 0).  Returns the record of the pair:
 // (c, s) and the two diagonal values after the rotation and position swap.
+// With d = aqq - app and n = 2 apq the same root is
+// t = sgn(tau) |n| / (|d| + sqrt(d^2 + n^2)) (sgn 0 = +1): three dependent
+// reciprocal/root steps instead of four (the step's critical path runs
+// through this record).  Where d^2 + n^2 could leave the FP32 range (|d| or
+// |n| beyond 1e18, or both below 1e-18) the scale-free tau form is taken.
 __device__ __forceinline__ float4 pair_record(float app, float aqq, float apq) {
   const float thr = 5.9604645e-08f * sqrt_est(fabsf(app)) * sqrt_est(fabsf(aqq));
   if (!(fabsf(apq) > thr)) return make_float4(1.f, 0.f, aqq, app);
+  {
+    const float d = aqq - app, n = 2.f * apq;
+    const float ad = fabsf(d), an = fabsf(n);
+    if (ad < 1e18f && an < 1e18f && (ad > 1e-18f || an > 1e-18f)) {
+      const float q = fmaf(d, d, n * n);
+      float tt = an * rcp_nr(ad + q * rsqrt_nr(q));
+      tt = (d != 0.f && ((d < 0.f) != (n < 0.f))) ? -tt : tt;
+      const float c = rsqrt_nr(fmaf(tt, tt, 1.f));
+      return make_float4(c, tt * c, fmaf(tt, apq, aqq), fmaf(-tt, apq, app));
+    }
+  }
   const float tau = (aqq - app) * rcp_nr(2.f * apq);
   const float at = fabsf(tau);
   float tt;
@@ -155,6 +171,7 @@ struct Shared {
   int flag;
   int ovf;
   double off_rel, fro;
+  int escale;                // the matrix is held scaled by 2^-escale
 };
 
 // Record index of pair J = H q + t: row t of a 32-wide table, column q
@@ -307,13 +324,37 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
     return;
   }
 
+  // ---- the matrix is held scaled by 2^-E, with max_i |a_ii| in [2^(E-1), 2^E)
+  //      (every CTA reads the whole diagonal and forms the same E): squares
+  //      and products of entries then stay inside the FP32 range whatever the
+  //      covariance's scale (|a_ij| <= max a_ii for a covariance); the
+  //      eigenvalues and the norm are scaled back on output, the rotations
+  //      and eigenvectors do not depend on it
+  {
+    double m = 0.0;
+    for (int i = tid; i < B; i += kThreads) m = fmax(m, fabs(C[(size_t)i * B + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+    if (lane == 0) sh.wred[0][warp] = m;
+    __syncthreads();
+    if (tid == 0) {
+      double cm = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) cm = fmax(cm, sh.wred[0][w]);
+      int E = 0;
+      if (cm > 0.0 && isfinite(cm)) frexp(cm, &E);
+      sh.escale = E;
+    }
+    __syncthreads();
+  }
+  const int escale = sh.escale;
+  const double dscale = ldexp(1.0, -escale);
   // ---- matrix rows, and records that reproduce the initial diagonal as the
   //      state after an odd step (slot 3) preceded by an even step (slot 2)
   for (int e = tid; e < nrows * Bp; e += kThreads) {
     const int i = R0 + e / Bp, j = e % Bp;
-    rows[e] = (i < B && j < B) ? (float)C[(size_t)i * B + j] : 0.f;
+    rows[e] = (i < B && j < B) ? (float)(C[(size_t)i * B + j] * dscale) : 0.f;
   }
-  auto d0 = [&](int i) { return i < B ? (float)C[(size_t)i * B + i] : 0.f; };
+  auto d0 = [&](int i) { return i < B ? (float)(C[(size_t)i * B + i] * dscale) : 0.f; };
   for (int J = tid; J < P; J += kThreads) {
     sh.cs[2][rix<H>(J)] = sh.cs[3][rix<H>(J)] = make_float2(1.f, 0.f);
     sh.dd[2][rix<H>(J)] = make_float2(d0(2 * J), d0(2 * J + 1));
@@ -675,13 +716,13 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
   if (rank == 0) {
     const int so = (gs + 3) % kSlots, se = (gs + 2) % kSlots;
     for (int x = tid; x < Bp; x += kThreads)
-      par(one, list).diag32[x] = ovf ? 0.f : diag_after_odd<H>(&sh, so, se, x, Bp);
+      par(one, list).diag32[x] = ovf ? 0.f : ldexpf(diag_after_odd<H>(&sh, so, se, x, Bp), escale);
     if (tid == 0) {
       par(one, list).hdr->sweeps = sweep;
       par(one, list).hdr->steps = sweep * Bp;
       par(one, list).hdr->tol_used = par(one, list).tol32;
       par(one, list).hdr->off_rel = sh.off_rel;
-      par(one, list).hdr->fro = sh.fro;
+      par(one, list).hdr->fro = ldexp(sh.fro, escale);
       if (status != PCA_OK) set_status(par(one, list).hdr, status);
     }
   }

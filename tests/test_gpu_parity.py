@@ -150,3 +150,22 @@ def test_plain_pca_config_exact(gbpca_lib, form):
     kc = min(cube.k, 4) if form == "p64" else cube.k
     mu, lam, V, Q = out
     compare((mu, lam, V, Q[:, :kc]), ref, kc, form)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("p2", [-40, 40])
+def test_cube_scaled_by_a_power_of_two(gbpca_lib, form, p2):
+    """A cube scaled by 2^p2 (values near 1e-12 or 1e12, covariance entries near
+    1e-26 or 1e22) fits like the unscaled one: the Jacobi's rotation angles are
+    formed from differences and products of covariance entries, whose squares
+    would leave the FP32 range at these scales (the scale-free form is taken
+    there).  Eigenvalues scale by 2^(2 p2), eigenvectors and the projection's
+    parity with the oracle are unchanged."""
+    cube = synth.linear_mixing(seed=91, rows=30, cols=40, bands=64, endmembers=5)
+    Ys = (cube.Y.astype(np.float64) * 2.0 ** p2).astype(np.float32)
+    k = 4
+    ref = oracle.pca_fit(Ys.astype(np.float64), k, tol=1e-14)
+    out, info = run(gbpca_lib, Ys, k, form)
+    assert info["status"] == 0, info
+    compare(out, ref, k, form)
