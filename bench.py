@@ -550,7 +550,7 @@ def fit_errors(gpu, ref, k, form):
     """Errors of one fit against the oracle's: eigenvalues per eigenvalue
     (separated components i <= k) and relative to lam_1, projection per
     component against that component's own scale; which components miss the
-    targets (spec: MIX 2e-5, P64 1e-10 per eigenvalue; 1e-4 projection)."""
+    targets (MIX 2e-5, P64 1e-10 per eigenvalue; 1e-4 projection)."""
     mu, lam, V, Q = gpu
     lam_ref = ref["lam"]
     l1 = abs(lam_ref[0])

@@ -29,7 +29,7 @@ it by perturbation theory of the symmetric eigenproblem:
       (max |Q_j| ~ sqrt(lam_j)) the error is at most
           q_bound_j = 1e-5 + 4 E_COV lam_1 max_{i != j} sqrt(lam_i/lam_j) / |lam_i - lam_j|
       (1e-5: the FP32 arithmetic of the projection kernel; 4: the spread of
-      max |Q_i| / sqrt(lam_i) over columns).  Where the benchmark spec's 1e-4 is
+      max |Q_i| / sqrt(lam_i) over columns).  Where the target of 1e-4 is
       reachable it is the bound; below, q_bound_j is, and the metrics say so.
 """
 import numpy as np
@@ -43,7 +43,7 @@ E_COV = {"p64": 1e-13, "mix": 5e-6, "p32": 2e-6}
 MU_TOL = {"p64": 1e-12, "mix": 1e-6, "p32": 1e-6}
 LAM_ALL_TOL = {"p64": 1e-7, "mix": 1e-4, "p32": 2e-3}
 ORTH_TOL = {"p64": 1e-11, "mix": 1e-6, "p32": 1e-4}
-Q_TOL = 1e-4           # the benchmark spec's projected-cube bound
+Q_TOL = 1e-4           # the stated projected-cube bound
 Q_ARITH = 1e-5         # FP32 arithmetic of the projection kernel, per column
 
 
