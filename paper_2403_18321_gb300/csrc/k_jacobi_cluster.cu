@@ -346,7 +346,8 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
     }
     __syncthreads();
   }
-  const double dscale = ldexp(1.0, -sh.escale);
+  const int escale = sh.escale;
+  const double dscale = ldexp(1.0, -escale);
   // ---- matrix rows, and records that reproduce the initial diagonal as the
   //      state after an odd step (slot 3) preceded by an even step (slot 2)
   for (int e = tid; e < nrows * Bp; e += kThreads) {
@@ -715,13 +716,13 @@ k_jacobi_cluster(const __grid_constant__ Params one, const Params* __restrict__ 
   if (rank == 0) {
     const int so = (gs + 3) % kSlots, se = (gs + 2) % kSlots;
     for (int x = tid; x < Bp; x += kThreads)
-      par(one, list).diag32[x] = ovf ? 0.f : ldexpf(diag_after_odd<H>(&sh, so, se, x, Bp), sh.escale);
+      par(one, list).diag32[x] = ovf ? 0.f : ldexpf(diag_after_odd<H>(&sh, so, se, x, Bp), escale);
     if (tid == 0) {
       par(one, list).hdr->sweeps = sweep;
       par(one, list).hdr->steps = sweep * Bp;
       par(one, list).hdr->tol_used = par(one, list).tol32;
       par(one, list).hdr->off_rel = sh.off_rel;
-      par(one, list).hdr->fro = ldexp(sh.fro, sh.escale);
+      par(one, list).hdr->fro = ldexp(sh.fro, escale);
       if (status != PCA_OK) set_status(par(one, list).hdr, status);
     }
   }
